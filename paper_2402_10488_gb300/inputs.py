@@ -1,0 +1,224 @@
+"""Seeded synthetic workloads for the parametric radiative transfer equation.
+
+This module is shared by the CPU oracle, the tests and ``bench.py``.  It only *describes*
+problems: mesh sizes, the angular rule's name and sizes, a material map, per-instance cross
+sections, a cellwise-constant isotropic source value and an isotropic inflow value per domain
+side.  It holds none of the method's arithmetic (no quadrature nodes, no DG projections, no
+matrices), so that the oracle and the CUDA path share inputs but no computation.
+
+Problem statement: steady one-group RTE with isotropic scattering, isotropic source G and
+isotropic inflow g (paper Sec. 2, Eq. (1); slab form Eq. (2)).  Cross sections are cellwise
+constant: each cell carries a material id, each instance a table sigma_t[m], sigma_s[m].
+
+Layout conventions (an interface, used identically by every consumer):
+  * cell index ``c = j * nx + i`` (i along x, j along y; ny = 1 in 1D);
+  * ``inflow`` sides are ordered (x-, x+, y-, y+) -- the value of g on the side where the
+    particles enter the domain.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+from typing import Sequence
+
+import numpy as np
+
+# Seeds: training and test parameter sets are disjoint (paper Sec. 4 requires
+# P_train and P_test to be disjoint).
+TRAIN_SEED0 = 1000
+TEST_SEED0 = 2000
+BATCH_SEED = 3000
+SERVE_SEED = 5000
+
+
+@dataclass
+class Problem:
+    """A batch of B parametric instances sharing mesh, angular rule and material map."""
+
+    dim: int                      # 1 (slab) or 2 (X-Y geometry)
+    nx: int
+    ny: int                       # 1 when dim == 1
+    domain: tuple                 # (x0, x1) in 1D, (x0, x1, y0, y1) in 2D
+    quad: str                     # 'gl' (1D Gauss-Legendre) or 'cl' (2D Chebyshev-Legendre)
+    n_phi: int                    # number of GL points (1D) or Chebyshev points N_phi (2D)
+    n_vz: int                     # number of GL points in v_z (2D); 0 in 1D
+    mat_id: np.ndarray            # int32 [n_cells]
+    sigma_t: np.ndarray           # float64 [B, n_mat]
+    sigma_s: np.ndarray           # float64 [B, n_mat]
+    source: np.ndarray            # float64 [B, n_cells], cellwise-constant G
+    inflow: np.ndarray            # float64 [B, 2*dim], isotropic inflow per side
+    params: np.ndarray = field(default=None)  # float64 [B, p], the mu that made each instance
+    name: str = ""
+
+    # ---- sizes -------------------------------------------------------------------------
+    @property
+    def n_cells(self) -> int:
+        return self.nx * self.ny
+
+    @property
+    def n_mat(self) -> int:
+        return int(self.sigma_t.shape[1])
+
+    @property
+    def batch(self) -> int:
+        return int(self.sigma_t.shape[0])
+
+    @property
+    def n_angles(self) -> int:
+        return self.n_phi if self.dim == 1 else self.n_phi * self.n_vz
+
+    @property
+    def dofs_per_cell(self) -> int:
+        return 2 if self.dim == 1 else 4
+
+    @property
+    def n_dof(self) -> int:
+        return self.n_cells * self.dofs_per_cell
+
+    def instance(self, b: int) -> "Problem":
+        """The b-th instance as a batch of one."""
+        return self.subset([b])
+
+    def subset(self, idx: Sequence[int]) -> "Problem":
+        idx = list(idx)
+        return replace(
+            self,
+            sigma_t=self.sigma_t[idx].copy(),
+            sigma_s=self.sigma_s[idx].copy(),
+            source=self.source[idx].copy(),
+            inflow=self.inflow[idx].copy(),
+            params=None if self.params is None else self.params[idx].copy(),
+        )
+
+    def validate(self) -> None:
+        assert self.dim in (1, 2)
+        assert self.mat_id.shape == (self.n_cells,)
+        assert self.mat_id.min() >= 0 and self.mat_id.max() < self.n_mat
+        B = self.batch
+        assert self.sigma_s.shape == self.sigma_t.shape
+        assert self.source.shape == (B, self.n_cells)
+        assert self.inflow.shape == (B, 2 * self.dim)
+        assert np.all(self.sigma_t > 0) and np.all(self.sigma_s >= 0)
+        assert np.all(self.sigma_s <= self.sigma_t)
+
+
+def _stack(rows) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(rows, dtype=np.float64))
+
+
+# ---- 1D slab workloads ---------------------------------------------------------------------
+
+def slab(n_cells: int, n_angles: int, sigma_t, sigma_s, G=1.0, inflow=(0.0, 0.0),
+         domain=(0.0, 1.0), name="slab") -> Problem:
+    """Homogeneous slab, one material; sigma_t/sigma_s may be sequences (one per instance)."""
+    st = np.atleast_1d(np.asarray(sigma_t, dtype=np.float64))
+    ss = np.atleast_1d(np.asarray(sigma_s, dtype=np.float64))
+    B = max(st.size, ss.size)
+    st = np.broadcast_to(st, (B,)).copy()
+    ss = np.broadcast_to(ss, (B,)).copy()
+    return Problem(
+        dim=1, nx=n_cells, ny=1, domain=tuple(domain), quad="gl", n_phi=n_angles, n_vz=0,
+        mat_id=np.zeros(n_cells, np.int32),
+        sigma_t=st[:, None].copy(), sigma_s=ss[:, None].copy(),
+        source=np.full((B, n_cells), float(G)),
+        inflow=np.tile(_stack(inflow), (B, 1)),
+        params=np.stack([st, ss], 1), name=name,
+    )
+
+
+def slab_diffusive(n_cells: int = 128, n_angles: int = 16, eps: float = 0.01) -> Problem:
+    """Diffusive slab on [0,1]: sigma_t = 1/eps, sigma_a = eps, G = 1, vacuum inflow."""
+    st = 1.0 / eps
+    return slab(n_cells, n_angles, st, st - eps, G=1.0, name=f"slab{n_cells}_S{n_angles}_eps{eps}")
+
+
+def slab_random(n_cells: int, n_angles: int, n_mat: int, seed: int, B: int = 1,
+                inflow=(0.0, 0.0)) -> Problem:
+    """Slab with random per-cell materials (for parity tests): c = sigma_s/sigma_t in [0, 0.99]."""
+    rng = np.random.default_rng(seed)
+    mat = rng.integers(0, n_mat, n_cells).astype(np.int32)
+    st = rng.uniform(0.5, 20.0, (B, n_mat))
+    ss = st * rng.uniform(0.0, 0.99, (B, n_mat))
+    G = rng.uniform(0.0, 2.0, (B, n_cells))
+    return Problem(1, n_cells, 1, (0.0, 1.0), "gl", n_angles, 0, mat, st, ss, G,
+                   np.tile(_stack(inflow), (B, 1)), None, f"slab_random{seed}")
+
+
+# ---- 2D lattice-cell workloads -------------------------------------------------------------
+
+def lattice_map(n: int) -> np.ndarray:
+    """Material id per cell of an n x n mesh of [0,1]^2: 1 inside the centred square inclusion
+    of side 0.4, else 0.  A cell is inside iff its centre satisfies |x-0.5| < 0.2 and
+    |y-0.5| < 0.2, decided in integers: 6n < 20i+10 < 14n (same for j)."""
+    i = np.arange(n)
+    inside_1d = (6 * n < 20 * i + 10) & (20 * i + 10 < 14 * n)
+    inside = inside_1d[None, :] & inside_1d[:, None]  # [j, i]
+    return inside.astype(np.int32).reshape(-1)
+
+
+def lattice_params(seeds: Sequence[int]) -> np.ndarray:
+    """mu = (mu_in, mu_out, mu_a): sigma_s ~ U[1,100] in the inclusion, U[0.1,1] outside,
+    sigma_a ~ U[0.01,0.1] everywhere; one numpy Generator per seed."""
+    out = []
+    for s in seeds:
+        rng = np.random.default_rng(int(s))
+        out.append((rng.uniform(1.0, 100.0), rng.uniform(0.1, 1.0), rng.uniform(0.01, 0.1)))
+    return _stack(out)
+
+
+def lattice_from_params(n: int, n_phi: int, n_vz: int, mu: np.ndarray, G: float = 1.0,
+                        name: str = "") -> Problem:
+    mu = np.atleast_2d(np.asarray(mu, dtype=np.float64))
+    B = mu.shape[0]
+    mu_in, mu_out, mu_a = mu[:, 0], mu[:, 1], mu[:, 2]
+    sigma_s = np.stack([mu_out, mu_in], 1)          # material 0 = outside, 1 = inclusion
+    sigma_t = sigma_s + mu_a[:, None]
+    return Problem(
+        dim=2, nx=n, ny=n, domain=(0.0, 1.0, 0.0, 1.0), quad="cl", n_phi=n_phi, n_vz=n_vz,
+        mat_id=lattice_map(n), sigma_t=sigma_t, sigma_s=sigma_s,
+        source=np.full((B, n * n), float(G)), inflow=np.zeros((B, 4)), params=mu.copy(),
+        name=name or f"lattice{n}_CL({n_phi},{n_vz})",
+    )
+
+
+def lattice(n: int, n_angles: int, seeds: Sequence[int], n_vz: int = 4) -> Problem:
+    """Two-material lattice cell on [0,1]^2 with CL(n_angles/n_vz, n_vz), vacuum inflow, G=1."""
+    assert n_angles % n_vz == 0
+    return lattice_from_params(n, n_angles // n_vz, n_vz, lattice_params(seeds))
+
+
+def lattice_train(n: int, n_angles: int, n_train: int = 32, n_vz: int = 4) -> Problem:
+    return lattice(n, n_angles, [TRAIN_SEED0 + k for k in range(n_train)], n_vz)
+
+
+def lattice_test(n: int, n_angles: int, n_test: int = 10, n_vz: int = 4, first: int = 0) -> Problem:
+    return lattice(n, n_angles, [TEST_SEED0 + first + k for k in range(n_test)], n_vz)
+
+
+def random_2d(n: int, n_phi: int, n_vz: int, n_mat: int, seed: int, B: int = 1,
+              inflow=(0.0, 0.0, 0.0, 0.0), ny: int | None = None) -> Problem:
+    """Random material map and cross sections on [0,1]^2 (for parity tests); c in [0, 0.99]."""
+    ny = n if ny is None else ny
+    rng = np.random.default_rng(seed)
+    mat = rng.integers(0, n_mat, n * ny).astype(np.int32)
+    st = rng.uniform(0.5, 60.0, (B, n_mat))
+    ss = st * rng.uniform(0.0, 0.99, (B, n_mat))
+    G = rng.uniform(0.0, 2.0, (B, n * ny))
+    return Problem(2, n, ny, (0.0, 1.0, 0.0, 1.0), "cl", n_phi, n_vz, mat, st, ss, G,
+                   np.tile(_stack(inflow), (B, 1)), None, f"random2d_{n}x{ny}_{seed}")
+
+
+# ---- batched / serving workloads ------------------------------------------------------------
+
+MESH_SIDES_BATCH = (64, 96, 128, 192)
+ANGLES_BATCH = (32, 64, 128)
+
+
+def mixed_batch_spec(n_instances: int = 256, seed: int = BATCH_SEED):
+    """Per-instance (mesh side, angle count, mu) for the batched workload: side from
+    {64,96,128,192}, angles from {32,64,128}, mu as in the lattice workload."""
+    rng = np.random.default_rng(seed)
+    sides = rng.choice(MESH_SIDES_BATCH, n_instances)
+    angles = rng.choice(ANGLES_BATCH, n_instances)
+    mu = np.stack([rng.uniform(1.0, 100.0, n_instances), rng.uniform(0.1, 1.0, n_instances),
+                   rng.uniform(0.01, 0.1, n_instances)], 1)
+    return [(int(s), int(a), mu[k]) for k, (s, a) in enumerate(zip(sides, angles))]
