@@ -1,0 +1,234 @@
+/*
+ * rte.h -- C ABI of the GB300 (sm_103a) library for ROM-enhanced source iteration with
+ * synthetic acceleration (SISA) on the parametric steady radiative transfer equation,
+ * after Peng, "Reduced Order Model Enhanced Source Iteration with Synthetic Acceleration for
+ * Parametric Radiative Transfer Equation" (arXiv 2402.10488).
+ *
+ * Problem (paper Sec. 2, Eq. (1)/(2)): one energy group, isotropic scattering, isotropic
+ * source G and isotropic inflow g,
+ *     v . grad f + sigma_t f = sigma_s rho + G,   rho = normalised angular integral of f.
+ * Discretisation: S_N in angle (Sec. 2.1; 1D Gauss-Legendre, 2D Chebyshev-Legendre
+ * CL(N_phi, N_vz), weights summing to 1) and upwind DG with Q^1 elements and an orthonormal
+ * basis on each cell (Sec. 2.2, Eq. (dg_matrix_vec)).
+ *
+ * Conventions shared by every call
+ *   - Status: every call returns RTE_OK (0) or a negative RTE_E* code; rte_last_error() gives
+ *     a message for the calling thread.  No C++ exception crosses this boundary.
+ *   - Handles (rte_disc_t, rte_batch_t, rte_rom_t) are owned by the library; destroy them with
+ *     the matching *_destroy call.  Arrays passed in are owned by the caller and are only read
+ *     (or written) during the call, or -- for calls taking a stream -- until the stream reaches
+ *     the work the call enqueued.
+ *   - "device" pointers are CUDA global-memory pointers on the handle's device; "host"
+ *     pointers are ordinary CPU memory.  Each argument states which it is.
+ *   - Streams are passed as void* (a cudaStream_t; NULL = the legacy default stream).
+ *   - Layouts: cell index c = j*nx + i (i along x).  A DG vector (rho, G, ...) of one instance
+ *     is double[n_cells][P] with P = 2 in 1D (local index a, Legendre degree in x) and P = 4
+ *     in 2D (local index k = a + 2b, a the degree in x, b in y).  A batch of B instances stores
+ *     B such vectors back to back: double[B][n_dof], n_dof = n_cells*P.
+ *   - Orthonormal cell basis: phi_a(x) = sqrt((2a+1)/h) P_a(2(x-x_c)/h), tensorised in 2D.
+ *     Coefficient vectors are in this basis (rho's cell average is rho[c][0]/sqrt(|T_c|)).
+ *   - FP64 is the interface precision.
+ */
+#ifndef RTE_GB300_H
+#define RTE_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RTE_OK 0
+#define RTE_EINVAL (-1)    /* bad shape, NaN/Inf, sigma_s > sigma_t, negative sigma, bad mode  */
+#define RTE_ENOMEM (-2)    /* device allocation failed / admission refused by memory budget     */
+#define RTE_ENOCONV (-3)   /* iteration cap reached; results are still written                  */
+#define RTE_ETIMEOUT (-4)  /* a bounded device-side wait gave up; the context remains usable    */
+#define RTE_ECUDA (-5)     /* a CUDA runtime call failed                                        */
+#define RTE_ESTATE (-6)    /* call out of order (e.g. parameters not set, ROM not built)       */
+
+typedef struct rte_disc_s* rte_disc_t;
+typedef struct rte_batch_s* rte_batch_t;
+typedef struct rte_rom_s* rte_rom_t;
+
+/* ---- library ------------------------------------------------------------------------- */
+
+/* ABI version of this header (major*10000 + minor*100 + patch). */
+int rte_version(void);
+/* Message of the last failed call on this thread ("" if none).  Pointer valid until the next
+ * call on the same thread. */
+const char* rte_last_error(void);
+
+/* ---- discretisation -------------------------------------------------------------------- */
+
+/* Mesh, angular rule and material map, shared by every instance of a batch.
+ *   dim            1 (slab geometry, Eq. (2)) or 2 (X-Y geometry on S^2)
+ *   nx, ny         cells along x and y (ny = 1 when dim == 1); uniform mesh
+ *   x0,x1,y0,y1    domain [x0,x1] (x [y0,y1] in 2D)
+ *   n_phi, n_vz    1D: n_phi = number of Gauss-Legendre points, n_vz = 0
+ *                  2D: the CL(n_phi, n_vz) rule of Sec. 2.1; n_phi must be even (reflection
+ *                  symmetry used by the 2D DSA moments)
+ *   n_mat          number of materials (cross sections are constant per material)
+ *   mat_id         HOST int32[n_cells], material of each cell, copied during the call      */
+typedef struct {
+  int dim;
+  int nx, ny;
+  double x0, x1, y0, y1;
+  int n_phi, n_vz;
+  int n_mat;
+  const int32_t* mat_id;
+} rte_disc_desc;
+
+/* Creates the discretisation on CUDA device `device`: builds the quadrature (Sec. 2.1), the
+ * list of distinct sweep directions (in X-Y geometry f_j depends only on (v_x, v_y), so the
+ * +-v_z pair of a CL direction is swept once with the pair's summed weight) and uploads the
+ * material map.  Errors: RTE_EINVAL for bad sizes, RTE_ECUDA/RTE_ENOMEM. */
+int rte_disc_create(const rte_disc_desc* desc, int device, rte_disc_t* out);
+int rte_disc_destroy(rte_disc_t disc);
+
+/* info (HOST int64[8]): n_cells, n_dof, P, n_angles, n_dirs (distinct swept directions),
+ * n_mat, dim, device. */
+int rte_disc_info(rte_disc_t disc, int64_t* info);
+
+/* The S_N rule: v (HOST double[n_angles][3]) and omega (HOST double[n_angles]), in the paper's
+ * index order j = (j2-1) N_phi + j1 for CL; 1D: v[j] = (xi_j, 0, 0), ascending xi. */
+int rte_disc_quadrature(rte_disc_t disc, double* v, double* omega);
+
+/* ---- batches of parametric instances ------------------------------------------------ */
+
+/* A batch of B instances on one discretisation.  Allocates all per-instance device state
+ * (parameters, sweep tables, DSA operators, iteration scratch).  RTE_ENOMEM if it does not
+ * fit.  `stream` is used for every later call that takes no stream of its own. */
+int rte_batch_create(rte_disc_t disc, int B, rte_batch_t* out);
+int rte_batch_destroy(rte_batch_t batch);
+
+/* Sets the parameters mu of every instance (Sec. 3.1: cross sections, source, inflow) and
+ * runs the per-instance set-up kernels (sweep cell tables, source moments, DSA operator):
+ *   sigma_t, sigma_s  HOST double[B][n_mat]; 0 <= sigma_s <= sigma_t, sigma_t > 0
+ *   source            HOST double[B][n_cells], cellwise-constant isotropic G
+ *   inflow            HOST double[B][2*dim], isotropic inflow g on the sides (x-, x+[, y-, y+])
+ * Errors: RTE_EINVAL (NaN/Inf, negative values, sigma_s > sigma_t), RTE_ECUDA.
+ * Synchronous with respect to the host (returns after the set-up has run). */
+int rte_batch_set_params(rte_batch_t batch, const double* sigma_t, const double* sigma_s,
+                         const double* source, const double* inflow);
+
+/* ---- hot path: one source iteration --------------------------------------------------- */
+
+/* Transport sweep fused with the scalar-flux reduction (Alg. 1; Eq. (transport_sweep)):
+ *     f_j = (D_j + Sigma_t)^{-1} (Sigma_s rho_in + [G + g^bc_j]),   rho_out = sum_j omega_j f_j
+ * for every instance of the batch.  with_source = 0 drops G and g^bc (rho_out = L rho_in,
+ * Eq. (rho_matrix_vec_def)).  f_j itself is not stored unless psi_out != NULL.
+ *   rho_in   DEVICE double[B][n_dof]
+ *   rho_out  DEVICE double[B][n_dof] (must not alias rho_in)
+ *   psi_out  DEVICE double[B][n_dirs][n_dof] or NULL: f of each distinct swept direction, in
+ *            the order of rte_batch_directions()
+ *   active   DEVICE uint8[B] or NULL: instances with active[b] == 0 are skipped (outputs
+ *            untouched)
+ * Asynchronous on `stream`.  Errors: RTE_ESTATE (no parameters), RTE_EINVAL, RTE_ECUDA. */
+int rte_sweep(rte_batch_t batch, const double* rho_in, double* rho_out, double* psi_out,
+              int with_source, const uint8_t* active, void* stream);
+
+/* The distinct swept directions: dirs (HOST double[n_dirs][4]) = (v_x, v_y, summed weight,
+ * multiplicity), in the order used by psi_out and the ROM bases. */
+int rte_batch_directions(rte_batch_t batch, double* dirs);
+
+/* Stop-test norms (Alg. 1): norms[b] = (||rho_star_b - rho_prev_b||_inf, ||rho_star_b||_inf)
+ * over the coefficient vectors.  norms: DEVICE double[B][2].  Asynchronous. */
+int rte_change_norm(rte_batch_t batch, const double* rho_star, const double* rho_prev,
+                    double* norms, void* stream);
+
+/* Consistent DSA correction (App. B; 2D by the same P1-ansatz moment derivation):
+ * solves the diffusion system for delta rho given R = Sigma_s (rho^(l,*) - rho^(l-1)).
+ *   R      DEVICE double[B][n_dof];  drho  DEVICE double[B][n_dof]
+ *   rtol   relative residual tolerance of the iterative solve (2D); 1D is a direct solve
+ *   max_it iteration cap (2D); iters (HOST int[B], may be NULL) receives iterations used
+ *   active DEVICE uint8[B] or NULL
+ * Synchronises `stream` (the 2D Krylov solve reads residual norms on the host).
+ * Errors: RTE_ENOCONV if max_it was reached for some instance (drho still written). */
+int rte_dsa_correction(rte_batch_t batch, const double* R, double* drho, double rtol,
+                       int max_it, const uint8_t* active, int* iters, void* stream);
+
+/* Forms R = Sigma_s (rho_star - rho_prev) (the source of the kinetic correction equation,
+ * Eq. (discrete_correction)).  All DEVICE double[B][n_dof].  Asynchronous. */
+int rte_correction_source(rte_batch_t batch, const double* rho_star, const double* rho_prev,
+                          double* R, void* stream);
+
+/* ---- reduced order models (Sec. 3) ------------------------------------------------------ */
+
+typedef struct {
+  double eps_train;   /* SISA tolerance of the training solves (absolute, Alg. 1)           */
+  int window;         /* window size w for correction snapshots (Sec. 3.2.1)                 */
+  int rank_p;         /* POD rank of the parametric ROM (0: use eps_pod)                     */
+  int rank_c;         /* POD rank of the correction ROM (0: use eps_pod)                     */
+  double eps_pod;     /* truncation tolerance of Eq. (pod_truncation) when a rank is 0       */
+  int max_iter;       /* iteration cap of the training solves                                */
+  double dsa_rtol;    /* DSA solve tolerance used in the training solves                     */
+} rte_rom_opts;
+
+/* Offline stage (Sec. 3.1.1, 3.2.1) on the GPU: SI-DSA solves of every training instance of
+ * `train` (f stored), snapshot matrices F and delta F (window w), thin SVD via a stabilised
+ * Gram-Schmidt QR and a Jacobi SVD of the small factor, truncation, U^rho, U^iso and the affine
+ * reduced operators A_{k,r} = U^T A_k U.  Produces the parametric ROM (rom_p, for ROMIG) and
+ * the correction ROM (rom_c, for ROMSA).  Either output pointer may be NULL.  Synchronous. */
+int rte_rom_build(rte_batch_t train, const rte_rom_opts* opts, rte_rom_t* rom_p,
+                  rte_rom_t* rom_c, void* stream);
+int rte_rom_destroy(rte_rom_t rom);
+
+/* info (HOST double[6]): r, n_snapshots, eps_pod of the kept rank (1 - sum_{k<=r} s_k /
+ * sum s_k), n_dirs, n_dof, sum of singular values.  sv (HOST double[n_snapshots] or NULL):
+ * singular values of the snapshot matrix. */
+int rte_rom_info(rte_rom_t rom, double* info, double* sv);
+
+/* ROMIG (Sec. 3.1.1): rho0 = U^rho c with (sum_k psi_k(mu) A_{k,r}) c = U^T b_mu, for every
+ * instance of `batch` (same discretisation as the ROM).  rho0: DEVICE double[B][n_dof]. */
+int rte_rom_initial_guess(rte_rom_t rom_p, rte_batch_t batch, double* rho0,
+                          const uint8_t* active, void* stream);
+
+/* ROMSA correction (Eq. (rom_correction)): delta rho = dU^rho dc with
+ * (dU^T A_mu dU) dc = (dU^iso)^T R.  R, drho: DEVICE double[B][n_dof]. */
+int rte_romsa_correction(rte_rom_t rom_c, rte_batch_t batch, const double* R, double* drho,
+                         const uint8_t* active, void* stream);
+
+/* ---- full solves (Alg. 1 with the SA of choice, Alg. 2) --------------------------------- */
+
+#define RTE_SA_NONE 0
+#define RTE_SA_DSA 1
+#define RTE_SA_ROMSA 2
+#define RTE_SA_ROMSAD 3
+
+typedef struct {
+  double eps;          /* stop tolerance eps_SISA                                           */
+  int rel;             /* 0: ||rho* - rho||_inf < eps (Alg. 1); 1: divided by ||rho*||_inf   */
+  int max_iter;        /* N_iter                                                             */
+  int sa;              /* RTE_SA_*                                                           */
+  int theta;           /* ROMSAD: ROMSA allowed after iterations 1..theta (Alg. 2)           */
+  double eps_romsad;   /* ROMSAD threshold on the absolute change (Eq. (romsad_parameters)) */
+  double dsa_rtol;     /* DSA iterative solve tolerance (2D)                                 */
+  int dsa_max_it;      /* DSA iteration cap (2D)                                             */
+  const uint8_t* schedule; /* HOST uint8[max_iter] or NULL: forces ROMSAD's choice per
+                              iteration (1 = ROMSA, 0 = DSA), for reproducibility tests      */
+} rte_solve_opts;
+
+typedef struct {
+  int n_sweep;         /* sweeps performed                                                  */
+  int converged;       /* 1 if the stop test fired                                          */
+  int n_romsa;         /* corrections done by ROMSA                                         */
+  int n_dsa;           /* corrections done by DSA                                           */
+  int dsa_iters;       /* total DSA Krylov iterations                                       */
+  double last_change;  /* last ||rho* - rho||_inf                                           */
+  double rho_inf;      /* ||rho*||_inf at exit                                              */
+} rte_solve_report;
+
+/* Runs Alg. 1 on every instance of the batch, each stopping on its own test.
+ *   rho      DEVICE double[B][n_dof]: in = initial guess rho^(0), out = solution (rho^(l,*) of
+ *            the sweep at which the test fired; the last corrected iterate otherwise)
+ *   rom_c    correction ROM for RTE_SA_ROMSA / RTE_SA_ROMSAD (NULL otherwise)
+ *   reports  HOST rte_solve_report[B] (may be NULL)
+ *   history  HOST double[B][max_iter] or NULL: ||rho^(l,*) - rho^(l-1)||_inf per iteration
+ * Synchronous.  Returns RTE_ENOCONV if some instance hit max_iter. */
+int rte_solve(rte_batch_t batch, const rte_solve_opts* opts, rte_rom_t rom_c, double* rho,
+              rte_solve_report* reports, double* history, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTE_GB300_H */

@@ -1,0 +1,333 @@
+// Library-level entry points: errors, discretisation (quadrature, distinct sweep directions),
+// batches of parametric instances and their parameters.
+#include <algorithm>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace rte {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+// Gauss-Legendre nodes on [-1,1] (ascending) with weights normalised to sum 1 (Sec. 2.1):
+// Newton iterations on P_n from the recurrence (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1}.
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 1; k < n; ++k) {
+        double p2 = ((2.0 * k + 1.0) * z * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) {
+        p1 = z;
+        p0 = 1.0;
+      }
+      dp = n * (p0 - z * p1) / (1.0 - z * z);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    {  // final derivative at the converged node
+      double p0 = 1.0, p1 = z;
+      for (int k = 1; k < n; ++k) {
+        double p2 = ((2.0 * k + 1.0) * z * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) p0 = 1.0, p1 = z;
+      dp = n * (p0 - z * p1) / (1.0 - z * z);
+    }
+    x[i] = z;
+    w[i] = 1.0 / ((1.0 - z * z) * dp * dp);  // textbook 2/(...) times 1/2
+  }
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  std::sort(idx.begin(), idx.end(), [&](int a, int b) { return x[a] < x[b]; });
+  std::vector<double> xs(n), ws(n);
+  for (int i = 0; i < n; ++i) xs[i] = x[idx[i]], ws[i] = w[idx[i]];
+  x.swap(xs);
+  w.swap(ws);
+}
+
+}  // namespace rte
+
+using namespace rte;
+
+extern "C" int rte_version(void) { return 10000; }
+extern "C" const char* rte_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int rte_disc_create(const rte_disc_desc* d, int device, rte_disc_t* out) {
+  if (!d || !out) return fail(RTE_EINVAL, "rte_disc_create: null argument");
+  *out = nullptr;
+  if (d->dim != 1 && d->dim != 2) return fail(RTE_EINVAL, "dim must be 1 or 2");
+  if (d->nx < 1 || d->ny < 1 || (d->dim == 1 && d->ny != 1))
+    return fail(RTE_EINVAL, "bad mesh size");
+  if (!(d->x1 > d->x0) || (d->dim == 2 && !(d->y1 > d->y0)))
+    return fail(RTE_EINVAL, "empty domain");
+  if (d->n_mat < 1 || !d->mat_id) return fail(RTE_EINVAL, "need n_mat >= 1 and a material map");
+  if (d->dim == 1 && (d->n_phi < 2 || d->n_phi % 2))
+    return fail(RTE_EINVAL, "1D: n_phi (GL points) must be even and >= 2");
+  if (d->dim == 2 && (d->n_phi < 2 || d->n_phi % 2 || d->n_vz < 1))
+    return fail(RTE_EINVAL, "2D: CL(n_phi, n_vz) needs even n_phi >= 2 and n_vz >= 1");
+  if ((long long)d->nx * d->ny > (1LL << 28)) return fail(RTE_EINVAL, "mesh too large");
+  int ndev = 0;
+  RTE_CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(RTE_EINVAL, "bad device index");
+  DeviceGuard g(device);
+
+  auto* disc = new rte_disc_s();
+  disc->device = device;
+  disc->dim = d->dim;
+  disc->nx = d->nx;
+  disc->ny = d->ny;
+  disc->n_cells = d->nx * d->ny;
+  disc->P = d->dim == 1 ? 2 : 4;
+  disc->n_dof = disc->n_cells * disc->P;
+  disc->x0 = d->x0, disc->x1 = d->x1, disc->y0 = d->y0, disc->y1 = d->y1;
+  disc->hx = (d->x1 - d->x0) / d->nx;
+  disc->hy = d->dim == 2 ? (d->y1 - d->y0) / d->ny : 1.0;
+  disc->n_phi = d->n_phi;
+  disc->n_vz = d->n_vz;
+  disc->n_mat = d->n_mat;
+  disc->mat_host.assign(d->mat_id, d->mat_id + disc->n_cells);
+  for (int c = 0; c < disc->n_cells; ++c)
+    if (disc->mat_host[c] < 0 || disc->mat_host[c] >= d->n_mat) {
+      delete disc;
+      return fail(RTE_EINVAL, "material id out of range");
+    }
+
+  // ---- quadrature (Sec. 2.1) and distinct directions --------------------------------------
+  if (d->dim == 1) {
+    std::vector<double> x, w;
+    gauss_legendre(d->n_phi, x, w);
+    disc->n_angles = d->n_phi;
+    disc->v.assign(3 * d->n_phi, 0.0);
+    disc->w = w;
+    for (int j = 0; j < d->n_phi; ++j) {
+      disc->v[3 * j] = x[j];
+      Dir dd{x[j], 0.0, w[j], 1, x[j] < 0 ? 1 : 0};
+      disc->dirs.push_back(dd);
+    }
+  } else {
+    std::vector<double> vz, wz;
+    gauss_legendre(d->n_vz, vz, wz);
+    const int np = d->n_phi, nz = d->n_vz;
+    disc->n_angles = np * nz;
+    disc->v.assign(3 * np * nz, 0.0);
+    disc->w.assign(np * nz, 0.0);
+    for (int j2 = 0; j2 < nz; ++j2) {
+      double s = std::sqrt(1.0 - vz[j2] * vz[j2]);
+      for (int j1 = 0; j1 < np; ++j1) {
+        double phi = 2.0 * (j1 + 1) * M_PI / np - M_PI / np;
+        int j = j2 * np + j1;
+        disc->v[3 * j] = std::cos(phi) * s;
+        disc->v[3 * j + 1] = std::sin(phi) * s;
+        disc->v[3 * j + 2] = vz[j2];
+        disc->w[j] = (1.0 / np) * wz[j2];
+      }
+    }
+    // GL in v_z is symmetric: level j2 and nz-1-j2 carry the same (v_x, v_y) and weight, so
+    // their transport solutions coincide; sweep each pair once with the summed weight.
+    for (int j2 = 0; j2 < (nz + 1) / 2; ++j2) {
+      int mirror = nz - 1 - j2;
+      int mult = mirror == j2 ? 1 : 2;
+      for (int j1 = 0; j1 < np; ++j1) {
+        int j = j2 * np + j1;
+        double vx = disc->v[3 * j], vy = disc->v[3 * j + 1];
+        double w = disc->w[j] + (mult == 2 ? disc->w[mirror * np + j1] : 0.0);
+        disc->dirs.push_back(Dir{vx, vy, w, mult, (vx < 0 ? 1 : 0) + (vy < 0 ? 2 : 0)});
+      }
+    }
+  }
+  std::stable_sort(disc->dirs.begin(), disc->dirs.end(),
+                   [](const Dir& a, const Dir& b) { return a.quad < b.quad; });
+  disc->n_dirs = (int)disc->dirs.size();
+
+  // DSA moments over the full rule (App. B)
+  {
+    DsaMoments m{};
+    for (int j = 0; j < disc->n_angles; ++j) {
+      double vx = disc->v[3 * j], vy = disc->v[3 * j + 1], w = disc->w[j];
+      m.abs_x += w * std::fabs(vx);
+      m.abs_y += w * std::fabs(vy);
+      m.xx += w * vx * vx;
+      m.yy += w * vy * vy;
+      m.abs3_x += w * std::fabs(vx) * vx * vx;
+      m.abs3_y += w * std::fabs(vy) * vy * vy;
+      m.xx_absy += w * vx * vx * std::fabs(vy);
+      m.yy_absx += w * vy * vy * std::fabs(vx);
+    }
+    disc->mom = m;
+  }
+
+  int st = disc->mat_id.alloc(disc->n_cells);
+  if (st == RTE_OK) st = disc->dir_dev.alloc(4 * (size_t)disc->n_dirs);
+  if (st != RTE_OK) {
+    delete disc;
+    return st;
+  }
+  std::vector<double> dh(4 * disc->n_dirs);
+  for (int k = 0; k < disc->n_dirs; ++k) {
+    dh[4 * k] = disc->dirs[k].vx;
+    dh[4 * k + 1] = disc->dirs[k].vy;
+    dh[4 * k + 2] = disc->dirs[k].w;
+    dh[4 * k + 3] = disc->dirs[k].mult;
+  }
+  cudaError_t e1 = cudaMemcpy(disc->mat_id.p, disc->mat_host.data(),
+                              sizeof(int32_t) * disc->n_cells, cudaMemcpyHostToDevice);
+  cudaError_t e2 =
+      cudaMemcpy(disc->dir_dev.p, dh.data(), sizeof(double) * dh.size(), cudaMemcpyHostToDevice);
+  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    delete disc;
+    return fail(RTE_ECUDA, "rte_disc_create: upload failed");
+  }
+  *out = disc;
+  return RTE_OK;
+}
+
+extern "C" int rte_disc_destroy(rte_disc_t disc) {
+  if (!disc) return RTE_OK;
+  DeviceGuard g(disc->device);
+  delete disc;
+  return RTE_OK;
+}
+
+extern "C" int rte_disc_info(rte_disc_t disc, int64_t* info) {
+  if (!disc || !info) return fail(RTE_EINVAL, "rte_disc_info: null argument");
+  info[0] = disc->n_cells;
+  info[1] = disc->n_dof;
+  info[2] = disc->P;
+  info[3] = disc->n_angles;
+  info[4] = disc->n_dirs;
+  info[5] = disc->n_mat;
+  info[6] = disc->dim;
+  info[7] = disc->device;
+  return RTE_OK;
+}
+
+extern "C" int rte_disc_quadrature(rte_disc_t disc, double* v, double* omega) {
+  if (!disc || !v || !omega) return fail(RTE_EINVAL, "rte_disc_quadrature: null argument");
+  std::memcpy(v, disc->v.data(), sizeof(double) * disc->v.size());
+  std::memcpy(omega, disc->w.data(), sizeof(double) * disc->w.size());
+  return RTE_OK;
+}
+
+// ---- batches ------------------------------------------------------------------------------
+
+rte_batch_s::~rte_batch_s() { rte::dsa_state_free(dsa); }
+
+extern "C" int rte_batch_create(rte_disc_t disc, int B, rte_batch_t* out) {
+  if (!disc || !out || B < 1) return fail(RTE_EINVAL, "rte_batch_create: bad argument");
+  *out = nullptr;
+  DeviceGuard g(disc->device);
+  auto* b = new rte_batch_s();
+  b->disc = disc;
+  b->B = B;
+  // sweep work groups: per quadrant, consecutive runs of <= dpw directions
+  b->dpw = disc->dim == 1 ? 1 : 4;
+  {
+    int d = 0;
+    while (d < disc->n_dirs) {
+      int q = disc->dirs[d].quad;
+      int e = d;
+      while (e < disc->n_dirs && disc->dirs[e].quad == q && e - d < b->dpw) ++e;
+      b->groups.push_back(SweepGroup{d, e - d, q, 0});
+      d = e;
+    }
+  }
+  const size_t nb = (size_t)B;
+  const size_t tab = disc->dim == 1 ? kTab1D : kTab2D;
+  int st = RTE_OK;
+  if (st == RTE_OK) st = b->groups_dev.alloc(b->groups.size());
+  if (st == RTE_OK) st = b->sigma_t.alloc(nb * disc->n_mat);
+  if (st == RTE_OK) st = b->sigma_s.alloc(nb * disc->n_mat);
+  if (st == RTE_OK) st = b->G0.alloc(nb * disc->n_cells);
+  if (st == RTE_OK) st = b->inflow.alloc(nb * 4);
+  if (st == RTE_OK) st = b->tables.alloc(nb * disc->n_mat * disc->n_dirs * tab);
+  if (st == RTE_OK) st = b->partial.alloc(nb * b->groups.size() * disc->n_dof);
+  if (st == RTE_OK) st = b->norms.alloc(nb * 2);
+  if (st == RTE_OK) st = b->work.alloc(nb * disc->n_dof * 4);
+  if (st != RTE_OK) {
+    delete b;
+    return st;
+  }
+  if (cudaMemcpy(b->groups_dev.p, b->groups.data(), sizeof(SweepGroup) * b->groups.size(),
+                 cudaMemcpyHostToDevice) != cudaSuccess) {
+    delete b;
+    return fail(RTE_ECUDA, "rte_batch_create: upload failed");
+  }
+  *out = b;
+  return RTE_OK;
+}
+
+extern "C" int rte_batch_destroy(rte_batch_t b) {
+  if (!b) return RTE_OK;
+  DeviceGuard g(b->disc->device);
+  delete b;
+  return RTE_OK;
+}
+
+extern "C" int rte_batch_set_params(rte_batch_t b, const double* sigma_t, const double* sigma_s,
+                                    const double* source, const double* inflow) {
+  if (!b || !sigma_t || !sigma_s || !source || !inflow)
+    return fail(RTE_EINVAL, "rte_batch_set_params: null argument");
+  rte_disc_s* d = b->disc;
+  const size_t nm = (size_t)b->B * d->n_mat, nc = (size_t)b->B * d->n_cells;
+  const size_t ni = (size_t)b->B * 2 * d->dim;
+  for (size_t k = 0; k < nm; ++k) {
+    if (!std::isfinite(sigma_t[k]) || !std::isfinite(sigma_s[k]))
+      return fail(RTE_EINVAL, "cross section is not finite");
+    if (!(sigma_t[k] > 0.0) || sigma_s[k] < 0.0 || sigma_s[k] > sigma_t[k])
+      return fail(RTE_EINVAL, "need sigma_t > 0 and 0 <= sigma_s <= sigma_t");
+  }
+  for (size_t k = 0; k < nc; ++k)
+    if (!std::isfinite(source[k])) return fail(RTE_EINVAL, "source is not finite");
+  for (size_t k = 0; k < ni; ++k)
+    if (!std::isfinite(inflow[k])) return fail(RTE_EINVAL, "inflow is not finite");
+  DeviceGuard g(d->device);
+  b->sigma_t_h.assign(sigma_t, sigma_t + nm);
+  b->sigma_s_h.assign(sigma_s, sigma_s + nm);
+  b->source_h.assign(source, source + nc);
+  b->inflow_h.assign(4 * (size_t)b->B, 0.0);
+  for (int i = 0; i < b->B; ++i)
+    for (int s = 0; s < 2 * d->dim; ++s) b->inflow_h[4 * i + s] = inflow[2 * d->dim * i + s];
+  // zeroth moment of a cellwise-constant source: int_T G phi_0 = G sqrt(|T|)
+  std::vector<double> g0(nc);
+  const double sq = std::sqrt(d->hx * d->hy);
+  for (size_t k = 0; k < nc; ++k) g0[k] = source[k] * sq;
+  RTE_CUDA_TRY(cudaMemcpy(b->sigma_t.p, sigma_t, sizeof(double) * nm, cudaMemcpyHostToDevice));
+  RTE_CUDA_TRY(cudaMemcpy(b->sigma_s.p, sigma_s, sizeof(double) * nm, cudaMemcpyHostToDevice));
+  RTE_CUDA_TRY(cudaMemcpy(b->G0.p, g0.data(), sizeof(double) * nc, cudaMemcpyHostToDevice));
+  RTE_CUDA_TRY(cudaMemcpy(b->inflow.p, b->inflow_h.data(), sizeof(double) * 4 * b->B,
+                          cudaMemcpyHostToDevice));
+  RTE_TRY(setup_tables(b, 0));
+  RTE_TRY(dsa_setup(b, 0));
+  RTE_CUDA_TRY(cudaDeviceSynchronize());
+  b->params_set = true;
+  return RTE_OK;
+}
+
+extern "C" int rte_batch_directions(rte_batch_t b, double* dirs) {
+  if (!b || !dirs) return fail(RTE_EINVAL, "rte_batch_directions: null argument");
+  const rte_disc_s* d = b->disc;
+  for (int k = 0; k < d->n_dirs; ++k) {
+    dirs[4 * k] = d->dirs[k].vx;
+    dirs[4 * k + 1] = d->dirs[k].vy;
+    dirs[4 * k + 2] = d->dirs[k].w;
+    dirs[4 * k + 3] = d->dirs[k].mult;
+  }
+  return RTE_OK;
+}

@@ -1,0 +1,163 @@
+// Internal declarations shared by the translation units of the RTE library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstring>
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/rte.h"
+
+namespace rte {
+
+// ---- error plumbing ------------------------------------------------------------------------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+#define RTE_CUDA_TRY(expr)                                                                    \
+  do {                                                                                        \
+    cudaError_t _e = (expr);                                                                  \
+    if (_e != cudaSuccess)                                                                    \
+      return ::rte::fail(_e == cudaErrorMemoryAllocation ? RTE_ENOMEM : RTE_ECUDA,            \
+                         std::string(#expr) + ": " + cudaGetErrorString(_e));                 \
+  } while (0)
+
+#define RTE_TRY(expr)                                                                         \
+  do {                                                                                        \
+    int _s = (expr);                                                                          \
+    if (_s != RTE_OK) return _s;                                                              \
+  } while (0)
+
+// Switches the calling thread to the handle's device for the scope of a call.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Device buffer owned by a handle.
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  int alloc(size_t count) {
+    release();
+    if (count == 0) return RTE_OK;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return fail(e == cudaErrorMemoryAllocation ? RTE_ENOMEM : RTE_ECUDA,
+                  std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    n = count;
+    return RTE_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  ~DevBuf() { release(); }
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+};
+
+constexpr int kTab2D = 32;  // doubles per (material, direction) sweep table in 2D
+constexpr int kTab1D = 8;   // ... in 1D (Minv 2x2, Px 2x1, pad)
+constexpr int kMaxDirsPerWarp = 8;
+
+// A distinct swept direction: X-Y geometry depends on (v_x, v_y) only.
+struct Dir {
+  double vx, vy, w;  // w = summed weight of the merged quadrature directions
+  int mult;          // how many quadrature directions were merged
+  int quad;          // (v_x < 0) + 2 (v_y < 0)
+};
+
+// Consistent-DSA quadrature moments (2D); in 1D only abs_x, xx, abs3_x are used.
+struct DsaMoments {
+  double abs_x, abs_y, xx, yy, abs3_x, abs3_y, xx_absy, yy_absx;
+};
+
+struct SweepGroup {
+  int d0, nd, quad, pad;
+};
+
+}  // namespace rte
+
+// ---- handles -----------------------------------------------------------------------------
+struct rte_disc_s {
+  int device = 0;
+  int dim = 2, nx = 0, ny = 1, n_cells = 0, P = 4, n_dof = 0;
+  double x0 = 0, x1 = 1, y0 = 0, y1 = 1, hx = 0, hy = 0;
+  int n_phi = 0, n_vz = 0, n_angles = 0, n_dirs = 0, n_mat = 0;
+  std::vector<double> v, w;           // full rule, paper index order
+  std::vector<rte::Dir> dirs;         // distinct directions sorted by quadrant
+  std::vector<int32_t> mat_host;
+  rte::DsaMoments mom{};
+  rte::DevBuf<int32_t> mat_id;        // [n_cells]
+  rte::DevBuf<double> dir_dev;        // [n_dirs][4] vx, vy, w, mult
+};
+
+namespace rte {
+struct DsaState;   // 2D/1D DSA per-batch state (dsa.cu)
+void dsa_state_free(DsaState*);
+int dsa_setup(rte_batch_t batch, cudaStream_t st);
+}
+
+struct rte_batch_s {
+  rte_disc_s* disc = nullptr;
+  int B = 0;
+  bool params_set = false;
+  int dpw = 4;                        // directions per warp in the 2D sweep
+  std::vector<rte::SweepGroup> groups;
+  rte::DevBuf<rte::SweepGroup> groups_dev;
+  std::vector<double> sigma_t_h, sigma_s_h, source_h, inflow_h;
+  rte::DevBuf<double> sigma_t, sigma_s;   // [B][n_mat]
+  rte::DevBuf<double> G0;                 // [B][n_cells] zeroth source moment int G phi_0
+  rte::DevBuf<double> inflow;             // [B][4] (2D) or [B][2] (1D)
+  rte::DevBuf<double> tables;             // [B][n_mat][n_dirs][kTab*]
+  rte::DevBuf<double> partial;            // [B][n_groups][n_dof] per-group scalar-flux partials
+  rte::DevBuf<unsigned long long> norms;  // [B][2] stop-test norms as ordered bit patterns
+  rte::DevBuf<double> work;               // [B][n_dof] x 4 iteration scratch for rte_solve
+  rte::DsaState* dsa = nullptr;
+  ~rte_batch_s();
+};
+
+namespace rte {
+// sweep.cu
+int sweep_launch(rte_batch_t b, const double* rho_in, double* rho_out, double* psi_out,
+                 int with_source, const uint8_t* active, cudaStream_t st, bool fuse_norms);
+int norms_to_host(rte_batch_t b, double* host, cudaStream_t st);
+int setup_tables(rte_batch_t b, cudaStream_t st);
+int correction_source_launch(rte_batch_t b, const double* rs, const double* rp, double* R,
+                             const uint8_t* active, cudaStream_t st);
+int axpy_launch(rte_batch_t b, const double* x, const double* y, double* out,
+                const uint8_t* active, cudaStream_t st);  // out = x + y
+int dsa_apply(rte_batch_t b, const double* R, double* drho, double rtol, int max_it,
+              const uint8_t* active, int* iters, cudaStream_t st);
+}  // namespace rte
+
+struct rte_rom_s {
+  rte_disc_s* disc = nullptr;
+  int r = 0, n_snap = 0;
+  std::vector<double> sv;
+  double eps_equiv = 0;
+  rte::DevBuf<double> U;       // [n_dirs][n_dof][r]  per distinct direction (row blocks U_j)
+  rte::DevBuf<double> U_rho;   // [n_dof][r]
+  rte::DevBuf<double> U_iso;   // [n_dof][r]
+  std::vector<double> A0;      // [r][r]
+  std::vector<double> Aa, As;  // [n_mat][r][r]
+  rte::DevBuf<double> scratch; // per-call workspace
+};

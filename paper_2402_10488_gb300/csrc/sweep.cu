@@ -1,0 +1,539 @@
+// Transport sweep fused with the scalar-flux reduction (paper Alg. 1, Eq. (transport_sweep)).
+//
+// 2D: upwind DG-Q^1 on a uniform Cartesian mesh.  In every cell and direction the local system
+//     M a = s + E_x t_x + E_y t_y,   M = sigma_t I + a_x (K_x (x) I) + a_y (I (x) K_y)
+// is solved with a per-(material, direction) table {M^-1, M^-1 E_x, M^-1 E_y} computed once per
+// parameter set, where a_x = |v_x|/h_x, K_x = [[1, s_x sqrt3], [-s_x sqrt3, 3]] (s_x the sign
+// of v_x), s = Sigma_s rho + G are the cell's source moments and t_x, t_y the upwind traces
+//     t_x[b] = a_{0b} + s_x sqrt3 a_{1b}   (x-outflow face, expanded along y),
+//     t_y[a] = a_{a0} + s_y sqrt3 a_{a1}   (y-outflow face, expanded along x).
+// On an inflow boundary t = g sqrt(h_x h_y) (isotropic inflow g, zeroth moment only).
+//
+// Parallel layout (GB300): one warp per (instance, quadrant, group of <= DPW directions).  The
+// warp sweeps the mesh in blocks of H = min(32, n_x) rows; lane l owns row l of the block and
+// processes column t at step s = (block)*n_x + t + l, so each step is one wavefront diagonal.
+// The y-inflow comes from lane l-1 of the previous step by a register shuffle; lane 0 of the
+// next row block reads the previous block's last row from a shared-memory line buffer; the
+// x-inflow stays in registers.  No block-wide barrier is needed.  Each warp writes its
+// omega-weighted partial scalar flux per cell; a second kernel sums the partials in a fixed
+// order (deterministic) and fuses the stop-test norms.
+#include "common.cuh"
+
+namespace rte {
+
+__device__ __forceinline__ void inv4(double m[16]) {
+  // Gauss-Jordan with partial pivoting on a 4x4 row-major matrix, in place.
+  double a[4][8];
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 8; ++c) a[r][c] = c < 4 ? m[4 * r + c] : (c - 4 == r ? 1.0 : 0.0);
+  for (int k = 0; k < 4; ++k) {
+    int p = k;
+    for (int r = k + 1; r < 4; ++r)
+      if (fabs(a[r][k]) > fabs(a[p][k])) p = r;
+    if (p != k)
+      for (int c = 0; c < 8; ++c) {
+        double tmp = a[k][c];
+        a[k][c] = a[p][c];
+        a[p][c] = tmp;
+      }
+    double piv = 1.0 / a[k][k];
+    for (int c = 0; c < 8; ++c) a[k][c] *= piv;
+    for (int r = 0; r < 4; ++r)
+      if (r != k) {
+        double f = a[r][k];
+        for (int c = 0; c < 8; ++c) a[r][c] -= f * a[k][c];
+      }
+  }
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c) m[4 * r + c] = a[r][c + 4];
+}
+
+// One thread per (instance, material, direction): the cell tables.
+__global__ void tables2d_kernel(double* tables, const double* sigma_t, const double* dirs,
+                                int B, int n_mat, int n_dirs, double hx, double hy) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= B * n_mat * n_dirs) return;
+  const int d = idx % n_dirs;
+  const int m = (idx / n_dirs) % n_mat;
+  const int b = idx / (n_dirs * n_mat);
+  const double st = sigma_t[b * n_mat + m];
+  const double vx = dirs[4 * d], vy = dirs[4 * d + 1];
+  const double s3 = sqrt(3.0);
+  const double sx = vx < 0 ? -1.0 : 1.0, sy = vy < 0 ? -1.0 : 1.0;
+  const double ax = fabs(vx) / hx, ay = fabs(vy) / hy;
+  const double K[2][2][2] = {{{1.0, sx * s3}, {-sx * s3, 3.0}}, {{1.0, sy * s3}, {-sy * s3, 3.0}}};
+  double M[16];
+  for (int bb = 0; bb < 2; ++bb)
+    for (int aa = 0; aa < 2; ++aa)
+      for (int b2 = 0; b2 < 2; ++b2)
+        for (int a2 = 0; a2 < 2; ++a2) {
+          double v = 0.0;
+          if (aa == a2 && bb == b2) v += st;
+          if (bb == b2) v += ax * K[0][aa][a2];
+          if (aa == a2) v += ay * K[1][bb][b2];
+          M[4 * (aa + 2 * bb) + (a2 + 2 * b2)] = v;
+        }
+  inv4(M);
+  double Ex[4][2] = {{0}}, Ey[4][2] = {{0}};
+  for (int q = 0; q < 2; ++q) {
+    Ex[0 + 2 * q][q] = ax;
+    Ex[1 + 2 * q][q] = -sx * s3 * ax;
+    Ey[q][q] = ay;
+    Ey[q + 2][q] = -sy * s3 * ay;
+  }
+  double* T = tables + (size_t)idx * kTab2D;
+  for (int k = 0; k < 16; ++k) T[k] = M[k];
+  for (int k = 0; k < 4; ++k)
+    for (int q = 0; q < 2; ++q) {
+      double px = 0.0, py = 0.0;
+      for (int l = 0; l < 4; ++l) {
+        px += M[4 * k + l] * Ex[l][q];
+        py += M[4 * k + l] * Ey[l][q];
+      }
+      T[16 + 2 * k + q] = px;
+      T[24 + 2 * k + q] = py;
+    }
+}
+
+__global__ void tables1d_kernel(double* tables, const double* sigma_t, const double* dirs, int B,
+                                int n_mat, int n_dirs, double h) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= B * n_mat * n_dirs) return;
+  const int d = idx % n_dirs;
+  const int m = (idx / n_dirs) % n_mat;
+  const int b = idx / (n_dirs * n_mat);
+  const double st = sigma_t[b * n_mat + m];
+  const double xi = dirs[4 * d];
+  const double s3 = sqrt(3.0), sg = xi < 0 ? -1.0 : 1.0, a = fabs(xi) / h;
+  // M = st I + a [[1, sg s3], [-sg s3, 3]]
+  const double m00 = st + a, m01 = a * sg * s3, m10 = -a * sg * s3, m11 = st + 3.0 * a;
+  const double det = m00 * m11 - m01 * m10;
+  const double i00 = m11 / det, i01 = -m01 / det, i10 = -m10 / det, i11 = m00 / det;
+  double* T = tables + (size_t)idx * kTab1D;
+  T[0] = i00, T[1] = i01, T[2] = i10, T[3] = i11;
+  // inflow coupling E = a (1, -sg s3)
+  T[4] = i00 * a + i01 * (-sg * s3 * a);
+  T[5] = i10 * a + i11 * (-sg * s3 * a);
+  T[6] = T[7] = 0.0;
+}
+
+struct Sweep2DArgs {
+  const double* rho_in;
+  double* partial;
+  double* psi_out;
+  const uint8_t* active;
+  const double* tables;
+  const double* sigma_s;
+  const double* G0;
+  const double* inflow;
+  const int32_t* mat;
+  const double* dirs;
+  const SweepGroup* groups;
+  int nx, ny, n_cells, n_dof, n_mat, n_dirs, n_groups, with_source;
+  double sq_area;
+};
+
+template <int DPW, bool SMEM_TAB>
+__global__ void __launch_bounds__(32) sweep2d_kernel(const Sweep2DArgs A) {
+  const int g = blockIdx.x, b = blockIdx.y, lane = threadIdx.x;
+  if (A.active && !A.active[b]) return;
+  const SweepGroup grp = A.groups[g];
+  const bool xneg = grp.quad & 1, yneg = (grp.quad & 2) != 0;
+  extern __shared__ double smem[];
+  double* ybuf = smem;                                   // [nx][DPW][2]
+  double* tab_s = smem + (size_t)A.nx * DPW * 2;         // [n_mat][DPW][32]
+  double* sig_s = tab_s + (SMEM_TAB ? A.n_mat * DPW * kTab2D : 0);
+  const double* __restrict__ tabg = A.tables + (size_t)b * A.n_mat * A.n_dirs * kTab2D;
+  if (SMEM_TAB) {
+    for (int e = lane; e < A.n_mat * DPW * kTab2D; e += 32) {
+      const int m = e / (DPW * kTab2D), r = e % (DPW * kTab2D), dd = r / kTab2D, k = r % kTab2D;
+      tab_s[e] = dd < grp.nd ? tabg[((size_t)m * A.n_dirs + grp.d0 + dd) * kTab2D + k] : 0.0;
+    }
+  }
+  for (int m = lane; m < A.n_mat; m += 32) sig_s[m] = A.sigma_s[(size_t)b * A.n_mat + m];
+  __syncwarp();
+
+  double w[DPW];
+#pragma unroll
+  for (int dd = 0; dd < DPW; ++dd) w[dd] = dd < grp.nd ? A.dirs[4 * (grp.d0 + dd) + 2] : 0.0;
+  const double s3 = sqrt(3.0);
+  const double c3x = xneg ? -s3 : s3, c3y = yneg ? -s3 : s3;
+  const double gxb = A.with_source ? A.inflow[4 * b + (xneg ? 1 : 0)] * A.sq_area : 0.0;
+  const double gyb = A.with_source ? A.inflow[4 * b + (yneg ? 3 : 2)] * A.sq_area : 0.0;
+  const int H = A.nx < 32 ? A.nx : 32;
+  const int nrb = (A.ny + H - 1) / H;
+  const int total = nrb * A.nx;
+  const double* __restrict__ rin = A.rho_in + (size_t)b * A.n_dof;
+  const double* __restrict__ G0 = A.G0 + (size_t)b * A.n_cells;
+  double* part = A.partial + ((size_t)b * A.n_groups + g) * A.n_dof;
+  double* psi = A.psi_out ? A.psi_out + ((size_t)b * A.n_dirs + grp.d0) * A.n_dof : nullptr;
+
+  double tx[DPW][2], typ[DPW][2];
+#pragma unroll
+  for (int dd = 0; dd < DPW; ++dd) tx[dd][0] = tx[dd][1] = typ[dd][0] = typ[dd][1] = 0.0;
+
+  for (int s = 0; s < total + H - 1; ++s) {
+    const int u = s - lane;
+    const bool inrange = lane < H && u >= 0 && u < total;
+    const int rb = inrange ? u / A.nx : 0;
+    const int t = inrange ? u - rb * A.nx : 0;
+    const int r = rb * H + lane;
+    const bool act = inrange && r < A.ny;
+    double ty[DPW][2];
+#pragma unroll
+    for (int dd = 0; dd < DPW; ++dd) {
+      ty[dd][0] = __shfl_up_sync(0xffffffffu, typ[dd][0], 1);
+      ty[dd][1] = __shfl_up_sync(0xffffffffu, typ[dd][1], 1);
+    }
+    if (act) {
+      if (r == 0) {
+#pragma unroll
+        for (int dd = 0; dd < DPW; ++dd) ty[dd][0] = gyb, ty[dd][1] = 0.0;
+      } else if (lane == 0) {
+#pragma unroll
+        for (int dd = 0; dd < DPW; ++dd) {
+          ty[dd][0] = ybuf[(t * DPW + dd) * 2];
+          ty[dd][1] = ybuf[(t * DPW + dd) * 2 + 1];
+        }
+      }
+      if (t == 0) {
+#pragma unroll
+        for (int dd = 0; dd < DPW; ++dd) tx[dd][0] = gxb, tx[dd][1] = 0.0;
+      }
+      const int i = xneg ? A.nx - 1 - t : t;
+      const int j = yneg ? A.ny - 1 - r : r;
+      const int c = j * A.nx + i;
+      const int m = A.mat[c];
+      const double ss = sig_s[m];
+      const double2 r01 = reinterpret_cast<const double2*>(rin + 4 * (size_t)c)[0];
+      const double2 r23 = reinterpret_cast<const double2*>(rin + 4 * (size_t)c)[1];
+      const double s0 = fma(ss, r01.x, A.with_source ? G0[c] : 0.0);
+      const double s1 = ss * r01.y, s2 = ss * r23.x, s3v = ss * r23.y;
+      double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+#pragma unroll
+      for (int dd = 0; dd < DPW; ++dd) {
+        if (dd < grp.nd) {
+          const double* T = SMEM_TAB ? tab_s + (m * DPW + dd) * kTab2D
+                                     : tabg + ((size_t)m * A.n_dirs + grp.d0 + dd) * kTab2D;
+          double a[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            double v = T[4 * k] * s0;
+            v = fma(T[4 * k + 1], s1, v);
+            v = fma(T[4 * k + 2], s2, v);
+            v = fma(T[4 * k + 3], s3v, v);
+            v = fma(T[16 + 2 * k], tx[dd][0], v);
+            v = fma(T[17 + 2 * k], tx[dd][1], v);
+            v = fma(T[24 + 2 * k], ty[dd][0], v);
+            v = fma(T[25 + 2 * k], ty[dd][1], v);
+            a[k] = v;
+          }
+          tx[dd][0] = fma(c3x, a[1], a[0]);
+          tx[dd][1] = fma(c3x, a[3], a[2]);
+          typ[dd][0] = fma(c3y, a[2], a[0]);
+          typ[dd][1] = fma(c3y, a[3], a[1]);
+          acc0 = fma(w[dd], a[0], acc0);
+          acc1 = fma(w[dd], a[1], acc1);
+          acc2 = fma(w[dd], a[2], acc2);
+          acc3 = fma(w[dd], a[3], acc3);
+          if (psi) {
+            double2* p = reinterpret_cast<double2*>(psi + (size_t)dd * A.n_dof + 4 * (size_t)c);
+            p[0] = make_double2(a[0], a[1]);
+            p[1] = make_double2(a[2], a[3]);
+          }
+        }
+      }
+      double2* po = reinterpret_cast<double2*>(part + 4 * (size_t)c);
+      po[0] = make_double2(acc0, acc1);
+      po[1] = make_double2(acc2, acc3);
+      if (lane == H - 1 && rb + 1 < nrb) {
+#pragma unroll
+        for (int dd = 0; dd < DPW; ++dd) {
+          ybuf[(t * DPW + dd) * 2] = typ[dd][0];
+          ybuf[(t * DPW + dd) * 2 + 1] = typ[dd][1];
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+struct Sweep1DArgs {
+  const double* rho_in;
+  double* partial;
+  double* psi_out;
+  const uint8_t* active;
+  const double* tables;
+  const double* sigma_s;
+  const double* G0;
+  const double* inflow;
+  const int32_t* mat;
+  const double* dirs;
+  int B, nx, n_dof, n_mat, n_dirs, with_source;
+  double sq_h;
+};
+
+// 1D slab: one thread per (instance, direction), sequential in upwind order (2x2 cell solves).
+__global__ void sweep1d_kernel(const Sweep1DArgs A) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= A.B * A.n_dirs) return;
+  const int b = idx / A.n_dirs, d = idx % A.n_dirs;
+  if (A.active && !A.active[b]) return;
+  const double xi = A.dirs[4 * d], w = A.dirs[4 * d + 2];
+  const bool neg = xi < 0;
+  const double c3 = neg ? -sqrt(3.0) : sqrt(3.0);
+  double t = A.with_source ? A.inflow[4 * b + (neg ? 1 : 0)] * A.sq_h : 0.0;
+  const double* rin = A.rho_in + (size_t)b * A.n_dof;
+  double* part = A.partial + ((size_t)b * A.n_dirs + d) * A.n_dof;
+  double* psi = A.psi_out ? A.psi_out + ((size_t)b * A.n_dirs + d) * A.n_dof : nullptr;
+  const double* tab = A.tables + (size_t)b * A.n_mat * A.n_dirs * kTab1D;
+  for (int step = 0; step < A.nx; ++step) {
+    const int c = neg ? A.nx - 1 - step : step;
+    const int m = A.mat[c];
+    const double* T = tab + ((size_t)m * A.n_dirs + d) * kTab1D;
+    const double ss = A.sigma_s[(size_t)b * A.n_mat + m];
+    const double s0 = fma(ss, rin[2 * c], A.with_source ? A.G0[(size_t)b * A.nx + c] : 0.0);
+    const double s1 = ss * rin[2 * c + 1];
+    const double a0 = fma(T[4], t, fma(T[1], s1, T[0] * s0));
+    const double a1 = fma(T[5], t, fma(T[3], s1, T[2] * s0));
+    t = fma(c3, a1, a0);
+    part[2 * c] = w * a0;
+    part[2 * c + 1] = w * a1;
+    if (psi) psi[2 * c] = a0, psi[2 * c + 1] = a1;
+  }
+}
+
+// rho_out = sum of the group partials (fixed order); optional stop-test norms per instance.
+__global__ void reduce_partials_kernel(const double* __restrict__ partial,
+                                       const double* __restrict__ rho_in, double* rho_out,
+                                       unsigned long long* norms, const uint8_t* active,
+                                       int n_groups, int n_dof) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  double dmax = 0.0, rmax = 0.0;
+  if (e < n_dof) {
+    const double* p = partial + (size_t)b * n_groups * n_dof + e;
+    double2 acc = reinterpret_cast<const double2*>(p)[0];
+    for (int g = 1; g < n_groups; ++g) {
+      const double2 v = reinterpret_cast<const double2*>(p + (size_t)g * n_dof)[0];
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    reinterpret_cast<double2*>(rho_out + (size_t)b * n_dof + e)[0] = acc;
+    if (norms) {
+      const double2 ri = reinterpret_cast<const double2*>(rho_in + (size_t)b * n_dof + e)[0];
+      dmax = fmax(fabs(acc.x - ri.x), fabs(acc.y - ri.y));
+      rmax = fmax(fabs(acc.x), fabs(acc.y));
+    }
+  }
+  if (!norms) return;
+  for (int o = 16; o > 0; o >>= 1) {
+    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+  }
+  __shared__ double sd[32], sr[32];
+  const int wid = threadIdx.x >> 5, ln = threadIdx.x & 31;
+  if (ln == 0) sd[wid] = dmax, sr[wid] = rmax;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    dmax = ln < nw ? sd[ln] : 0.0;
+    rmax = ln < nw ? sr[ln] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    }
+    if (ln == 0) {
+      // non-negative doubles order like their bit patterns: atomicMax on the bits is exact
+      atomicMax(norms + 2 * b, (unsigned long long)__double_as_longlong(dmax));
+      atomicMax(norms + 2 * b + 1, (unsigned long long)__double_as_longlong(rmax));
+    }
+  }
+}
+
+__global__ void change_norm_kernel(const double* __restrict__ rs, const double* __restrict__ rp,
+                                   unsigned long long* norms, int n_dof) {
+  const int b = blockIdx.y;
+  double dmax = 0.0, rmax = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_dof; e += gridDim.x * blockDim.x) {
+    const double a = rs[(size_t)b * n_dof + e], c = rp[(size_t)b * n_dof + e];
+    dmax = fmax(dmax, fabs(a - c));
+    rmax = fmax(rmax, fabs(a));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(norms + 2 * b, (unsigned long long)__double_as_longlong(dmax));
+    atomicMax(norms + 2 * b + 1, (unsigned long long)__double_as_longlong(rmax));
+  }
+}
+
+__global__ void bits_to_double_kernel(const unsigned long long* bits, double* out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = __longlong_as_double((long long)bits[i]);
+}
+
+// R = Sigma_s (rho_star - rho_prev), cellwise-constant sigma_s (orthonormal basis).
+__global__ void correction_source_kernel(const double* rs, const double* rp, double* R,
+                                         const double* sigma_s, const int32_t* mat,
+                                         const uint8_t* active, int n_dof, int P, int n_mat) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_dof; e += gridDim.x * blockDim.x) {
+    const size_t o = (size_t)b * n_dof + e;
+    R[o] = sigma_s[(size_t)b * n_mat + mat[e / P]] * (rs[o] - rp[o]);
+  }
+}
+
+__global__ void add_kernel(const double* x, const double* y, double* out, const uint8_t* active,
+                           int n_dof) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_dof; e += gridDim.x * blockDim.x) {
+    const size_t o = (size_t)b * n_dof + e;
+    out[o] = x[o] + y[o];
+  }
+}
+
+// ---- host side ----------------------------------------------------------------------------
+
+int setup_tables(rte_batch_t bt, cudaStream_t st) {
+  const rte_disc_s* d = bt->disc;
+  const int n = bt->B * d->n_mat * d->n_dirs;
+  const int th = 128, bl = (n + th - 1) / th;
+  if (d->dim == 2)
+    tables2d_kernel<<<bl, th, 0, st>>>(bt->tables.p, bt->sigma_t.p, d->dir_dev.p, bt->B, d->n_mat,
+                                       d->n_dirs, d->hx, d->hy);
+  else
+    tables1d_kernel<<<bl, th, 0, st>>>(bt->tables.p, bt->sigma_t.p, d->dir_dev.p, bt->B, d->n_mat,
+                                       d->n_dirs, d->hx);
+  RTE_CUDA_TRY(cudaGetLastError());
+  return RTE_OK;
+}
+
+template <int DPW>
+static int launch2d(const Sweep2DArgs& A, int B, int n_groups, cudaStream_t st) {
+  const size_t ybytes = (size_t)A.nx * DPW * 2 * sizeof(double);
+  const size_t tbytes = (size_t)A.n_mat * DPW * kTab2D * sizeof(double);
+  const size_t sbytes = (size_t)A.n_mat * sizeof(double);
+  dim3 grid(n_groups, B);
+  if (ybytes + tbytes + sbytes <= 48 * 1024) {
+    sweep2d_kernel<DPW, true><<<grid, 32, ybytes + tbytes + sbytes, st>>>(A);
+  } else {
+    const size_t bytes = ybytes + sbytes;
+    if (bytes > 200 * 1024) return fail(RTE_EINVAL, "sweep: mesh row too long for shared memory");
+    if (bytes > 48 * 1024)
+      RTE_CUDA_TRY(cudaFuncSetAttribute(sweep2d_kernel<DPW, false>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    sweep2d_kernel<DPW, false><<<grid, 32, bytes, st>>>(A);
+  }
+  RTE_CUDA_TRY(cudaGetLastError());
+  return RTE_OK;
+}
+
+int sweep_launch(rte_batch_t bt, const double* rho_in, double* rho_out, double* psi_out,
+                 int with_source, const uint8_t* active, cudaStream_t st, bool fuse_norms) {
+  const rte_disc_s* d = bt->disc;
+  const int n_groups = (int)bt->groups.size();
+  if (d->dim == 2) {
+    Sweep2DArgs A{rho_in,       bt->partial.p, psi_out,        active,      bt->tables.p,
+                  bt->sigma_s.p, bt->G0.p,     bt->inflow.p,   d->mat_id.p, d->dir_dev.p,
+                  bt->groups_dev.p, d->nx,     d->ny,          d->n_cells,  d->n_dof,
+                  d->n_mat,     d->n_dirs,     n_groups,       with_source, std::sqrt(d->hx * d->hy)};
+    switch (bt->dpw) {
+      case 1: RTE_TRY(launch2d<1>(A, bt->B, n_groups, st)); break;
+      case 2: RTE_TRY(launch2d<2>(A, bt->B, n_groups, st)); break;
+      case 4: RTE_TRY(launch2d<4>(A, bt->B, n_groups, st)); break;
+      case 8: RTE_TRY(launch2d<8>(A, bt->B, n_groups, st)); break;
+      default: return fail(RTE_EINVAL, "unsupported directions-per-warp");
+    }
+  } else {
+    Sweep1DArgs A{rho_in,      bt->partial.p, psi_out,  active, bt->tables.p, bt->sigma_s.p,
+                  bt->G0.p,    bt->inflow.p,  d->mat_id.p, d->dir_dev.p, bt->B, d->nx,
+                  d->n_dof,    d->n_mat,      d->n_dirs, with_source, std::sqrt(d->hx)};
+    const int n = bt->B * d->n_dirs;
+    sweep1d_kernel<<<(n + 63) / 64, 64, 0, st>>>(A);
+    RTE_CUDA_TRY(cudaGetLastError());
+  }
+  if (fuse_norms) RTE_CUDA_TRY(cudaMemsetAsync(bt->norms.p, 0, sizeof(unsigned long long) * 2 * bt->B, st));
+  const int th = 256;
+  dim3 grid((d->n_dof / 2 + th - 1) / th, bt->B);
+  reduce_partials_kernel<<<grid, th, 0, st>>>(bt->partial.p, rho_in, rho_out,
+                                             fuse_norms ? bt->norms.p : nullptr, active, n_groups,
+                                             d->n_dof);
+  RTE_CUDA_TRY(cudaGetLastError());
+  return RTE_OK;
+}
+
+int norms_to_host(rte_batch_t bt, double* host, cudaStream_t st) {
+  std::vector<unsigned long long> bits(2 * bt->B);
+  RTE_CUDA_TRY(cudaMemcpyAsync(bits.data(), bt->norms.p, sizeof(unsigned long long) * bits.size(),
+                               cudaMemcpyDeviceToHost, st));
+  RTE_CUDA_TRY(cudaStreamSynchronize(st));
+  for (size_t k = 0; k < bits.size(); ++k) {
+    long long v = (long long)bits[k];
+    double x;
+    std::memcpy(&x, &v, sizeof(double));
+    host[k] = x;
+  }
+  return RTE_OK;
+}
+
+int correction_source_launch(rte_batch_t bt, const double* rs, const double* rp, double* R,
+                             const uint8_t* active, cudaStream_t st) {
+  const rte_disc_s* d = bt->disc;
+  dim3 grid(std::min((d->n_dof + 255) / 256, 1024), bt->B);
+  correction_source_kernel<<<grid, 256, 0, st>>>(rs, rp, R, bt->sigma_s.p, d->mat_id.p, active,
+                                                 d->n_dof, d->P, d->n_mat);
+  RTE_CUDA_TRY(cudaGetLastError());
+  return RTE_OK;
+}
+
+int axpy_launch(rte_batch_t bt, const double* x, const double* y, double* out,
+                const uint8_t* active, cudaStream_t st) {
+  const rte_disc_s* d = bt->disc;
+  dim3 grid(std::min((d->n_dof + 255) / 256, 1024), bt->B);
+  add_kernel<<<grid, 256, 0, st>>>(x, y, out, active, d->n_dof);
+  RTE_CUDA_TRY(cudaGetLastError());
+  return RTE_OK;
+}
+
+}  // namespace rte
+
+using namespace rte;
+
+extern "C" int rte_sweep(rte_batch_t b, const double* rho_in, double* rho_out, double* psi_out,
+                         int with_source, const uint8_t* active, void* stream) {
+  if (!b || !rho_in || !rho_out) return fail(RTE_EINVAL, "rte_sweep: null argument");
+  if (!b->params_set) return fail(RTE_ESTATE, "rte_sweep: parameters not set");
+  if (rho_in == rho_out) return fail(RTE_EINVAL, "rte_sweep: rho_out aliases rho_in");
+  if (((uintptr_t)rho_in | (uintptr_t)rho_out | (uintptr_t)psi_out) & 15)
+    return fail(RTE_EINVAL, "rte_sweep: arrays must be 16-byte aligned");
+  DeviceGuard g(b->disc->device);
+  return sweep_launch(b, rho_in, rho_out, psi_out, with_source, active, (cudaStream_t)stream,
+                      false);
+}
+
+extern "C" int rte_change_norm(rte_batch_t b, const double* rho_star, const double* rho_prev,
+                               double* norms, void* stream) {
+  if (!b || !rho_star || !rho_prev || !norms) return fail(RTE_EINVAL, "rte_change_norm: null");
+  DeviceGuard g(b->disc->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  RTE_CUDA_TRY(cudaMemsetAsync(b->norms.p, 0, sizeof(unsigned long long) * 2 * b->B, st));
+  dim3 grid(std::min((b->disc->n_dof + 255) / 256, 256), b->B);
+  change_norm_kernel<<<grid, 256, 0, st>>>(rho_star, rho_prev, b->norms.p, b->disc->n_dof);
+  bits_to_double_kernel<<<(2 * b->B + 127) / 128, 128, 0, st>>>(b->norms.p, norms, 2 * b->B);
+  RTE_CUDA_TRY(cudaGetLastError());
+  return RTE_OK;
+}
+
+extern "C" int rte_correction_source(rte_batch_t b, const double* rho_star, const double* rho_prev,
+                                     double* R, void* stream) {
+  if (!b || !rho_star || !rho_prev || !R) return fail(RTE_EINVAL, "rte_correction_source: null");
+  if (!b->params_set) return fail(RTE_ESTATE, "parameters not set");
+  DeviceGuard g(b->disc->device);
+  return correction_source_launch(b, rho_star, rho_prev, R, nullptr, (cudaStream_t)stream);
+}

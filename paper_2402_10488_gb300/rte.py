@@ -1,0 +1,278 @@
+"""Thin ctypes binding of the C ABI in include/rte.h (argument marshalling only).
+
+Device arrays are torch CUDA tensors (float64, contiguous) passed by ``data_ptr()``; streams
+default to torch's current stream.  Every computation runs in the CUDA library; if the compiled
+library is missing, ``lib()`` raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librte_gb300.so")
+
+RTE_OK, RTE_EINVAL, RTE_ENOMEM, RTE_ENOCONV, RTE_ETIMEOUT, RTE_ECUDA, RTE_ESTATE = 0, -1, -2, -3, -4, -5, -6
+SA_NONE, SA_DSA, SA_ROMSA, SA_ROMSAD = 0, 1, 2, 3
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+# exported symbol -> (restype, argtypes); mirrors include/rte.h
+SIGNATURES = {
+    "rte_version": (_I, []),
+    "rte_last_error": (ctypes.c_char_p, []),
+    "rte_disc_create": (_I, [_P, _I, _P]),
+    "rte_disc_destroy": (_I, [_P]),
+    "rte_disc_info": (_I, [_P, _P]),
+    "rte_disc_quadrature": (_I, [_P, _P, _P]),
+    "rte_batch_create": (_I, [_P, _I, _P]),
+    "rte_batch_destroy": (_I, [_P]),
+    "rte_batch_set_params": (_I, [_P, _P, _P, _P, _P]),
+    "rte_batch_directions": (_I, [_P, _P]),
+    "rte_sweep": (_I, [_P, _P, _P, _P, _I, _P, _P]),
+    "rte_change_norm": (_I, [_P, _P, _P, _P, _P]),
+    "rte_dsa_correction": (_I, [_P, _P, _P, _D, _I, _P, _P, _P]),
+    "rte_correction_source": (_I, [_P, _P, _P, _P, _P]),
+    "rte_rom_build": (_I, [_P, _P, _P, _P, _P]),
+    "rte_rom_destroy": (_I, [_P]),
+    "rte_rom_info": (_I, [_P, _P, _P]),
+    "rte_rom_initial_guess": (_I, [_P, _P, _P, _P, _P]),
+    "rte_romsa_correction": (_I, [_P, _P, _P, _P, _P, _P]),
+    "rte_solve": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+}
+
+
+class RTEError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"RTE status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load the compiled library (no fallback: raises when it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run paper_2402_10488_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name, None)
+            if fn is None:
+                continue
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status, allow=()):
+    if status != RTE_OK and status not in allow:
+        raise RTEError(status, lib().rte_last_error().decode())
+    return status
+
+
+class _DiscDesc(ctypes.Structure):
+    _fields_ = [("dim", _I), ("nx", _I), ("ny", _I), ("x0", _D), ("x1", _D), ("y0", _D),
+                ("y1", _D), ("n_phi", _I), ("n_vz", _I), ("n_mat", _I), ("mat_id", _P)]
+
+
+class _RomOpts(ctypes.Structure):
+    _fields_ = [("eps_train", _D), ("window", _I), ("rank_p", _I), ("rank_c", _I),
+                ("eps_pod", _D), ("max_iter", _I), ("dsa_rtol", _D)]
+
+
+class _SolveOpts(ctypes.Structure):
+    _fields_ = [("eps", _D), ("rel", _I), ("max_iter", _I), ("sa", _I), ("theta", _I),
+                ("eps_romsad", _D), ("dsa_rtol", _D), ("dsa_max_it", _I), ("schedule", _P)]
+
+
+class SolveReport(ctypes.Structure):
+    _fields_ = [("n_sweep", _I), ("converged", _I), ("n_romsa", _I), ("n_dsa", _I),
+                ("dsa_iters", _I), ("last_change", _D), ("rho_inf", _D)]
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _host(a, dtype=np.float64):
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+class Disc:
+    """Discretisation handle: mesh, S_N rule, material map (rte_disc_create)."""
+
+    def __init__(self, problem, device=0):
+        L = lib()
+        self._mat = _host(problem.mat_id, np.int32)
+        dom = tuple(problem.domain) + ((0.0, 1.0) if problem.dim == 1 else ())
+        d = _DiscDesc(problem.dim, problem.nx, problem.ny, dom[0], dom[1], dom[2], dom[3],
+                      problem.n_phi, problem.n_vz, problem.n_mat,
+                      self._mat.ctypes.data_as(_P))
+        h = _P()
+        check(L.rte_disc_create(ctypes.byref(d), device, ctypes.byref(h)))
+        self.h = h
+        self.device = device
+        info = np.zeros(8, np.int64)
+        check(L.rte_disc_info(h, info.ctypes.data_as(_P)))
+        (self.n_cells, self.n_dof, self.P, self.n_angles, self.n_dirs, self.n_mat, self.dim,
+         _) = (int(x) for x in info)
+
+    def quadrature(self):
+        v = np.zeros((self.n_angles, 3))
+        w = np.zeros(self.n_angles)
+        check(lib().rte_disc_quadrature(self.h, v.ctypes.data_as(_P), w.ctypes.data_as(_P)))
+        return v, w
+
+    def close(self):
+        if self.h:
+            lib().rte_disc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """B parametric instances on one discretisation (rte_batch_create / _set_params)."""
+
+    def __init__(self, disc: Disc, B: int):
+        h = _P()
+        check(lib().rte_batch_create(disc.h, int(B), ctypes.byref(h)))
+        self.h = h
+        self.disc = disc
+        self.B = int(B)
+
+    @classmethod
+    def from_problem(cls, problem, disc: Disc | None = None, device=0):
+        disc = disc or Disc(problem, device)
+        b = cls(disc, problem.batch)
+        b.set_params(problem)
+        return b
+
+    def set_params(self, problem):
+        st = _host(problem.sigma_t)
+        ss = _host(problem.sigma_s)
+        src = _host(problem.source)
+        inf = _host(problem.inflow)
+        check(lib().rte_batch_set_params(self.h, st.ctypes.data_as(_P), ss.ctypes.data_as(_P),
+                                         src.ctypes.data_as(_P), inf.ctypes.data_as(_P)))
+
+    def directions(self):
+        d = np.zeros((self.disc.n_dirs, 4))
+        check(lib().rte_batch_directions(self.h, d.ctypes.data_as(_P)))
+        return d
+
+    def sweep(self, rho_in, rho_out, psi_out=None, with_source=True, active=None, stream=None):
+        check(lib().rte_sweep(self.h, _ptr(rho_in), _ptr(rho_out), _ptr(psi_out),
+                              1 if with_source else 0, _ptr(active), _stream(stream)))
+
+    def change_norm(self, rho_star, rho_prev, norms, stream=None):
+        check(lib().rte_change_norm(self.h, _ptr(rho_star), _ptr(rho_prev), _ptr(norms),
+                                    _stream(stream)))
+
+    def correction_source(self, rho_star, rho_prev, R, stream=None):
+        check(lib().rte_correction_source(self.h, _ptr(rho_star), _ptr(rho_prev), _ptr(R),
+                                          _stream(stream)))
+
+    def dsa_correction(self, R, drho, rtol=1e-10, max_it=500, active=None, stream=None):
+        iters = np.zeros(self.B, np.int32)
+        st = check(lib().rte_dsa_correction(self.h, _ptr(R), _ptr(drho), float(rtol), int(max_it),
+                                            _ptr(active), iters.ctypes.data_as(_P),
+                                            _stream(stream)), allow=(RTE_ENOCONV,))
+        return iters, st
+
+    def solve(self, rho, eps, sa=SA_DSA, rel=False, max_iter=1000, theta=0, eps_romsad=0.0,
+              dsa_rtol=1e-10, dsa_max_it=500, rom_c=None, schedule=None, history=False,
+              stream=None):
+        sched = None if schedule is None else _host(schedule, np.uint8)
+        opts = _SolveOpts(float(eps), 1 if rel else 0, int(max_iter), int(sa), int(theta),
+                          float(eps_romsad), float(dsa_rtol), int(dsa_max_it),
+                          None if sched is None else sched.ctypes.data_as(_P))
+        reps = (SolveReport * self.B)()
+        hist = np.zeros((self.B, max_iter)) if history else None
+        st = check(lib().rte_solve(self.h, ctypes.byref(opts), None if rom_c is None else rom_c.h,
+                                   _ptr(rho), reps,
+                                   None if hist is None else hist.ctypes.data_as(_P),
+                                   _stream(stream)), allow=(RTE_ENOCONV,))
+        rep = [dict(n_sweep=r.n_sweep, converged=bool(r.converged), n_romsa=r.n_romsa,
+                    n_dsa=r.n_dsa, dsa_iters=r.dsa_iters, last_change=r.last_change,
+                    rho_inf=r.rho_inf) for r in reps]
+        return rep, hist, st
+
+    def close(self):
+        if self.h:
+            lib().rte_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Rom:
+    """A POD reduced model built on the GPU (rte_rom_build)."""
+
+    def __init__(self, h):
+        self.h = h
+        info = np.zeros(6)
+        check(lib().rte_rom_info(h, info.ctypes.data_as(_P), None))
+        self.r, self.n_snap = int(info[0]), int(info[1])
+        self.eps_pod = float(info[2])
+        sv = np.zeros(max(self.n_snap, 1))
+        check(lib().rte_rom_info(h, info.ctypes.data_as(_P), sv.ctypes.data_as(_P)))
+        self.sv = sv[: self.n_snap]
+
+    @staticmethod
+    def build(train: Batch, eps_train=1e-12, window=3, rank_p=20, rank_c=20, eps_pod=1e-9,
+              max_iter=2000, dsa_rtol=1e-12, stream=None):
+        o = _RomOpts(float(eps_train), int(window), int(rank_p), int(rank_c), float(eps_pod),
+                     int(max_iter), float(dsa_rtol))
+        hp, hc = _P(), _P()
+        check(lib().rte_rom_build(train.h, ctypes.byref(o), ctypes.byref(hp), ctypes.byref(hc),
+                                  _stream(stream)))
+        return Rom(hp), Rom(hc)
+
+    def initial_guess(self, batch: Batch, rho0, active=None, stream=None):
+        check(lib().rte_rom_initial_guess(self.h, batch.h, _ptr(rho0), _ptr(active),
+                                          _stream(stream)))
+
+    def romsa_correction(self, batch: Batch, R, drho, active=None, stream=None):
+        check(lib().rte_romsa_correction(self.h, batch.h, _ptr(R), _ptr(drho), _ptr(active),
+                                         _stream(stream)))
+
+    def close(self):
+        if self.h:
+            lib().rte_rom_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
