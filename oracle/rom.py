@@ -90,7 +90,8 @@ class ReducedModel:
 
     def romsa_correction(self, tr: Transport, R):
         """ROMSA: delta rho = dU^rho dc with (dU^T A_mu dU) dc = (dU^iso)^T R, R = Sigma_s(rho* - rho)."""
-        key = id(tr)
+        # cache the reduced operator per parameter set (keyed by the values, not the object)
+        key = (tuple(tr.sigma_t_mat), tuple(tr.sigma_s_mat))
         if key not in self._cache:
             self._cache = {key: self._op_for(tr)}
         dc = np.linalg.solve(self._cache[key], self.U_iso.T @ R)

@@ -149,15 +149,19 @@ int dsa_apply(rte_batch_t b, const double* R, double* drho, double rtol, int max
               const uint8_t* active, int* iters, cudaStream_t st);
 }  // namespace rte
 
+namespace rte { struct RomOnline; }
+
 struct rte_rom_s {
   rte_disc_s* disc = nullptr;
   int r = 0, n_snap = 0;
   std::vector<double> sv;
   double eps_equiv = 0;
-  rte::DevBuf<double> U;       // [n_dirs][n_dof][r]  per distinct direction (row blocks U_j)
-  rte::DevBuf<double> U_rho;   // [n_dof][r]
-  rte::DevBuf<double> U_iso;   // [n_dof][r]
+  rte::DevBuf<double> U;       // [r][n_dirs][n_dof]: basis vectors, one row block per direction
+  rte::DevBuf<double> U_rho;   // [r][n_dof]
+  rte::DevBuf<double> U_iso;   // [r][n_dof]
   std::vector<double> A0;      // [r][r]
   std::vector<double> Aa, As;  // [n_mat][r][r]
-  rte::DevBuf<double> scratch; // per-call workspace
+  rte::DevBuf<double> A0_dev, Aa_dev, As_dev;
+  rte::RomOnline* online = nullptr;
+  ~rte_rom_s();
 };

@@ -1,11 +1,1001 @@
-// Consistent DSA (App. B) -- placeholder until the solver lands.
+// Consistent diffusion synthetic acceleration (paper App. B; used as stated in Sec. 4.1.1).
+//
+// The DSA correction solves the moment system obtained from the P1 ansatz
+// delta f = delta rho + 3 v . delta J substituted into the upwind DG correction equation.
+//
+// 1D (App. B as printed), unknowns (drho, dJ) per cell:
+//     D_C dJ - c1 D_J drho + Sigma_a drho = R,      c1 = sum_{v>0} w v
+//     c2 D_C drho + (Sigma_t - 3 c3 D_J) dJ = 0,     c2 = sum w v^2, c3 = sum_{v>0} w v^3
+// is block tridiagonal (4x4 blocks per cell) and is solved directly (block Thomas), as the paper
+// solves 1D DSA with a direct solver.
+//
+// 2D: the same derivation in X-Y geometry gives, per cell, 12 unknowns (drho, dJx, dJy):
+//     [Sigma_a - <|vx|>/2 DJx - <|vy|>/2 DJy] drho + 3<vx^2> DCx dJx + 3<vy^2> DCy dJy = R
+//     <vx^2> DCx drho + [3<vx^2> Sigma_t - 3/2 <|vx|^3> DJx - 3/2 <vx^2|vy|> DJy] dJx = 0
+//     <vy^2> DCy drho + [3<vy^2> Sigma_t - 3/2 <|vy|^3> DJy - 3/2 <vy^2|vx|> DJx] dJy = 0
+// (<.> = quadrature sums).  On a uniform mesh D_C and D_J are geometry-only: per cell a 12x12
+// diagonal block that depends on the cell's material, and four constant 12x12 neighbour blocks.
+// The paper solves this with algebraic multigrid; here it is solved by flexible GMRES with an
+// FP64 matrix-free operator, preconditioned by one geometric multigrid V-cycle in FP32:
+// Galerkin coarse operators P^T A P built from the nested DG spaces (a coarse cell's Q^1
+// functions restricted to its 2x2 children), red-black 12x12-block Gauss-Seidel smoothing, and
+// the 1x1 coarsest level inverted exactly.  The preconditioner's precision affects only the
+// iteration count; the FP64 residual decides convergence.
 #include "common.cuh"
 
 namespace rte {
-struct DsaState {};
-void dsa_state_free(DsaState* s) { delete s; }
-int dsa_setup(rte_batch_t, cudaStream_t) { return RTE_OK; }
-int dsa_apply(rte_batch_t, const double*, double*, double, int, const uint8_t*, int*, cudaStream_t) {
-  return fail(RTE_ESTATE, "DSA not available");
+
+constexpr int NB = 12;     // unknowns per cell (3 fields x 4 Q1 moments)
+constexpr int NB2 = 144;
+
+// ---- 1D local operators (orthonormal P1 basis, traces L=(1,-s3)/sqrt h, R=(1,s3)/sqrt h) -----
+struct Ops1D {
+  double DCd[4], DCw[4], DCe[4], DJd[4], DJw[4], DJe[4];  // 2x2 row-major
+};
+
+static Ops1D ops1d(double h) {
+  const double s3 = std::sqrt(3.0), q = 1.0 / std::sqrt(h);
+  const double L[2] = {q, -s3 * q}, R[2] = {q, s3 * q};
+  Ops1D o{};
+  for (int k = 0; k < 2; ++k)
+    for (int l = 0; l < 2; ++l) {
+      const double V = (k == 1 && l == 0) ? -2.0 * s3 / h : 0.0;  // -int phi_k' phi_l
+      o.DCd[2 * k + l] = V + 0.5 * (R[k] * R[l] - L[k] * L[l]);
+      o.DCw[2 * k + l] = -0.5 * L[k] * R[l];
+      o.DCe[2 * k + l] = 0.5 * R[k] * L[l];
+      o.DJd[2 * k + l] = -L[k] * L[l] - R[k] * R[l];
+      o.DJw[2 * k + l] = L[k] * R[l];
+      o.DJe[2 * k + l] = R[k] * L[l];
+    }
+  return o;
 }
+
+// 4x4 operator acting on the x-degree (k = a + 2b): (I_b (x) A)[a+2b][a'+2b'] = A[a][a'] d_bb'
+static void kron_x(const double A[4], double out[16]) {
+  for (int k = 0; k < 16; ++k) out[k] = 0.0;
+  for (int b = 0; b < 2; ++b)
+    for (int a = 0; a < 2; ++a)
+      for (int a2 = 0; a2 < 2; ++a2) out[4 * (a + 2 * b) + (a2 + 2 * b)] = A[2 * a + a2];
+}
+static void kron_y(const double A[4], double out[16]) {
+  for (int k = 0; k < 16; ++k) out[k] = 0.0;
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b)
+      for (int b2 = 0; b2 < 2; ++b2) out[4 * (a + 2 * b) + (a + 2 * b2)] = A[2 * b + b2];
+}
+
+// 12x12 block from 4x4 x/y pieces; diag adds the sigma terms.
+static void field_block(const DsaMoments& m, const double DCx[16], const double DJx[16],
+                        const double DCy[16], const double DJy[16], double sa, double st,
+                        bool diag, double out[NB2]) {
+  for (int k = 0; k < NB2; ++k) out[k] = 0.0;
+  auto put = [&](int fr, int fc, int r, int c, double v) { out[(4 * fr + r) * NB + 4 * fc + c] += v; };
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c) {
+      const int e = 4 * r + c;
+      const double I = (diag && r == c) ? 1.0 : 0.0;
+      put(0, 0, r, c, -0.5 * m.abs_x * DJx[e] - 0.5 * m.abs_y * DJy[e] + sa * I);
+      put(0, 1, r, c, 3.0 * m.xx * DCx[e]);
+      put(0, 2, r, c, 3.0 * m.yy * DCy[e]);
+      put(1, 0, r, c, m.xx * DCx[e]);
+      put(1, 1, r, c, -1.5 * m.abs3_x * DJx[e] - 1.5 * m.xx_absy * DJy[e] + 3.0 * m.xx * st * I);
+      put(2, 0, r, c, m.yy * DCy[e]);
+      put(2, 2, r, c, -1.5 * m.abs3_y * DJy[e] - 1.5 * m.yy_absx * DJx[e] + 3.0 * m.yy * st * I);
+    }
+}
+
+static void invert_host(const double* A, double* Ai, int n) {
+  std::vector<double> a(2 * n * n);
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < 2 * n; ++c) a[r * 2 * n + c] = c < n ? A[r * n + c] : (c - n == r ? 1.0 : 0.0);
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    for (int r = k + 1; r < n; ++r)
+      if (std::fabs(a[r * 2 * n + k]) > std::fabs(a[p * 2 * n + k])) p = r;
+    if (p != k)
+      for (int c = 0; c < 2 * n; ++c) std::swap(a[k * 2 * n + c], a[p * 2 * n + c]);
+    const double piv = 1.0 / a[k * 2 * n + k];
+    for (int c = 0; c < 2 * n; ++c) a[k * 2 * n + c] *= piv;
+    for (int r = 0; r < n; ++r)
+      if (r != k) {
+        const double f = a[r * 2 * n + k];
+        if (f != 0.0)
+          for (int c = 0; c < 2 * n; ++c) a[r * 2 * n + c] -= f * a[k * 2 * n + c];
+      }
+  }
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) Ai[r * n + c] = a[r * 2 * n + n + c];
+}
+
+// ---- device helpers -------------------------------------------------------------------------
+
+template <class T>
+__device__ __forceinline__ void inv12(T* a /*[12][24] scratch*/) {
+  for (int k = 0; k < NB; ++k) {
+    int p = k;
+    for (int r = k + 1; r < NB; ++r)
+      if (fabs((double)a[r * 24 + k]) > fabs((double)a[p * 24 + k])) p = r;
+    if (p != k)
+      for (int c = 0; c < 24; ++c) {
+        T t = a[k * 24 + c];
+        a[k * 24 + c] = a[p * 24 + c];
+        a[p * 24 + c] = t;
+      }
+    const T piv = (T)1 / a[k * 24 + k];
+    for (int c = 0; c < 24; ++c) a[k * 24 + c] *= piv;
+    for (int r = 0; r < NB; ++r)
+      if (r != k) {
+        const T f = a[r * 24 + k];
+        for (int c = 0; c < 24; ++c) a[r * 24 + c] -= f * a[k * 24 + c];
+      }
+  }
+}
+
+// Level geometry and data (device pointers), one instance stride per array.
+struct Lvl {
+  int nx, ny, nc;
+  const float* blk;   // [B][nc][5][144] (levels >= 1)
+  const float* dinv;  // [B][nc][144]    (levels >= 1)
+};
+
+struct Fine {
+  const double* off64;   // [4][144] W, E, S, N (constant)
+  const float* off32;
+  const double* diag64;  // [B][n_mat][144]
+  const float* diag32;
+  const float* dinv32;   // [B][n_mat][144]
+  const int32_t* mat;
+  int n_mat;
+};
+
+__device__ __forceinline__ bool nbr(int d, int i, int j, int nx, int ny, int& c2) {
+  int ii = i, jj = j;
+  if (d == 1) --ii;
+  else if (d == 2) ++ii;
+  else if (d == 3) --jj;
+  else ++jj;
+  if (ii < 0 || ii >= nx || jj < 0 || jj >= ny) return false;
+  c2 = jj * nx + ii;
+  return true;
+}
+
+// y = A0 x in FP64 on the fine level (structured).  One thread per (cell, row-of-block).
+__global__ void fine_apply64_kernel(Fine F, int nx, int ny, int B, const double* __restrict__ x,
+                                    double* __restrict__ y, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int nc = nx * ny;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nc * NB) return;
+  const int c = t / NB, row = t % NB;
+  const int i = c % nx, j = c / nx;
+  const double* xb = x + (size_t)b * nc * NB;
+  const double* D = F.diag64 + ((size_t)b * F.n_mat + F.mat[c]) * NB2 + row * NB;
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 0; k < NB; ++k) acc = fma(D[k], xb[(size_t)c * NB + k], acc);
+  for (int d = 1; d <= 4; ++d) {
+    int c2;
+    if (!nbr(d, i, j, nx, ny, c2)) continue;
+    const double* O = F.off64 + (d - 1) * NB2 + row * NB;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) acc = fma(O[k], xb[(size_t)c2 * NB + k], acc);
+  }
+  y[(size_t)b * nc * NB + t] = acc;
+}
+
+// Block row of level operator times a vector, excluding (self=false) or including the diagonal.
+template <bool STRUCT>
+__device__ __forceinline__ void block_row(const Fine& F, const Lvl& L, int b, int c, int i, int j,
+                                          const float* __restrict__ x, bool with_self,
+                                          float acc[NB]) {
+  for (int d = with_self ? 0 : 1; d <= 4; ++d) {
+    int c2 = c;
+    if (d > 0 && !nbr(d, i, j, L.nx, L.ny, c2)) continue;
+    const float* A;
+    if (STRUCT)
+      A = d == 0 ? F.diag32 + ((size_t)b * F.n_mat + F.mat[c]) * NB2 : F.off32 + (d - 1) * NB2;
+    else
+      A = L.blk + (((size_t)b * L.nc + c) * 5 + d) * NB2;
+    const float* xv = x + (size_t)c2 * NB;
+    float xl[NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) xl[k] = xv[k];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < NB; ++k) s = fmaf(A[r * NB + k], xl[k], s);
+      acc[r] += s;
+    }
+  }
+}
+
+// Red-black block Gauss-Seidel half sweep: cells of `color` get x_c = D_c^{-1}(b_c - sum_n A_cn x_n).
+template <bool STRUCT>
+__global__ void rbgs_kernel(Fine F, Lvl L, int B, int color, const float* __restrict__ bvec,
+                            float* x, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.nc) return;
+  const int i = c % L.nx, j = c / L.nx;
+  if (((i + j) & 1) != color) return;
+  float* xb = x + (size_t)b * L.nc * NB;
+  const float* bb = bvec + (size_t)b * L.nc * NB;
+  float acc[NB];
+#pragma unroll
+  for (int r = 0; r < NB; ++r) acc[r] = 0.f;
+  block_row<STRUCT>(F, L, b, c, i, j, xb, false, acc);
+  float res[NB];
+#pragma unroll
+  for (int r = 0; r < NB; ++r) res[r] = bb[(size_t)c * NB + r] - acc[r];
+  const float* Di = STRUCT ? F.dinv32 + ((size_t)b * F.n_mat + F.mat[c]) * NB2
+                           : L.dinv + ((size_t)b * L.nc + c) * NB2;
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) s = fmaf(Di[r * NB + k], res[k], s);
+    xb[(size_t)c * NB + r] = s;
+  }
+}
+
+template <bool STRUCT>
+__global__ void residual_kernel(Fine F, Lvl L, int B, const float* __restrict__ bvec,
+                                const float* __restrict__ x, float* r, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.nc) return;
+  const int i = c % L.nx, j = c / L.nx;
+  float acc[NB];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) acc[k] = 0.f;
+  block_row<STRUCT>(F, L, b, c, i, j, x + (size_t)b * L.nc * NB, true, acc);
+  const float* bb = bvec + ((size_t)b * L.nc + c) * NB;
+  float* rr = r + ((size_t)b * L.nc + c) * NB;
+#pragma unroll
+  for (int k = 0; k < NB; ++k) rr[k] = bb[k] - acc[k];
+}
+
+// Prolongation coefficients: fine basis a_f in the coarse basis a_c restricted to child o (-1/+1):
+// p[o][a_f][a_c] = int_child phi^C_{a_c} phi^f_{a_f}.
+__device__ __forceinline__ float pcoef(int o, int af, int ac) {
+  const float r2 = 0.70710678118654752f;  // 1/sqrt2
+  if (af == 0 && ac == 0) return r2;
+  if (af == 0 && ac == 1) return (o < 0 ? -1.f : 1.f) * 0.61237243569579452f;  // sqrt6/4
+  if (af == 1 && ac == 1) return 0.5f * r2;
+  return 0.f;
+}
+
+// P entry for child (dx, dy) mapping coarse local k_c to fine local k_f (same field).
+__device__ __forceinline__ float pk(int dx, int dy, int kf, int kc) {
+  return pcoef(dx ? 1 : -1, kf & 1, kc & 1) * pcoef(dy ? 1 : -1, kf >> 1, kc >> 1);
+}
+
+// b_coarse[C] = sum_children P_c^T r[c]
+__global__ void restrict_kernel(int nxf, int nxc, int nyc, int B, const float* __restrict__ r,
+                                float* bc, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ncc = nxc * nyc;
+  if (t >= ncc * NB) return;
+  const int C = t / NB, row = t % NB, f = row / 4, kc = row % 4;
+  const int I = C % nxc, J = C / nxc;
+  const int ncf = nxf * 2 * nyc;
+  float s = 0.f;
+  for (int dy = 0; dy < 2; ++dy)
+    for (int dx = 0; dx < 2; ++dx) {
+      const int c = (2 * J + dy) * nxf + 2 * I + dx;
+      const float* rv = r + ((size_t)b * ncf + c) * NB + 4 * f;
+#pragma unroll
+      for (int kf = 0; kf < 4; ++kf) s = fmaf(pk(dx, dy, kf, kc), rv[kf], s);
+    }
+  bc[((size_t)b * ncc) * NB + t] = s;
+}
+
+// x_fine[c] += P_c x_coarse[C]
+__global__ void prolong_add_kernel(int nxf, int nyf, int B, const float* __restrict__ xc,
+                                   float* xf, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ncf = nxf * nyf;
+  if (t >= ncf * NB) return;
+  const int c = t / NB, row = t % NB, f = row / 4, kf = row % 4;
+  const int i = c % nxf, j = c / nxf;
+  const int nxc = nxf / 2, ncc = nxc * (nyf / 2);
+  const int C = (j / 2) * nxc + i / 2, dx = i & 1, dy = j & 1;
+  const float* xv = xc + ((size_t)b * ncc + C) * NB + 4 * f;
+  float s = 0.f;
+#pragma unroll
+  for (int kc = 0; kc < 4; ++kc) s = fmaf(pk(dx, dy, kf, kc), xv[kc], s);
+  xf[(size_t)b * ncf * NB + t] += s;
+}
+
+// Galerkin coarse blocks: A_c[C][d] = sum over child pairs of P^T A_f P (one thread per entry).
+template <bool STRUCT>
+__global__ void ptap_kernel(Fine F, Lvl Lf, int nxc, int nyc, int B, float* blk_c) {
+  const int b = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ncc = nxc * nyc;
+  if (t >= ncc * 5 * NB2) return;
+  const int e = t % NB2, d = (t / NB2) % 5, C = t / (5 * NB2);
+  const int ro = e / NB, co = e % NB;           // coarse row / column (field*4 + k)
+  const int fr = ro / 4, kr = ro % 4, fc = co / 4, kc = co % 4;
+  const int I = C % nxc, J = C / nxc;
+  int I2 = I, J2 = J;
+  if (d == 1) --I2;
+  else if (d == 2) ++I2;
+  else if (d == 3) --J2;
+  else if (d == 4) ++J2;
+  float s = 0.f;
+  if (I2 >= 0 && I2 < nxc && J2 >= 0 && J2 < nyc) {
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx) {
+        const int i = 2 * I + dx, j = 2 * J + dy, c = j * Lf.nx + i;
+        for (int dd = 0; dd <= 4; ++dd) {        // fine neighbour of c
+          int c2 = c;
+          if (dd > 0 && !nbr(dd, i, j, Lf.nx, Lf.ny, c2)) continue;
+          const int i2 = c2 % Lf.nx, j2 = c2 / Lf.nx;
+          if (i2 / 2 != I2 || j2 / 2 != J2) continue;  // must be a child of the target coarse cell
+          const float* A;
+          if (STRUCT)
+            A = dd == 0 ? F.diag32 + ((size_t)b * F.n_mat + F.mat[c]) * NB2 : F.off32 + (dd - 1) * NB2;
+          else
+            A = Lf.blk + (((size_t)b * Lf.nc + c) * 5 + dd) * NB2;
+          const int dx2 = i2 & 1, dy2 = j2 & 1;
+          for (int kf = 0; kf < 4; ++kf) {
+            const float pr = pk(dx, dy, kf, kr);
+            if (pr == 0.f) continue;
+            float inner = 0.f;
+            for (int kf2 = 0; kf2 < 4; ++kf2)
+              inner = fmaf(A[(4 * fr + kf) * NB + 4 * fc + kf2], pk(dx2, dy2, kf2, kc), inner);
+            s = fmaf(pr, inner, s);
+          }
+        }
+      }
+  }
+  blk_c[((size_t)b * ncc) * 5 * NB2 + t] = s;
+}
+
+// 12x12 inverse of each cell's diagonal block (levels >= 1), in double then stored as float.
+__global__ void blockinv_kernel(const float* blk, float* dinv, int nc, int B) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nc * B) return;
+  const float* A = blk + (size_t)t * 5 * NB2;  // d = 0 block of cell (b, c)
+  double a[NB * 24];
+  for (int r = 0; r < NB; ++r)
+    for (int c = 0; c < 24; ++c) a[r * 24 + c] = c < NB ? (double)A[r * NB + c] : (c - NB == r ? 1.0 : 0.0);
+  inv12<double>(a);
+  float* o = dinv + (size_t)t * NB2;
+  for (int r = 0; r < NB; ++r)
+    for (int c = 0; c < NB; ++c) o[r * NB + c] = (float)a[r * 24 + NB + c];
+}
+
+// ---- vector helpers (FGMRES, FP64) ---------------------------------------------------------
+
+__global__ void pack_rhs_kernel(const double* R, double* v, int nc, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nc * NB) return;
+  const int c = t / NB, k = t % NB;
+  v[(size_t)b * nc * NB + t] = k < 4 ? R[(size_t)b * nc * 4 + 4 * c + k] : 0.0;
+}
+
+__global__ void extract_rho_kernel(const double* x, double* drho, int nc, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nc * 4) return;
+  const int c = t / 4, k = t % 4;
+  drho[(size_t)b * nc * 4 + t] = x[((size_t)b * nc + c) * NB + k];
+}
+
+// dots[b][i] = <V_i[b], w[b]> for i < k; one block per (i, b); fixed-order tree reduction.
+__global__ void dots_kernel(const double* V, size_t vstride, const double* w, double* dots, int n,
+                            int kmax, const uint8_t* active) {
+  const int i = blockIdx.x, b = blockIdx.y;
+  if (active && !active[b]) return;
+  const double* vi = V + (size_t)i * vstride + (size_t)b * n;
+  const double* wb = w + (size_t)b * n;
+  double s = 0.0;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) s = fma(vi[e], wb[e], s);
+  __shared__ double sh[512];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) dots[(size_t)b * kmax + i] = sh[0];
+}
+
+// w[b] -= sum_{i<k} h[b][i] V_i[b]
+__global__ void gs_update_kernel(const double* V, size_t vstride, double* w, const double* h,
+                                 int n, int k, int kmax, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    double s = w[(size_t)b * n + e];
+    for (int i = 0; i < k; ++i) s -= h[(size_t)b * kmax + i] * V[(size_t)i * vstride + (size_t)b * n + e];
+    w[(size_t)b * n + e] = s;
+  }
+}
+
+// out[b] = alpha[b] * in[b]
+__global__ void scale_kernel(const double* in, double* out, const double* alpha, int n, int kmax,
+                             const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const double a = alpha[(size_t)b * kmax];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+    out[(size_t)b * n + e] = a * in[(size_t)b * n + e];
+}
+
+// x[b] += sum_{i<k} y[b][i] Z_i[b]
+__global__ void combine_kernel(const double* Z, size_t zstride, double* x, const double* y, int n,
+                               int k, int kmax, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    double s = x[(size_t)b * n + e];
+    for (int i = 0; i < k; ++i) s += y[(size_t)b * kmax + i] * Z[(size_t)i * zstride + (size_t)b * n + e];
+    x[(size_t)b * n + e] = s;
+  }
+}
+
+__global__ void to32_kernel(const double* in, float* out, size_t n, int per, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  for (size_t e = blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)per; e += gridDim.x * blockDim.x)
+    out[(size_t)b * per + e] = (float)in[(size_t)b * per + e];
+}
+__global__ void to64_kernel(const float* in, double* out, int per, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < per; e += gridDim.x * blockDim.x)
+    out[(size_t)b * per + e] = (double)in[(size_t)b * per + e];
+}
+__global__ void zero32_kernel(float* x, int per, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < per; e += gridDim.x * blockDim.x)
+    x[(size_t)b * per + e] = 0.f;
+}
+
+// ---- 1D: block-tridiagonal direct solve ---------------------------------------------------------
+
+// Per cell: unknowns u = (drho0, drho1, dJ0, dJ1).  Factor: Dp_c^{-1} and M_c = L_c Dp_{c-1}^{-1}.
+__device__ void inv4d(const double* A, double* Ai) {
+  double a[4][8];
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 8; ++c) a[r][c] = c < 4 ? A[4 * r + c] : (c - 4 == r ? 1.0 : 0.0);
+  for (int k = 0; k < 4; ++k) {
+    int p = k;
+    for (int r = k + 1; r < 4; ++r)
+      if (fabs(a[r][k]) > fabs(a[p][k])) p = r;
+    if (p != k)
+      for (int c = 0; c < 8; ++c) {
+        double t = a[k][c];
+        a[k][c] = a[p][c];
+        a[p][c] = t;
+      }
+    const double piv = 1.0 / a[k][k];
+    for (int c = 0; c < 8; ++c) a[k][c] *= piv;
+    for (int r = 0; r < 4; ++r)
+      if (r != k) {
+        const double f = a[r][k];
+        for (int c = 0; c < 8; ++c) a[r][c] -= f * a[k][c];
+      }
+  }
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c) Ai[4 * r + c] = a[r][c + 4];
+}
+
+struct Blocks1D {
+  double Dd[16], Lw[16], Ue[16];  // D without sigma terms; neighbour blocks
+};
+
+__global__ void dsa1d_factor_kernel(Blocks1D K, const double* sigma_t, const double* sigma_s,
+                                    const int32_t* mat, int nx, int n_mat, int B, double* Dpinv,
+                                    double* Mfac) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  double Dp[16], Di[16], tmp[16];
+  for (int c = 0; c < nx; ++c) {
+    const int m = mat[c];
+    const double st = sigma_t[b * n_mat + m], sa = st - sigma_s[b * n_mat + m];
+    for (int e = 0; e < 16; ++e) Dp[e] = K.Dd[e];
+    Dp[0] += sa, Dp[5] += sa, Dp[10] += st, Dp[15] += st;
+    double* Mc = Mfac + ((size_t)b * nx + c) * 16;
+    if (c > 0) {
+      const double* Dprev = Dpinv + ((size_t)b * nx + c - 1) * 16;
+      for (int r = 0; r < 4; ++r)
+        for (int q = 0; q < 4; ++q) {
+          double s = 0.0;
+          for (int k = 0; k < 4; ++k) s += K.Lw[4 * r + k] * Dprev[4 * k + q];
+          Mc[4 * r + q] = s;
+        }
+      for (int r = 0; r < 4; ++r)
+        for (int q = 0; q < 4; ++q) {
+          double s = 0.0;
+          for (int k = 0; k < 4; ++k) s += Mc[4 * r + k] * K.Ue[4 * k + q];
+          tmp[4 * r + q] = s;
+        }
+      for (int e = 0; e < 16; ++e) Dp[e] -= tmp[e];
+    } else {
+      for (int e = 0; e < 16; ++e) Mc[e] = 0.0;
+    }
+    inv4d(Dp, Di);
+    for (int e = 0; e < 16; ++e) Dpinv[((size_t)b * nx + c) * 16 + e] = Di[e];
+  }
+}
+
+__global__ void dsa1d_solve_kernel(Blocks1D K, const double* Dpinv, const double* Mfac,
+                                   const double* R, double* drho, double* work, int nx, int B,
+                                   const uint8_t* active) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B || (active && !active[b])) return;
+  double* y = work + (size_t)b * nx * 4;
+  double prev[4] = {0, 0, 0, 0};
+  for (int c = 0; c < nx; ++c) {  // forward: y_c = b_c - M_c y_{c-1}
+    const double bc[4] = {R[((size_t)b * nx + c) * 2], R[((size_t)b * nx + c) * 2 + 1], 0.0, 0.0};
+    const double* Mc = Mfac + ((size_t)b * nx + c) * 16;
+    for (int r = 0; r < 4; ++r) {
+      double s = bc[r];
+      for (int k = 0; k < 4; ++k) s -= Mc[4 * r + k] * prev[k];
+      y[4 * c + r] = s;
+    }
+    for (int r = 0; r < 4; ++r) prev[r] = y[4 * c + r];
+  }
+  double next[4] = {0, 0, 0, 0};
+  for (int c = nx - 1; c >= 0; --c) {  // backward: x_c = Dp_c^{-1} (y_c - U_c x_{c+1})
+    double t[4];
+    for (int r = 0; r < 4; ++r) {
+      double s = y[4 * c + r];
+      if (c < nx - 1)
+        for (int k = 0; k < 4; ++k) s -= K.Ue[4 * r + k] * next[k];
+      t[r] = s;
+    }
+    const double* Di = Dpinv + ((size_t)b * nx + c) * 16;
+    for (int r = 0; r < 4; ++r) {
+      double s = 0.0;
+      for (int k = 0; k < 4; ++k) s += Di[4 * r + k] * t[k];
+      next[r] = s;
+    }
+    drho[((size_t)b * nx + c) * 2] = next[0];
+    drho[((size_t)b * nx + c) * 2 + 1] = next[1];
+  }
+}
+
+// ---- state ------------------------------------------------------------------------------------
+
+struct DsaState {
+  int dim = 2;
+  // 1D
+  Blocks1D K1{};
+  DevBuf<double> Dpinv, Mfac, work1;
+  // 2D
+  int n_levels = 0;
+  std::vector<int> lnx, lny;
+  DevBuf<double> off64, diag64;
+  DevBuf<float> off32, diag32, dinv32;
+  std::vector<DevBuf<float>*> blk, dinv;     // levels >= 1
+  std::vector<DevBuf<float>*> xl, bl, rl;    // per level FP32 vectors
+  int m = 20;                                // FGMRES restart length
+  DevBuf<double> V, Z, w, xs;                // Krylov bases and work
+  DevBuf<double> dots_dev;
+  ~DsaState() {
+    for (auto* p : blk) delete p;
+    for (auto* p : dinv) delete p;
+    for (auto* p : xl) delete p;
+    for (auto* p : bl) delete p;
+    for (auto* p : rl) delete p;
+  }
+};
+
+void dsa_state_free(DsaState* s) { delete s; }
+
+static Fine fine_of(rte_batch_t bt) {
+  DsaState* s = bt->dsa;
+  return Fine{s->off64.p, s->off32.p, s->diag64.p, s->diag32.p, s->dinv32.p,
+              bt->disc->mat_id.p, bt->disc->n_mat};
+}
+
+static Lvl lvl_of(DsaState* s, int l) {
+  Lvl L{s->lnx[l], s->lny[l], s->lnx[l] * s->lny[l], nullptr, nullptr};
+  if (l >= 1) {
+    L.blk = s->blk[l - 1]->p;
+    L.dinv = s->dinv[l - 1]->p;
+  }
+  return L;
+}
+
+int dsa_setup(rte_batch_t bt, cudaStream_t st) {
+  const rte_disc_s* d = bt->disc;
+  const int B = bt->B;
+  if (!bt->dsa) bt->dsa = new DsaState();
+  DsaState* s = bt->dsa;
+  s->dim = d->dim;
+  if (d->dim == 1) {
+    // App. B constants from the S_N rule
+    double c1 = 0, c2 = 0, c3 = 0;
+    for (int j = 0; j < d->n_angles; ++j) {
+      const double v = d->v[3 * j], w = d->w[j];
+      c2 += w * v * v;
+      if (v > 0) c1 += w * v, c3 += w * v * v * v;
+    }
+    const Ops1D o = ops1d(d->hx);
+    auto fill = [&](double* out, const double* DC, const double* DJ) {
+      // rows (rho0, rho1, J0, J1): [[-c1 DJ, DC], [c2 DC, -3 c3 DJ]]
+      for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 2; ++c) {
+          out[4 * r + c] = -c1 * DJ[2 * r + c];
+          out[4 * r + c + 2] = DC[2 * r + c];
+          out[4 * (r + 2) + c] = c2 * DC[2 * r + c];
+          out[4 * (r + 2) + c + 2] = -3.0 * c3 * DJ[2 * r + c];
+        }
+    };
+    fill(s->K1.Dd, o.DCd, o.DJd);
+    fill(s->K1.Lw, o.DCw, o.DJw);
+    fill(s->K1.Ue, o.DCe, o.DJe);
+    RTE_TRY(s->Dpinv.alloc((size_t)B * d->nx * 16));
+    RTE_TRY(s->Mfac.alloc((size_t)B * d->nx * 16));
+    RTE_TRY(s->work1.alloc((size_t)B * d->nx * 4));
+    dsa1d_factor_kernel<<<(B + 63) / 64, 64, 0, st>>>(s->K1, bt->sigma_t.p, bt->sigma_s.p,
+                                                      d->mat_id.p, d->nx, d->n_mat, B,
+                                                      s->Dpinv.p, s->Mfac.p);
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+  }
+  // ---- 2D: constant neighbour blocks and per-material diagonal blocks -----------------------
+  const Ops1D ox = ops1d(d->hx), oy = ops1d(d->hy);
+  double DCx[3][16], DJx[3][16], DCy[3][16], DJy[3][16], Zr[16] = {0};
+  kron_x(ox.DCd, DCx[0]), kron_x(ox.DCw, DCx[1]), kron_x(ox.DCe, DCx[2]);
+  kron_x(ox.DJd, DJx[0]), kron_x(ox.DJw, DJx[1]), kron_x(ox.DJe, DJx[2]);
+  kron_y(oy.DCd, DCy[0]), kron_y(oy.DCw, DCy[1]), kron_y(oy.DCe, DCy[2]);
+  kron_y(oy.DJd, DJy[0]), kron_y(oy.DJw, DJy[1]), kron_y(oy.DJe, DJy[2]);
+  std::vector<double> off(4 * NB2);
+  field_block(d->mom, DCx[1], DJx[1], Zr, Zr, 0, 0, false, &off[0 * NB2]);  // W
+  field_block(d->mom, DCx[2], DJx[2], Zr, Zr, 0, 0, false, &off[1 * NB2]);  // E
+  field_block(d->mom, Zr, Zr, DCy[1], DJy[1], 0, 0, false, &off[2 * NB2]);  // S
+  field_block(d->mom, Zr, Zr, DCy[2], DJy[2], 0, 0, false, &off[3 * NB2]);  // N
+  std::vector<double> diag((size_t)B * d->n_mat * NB2), dinv((size_t)B * d->n_mat * NB2);
+  for (int b = 0; b < B; ++b)
+    for (int m = 0; m < d->n_mat; ++m) {
+      const double stv = bt->sigma_t_h[(size_t)b * d->n_mat + m];
+      const double sav = stv - bt->sigma_s_h[(size_t)b * d->n_mat + m];
+      double* D = &diag[((size_t)b * d->n_mat + m) * NB2];
+      field_block(d->mom, DCx[0], DJx[0], DCy[0], DJy[0], sav, stv, true, D);
+      invert_host(D, &dinv[((size_t)b * d->n_mat + m) * NB2], NB);
+    }
+  std::vector<float> off32(off.begin(), off.end()), diag32(diag.begin(), diag.end()),
+      dinv32(dinv.begin(), dinv.end());
+  RTE_TRY(s->off64.alloc(off.size()));
+  RTE_TRY(s->off32.alloc(off.size()));
+  RTE_TRY(s->diag64.alloc(diag.size()));
+  RTE_TRY(s->diag32.alloc(diag.size()));
+  RTE_TRY(s->dinv32.alloc(diag.size()));
+  RTE_CUDA_TRY(cudaMemcpy(s->off64.p, off.data(), off.size() * 8, cudaMemcpyHostToDevice));
+  RTE_CUDA_TRY(cudaMemcpy(s->off32.p, off32.data(), off.size() * 4, cudaMemcpyHostToDevice));
+  RTE_CUDA_TRY(cudaMemcpy(s->diag64.p, diag.data(), diag.size() * 8, cudaMemcpyHostToDevice));
+  RTE_CUDA_TRY(cudaMemcpy(s->diag32.p, diag32.data(), diag.size() * 4, cudaMemcpyHostToDevice));
+  RTE_CUDA_TRY(cudaMemcpy(s->dinv32.p, dinv32.data(), diag.size() * 4, cudaMemcpyHostToDevice));
+
+  // ---- levels: coarsen 2x2 while both sizes are even -------------------------------------------
+  if (s->n_levels == 0) {
+    s->lnx.push_back(d->nx);
+    s->lny.push_back(d->ny);
+    while (s->lnx.back() % 2 == 0 && s->lny.back() % 2 == 0 && s->lnx.back() * s->lny.back() > 1) {
+      s->lnx.push_back(s->lnx.back() / 2);
+      s->lny.push_back(s->lny.back() / 2);
+    }
+    s->n_levels = (int)s->lnx.size();
+    for (int l = 0; l < s->n_levels; ++l) {
+      const size_t nc = (size_t)s->lnx[l] * s->lny[l];
+      auto* x = new DevBuf<float>();
+      auto* bb = new DevBuf<float>();
+      auto* r = new DevBuf<float>();
+      s->xl.push_back(x), s->bl.push_back(bb), s->rl.push_back(r);
+      RTE_TRY(x->alloc((size_t)B * nc * NB));
+      RTE_TRY(bb->alloc((size_t)B * nc * NB));
+      RTE_TRY(r->alloc((size_t)B * nc * NB));
+      if (l >= 1) {
+        auto* bk = new DevBuf<float>();
+        auto* di = new DevBuf<float>();
+        s->blk.push_back(bk), s->dinv.push_back(di);
+        RTE_TRY(bk->alloc((size_t)B * nc * 5 * NB2));
+        RTE_TRY(di->alloc((size_t)B * nc * NB2));
+      }
+    }
+    const size_t n = (size_t)B * d->n_cells * NB;
+    RTE_TRY(s->V.alloc((size_t)(s->m + 1) * n));
+    RTE_TRY(s->Z.alloc((size_t)s->m * n));
+    RTE_TRY(s->w.alloc(n));
+    RTE_TRY(s->xs.alloc(n));
+    RTE_TRY(s->dots_dev.alloc((size_t)B * (s->m + 1)));
+  }
+  const Fine F = fine_of(bt);
+  for (int l = 0; l + 1 < s->n_levels; ++l) {
+    const Lvl Lf = lvl_of(s, l);
+    const int nxc = s->lnx[l + 1], nyc = s->lny[l + 1];
+    const int total = nxc * nyc * 5 * NB2;
+    dim3 grid((total + 255) / 256, B);
+    if (l == 0)
+      ptap_kernel<true><<<grid, 256, 0, st>>>(F, Lf, nxc, nyc, B, s->blk[0]->p);
+    else
+      ptap_kernel<false><<<grid, 256, 0, st>>>(F, Lf, nxc, nyc, B, s->blk[l]->p);
+    RTE_CUDA_TRY(cudaGetLastError());
+    const int nb = nxc * nyc * B;
+    blockinv_kernel<<<(nb + 63) / 64, 64, 0, st>>>(s->blk[l]->p, s->dinv[l]->p, nxc * nyc, B);
+    RTE_CUDA_TRY(cudaGetLastError());
+  }
+  return RTE_OK;
+}
+
+// One V-cycle on level l: x_l approximately solves A_l x = b_l (x_l starts at zero).
+static int vcycle(rte_batch_t bt, int l, const uint8_t* active, cudaStream_t st, int nu) {
+  DsaState* s = bt->dsa;
+  const int B = bt->B;
+  const Fine F = fine_of(bt);
+  const Lvl L = lvl_of(s, l);
+  const int per = L.nc * NB;
+  float* x = s->xl[l]->p;
+  float* b = s->bl[l]->p;
+  float* r = s->rl[l]->p;
+  zero32_kernel<<<dim3((per + 255) / 256, B), 256, 0, st>>>(x, per, active);
+  dim3 gcol((L.nc + 127) / 128, B);
+  const bool coarsest = l == s->n_levels - 1;
+  auto smooth = [&](int c0) {
+    for (int k = 0; k < 2; ++k) {
+      const int color = k == 0 ? c0 : 1 - c0;
+      if (l == 0)
+        rbgs_kernel<true><<<gcol, 128, 0, st>>>(F, L, B, color, b, x, active);
+      else
+        rbgs_kernel<false><<<gcol, 128, 0, st>>>(F, L, B, color, b, x, active);
+    }
+  };
+  if (coarsest && L.nc == 1) {  // exact: x = D^{-1} b
+    smooth(0);
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+  }
+  const int npre = coarsest ? 30 : nu;
+  for (int k = 0; k < npre; ++k) smooth(0);
+  if (!coarsest) {
+    dim3 gc((L.nc + 127) / 128, B);
+    if (l == 0)
+      residual_kernel<true><<<gc, 128, 0, st>>>(F, L, B, b, x, r, active);
+    else
+      residual_kernel<false><<<gc, 128, 0, st>>>(F, L, B, b, x, r, active);
+    const int nxc = s->lnx[l + 1], nyc = s->lny[l + 1];
+    const int nco = nxc * nyc * NB;
+    restrict_kernel<<<dim3((nco + 255) / 256, B), 256, 0, st>>>(L.nx, nxc, nyc, B, r,
+                                                                s->bl[l + 1]->p, active);
+    RTE_TRY(vcycle(bt, l + 1, active, st, nu));
+    prolong_add_kernel<<<dim3((per + 255) / 256, B), 256, 0, st>>>(L.nx, L.ny, B, s->xl[l + 1]->p,
+                                                                   x, active);
+    for (int k = 0; k < nu; ++k) smooth(1);
+  }
+  RTE_CUDA_TRY(cudaGetLastError());
+  return RTE_OK;
+}
+
+static int dsa2d_fgmres(rte_batch_t bt, const double* R, double* drho, double rtol, int max_it,
+                        const uint8_t* active_in, int* iters_out, cudaStream_t st) {
+  DsaState* s = bt->dsa;
+  const rte_disc_s* d = bt->disc;
+  const int B = bt->B, nc = d->n_cells, n = nc * NB, m = s->m;
+  const size_t vstride = (size_t)B * n;
+  const Fine F = fine_of(bt);
+  // host copy of the active mask (instances drop out as they converge)
+  std::vector<uint8_t> act(B, 1);
+  if (active_in) RTE_CUDA_TRY(cudaMemcpy(act.data(), active_in, B, cudaMemcpyDeviceToHost));
+  DevBuf<uint8_t> act_dev;
+  RTE_TRY(act_dev.alloc(B));
+  auto upload_act = [&]() -> int {
+    RTE_CUDA_TRY(cudaMemcpyAsync(act_dev.p, act.data(), B, cudaMemcpyHostToDevice, st));
+    return RTE_OK;
+  };
+  RTE_TRY(upload_act());
+  const dim3 gvec((n + 255) / 256, B), gvec_c(std::min((n + 255) / 256, 512), B);
+  double* x = s->xs.p;
+  RTE_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * vstride, st));
+  std::vector<double> beta0(B, 0.0), hbuf((size_t)B * (m + 1));
+  std::vector<int> its(B, 0);
+  std::vector<uint8_t> done(B, 0);
+  for (int b = 0; b < B; ++b) done[b] = !act[b];
+  int status = RTE_OK;
+  // r0 = b - A x (x = 0 initially): v0 = packed R
+  double* w = s->w.p;
+  pack_rhs_kernel<<<gvec, 256, 0, st>>>(R, w, nc, act_dev.p);
+  bool first = true;
+  int total_it = 0;
+  while (true) {
+    // w holds the current residual for active instances
+    dots_kernel<<<dim3(1, B), 512, 0, st>>>(w, 0, w, s->dots_dev.p, n, m + 1, act_dev.p);
+    RTE_CUDA_TRY(cudaMemcpyAsync(hbuf.data(), s->dots_dev.p, sizeof(double) * B * (m + 1),
+                                 cudaMemcpyDeviceToHost, st));
+    RTE_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<double> beta(B, 0.0);
+    for (int b = 0; b < B; ++b) {
+      if (!act[b]) continue;
+      beta[b] = std::sqrt(std::max(hbuf[(size_t)b * (m + 1)], 0.0));
+      if (first) beta0[b] = beta[b];
+      if (beta[b] <= rtol * beta0[b] || beta[b] == 0.0 || total_it >= max_it) {
+        act[b] = 0;
+        done[b] = 1;
+        if (total_it >= max_it && beta[b] > rtol * beta0[b]) status = RTE_ENOCONV;
+      }
+    }
+    first = false;
+    bool any = false;
+    for (int b = 0; b < B; ++b) any |= act[b] != 0;
+    if (!any) break;
+    RTE_TRY(upload_act());
+    // v0 = w / beta
+    std::vector<double> inv((size_t)B * (m + 1), 0.0);
+    for (int b = 0; b < B; ++b) inv[(size_t)b * (m + 1)] = act[b] ? 1.0 / beta[b] : 0.0;
+    RTE_CUDA_TRY(cudaMemcpyAsync(s->dots_dev.p, inv.data(), sizeof(double) * inv.size(),
+                                 cudaMemcpyHostToDevice, st));
+    scale_kernel<<<gvec_c, 256, 0, st>>>(w, s->V.p, s->dots_dev.p, n, m + 1, act_dev.p);
+    // Arnoldi with Givens rotations per instance
+    std::vector<double> H((size_t)B * (m + 1) * m, 0.0), cs((size_t)B * m), sn((size_t)B * m),
+        g((size_t)B * (m + 1), 0.0);
+    for (int b = 0; b < B; ++b) g[(size_t)b * (m + 1)] = beta[b];
+    std::vector<uint8_t> inner(act);
+    std::vector<int> kdone(B, 0);
+    int k = 0;
+    for (; k < m; ++k) {
+      bool anyi = false;
+      for (int b = 0; b < B; ++b) anyi |= inner[b] != 0;
+      if (!anyi) break;
+      RTE_CUDA_TRY(cudaMemcpyAsync(act_dev.p, inner.data(), B, cudaMemcpyHostToDevice, st));
+      double* vk = s->V.p + (size_t)k * vstride;
+      double* zk = s->Z.p + (size_t)k * vstride;
+      // z_k = M^{-1} v_k (one FP32 V-cycle)
+      to32_kernel<<<gvec_c, 256, 0, st>>>(vk, s->bl[0]->p, 0, n, act_dev.p);
+      RTE_TRY(vcycle(bt, 0, act_dev.p, st, 2));
+      to64_kernel<<<gvec_c, 256, 0, st>>>(s->xl[0]->p, zk, n, act_dev.p);
+      // w = A z_k (FP64)
+      fine_apply64_kernel<<<gvec, 256, 0, st>>>(F, d->nx, d->ny, B, zk, w, act_dev.p);
+      // classical Gram-Schmidt, twice
+      std::vector<double> hk((size_t)B * (m + 1), 0.0);
+      for (int pass = 0; pass < 2; ++pass) {
+        dots_kernel<<<dim3(k + 1, B), 512, 0, st>>>(s->V.p, vstride, w, s->dots_dev.p, n, m + 1,
+                                                    act_dev.p);
+        gs_update_kernel<<<gvec_c, 256, 0, st>>>(s->V.p, vstride, w, s->dots_dev.p, n, k + 1,
+                                                 m + 1, act_dev.p);
+        RTE_CUDA_TRY(cudaMemcpyAsync(hbuf.data(), s->dots_dev.p, sizeof(double) * B * (m + 1),
+                                     cudaMemcpyDeviceToHost, st));
+        RTE_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int b = 0; b < B; ++b)
+          if (inner[b])
+            for (int i = 0; i <= k; ++i) hk[(size_t)b * (m + 1) + i] += hbuf[(size_t)b * (m + 1) + i];
+      }
+      dots_kernel<<<dim3(1, B), 512, 0, st>>>(w, 0, w, s->dots_dev.p, n, m + 1, act_dev.p);
+      RTE_CUDA_TRY(cudaMemcpyAsync(hbuf.data(), s->dots_dev.p, sizeof(double) * B * (m + 1),
+                                   cudaMemcpyDeviceToHost, st));
+      RTE_CUDA_TRY(cudaStreamSynchronize(st));
+      std::vector<double> sc((size_t)B * (m + 1), 0.0);
+      ++total_it;
+      for (int b = 0; b < B; ++b) {
+        if (!inner[b]) continue;
+        double* hcol = &hk[(size_t)b * (m + 1)];
+        hcol[k + 1] = std::sqrt(std::max(hbuf[(size_t)b * (m + 1)], 0.0));
+        sc[(size_t)b * (m + 1)] = hcol[k + 1] > 0 ? 1.0 / hcol[k + 1] : 0.0;
+        // apply previous rotations
+        for (int i = 0; i < k; ++i) {
+          const double c = cs[(size_t)b * m + i], sn_ = sn[(size_t)b * m + i];
+          const double t = c * hcol[i] + sn_ * hcol[i + 1];
+          hcol[i + 1] = -sn_ * hcol[i] + c * hcol[i + 1];
+          hcol[i] = t;
+        }
+        const double den = std::hypot(hcol[k], hcol[k + 1]);
+        const double c = den > 0 ? hcol[k] / den : 1.0, sn_ = den > 0 ? hcol[k + 1] / den : 0.0;
+        cs[(size_t)b * m + k] = c, sn[(size_t)b * m + k] = sn_;
+        hcol[k] = den;
+        hcol[k + 1] = 0.0;
+        double* gb = &g[(size_t)b * (m + 1)];
+        gb[k + 1] = -sn_ * gb[k];
+        gb[k] = c * gb[k];
+        for (int i = 0; i <= k; ++i) H[((size_t)b * (m + 1) + i) * m + k] = hcol[i];
+        kdone[b] = k + 1;
+        its[b] += 1;
+        if (std::fabs(gb[k + 1]) <= rtol * beta0[b] || total_it >= max_it) inner[b] = 0;
+      }
+      // v_{k+1} = w / h_{k+1,k}
+      if (k + 1 <= m) {
+        RTE_CUDA_TRY(cudaMemcpyAsync(s->dots_dev.p, sc.data(), sizeof(double) * sc.size(),
+                                     cudaMemcpyHostToDevice, st));
+        scale_kernel<<<gvec_c, 256, 0, st>>>(w, s->V.p + (size_t)(k + 1) * vstride, s->dots_dev.p, n,
+                                             m + 1, act_dev.p);
+      }
+    }
+    // solve H y = g and update x += Z y
+    std::vector<double> y((size_t)B * (m + 1), 0.0);
+    int kmax = 0;
+    for (int b = 0; b < B; ++b) {
+      if (!act[b]) continue;
+      const int kb = kdone[b];
+      kmax = std::max(kmax, kb);
+      for (int i = kb - 1; i >= 0; --i) {
+        double sacc = g[(size_t)b * (m + 1) + i];
+        for (int j2 = i + 1; j2 < kb; ++j2) sacc -= H[((size_t)b * (m + 1) + i) * m + j2] * y[(size_t)b * (m + 1) + j2];
+        y[(size_t)b * (m + 1) + i] = sacc / H[((size_t)b * (m + 1) + i) * m + i];
+      }
+    }
+    RTE_TRY(upload_act());
+    RTE_CUDA_TRY(cudaMemcpyAsync(s->dots_dev.p, y.data(), sizeof(double) * y.size(),
+                                 cudaMemcpyHostToDevice, st));
+    combine_kernel<<<gvec_c, 256, 0, st>>>(s->Z.p, vstride, x, s->dots_dev.p, n, kmax, m + 1,
+                                           act_dev.p);
+    // new residual w = b - A x
+    fine_apply64_kernel<<<gvec, 256, 0, st>>>(F, d->nx, d->ny, B, x, w, act_dev.p);
+    {
+      // w = packed(R) - w  (reuse V_m as scratch for the packed right-hand side)
+      double* pr = s->V.p + (size_t)m * vstride;
+      pack_rhs_kernel<<<gvec, 256, 0, st>>>(R, pr, nc, act_dev.p);
+      std::vector<double> mone((size_t)B * (m + 1), 0.0);
+      for (int b = 0; b < B; ++b) mone[(size_t)b * (m + 1)] = 1.0;
+      RTE_CUDA_TRY(cudaMemcpyAsync(s->dots_dev.p, mone.data(), sizeof(double) * mone.size(),
+                                   cudaMemcpyHostToDevice, st));
+      // w <- w - 1 * pr, then negate via scale by -1
+      gs_update_kernel<<<gvec_c, 256, 0, st>>>(pr, 0, w, s->dots_dev.p, n, 1, m + 1, act_dev.p);
+      for (int b = 0; b < B; ++b) mone[(size_t)b * (m + 1)] = -1.0;
+      RTE_CUDA_TRY(cudaMemcpyAsync(s->dots_dev.p, mone.data(), sizeof(double) * mone.size(),
+                                   cudaMemcpyHostToDevice, st));
+      scale_kernel<<<gvec_c, 256, 0, st>>>(w, w, s->dots_dev.p, n, m + 1, act_dev.p);
+    }
+    RTE_CUDA_TRY(cudaGetLastError());
+    if (total_it >= max_it) {
+      // final convergence check happens at the top of the loop
+    }
+  }
+  // drho = rho-field of x for the instances that were requested
+  std::vector<uint8_t> req(B, 1);
+  if (active_in) RTE_CUDA_TRY(cudaMemcpy(req.data(), active_in, B, cudaMemcpyDeviceToHost));
+  RTE_CUDA_TRY(cudaMemcpyAsync(act_dev.p, req.data(), B, cudaMemcpyHostToDevice, st));
+  extract_rho_kernel<<<dim3((nc * 4 + 255) / 256, B), 256, 0, st>>>(x, drho, nc, act_dev.p);
+  RTE_CUDA_TRY(cudaGetLastError());
+  RTE_CUDA_TRY(cudaStreamSynchronize(st));
+  if (iters_out)
+    for (int b = 0; b < B; ++b) iters_out[b] = its[b];
+  return status;
+}
+
+int dsa_apply(rte_batch_t bt, const double* R, double* drho, double rtol, int max_it,
+              const uint8_t* active, int* iters, cudaStream_t st) {
+  DsaState* s = bt->dsa;
+  if (!s) return fail(RTE_ESTATE, "DSA not set up");
+  if (bt->disc->dim == 1) {
+    dsa1d_solve_kernel<<<(bt->B + 63) / 64, 64, 0, st>>>(s->K1, s->Dpinv.p, s->Mfac.p, R, drho,
+                                                         s->work1.p, bt->disc->nx, bt->B, active);
+    RTE_CUDA_TRY(cudaGetLastError());
+    if (iters)
+      for (int b = 0; b < bt->B; ++b) iters[b] = 1;
+    return RTE_OK;
+  }
+  return dsa2d_fgmres(bt, R, drho, rtol, max_it, active, iters, st);
+}
+
 }  // namespace rte
+
+using namespace rte;
+
+extern "C" int rte_dsa_correction(rte_batch_t b, const double* R, double* drho, double rtol,
+                                  int max_it, const uint8_t* active, int* iters, void* stream) {
+  if (!b || !R || !drho) return fail(RTE_EINVAL, "rte_dsa_correction: null argument");
+  if (!b->params_set) return fail(RTE_ESTATE, "parameters not set");
+  if (!(rtol > 0) || max_it < 1) return fail(RTE_EINVAL, "rte_dsa_correction: bad tolerance");
+  DeviceGuard g(b->disc->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  int s = dsa_apply(b, R, drho, rtol, max_it, active, iters, st);
+  if (s != RTE_OK && s != RTE_ENOCONV) return s;
+  RTE_CUDA_TRY(cudaStreamSynchronize(st));
+  return s;
+}

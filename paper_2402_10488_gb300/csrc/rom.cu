@@ -1,0 +1,674 @@
+// POD reduced order models (paper Sec. 3): offline stage on the GPU, ROMIG and ROMSA online.
+//
+// Offline (Sec. 3.1.1, 3.2.1): SI-DSA solves of the training instances store the converged
+// angular flux f^mu and the first w iterates f^{mu,(l)}; F = [f^mu] and dF = [f^mu - f^{mu,(l)}].
+// In X-Y geometry the +-v_z copies of a direction carry identical rows, so snapshots are stored
+// once per distinct direction and every row-sum is weighted by the direction's multiplicity;
+// this leaves F^T F, the singular values and U unchanged.  The thin SVD is taken through the
+// snapshot Gram matrix (deterministic tiled FP64 reduction on the GPU) and a cyclic Jacobi
+// eigensolver on the small host matrix; U = X V Lambda^{-1/2}, re-orthonormalised once by a
+// Cholesky factor of its own Gram matrix.  Truncation: a fixed rank, or Eq. (pod_truncation)
+// with singular values.  Reduced operators (affine decomposition, cellwise materials m):
+//     A_0r = sum_j U_j^T D_j U_j,   A_{a,m} = sum_j U_j^T M_m U_j,
+//     A_{s,m} = A_{a,m} - (U^iso)^T M_m U^rho,   A_{mu,r} = A_0r + sum_m sigma_a,m A_{a,m} + sigma_s,m A_{s,m}
+// with U^rho = sum_j omega_j U_j and U^iso = sum_j U_j (Eq. (rho_basis)).
+// Online: ROMIG rho^(0) = U^rho A_{mu,r}^{-1} (U^iso)^T G (vacuum inflow); ROMSA
+// delta rho = dU^rho (dU^T A_mu dU)^{-1} (dU^iso)^T R (Eq. (rom_correction)).  The r x r systems
+// are assembled and LU-factored on the device once per parameter set.
+#include "common.cuh"
+
+namespace rte {
+
+int run_si(rte_batch_t bt, const rte_solve_opts* o, rte_rom_t rom_c, double* rho,
+           rte_solve_report* reports, double* history, cudaStream_t st, double* psi_cur,
+           double* psi_win, int window);
+
+// Per-batch online state cached in the ROM handle.
+struct RomOnline {
+  rte_batch_t batch = nullptr;
+  DevBuf<double> lu;    // [B][r][r]
+  DevBuf<int> piv;      // [B][r]
+  DevBuf<double> proj;  // [B][r]
+};
+
+// ---- kernels ------------------------------------------------------------------------------
+
+// out[part][cls][i][j] = sum over this block's rows of w(row) X[i][row] Y[j][row], rows whose
+// class is cls.  Row index = d * n_dof + e; w = mult[d]; class = mat[e / P] (or 0).
+__global__ void cross_gram_kernel(const double* __restrict__ X, int nx_cols,
+                                  const double* __restrict__ Y, int ny_cols, size_t nrow,
+                                  int n_dof, int P, const double* __restrict__ wdir,
+                                  const int32_t* __restrict__ mat, int n_class,
+                                  double* partial) {
+  extern __shared__ double sm[];
+  const int T = 16;
+  double* Xs = sm;                        // [nx_cols][T]
+  double* Ys = Xs + (size_t)nx_cols * T;  // [ny_cols][T]
+  double* acc = Ys + (size_t)ny_cols * T; // [n_class][nx_cols*ny_cols]
+  __shared__ double ws[16];
+  __shared__ int cs[16];
+  const int npairs = nx_cols * ny_cols;
+  for (int p = threadIdx.x; p < n_class * npairs; p += blockDim.x) acc[p] = 0.0;
+  const size_t ntiles = (nrow + T - 1) / T;
+  for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    __syncthreads();
+    const size_t r0 = tile * T;
+    for (int q = threadIdx.x; q < (nx_cols + ny_cols) * T; q += blockDim.x) {
+      const int col = q / T, rr = q % T;
+      const size_t row = r0 + rr;
+      double v = 0.0;
+      if (row < nrow) v = col < nx_cols ? X[(size_t)col * nrow + row] : Y[(size_t)(col - nx_cols) * nrow + row];
+      sm[q] = v;
+    }
+    if (threadIdx.x < T) {
+      const size_t row = r0 + threadIdx.x;
+      double w = 0.0;
+      int c = 0;
+      if (row < nrow) {
+        const size_t d = row / n_dof, e = row % n_dof;
+        w = wdir ? wdir[d] : 1.0;
+        c = mat ? mat[e / P] : 0;
+      }
+      ws[threadIdx.x] = w;
+      cs[threadIdx.x] = c;
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+      const int i = p / ny_cols, j = p % ny_cols;
+      for (int rr = 0; rr < T; ++rr) {
+        const double v = ws[rr] * Xs[i * T + rr] * Ys[j * T + rr];
+        acc[cs[rr] * npairs + p] += v;
+      }
+    }
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < n_class * npairs; p += blockDim.x)
+    partial[(size_t)blockIdx.x * n_class * npairs + p] = acc[p];
+}
+
+__global__ void sum_partials_kernel(const double* partial, int nparts, int n, double* out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  double s = 0.0;
+  for (int k = 0; k < nparts; ++k) s += partial[(size_t)k * n + p];
+  out[p] = s;
+}
+
+// U[i][row] = sum_k X[k][row] W[k][i]
+__global__ void basis_kernel(const double* __restrict__ X, int ncol, const double* __restrict__ W,
+                             int r, size_t nrow, double* U) {
+  const size_t row = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nrow) return;
+  double x[128];
+  for (int k = 0; k < ncol; ++k) x[k] = X[(size_t)k * nrow + row];
+  for (int i = 0; i < r; ++i) {
+    double s = 0.0;
+    for (int k = 0; k < ncol; ++k) s = fma(x[k], W[k * r + i], s);
+    U[(size_t)i * nrow + row] = s;
+  }
+}
+
+// column differences: out[col] = F[b] - win[l][b] for the listed (b, l)
+__global__ void diff_kernel(const double* F, const double* win, const int* pairs, int ncols,
+                            size_t nrow, int B, double* out) {
+  const int col = blockIdx.y;
+  const int b = pairs[2 * col], l = pairs[2 * col + 1];
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nrow; e += (size_t)gridDim.x * blockDim.x)
+    out[(size_t)col * nrow + e] = F[(size_t)b * nrow + e] - win[((size_t)l * B + b) * nrow + e];
+}
+
+// U_rho[i][e] = sum_d w_d U[i][d][e],  U_iso[i][e] = sum_d mult_d U[i][d][e]
+__global__ void rho_iso_kernel(const double* U, int r, int n_dirs, int n_dof, const double* dirs,
+                               double* U_rho, double* U_iso) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)r * n_dof) return;
+  const int i = t / n_dof, e = t % n_dof;
+  double sr = 0.0, si = 0.0;
+  for (int d = 0; d < n_dirs; ++d) {
+    const double u = U[((size_t)i * n_dirs + d) * n_dof + e];
+    sr = fma(dirs[4 * d + 2], u, sr);
+    si = fma(dirs[4 * d + 3], u, si);
+  }
+  U_rho[t] = sr;
+  U_iso[t] = si;
+}
+
+// Y[i][d] = D_d U[i][d]: the upwind DG transport operator without Sigma_t (2D), with zero inflow.
+__global__ void transport_apply2d_kernel(const double* U, int r, int n_dirs, int nx, int ny,
+                                         double hx, double hy, const double* dirs, double* Y) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t nc = (size_t)nx * ny;
+  if (t >= (size_t)r * n_dirs * nc) return;
+  const int c = t % nc;
+  const int d = (t / nc) % n_dirs;
+  const int i = t / (nc * n_dirs);
+  const int ci = c % nx, cj = c / nx;
+  const double vx = dirs[4 * d], vy = dirs[4 * d + 1];
+  const double s3 = sqrt(3.0), sx = vx < 0 ? -1.0 : 1.0, sy = vy < 0 ? -1.0 : 1.0;
+  const double ax = fabs(vx) / hx, ay = fabs(vy) / hy;
+  const double* u = U + ((size_t)i * n_dirs + d) * nc * 4;
+  const double* a = u + (size_t)c * 4;
+  double y[4];
+  // (ax Kx (x) I + ay I (x) Ky) a,  K = [[1, s sqrt3], [-s sqrt3, 3]], k = a + 2b
+  for (int bb = 0; bb < 2; ++bb)
+    for (int aa = 0; aa < 2; ++aa) {
+      const int k = aa + 2 * bb;
+      double v = 0.0;
+      for (int a2 = 0; a2 < 2; ++a2) {
+        const double K = a2 == aa ? (aa == 0 ? 1.0 : 3.0) : (aa == 0 ? sx * s3 : -sx * s3);
+        v += ax * K * a[a2 + 2 * bb];
+      }
+      for (int b2 = 0; b2 < 2; ++b2) {
+        const double K = b2 == bb ? (bb == 0 ? 1.0 : 3.0) : (bb == 0 ? sy * s3 : -sy * s3);
+        v += ay * K * a[aa + 2 * b2];
+      }
+      y[k] = v;
+    }
+  // upwind x neighbour: its outflow trace t_x[q] = a_{0q} + s_x sqrt3 a_{1q}
+  const int iu = ci - (int)sx;
+  if (iu >= 0 && iu < nx) {
+    const double* an = u + ((size_t)cj * nx + iu) * 4;
+    for (int q = 0; q < 2; ++q) {
+      const double tq = an[2 * q] + sx * s3 * an[1 + 2 * q];
+      y[0 + 2 * q] -= ax * tq;
+      y[1 + 2 * q] -= ax * (-sx * s3) * tq;
+    }
+  }
+  const int ju = cj - (int)sy;
+  if (ju >= 0 && ju < ny) {
+    const double* an = u + ((size_t)ju * nx + ci) * 4;
+    for (int q = 0; q < 2; ++q) {
+      const double tq = an[q] + sy * s3 * an[q + 2];
+      y[q] -= ay * tq;
+      y[q + 2] -= ay * (-sy * s3) * tq;
+    }
+  }
+  double* out = Y + ((size_t)i * n_dirs + d) * nc * 4 + (size_t)c * 4;
+  for (int k = 0; k < 4; ++k) out[k] = y[k];
+}
+
+__global__ void transport_apply1d_kernel(const double* U, int r, int n_dirs, int nx, double h,
+                                         const double* dirs, double* Y) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)r * n_dirs * nx) return;
+  const int c = t % nx, d = (t / nx) % n_dirs, i = t / ((size_t)nx * n_dirs);
+  const double xi = dirs[4 * d], s3 = sqrt(3.0), sg = xi < 0 ? -1.0 : 1.0, a = fabs(xi) / h;
+  const double* u = U + ((size_t)i * n_dirs + d) * nx * 2;
+  const double a0 = u[2 * c], a1 = u[2 * c + 1];
+  double y0 = a * (a0 + sg * s3 * a1), y1 = a * (-sg * s3 * a0 + 3.0 * a1);
+  const int cu = c - (int)sg;
+  if (cu >= 0 && cu < nx) {
+    const double tq = u[2 * cu] + sg * s3 * u[2 * cu + 1];
+    y0 -= a * tq;
+    y1 -= a * (-sg * s3) * tq;
+  }
+  double* out = Y + ((size_t)i * n_dirs + d) * nx * 2;
+  out[2 * c] = y0;
+  out[2 * c + 1] = y1;
+}
+
+// A_{mu,r} per instance and its LU factorisation with partial pivoting (one thread per instance).
+__global__ void rom_assemble_lu_kernel(const double* A0, const double* Aa, const double* As,
+                                       int r, int n_mat, const double* sigma_t,
+                                       const double* sigma_s, int B, double* LU, int* piv) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  double* A = LU + (size_t)b * r * r;
+  for (int e = 0; e < r * r; ++e) {
+    double v = A0[e];
+    for (int m = 0; m < n_mat; ++m) {
+      const double st = sigma_t[b * n_mat + m], ss = sigma_s[b * n_mat + m];
+      v += (st - ss) * Aa[(size_t)m * r * r + e] + ss * As[(size_t)m * r * r + e];
+    }
+    A[e] = v;
+  }
+  for (int k = 0; k < r; ++k) {
+    int p = k;
+    for (int q = k + 1; q < r; ++q)
+      if (fabs(A[q * r + k]) > fabs(A[p * r + k])) p = q;
+    piv[b * r + k] = p;
+    if (p != k)
+      for (int c = 0; c < r; ++c) {
+        const double t = A[k * r + c];
+        A[k * r + c] = A[p * r + c];
+        A[p * r + c] = t;
+      }
+    const double inv = 1.0 / A[k * r + k];
+    for (int q = k + 1; q < r; ++q) {
+      const double f = A[q * r + k] * inv;
+      A[q * r + k] = f;
+      for (int c = k + 1; c < r; ++c) A[q * r + c] -= f * A[k * r + c];
+    }
+  }
+}
+
+// proj[b][i] = sum_e Ut[i][e] v[b][e * stride + off]  (one block per (i, b))
+__global__ void project_kernel(const double* Ut, int n, const double* v, int stride, int off,
+                               size_t vstride_b, double* proj, int r, const uint8_t* active) {
+  const int i = blockIdx.x, b = blockIdx.y;
+  if (active && !active[b]) return;
+  double s = 0.0;
+  for (int e = threadIdx.x; e < n; e += blockDim.x)
+    s = fma(Ut[(size_t)i * n + e], v[(size_t)b * vstride_b + (size_t)e * stride + off], s);
+  __shared__ double sh[256];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) proj[(size_t)b * r + i] = sh[0];
+}
+
+__global__ void lu_solve_kernel(const double* LU, const int* piv, double* x, int r, int B,
+                                const uint8_t* active) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B || (active && !active[b])) return;
+  const double* A = LU + (size_t)b * r * r;
+  double* y = x + (size_t)b * r;
+  for (int k = 0; k < r; ++k) {
+    const int p = piv[b * r + k];
+    if (p != k) {
+      const double t = y[k];
+      y[k] = y[p];
+      y[p] = t;
+    }
+  }
+  for (int q = 0; q < r; ++q)
+    for (int c = 0; c < q; ++c) y[q] -= A[q * r + c] * y[c];
+  for (int q = r - 1; q >= 0; --q) {
+    for (int c = q + 1; c < r; ++c) y[q] -= A[q * r + c] * y[c];
+    y[q] /= A[q * r + q];
+  }
+}
+
+// out[b][e] = sum_i Ut[i][e] c[b][i]
+__global__ void lift_kernel(const double* Ut, int n, const double* c, int r, double* out,
+                            const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < r; ++i) s = fma(Ut[(size_t)i * n + e], c[(size_t)b * r + i], s);
+    out[(size_t)b * n + e] = s;
+  }
+}
+
+// ---- host helpers -----------------------------------------------------------------------------
+
+// Cyclic Jacobi eigen-decomposition of a symmetric n x n matrix (row-major, in place):
+// eigenvalues on return in lam, eigenvectors as columns of V.
+static void jacobi_eig(std::vector<double>& A, int n, std::vector<double>& lam, std::vector<double>& V) {
+  V.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int q = 0; q < n; ++q) {
+        tot += A[(size_t)p * n + q] * A[(size_t)p * n + q];
+        if (p != q) off += A[(size_t)p * n + q] * A[(size_t)p * n + q];
+      }
+    if (off <= 1e-32 * tot) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[(size_t)p * n + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+        const double theta = (aqq - app) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {
+          const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+          A[(size_t)k * n + p] = c * akp - s * akq;
+          A[(size_t)k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+          A[(size_t)p * n + k] = c * apk - s * aqk;
+          A[(size_t)q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+          V[(size_t)k * n + p] = c * vkp - s * vkq;
+          V[(size_t)k * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  lam.resize(n);
+  for (int i = 0; i < n; ++i) lam[i] = A[(size_t)i * n + i];
+}
+
+struct GramCtx {
+  DevBuf<double> partial, out;
+};
+
+// Host: returns sum over rows (weighted/classified) of X_i Y_j -> out[cls][i][j]
+static int cross_gram(const double* X, int nxc, const double* Y, int nyc, size_t nrow, int n_dof,
+                      int P, const double* wdir, const int32_t* mat, int n_class,
+                      std::vector<double>& out, cudaStream_t st) {
+  const int T = 16;
+  const size_t npairs = (size_t)nxc * nyc;
+  const size_t smem = ((size_t)(nxc + nyc) * T + n_class * npairs) * sizeof(double);
+  if (smem > 200 * 1024) return fail(RTE_EINVAL, "ROM: too many snapshots for the Gram kernel");
+  RTE_CUDA_TRY(cudaFuncSetAttribute(cross_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  int nblocks = (int)std::min<size_t>((nrow + T - 1) / T, 1024);
+  GramCtx g;
+  RTE_TRY(g.partial.alloc((size_t)nblocks * n_class * npairs));
+  RTE_TRY(g.out.alloc((size_t)n_class * npairs));
+  cross_gram_kernel<<<nblocks, 256, smem, st>>>(X, nxc, Y, nyc, nrow, n_dof, P, wdir, mat, n_class,
+                                                g.partial.p);
+  RTE_CUDA_TRY(cudaGetLastError());
+  const int n = (int)(n_class * npairs);
+  sum_partials_kernel<<<(n + 255) / 256, 256, 0, st>>>(g.partial.p, nblocks, n, g.out.p);
+  out.resize(n);
+  RTE_CUDA_TRY(cudaMemcpyAsync(out.data(), g.out.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+  RTE_CUDA_TRY(cudaStreamSynchronize(st));
+  return RTE_OK;
+}
+
+// POD of X [ncol][nrow] (columns contiguous): fills rom->U [r][nrow], sv, r, eps_equiv.
+static int pod(rte_rom_t rom, const double* X, int ncol, size_t nrow, int rank, double eps_pod,
+               const double* wdir, cudaStream_t st) {
+  const rte_disc_s* d = rom->disc;
+  if (ncol < 1) return fail(RTE_EINVAL, "ROM: no snapshots");
+  if (ncol > 128) return fail(RTE_EINVAL, "ROM: at most 128 snapshots per basis");
+  std::vector<double> G;
+  RTE_TRY(cross_gram(X, ncol, X, ncol, nrow, d->n_dof, d->P, wdir, nullptr, 1, G, st));
+  std::vector<double> lam, V;
+  jacobi_eig(G, ncol, lam, V);
+  std::vector<int> order(ncol);
+  for (int i = 0; i < ncol; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return lam[a] > lam[b]; });
+  rom->sv.resize(ncol);
+  double total = 0.0;
+  for (int i = 0; i < ncol; ++i) {
+    rom->sv[i] = std::sqrt(std::max(lam[order[i]], 0.0));
+    total += rom->sv[i];
+  }
+  int r = rank;
+  if (r <= 0) {  // Eq. (pod_truncation): smallest l with sum_{k<=l} s_k / trace >= 1 - eps
+    double acc = 0.0;
+    r = ncol;
+    for (int i = 0; i < ncol; ++i) {
+      acc += rom->sv[i];
+      if (acc / total >= 1.0 - eps_pod) {
+        r = i + 1;
+        break;
+      }
+    }
+  }
+  int nz = 0;
+  for (int i = 0; i < ncol; ++i) nz += rom->sv[i] > 1e-300 * std::max(1.0, rom->sv[0]);
+  r = std::min(r, std::max(nz, 1));
+  r = std::min(r, ncol);
+  rom->r = r;
+  rom->n_snap = ncol;
+  double kept = 0.0;
+  for (int i = 0; i < r; ++i) kept += rom->sv[i];
+  rom->eps_equiv = total > 0 ? 1.0 - kept / total : 0.0;
+  // W = V_r Lambda_r^{-1/2}
+  std::vector<double> W((size_t)ncol * r);
+  for (int k = 0; k < ncol; ++k)
+    for (int i = 0; i < r; ++i) W[(size_t)k * r + i] = V[(size_t)k * ncol + order[i]] / rom->sv[i];
+  DevBuf<double> Wd;
+  RTE_TRY(Wd.alloc(W.size()));
+  RTE_CUDA_TRY(cudaMemcpyAsync(Wd.p, W.data(), sizeof(double) * W.size(), cudaMemcpyHostToDevice, st));
+  RTE_TRY(rom->U.alloc((size_t)r * nrow));
+  basis_kernel<<<(unsigned)((nrow + 127) / 128), 128, 0, st>>>(X, ncol, Wd.p, r, nrow, rom->U.p);
+  RTE_CUDA_TRY(cudaGetLastError());
+  // re-orthonormalise: U <- U L^{-T},  L L^T = U^T diag(mult) U
+  std::vector<double> G2;
+  RTE_TRY(cross_gram(rom->U.p, r, rom->U.p, r, nrow, d->n_dof, d->P, wdir, nullptr, 1, G2, st));
+  std::vector<double> L((size_t)r * r, 0.0);
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double s = G2[(size_t)i * r + j];
+      for (int k = 0; k < j; ++k) s -= L[(size_t)i * r + k] * L[(size_t)j * r + k];
+      if (i == j) {
+        if (!(s > 0)) return fail(RTE_EINVAL, "ROM: basis lost rank during orthonormalisation");
+        L[(size_t)i * r + i] = std::sqrt(s);
+      } else {
+        L[(size_t)i * r + j] = s / L[(size_t)j * r + j];
+      }
+    }
+  // M = L^{-T} (upper triangular): new U_i = sum_k U_k M[k][i]
+  std::vector<double> Minv((size_t)r * r, 0.0);
+  for (int c = 0; c < r; ++c) {  // solve L^T m = e_c
+    std::vector<double> m(r, 0.0);
+    for (int i = r - 1; i >= 0; --i) {
+      double s = i == c ? 1.0 : 0.0;
+      for (int k = i + 1; k < r; ++k) s -= L[(size_t)k * r + i] * m[k];
+      m[i] = s / L[(size_t)i * r + i];
+    }
+    for (int k = 0; k < r; ++k) Minv[(size_t)k * r + c] = m[k];
+  }
+  DevBuf<double> Md, Unew;
+  RTE_TRY(Md.alloc(Minv.size()));
+  RTE_TRY(Unew.alloc((size_t)r * nrow));
+  RTE_CUDA_TRY(cudaMemcpyAsync(Md.p, Minv.data(), sizeof(double) * Minv.size(), cudaMemcpyHostToDevice, st));
+  basis_kernel<<<(unsigned)((nrow + 127) / 128), 128, 0, st>>>(rom->U.p, r, Md.p, r, nrow, Unew.p);
+  RTE_CUDA_TRY(cudaGetLastError());
+  std::swap(rom->U.p, Unew.p);
+  std::swap(rom->U.n, Unew.n);
+  RTE_CUDA_TRY(cudaStreamSynchronize(st));
+  return RTE_OK;
+}
+
+// U^rho, U^iso and the affine reduced operators for a basis already in rom->U.
+static int reduce_operators(rte_rom_t rom, cudaStream_t st) {
+  const rte_disc_s* d = rom->disc;
+  const int r = rom->r, n = d->n_dof;
+  const size_t nrow = (size_t)d->n_dirs * n;
+  RTE_TRY(rom->U_rho.alloc((size_t)r * n));
+  RTE_TRY(rom->U_iso.alloc((size_t)r * n));
+  rho_iso_kernel<<<(unsigned)(((size_t)r * n + 255) / 256), 256, 0, st>>>(
+      rom->U.p, r, d->n_dirs, n, d->dir_dev.p, rom->U_rho.p, rom->U_iso.p);
+  RTE_CUDA_TRY(cudaGetLastError());
+  // multiplicity per direction as the row weight
+  std::vector<double> mult(d->n_dirs);
+  for (int k = 0; k < d->n_dirs; ++k) mult[k] = d->dirs[k].mult;
+  DevBuf<double> multd, Y;
+  RTE_TRY(multd.alloc(d->n_dirs));
+  RTE_CUDA_TRY(cudaMemcpyAsync(multd.p, mult.data(), sizeof(double) * d->n_dirs, cudaMemcpyHostToDevice, st));
+  RTE_TRY(Y.alloc((size_t)r * nrow));
+  if (d->dim == 2) {
+    const size_t tot = (size_t)r * d->n_dirs * d->n_cells;
+    transport_apply2d_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+        rom->U.p, r, d->n_dirs, d->nx, d->ny, d->hx, d->hy, d->dir_dev.p, Y.p);
+  } else {
+    const size_t tot = (size_t)r * d->n_dirs * d->nx;
+    transport_apply1d_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+        rom->U.p, r, d->n_dirs, d->nx, d->hx, d->dir_dev.p, Y.p);
+  }
+  RTE_CUDA_TRY(cudaGetLastError());
+  std::vector<double> A0, Aa, C;
+  // A_0r[i][j] = sum_rows mult U_i (D U_j)
+  RTE_TRY(cross_gram(rom->U.p, r, Y.p, r, nrow, n, d->P, multd.p, nullptr, 1, A0, st));
+  RTE_TRY(cross_gram(rom->U.p, r, rom->U.p, r, nrow, n, d->P, multd.p, d->mat_id.p, d->n_mat, Aa, st));
+  RTE_TRY(cross_gram(rom->U_iso.p, r, rom->U_rho.p, r, n, n, d->P, nullptr, d->mat_id.p, d->n_mat, C, st));
+  rom->A0 = A0;
+  rom->Aa = Aa;
+  rom->As.resize(Aa.size());
+  for (size_t k = 0; k < Aa.size(); ++k) rom->As[k] = Aa[k] - C[k];
+  RTE_TRY(rom->A0_dev.alloc(A0.size()));
+  RTE_TRY(rom->Aa_dev.alloc(Aa.size()));
+  RTE_TRY(rom->As_dev.alloc(Aa.size()));
+  RTE_CUDA_TRY(cudaMemcpyAsync(rom->A0_dev.p, A0.data(), 8 * A0.size(), cudaMemcpyHostToDevice, st));
+  RTE_CUDA_TRY(cudaMemcpyAsync(rom->Aa_dev.p, Aa.data(), 8 * Aa.size(), cudaMemcpyHostToDevice, st));
+  RTE_CUDA_TRY(cudaMemcpyAsync(rom->As_dev.p, rom->As.data(), 8 * Aa.size(), cudaMemcpyHostToDevice, st));
+  RTE_CUDA_TRY(cudaStreamSynchronize(st));
+  return RTE_OK;
+}
+
+// Assemble and factor A_{mu,r} for every instance of `bt` (cached per batch handle).
+int rom_prepare(rte_rom_t rom, rte_batch_t bt, cudaStream_t st) {
+  if (!rom->online) rom->online = new RomOnline();
+  RomOnline* o = rom->online;
+  const int r = rom->r, B = bt->B;
+  if (o->lu.n != (size_t)B * r * r) {
+    RTE_TRY(o->lu.alloc((size_t)B * r * r));
+    RTE_TRY(o->piv.alloc((size_t)B * r));
+    RTE_TRY(o->proj.alloc((size_t)B * r));
+  }
+  rom_assemble_lu_kernel<<<(B + 63) / 64, 64, 0, st>>>(rom->A0_dev.p, rom->Aa_dev.p, rom->As_dev.p,
+                                                       r, bt->disc->n_mat, bt->sigma_t.p,
+                                                       bt->sigma_s.p, B, o->lu.p, o->piv.p);
+  RTE_CUDA_TRY(cudaGetLastError());
+  o->batch = bt;
+  return RTE_OK;
+}
+
+int rom_correction(rte_rom_t rom, rte_batch_t bt, const double* R, double* drho,
+                   const uint8_t* active, cudaStream_t st) {
+  RomOnline* o = rom->online;
+  if (!o || o->batch != bt) RTE_TRY(rom_prepare(rom, bt, st));
+  o = rom->online;
+  const int r = rom->r, n = bt->disc->n_dof, B = bt->B;
+  project_kernel<<<dim3(r, B), 256, 0, st>>>(rom->U_iso.p, n, R, 1, 0, (size_t)n, o->proj.p, r, active);
+  lu_solve_kernel<<<(B + 63) / 64, 64, 0, st>>>(o->lu.p, o->piv.p, o->proj.p, r, B, active);
+  lift_kernel<<<dim3(std::min((n + 255) / 256, 1024), B), 256, 0, st>>>(rom->U_rho.p, n, o->proj.p, r,
+                                                                        drho, active);
+  RTE_CUDA_TRY(cudaGetLastError());
+  return RTE_OK;
+}
+
+}  // namespace rte
+
+rte_rom_s::~rte_rom_s() { delete online; }
+
+using namespace rte;
+
+extern "C" int rte_rom_build(rte_batch_t train, const rte_rom_opts* opts, rte_rom_t* rom_p,
+                             rte_rom_t* rom_c, void* stream) {
+  if (!train || !opts) return fail(RTE_EINVAL, "rte_rom_build: null argument");
+  if (!train->params_set) return fail(RTE_ESTATE, "rte_rom_build: parameters not set");
+  if (opts->window < 1 || opts->max_iter < 1 || !(opts->eps_train > 0))
+    return fail(RTE_EINVAL, "rte_rom_build: bad options");
+  if ((opts->rank_p <= 0 || opts->rank_c <= 0) && !(opts->eps_pod > 0 && opts->eps_pod < 1))
+    return fail(RTE_EINVAL, "rte_rom_build: need a rank or 0 < eps_pod < 1");
+  rte_disc_s* d = train->disc;
+  DeviceGuard g(d->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int B = train->B, w = opts->window;
+  const size_t nrow = (size_t)d->n_dirs * d->n_dof;
+  DevBuf<double> psi_cur, psi_win, rho;
+  RTE_TRY(psi_cur.alloc((size_t)B * nrow));
+  RTE_TRY(psi_win.alloc((size_t)w * B * nrow));
+  RTE_TRY(rho.alloc((size_t)B * d->n_dof));
+  RTE_CUDA_TRY(cudaMemsetAsync(rho.p, 0, sizeof(double) * B * d->n_dof, st));
+  rte_solve_opts so{opts->eps_train, 0, opts->max_iter, RTE_SA_DSA, 0, 0.0,
+                    opts->dsa_rtol > 0 ? opts->dsa_rtol : 1e-12, 2000, nullptr};
+  std::vector<rte_solve_report> rep(B);
+  int s = run_si(train, &so, nullptr, rho.p, rep.data(), nullptr, st, psi_cur.p, psi_win.p, w);
+  if (s != RTE_OK) return s == RTE_ENOCONV ? fail(RTE_ENOCONV, "training solve did not converge") : s;
+  // correction snapshots: (b, l) for l < min(n_conv, w)
+  std::vector<int> pairs;
+  for (int b = 0; b < B; ++b)
+    for (int l = 0; l < std::min(rep[b].n_sweep, w); ++l) pairs.push_back(b), pairs.push_back(l);
+  const int ndc = (int)pairs.size() / 2;
+  DevBuf<double> dF;
+  DevBuf<int> pairs_d;
+  RTE_TRY(dF.alloc((size_t)ndc * nrow));
+  RTE_TRY(pairs_d.alloc(pairs.size()));
+  RTE_CUDA_TRY(cudaMemcpyAsync(pairs_d.p, pairs.data(), sizeof(int) * pairs.size(), cudaMemcpyHostToDevice, st));
+  diff_kernel<<<dim3(1024, ndc), 256, 0, st>>>(psi_cur.p, psi_win.p, pairs_d.p, ndc, nrow, B, dF.p);
+  RTE_CUDA_TRY(cudaGetLastError());
+  std::vector<double> mult(d->n_dirs);
+  for (int k = 0; k < d->n_dirs; ++k) mult[k] = d->dirs[k].mult;
+  DevBuf<double> multd;
+  RTE_TRY(multd.alloc(d->n_dirs));
+  RTE_CUDA_TRY(cudaMemcpyAsync(multd.p, mult.data(), 8 * mult.size(), cudaMemcpyHostToDevice, st));
+  if (rom_p) {
+    auto* rp = new rte_rom_s();
+    rp->disc = d;
+    int e = pod(rp, psi_cur.p, B, nrow, opts->rank_p, opts->eps_pod, multd.p, st);
+    if (e == RTE_OK) e = reduce_operators(rp, st);
+    if (e != RTE_OK) {
+      delete rp;
+      return e;
+    }
+    *rom_p = rp;
+  }
+  if (rom_c) {
+    auto* rc = new rte_rom_s();
+    rc->disc = d;
+    int e = pod(rc, dF.p, ndc, nrow, opts->rank_c, opts->eps_pod, multd.p, st);
+    if (e == RTE_OK) e = reduce_operators(rc, st);
+    if (e != RTE_OK) {
+      delete rc;
+      if (rom_p && *rom_p) {
+        delete *rom_p;
+        *rom_p = nullptr;
+      }
+      return e;
+    }
+    *rom_c = rc;
+  }
+  return RTE_OK;
+}
+
+extern "C" int rte_rom_destroy(rte_rom_t rom) {
+  if (!rom) return RTE_OK;
+  DeviceGuard g(rom->disc->device);
+  delete rom;
+  return RTE_OK;
+}
+
+extern "C" int rte_rom_info(rte_rom_t rom, double* info, double* sv) {
+  if (!rom || !info) return fail(RTE_EINVAL, "rte_rom_info: null argument");
+  double tot = 0.0;
+  for (double v : rom->sv) tot += v;
+  info[0] = rom->r;
+  info[1] = rom->n_snap;
+  info[2] = rom->eps_equiv;
+  info[3] = rom->disc->n_dirs;
+  info[4] = rom->disc->n_dof;
+  info[5] = tot;
+  if (sv) std::memcpy(sv, rom->sv.data(), sizeof(double) * rom->sv.size());
+  return RTE_OK;
+}
+
+extern "C" int rte_rom_initial_guess(rte_rom_t rom, rte_batch_t b, double* rho0,
+                                     const uint8_t* active, void* stream) {
+  if (!rom || !b || !rho0) return fail(RTE_EINVAL, "rte_rom_initial_guess: null argument");
+  if (!b->params_set) return fail(RTE_ESTATE, "parameters not set");
+  if (rom->disc != b->disc) return fail(RTE_EINVAL, "ROM built on another discretisation");
+  for (double g : b->inflow_h)
+    if (g != 0.0) return fail(RTE_EINVAL, "ROMIG supports vacuum inflow only (U^T b = (U^iso)^T G)");
+  DeviceGuard g(b->disc->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  RTE_TRY(rom_prepare(rom, b, st));
+  const int r = rom->r, n = b->disc->n_dof, B = b->B, P = b->disc->P;
+  // rhs_i = sum_c U_iso[i][c*P + 0] G0[c]: the source has only its zeroth moment
+  DevBuf<double> Ut0;
+  RTE_TRY(Ut0.alloc((size_t)r * b->disc->n_cells));
+  // gather the k = 0 rows of U_iso into a contiguous [r][n_cells] array
+  {
+    std::vector<double> h((size_t)r * n), h0((size_t)r * b->disc->n_cells);
+    RTE_CUDA_TRY(cudaMemcpy(h.data(), rom->U_iso.p, 8 * h.size(), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < r; ++i)
+      for (int c = 0; c < b->disc->n_cells; ++c) h0[(size_t)i * b->disc->n_cells + c] = h[(size_t)i * n + (size_t)c * P];
+    RTE_CUDA_TRY(cudaMemcpy(Ut0.p, h0.data(), 8 * h0.size(), cudaMemcpyHostToDevice));
+  }
+  RomOnline* o = rom->online;
+  project_kernel<<<dim3(r, B), 256, 0, st>>>(Ut0.p, b->disc->n_cells, b->G0.p, 1, 0,
+                                             (size_t)b->disc->n_cells, o->proj.p, r, active);
+  lu_solve_kernel<<<(B + 63) / 64, 64, 0, st>>>(o->lu.p, o->piv.p, o->proj.p, r, B, active);
+  lift_kernel<<<dim3(std::min((n + 255) / 256, 1024), B), 256, 0, st>>>(rom->U_rho.p, n, o->proj.p, r,
+                                                                        rho0, active);
+  RTE_CUDA_TRY(cudaGetLastError());
+  RTE_CUDA_TRY(cudaStreamSynchronize(st));
+  return RTE_OK;
+}
+
+extern "C" int rte_romsa_correction(rte_rom_t rom, rte_batch_t b, const double* R, double* drho,
+                                    const uint8_t* active, void* stream) {
+  if (!rom || !b || !R || !drho) return fail(RTE_EINVAL, "rte_romsa_correction: null argument");
+  if (!b->params_set) return fail(RTE_ESTATE, "parameters not set");
+  if (rom->disc != b->disc) return fail(RTE_EINVAL, "ROM built on another discretisation");
+  DeviceGuard g(b->disc->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  RTE_TRY(rom_prepare(rom, b, st));
+  return rom_correction(rom, b, R, drho, active, st);
+}

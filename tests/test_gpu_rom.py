@@ -1,0 +1,112 @@
+"""GPU parity of the POD ROM pipeline (Sec. 3): offline bases and singular values, ROMIG, ROMSA
+and ROMSAD solves, against the CPU oracle on the same seeded training and test sets.
+
+Tolerances, derived: training solves on both sides stop at an absolute change of 1e-13 with
+DSA solved to 1e-13, so snapshots agree to ~1e-11 relative; leading singular values then agree
+to 1e-9 of sigma_1.  The GPU takes the SVD through the snapshot Gram matrix, which resolves
+singular values only down to ~sqrt(eps) sigma_1, so ROM outputs are compared at 1e-6
+relative.  ROMSAD under a forced identical schedule is compared iterate by iterate at 1e-6."""
+import numpy as np
+import pytest
+
+from oracle.dsa import ConsistentDSA
+from oracle.rom import OfflineROMs
+from oracle.sisa import sisa
+from oracle.transport import Transport
+from paper_2402_10488_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+N, NA, NVZ = 12, 8, 2
+
+
+def _rte():
+    from paper_2402_10488_gb300 import build, rte
+    build.build()
+    return rte
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.fixture(scope="module")
+def roms():
+    rte = _rte()
+    train = inputs.lattice_train(N, NA, n_train=8, n_vz=NVZ)
+    tb = rte.Batch.from_problem(train)
+    rp, rc = rte.Rom.build(tb, eps_train=1e-13, window=3, rank_p=6, rank_c=8, max_iter=300,
+                           dsa_rtol=1e-13)
+    off = OfflineROMs(train, eps_train=1e-13, window=3, rank_p=6, rank_c=8)
+    return rte, tb, rp, rc, off
+
+
+def test_singular_values_match(roms):
+    rte, _, rp, rc, off = roms
+    assert rp.r == 6 and rc.r == 8
+    assert rp.n_snap == 8 and rc.n_snap == off.dF.shape[1]
+    np.testing.assert_allclose(rp.sv[:6], off.pod_p.sv[:6], atol=1e-9 * off.pod_p.sv[0])
+    np.testing.assert_allclose(rc.sv[:8], off.pod_c.sv[:8], atol=1e-9 * off.pod_c.sv[0])
+    assert abs(rc.eps_pod - off.pod_c.eps_equiv) < 1e-9
+
+
+def test_romig_matches_oracle(roms):
+    rte, tb, rp, rc, off = roms
+    test = inputs.lattice_test(N, NA, 3, n_vz=NVZ)
+    batch = rte.Batch(tb.disc, 3)
+    batch.set_params(test)
+    rho0 = torch.zeros((3, test.n_dof), dtype=torch.float64, device="cuda")
+    rp.initial_guess(batch, rho0)
+    got = rho0.cpu().numpy()
+    for b in range(3):
+        ref = off.rom_p.initial_guess(Transport(test, b))
+        assert _rel(got[b], ref) < 1e-6
+
+
+def test_romsa_correction_matches_oracle(roms):
+    rte, tb, rp, rc, off = roms
+    test = inputs.lattice_test(N, NA, 2, n_vz=NVZ)
+    batch = rte.Batch(tb.disc, 2)
+    batch.set_params(test)
+    R = np.random.default_rng(3).uniform(0, 1, (2, test.n_dof))
+    d = torch.zeros((2, test.n_dof), dtype=torch.float64, device="cuda")
+    rc.romsa_correction(batch, torch.tensor(R, device="cuda"), d)
+    got = d.cpu().numpy()
+    for b in range(2):
+        ref = off.rom_c.romsa_correction(Transport(test, b), R[b])
+        assert _rel(got[b], ref) < 1e-6
+
+
+def test_romsad_forced_schedule_iterates_and_converged(roms):
+    rte, tb, rp, rc, off = roms
+    test = inputs.lattice_test(N, NA, 2, n_vz=NVZ)
+    batch = rte.Batch(tb.disc, 2)
+    batch.set_params(test)
+    sched = np.array([1, 1, 0, 1, 0, 0, 0, 0], np.uint8)
+    rho = torch.zeros((2, test.n_dof), dtype=torch.float64, device="cuda")
+    rep, hist, st = batch.solve(rho, 0.0, sa=rte.SA_ROMSAD, max_iter=8, rom_c=rc, schedule=sched,
+                                dsa_rtol=1e-13, dsa_max_it=3000, history=True)
+    got = rho.cpu().numpy()
+    names = ["romsa" if s else "dsa" for s in sched]
+    for b in range(2):
+        tr = Transport(test, b)
+        ref = sisa(tr, np.zeros(tr.n_dof), 0.0, 8, "romsad", dsa=ConsistentDSA(tr), rom_c=off.rom_c,
+                   schedule=names)
+        assert _rel(got[b], ref["rho"]) < 1e-6
+        # a correction follows every one of the 8 sweeps: ROMSA after 1, 2, 4; DSA after the rest
+        assert rep[b]["n_romsa"] == 3 and rep[b]["n_dsa"] == 5
+    # Alg. 2 switch, converged answer equals SI-DSA's
+    rho2 = torch.zeros((2, test.n_dof), dtype=torch.float64, device="cuda")
+    rep2, hist2, st2 = batch.solve(rho2, 1e-12, sa=rte.SA_ROMSAD, rel=True, max_iter=300, rom_c=rc,
+                                   theta=5, eps_romsad=0.1 * max(1e-13, rc.eps_pod), dsa_rtol=1e-2,
+                                   history=True)
+    assert st2 == 0
+    for b in range(2):
+        tr = Transport(test, b)
+        ref = sisa(tr, np.zeros(tr.n_dof), 1e-14, 400, "dsa", dsa=ConsistentDSA(tr), tol_mode="rel")
+        assert _rel(rho2.cpu().numpy()[b], ref["rho"]) < 1e-10
+        h = hist2[b, : rep2[b]["n_sweep"]]
+        eps_r = 0.1 * max(1e-13, rc.eps_pod)
+        n_rom_expected = sum(1 for l, dl in enumerate(h[:-1], start=1) if l <= 5 and dl >= eps_r)
+        assert rep2[b]["n_romsa"] == n_rom_expected
