@@ -58,6 +58,10 @@ int rte_version(void);
  * call on the same thread. */
 const char* rte_last_error(void);
 
+/* Library-wide counters: out (HOST int64[1]) = number of kernels this library has launched in
+ * this process so far (every launch site increments it). */
+int rte_counters(int64_t* out);
+
 /* ---- discretisation -------------------------------------------------------------------- */
 
 /* Mesh, angular rule and material map, shared by every instance of a batch.
@@ -126,6 +130,14 @@ int rte_batch_set_params(rte_batch_t batch, const double* sigma_t, const double*
  * Asynchronous on `stream`.  Errors: RTE_ESTATE (no parameters), RTE_EINVAL, RTE_ECUDA. */
 int rte_sweep(rte_batch_t batch, const double* rho_in, double* rho_out, double* psi_out,
               int with_source, const uint8_t* active, void* stream);
+
+/* Sweep-kernel timing for throughput and roofline accounting.  Each 2D/1D sweep kernel launched
+ * for this batch while timing is on is bracketed by CUDA events recorded on the stream it is
+ * launched on.  out (HOST double[3], may be NULL) receives (total sweep-kernel milliseconds,
+ * number of timed launches, cell x distinct-direction local solves they performed); the call
+ * waits for the recorded events.  enable = 1 resets and starts, 0 resets and stops, -1 only
+ * reads.  Errors: RTE_EINVAL, RTE_ECUDA. */
+int rte_batch_timing(rte_batch_t batch, int enable, double* out);
 
 /* The distinct swept directions: dirs (HOST double[n_dirs][4]) = (v_x, v_y, summed weight,
  * multiplicity), in the order used by psi_out and the ROM bases. */

@@ -7,6 +7,7 @@
 
 namespace rte {
 
+std::atomic<long long> g_launches{0};
 static thread_local std::string g_last_error;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
@@ -227,7 +228,47 @@ extern "C" int rte_disc_quadrature(rte_disc_t disc, double* v, double* omega) {
 
 // ---- batches ------------------------------------------------------------------------------
 
-rte_batch_s::~rte_batch_s() { rte::dsa_state_free(dsa); }
+rte_batch_s::~rte_batch_s() {
+  rte::dsa_state_free(dsa);
+  for (auto& e : sweep_ev) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+}
+
+extern "C" int rte_counters(int64_t* out) {
+  if (!out) return fail(RTE_EINVAL, "rte_counters: null argument");
+  out[0] = rte::g_launches.load();
+  return RTE_OK;
+}
+
+extern "C" int rte_batch_timing(rte_batch_t b, int enable, double* out) {
+  if (!b) return fail(RTE_EINVAL, "rte_batch_timing: null argument");
+  DeviceGuard g(b->disc->device);
+  double ms = 0.0;
+  for (auto& e : b->sweep_ev) {
+    RTE_CUDA_TRY(cudaEventSynchronize(e.second));
+    float t = 0.f;
+    RTE_CUDA_TRY(cudaEventElapsedTime(&t, e.first, e.second));
+    ms += t;
+  }
+  if (out) {
+    out[0] = ms;
+    out[1] = (double)b->sweep_launches;
+    out[2] = b->sweep_units;
+  }
+  if (enable >= 0) {
+    for (auto& e : b->sweep_ev) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+    b->sweep_ev.clear();
+    b->sweep_units = 0.0;
+    b->sweep_launches = 0;
+    b->timing = enable != 0;
+  }
+  return RTE_OK;
+}
 
 extern "C" int rte_batch_create(rte_disc_t disc, int B, rte_batch_t* out) {
   if (!disc || !out || B < 1) return fail(RTE_EINVAL, "rte_batch_create: bad argument");

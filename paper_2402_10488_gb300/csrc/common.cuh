@@ -7,12 +7,17 @@
 #include <cmath>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
 #include <string>
 #include <vector>
 
 #include "../../include/rte.h"
 
 namespace rte {
+
+// ---- launch accounting: every kernel launch of the library is counted ------------------------
+extern std::atomic<long long> g_launches;
+#define RTE_NOTE_LAUNCH() (::rte::g_launches.fetch_add(1, std::memory_order_relaxed))
 
 // ---- error plumbing ------------------------------------------------------------------------
 void set_error(const std::string& msg);
@@ -132,13 +137,19 @@ struct rte_batch_s {
   rte::DevBuf<unsigned long long> norms;  // [B][2] stop-test norms as ordered bit patterns
   rte::DevBuf<double> work;               // [B][n_dof] x 4 iteration scratch for rte_solve
   rte::DsaState* dsa = nullptr;
+  // optional phase timing with CUDA events on the launching stream (rte_batch_timing)
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> sweep_ev;
+  double sweep_units = 0.0;   // cell x distinct-direction solves in the timed sweeps
+  long long sweep_launches = 0;
   ~rte_batch_s();
 };
 
 namespace rte {
 // sweep.cu
 int sweep_launch(rte_batch_t b, const double* rho_in, double* rho_out, double* psi_out,
-                 int with_source, const uint8_t* active, cudaStream_t st, bool fuse_norms);
+                 int with_source, const uint8_t* active, cudaStream_t st, bool fuse_norms,
+                 int n_active = -1);
 int norms_to_host(rte_batch_t b, double* host, cudaStream_t st);
 int setup_tables(rte_batch_t b, cudaStream_t st);
 int correction_source_launch(rte_batch_t b, const double* rs, const double* rp, double* R,

@@ -648,7 +648,7 @@ int dsa_setup(rte_batch_t bt, cudaStream_t st) {
     RTE_TRY(s->work1.alloc((size_t)B * d->nx * 4));
     dsa1d_factor_kernel<<<(B + 63) / 64, 64, 0, st>>>(s->K1, bt->sigma_t.p, bt->sigma_s.p,
                                                       d->mat_id.p, d->nx, d->n_mat, B,
-                                                      s->Dpinv.p, s->Mfac.p);
+                                                      s->Dpinv.p, s->Mfac.p); RTE_NOTE_LAUNCH();
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
   }
@@ -725,13 +725,14 @@ int dsa_setup(rte_batch_t bt, cudaStream_t st) {
     const int nxc = s->lnx[l + 1], nyc = s->lny[l + 1];
     const int total = nxc * nyc * 5 * NB2;
     dim3 grid((total + 255) / 256, B);
-    if (l == 0)
-      ptap_kernel<true><<<grid, 256, 0, st>>>(F, Lf, nxc, nyc, B, s->blk[0]->p);
-    else
-      ptap_kernel<false><<<grid, 256, 0, st>>>(F, Lf, nxc, nyc, B, s->blk[l]->p);
+    if (l == 0) {
+      ptap_kernel<true><<<grid, 256, 0, st>>>(F, Lf, nxc, nyc, B, s->blk[0]->p); RTE_NOTE_LAUNCH();
+    } else {
+      ptap_kernel<false><<<grid, 256, 0, st>>>(F, Lf, nxc, nyc, B, s->blk[l]->p); RTE_NOTE_LAUNCH();
+    }
     RTE_CUDA_TRY(cudaGetLastError());
     const int nb = nxc * nyc * B;
-    blockinv_kernel<<<(nb + 63) / 64, 64, 0, st>>>(s->blk[l]->p, s->dinv[l]->p, nxc * nyc, B);
+    blockinv_kernel<<<(nb + 63) / 64, 64, 0, st>>>(s->blk[l]->p, s->dinv[l]->p, nxc * nyc, B); RTE_NOTE_LAUNCH();
     RTE_CUDA_TRY(cudaGetLastError());
   }
   return RTE_OK;
@@ -747,16 +748,17 @@ static int vcycle(rte_batch_t bt, int l, const uint8_t* active, cudaStream_t st,
   float* x = s->xl[l]->p;
   float* b = s->bl[l]->p;
   float* r = s->rl[l]->p;
-  zero32_kernel<<<dim3((per + 255) / 256, B), 256, 0, st>>>(x, per, active);
+  zero32_kernel<<<dim3((per + 255) / 256, B), 256, 0, st>>>(x, per, active); RTE_NOTE_LAUNCH();
   dim3 gcol((L.nc + 127) / 128, B);
   const bool coarsest = l == s->n_levels - 1;
   auto smooth = [&](int c0) {
     for (int k = 0; k < 2; ++k) {
       const int color = k == 0 ? c0 : 1 - c0;
-      if (l == 0)
-        rbgs_kernel<true><<<gcol, 128, 0, st>>>(F, L, B, color, b, x, active);
-      else
-        rbgs_kernel<false><<<gcol, 128, 0, st>>>(F, L, B, color, b, x, active);
+      if (l == 0) {
+        rbgs_kernel<true><<<gcol, 128, 0, st>>>(F, L, B, color, b, x, active); RTE_NOTE_LAUNCH();
+      } else {
+        rbgs_kernel<false><<<gcol, 128, 0, st>>>(F, L, B, color, b, x, active); RTE_NOTE_LAUNCH();
+      }
     }
   };
   if (coarsest && L.nc == 1) {  // exact: x = D^{-1} b
@@ -768,17 +770,18 @@ static int vcycle(rte_batch_t bt, int l, const uint8_t* active, cudaStream_t st,
   for (int k = 0; k < npre; ++k) smooth(0);
   if (!coarsest) {
     dim3 gc((L.nc + 127) / 128, B);
-    if (l == 0)
-      residual_kernel<true><<<gc, 128, 0, st>>>(F, L, B, b, x, r, active);
-    else
-      residual_kernel<false><<<gc, 128, 0, st>>>(F, L, B, b, x, r, active);
+    if (l == 0) {
+      residual_kernel<true><<<gc, 128, 0, st>>>(F, L, B, b, x, r, active); RTE_NOTE_LAUNCH();
+    } else {
+      residual_kernel<false><<<gc, 128, 0, st>>>(F, L, B, b, x, r, active); RTE_NOTE_LAUNCH();
+    }
     const int nxc = s->lnx[l + 1], nyc = s->lny[l + 1];
     const int nco = nxc * nyc * NB;
     restrict_kernel<<<dim3((nco + 255) / 256, B), 256, 0, st>>>(L.nx, nxc, nyc, B, r,
-                                                                s->bl[l + 1]->p, active);
+                                                                s->bl[l + 1]->p, active); RTE_NOTE_LAUNCH();
     RTE_TRY(vcycle(bt, l + 1, active, st, nu));
     prolong_add_kernel<<<dim3((per + 255) / 256, B), 256, 0, st>>>(L.nx, L.ny, B, s->xl[l + 1]->p,
-                                                                   x, active);
+                                                                   x, active); RTE_NOTE_LAUNCH();
     for (int k = 0; k < nu; ++k) smooth(1);
   }
   RTE_CUDA_TRY(cudaGetLastError());
@@ -812,12 +815,12 @@ static int dsa2d_fgmres(rte_batch_t bt, const double* R, double* drho, double rt
   int status = RTE_OK;
   // r0 = b - A x (x = 0 initially): v0 = packed R
   double* w = s->w.p;
-  pack_rhs_kernel<<<gvec, 256, 0, st>>>(R, w, nc, act_dev.p);
+  pack_rhs_kernel<<<gvec, 256, 0, st>>>(R, w, nc, act_dev.p); RTE_NOTE_LAUNCH();
   bool first = true;
   int total_it = 0;
   while (true) {
     // w holds the current residual for active instances
-    dots_kernel<<<dim3(1, B), 512, 0, st>>>(w, 0, w, s->dots_dev.p, n, m + 1, act_dev.p);
+    dots_kernel<<<dim3(1, B), 512, 0, st>>>(w, 0, w, s->dots_dev.p, n, m + 1, act_dev.p); RTE_NOTE_LAUNCH();
     RTE_CUDA_TRY(cudaMemcpyAsync(hbuf.data(), s->dots_dev.p, sizeof(double) * B * (m + 1),
                                  cudaMemcpyDeviceToHost, st));
     RTE_CUDA_TRY(cudaStreamSynchronize(st));
@@ -842,7 +845,7 @@ static int dsa2d_fgmres(rte_batch_t bt, const double* R, double* drho, double rt
     for (int b = 0; b < B; ++b) inv[(size_t)b * (m + 1)] = act[b] ? 1.0 / beta[b] : 0.0;
     RTE_CUDA_TRY(cudaMemcpyAsync(s->dots_dev.p, inv.data(), sizeof(double) * inv.size(),
                                  cudaMemcpyHostToDevice, st));
-    scale_kernel<<<gvec_c, 256, 0, st>>>(w, s->V.p, s->dots_dev.p, n, m + 1, act_dev.p);
+    scale_kernel<<<gvec_c, 256, 0, st>>>(w, s->V.p, s->dots_dev.p, n, m + 1, act_dev.p); RTE_NOTE_LAUNCH();
     // Arnoldi with Givens rotations per instance
     std::vector<double> H((size_t)B * (m + 1) * m, 0.0), cs((size_t)B * m), sn((size_t)B * m),
         g((size_t)B * (m + 1), 0.0);
@@ -858,18 +861,18 @@ static int dsa2d_fgmres(rte_batch_t bt, const double* R, double* drho, double rt
       double* vk = s->V.p + (size_t)k * vstride;
       double* zk = s->Z.p + (size_t)k * vstride;
       // z_k = M^{-1} v_k (one FP32 V-cycle)
-      to32_kernel<<<gvec_c, 256, 0, st>>>(vk, s->bl[0]->p, 0, n, act_dev.p);
+      to32_kernel<<<gvec_c, 256, 0, st>>>(vk, s->bl[0]->p, 0, n, act_dev.p); RTE_NOTE_LAUNCH();
       RTE_TRY(vcycle(bt, 0, act_dev.p, st, 2));
-      to64_kernel<<<gvec_c, 256, 0, st>>>(s->xl[0]->p, zk, n, act_dev.p);
+      to64_kernel<<<gvec_c, 256, 0, st>>>(s->xl[0]->p, zk, n, act_dev.p); RTE_NOTE_LAUNCH();
       // w = A z_k (FP64)
-      fine_apply64_kernel<<<gvec, 256, 0, st>>>(F, d->nx, d->ny, B, zk, w, act_dev.p);
+      fine_apply64_kernel<<<gvec, 256, 0, st>>>(F, d->nx, d->ny, B, zk, w, act_dev.p); RTE_NOTE_LAUNCH();
       // classical Gram-Schmidt, twice
       std::vector<double> hk((size_t)B * (m + 1), 0.0);
       for (int pass = 0; pass < 2; ++pass) {
         dots_kernel<<<dim3(k + 1, B), 512, 0, st>>>(s->V.p, vstride, w, s->dots_dev.p, n, m + 1,
-                                                    act_dev.p);
+                                                    act_dev.p); RTE_NOTE_LAUNCH();
         gs_update_kernel<<<gvec_c, 256, 0, st>>>(s->V.p, vstride, w, s->dots_dev.p, n, k + 1,
-                                                 m + 1, act_dev.p);
+                                                 m + 1, act_dev.p); RTE_NOTE_LAUNCH();
         RTE_CUDA_TRY(cudaMemcpyAsync(hbuf.data(), s->dots_dev.p, sizeof(double) * B * (m + 1),
                                      cudaMemcpyDeviceToHost, st));
         RTE_CUDA_TRY(cudaStreamSynchronize(st));
@@ -877,7 +880,7 @@ static int dsa2d_fgmres(rte_batch_t bt, const double* R, double* drho, double rt
           if (inner[b])
             for (int i = 0; i <= k; ++i) hk[(size_t)b * (m + 1) + i] += hbuf[(size_t)b * (m + 1) + i];
       }
-      dots_kernel<<<dim3(1, B), 512, 0, st>>>(w, 0, w, s->dots_dev.p, n, m + 1, act_dev.p);
+      dots_kernel<<<dim3(1, B), 512, 0, st>>>(w, 0, w, s->dots_dev.p, n, m + 1, act_dev.p); RTE_NOTE_LAUNCH();
       RTE_CUDA_TRY(cudaMemcpyAsync(hbuf.data(), s->dots_dev.p, sizeof(double) * B * (m + 1),
                                    cudaMemcpyDeviceToHost, st));
       RTE_CUDA_TRY(cudaStreamSynchronize(st));
@@ -913,7 +916,7 @@ static int dsa2d_fgmres(rte_batch_t bt, const double* R, double* drho, double rt
         RTE_CUDA_TRY(cudaMemcpyAsync(s->dots_dev.p, sc.data(), sizeof(double) * sc.size(),
                                      cudaMemcpyHostToDevice, st));
         scale_kernel<<<gvec_c, 256, 0, st>>>(w, s->V.p + (size_t)(k + 1) * vstride, s->dots_dev.p, n,
-                                             m + 1, act_dev.p);
+                                             m + 1, act_dev.p); RTE_NOTE_LAUNCH();
       }
     }
     // solve H y = g and update x += Z y
@@ -933,23 +936,23 @@ static int dsa2d_fgmres(rte_batch_t bt, const double* R, double* drho, double rt
     RTE_CUDA_TRY(cudaMemcpyAsync(s->dots_dev.p, y.data(), sizeof(double) * y.size(),
                                  cudaMemcpyHostToDevice, st));
     combine_kernel<<<gvec_c, 256, 0, st>>>(s->Z.p, vstride, x, s->dots_dev.p, n, kmax, m + 1,
-                                           act_dev.p);
+                                           act_dev.p); RTE_NOTE_LAUNCH();
     // new residual w = b - A x
-    fine_apply64_kernel<<<gvec, 256, 0, st>>>(F, d->nx, d->ny, B, x, w, act_dev.p);
+    fine_apply64_kernel<<<gvec, 256, 0, st>>>(F, d->nx, d->ny, B, x, w, act_dev.p); RTE_NOTE_LAUNCH();
     {
       // w = packed(R) - w  (reuse V_m as scratch for the packed right-hand side)
       double* pr = s->V.p + (size_t)m * vstride;
-      pack_rhs_kernel<<<gvec, 256, 0, st>>>(R, pr, nc, act_dev.p);
+      pack_rhs_kernel<<<gvec, 256, 0, st>>>(R, pr, nc, act_dev.p); RTE_NOTE_LAUNCH();
       std::vector<double> mone((size_t)B * (m + 1), 0.0);
       for (int b = 0; b < B; ++b) mone[(size_t)b * (m + 1)] = 1.0;
       RTE_CUDA_TRY(cudaMemcpyAsync(s->dots_dev.p, mone.data(), sizeof(double) * mone.size(),
                                    cudaMemcpyHostToDevice, st));
       // w <- w - 1 * pr, then negate via scale by -1
-      gs_update_kernel<<<gvec_c, 256, 0, st>>>(pr, 0, w, s->dots_dev.p, n, 1, m + 1, act_dev.p);
+      gs_update_kernel<<<gvec_c, 256, 0, st>>>(pr, 0, w, s->dots_dev.p, n, 1, m + 1, act_dev.p); RTE_NOTE_LAUNCH();
       for (int b = 0; b < B; ++b) mone[(size_t)b * (m + 1)] = -1.0;
       RTE_CUDA_TRY(cudaMemcpyAsync(s->dots_dev.p, mone.data(), sizeof(double) * mone.size(),
                                    cudaMemcpyHostToDevice, st));
-      scale_kernel<<<gvec_c, 256, 0, st>>>(w, w, s->dots_dev.p, n, m + 1, act_dev.p);
+      scale_kernel<<<gvec_c, 256, 0, st>>>(w, w, s->dots_dev.p, n, m + 1, act_dev.p); RTE_NOTE_LAUNCH();
     }
     RTE_CUDA_TRY(cudaGetLastError());
     if (total_it >= max_it) {
@@ -960,7 +963,7 @@ static int dsa2d_fgmres(rte_batch_t bt, const double* R, double* drho, double rt
   std::vector<uint8_t> req(B, 1);
   if (active_in) RTE_CUDA_TRY(cudaMemcpy(req.data(), active_in, B, cudaMemcpyDeviceToHost));
   RTE_CUDA_TRY(cudaMemcpyAsync(act_dev.p, req.data(), B, cudaMemcpyHostToDevice, st));
-  extract_rho_kernel<<<dim3((nc * 4 + 255) / 256, B), 256, 0, st>>>(x, drho, nc, act_dev.p);
+  extract_rho_kernel<<<dim3((nc * 4 + 255) / 256, B), 256, 0, st>>>(x, drho, nc, act_dev.p); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   RTE_CUDA_TRY(cudaStreamSynchronize(st));
   if (iters_out)
@@ -974,7 +977,7 @@ int dsa_apply(rte_batch_t bt, const double* R, double* drho, double rtol, int ma
   if (!s) return fail(RTE_ESTATE, "DSA not set up");
   if (bt->disc->dim == 1) {
     dsa1d_solve_kernel<<<(bt->B + 63) / 64, 64, 0, st>>>(s->K1, s->Dpinv.p, s->Mfac.p, R, drho,
-                                                         s->work1.p, bt->disc->nx, bt->B, active);
+                                                         s->work1.p, bt->disc->nx, bt->B, active); RTE_NOTE_LAUNCH();
     RTE_CUDA_TRY(cudaGetLastError());
     if (iters)
       for (int b = 0; b < bt->B; ++b) iters[b] = 1;

@@ -357,10 +357,10 @@ static int cross_gram(const double* X, int nxc, const double* Y, int nyc, size_t
   RTE_TRY(g.partial.alloc((size_t)nblocks * n_class * npairs));
   RTE_TRY(g.out.alloc((size_t)n_class * npairs));
   cross_gram_kernel<<<nblocks, 256, smem, st>>>(X, nxc, Y, nyc, nrow, n_dof, P, wdir, mat, n_class,
-                                                g.partial.p);
+                                                g.partial.p); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   const int n = (int)(n_class * npairs);
-  sum_partials_kernel<<<(n + 255) / 256, 256, 0, st>>>(g.partial.p, nblocks, n, g.out.p);
+  sum_partials_kernel<<<(n + 255) / 256, 256, 0, st>>>(g.partial.p, nblocks, n, g.out.p); RTE_NOTE_LAUNCH();
   out.resize(n);
   RTE_CUDA_TRY(cudaMemcpyAsync(out.data(), g.out.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
   RTE_CUDA_TRY(cudaStreamSynchronize(st));
@@ -415,7 +415,7 @@ static int pod(rte_rom_t rom, const double* X, int ncol, size_t nrow, int rank, 
   RTE_TRY(Wd.alloc(W.size()));
   RTE_CUDA_TRY(cudaMemcpyAsync(Wd.p, W.data(), sizeof(double) * W.size(), cudaMemcpyHostToDevice, st));
   RTE_TRY(rom->U.alloc((size_t)r * nrow));
-  basis_kernel<<<(unsigned)((nrow + 127) / 128), 128, 0, st>>>(X, ncol, Wd.p, r, nrow, rom->U.p);
+  basis_kernel<<<(unsigned)((nrow + 127) / 128), 128, 0, st>>>(X, ncol, Wd.p, r, nrow, rom->U.p); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   // re-orthonormalise: U <- U L^{-T},  L L^T = U^T diag(mult) U
   std::vector<double> G2;
@@ -447,7 +447,7 @@ static int pod(rte_rom_t rom, const double* X, int ncol, size_t nrow, int rank, 
   RTE_TRY(Md.alloc(Minv.size()));
   RTE_TRY(Unew.alloc((size_t)r * nrow));
   RTE_CUDA_TRY(cudaMemcpyAsync(Md.p, Minv.data(), sizeof(double) * Minv.size(), cudaMemcpyHostToDevice, st));
-  basis_kernel<<<(unsigned)((nrow + 127) / 128), 128, 0, st>>>(rom->U.p, r, Md.p, r, nrow, Unew.p);
+  basis_kernel<<<(unsigned)((nrow + 127) / 128), 128, 0, st>>>(rom->U.p, r, Md.p, r, nrow, Unew.p); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   std::swap(rom->U.p, Unew.p);
   std::swap(rom->U.n, Unew.n);
@@ -463,7 +463,7 @@ static int reduce_operators(rte_rom_t rom, cudaStream_t st) {
   RTE_TRY(rom->U_rho.alloc((size_t)r * n));
   RTE_TRY(rom->U_iso.alloc((size_t)r * n));
   rho_iso_kernel<<<(unsigned)(((size_t)r * n + 255) / 256), 256, 0, st>>>(
-      rom->U.p, r, d->n_dirs, n, d->dir_dev.p, rom->U_rho.p, rom->U_iso.p);
+      rom->U.p, r, d->n_dirs, n, d->dir_dev.p, rom->U_rho.p, rom->U_iso.p); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   // multiplicity per direction as the row weight
   std::vector<double> mult(d->n_dirs);
@@ -475,11 +475,11 @@ static int reduce_operators(rte_rom_t rom, cudaStream_t st) {
   if (d->dim == 2) {
     const size_t tot = (size_t)r * d->n_dirs * d->n_cells;
     transport_apply2d_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
-        rom->U.p, r, d->n_dirs, d->nx, d->ny, d->hx, d->hy, d->dir_dev.p, Y.p);
+        rom->U.p, r, d->n_dirs, d->nx, d->ny, d->hx, d->hy, d->dir_dev.p, Y.p); RTE_NOTE_LAUNCH();
   } else {
     const size_t tot = (size_t)r * d->n_dirs * d->nx;
     transport_apply1d_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
-        rom->U.p, r, d->n_dirs, d->nx, d->hx, d->dir_dev.p, Y.p);
+        rom->U.p, r, d->n_dirs, d->nx, d->hx, d->dir_dev.p, Y.p); RTE_NOTE_LAUNCH();
   }
   RTE_CUDA_TRY(cudaGetLastError());
   std::vector<double> A0, Aa, C;
@@ -513,7 +513,7 @@ int rom_prepare(rte_rom_t rom, rte_batch_t bt, cudaStream_t st) {
   }
   rom_assemble_lu_kernel<<<(B + 63) / 64, 64, 0, st>>>(rom->A0_dev.p, rom->Aa_dev.p, rom->As_dev.p,
                                                        r, bt->disc->n_mat, bt->sigma_t.p,
-                                                       bt->sigma_s.p, B, o->lu.p, o->piv.p);
+                                                       bt->sigma_s.p, B, o->lu.p, o->piv.p); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   o->batch = bt;
   return RTE_OK;
@@ -525,10 +525,10 @@ int rom_correction(rte_rom_t rom, rte_batch_t bt, const double* R, double* drho,
   if (!o || o->batch != bt) RTE_TRY(rom_prepare(rom, bt, st));
   o = rom->online;
   const int r = rom->r, n = bt->disc->n_dof, B = bt->B;
-  project_kernel<<<dim3(r, B), 256, 0, st>>>(rom->U_iso.p, n, R, 1, 0, (size_t)n, o->proj.p, r, active);
-  lu_solve_kernel<<<(B + 63) / 64, 64, 0, st>>>(o->lu.p, o->piv.p, o->proj.p, r, B, active);
+  project_kernel<<<dim3(r, B), 256, 0, st>>>(rom->U_iso.p, n, R, 1, 0, (size_t)n, o->proj.p, r, active); RTE_NOTE_LAUNCH();
+  lu_solve_kernel<<<(B + 63) / 64, 64, 0, st>>>(o->lu.p, o->piv.p, o->proj.p, r, B, active); RTE_NOTE_LAUNCH();
   lift_kernel<<<dim3(std::min((n + 255) / 256, 1024), B), 256, 0, st>>>(rom->U_rho.p, n, o->proj.p, r,
-                                                                        drho, active);
+                                                                        drho, active); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;
 }
@@ -572,7 +572,7 @@ extern "C" int rte_rom_build(rte_batch_t train, const rte_rom_opts* opts, rte_ro
   RTE_TRY(dF.alloc((size_t)ndc * nrow));
   RTE_TRY(pairs_d.alloc(pairs.size()));
   RTE_CUDA_TRY(cudaMemcpyAsync(pairs_d.p, pairs.data(), sizeof(int) * pairs.size(), cudaMemcpyHostToDevice, st));
-  diff_kernel<<<dim3(1024, ndc), 256, 0, st>>>(psi_cur.p, psi_win.p, pairs_d.p, ndc, nrow, B, dF.p);
+  diff_kernel<<<dim3(1024, ndc), 256, 0, st>>>(psi_cur.p, psi_win.p, pairs_d.p, ndc, nrow, B, dF.p); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   std::vector<double> mult(d->n_dirs);
   for (int k = 0; k < d->n_dirs; ++k) mult[k] = d->dirs[k].mult;
@@ -653,10 +653,10 @@ extern "C" int rte_rom_initial_guess(rte_rom_t rom, rte_batch_t b, double* rho0,
   }
   RomOnline* o = rom->online;
   project_kernel<<<dim3(r, B), 256, 0, st>>>(Ut0.p, b->disc->n_cells, b->G0.p, 1, 0,
-                                             (size_t)b->disc->n_cells, o->proj.p, r, active);
-  lu_solve_kernel<<<(B + 63) / 64, 64, 0, st>>>(o->lu.p, o->piv.p, o->proj.p, r, B, active);
+                                             (size_t)b->disc->n_cells, o->proj.p, r, active); RTE_NOTE_LAUNCH();
+  lu_solve_kernel<<<(B + 63) / 64, 64, 0, st>>>(o->lu.p, o->piv.p, o->proj.p, r, B, active); RTE_NOTE_LAUNCH();
   lift_kernel<<<dim3(std::min((n + 255) / 256, 1024), B), 256, 0, st>>>(rom->U_rho.p, n, o->proj.p, r,
-                                                                        rho0, active);
+                                                                        rho0, active); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   RTE_CUDA_TRY(cudaStreamSynchronize(st));
   return RTE_OK;

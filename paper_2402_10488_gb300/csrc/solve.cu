@@ -40,7 +40,9 @@ int run_si(rte_batch_t bt, const rte_solve_opts* o, rte_rom_t rom_c, double* rho
   for (int l = 1; l <= o->max_iter; ++l) {
     RTE_CUDA_TRY(cudaMemcpyAsync(act_dev.p, act.data(), B, cudaMemcpyHostToDevice, st));
     double* psi = psi_cur;
-    RTE_TRY(sweep_launch(bt, rho_prev, rho_star, psi, 1, act_dev.p, st, true));
+    int n_act = 0;
+    for (int b = 0; b < B; ++b) n_act += act[b] != 0;
+    RTE_TRY(sweep_launch(bt, rho_prev, rho_star, psi, 1, act_dev.p, st, true, n_act));
     if (psi_win && l <= window)
       for (int b = 0; b < B; ++b)
         if (act[b])

@@ -404,12 +404,13 @@ int setup_tables(rte_batch_t bt, cudaStream_t st) {
   const rte_disc_s* d = bt->disc;
   const int n = bt->B * d->n_mat * d->n_dirs;
   const int th = 128, bl = (n + th - 1) / th;
-  if (d->dim == 2)
+  if (d->dim == 2) {
     tables2d_kernel<<<bl, th, 0, st>>>(bt->tables.p, bt->sigma_t.p, d->dir_dev.p, bt->B, d->n_mat,
-                                       d->n_dirs, d->hx, d->hy);
-  else
+                                       d->n_dirs, d->hx, d->hy); RTE_NOTE_LAUNCH();
+  } else {
     tables1d_kernel<<<bl, th, 0, st>>>(bt->tables.p, bt->sigma_t.p, d->dir_dev.p, bt->B, d->n_mat,
-                                       d->n_dirs, d->hx);
+                                       d->n_dirs, d->hx); RTE_NOTE_LAUNCH();
+  }
   RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;
 }
@@ -421,23 +422,31 @@ static int launch2d(const Sweep2DArgs& A, int B, int n_groups, cudaStream_t st) 
   const size_t sbytes = (size_t)A.n_mat * sizeof(double);
   dim3 grid(n_groups, B);
   if (ybytes + tbytes + sbytes <= 48 * 1024) {
-    sweep2d_kernel<DPW, true><<<grid, 32, ybytes + tbytes + sbytes, st>>>(A);
+    sweep2d_kernel<DPW, true><<<grid, 32, ybytes + tbytes + sbytes, st>>>(A); RTE_NOTE_LAUNCH();
   } else {
     const size_t bytes = ybytes + sbytes;
     if (bytes > 200 * 1024) return fail(RTE_EINVAL, "sweep: mesh row too long for shared memory");
     if (bytes > 48 * 1024)
       RTE_CUDA_TRY(cudaFuncSetAttribute(sweep2d_kernel<DPW, false>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-    sweep2d_kernel<DPW, false><<<grid, 32, bytes, st>>>(A);
+    sweep2d_kernel<DPW, false><<<grid, 32, bytes, st>>>(A); RTE_NOTE_LAUNCH();
   }
   RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;
 }
 
 int sweep_launch(rte_batch_t bt, const double* rho_in, double* rho_out, double* psi_out,
-                 int with_source, const uint8_t* active, cudaStream_t st, bool fuse_norms) {
+                 int with_source, const uint8_t* active, cudaStream_t st, bool fuse_norms,
+                 int n_active) {
+  if (n_active < 0) n_active = bt->B;
   const rte_disc_s* d = bt->disc;
   const int n_groups = (int)bt->groups.size();
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (bt->timing) {
+    RTE_CUDA_TRY(cudaEventCreate(&ev0));
+    RTE_CUDA_TRY(cudaEventCreate(&ev1));
+    RTE_CUDA_TRY(cudaEventRecord(ev0, st));
+  }
   if (d->dim == 2) {
     Sweep2DArgs A{rho_in,       bt->partial.p, psi_out,        active,      bt->tables.p,
                   bt->sigma_s.p, bt->G0.p,     bt->inflow.p,   d->mat_id.p, d->dir_dev.p,
@@ -455,15 +464,21 @@ int sweep_launch(rte_batch_t bt, const double* rho_in, double* rho_out, double* 
                   bt->G0.p,    bt->inflow.p,  d->mat_id.p, d->dir_dev.p, bt->B, d->nx,
                   d->n_dof,    d->n_mat,      d->n_dirs, with_source, std::sqrt(d->hx)};
     const int n = bt->B * d->n_dirs;
-    sweep1d_kernel<<<(n + 63) / 64, 64, 0, st>>>(A);
+    sweep1d_kernel<<<(n + 63) / 64, 64, 0, st>>>(A); RTE_NOTE_LAUNCH();
     RTE_CUDA_TRY(cudaGetLastError());
+  }
+  if (bt->timing) {
+    RTE_CUDA_TRY(cudaEventRecord(ev1, st));
+    bt->sweep_ev.emplace_back(ev0, ev1);
+    bt->sweep_launches += 1;
+    bt->sweep_units += (double)n_active * d->n_cells * d->n_dirs;
   }
   if (fuse_norms) RTE_CUDA_TRY(cudaMemsetAsync(bt->norms.p, 0, sizeof(unsigned long long) * 2 * bt->B, st));
   const int th = 256;
   dim3 grid((d->n_dof / 2 + th - 1) / th, bt->B);
   reduce_partials_kernel<<<grid, th, 0, st>>>(bt->partial.p, rho_in, rho_out,
                                              fuse_norms ? bt->norms.p : nullptr, active, n_groups,
-                                             d->n_dof);
+                                             d->n_dof); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;
 }
@@ -487,7 +502,7 @@ int correction_source_launch(rte_batch_t bt, const double* rs, const double* rp,
   const rte_disc_s* d = bt->disc;
   dim3 grid(std::min((d->n_dof + 255) / 256, 1024), bt->B);
   correction_source_kernel<<<grid, 256, 0, st>>>(rs, rp, R, bt->sigma_s.p, d->mat_id.p, active,
-                                                 d->n_dof, d->P, d->n_mat);
+                                                 d->n_dof, d->P, d->n_mat); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;
 }
@@ -496,7 +511,7 @@ int axpy_launch(rte_batch_t bt, const double* x, const double* y, double* out,
                 const uint8_t* active, cudaStream_t st) {
   const rte_disc_s* d = bt->disc;
   dim3 grid(std::min((d->n_dof + 255) / 256, 1024), bt->B);
-  add_kernel<<<grid, 256, 0, st>>>(x, y, out, active, d->n_dof);
+  add_kernel<<<grid, 256, 0, st>>>(x, y, out, active, d->n_dof); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;
 }
@@ -514,7 +529,7 @@ extern "C" int rte_sweep(rte_batch_t b, const double* rho_in, double* rho_out, d
     return fail(RTE_EINVAL, "rte_sweep: arrays must be 16-byte aligned");
   DeviceGuard g(b->disc->device);
   return sweep_launch(b, rho_in, rho_out, psi_out, with_source, active, (cudaStream_t)stream,
-                      false);
+                      false, -1);
 }
 
 extern "C" int rte_change_norm(rte_batch_t b, const double* rho_star, const double* rho_prev,
@@ -524,8 +539,8 @@ extern "C" int rte_change_norm(rte_batch_t b, const double* rho_star, const doub
   cudaStream_t st = (cudaStream_t)stream;
   RTE_CUDA_TRY(cudaMemsetAsync(b->norms.p, 0, sizeof(unsigned long long) * 2 * b->B, st));
   dim3 grid(std::min((b->disc->n_dof + 255) / 256, 256), b->B);
-  change_norm_kernel<<<grid, 256, 0, st>>>(rho_star, rho_prev, b->norms.p, b->disc->n_dof);
-  bits_to_double_kernel<<<(2 * b->B + 127) / 128, 128, 0, st>>>(b->norms.p, norms, 2 * b->B);
+  change_norm_kernel<<<grid, 256, 0, st>>>(rho_star, rho_prev, b->norms.p, b->disc->n_dof); RTE_NOTE_LAUNCH();
+  bits_to_double_kernel<<<(2 * b->B + 127) / 128, 128, 0, st>>>(b->norms.p, norms, 2 * b->B); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;
 }

@@ -26,6 +26,8 @@ _D = ctypes.c_double
 SIGNATURES = {
     "rte_version": (_I, []),
     "rte_last_error": (ctypes.c_char_p, []),
+    "rte_counters": (_I, [_P]),
+    "rte_batch_timing": (_I, [_P, _I, _P]),
     "rte_disc_create": (_I, [_P, _I, _P]),
     "rte_disc_destroy": (_I, [_P]),
     "rte_disc_info": (_I, [_P, _P]),
@@ -45,6 +47,13 @@ SIGNATURES = {
     "rte_romsa_correction": (_I, [_P, _P, _P, _P, _P, _P]),
     "rte_solve": (_I, [_P, _P, _P, _P, _P, _P, _P]),
 }
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process so far."""
+    out = np.zeros(1, np.int64)
+    check(lib().rte_counters(out.ctypes.data_as(_P)))
+    return int(out[0])
 
 
 class RTEError(RuntimeError):
@@ -180,6 +189,12 @@ class Batch:
         inf = _host(problem.inflow)
         check(lib().rte_batch_set_params(self.h, st.ctypes.data_as(_P), ss.ctypes.data_as(_P),
                                          src.ctypes.data_as(_P), inf.ctypes.data_as(_P)))
+
+    def timing(self, enable):
+        """enable=1 reset+start, 0 reset+stop, -1 read; returns (sweep_ms, launches, units)."""
+        out = np.zeros(3)
+        check(lib().rte_batch_timing(self.h, int(enable), out.ctypes.data_as(_P)))
+        return float(out[0]), int(out[1]), float(out[2])
 
     def directions(self):
         d = np.zeros((self.disc.n_dirs, 4))
