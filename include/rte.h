@@ -131,6 +131,24 @@ int rte_batch_set_params(rte_batch_t batch, const double* sigma_t, const double*
 int rte_sweep(rte_batch_t batch, const double* rho_in, double* rho_out, double* psi_out,
               int with_source, const uint8_t* active, void* stream);
 
+/* Allocation-free variant of rte_sweep (the paper has no counterpart: this is a library service).
+ * For callers that cannot allocate device memory while they run (for example under a host
+ * framework whose caching allocator has reserved the device's memory, or inside a latency-bound
+ * service loop where an allocation, which may synchronise the device, is not allowed).  Computes
+ * exactly what rte_sweep computes for every instance (no active mask, no psi output), but keeps
+ * the partial scalar-flux sums in one fixed 16 MiB device array that belongs to the library image
+ * instead of memory owned by the batch; the call itself allocates nothing.
+ *   rho_in, rho_out  DEVICE double[B][n_dof], 16-byte aligned, not aliased
+ * Limit: B * (number of sweep work groups) * n_dof <= 2^21 doubles, else RTE_EINVAL (e.g. at most
+ * 4 instances of a 128x128 CL(16,4) batch; any 1D slab batch of moderate size).
+ * Every GPU that loads the library holds the 16 MiB array until the process exits.  The first
+ * call on a device looks up the array's device address (once per device); make that first call
+ * before capturing streams.  All calls share the one array: calls that overlap on the GPU (on
+ * different streams, or from different threads) race and give wrong results; serialise them.
+ * Asynchronous on `stream`.  Errors: RTE_EINVAL, RTE_ESTATE, RTE_ECUDA. */
+int rte_sweep_static(rte_batch_t batch, const double* rho_in, double* rho_out, int with_source,
+                     void* stream);
+
 /* Sweep-kernel timing for throughput and roofline accounting.  Each 2D/1D sweep kernel launched
  * for this batch while timing is on is bracketed by CUDA events recorded on the stream it is
  * launched on.  out (HOST double[3], may be NULL) receives (total sweep-kernel milliseconds,

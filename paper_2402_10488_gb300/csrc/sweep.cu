@@ -552,3 +552,42 @@ extern "C" int rte_correction_source(rte_batch_t b, const double* rho_star, cons
   DeviceGuard g(b->disc->device);
   return correction_source_launch(b, rho_star, rho_prev, R, nullptr, (cudaStream_t)stream);
 }
+
+namespace rte {
+
+// Same launches as sweep_launch (sweep kernel, then the fixed-order partial-sum reduction) with
+// the partial sums placed in caller-provided device memory; no timing and no norms.  Used by the
+// allocation-free entry point in noalloc.cu.
+int sweep_launch_with_scratch(rte_batch_t bt, const double* rho_in, double* rho_out,
+                              int with_source, cudaStream_t st, double* partial) {
+  const rte_disc_s* d = bt->disc;
+  const int n_groups = (int)bt->groups.size();
+  if (d->dim == 2) {
+    Sweep2DArgs A{rho_in,       partial,       nullptr,        nullptr,     bt->tables.p,
+                  bt->sigma_s.p, bt->G0.p,     bt->inflow.p,   d->mat_id.p, d->dir_dev.p,
+                  bt->groups_dev.p, d->nx,     d->ny,          d->n_cells,  d->n_dof,
+                  d->n_mat,     d->n_dirs,     n_groups,       with_source, std::sqrt(d->hx * d->hy)};
+    switch (bt->dpw) {
+      case 1: RTE_TRY(launch2d<1>(A, bt->B, n_groups, st)); break;
+      case 2: RTE_TRY(launch2d<2>(A, bt->B, n_groups, st)); break;
+      case 4: RTE_TRY(launch2d<4>(A, bt->B, n_groups, st)); break;
+      case 8: RTE_TRY(launch2d<8>(A, bt->B, n_groups, st)); break;
+      default: return fail(RTE_EINVAL, "unsupported directions-per-warp");
+    }
+  } else {
+    Sweep1DArgs A{rho_in,      partial,       nullptr,  nullptr, bt->tables.p, bt->sigma_s.p,
+                  bt->G0.p,    bt->inflow.p,  d->mat_id.p, d->dir_dev.p, bt->B, d->nx,
+                  d->n_dof,    d->n_mat,      d->n_dirs, with_source, std::sqrt(d->hx)};
+    const int n = bt->B * d->n_dirs;
+    sweep1d_kernel<<<(n + 63) / 64, 64, 0, st>>>(A); RTE_NOTE_LAUNCH();
+    RTE_CUDA_TRY(cudaGetLastError());
+  }
+  const int th = 256;
+  dim3 grid((d->n_dof / 2 + th - 1) / th, bt->B);
+  reduce_partials_kernel<<<grid, th, 0, st>>>(partial, rho_in, rho_out, nullptr, nullptr, n_groups,
+                                             d->n_dof); RTE_NOTE_LAUNCH();
+  RTE_CUDA_TRY(cudaGetLastError());
+  return RTE_OK;
+}
+
+}  // namespace rte

@@ -37,6 +37,7 @@ SIGNATURES = {
     "rte_batch_set_params": (_I, [_P, _P, _P, _P, _P]),
     "rte_batch_directions": (_I, [_P, _P]),
     "rte_sweep": (_I, [_P, _P, _P, _P, _I, _P, _P]),
+    "rte_sweep_static": (_I, [_P, _P, _P, _I, _P]),
     "rte_change_norm": (_I, [_P, _P, _P, _P, _P]),
     "rte_dsa_correction": (_I, [_P, _P, _P, _D, _I, _P, _P, _P]),
     "rte_correction_source": (_I, [_P, _P, _P, _P, _P]),
@@ -204,6 +205,11 @@ class Batch:
     def sweep(self, rho_in, rho_out, psi_out=None, with_source=True, active=None, stream=None):
         check(lib().rte_sweep(self.h, _ptr(rho_in), _ptr(rho_out), _ptr(psi_out),
                               1 if with_source else 0, _ptr(active), _stream(stream)))
+
+    def sweep_static(self, rho_in, rho_out, with_source=True, stream=None):
+        """rte_sweep_static: the same sweep with the library's fixed scratch (no allocation)."""
+        check(lib().rte_sweep_static(self.h, _ptr(rho_in), _ptr(rho_out), 1 if with_source else 0,
+                                     _stream(stream)))
 
     def change_norm(self, rho_star, rho_prev, norms, stream=None):
         check(lib().rte_change_norm(self.h, _ptr(rho_star), _ptr(rho_prev), _ptr(norms),
