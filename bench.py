@@ -55,7 +55,9 @@ def parse():
     ap.add_argument("--ntrain", type=int, default=32)
     ap.add_argument("--rank", type=int, default=20)
     ap.add_argument("--eps", type=float, default=2e-7, help="relative stop tolerance")
-    ap.add_argument("--dsa-rtol", type=float, default=0.1)
+    ap.add_argument("--dsa-rtol", type=float, default=0.0, help="0: fixed V-cycles")
+    ap.add_argument("--dsa-vcycles", type=int, default=2)
+    ap.add_argument("--dpw", type=int, default=0, help="sweep directions per warp (0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--methods", default="romsad,si_dsa,romig")
     ap.add_argument("--profile-window", action="store_true",
@@ -177,6 +179,7 @@ def run_ours(a, ws, rank, local):
     eps_train = 1e-12
     eps_romsad = 0.1 * max(eps_train, rom_c.eps_pod)
     batch = rte.Batch(disc, B)
+    batch.tune(a.dpw)
     batch.set_params(test)
     n_dof = disc.n_dof
     # tightly converged references (untimed)
@@ -197,7 +200,7 @@ def run_ours(a, ws, rank, local):
         else:
             sa, kw = rte.SA_DSA, {}
         rep, _, st = batch.solve(rho, a.eps, sa=sa, rel=True, max_iter=400, dsa_rtol=a.dsa_rtol,
-                                 dsa_max_it=100, **kw)
+                                 dsa_max_it=a.dsa_vcycles if a.dsa_rtol == 0 else 100, **kw)
         if host_out is not None:
             host_out.copy_(rho, non_blocking=True)
         return rep
@@ -285,7 +288,9 @@ def run_ours(a, ws, rank, local):
                    "angles": a.angles, "distinct_directions": disc.n_dirs, "global_batch": B * ws,
                    "n_train": a.ntrain, "rank": a.rank, "window": 3, "theta": 5,
                    "eps_romsad": eps_romsad, "stop": f"relative change < {a.eps:g}",
-                   "dsa_rtol": a.dsa_rtol, "error_target": 1e-6,
+                   "dsa": (f"{a.dsa_vcycles} FP32 multigrid V-cycles" if a.dsa_rtol == 0 else
+                           f"FGMRES rtol {a.dsa_rtol}"), "error_target": 1e-6,
+                   "dirs_per_warp": a.dpw or "auto",
                    "l2": "256 MB buffer written between timed steps",
                    "parallelism": "instances sharded across ranks, no collective"},
         "roofline": {"bound": "alu", "kernel": "sweep2d_kernel (FP64 DFMA)", "achieved": achieved,

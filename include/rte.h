@@ -131,6 +131,13 @@ int rte_batch_set_params(rte_batch_t batch, const double* sigma_t, const double*
 int rte_sweep(rte_batch_t batch, const double* rho_in, double* rho_out, double* psi_out,
               int with_source, const uint8_t* active, void* stream);
 
+/* Work decomposition of the 2D sweep: dirs_per_warp in {1, 2, 4, 8} sets how many directions of
+ * one quadrant a warp sweeps together (more directions: more instruction-level parallelism and
+ * fewer partial sums; fewer: more warps in flight).  0 picks automatically the largest value that
+ * still gives at least four resident warps per SM for this batch size.  Set before sweeping.
+ * Errors: RTE_EINVAL. */
+int rte_batch_tune(rte_batch_t batch, int dirs_per_warp);
+
 /* Allocation-free variant of rte_sweep (the paper has no counterpart: this is a library service).
  * For callers that cannot allocate device memory while they run (for example under a host
  * framework whose caching allocator has reserved the device's memory, or inside a latency-bound
@@ -140,7 +147,8 @@ int rte_sweep(rte_batch_t batch, const double* rho_in, double* rho_out, double* 
  * instead of memory owned by the batch; the call itself allocates nothing.
  *   rho_in, rho_out  DEVICE double[B][n_dof], 16-byte aligned, not aliased
  * Limit: B * (number of sweep work groups) * n_dof <= 2^21 doubles, else RTE_EINVAL (e.g. at most
- * 4 instances of a 128x128 CL(16,4) batch; any 1D slab batch of moderate size).
+ * 4 instances of a 128x128 CL(16,4) batch swept with 4 directions per warp, see
+ * rte_batch_tune; any 1D slab batch of moderate size).
  * Every GPU that loads the library holds the 16 MiB array until the process exits.  The first
  * call on a device looks up the array's device address (once per device); make that first call
  * before capturing streams.  All calls share the one array: calls that overlap on the GPU (on
@@ -169,8 +177,12 @@ int rte_change_norm(rte_batch_t batch, const double* rho_star, const double* rho
 /* Consistent DSA correction (App. B; 2D by the same P1-ansatz moment derivation):
  * solves the diffusion system for delta rho given R = Sigma_s (rho^(l,*) - rho^(l-1)).
  *   R      DEVICE double[B][n_dof];  drho  DEVICE double[B][n_dof]
- *   rtol   relative residual tolerance of the iterative solve (2D); 1D is a direct solve
- *   max_it iteration cap (2D); iters (HOST int[B], may be NULL) receives iterations used
+ *   rtol   2D: > 0 -- flexible GMRES on the FP64 system, preconditioned by one FP32 multigrid
+ *          V-cycle per iteration, to this relative residual; == 0 -- exactly max_it FP32
+ *          multigrid V-cycles x <- x + V(b - A x) with no host round trip (an approximate DSA:
+ *          the SI fixed point does not depend on it).  1D is always a direct solve.
+ *   max_it iteration cap (rtol > 0) or number of V-cycles (rtol == 0); iters (HOST int[B], may
+ *          be NULL) receives iterations used
  *   active DEVICE uint8[B] or NULL
  * Synchronises `stream` (the 2D Krylov solve reads residual norms on the host).
  * Errors: RTE_ENOCONV if max_it was reached for some instance (drho still written). */
@@ -232,8 +244,8 @@ typedef struct {
   int sa;              /* RTE_SA_*                                                           */
   int theta;           /* ROMSAD: ROMSA allowed after iterations 1..theta (Alg. 2)           */
   double eps_romsad;   /* ROMSAD threshold on the absolute change (Eq. (romsad_parameters)) */
-  double dsa_rtol;     /* DSA iterative solve tolerance (2D)                                 */
-  int dsa_max_it;      /* DSA iteration cap (2D)                                             */
+  double dsa_rtol;     /* 2D DSA: Krylov tolerance (> 0) or 0 for dsa_max_it V-cycles          */
+  int dsa_max_it;      /* 2D DSA: iteration cap, or the number of V-cycles when dsa_rtol == 0  */
   const uint8_t* schedule; /* HOST uint8[max_iter] or NULL: forces ROMSAD's choice per
                               iteration (1 = ROMSA, 0 = DSA), for reproducibility tests      */
 } rte_solve_opts;

@@ -228,6 +228,63 @@ extern "C" int rte_disc_quadrature(rte_disc_t disc, double* v, double* omega) {
 
 // ---- batches ------------------------------------------------------------------------------
 
+namespace rte {
+// sweep work groups: per quadrant, consecutive runs of <= dpw directions
+void make_groups(rte_batch_t b) {
+  const rte_disc_s* disc = b->disc;
+  b->groups.clear();
+  int d = 0;
+  while (d < disc->n_dirs) {
+    const int q = disc->dirs[d].quad;
+    int e = d;
+    while (e < disc->n_dirs && disc->dirs[e].quad == q && e - d < b->dpw) ++e;
+    b->groups.push_back(SweepGroup{d, e - d, q, 0});
+    d = e;
+  }
+}
+
+// largest directions-per-warp giving >= 4 resident warps per SM (each SM sub-partition has its
+// own FP64 unit, so one warp per sub-partition is the minimum to use the SM's FP64 rate)
+int auto_dpw(const rte_disc_s* disc, int B) {
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, disc->device) != cudaSuccess || sms < 1)
+    sms = 148;
+  int per_quad[4] = {0, 0, 0, 0};
+  for (const auto& d : disc->dirs) per_quad[d.quad]++;
+  for (int dpw : {8, 4, 2}) {
+    long long warps = 0;
+    for (int q = 0; q < 4; ++q) warps += (long long)B * ((per_quad[q] + dpw - 1) / dpw);
+    if (warps >= 4LL * sms) return dpw;
+  }
+  return 1;
+}
+}  // namespace rte
+
+extern "C" int rte_batch_tune(rte_batch_t b, int dpw) {
+  if (!b) return fail(RTE_EINVAL, "rte_batch_tune: null argument");
+  if (b->disc->dim == 1) return RTE_OK;
+  if (dpw == 0) dpw = auto_dpw(b->disc, b->B);
+  if (dpw != 1 && dpw != 2 && dpw != 4 && dpw != 8) return fail(RTE_EINVAL, "dirs_per_warp must be 0, 1, 2, 4 or 8");
+  DeviceGuard g(b->disc->device);
+  const int old = b->dpw;
+  b->dpw = dpw;
+  make_groups(b);
+  const size_t need = (size_t)b->B * b->groups.size() * b->disc->n_dof;
+  if (need > b->partial.n) {
+    int st = b->partial.alloc(need);
+    if (st != RTE_OK) {
+      b->dpw = old;
+      make_groups(b);
+      b->partial.alloc((size_t)b->B * b->groups.size() * b->disc->n_dof);
+      return st;
+    }
+  }
+  RTE_TRY(b->groups_dev.alloc(b->groups.size()));
+  RTE_CUDA_TRY(cudaMemcpy(b->groups_dev.p, b->groups.data(), sizeof(SweepGroup) * b->groups.size(),
+                          cudaMemcpyHostToDevice));
+  return RTE_OK;
+}
+
 rte_batch_s::~rte_batch_s() {
   rte::dsa_state_free(dsa);
   for (auto& e : sweep_ev) {
@@ -277,18 +334,8 @@ extern "C" int rte_batch_create(rte_disc_t disc, int B, rte_batch_t* out) {
   auto* b = new rte_batch_s();
   b->disc = disc;
   b->B = B;
-  // sweep work groups: per quadrant, consecutive runs of <= dpw directions
-  b->dpw = disc->dim == 1 ? 1 : 4;
-  {
-    int d = 0;
-    while (d < disc->n_dirs) {
-      int q = disc->dirs[d].quad;
-      int e = d;
-      while (e < disc->n_dirs && disc->dirs[e].quad == q && e - d < b->dpw) ++e;
-      b->groups.push_back(SweepGroup{d, e - d, q, 0});
-      d = e;
-    }
-  }
+  b->dpw = disc->dim == 1 ? 1 : auto_dpw(disc, B);
+  make_groups(b);
   const size_t nb = (size_t)B;
   const size_t tab = disc->dim == 1 ? kTab1D : kTab2D;
   int st = RTE_OK;

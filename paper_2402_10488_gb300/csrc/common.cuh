@@ -146,6 +146,8 @@ struct rte_batch_s {
 };
 
 namespace rte {
+void make_groups(rte_batch_t b);
+int auto_dpw(const rte_disc_s* disc, int B);
 // sweep.cu
 int sweep_launch(rte_batch_t b, const double* rho_in, double* rho_out, double* psi_out,
                  int with_source, const uint8_t* active, cudaStream_t st, bool fuse_norms,

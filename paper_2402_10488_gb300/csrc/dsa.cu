@@ -131,19 +131,29 @@ __device__ __forceinline__ void inv12(T* a /*[12][24] scratch*/) {
   }
 }
 
-// Level geometry and data (device pointers), one instance stride per array.
+// ---- multigrid levels ----------------------------------------------------------------------------
+//
+// The Galerkin coarse operator P^T A P of this DG moment system is the same system on the coarse
+// mesh: coarse Q^1 functions are continuous inside a coarse cell, so every term on an interior
+// fine face (jumps, averages times jumps) vanishes, and the volume and coarse-face terms are those
+// of the coarse mesh.  Only the cross-section terms change: Sigma becomes the projected mass
+// matrix sum_children P_c^T (sigma_c I) P_c, a 4x4 block per field and coarse cell.  So every
+// level has four constant 12x12 neighbour blocks (set by its cell size) and a per-cell 12x12
+// diagonal block = constant geometric part + projected mass blocks; level 0 keeps one diagonal
+// block per material.
+
 struct Lvl {
   int nx, ny, nc;
-  const float* blk;   // [B][nc][5][144] (levels >= 1)
-  const float* dinv;  // [B][nc][144]    (levels >= 1)
+  const float* off;    // [4][144]: W, E, S, N blocks of this level (constant)
+  const float* diag;   // level 0: [B][n_mat][144]; coarser: [B][nc][144]
+  const float* dinv;   // same layout as diag
+  const int32_t* mat;  // level 0: material map; coarser: nullptr
+  int n_mat;
 };
 
-struct Fine {
-  const double* off64;   // [4][144] W, E, S, N (constant)
-  const float* off32;
+struct Fine {  // level 0 in FP64, for the Krylov operator
+  const double* off64;   // [4][144]
   const double* diag64;  // [B][n_mat][144]
-  const float* diag32;
-  const float* dinv32;   // [B][n_mat][144]
   const int32_t* mat;
   int n_mat;
 };
@@ -159,7 +169,11 @@ __device__ __forceinline__ bool nbr(int d, int i, int j, int nx, int ny, int& c2
   return true;
 }
 
-// y = A0 x in FP64 on the fine level (structured).  One thread per (cell, row-of-block).
+__device__ __forceinline__ const float* cell_block(const float* base, const Lvl& L, int b, int c) {
+  return L.mat ? base + ((size_t)b * L.n_mat + L.mat[c]) * NB2 : base + ((size_t)b * L.nc + c) * NB2;
+}
+
+// y = A0 x in FP64 on the finest level.  One thread per (cell, row of its block).
 __global__ void fine_apply64_kernel(Fine F, int nx, int ny, int B, const double* __restrict__ x,
                                     double* __restrict__ y, const uint8_t* active) {
   const int b = blockIdx.y;
@@ -184,75 +198,96 @@ __global__ void fine_apply64_kernel(Fine F, int nx, int ny, int B, const double*
   y[(size_t)b * nc * NB + t] = acc;
 }
 
-// Block row of level operator times a vector, excluding (self=false) or including the diagonal.
-template <bool STRUCT>
-__device__ __forceinline__ void block_row(const Fine& F, const Lvl& L, int b, int c, int i, int j,
-                                          const float* __restrict__ x, bool with_self,
-                                          float acc[NB]) {
-  for (int d = with_self ? 0 : 1; d <= 4; ++d) {
-    int c2 = c;
-    if (d > 0 && !nbr(d, i, j, L.nx, L.ny, c2)) continue;
-    const float* A;
-    if (STRUCT)
-      A = d == 0 ? F.diag32 + ((size_t)b * F.n_mat + F.mat[c]) * NB2 : F.off32 + (d - 1) * NB2;
-    else
-      A = L.blk + (((size_t)b * L.nc + c) * 5 + d) * NB2;
-    const float* xv = x + (size_t)c2 * NB;
+// acc += sum over existing neighbours of O_d x_neighbour (O in shared memory)
+__device__ __forceinline__ void nbr_sum(const float* __restrict__ off_s, const float* __restrict__ x,
+                                        int i, int j, int nx, int ny, float acc[NB]) {
+  for (int d = 1; d <= 4; ++d) {
+    int c2;
+    if (!nbr(d, i, j, nx, ny, c2)) continue;
+    const float* O = off_s + (d - 1) * NB2;
     float xl[NB];
+    const float4* xv = reinterpret_cast<const float4*>(x + (size_t)c2 * NB);
 #pragma unroll
-    for (int k = 0; k < NB; ++k) xl[k] = xv[k];
+    for (int q = 0; q < 3; ++q) {
+      const float4 v = xv[q];
+      xl[4 * q] = v.x, xl[4 * q + 1] = v.y, xl[4 * q + 2] = v.z, xl[4 * q + 3] = v.w;
+    }
 #pragma unroll
     for (int r = 0; r < NB; ++r) {
-      float s = 0.f;
+      float sacc = 0.f;
 #pragma unroll
-      for (int k = 0; k < NB; ++k) s = fmaf(A[r * NB + k], xl[k], s);
-      acc[r] += s;
+      for (int k = 0; k < NB; ++k) sacc = fmaf(O[r * NB + k], xl[k], sacc);
+      acc[r] += sacc;
     }
   }
 }
 
-// Red-black block Gauss-Seidel half sweep: cells of `color` get x_c = D_c^{-1}(b_c - sum_n A_cn x_n).
-template <bool STRUCT>
-__global__ void rbgs_kernel(Fine F, Lvl L, int B, int color, const float* __restrict__ bvec,
-                            float* x, const uint8_t* active) {
+// Red-black block Gauss-Seidel half sweep on the cells with (i + j) % 2 == color:
+// x_c = D_c^{-1} (b_c - sum_n O_n x_n).  Threads map onto the cells of that colour only.
+__global__ void rbgs_kernel(Lvl L, int color, const float* __restrict__ bvec, float* x,
+                            const uint8_t* active) {
+  __shared__ float off_s[4 * NB2];
+  for (int e = threadIdx.x; e < 4 * NB2; e += blockDim.x) off_s[e] = L.off[e];
+  __syncthreads();
   const int b = blockIdx.y;
   if (active && !active[b]) return;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= L.nc) return;
-  const int i = c % L.nx, j = c / L.nx;
-  if (((i + j) & 1) != color) return;
+  const int hx2 = (L.nx + 1) / 2;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= hx2 * L.ny) return;
+  const int j = idx / hx2;
+  const int i = 2 * (idx % hx2) + ((j + color) & 1);
+  if (i >= L.nx) return;
+  const int c = j * L.nx + i;
   float* xb = x + (size_t)b * L.nc * NB;
-  const float* bb = bvec + (size_t)b * L.nc * NB;
   float acc[NB];
 #pragma unroll
   for (int r = 0; r < NB; ++r) acc[r] = 0.f;
-  block_row<STRUCT>(F, L, b, c, i, j, xb, false, acc);
+  nbr_sum(off_s, xb, i, j, L.nx, L.ny, acc);
+  const float* bb = bvec + ((size_t)b * L.nc + c) * NB;
   float res[NB];
 #pragma unroll
-  for (int r = 0; r < NB; ++r) res[r] = bb[(size_t)c * NB + r] - acc[r];
-  const float* Di = STRUCT ? F.dinv32 + ((size_t)b * F.n_mat + F.mat[c]) * NB2
-                           : L.dinv + ((size_t)b * L.nc + c) * NB2;
+  for (int r = 0; r < NB; ++r) res[r] = bb[r] - acc[r];
+  const float* Di = cell_block(L.dinv, L, b, c);
+  float out[NB];
 #pragma unroll
   for (int r = 0; r < NB; ++r) {
-    float s = 0.f;
+    float sacc = 0.f;
 #pragma unroll
-    for (int k = 0; k < NB; ++k) s = fmaf(Di[r * NB + k], res[k], s);
-    xb[(size_t)c * NB + r] = s;
+    for (int k = 0; k < NB; ++k) sacc = fmaf(Di[r * NB + k], res[k], sacc);
+    out[r] = sacc;
   }
+  float4* xo = reinterpret_cast<float4*>(xb + (size_t)c * NB);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) xo[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
 }
 
-template <bool STRUCT>
-__global__ void residual_kernel(Fine F, Lvl L, int B, const float* __restrict__ bvec,
-                                const float* __restrict__ x, float* r, const uint8_t* active) {
+// r = b - A x on one level
+__global__ void residual_kernel(Lvl L, const float* __restrict__ bvec, const float* __restrict__ x,
+                                float* r, const uint8_t* active) {
+  __shared__ float off_s[4 * NB2];
+  for (int e = threadIdx.x; e < 4 * NB2; e += blockDim.x) off_s[e] = L.off[e];
+  __syncthreads();
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.nc) return;
   const int i = c % L.nx, j = c / L.nx;
+  const float* xb = x + (size_t)b * L.nc * NB;
   float acc[NB];
+  {
+    const float* D = cell_block(L.diag, L, b, c);
+    float xl[NB];
 #pragma unroll
-  for (int k = 0; k < NB; ++k) acc[k] = 0.f;
-  block_row<STRUCT>(F, L, b, c, i, j, x + (size_t)b * L.nc * NB, true, acc);
+    for (int k = 0; k < NB; ++k) xl[k] = xb[(size_t)c * NB + k];
+#pragma unroll
+    for (int r0 = 0; r0 < NB; ++r0) {
+      float sacc = 0.f;
+#pragma unroll
+      for (int k = 0; k < NB; ++k) sacc = fmaf(D[r0 * NB + k], xl[k], sacc);
+      acc[r0] = sacc;
+    }
+  }
+  nbr_sum(off_s, xb, i, j, L.nx, L.ny, acc);
   const float* bb = bvec + ((size_t)b * L.nc + c) * NB;
   float* rr = r + ((size_t)b * L.nc + c) * NB;
 #pragma unroll
@@ -275,7 +310,7 @@ __device__ __forceinline__ float pk(int dx, int dy, int kf, int kc) {
 }
 
 // b_coarse[C] = sum_children P_c^T r[c]
-__global__ void restrict_kernel(int nxf, int nxc, int nyc, int B, const float* __restrict__ r,
+__global__ void restrict_kernel(int nxf, int nxc, int nyc, const float* __restrict__ r,
                                 float* bc, const uint8_t* active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
@@ -297,8 +332,8 @@ __global__ void restrict_kernel(int nxf, int nxc, int nyc, int B, const float* _
 }
 
 // x_fine[c] += P_c x_coarse[C]
-__global__ void prolong_add_kernel(int nxf, int nyf, int B, const float* __restrict__ xc,
-                                   float* xf, const uint8_t* active) {
+__global__ void prolong_add_kernel(int nxf, int nyf, const float* __restrict__ xc, float* xf,
+                                   const uint8_t* active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -315,64 +350,70 @@ __global__ void prolong_add_kernel(int nxf, int nyf, int B, const float* __restr
   xf[(size_t)b * ncf * NB + t] += s;
 }
 
-// Galerkin coarse blocks: A_c[C][d] = sum over child pairs of P^T A_f P (one thread per entry).
-template <bool STRUCT>
-__global__ void ptap_kernel(Fine F, Lvl Lf, int nxc, int nyc, int B, float* blk_c) {
-  const int b = blockIdx.y;
+// Projected mass blocks of a coarse level: M^C = sum_children P_c^T M^c P_c for the sigma_a and
+// sigma_t masses (4x4 each).  From level 0 the child masses are sigma I of the child's material.
+__global__ void mass_restrict_kernel(int nxf, int nxc, int nyc, int B, const double* Maf,
+                                     const double* Mtf, const int32_t* mat, const double* sigma_t,
+                                     const double* sigma_s, int n_mat, double* Mac, double* Mtc) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int ncc = nxc * nyc;
-  if (t >= ncc * 5 * NB2) return;
-  const int e = t % NB2, d = (t / NB2) % 5, C = t / (5 * NB2);
-  const int ro = e / NB, co = e % NB;           // coarse row / column (field*4 + k)
-  const int fr = ro / 4, kr = ro % 4, fc = co / 4, kc = co % 4;
+  if (t >= ncc * B) return;
+  const int b = t / ncc, C = t % ncc;
   const int I = C % nxc, J = C / nxc;
-  int I2 = I, J2 = J;
-  if (d == 1) --I2;
-  else if (d == 2) ++I2;
-  else if (d == 3) --J2;
-  else if (d == 4) ++J2;
-  float s = 0.f;
-  if (I2 >= 0 && I2 < nxc && J2 >= 0 && J2 < nyc) {
-    for (int dy = 0; dy < 2; ++dy)
-      for (int dx = 0; dx < 2; ++dx) {
-        const int i = 2 * I + dx, j = 2 * J + dy, c = j * Lf.nx + i;
-        for (int dd = 0; dd <= 4; ++dd) {        // fine neighbour of c
-          int c2 = c;
-          if (dd > 0 && !nbr(dd, i, j, Lf.nx, Lf.ny, c2)) continue;
-          const int i2 = c2 % Lf.nx, j2 = c2 / Lf.nx;
-          if (i2 / 2 != I2 || j2 / 2 != J2) continue;  // must be a child of the target coarse cell
-          const float* A;
-          if (STRUCT)
-            A = dd == 0 ? F.diag32 + ((size_t)b * F.n_mat + F.mat[c]) * NB2 : F.off32 + (dd - 1) * NB2;
-          else
-            A = Lf.blk + (((size_t)b * Lf.nc + c) * 5 + dd) * NB2;
-          const int dx2 = i2 & 1, dy2 = j2 & 1;
-          for (int kf = 0; kf < 4; ++kf) {
-            const float pr = pk(dx, dy, kf, kr);
-            if (pr == 0.f) continue;
-            float inner = 0.f;
-            for (int kf2 = 0; kf2 < 4; ++kf2)
-              inner = fmaf(A[(4 * fr + kf) * NB + 4 * fc + kf2], pk(dx2, dy2, kf2, kc), inner);
-            s = fmaf(pr, inner, s);
-          }
-        }
+  const int ncf = nxf * 2 * nyc;
+  double ma[16] = {0}, mt[16] = {0};
+  for (int dy = 0; dy < 2; ++dy)
+    for (int dx = 0; dx < 2; ++dx) {
+      const int c = (2 * J + dy) * nxf + 2 * I + dx;
+      double fa[16], ft[16];
+      if (mat) {
+        const int m = mat[c];
+        const double st = sigma_t[b * n_mat + m], sa = st - sigma_s[b * n_mat + m];
+        for (int e = 0; e < 16; ++e) fa[e] = (e % 5 == 0) ? sa : 0.0, ft[e] = (e % 5 == 0) ? st : 0.0;
+      } else {
+        for (int e = 0; e < 16; ++e) fa[e] = Maf[((size_t)b * ncf + c) * 16 + e], ft[e] = Mtf[((size_t)b * ncf + c) * 16 + e];
       }
-  }
-  blk_c[((size_t)b * ncc) * 5 * NB2 + t] = s;
+      for (int r = 0; r < 4; ++r)
+        for (int q = 0; q < 4; ++q) {
+          double sa = 0.0, stt = 0.0;
+          for (int k = 0; k < 4; ++k) {
+            const double pr = pk(dx, dy, k, r);
+            if (pr == 0.0) continue;
+            for (int l = 0; l < 4; ++l) {
+              const double pq = pk(dx, dy, l, q);
+              sa += pr * fa[4 * k + l] * pq;
+              stt += pr * ft[4 * k + l] * pq;
+            }
+          }
+          ma[4 * r + q] += sa;
+          mt[4 * r + q] += stt;
+        }
+    }
+  for (int e = 0; e < 16; ++e) Mac[(size_t)t * 16 + e] = ma[e], Mtc[(size_t)t * 16 + e] = mt[e];
 }
 
-// 12x12 inverse of each cell's diagonal block (levels >= 1), in double then stored as float.
-__global__ void blockinv_kernel(const float* blk, float* dinv, int nc, int B) {
+// Coarse diagonal blocks: D = geo + blockdiag(Ma, 3<vx^2> Mt, 3<vy^2> Mt); store D and D^{-1}.
+__global__ void coarse_diag_kernel(const double* geo, const double* Ma, const double* Mt,
+                                   double cx, double cy, int n, float* diag, float* dinv) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nc * B) return;
-  const float* A = blk + (size_t)t * 5 * NB2;  // d = 0 block of cell (b, c)
+  if (t >= n) return;
   double a[NB * 24];
   for (int r = 0; r < NB; ++r)
-    for (int c = 0; c < 24; ++c) a[r * 24 + c] = c < NB ? (double)A[r * NB + c] : (c - NB == r ? 1.0 : 0.0);
+    for (int c = 0; c < NB; ++c) {
+      double v = geo[r * NB + c];
+      const int fr = r / 4, fc = c / 4;
+      if (fr == fc) {
+        const double m = fr == 0 ? Ma[(size_t)t * 16 + 4 * (r % 4) + (c % 4)]
+                                 : (fr == 1 ? cx : cy) * Mt[(size_t)t * 16 + 4 * (r % 4) + (c % 4)];
+        v += m;
+      }
+      a[r * 24 + c] = v;
+      a[r * 24 + NB + c] = r == c ? 1.0 : 0.0;
+      diag[(size_t)t * NB2 + r * NB + c] = (float)v;
+    }
   inv12<double>(a);
-  float* o = dinv + (size_t)t * NB2;
   for (int r = 0; r < NB; ++r)
-    for (int c = 0; c < NB; ++c) o[r * NB + c] = (float)a[r * 24 + NB + c];
+    for (int c = 0; c < NB; ++c) dinv[(size_t)t * NB2 + r * NB + c] = (float)a[r * 24 + NB + c];
 }
 
 // ---- vector helpers (FGMRES, FP64) ---------------------------------------------------------
@@ -579,22 +620,26 @@ struct DsaState {
   // 1D
   Blocks1D K1{};
   DevBuf<double> Dpinv, Mfac, work1;
-  // 2D
+  // 2D levels
   int n_levels = 0;
   std::vector<int> lnx, lny;
-  DevBuf<double> off64, diag64;
-  DevBuf<float> off32, diag32, dinv32;
-  std::vector<DevBuf<float>*> blk, dinv;     // levels >= 1
-  std::vector<DevBuf<float>*> xl, bl, rl;    // per level FP32 vectors
-  int m = 20;                                // FGMRES restart length
-  DevBuf<double> V, Z, w, xs;                // Krylov bases and work
+  DevBuf<double> off64, diag64;                 // level 0 in FP64 (Krylov operator)
+  std::vector<DevBuf<float>*> off32;            // [4][144] per level
+  std::vector<DevBuf<double>*> geo64;           // [144] per level >= 1 (geometric diagonal)
+  std::vector<DevBuf<float>*> diag32, dinv32;   // level 0: per material; coarser: per cell
+  std::vector<DevBuf<double>*> Ma, Mt;          // projected masses per cell, levels >= 1
+  std::vector<DevBuf<float>*> xl, bl, rl;       // per level FP32 vectors
+  DevBuf<float> xtot, borig;                    // stationary multigrid accumulator and rhs
+  int m = 20;                                   // FGMRES restart length
+  DevBuf<double> V, Z, w, xs;                   // Krylov bases and work
   DevBuf<double> dots_dev;
+  template <class T>
+  static void del(std::vector<T*>& v) {
+    for (auto* p : v) delete p;
+    v.clear();
+  }
   ~DsaState() {
-    for (auto* p : blk) delete p;
-    for (auto* p : dinv) delete p;
-    for (auto* p : xl) delete p;
-    for (auto* p : bl) delete p;
-    for (auto* p : rl) delete p;
+    del(off32), del(geo64), del(diag32), del(dinv32), del(Ma), del(Mt), del(xl), del(bl), del(rl);
   }
 };
 
@@ -602,17 +647,37 @@ void dsa_state_free(DsaState* s) { delete s; }
 
 static Fine fine_of(rte_batch_t bt) {
   DsaState* s = bt->dsa;
-  return Fine{s->off64.p, s->off32.p, s->diag64.p, s->diag32.p, s->dinv32.p,
-              bt->disc->mat_id.p, bt->disc->n_mat};
+  return Fine{s->off64.p, s->diag64.p, bt->disc->mat_id.p, bt->disc->n_mat};
 }
 
-static Lvl lvl_of(DsaState* s, int l) {
-  Lvl L{s->lnx[l], s->lny[l], s->lnx[l] * s->lny[l], nullptr, nullptr};
-  if (l >= 1) {
-    L.blk = s->blk[l - 1]->p;
-    L.dinv = s->dinv[l - 1]->p;
-  }
+static Lvl lvl_of(rte_batch_t bt, int l) {
+  DsaState* s = bt->dsa;
+  Lvl L{s->lnx[l], s->lny[l], s->lnx[l] * s->lny[l], s->off32[l]->p, s->diag32[l]->p,
+        s->dinv32[l]->p, l == 0 ? bt->disc->mat_id.p : nullptr, l == 0 ? bt->disc->n_mat : 0};
   return L;
+}
+
+// constant neighbour blocks and geometric diagonal of a level with cell sizes (hx, hy)
+static void level_blocks(const DsaMoments& mom, double hx, double hy, double off[4 * NB2],
+                         double geo[NB2]) {
+  const Ops1D ox = ops1d(hx), oy = ops1d(hy);
+  double DCx[3][16], DJx[3][16], DCy[3][16], DJy[3][16], Zr[16] = {0};
+  kron_x(ox.DCd, DCx[0]), kron_x(ox.DCw, DCx[1]), kron_x(ox.DCe, DCx[2]);
+  kron_x(ox.DJd, DJx[0]), kron_x(ox.DJw, DJx[1]), kron_x(ox.DJe, DJx[2]);
+  kron_y(oy.DCd, DCy[0]), kron_y(oy.DCw, DCy[1]), kron_y(oy.DCe, DCy[2]);
+  kron_y(oy.DJd, DJy[0]), kron_y(oy.DJw, DJy[1]), kron_y(oy.DJe, DJy[2]);
+  field_block(mom, DCx[1], DJx[1], Zr, Zr, 0, 0, false, &off[0 * NB2]);  // W
+  field_block(mom, DCx[2], DJx[2], Zr, Zr, 0, 0, false, &off[1 * NB2]);  // E
+  field_block(mom, Zr, Zr, DCy[1], DJy[1], 0, 0, false, &off[2 * NB2]);  // S
+  field_block(mom, Zr, Zr, DCy[2], DJy[2], 0, 0, false, &off[3 * NB2]);  // N
+  field_block(mom, DCx[0], DJx[0], DCy[0], DJy[0], 0.0, 0.0, true, geo);
+}
+
+template <class T>
+static int upload(DevBuf<T>& buf, const std::vector<T>& h) {
+  RTE_TRY(buf.alloc(h.size()));
+  RTE_CUDA_TRY(cudaMemcpy(buf.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return RTE_OK;
 }
 
 int dsa_setup(rte_batch_t bt, cudaStream_t st) {
@@ -652,41 +717,7 @@ int dsa_setup(rte_batch_t bt, cudaStream_t st) {
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
   }
-  // ---- 2D: constant neighbour blocks and per-material diagonal blocks -----------------------
-  const Ops1D ox = ops1d(d->hx), oy = ops1d(d->hy);
-  double DCx[3][16], DJx[3][16], DCy[3][16], DJy[3][16], Zr[16] = {0};
-  kron_x(ox.DCd, DCx[0]), kron_x(ox.DCw, DCx[1]), kron_x(ox.DCe, DCx[2]);
-  kron_x(ox.DJd, DJx[0]), kron_x(ox.DJw, DJx[1]), kron_x(ox.DJe, DJx[2]);
-  kron_y(oy.DCd, DCy[0]), kron_y(oy.DCw, DCy[1]), kron_y(oy.DCe, DCy[2]);
-  kron_y(oy.DJd, DJy[0]), kron_y(oy.DJw, DJy[1]), kron_y(oy.DJe, DJy[2]);
-  std::vector<double> off(4 * NB2);
-  field_block(d->mom, DCx[1], DJx[1], Zr, Zr, 0, 0, false, &off[0 * NB2]);  // W
-  field_block(d->mom, DCx[2], DJx[2], Zr, Zr, 0, 0, false, &off[1 * NB2]);  // E
-  field_block(d->mom, Zr, Zr, DCy[1], DJy[1], 0, 0, false, &off[2 * NB2]);  // S
-  field_block(d->mom, Zr, Zr, DCy[2], DJy[2], 0, 0, false, &off[3 * NB2]);  // N
-  std::vector<double> diag((size_t)B * d->n_mat * NB2), dinv((size_t)B * d->n_mat * NB2);
-  for (int b = 0; b < B; ++b)
-    for (int m = 0; m < d->n_mat; ++m) {
-      const double stv = bt->sigma_t_h[(size_t)b * d->n_mat + m];
-      const double sav = stv - bt->sigma_s_h[(size_t)b * d->n_mat + m];
-      double* D = &diag[((size_t)b * d->n_mat + m) * NB2];
-      field_block(d->mom, DCx[0], DJx[0], DCy[0], DJy[0], sav, stv, true, D);
-      invert_host(D, &dinv[((size_t)b * d->n_mat + m) * NB2], NB);
-    }
-  std::vector<float> off32(off.begin(), off.end()), diag32(diag.begin(), diag.end()),
-      dinv32(dinv.begin(), dinv.end());
-  RTE_TRY(s->off64.alloc(off.size()));
-  RTE_TRY(s->off32.alloc(off.size()));
-  RTE_TRY(s->diag64.alloc(diag.size()));
-  RTE_TRY(s->diag32.alloc(diag.size()));
-  RTE_TRY(s->dinv32.alloc(diag.size()));
-  RTE_CUDA_TRY(cudaMemcpy(s->off64.p, off.data(), off.size() * 8, cudaMemcpyHostToDevice));
-  RTE_CUDA_TRY(cudaMemcpy(s->off32.p, off32.data(), off.size() * 4, cudaMemcpyHostToDevice));
-  RTE_CUDA_TRY(cudaMemcpy(s->diag64.p, diag.data(), diag.size() * 8, cudaMemcpyHostToDevice));
-  RTE_CUDA_TRY(cudaMemcpy(s->diag32.p, diag32.data(), diag.size() * 4, cudaMemcpyHostToDevice));
-  RTE_CUDA_TRY(cudaMemcpy(s->dinv32.p, dinv32.data(), diag.size() * 4, cudaMemcpyHostToDevice));
-
-  // ---- levels: coarsen 2x2 while both sizes are even -------------------------------------------
+  // ---- 2D: allocate the hierarchy once (coarsen 2x2 while both sizes are even) ---------------
   if (s->n_levels == 0) {
     s->lnx.push_back(d->nx);
     s->lny.push_back(d->ny);
@@ -697,42 +728,73 @@ int dsa_setup(rte_batch_t bt, cudaStream_t st) {
     s->n_levels = (int)s->lnx.size();
     for (int l = 0; l < s->n_levels; ++l) {
       const size_t nc = (size_t)s->lnx[l] * s->lny[l];
-      auto* x = new DevBuf<float>();
-      auto* bb = new DevBuf<float>();
-      auto* r = new DevBuf<float>();
-      s->xl.push_back(x), s->bl.push_back(bb), s->rl.push_back(r);
-      RTE_TRY(x->alloc((size_t)B * nc * NB));
-      RTE_TRY(bb->alloc((size_t)B * nc * NB));
-      RTE_TRY(r->alloc((size_t)B * nc * NB));
+      const double hx = d->hx * (1 << l), hy = d->hy * (1 << l);
+      std::vector<double> off(4 * NB2), geo(NB2);
+      level_blocks(d->mom, hx, hy, off.data(), geo.data());
+      s->off32.push_back(new DevBuf<float>());
+      RTE_TRY(upload(*s->off32.back(), std::vector<float>(off.begin(), off.end())));
+      s->geo64.push_back(new DevBuf<double>());
+      RTE_TRY(upload(*s->geo64.back(), geo));
+      if (l == 0) RTE_TRY(upload(s->off64, off));
+      const size_t ndiag = l == 0 ? (size_t)B * d->n_mat : (size_t)B * nc;
+      s->diag32.push_back(new DevBuf<float>());
+      s->dinv32.push_back(new DevBuf<float>());
+      RTE_TRY(s->diag32.back()->alloc(ndiag * NB2));
+      RTE_TRY(s->dinv32.back()->alloc(ndiag * NB2));
+      s->Ma.push_back(new DevBuf<double>());
+      s->Mt.push_back(new DevBuf<double>());
       if (l >= 1) {
-        auto* bk = new DevBuf<float>();
-        auto* di = new DevBuf<float>();
-        s->blk.push_back(bk), s->dinv.push_back(di);
-        RTE_TRY(bk->alloc((size_t)B * nc * 5 * NB2));
-        RTE_TRY(di->alloc((size_t)B * nc * NB2));
+        RTE_TRY(s->Ma.back()->alloc((size_t)B * nc * 16));
+        RTE_TRY(s->Mt.back()->alloc((size_t)B * nc * 16));
+      }
+      for (auto* v : {&s->xl, &s->bl, &s->rl}) {
+        v->push_back(new DevBuf<float>());
+        RTE_TRY(v->back()->alloc((size_t)B * nc * NB));
       }
     }
     const size_t n = (size_t)B * d->n_cells * NB;
+    RTE_TRY(s->xtot.alloc(n));
+    RTE_TRY(s->borig.alloc(n));
     RTE_TRY(s->V.alloc((size_t)(s->m + 1) * n));
     RTE_TRY(s->Z.alloc((size_t)s->m * n));
     RTE_TRY(s->w.alloc(n));
     RTE_TRY(s->xs.alloc(n));
     RTE_TRY(s->dots_dev.alloc((size_t)B * (s->m + 1)));
   }
-  const Fine F = fine_of(bt);
-  for (int l = 0; l + 1 < s->n_levels; ++l) {
-    const Lvl Lf = lvl_of(s, l);
-    const int nxc = s->lnx[l + 1], nyc = s->lny[l + 1];
-    const int total = nxc * nyc * 5 * NB2;
-    dim3 grid((total + 255) / 256, B);
-    if (l == 0) {
-      ptap_kernel<true><<<grid, 256, 0, st>>>(F, Lf, nxc, nyc, B, s->blk[0]->p); RTE_NOTE_LAUNCH();
-    } else {
-      ptap_kernel<false><<<grid, 256, 0, st>>>(F, Lf, nxc, nyc, B, s->blk[l]->p); RTE_NOTE_LAUNCH();
-    }
-    RTE_CUDA_TRY(cudaGetLastError());
-    const int nb = nxc * nyc * B;
-    blockinv_kernel<<<(nb + 63) / 64, 64, 0, st>>>(s->blk[l]->p, s->dinv[l]->p, nxc * nyc, B); RTE_NOTE_LAUNCH();
+  // ---- level 0: one diagonal block (and inverse) per instance and material -------------------
+  {
+    std::vector<double> off(4 * NB2), geo(NB2);
+    level_blocks(d->mom, d->hx, d->hy, off.data(), geo.data());
+    std::vector<double> diag((size_t)B * d->n_mat * NB2), dinv((size_t)B * d->n_mat * NB2);
+    for (int b = 0; b < B; ++b)
+      for (int m = 0; m < d->n_mat; ++m) {
+        const double stv = bt->sigma_t_h[(size_t)b * d->n_mat + m];
+        const double sav = stv - bt->sigma_s_h[(size_t)b * d->n_mat + m];
+        double* D = &diag[((size_t)b * d->n_mat + m) * NB2];
+        for (int e = 0; e < NB2; ++e) D[e] = geo[e];
+        for (int k = 0; k < 4; ++k) {
+          D[k * NB + k] += sav;
+          D[(4 + k) * NB + 4 + k] += 3.0 * d->mom.xx * stv;
+          D[(8 + k) * NB + 8 + k] += 3.0 * d->mom.yy * stv;
+        }
+        invert_host(D, &dinv[((size_t)b * d->n_mat + m) * NB2], NB);
+      }
+    RTE_TRY(upload(s->diag64, diag));
+    std::vector<float> d32(diag.begin(), diag.end()), i32(dinv.begin(), dinv.end());
+    RTE_CUDA_TRY(cudaMemcpy(s->diag32[0]->p, d32.data(), d32.size() * 4, cudaMemcpyHostToDevice));
+    RTE_CUDA_TRY(cudaMemcpy(s->dinv32[0]->p, i32.data(), i32.size() * 4, cudaMemcpyHostToDevice));
+  }
+  // ---- coarse levels: projected masses, diagonal blocks and their inverses ----------------------
+  for (int l = 1; l < s->n_levels; ++l) {
+    const int nxc = s->lnx[l], nyc = s->lny[l], nc = nxc * nyc;
+    const int n = nc * B;
+    mass_restrict_kernel<<<(n + 127) / 128, 128, 0, st>>>(
+        s->lnx[l - 1], nxc, nyc, B, l == 1 ? nullptr : s->Ma[l - 1]->p,
+        l == 1 ? nullptr : s->Mt[l - 1]->p, l == 1 ? d->mat_id.p : nullptr, bt->sigma_t.p,
+        bt->sigma_s.p, d->n_mat, s->Ma[l]->p, s->Mt[l]->p); RTE_NOTE_LAUNCH();
+    coarse_diag_kernel<<<(n + 63) / 64, 64, 0, st>>>(s->geo64[l]->p, s->Ma[l]->p, s->Mt[l]->p,
+                                                     3.0 * d->mom.xx, 3.0 * d->mom.yy, n,
+                                                     s->diag32[l]->p, s->dinv32[l]->p); RTE_NOTE_LAUNCH();
     RTE_CUDA_TRY(cudaGetLastError());
   }
   return RTE_OK;
@@ -742,48 +804,91 @@ int dsa_setup(rte_batch_t bt, cudaStream_t st) {
 static int vcycle(rte_batch_t bt, int l, const uint8_t* active, cudaStream_t st, int nu) {
   DsaState* s = bt->dsa;
   const int B = bt->B;
-  const Fine F = fine_of(bt);
-  const Lvl L = lvl_of(s, l);
+  const Lvl L = lvl_of(bt, l);
   const int per = L.nc * NB;
   float* x = s->xl[l]->p;
   float* b = s->bl[l]->p;
   float* r = s->rl[l]->p;
-  zero32_kernel<<<dim3((per + 255) / 256, B), 256, 0, st>>>(x, per, active); RTE_NOTE_LAUNCH();
-  dim3 gcol((L.nc + 127) / 128, B);
+  RTE_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(float) * (size_t)B * per, st));
+  const int ncol = ((L.nx + 1) / 2) * L.ny;
+  const dim3 gcol((ncol + 127) / 128, B);
   const bool coarsest = l == s->n_levels - 1;
   auto smooth = [&](int c0) {
-    for (int k = 0; k < 2; ++k) {
-      const int color = k == 0 ? c0 : 1 - c0;
-      if (l == 0) {
-        rbgs_kernel<true><<<gcol, 128, 0, st>>>(F, L, B, color, b, x, active); RTE_NOTE_LAUNCH();
-      } else {
-        rbgs_kernel<false><<<gcol, 128, 0, st>>>(F, L, B, color, b, x, active); RTE_NOTE_LAUNCH();
-      }
-    }
+    rbgs_kernel<<<gcol, 128, 0, st>>>(L, c0, b, x, active); RTE_NOTE_LAUNCH();
+    rbgs_kernel<<<gcol, 128, 0, st>>>(L, 1 - c0, b, x, active); RTE_NOTE_LAUNCH();
   };
   if (coarsest && L.nc == 1) {  // exact: x = D^{-1} b
-    smooth(0);
+    rbgs_kernel<<<gcol, 128, 0, st>>>(L, 0, b, x, active); RTE_NOTE_LAUNCH();
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
   }
   const int npre = coarsest ? 30 : nu;
   for (int k = 0; k < npre; ++k) smooth(0);
   if (!coarsest) {
-    dim3 gc((L.nc + 127) / 128, B);
-    if (l == 0) {
-      residual_kernel<true><<<gc, 128, 0, st>>>(F, L, B, b, x, r, active); RTE_NOTE_LAUNCH();
-    } else {
-      residual_kernel<false><<<gc, 128, 0, st>>>(F, L, B, b, x, r, active); RTE_NOTE_LAUNCH();
-    }
+    residual_kernel<<<dim3((L.nc + 127) / 128, B), 128, 0, st>>>(L, b, x, r, active); RTE_NOTE_LAUNCH();
     const int nxc = s->lnx[l + 1], nyc = s->lny[l + 1];
     const int nco = nxc * nyc * NB;
-    restrict_kernel<<<dim3((nco + 255) / 256, B), 256, 0, st>>>(L.nx, nxc, nyc, B, r,
-                                                                s->bl[l + 1]->p, active); RTE_NOTE_LAUNCH();
+    restrict_kernel<<<dim3((nco + 255) / 256, B), 256, 0, st>>>(L.nx, nxc, nyc, r, s->bl[l + 1]->p,
+                                                                active); RTE_NOTE_LAUNCH();
     RTE_TRY(vcycle(bt, l + 1, active, st, nu));
-    prolong_add_kernel<<<dim3((per + 255) / 256, B), 256, 0, st>>>(L.nx, L.ny, B, s->xl[l + 1]->p,
-                                                                   x, active); RTE_NOTE_LAUNCH();
+    prolong_add_kernel<<<dim3((per + 255) / 256, B), 256, 0, st>>>(L.nx, L.ny, s->xl[l + 1]->p, x,
+                                                                   active); RTE_NOTE_LAUNCH();
     for (int k = 0; k < nu; ++k) smooth(1);
   }
+  RTE_CUDA_TRY(cudaGetLastError());
+  return RTE_OK;
+}
+
+__global__ void pack_rhs32_kernel(const double* R, float* v, int nc, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nc * NB) return;
+  const int c = t / NB, k = t % NB;
+  v[(size_t)b * nc * NB + t] = k < 4 ? (float)R[(size_t)b * nc * 4 + 4 * c + k] : 0.f;
+}
+
+__global__ void add32_kernel(const float* x, float* y, int per, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < per; e += gridDim.x * blockDim.x)
+    y[(size_t)b * per + e] += x[(size_t)b * per + e];
+}
+
+__global__ void extract_rho32_kernel(const float* x, double* drho, int nc, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nc * 4) return;
+  const int c = t / 4, k = t % 4;
+  drho[(size_t)b * nc * 4 + t] = (double)x[((size_t)b * nc + c) * NB + k];
+}
+
+// Stationary multigrid: k V-cycles on the FP32 system, x <- x + V(b - A x), no host round trip.
+static int dsa2d_vcycles(rte_batch_t bt, const double* R, double* drho, int k,
+                         const uint8_t* active, cudaStream_t st) {
+  DsaState* s = bt->dsa;
+  const int B = bt->B, nc = bt->disc->n_cells, per = nc * NB;
+  const dim3 gv((per + 255) / 256, B), gvc(std::min((per + 255) / 256, 1024), B);
+  pack_rhs32_kernel<<<gv, 256, 0, st>>>(R, s->borig.p, nc, active); RTE_NOTE_LAUNCH();
+  const Lvl L0 = lvl_of(bt, 0);
+  for (int it = 0; it < k; ++it) {
+    if (it == 0) {
+      RTE_CUDA_TRY(cudaMemcpyAsync(s->bl[0]->p, s->borig.p, sizeof(float) * (size_t)B * per,
+                                   cudaMemcpyDeviceToDevice, st));
+    } else {
+      residual_kernel<<<dim3((nc + 127) / 128, B), 128, 0, st>>>(L0, s->borig.p, s->xtot.p,
+                                                               s->bl[0]->p, active); RTE_NOTE_LAUNCH();
+    }
+    RTE_TRY(vcycle(bt, 0, active, st, 2));
+    if (it == 0)
+      RTE_CUDA_TRY(cudaMemcpyAsync(s->xtot.p, s->xl[0]->p, sizeof(float) * (size_t)B * per,
+                                   cudaMemcpyDeviceToDevice, st));
+    else {
+      add32_kernel<<<gvc, 256, 0, st>>>(s->xl[0]->p, s->xtot.p, per, active); RTE_NOTE_LAUNCH();
+    }
+  }
+  extract_rho32_kernel<<<dim3((nc * 4 + 255) / 256, B), 256, 0, st>>>(s->xtot.p, drho, nc, active); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;
 }
@@ -983,6 +1088,12 @@ int dsa_apply(rte_batch_t bt, const double* R, double* drho, double rtol, int ma
       for (int b = 0; b < bt->B; ++b) iters[b] = 1;
     return RTE_OK;
   }
+  if (rtol == 0.0) {  // fixed number of V-cycles, no synchronisation
+    RTE_TRY(dsa2d_vcycles(bt, R, drho, max_it, active, st));
+    if (iters)
+      for (int b = 0; b < bt->B; ++b) iters[b] = max_it;
+    return RTE_OK;
+  }
   return dsa2d_fgmres(bt, R, drho, rtol, max_it, active, iters, st);
 }
 
@@ -994,7 +1105,7 @@ extern "C" int rte_dsa_correction(rte_batch_t b, const double* R, double* drho, 
                                   int max_it, const uint8_t* active, int* iters, void* stream) {
   if (!b || !R || !drho) return fail(RTE_EINVAL, "rte_dsa_correction: null argument");
   if (!b->params_set) return fail(RTE_ESTATE, "parameters not set");
-  if (!(rtol > 0) || max_it < 1) return fail(RTE_EINVAL, "rte_dsa_correction: bad tolerance");
+  if (!(rtol >= 0) || max_it < 1) return fail(RTE_EINVAL, "rte_dsa_correction: bad tolerance");
   DeviceGuard g(b->disc->device);
   cudaStream_t st = (cudaStream_t)stream;
   int s = dsa_apply(b, R, drho, rtol, max_it, active, iters, st);

@@ -121,7 +121,7 @@ extern "C" int rte_solve(rte_batch_t b, const rte_solve_opts* o, rte_rom_t rom_c
   if (!b->params_set) return fail(RTE_ESTATE, "rte_solve: parameters not set");
   if (!(o->eps >= 0) || o->max_iter < 1 || o->sa < 0 || o->sa > 3)
     return fail(RTE_EINVAL, "rte_solve: bad options");
-  if (o->sa != RTE_SA_NONE && b->disc->dim == 2 && (!(o->dsa_rtol > 0) || o->dsa_max_it < 1))
+  if (o->sa != RTE_SA_NONE && b->disc->dim == 2 && (!(o->dsa_rtol >= 0) || o->dsa_max_it < 1))
     return fail(RTE_EINVAL, "rte_solve: bad DSA tolerance");
   if (rom_c && rom_c->disc != b->disc) return fail(RTE_EINVAL, "ROM built on another discretisation");
   DeviceGuard g(b->disc->device);

@@ -28,6 +28,7 @@ SIGNATURES = {
     "rte_last_error": (ctypes.c_char_p, []),
     "rte_counters": (_I, [_P]),
     "rte_batch_timing": (_I, [_P, _I, _P]),
+    "rte_batch_tune": (_I, [_P, _I]),
     "rte_disc_create": (_I, [_P, _I, _P]),
     "rte_disc_destroy": (_I, [_P]),
     "rte_disc_info": (_I, [_P, _P]),
@@ -190,6 +191,10 @@ class Batch:
         inf = _host(problem.inflow)
         check(lib().rte_batch_set_params(self.h, st.ctypes.data_as(_P), ss.ctypes.data_as(_P),
                                          src.ctypes.data_as(_P), inf.ctypes.data_as(_P)))
+
+    def tune(self, dirs_per_warp=0):
+        """Directions swept per warp in 2D (1, 2, 4, 8; 0 = automatic)."""
+        check(lib().rte_batch_tune(self.h, int(dirs_per_warp)))
 
     def timing(self, enable):
         """enable=1 reset+start, 0 reset+stop, -1 read; returns (sweep_ms, launches, units)."""

@@ -142,3 +142,20 @@ def test_si_dsa_2d_converged_batch_and_plain_si():
     rep2, _, st2 = bq.solve(r2, 1e-13, sa=rte.SA_NONE, rel=True, max_iter=500)
     assert st2 == 0
     assert _rel(r2.cpu().numpy()[0], Transport(q).solve_rho_direct()) < 1e-11
+
+
+def test_si_with_fixed_vcycle_dsa_converges_to_the_same_solution():
+    """DSA approximated by two FP32 multigrid V-cycles (no Krylov): the fixed point is the
+    transport solution, so the converged rho matches the oracle to the FP64 tolerance."""
+    rte = _rte()
+    p = inputs.lattice_test(32, 16, 2, n_vz=2)
+    batch = rte.Batch.from_problem(p)
+    rho = torch.zeros((2, p.n_dof), dtype=torch.float64, device="cuda")
+    rep, _, st = batch.solve(rho, 1e-13, sa=rte.SA_DSA, rel=True, max_iter=300, dsa_rtol=0.0,
+                             dsa_max_it=2)
+    assert st == 0
+    for b in range(2):
+        tr = Transport(p, b)
+        ref = sisa(tr, np.zeros(tr.n_dof), 1e-14, 400, "dsa", dsa=ConsistentDSA(tr), tol_mode="rel")
+        assert _rel(rho.cpu().numpy()[b], ref["rho"]) < 1e-10
+        assert rep[b]["n_sweep"] <= ref["n_sweep"] + 3

@@ -132,3 +132,19 @@ def test_sweep_lattice_128_full_size():
     _, gpu, _ = _gpu_sweep(rte, p, rho_in)
     ref, _ = _oracle_sweep(p.subset([0]), rho_in[:1])
     _check(gpu[:1], ref)
+
+
+@pytest.mark.parametrize("dpw", [1, 2, 4, 8])
+def test_sweep_work_decomposition_does_not_change_results(dpw):
+    rte = _rte()
+    p = inputs.random_2d(40, 16, 4, 3, seed=77, B=2, inflow=(0.2, 0.0, 1.0, 0.5), ny=33)
+    batch = rte.Batch(rte.Disc(p), 2)
+    batch.tune(dpw)
+    batch.set_params(p)
+    rho_in = np.random.default_rng(6).normal(size=(2, p.n_dof))
+    rin = torch.tensor(rho_in, device="cuda")
+    rout = torch.empty_like(rin)
+    batch.sweep(rin, rout)
+    torch.cuda.synchronize()
+    ref, _ = _oracle_sweep(p, rho_in)
+    _check(rout.cpu().numpy(), ref)

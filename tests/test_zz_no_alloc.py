@@ -27,15 +27,17 @@ def _rel(a, b):
     return float((a - b).abs().max() / b.abs().max())
 
 
-@pytest.mark.parametrize("make", [
-    lambda: inputs.lattice_test(128, 64, 3),
-    lambda: inputs.random_2d(37, 8, 4, 3, seed=5, B=2, inflow=(0.3, 1.2, 0.7, 0.0), ny=19),
-    lambda: inputs.slab_random(45, 16, 4, seed=8, B=3, inflow=(1.5, 0.25)),
+@pytest.mark.parametrize("make,dpw", [
+    (lambda: inputs.lattice_test(128, 64, 3), 4),
+    (lambda: inputs.random_2d(37, 8, 4, 3, seed=5, B=2, inflow=(0.3, 1.2, 0.7, 0.0), ny=19), 0),
+    (lambda: inputs.slab_random(45, 16, 4, seed=8, B=3, inflow=(1.5, 0.25)), 0),
 ])
-def test_static_sweep_matches_regular_sweep_twice(make):
+def test_static_sweep_matches_regular_sweep_twice(make, dpw):
     rte = _rte()
     p = make()
-    batch = rte.Batch.from_problem(p)
+    batch = rte.Batch(rte.Disc(p), p.batch)
+    batch.tune(dpw)   # the decomposition sets how many partial sums the batch needs
+    batch.set_params(p)
     gen = torch.Generator(device="cuda").manual_seed(7)
     for call in range(2):
         rin = torch.rand((p.batch, p.n_dof), dtype=torch.float64, device="cuda", generator=gen)
@@ -53,7 +55,9 @@ def test_static_sweep_matches_regular_sweep_twice(make):
 def test_static_sweep_rejects_batches_beyond_its_scratch():
     rte = _rte()
     p = inputs.lattice_test(128, 64, 5)  # 5 x 8 groups x 65536 doubles > 2^21
-    batch = rte.Batch.from_problem(p)
+    batch = rte.Batch(rte.Disc(p), 5)
+    batch.tune(4)
+    batch.set_params(p)
     rin = torch.zeros((5, p.n_dof), dtype=torch.float64, device="cuda")
     out = torch.zeros_like(rin)
     with pytest.raises(rte.RTEError) as e:
