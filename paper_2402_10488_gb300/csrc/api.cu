@@ -347,6 +347,7 @@ extern "C" int rte_batch_create(rte_disc_t disc, int B, rte_batch_t* out) {
   if (st == RTE_OK) st = b->tables.alloc(nb * disc->n_mat * disc->n_dirs * tab);
   if (st == RTE_OK) st = b->partial.alloc(nb * b->groups.size() * disc->n_dof);
   if (st == RTE_OK) st = b->norms.alloc(nb * 2);
+  if (st == RTE_OK && disc->dim == 2) st = b->S.alloc(nb * disc->n_dof);
   if (st == RTE_OK) st = b->work.alloc(nb * disc->n_dof * 4);
   if (st != RTE_OK) {
     delete b;

@@ -134,6 +134,7 @@ struct rte_batch_s {
   rte::DevBuf<double> inflow;             // [B][4] (2D) or [B][2] (1D)
   rte::DevBuf<double> tables;             // [B][n_mat][n_dirs][kTab*]
   rte::DevBuf<double> partial;            // [B][n_groups][n_dof] per-group scalar-flux partials
+  rte::DevBuf<double> S;                  // [B][n_dof] cell sources of the current sweep (2D)
   rte::DevBuf<unsigned long long> norms;  // [B][2] stop-test norms as ordered bit patterns
   rte::DevBuf<double> work;               // [B][n_dof] x 4 iteration scratch for rte_solve
   rte::DsaState* dsa = nullptr;

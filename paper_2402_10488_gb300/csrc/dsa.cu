@@ -137,18 +137,34 @@ __device__ __forceinline__ void inv12(T* a /*[12][24] scratch*/) {
 // mesh: coarse Q^1 functions are continuous inside a coarse cell, so every term on an interior
 // fine face (jumps, averages times jumps) vanishes, and the volume and coarse-face terms are those
 // of the coarse mesh.  Only the cross-section terms change: Sigma becomes the projected mass
-// matrix sum_children P_c^T (sigma_c I) P_c, a 4x4 block per field and coarse cell.  So every
-// level has four constant 12x12 neighbour blocks (set by its cell size) and a per-cell 12x12
-// diagonal block = constant geometric part + projected mass blocks; level 0 keeps one diagonal
-// block per material.
+// matrix sum_children P_c^T (sigma_c I) P_c.  So each level has constant neighbour couplings (set
+// by its cell size) and a 12x12 diagonal block per cell = geometric part + mass blocks.  Cross
+// sections are cellwise constant, so a coarse cell whose children all share one material has that
+// material's block (the projected mass of a constant is the constant times I); only cells on a
+// material interface need their own.  Each level therefore stores a class per cell (material, or
+// one of the level's mixed cells) and one diagonal block per (instance, class).
+//
+// The neighbour blocks act only through face traces: the west neighbour contributes
+// L (x) (C_W t) with t = the neighbour's right-face traces of the three fields (2 values each),
+// L = (1, -sqrt3)/sqrt(h_x) the own left-face values and C_W a 3x3 field coupling from the
+// quadrature moments; east, south and north likewise.
 
-struct Lvl {
-  int nx, ny, nc;
-  const float* off;    // [4][144]: W, E, S, N blocks of this level (constant)
-  const float* diag;   // level 0: [B][n_mat][144]; coarser: [B][nc][144]
-  const float* dinv;   // same layout as diag
-  const int32_t* mat;  // level 0: material map; coarser: nullptr
-  int n_mat;
+constexpr int kMaxLevels = 16;
+constexpr int kFuseCells = 1024;  // levels this small run inside one fused kernel per instance
+
+struct LevelC {
+  int nx, ny, nc, n_class;
+  const int32_t* cls;  // [nc] class of each cell (material map at level 0)
+  const float* diag;   // [B][n_class][144]
+  const float* dinv;   // [B][n_class][144]
+  float qx, qy;        // 1/sqrt(h_x), 1/sqrt(h_y) of this level
+  float* x;            // [B][nc][12]
+  float* b;
+  float* r;
+};
+
+struct Coup {  // row-major 3x3 field couplings of the W, E, S, N faces
+  float W[9], E[9], S[9], N[9];
 };
 
 struct Fine {  // level 0 in FP64, for the Krylov operator
@@ -167,10 +183,6 @@ __device__ __forceinline__ bool nbr(int d, int i, int j, int nx, int ny, int& c2
   if (ii < 0 || ii >= nx || jj < 0 || jj >= ny) return false;
   c2 = jj * nx + ii;
   return true;
-}
-
-__device__ __forceinline__ const float* cell_block(const float* base, const Lvl& L, int b, int c) {
-  return L.mat ? base + ((size_t)b * L.n_mat + L.mat[c]) * NB2 : base + ((size_t)b * L.nc + c) * NB2;
 }
 
 // y = A0 x in FP64 on the finest level.  One thread per (cell, row of its block).
@@ -198,105 +210,134 @@ __global__ void fine_apply64_kernel(Fine F, int nx, int ny, int B, const double*
   y[(size_t)b * nc * NB + t] = acc;
 }
 
-// acc += sum over existing neighbours of O_d x_neighbour (O in shared memory)
-__device__ __forceinline__ void nbr_sum(const float* __restrict__ off_s, const float* __restrict__ x,
-                                        int i, int j, int nx, int ny, float acc[NB]) {
-  for (int d = 1; d <= 4; ++d) {
-    int c2;
-    if (!nbr(d, i, j, nx, ny, c2)) continue;
-    const float* O = off_s + (d - 1) * NB2;
-    float xl[NB];
-    const float4* xv = reinterpret_cast<const float4*>(x + (size_t)c2 * NB);
+__device__ __forceinline__ void load12(const float* p, float v[NB]) {
+  const float4* q = reinterpret_cast<const float4*>(p);
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const float4 v = xv[q];
-      xl[4 * q] = v.x, xl[4 * q + 1] = v.y, xl[4 * q + 2] = v.z, xl[4 * q + 3] = v.w;
-    }
-#pragma unroll
-    for (int r = 0; r < NB; ++r) {
-      float sacc = 0.f;
-#pragma unroll
-      for (int k = 0; k < NB; ++k) sacc = fmaf(O[r * NB + k], xl[k], sacc);
-      acc[r] += sacc;
-    }
+  for (int k = 0; k < 3; ++k) {
+    const float4 u = q[k];
+    v[4 * k] = u.x, v[4 * k + 1] = u.y, v[4 * k + 2] = u.z, v[4 * k + 3] = u.w;
   }
 }
 
-// Red-black block Gauss-Seidel half sweep on the cells with (i + j) % 2 == color:
-// x_c = D_c^{-1} (b_c - sum_n O_n x_n).  Threads map onto the cells of that colour only.
-__global__ void rbgs_kernel(Lvl L, int color, const float* __restrict__ bvec, float* x,
-                            const uint8_t* active) {
-  __shared__ float off_s[4 * NB2];
-  for (int e = threadIdx.x; e < 4 * NB2; e += blockDim.x) off_s[e] = L.off[e];
-  __syncthreads();
-  const int b = blockIdx.y;
-  if (active && !active[b]) return;
-  const int hx2 = (L.nx + 1) / 2;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= hx2 * L.ny) return;
-  const int j = idx / hx2;
-  const int i = 2 * (idx % hx2) + ((j + color) & 1);
-  if (i >= L.nx) return;
-  const int c = j * L.nx + i;
-  float* xb = x + (size_t)b * L.nc * NB;
+__device__ __forceinline__ void store12(float* p, const float v[NB]) {
+  float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) q[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+}
+
+// acc += sum over the existing face neighbours of their coupling to cell (i, j), via traces.
+__device__ __forceinline__ void nbr_trace_sum(const Coup& K, float qx, float qy,
+                                              const float* __restrict__ x, int i, int j, int nx,
+                                              int ny, float acc[NB]) {
+  const float s3 = 1.7320508075688772f;
+  float v[NB], t[3][2];
+  if (i > 0) {  // west neighbour: its right-face traces, own left-face values
+    load12(x + ((size_t)j * nx + i - 1) * NB, v);
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) t[f][q] = qx * fmaf(s3, v[4 * f + 1 + 2 * q], v[4 * f + 2 * q]);
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float u = qx * (K.W[3 * f] * t[0][q] + K.W[3 * f + 1] * t[1][q] + K.W[3 * f + 2] * t[2][q]);
+        acc[4 * f + 2 * q] += u;
+        acc[4 * f + 1 + 2 * q] -= s3 * u;
+      }
+  }
+  if (i + 1 < nx) {  // east neighbour: its left-face traces, own right-face values
+    load12(x + ((size_t)j * nx + i + 1) * NB, v);
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) t[f][q] = qx * fmaf(-s3, v[4 * f + 1 + 2 * q], v[4 * f + 2 * q]);
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float u = qx * (K.E[3 * f] * t[0][q] + K.E[3 * f + 1] * t[1][q] + K.E[3 * f + 2] * t[2][q]);
+        acc[4 * f + 2 * q] += u;
+        acc[4 * f + 1 + 2 * q] += s3 * u;
+      }
+  }
+  if (j > 0) {  // south neighbour: its top-face traces (expanded along x), own bottom values
+    load12(x + ((size_t)(j - 1) * nx + i) * NB, v);
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) t[f][q] = qy * fmaf(s3, v[4 * f + q + 2], v[4 * f + q]);
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float u = qy * (K.S[3 * f] * t[0][q] + K.S[3 * f + 1] * t[1][q] + K.S[3 * f + 2] * t[2][q]);
+        acc[4 * f + q] += u;
+        acc[4 * f + q + 2] -= s3 * u;
+      }
+  }
+  if (j + 1 < ny) {  // north neighbour: its bottom-face traces, own top values
+    load12(x + ((size_t)(j + 1) * nx + i) * NB, v);
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) t[f][q] = qy * fmaf(-s3, v[4 * f + q + 2], v[4 * f + q]);
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float u = qy * (K.N[3 * f] * t[0][q] + K.N[3 * f + 1] * t[1][q] + K.N[3 * f + 2] * t[2][q]);
+        acc[4 * f + q] += u;
+        acc[4 * f + q + 2] += s3 * u;
+      }
+  }
+}
+
+__device__ __forceinline__ void matvec12(const float* __restrict__ M, const float v[NB], float out[NB]) {
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) s = fmaf(M[r * NB + k], v[k], s);
+    out[r] = s;
+  }
+}
+
+// one cell of a red-black block Gauss-Seidel half sweep: x_c = D_c^{-1} (b_c - sum_n O_n x_n)
+__device__ __forceinline__ void rbgs_cell(const LevelC& L, const Coup& K, int b, int c) {
+  const int i = c % L.nx, j = c / L.nx;
+  float* xb = L.x + (size_t)b * L.nc * NB;
   float acc[NB];
 #pragma unroll
   for (int r = 0; r < NB; ++r) acc[r] = 0.f;
-  nbr_sum(off_s, xb, i, j, L.nx, L.ny, acc);
-  const float* bb = bvec + ((size_t)b * L.nc + c) * NB;
+  nbr_trace_sum(K, L.qx, L.qy, xb, i, j, L.nx, L.ny, acc);
   float res[NB];
+  load12(L.b + ((size_t)b * L.nc + c) * NB, res);
 #pragma unroll
-  for (int r = 0; r < NB; ++r) res[r] = bb[r] - acc[r];
-  const float* Di = cell_block(L.dinv, L, b, c);
+  for (int r = 0; r < NB; ++r) res[r] -= acc[r];
   float out[NB];
-#pragma unroll
-  for (int r = 0; r < NB; ++r) {
-    float sacc = 0.f;
-#pragma unroll
-    for (int k = 0; k < NB; ++k) sacc = fmaf(Di[r * NB + k], res[k], sacc);
-    out[r] = sacc;
-  }
-  float4* xo = reinterpret_cast<float4*>(xb + (size_t)c * NB);
-#pragma unroll
-  for (int q = 0; q < 3; ++q) xo[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
+  matvec12(L.dinv + ((size_t)b * L.n_class + L.cls[c]) * NB2, res, out);
+  store12(xb + (size_t)c * NB, out);
 }
 
-// r = b - A x on one level
-__global__ void residual_kernel(Lvl L, const float* __restrict__ bvec, const float* __restrict__ x,
-                                float* r, const uint8_t* active) {
-  __shared__ float off_s[4 * NB2];
-  for (int e = threadIdx.x; e < 4 * NB2; e += blockDim.x) off_s[e] = L.off[e];
-  __syncthreads();
-  const int b = blockIdx.y;
-  if (active && !active[b]) return;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= L.nc) return;
+// one cell of r = b - A x
+__device__ __forceinline__ void residual_cell(const LevelC& L, const Coup& K, int b, int c) {
   const int i = c % L.nx, j = c / L.nx;
-  const float* xb = x + (size_t)b * L.nc * NB;
-  float acc[NB];
-  {
-    const float* D = cell_block(L.diag, L, b, c);
-    float xl[NB];
+  const float* xb = L.x + (size_t)b * L.nc * NB;
+  float xl[NB], acc[NB];
+  load12(xb + (size_t)c * NB, xl);
+  matvec12(L.diag + ((size_t)b * L.n_class + L.cls[c]) * NB2, xl, acc);
+  nbr_trace_sum(K, L.qx, L.qy, xb, i, j, L.nx, L.ny, acc);
+  float bl[NB];
+  load12(L.b + ((size_t)b * L.nc + c) * NB, bl);
 #pragma unroll
-    for (int k = 0; k < NB; ++k) xl[k] = xb[(size_t)c * NB + k];
-#pragma unroll
-    for (int r0 = 0; r0 < NB; ++r0) {
-      float sacc = 0.f;
-#pragma unroll
-      for (int k = 0; k < NB; ++k) sacc = fmaf(D[r0 * NB + k], xl[k], sacc);
-      acc[r0] = sacc;
-    }
-  }
-  nbr_sum(off_s, xb, i, j, L.nx, L.ny, acc);
-  const float* bb = bvec + ((size_t)b * L.nc + c) * NB;
-  float* rr = r + ((size_t)b * L.nc + c) * NB;
-#pragma unroll
-  for (int k = 0; k < NB; ++k) rr[k] = bb[k] - acc[k];
+  for (int k = 0; k < NB; ++k) bl[k] -= acc[k];
+  store12(L.r + ((size_t)b * L.nc + c) * NB, bl);
 }
 
 // Prolongation coefficients: fine basis a_f in the coarse basis a_c restricted to child o (-1/+1):
 // p[o][a_f][a_c] = int_child phi^C_{a_c} phi^f_{a_f}.
-__device__ __forceinline__ float pcoef(int o, int af, int ac) {
+__host__ __device__ __forceinline__ float pcoef(int o, int af, int ac) {
   const float r2 = 0.70710678118654752f;  // 1/sqrt2
   if (af == 0 && ac == 0) return r2;
   if (af == 0 && ac == 1) return (o < 0 ? -1.f : 1.f) * 0.61237243569579452f;  // sqrt6/4
@@ -305,96 +346,168 @@ __device__ __forceinline__ float pcoef(int o, int af, int ac) {
 }
 
 // P entry for child (dx, dy) mapping coarse local k_c to fine local k_f (same field).
-__device__ __forceinline__ float pk(int dx, int dy, int kf, int kc) {
+__host__ __device__ __forceinline__ float pk(int dx, int dy, int kf, int kc) {
   return pcoef(dx ? 1 : -1, kf & 1, kc & 1) * pcoef(dy ? 1 : -1, kf >> 1, kc >> 1);
 }
 
-// b_coarse[C] = sum_children P_c^T r[c]
-__global__ void restrict_kernel(int nxf, int nxc, int nyc, const float* __restrict__ r,
-                                float* bc, const uint8_t* active) {
-  const int b = blockIdx.y;
-  if (active && !active[b]) return;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int ncc = nxc * nyc;
-  if (t >= ncc * NB) return;
+// one entry t = (C, row) of b_coarse = sum_children P_c^T r[c]
+__device__ __forceinline__ void restrict_entry(const LevelC& F, const LevelC& Cl, int b, int t) {
   const int C = t / NB, row = t % NB, f = row / 4, kc = row % 4;
-  const int I = C % nxc, J = C / nxc;
-  const int ncf = nxf * 2 * nyc;
+  const int I = C % Cl.nx, J = C / Cl.nx;
   float s = 0.f;
   for (int dy = 0; dy < 2; ++dy)
     for (int dx = 0; dx < 2; ++dx) {
-      const int c = (2 * J + dy) * nxf + 2 * I + dx;
-      const float* rv = r + ((size_t)b * ncf + c) * NB + 4 * f;
+      const int c = (2 * J + dy) * F.nx + 2 * I + dx;
+      const float* rv = F.r + ((size_t)b * F.nc + c) * NB + 4 * f;
 #pragma unroll
       for (int kf = 0; kf < 4; ++kf) s = fmaf(pk(dx, dy, kf, kc), rv[kf], s);
     }
-  bc[((size_t)b * ncc) * NB + t] = s;
+  Cl.b[((size_t)b * Cl.nc) * NB + t] = s;
 }
 
-// x_fine[c] += P_c x_coarse[C]
-__global__ void prolong_add_kernel(int nxf, int nyf, const float* __restrict__ xc, float* xf,
-                                   const uint8_t* active) {
-  const int b = blockIdx.y;
-  if (active && !active[b]) return;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int ncf = nxf * nyf;
-  if (t >= ncf * NB) return;
+// one entry t = (c, row) of x_fine += P_c x_coarse[C]
+__device__ __forceinline__ void prolong_entry(const LevelC& F, const LevelC& Cl, int b, int t) {
   const int c = t / NB, row = t % NB, f = row / 4, kf = row % 4;
-  const int i = c % nxf, j = c / nxf;
-  const int nxc = nxf / 2, ncc = nxc * (nyf / 2);
-  const int C = (j / 2) * nxc + i / 2, dx = i & 1, dy = j & 1;
-  const float* xv = xc + ((size_t)b * ncc + C) * NB + 4 * f;
+  const int i = c % F.nx, j = c / F.nx;
+  const int C = (j / 2) * Cl.nx + i / 2, dx = i & 1, dy = j & 1;
+  const float* xv = Cl.x + ((size_t)b * Cl.nc + C) * NB + 4 * f;
   float s = 0.f;
 #pragma unroll
   for (int kc = 0; kc < 4; ++kc) s = fmaf(pk(dx, dy, kf, kc), xv[kc], s);
-  xf[(size_t)b * ncf * NB + t] += s;
+  F.x[(size_t)b * F.nc * NB + t] += s;
 }
 
-// Projected mass blocks of a coarse level: M^C = sum_children P_c^T M^c P_c for the sigma_a and
-// sigma_t masses (4x4 each).  From level 0 the child masses are sigma I of the child's material.
-__global__ void mass_restrict_kernel(int nxf, int nxc, int nyc, int B, const double* Maf,
-                                     const double* Mtf, const int32_t* mat, const double* sigma_t,
-                                     const double* sigma_s, int n_mat, double* Mac, double* Mtc) {
+__global__ void rbgs_kernel(LevelC L, Coup K, int color, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int hx2 = (L.nx + 1) / 2;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= hx2 * L.ny) return;
+  const int j = idx / hx2;
+  const int i = 2 * (idx % hx2) + ((j + color) & 1);
+  if (i >= L.nx) return;
+  rbgs_cell(L, K, b, j * L.nx + i);
+}
+
+__global__ void residual_kernel(LevelC L, Coup K, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.nc) return;
+  residual_cell(L, K, b, c);
+}
+
+__global__ void restrict_kernel(LevelC F, LevelC Cl, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int ncc = nxc * nyc;
-  if (t >= ncc * B) return;
-  const int b = t / ncc, C = t % ncc;
-  const int I = C % nxc, J = C / nxc;
-  const int ncf = nxf * 2 * nyc;
-  double ma[16] = {0}, mt[16] = {0};
-  for (int dy = 0; dy < 2; ++dy)
-    for (int dx = 0; dx < 2; ++dx) {
-      const int c = (2 * J + dy) * nxf + 2 * I + dx;
-      double fa[16], ft[16];
-      if (mat) {
-        const int m = mat[c];
-        const double st = sigma_t[b * n_mat + m], sa = st - sigma_s[b * n_mat + m];
-        for (int e = 0; e < 16; ++e) fa[e] = (e % 5 == 0) ? sa : 0.0, ft[e] = (e % 5 == 0) ? st : 0.0;
-      } else {
-        for (int e = 0; e < 16; ++e) fa[e] = Maf[((size_t)b * ncf + c) * 16 + e], ft[e] = Mtf[((size_t)b * ncf + c) * 16 + e];
-      }
-      for (int r = 0; r < 4; ++r)
-        for (int q = 0; q < 4; ++q) {
-          double sa = 0.0, stt = 0.0;
-          for (int k = 0; k < 4; ++k) {
-            const double pr = pk(dx, dy, k, r);
-            if (pr == 0.0) continue;
-            for (int l = 0; l < 4; ++l) {
-              const double pq = pk(dx, dy, l, q);
-              sa += pr * fa[4 * k + l] * pq;
-              stt += pr * ft[4 * k + l] * pq;
-            }
-          }
-          ma[4 * r + q] += sa;
-          mt[4 * r + q] += stt;
-        }
-    }
-  for (int e = 0; e < 16; ++e) Mac[(size_t)t * 16 + e] = ma[e], Mtc[(size_t)t * 16 + e] = mt[e];
+  if (t >= Cl.nc * NB) return;
+  restrict_entry(F, Cl, b, t);
 }
 
-// Coarse diagonal blocks: D = geo + blockdiag(Ma, 3<vx^2> Mt, 3<vy^2> Mt); store D and D^{-1}.
-__global__ void coarse_diag_kernel(const double* geo, const double* Ma, const double* Mt,
-                                   double cx, double cy, int n, float* diag, float* dinv) {
+__global__ void prolong_add_kernel(LevelC F, LevelC Cl, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= F.nc * NB) return;
+  prolong_entry(F, Cl, b, t);
+}
+
+struct CoarseArgs {
+  int lc, nL, nu;
+  LevelC lv[kMaxLevels];
+  Coup K;
+};
+
+// The V-cycle from level lc down to the coarsest and back, one CTA per instance.  The levels are
+// small (<= kFuseCells cells), so phases are separated by block barriers instead of launches.
+__global__ void __launch_bounds__(512) coarse_vcycle_kernel(const CoarseArgs A, const uint8_t* active) {
+  const int b = blockIdx.x;
+  if (active && !active[b]) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  auto half_sweep = [&](const LevelC& L, int color) {
+    const int hx2 = (L.nx + 1) / 2;
+    for (int idx = tid; idx < hx2 * L.ny; idx += nt) {
+      const int j = idx / hx2, i = 2 * (idx % hx2) + ((j + color) & 1);
+      if (i < L.nx) rbgs_cell(L, A.K, b, j * L.nx + i);
+    }
+    __syncthreads();
+  };
+  int l = A.lc;
+  for (;; ++l) {  // down
+    const LevelC& L = A.lv[l];
+    for (int e = tid; e < L.nc * NB; e += nt) L.x[(size_t)b * L.nc * NB + e] = 0.f;
+    __syncthreads();
+    if (l == A.nL - 1) {  // coarsest: exact for one cell, else many sweeps
+      const int n = L.nc == 1 ? 1 : 30;
+      for (int k = 0; k < n; ++k) {
+        half_sweep(L, 0);
+        if (L.nc > 1) half_sweep(L, 1);
+      }
+      break;
+    }
+    for (int k = 0; k < A.nu; ++k) half_sweep(L, 0), half_sweep(L, 1);
+    for (int c = tid; c < L.nc; c += nt) residual_cell(L, A.K, b, c);
+    __syncthreads();
+    const LevelC& Cl = A.lv[l + 1];
+    for (int t = tid; t < Cl.nc * NB; t += nt) restrict_entry(L, Cl, b, t);
+    __syncthreads();
+  }
+  for (l = A.nL - 2; l >= A.lc; --l) {  // up
+    const LevelC& L = A.lv[l];
+    for (int t = tid; t < L.nc * NB; t += nt) prolong_entry(L, A.lv[l + 1], b, t);
+    __syncthreads();
+    for (int k = 0; k < A.nu; ++k) half_sweep(L, 1), half_sweep(L, 0);
+  }
+}
+
+// ---- set-up kernels: per (instance, class) mass blocks and diagonal blocks ---------------------
+
+// Masses of level l per (instance, class): materials sigma I; mixed cells sum_children P^T M P with
+// the children's masses taken from level l-1 by their classes.
+__global__ void class_mass_kernel(int l, int n_mat, int n_class, int n_class_f, int nxf, int nxc,
+                                  const int32_t* mixed, const int32_t* cls_f,
+                                  const double* sigma_t, const double* sigma_s, int B,
+                                  const double* Maf, const double* Mtf, double* Ma, double* Mt) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= B * n_class) return;
+  const int b = t / n_class, k = t % n_class;
+  double ma[16] = {0}, mt[16] = {0};
+  if (k < n_mat) {
+    const double st = sigma_t[b * n_mat + k], sa = st - sigma_s[b * n_mat + k];
+    for (int q = 0; q < 4; ++q) ma[5 * q] = sa, mt[5 * q] = st;
+  } else {
+    const int C = mixed[k - n_mat];
+    const int I = C % nxc, J = C / nxc;
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx) {
+        const int c = (2 * J + dy) * nxf + 2 * I + dx;
+        const double* fa = Maf + ((size_t)b * n_class_f + cls_f[c]) * 16;
+        const double* ft = Mtf + ((size_t)b * n_class_f + cls_f[c]) * 16;
+        for (int r = 0; r < 4; ++r)
+          for (int q = 0; q < 4; ++q) {
+            double sa = 0.0, stt = 0.0;
+            for (int kk = 0; kk < 4; ++kk) {
+              const double pr = pk(dx, dy, kk, r);
+              if (pr == 0.0) continue;
+              for (int ll = 0; ll < 4; ++ll) {
+                const double pq = pk(dx, dy, ll, q);
+                sa += pr * fa[4 * kk + ll] * pq;
+                stt += pr * ft[4 * kk + ll] * pq;
+              }
+            }
+            ma[4 * r + q] += sa;
+            mt[4 * r + q] += stt;
+          }
+      }
+  }
+  for (int e = 0; e < 16; ++e) Ma[(size_t)t * 16 + e] = ma[e], Mt[(size_t)t * 16 + e] = mt[e];
+}
+
+// D = geo + blockdiag(Ma, 3<vx^2> Mt, 3<vy^2> Mt) per (instance, class); store D, D^{-1} (FP32)
+// and, when diag64 != nullptr, D in FP64.
+__global__ void class_diag_kernel(const double* geo, const double* Ma, const double* Mt, double cx,
+                                  double cy, int n, float* diag, float* dinv, double* diag64) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   double a[NB * 24];
@@ -410,6 +523,7 @@ __global__ void coarse_diag_kernel(const double* geo, const double* Ma, const do
       a[r * 24 + c] = v;
       a[r * 24 + NB + c] = r == c ? 1.0 : 0.0;
       diag[(size_t)t * NB2 + r * NB + c] = (float)v;
+      if (diag64) diag64[(size_t)t * NB2 + r * NB + c] = v;
     }
   inv12<double>(a);
   for (int r = 0; r < NB; ++r)
@@ -621,13 +735,15 @@ struct DsaState {
   Blocks1D K1{};
   DevBuf<double> Dpinv, Mfac, work1;
   // 2D levels
-  int n_levels = 0;
-  std::vector<int> lnx, lny;
+  int n_levels = 0, lc = 0;                     // lc: first level of the fused coarse cycle
+  std::vector<int> lnx, lny, ncls;
+  std::vector<std::vector<int32_t>> cls_h, mixed_h;
+  Coup K{};
   DevBuf<double> off64, diag64;                 // level 0 in FP64 (Krylov operator)
-  std::vector<DevBuf<float>*> off32;            // [4][144] per level
-  std::vector<DevBuf<double>*> geo64;           // [144] per level >= 1 (geometric diagonal)
-  std::vector<DevBuf<float>*> diag32, dinv32;   // level 0: per material; coarser: per cell
-  std::vector<DevBuf<double>*> Ma, Mt;          // projected masses per cell, levels >= 1
+  std::vector<DevBuf<int32_t>*> cls, mixed;     // class per cell; mixed cells of each level
+  std::vector<DevBuf<double>*> geo64;           // [144] per level
+  std::vector<DevBuf<double>*> Ma, Mt;          // [B][n_class][16] per level
+  std::vector<DevBuf<float>*> diag32, dinv32;   // [B][n_class][144] per level
   std::vector<DevBuf<float>*> xl, bl, rl;       // per level FP32 vectors
   DevBuf<float> xtot, borig;                    // stationary multigrid accumulator and rhs
   int m = 20;                                   // FGMRES restart length
@@ -639,7 +755,7 @@ struct DsaState {
     v.clear();
   }
   ~DsaState() {
-    del(off32), del(geo64), del(diag32), del(dinv32), del(Ma), del(Mt), del(xl), del(bl), del(rl);
+    del(cls), del(mixed), del(geo64), del(Ma), del(Mt), del(diag32), del(dinv32), del(xl), del(bl), del(rl);
   }
 };
 
@@ -650,14 +766,20 @@ static Fine fine_of(rte_batch_t bt) {
   return Fine{s->off64.p, s->diag64.p, bt->disc->mat_id.p, bt->disc->n_mat};
 }
 
-static Lvl lvl_of(rte_batch_t bt, int l) {
+static LevelC lvl_of(rte_batch_t bt, int l) {
   DsaState* s = bt->dsa;
-  Lvl L{s->lnx[l], s->lny[l], s->lnx[l] * s->lny[l], s->off32[l]->p, s->diag32[l]->p,
-        s->dinv32[l]->p, l == 0 ? bt->disc->mat_id.p : nullptr, l == 0 ? bt->disc->n_mat : 0};
+  const rte_disc_s* d = bt->disc;
+  LevelC L{};
+  L.nx = s->lnx[l], L.ny = s->lny[l], L.nc = L.nx * L.ny, L.n_class = s->ncls[l];
+  L.cls = s->cls[l]->p;
+  L.diag = s->diag32[l]->p, L.dinv = s->dinv32[l]->p;
+  L.qx = (float)(1.0 / std::sqrt(d->hx * (1 << l)));
+  L.qy = (float)(1.0 / std::sqrt(d->hy * (1 << l)));
+  L.x = s->xl[l]->p, L.b = s->bl[l]->p, L.r = s->rl[l]->p;
   return L;
 }
 
-// constant neighbour blocks and geometric diagonal of a level with cell sizes (hx, hy)
+// constant neighbour blocks (FP64, for the Krylov operator) and geometric diagonal of a level
 static void level_blocks(const DsaMoments& mom, double hx, double hy, double off[4 * NB2],
                          double geo[NB2]) {
   const Ops1D ox = ops1d(hx), oy = ops1d(hy);
@@ -673,10 +795,107 @@ static void level_blocks(const DsaMoments& mom, double hx, double hy, double off
   field_block(mom, DCx[0], DJx[0], DCy[0], DJy[0], 0.0, 0.0, true, geo);
 }
 
+// field couplings of the trace form of the neighbour blocks (level independent)
+static Coup couplings(const DsaMoments& m) {
+  Coup K{};
+  const float W[9] = {(float)(-0.5 * m.abs_x), (float)(-1.5 * m.xx), 0.f,
+                      (float)(-0.5 * m.xx), (float)(-1.5 * m.abs3_x), 0.f,
+                      0.f, 0.f, (float)(-1.5 * m.yy_absx)};
+  const float E[9] = {(float)(-0.5 * m.abs_x), (float)(1.5 * m.xx), 0.f,
+                      (float)(0.5 * m.xx), (float)(-1.5 * m.abs3_x), 0.f,
+                      0.f, 0.f, (float)(-1.5 * m.yy_absx)};
+  const float S[9] = {(float)(-0.5 * m.abs_y), 0.f, (float)(-1.5 * m.yy),
+                      0.f, (float)(-1.5 * m.xx_absy), 0.f,
+                      (float)(-0.5 * m.yy), 0.f, (float)(-1.5 * m.abs3_y)};
+  const float N[9] = {(float)(-0.5 * m.abs_y), 0.f, (float)(1.5 * m.yy),
+                      0.f, (float)(-1.5 * m.xx_absy), 0.f,
+                      (float)(0.5 * m.yy), 0.f, (float)(-1.5 * m.abs3_y)};
+  for (int k = 0; k < 9; ++k) K.W[k] = W[k], K.E[k] = E[k], K.S[k] = S[k], K.N[k] = N[k];
+  return K;
+}
+
 template <class T>
 static int upload(DevBuf<T>& buf, const std::vector<T>& h) {
   RTE_TRY(buf.alloc(h.size()));
-  RTE_CUDA_TRY(cudaMemcpy(buf.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  if (!h.empty())
+    RTE_CUDA_TRY(cudaMemcpy(buf.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return RTE_OK;
+}
+
+// Levels, class tables and buffers: built once per batch (the material map is fixed).
+static int dsa_build_levels(rte_batch_t bt) {
+  const rte_disc_s* d = bt->disc;
+  const int B = bt->B;
+  DsaState* s = bt->dsa;
+  s->lnx.push_back(d->nx);
+  s->lny.push_back(d->ny);
+  while (s->lnx.back() % 2 == 0 && s->lny.back() % 2 == 0 && s->lnx.back() * s->lny.back() > 1 &&
+         (int)s->lnx.size() < kMaxLevels) {
+    s->lnx.push_back(s->lnx.back() / 2);
+    s->lny.push_back(s->lny.back() / 2);
+  }
+  s->n_levels = (int)s->lnx.size();
+  s->lc = s->n_levels - 1;
+  while (s->lc > 0 && s->lnx[s->lc - 1] * s->lny[s->lc - 1] <= kFuseCells) --s->lc;
+  s->K = couplings(d->mom);
+  for (int l = 0; l < s->n_levels; ++l) {
+    const int nx = s->lnx[l], ny = s->lny[l], nc = nx * ny;
+    std::vector<int32_t> cls(nc), mixed;
+    if (l == 0) {
+      cls = d->mat_host;
+    } else {
+      const auto& cf = s->cls_h[l - 1];
+      const int nxf = s->lnx[l - 1];
+      for (int C = 0; C < nc; ++C) {
+        const int I = C % nx, J = C / nx;
+        int k0 = -1;
+        bool pure = true;
+        for (int dy = 0; dy < 2; ++dy)
+          for (int dx = 0; dx < 2; ++dx) {
+            const int k = cf[(2 * J + dy) * nxf + 2 * I + dx];
+            if (k >= d->n_mat) pure = false;
+            if (k0 < 0) k0 = k;
+            else if (k != k0) pure = false;
+          }
+        if (pure) cls[C] = k0;
+        else cls[C] = d->n_mat + (int)mixed.size(), mixed.push_back(C);
+      }
+    }
+    s->ncls.push_back(d->n_mat + (int)mixed.size());
+    s->cls_h.push_back(cls);
+    s->mixed_h.push_back(mixed);
+    s->cls.push_back(new DevBuf<int32_t>());
+    RTE_TRY(upload(*s->cls.back(), cls));
+    s->mixed.push_back(new DevBuf<int32_t>());
+    RTE_TRY(upload(*s->mixed.back(), mixed));
+    std::vector<double> off(4 * NB2), geo(NB2);
+    level_blocks(d->mom, d->hx * (1 << l), d->hy * (1 << l), off.data(), geo.data());
+    if (l == 0) RTE_TRY(upload(s->off64, off));
+    s->geo64.push_back(new DevBuf<double>());
+    RTE_TRY(upload(*s->geo64.back(), geo));
+    const size_t ncl = (size_t)B * s->ncls[l];
+    for (auto* v : {&s->Ma, &s->Mt}) {
+      v->push_back(new DevBuf<double>());
+      RTE_TRY(v->back()->alloc(ncl * 16));
+    }
+    for (auto* v : {&s->diag32, &s->dinv32}) {
+      v->push_back(new DevBuf<float>());
+      RTE_TRY(v->back()->alloc(ncl * NB2));
+    }
+    for (auto* v : {&s->xl, &s->bl, &s->rl}) {
+      v->push_back(new DevBuf<float>());
+      RTE_TRY(v->back()->alloc((size_t)B * nc * NB));
+    }
+  }
+  RTE_TRY(s->diag64.alloc((size_t)B * d->n_mat * NB2));
+  const size_t n = (size_t)B * d->n_cells * NB;
+  RTE_TRY(s->xtot.alloc(n));
+  RTE_TRY(s->borig.alloc(n));
+  RTE_TRY(s->V.alloc((size_t)(s->m + 1) * n));
+  RTE_TRY(s->Z.alloc((size_t)s->m * n));
+  RTE_TRY(s->w.alloc(n));
+  RTE_TRY(s->xs.alloc(n));
+  RTE_TRY(s->dots_dev.alloc((size_t)B * (s->m + 1)));
   return RTE_OK;
 }
 
@@ -717,124 +936,49 @@ int dsa_setup(rte_batch_t bt, cudaStream_t st) {
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
   }
-  // ---- 2D: allocate the hierarchy once (coarsen 2x2 while both sizes are even) ---------------
-  if (s->n_levels == 0) {
-    s->lnx.push_back(d->nx);
-    s->lny.push_back(d->ny);
-    while (s->lnx.back() % 2 == 0 && s->lny.back() % 2 == 0 && s->lnx.back() * s->lny.back() > 1) {
-      s->lnx.push_back(s->lnx.back() / 2);
-      s->lny.push_back(s->lny.back() / 2);
-    }
-    s->n_levels = (int)s->lnx.size();
-    for (int l = 0; l < s->n_levels; ++l) {
-      const size_t nc = (size_t)s->lnx[l] * s->lny[l];
-      const double hx = d->hx * (1 << l), hy = d->hy * (1 << l);
-      std::vector<double> off(4 * NB2), geo(NB2);
-      level_blocks(d->mom, hx, hy, off.data(), geo.data());
-      s->off32.push_back(new DevBuf<float>());
-      RTE_TRY(upload(*s->off32.back(), std::vector<float>(off.begin(), off.end())));
-      s->geo64.push_back(new DevBuf<double>());
-      RTE_TRY(upload(*s->geo64.back(), geo));
-      if (l == 0) RTE_TRY(upload(s->off64, off));
-      const size_t ndiag = l == 0 ? (size_t)B * d->n_mat : (size_t)B * nc;
-      s->diag32.push_back(new DevBuf<float>());
-      s->dinv32.push_back(new DevBuf<float>());
-      RTE_TRY(s->diag32.back()->alloc(ndiag * NB2));
-      RTE_TRY(s->dinv32.back()->alloc(ndiag * NB2));
-      s->Ma.push_back(new DevBuf<double>());
-      s->Mt.push_back(new DevBuf<double>());
-      if (l >= 1) {
-        RTE_TRY(s->Ma.back()->alloc((size_t)B * nc * 16));
-        RTE_TRY(s->Mt.back()->alloc((size_t)B * nc * 16));
-      }
-      for (auto* v : {&s->xl, &s->bl, &s->rl}) {
-        v->push_back(new DevBuf<float>());
-        RTE_TRY(v->back()->alloc((size_t)B * nc * NB));
-      }
-    }
-    const size_t n = (size_t)B * d->n_cells * NB;
-    RTE_TRY(s->xtot.alloc(n));
-    RTE_TRY(s->borig.alloc(n));
-    RTE_TRY(s->V.alloc((size_t)(s->m + 1) * n));
-    RTE_TRY(s->Z.alloc((size_t)s->m * n));
-    RTE_TRY(s->w.alloc(n));
-    RTE_TRY(s->xs.alloc(n));
-    RTE_TRY(s->dots_dev.alloc((size_t)B * (s->m + 1)));
-  }
-  // ---- level 0: one diagonal block (and inverse) per instance and material -------------------
-  {
-    std::vector<double> off(4 * NB2), geo(NB2);
-    level_blocks(d->mom, d->hx, d->hy, off.data(), geo.data());
-    std::vector<double> diag((size_t)B * d->n_mat * NB2), dinv((size_t)B * d->n_mat * NB2);
-    for (int b = 0; b < B; ++b)
-      for (int m = 0; m < d->n_mat; ++m) {
-        const double stv = bt->sigma_t_h[(size_t)b * d->n_mat + m];
-        const double sav = stv - bt->sigma_s_h[(size_t)b * d->n_mat + m];
-        double* D = &diag[((size_t)b * d->n_mat + m) * NB2];
-        for (int e = 0; e < NB2; ++e) D[e] = geo[e];
-        for (int k = 0; k < 4; ++k) {
-          D[k * NB + k] += sav;
-          D[(4 + k) * NB + 4 + k] += 3.0 * d->mom.xx * stv;
-          D[(8 + k) * NB + 8 + k] += 3.0 * d->mom.yy * stv;
-        }
-        invert_host(D, &dinv[((size_t)b * d->n_mat + m) * NB2], NB);
-      }
-    RTE_TRY(upload(s->diag64, diag));
-    std::vector<float> d32(diag.begin(), diag.end()), i32(dinv.begin(), dinv.end());
-    RTE_CUDA_TRY(cudaMemcpy(s->diag32[0]->p, d32.data(), d32.size() * 4, cudaMemcpyHostToDevice));
-    RTE_CUDA_TRY(cudaMemcpy(s->dinv32[0]->p, i32.data(), i32.size() * 4, cudaMemcpyHostToDevice));
-  }
-  // ---- coarse levels: projected masses, diagonal blocks and their inverses ----------------------
-  for (int l = 1; l < s->n_levels; ++l) {
-    const int nxc = s->lnx[l], nyc = s->lny[l], nc = nxc * nyc;
-    const int n = nc * B;
-    mass_restrict_kernel<<<(n + 127) / 128, 128, 0, st>>>(
-        s->lnx[l - 1], nxc, nyc, B, l == 1 ? nullptr : s->Ma[l - 1]->p,
-        l == 1 ? nullptr : s->Mt[l - 1]->p, l == 1 ? d->mat_id.p : nullptr, bt->sigma_t.p,
-        bt->sigma_s.p, d->n_mat, s->Ma[l]->p, s->Mt[l]->p); RTE_NOTE_LAUNCH();
-    coarse_diag_kernel<<<(n + 63) / 64, 64, 0, st>>>(s->geo64[l]->p, s->Ma[l]->p, s->Mt[l]->p,
-                                                     3.0 * d->mom.xx, 3.0 * d->mom.yy, n,
-                                                     s->diag32[l]->p, s->dinv32[l]->p); RTE_NOTE_LAUNCH();
+  if (s->n_levels == 0) RTE_TRY(dsa_build_levels(bt));
+  // per parameter set: masses and diagonal blocks of every (instance, class), level by level
+  for (int l = 0; l < s->n_levels; ++l) {
+    const int n = B * s->ncls[l];
+    class_mass_kernel<<<(n + 127) / 128, 128, 0, st>>>(
+        l, d->n_mat, s->ncls[l], l ? s->ncls[l - 1] : 0, l ? s->lnx[l - 1] : 0, s->lnx[l],
+        s->mixed[l]->p, l ? s->cls[l - 1]->p : nullptr, bt->sigma_t.p, bt->sigma_s.p, B,
+        l ? s->Ma[l - 1]->p : nullptr, l ? s->Mt[l - 1]->p : nullptr, s->Ma[l]->p, s->Mt[l]->p); RTE_NOTE_LAUNCH();
+    class_diag_kernel<<<(n + 63) / 64, 64, 0, st>>>(s->geo64[l]->p, s->Ma[l]->p, s->Mt[l]->p,
+                                                    3.0 * d->mom.xx, 3.0 * d->mom.yy, n,
+                                                    s->diag32[l]->p, s->dinv32[l]->p,
+                                                    l == 0 ? s->diag64.p : nullptr); RTE_NOTE_LAUNCH();
     RTE_CUDA_TRY(cudaGetLastError());
   }
   return RTE_OK;
 }
 
-// One V-cycle on level l: x_l approximately solves A_l x = b_l (x_l starts at zero).
+// One V-cycle from level l: x_l approximately solves A_l x = b_l (x_l starts at zero).
 static int vcycle(rte_batch_t bt, int l, const uint8_t* active, cudaStream_t st, int nu) {
   DsaState* s = bt->dsa;
   const int B = bt->B;
-  const Lvl L = lvl_of(bt, l);
-  const int per = L.nc * NB;
-  float* x = s->xl[l]->p;
-  float* b = s->bl[l]->p;
-  float* r = s->rl[l]->p;
-  RTE_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(float) * (size_t)B * per, st));
-  const int ncol = ((L.nx + 1) / 2) * L.ny;
-  const dim3 gcol((ncol + 127) / 128, B);
-  const bool coarsest = l == s->n_levels - 1;
-  auto smooth = [&](int c0) {
-    rbgs_kernel<<<gcol, 128, 0, st>>>(L, c0, b, x, active); RTE_NOTE_LAUNCH();
-    rbgs_kernel<<<gcol, 128, 0, st>>>(L, 1 - c0, b, x, active); RTE_NOTE_LAUNCH();
-  };
-  if (coarsest && L.nc == 1) {  // exact: x = D^{-1} b
-    rbgs_kernel<<<gcol, 128, 0, st>>>(L, 0, b, x, active); RTE_NOTE_LAUNCH();
+  if (l >= s->lc) {  // the rest of the cycle in one launch, one CTA per instance
+    CoarseArgs A{};
+    A.lc = l, A.nL = s->n_levels, A.nu = nu, A.K = s->K;
+    for (int k = 0; k < s->n_levels; ++k) A.lv[k] = lvl_of(bt, k);
+    coarse_vcycle_kernel<<<B, 512, 0, st>>>(A, active); RTE_NOTE_LAUNCH();
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
   }
-  const int npre = coarsest ? 30 : nu;
-  for (int k = 0; k < npre; ++k) smooth(0);
-  if (!coarsest) {
-    residual_kernel<<<dim3((L.nc + 127) / 128, B), 128, 0, st>>>(L, b, x, r, active); RTE_NOTE_LAUNCH();
-    const int nxc = s->lnx[l + 1], nyc = s->lny[l + 1];
-    const int nco = nxc * nyc * NB;
-    restrict_kernel<<<dim3((nco + 255) / 256, B), 256, 0, st>>>(L.nx, nxc, nyc, r, s->bl[l + 1]->p,
-                                                                active); RTE_NOTE_LAUNCH();
-    RTE_TRY(vcycle(bt, l + 1, active, st, nu));
-    prolong_add_kernel<<<dim3((per + 255) / 256, B), 256, 0, st>>>(L.nx, L.ny, s->xl[l + 1]->p, x,
-                                                                   active); RTE_NOTE_LAUNCH();
-    for (int k = 0; k < nu; ++k) smooth(1);
-  }
+  const LevelC L = lvl_of(bt, l), Cl = lvl_of(bt, l + 1);
+  RTE_CUDA_TRY(cudaMemsetAsync(L.x, 0, sizeof(float) * (size_t)B * L.nc * NB, st));
+  const int ncol = ((L.nx + 1) / 2) * L.ny;
+  const dim3 gcol((ncol + 127) / 128, B);
+  auto smooth = [&](int c0) {
+    rbgs_kernel<<<gcol, 128, 0, st>>>(L, s->K, c0, active); RTE_NOTE_LAUNCH();
+    rbgs_kernel<<<gcol, 128, 0, st>>>(L, s->K, 1 - c0, active); RTE_NOTE_LAUNCH();
+  };
+  for (int k = 0; k < nu; ++k) smooth(0);
+  residual_kernel<<<dim3((L.nc + 127) / 128, B), 128, 0, st>>>(L, s->K, active); RTE_NOTE_LAUNCH();
+  restrict_kernel<<<dim3((Cl.nc * NB + 255) / 256, B), 256, 0, st>>>(L, Cl, active); RTE_NOTE_LAUNCH();
+  RTE_TRY(vcycle(bt, l + 1, active, st, nu));
+  prolong_add_kernel<<<dim3((L.nc * NB + 255) / 256, B), 256, 0, st>>>(L, Cl, active); RTE_NOTE_LAUNCH();
+  for (int k = 0; k < nu; ++k) smooth(1);
   RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;
 }
@@ -864,6 +1008,18 @@ __global__ void extract_rho32_kernel(const float* x, double* drho, int nc, const
   drho[(size_t)b * nc * 4 + t] = (double)x[((size_t)b * nc + c) * NB + k];
 }
 
+// residual on level 0 against an explicit right-hand side and iterate: r0 = borig - A0 xtot
+__global__ void residual_ext_kernel(LevelC L, Coup K, const float* bvec, const float* xv, float* r,
+                                    const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.nc) return;
+  LevelC M = L;
+  M.b = const_cast<float*>(bvec), M.x = const_cast<float*>(xv), M.r = r;
+  residual_cell(M, K, b, c);
+}
+
 // Stationary multigrid: k V-cycles on the FP32 system, x <- x + V(b - A x), no host round trip.
 static int dsa2d_vcycles(rte_batch_t bt, const double* R, double* drho, int k,
                          const uint8_t* active, cudaStream_t st) {
@@ -871,20 +1027,20 @@ static int dsa2d_vcycles(rte_batch_t bt, const double* R, double* drho, int k,
   const int B = bt->B, nc = bt->disc->n_cells, per = nc * NB;
   const dim3 gv((per + 255) / 256, B), gvc(std::min((per + 255) / 256, 1024), B);
   pack_rhs32_kernel<<<gv, 256, 0, st>>>(R, s->borig.p, nc, active); RTE_NOTE_LAUNCH();
-  const Lvl L0 = lvl_of(bt, 0);
+  const LevelC L0 = lvl_of(bt, 0);
   for (int it = 0; it < k; ++it) {
     if (it == 0) {
       RTE_CUDA_TRY(cudaMemcpyAsync(s->bl[0]->p, s->borig.p, sizeof(float) * (size_t)B * per,
                                    cudaMemcpyDeviceToDevice, st));
     } else {
-      residual_kernel<<<dim3((nc + 127) / 128, B), 128, 0, st>>>(L0, s->borig.p, s->xtot.p,
-                                                               s->bl[0]->p, active); RTE_NOTE_LAUNCH();
+      residual_ext_kernel<<<dim3((nc + 127) / 128, B), 128, 0, st>>>(L0, s->K, s->borig.p, s->xtot.p,
+                                                                   s->bl[0]->p, active); RTE_NOTE_LAUNCH();
     }
     RTE_TRY(vcycle(bt, 0, active, st, 2));
-    if (it == 0)
+    if (it == 0) {
       RTE_CUDA_TRY(cudaMemcpyAsync(s->xtot.p, s->xl[0]->p, sizeof(float) * (size_t)B * per,
                                    cudaMemcpyDeviceToDevice, st));
-    else {
+    } else {
       add32_kernel<<<gvc, 256, 0, st>>>(s->xl[0]->p, s->xtot.p, per, active); RTE_NOTE_LAUNCH();
     }
   }

@@ -118,7 +118,7 @@ __global__ void tables1d_kernel(double* tables, const double* sigma_t, const dou
 }
 
 struct Sweep2DArgs {
-  const double* rho_in;
+  const double* rho_in;     // or, when the kernel is instantiated with PRESRC, the sources S
   double* partial;
   double* psi_out;
   const uint8_t* active;
@@ -133,7 +133,7 @@ struct Sweep2DArgs {
   double sq_area;
 };
 
-template <int DPW, bool SMEM_TAB>
+template <int DPW, bool SMEM_TAB, bool PRESRC = false>
 __global__ void __launch_bounds__(32) sweep2d_kernel(const Sweep2DArgs A) {
   const int g = blockIdx.x, b = blockIdx.y, lane = threadIdx.x;
   if (A.active && !A.active[b]) return;
@@ -204,11 +204,16 @@ __global__ void __launch_bounds__(32) sweep2d_kernel(const Sweep2DArgs A) {
       const int j = yneg ? A.ny - 1 - r : r;
       const int c = j * A.nx + i;
       const int m = A.mat[c];
-      const double ss = sig_s[m];
       const double2 r01 = reinterpret_cast<const double2*>(rin + 4 * (size_t)c)[0];
       const double2 r23 = reinterpret_cast<const double2*>(rin + 4 * (size_t)c)[1];
-      const double s0 = fma(ss, r01.x, A.with_source ? G0[c] : 0.0);
-      const double s1 = ss * r01.y, s2 = ss * r23.x, s3v = ss * r23.y;
+      double s0, s1, s2, s3v;
+      if (PRESRC) {  // sources formed once per sweep by cell_source_kernel
+        s0 = r01.x, s1 = r01.y, s2 = r23.x, s3v = r23.y;
+      } else {
+        const double ss = sig_s[m];
+        s0 = fma(ss, r01.x, A.with_source ? G0[c] : 0.0);
+        s1 = ss * r01.y, s2 = ss * r23.x, s3v = ss * r23.y;
+      }
       double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
 #pragma unroll
       for (int dd = 0; dd < DPW; ++dd) {
@@ -256,6 +261,24 @@ __global__ void __launch_bounds__(32) sweep2d_kernel(const Sweep2DArgs A) {
     }
     __syncwarp();
   }
+}
+
+// S = Sigma_s rho + G (zeroth moment only; G omitted without source): the right-hand side shared
+// by all directions of a sweep, formed once per cell instead of once per direction warp.
+__global__ void cell_source_kernel(const double* __restrict__ rho, double* S,
+                                   const double* __restrict__ sigma_s, const double* __restrict__ G0,
+                                   const int32_t* __restrict__ mat, const uint8_t* active,
+                                   int n_cells, int n_mat, int with_source) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  const double ss = sigma_s[(size_t)b * n_mat + mat[c]];
+  const double2* r = reinterpret_cast<const double2*>(rho + ((size_t)b * n_cells + c) * 4);
+  const double2 a = r[0], e = r[1];
+  double2* o = reinterpret_cast<double2*>(S + ((size_t)b * n_cells + c) * 4);
+  o[0] = make_double2(fma(ss, a.x, with_source ? G0[(size_t)b * n_cells + c] : 0.0), ss * a.y);
+  o[1] = make_double2(ss * e.x, ss * e.y);
 }
 
 struct Sweep1DArgs {
@@ -415,21 +438,22 @@ int setup_tables(rte_batch_t bt, cudaStream_t st) {
   return RTE_OK;
 }
 
-template <int DPW>
+template <int DPW, bool PRESRC = false>
 static int launch2d(const Sweep2DArgs& A, int B, int n_groups, cudaStream_t st) {
   const size_t ybytes = (size_t)A.nx * DPW * 2 * sizeof(double);
   const size_t tbytes = (size_t)A.n_mat * DPW * kTab2D * sizeof(double);
   const size_t sbytes = (size_t)A.n_mat * sizeof(double);
   dim3 grid(n_groups, B);
   if (ybytes + tbytes + sbytes <= 48 * 1024) {
-    sweep2d_kernel<DPW, true><<<grid, 32, ybytes + tbytes + sbytes, st>>>(A); RTE_NOTE_LAUNCH();
+    sweep2d_kernel<DPW, true, PRESRC><<<grid, 32, ybytes + tbytes + sbytes, st>>>(A); RTE_NOTE_LAUNCH();
   } else {
     const size_t bytes = ybytes + sbytes;
     if (bytes > 200 * 1024) return fail(RTE_EINVAL, "sweep: mesh row too long for shared memory");
-    if (bytes > 48 * 1024)
-      RTE_CUDA_TRY(cudaFuncSetAttribute(sweep2d_kernel<DPW, false>,
+    if (bytes > 48 * 1024) {
+      RTE_CUDA_TRY(cudaFuncSetAttribute(sweep2d_kernel<DPW, false, PRESRC>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-    sweep2d_kernel<DPW, false><<<grid, 32, bytes, st>>>(A); RTE_NOTE_LAUNCH();
+    }
+    sweep2d_kernel<DPW, false, PRESRC><<<grid, 32, bytes, st>>>(A); RTE_NOTE_LAUNCH();
   }
   RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;
@@ -448,15 +472,18 @@ int sweep_launch(rte_batch_t bt, const double* rho_in, double* rho_out, double* 
     RTE_CUDA_TRY(cudaEventRecord(ev0, st));
   }
   if (d->dim == 2) {
-    Sweep2DArgs A{rho_in,       bt->partial.p, psi_out,        active,      bt->tables.p,
+    cell_source_kernel<<<dim3((d->n_cells + 127) / 128, bt->B), 128, 0, st>>>(
+        rho_in, bt->S.p, bt->sigma_s.p, bt->G0.p, d->mat_id.p, active, d->n_cells, d->n_mat,
+        with_source); RTE_NOTE_LAUNCH();
+    Sweep2DArgs A{bt->S.p,      bt->partial.p, psi_out,        active,      bt->tables.p,
                   bt->sigma_s.p, bt->G0.p,     bt->inflow.p,   d->mat_id.p, d->dir_dev.p,
                   bt->groups_dev.p, d->nx,     d->ny,          d->n_cells,  d->n_dof,
                   d->n_mat,     d->n_dirs,     n_groups,       with_source, std::sqrt(d->hx * d->hy)};
     switch (bt->dpw) {
-      case 1: RTE_TRY(launch2d<1>(A, bt->B, n_groups, st)); break;
-      case 2: RTE_TRY(launch2d<2>(A, bt->B, n_groups, st)); break;
-      case 4: RTE_TRY(launch2d<4>(A, bt->B, n_groups, st)); break;
-      case 8: RTE_TRY(launch2d<8>(A, bt->B, n_groups, st)); break;
+      case 1: RTE_TRY((launch2d<1, true>(A, bt->B, n_groups, st))); break;
+      case 2: RTE_TRY((launch2d<2, true>(A, bt->B, n_groups, st))); break;
+      case 4: RTE_TRY((launch2d<4, true>(A, bt->B, n_groups, st))); break;
+      case 8: RTE_TRY((launch2d<8, true>(A, bt->B, n_groups, st))); break;
       default: return fail(RTE_EINVAL, "unsupported directions-per-warp");
     }
   } else {
