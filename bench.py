@@ -74,9 +74,23 @@ def dist_init():
     if ws > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
     return ws, rank, local
+
+
+def test_seeds(rank, B):
+    """Test-instance seeds of one rank: instances are sharded across ranks (weak scaling)."""
+    from paper_2402_10488_gb300 import inputs
+    return [inputs.TEST_SEED0 + rank * B + k for k in range(B)]
+
+
+def _reduce_device():
+    import torch.distributed as dist
+    return "cuda" if dist.get_backend() == "nccl" else "cpu"
 
 
 def barrier(ws):
@@ -90,7 +104,7 @@ def max_over_ranks(ws, x):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_reduce_device())
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -100,9 +114,14 @@ def sum_over_ranks(ws, x):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_reduce_device())
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def job_throughput(ws, solves_local, seconds_local):
+    """Whole-job solves/s: solves of all ranks over the slowest rank's timed region."""
+    return sum_over_ranks(ws, solves_local) / max_over_ranks(ws, seconds_local)
 
 
 # ---- clocks ----------------------------------------------------------------------------------
@@ -167,8 +186,7 @@ def run_ours(a, ws, rank, local):
     nphi = a.angles // nvz
     B = a.batch
     train = inputs.lattice(a.n, a.angles, [inputs.TRAIN_SEED0 + k for k in range(a.ntrain)], nvz)
-    test = inputs.lattice(a.n, a.angles,
-                          [inputs.TEST_SEED0 + rank * B + k for k in range(B)], nvz)
+    test = inputs.lattice(a.n, a.angles, test_seeds(rank, B), nvz)
     disc = rte.Disc(train, device=dev)
     tb = rte.Batch(disc, train.batch)
     tb.set_params(train)
@@ -233,12 +251,13 @@ def run_ours(a, ws, rank, local):
         if prof:
             torch.cuda.profiler.stop()
         barrier(ws)
-        sweep_ms, launches, units = batch.timing(0)
+        ph = batch.timing(0)
+        sweep_ms, launches, units = ph["sweep_ms"], ph["sweep_launches"], ph["sweep_units"]
         n_launch = rte.launch_count() - launches0
         got = (hbuf.numpy() if host else rho.cpu().numpy())
         err = np.abs(got - ref_np).max(1) / np.abs(ref_np).max(1)
         return dict(times=np.array(times), reps=reps, err=err, sweep_ms=sweep_ms,
-                    sweep_launches=launches, sweep_units=units, launches=n_launch)
+                    sweep_launches=launches, sweep_units=units, launches=n_launch, phases=ph)
 
     results = {}
     clocks = ClockSampler(dev)
@@ -258,15 +277,15 @@ def run_ours(a, ws, rank, local):
                     n_dsa_mean=float(np.mean([x["n_dsa"] for x in r["reps"]])),
                     dsa_iters_mean=float(np.mean([x["dsa_iters"] for x in r["reps"]])),
                     sweep_share=r["sweep_ms"] / float(np.sum(r["times"])),
+                    phase_share={k: r["phases"][k + "_ms"] / float(np.sum(r["times"]))
+                                 for k in ("sweep", "dsa", "rom", "setup")},
                     p50_ms=float(np.percentile(r["times"], 50)),
                     p99_ms=float(np.percentile(r["times"], 99)))
 
     summ = {m: summary(r) for m, r in results.items()}
     head = results["romsad"]
     t_local = float(np.sum(head["times"])) / 1e3
-    t_max = max_over_ranks(ws, t_local)
-    solved = sum_over_ranks(ws, float(summ["romsad"]["solves_ok"] * a.steps))
-    value = solved / t_max
+    value = job_throughput(ws, float(summ["romsad"]["solves_ok"] * a.steps), t_local)
     # roofline of the dominant kernel (the sweep), from its CUDA-event time inside the timed region
     flops = head["sweep_units"] * FLOP_PER_CELL_DIR
     achieved = flops / (head["sweep_ms"] / 1e3) / 1e12

@@ -159,9 +159,11 @@ int rte_sweep_static(rte_batch_t batch, const double* rho_in, double* rho_out, i
 
 /* Sweep-kernel timing for throughput and roofline accounting.  Each 2D/1D sweep kernel launched
  * for this batch while timing is on is bracketed by CUDA events recorded on the stream it is
- * launched on.  out (HOST double[3], may be NULL) receives (total sweep-kernel milliseconds,
- * number of timed launches, cell x distinct-direction local solves they performed); the call
- * waits for the recorded events.  enable = 1 resets and starts, 0 resets and stops, -1 only
+ * launched on, and so is each DSA correction, each ROM step (ROMSA correction, ROMIG, reduced
+ * operator assembly) and each per-instance set-up.  out (HOST double[9], may be NULL) receives
+ * (sweep-kernel ms, timed sweep launches, cell x distinct-direction local solves they performed,
+ * DSA ms, DSA calls, ROM ms, ROM calls, set-up ms, set-up calls); the call waits for the
+ * recorded events.  enable = 1 resets and starts, 0 resets and stops, -1 only
  * reads.  Errors: RTE_EINVAL, RTE_ECUDA. */
 int rte_batch_timing(rte_batch_t batch, int enable, double* out);
 

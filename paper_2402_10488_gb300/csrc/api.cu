@@ -291,6 +291,10 @@ rte_batch_s::~rte_batch_s() {
     cudaEventDestroy(e.first);
     cudaEventDestroy(e.second);
   }
+  for (auto& e : phase_ev) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
 }
 
 extern "C" int rte_counters(int64_t* out) {
@@ -302,24 +306,40 @@ extern "C" int rte_counters(int64_t* out) {
 extern "C" int rte_batch_timing(rte_batch_t b, int enable, double* out) {
   if (!b) return fail(RTE_EINVAL, "rte_batch_timing: null argument");
   DeviceGuard g(b->disc->device);
-  double ms = 0.0;
+  double ms = 0.0, pms[4] = {0, 0, 0, 0};
   for (auto& e : b->sweep_ev) {
     RTE_CUDA_TRY(cudaEventSynchronize(e.second));
     float t = 0.f;
     RTE_CUDA_TRY(cudaEventElapsedTime(&t, e.first, e.second));
     ms += t;
   }
+  for (auto& e : b->phase_ev) {
+    RTE_CUDA_TRY(cudaEventSynchronize(e.b));
+    float t = 0.f;
+    RTE_CUDA_TRY(cudaEventElapsedTime(&t, e.a, e.b));
+    pms[e.phase] += t;
+  }
   if (out) {
     out[0] = ms;
     out[1] = (double)b->sweep_launches;
     out[2] = b->sweep_units;
+    for (int p = 1; p <= 3; ++p) {
+      out[1 + 2 * p] = pms[p];
+      out[2 + 2 * p] = (double)b->phase_calls[p];
+    }
   }
   if (enable >= 0) {
     for (auto& e : b->sweep_ev) {
       cudaEventDestroy(e.first);
       cudaEventDestroy(e.second);
     }
+    for (auto& e : b->phase_ev) {
+      cudaEventDestroy(e.a);
+      cudaEventDestroy(e.b);
+    }
     b->sweep_ev.clear();
+    b->phase_ev.clear();
+    for (auto& c : b->phase_calls) c = 0;
     b->sweep_units = 0.0;
     b->sweep_launches = 0;
     b->timing = enable != 0;
@@ -402,8 +422,11 @@ extern "C" int rte_batch_set_params(rte_batch_t b, const double* sigma_t, const 
   RTE_CUDA_TRY(cudaMemcpy(b->G0.p, g0.data(), sizeof(double) * nc, cudaMemcpyHostToDevice));
   RTE_CUDA_TRY(cudaMemcpy(b->inflow.p, b->inflow_h.data(), sizeof(double) * 4 * b->B,
                           cudaMemcpyHostToDevice));
-  RTE_TRY(setup_tables(b, 0));
-  RTE_TRY(dsa_setup(b, 0));
+  {
+    PhaseScope ps(b, 3, 0);
+    RTE_TRY(setup_tables(b, 0));
+    RTE_TRY(dsa_setup(b, 0));
+  }
   RTE_CUDA_TRY(cudaDeviceSynchronize());
   b->params_set = true;
   return RTE_OK;

@@ -143,10 +143,34 @@ struct rte_batch_s {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> sweep_ev;
   double sweep_units = 0.0;   // cell x distinct-direction solves in the timed sweeps
   long long sweep_launches = 0;
+  struct PhaseEv { int phase; cudaEvent_t a, b; };
+  std::vector<PhaseEv> phase_ev;   // phases: 1 DSA, 2 ROM, 3 set-up
+  long long phase_calls[4] = {0, 0, 0, 0};
   ~rte_batch_s();
 };
 
 namespace rte {
+// Brackets one phase of work on `st` with CUDA events when the batch is timing (no-op otherwise).
+struct PhaseScope {
+  rte_batch_t b;
+  int phase;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  PhaseScope(rte_batch_t b_, int phase_, cudaStream_t st_) : b(b_), phase(phase_), st(st_) {
+    if (b->timing && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, st);
+  }
+  ~PhaseScope() {
+    if (!a) return;
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) == cudaSuccess) {
+      cudaEventRecord(e, st);
+      b->phase_ev.push_back({phase, a, e});
+      b->phase_calls[phase] += 1;
+    } else {
+      cudaEventDestroy(a);
+    }
+  }
+};
 void make_groups(rte_batch_t b);
 int auto_dpw(const rte_disc_s* disc, int B);
 // sweep.cu

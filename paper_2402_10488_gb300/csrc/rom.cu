@@ -638,6 +638,7 @@ extern "C" int rte_rom_initial_guess(rte_rom_t rom, rte_batch_t b, double* rho0,
     if (g != 0.0) return fail(RTE_EINVAL, "ROMIG supports vacuum inflow only (U^T b = (U^iso)^T G)");
   DeviceGuard g(b->disc->device);
   cudaStream_t st = (cudaStream_t)stream;
+  PhaseScope ps(b, 2, st);
   RTE_TRY(rom_prepare(rom, b, st));
   const int r = rom->r, n = b->disc->n_dof, B = b->B, P = b->disc->P;
   // rhs_i = sum_c U_iso[i][c*P + 0] G0[c]: the source has only its zeroth moment

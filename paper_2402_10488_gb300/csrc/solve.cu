@@ -32,7 +32,10 @@ int run_si(rte_batch_t bt, const rte_solve_opts* o, rte_rom_t rom_c, double* rho
   for (auto& r : rep) r = rte_solve_report{0, 0, 0, 0, 0, 0.0, 0.0};
   if ((o->sa == RTE_SA_ROMSA || o->sa == RTE_SA_ROMSAD) && !rom_c)
     return fail(RTE_EINVAL, "ROMSA/ROMSAD need a correction ROM");
-  if (rom_c) RTE_TRY(rom_prepare(rom_c, bt, st));
+  if (rom_c) {
+    PhaseScope ps(bt, 2, st);
+    RTE_TRY(rom_prepare(rom_c, bt, st));
+  }
   std::vector<double> norms(2 * B);
   std::vector<int> iters(B);
   int status = RTE_OK;
@@ -87,6 +90,7 @@ int run_si(rte_batch_t bt, const rte_solve_opts* o, rte_rom_t rom_c, double* rho
     for (int b = 0; b < B; ++b) anyd |= use_dsa[b] != 0, anyr |= use_rom[b] != 0;
     if (anyd) {
       RTE_CUDA_TRY(cudaMemcpyAsync(dsa_dev.p, use_dsa.data(), B, cudaMemcpyHostToDevice, st));
+      PhaseScope ps(bt, 1, st);
       int s = dsa_apply(bt, R, drho, o->dsa_rtol, o->dsa_max_it, dsa_dev.p, iters.data(), st);
       if (s != RTE_OK && s != RTE_ENOCONV) return s;
       for (int b = 0; b < B; ++b)
@@ -94,6 +98,7 @@ int run_si(rte_batch_t bt, const rte_solve_opts* o, rte_rom_t rom_c, double* rho
     }
     if (anyr) {
       RTE_CUDA_TRY(cudaMemcpyAsync(rom_dev.p, use_rom.data(), B, cudaMemcpyHostToDevice, st));
+      PhaseScope ps(bt, 2, st);
       RTE_TRY(rom_correction(rom_c, bt, R, drho, rom_dev.p, st));
     }
     // rho^(l) = rho^(l,*) + delta rho^(l), written into the rho_prev slot

@@ -197,10 +197,13 @@ class Batch:
         check(lib().rte_batch_tune(self.h, int(dirs_per_warp)))
 
     def timing(self, enable):
-        """enable=1 reset+start, 0 reset+stop, -1 read; returns (sweep_ms, launches, units)."""
-        out = np.zeros(3)
+        """enable=1 reset+start, 0 reset+stop, -1 read.  Returns a dict of phase times (ms) and
+        counts: sweep (kernel only), dsa, rom, setup."""
+        out = np.zeros(9)
         check(lib().rte_batch_timing(self.h, int(enable), out.ctypes.data_as(_P)))
-        return float(out[0]), int(out[1]), float(out[2])
+        return dict(sweep_ms=float(out[0]), sweep_launches=int(out[1]), sweep_units=float(out[2]),
+                    dsa_ms=float(out[3]), dsa_calls=int(out[4]), rom_ms=float(out[5]),
+                    rom_calls=int(out[6]), setup_ms=float(out[7]), setup_calls=int(out[8]))
 
     def directions(self):
         d = np.zeros((self.disc.n_dirs, 4))
