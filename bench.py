@@ -49,17 +49,19 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--batch", type=int, default=32, help="test instances per step per GPU")
+    ap.add_argument("--batch", type=int, default=64, help="test instances per step per GPU")
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--angles", type=int, default=64)
     ap.add_argument("--ntrain", type=int, default=32)
     ap.add_argument("--rank", type=int, default=20)
     ap.add_argument("--eps", type=float, default=2e-7, help="relative stop tolerance")
     ap.add_argument("--dsa-rtol", type=float, default=0.0, help="0: fixed V-cycles")
-    ap.add_argument("--dsa-vcycles", type=int, default=2)
+    ap.add_argument("--dsa-vcycles", type=int, default=1)
+    ap.add_argument("--fp32-switch", type=float, default=1e-5,
+                    help="precision variant: FP32 sweeps until the relative change is below this")
     ap.add_argument("--dpw", type=int, default=0, help="sweep directions per warp (0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--methods", default="romsad,si_dsa,romig")
+    ap.add_argument("--methods", default="romsad,si_dsa,romig,romsad_mixed")
     ap.add_argument("--profile-window", action="store_true",
                     help="bracket the timed ROMSAD steps with cudaProfilerStart/Stop (for ncu)")
     return ap.parse_args()
@@ -215,6 +217,9 @@ def run_ours(a, ws, rank, local):
             sa, kw = rte.SA_DSA, {}
         elif method == "romsad":
             sa, kw = rte.SA_ROMSAD, dict(rom_c=rom_c, theta=5, eps_romsad=eps_romsad)
+        elif method == "romsad_mixed":
+            sa, kw = rte.SA_ROMSAD, dict(rom_c=rom_c, theta=5, eps_romsad=eps_romsad,
+                                         fp32_switch=a.fp32_switch)
         else:
             sa, kw = rte.SA_DSA, {}
         rep, _, st = batch.solve(rho, a.eps, sa=sa, rel=True, max_iter=400, dsa_rtol=a.dsa_rtol,
@@ -276,9 +281,13 @@ def run_ours(a, ws, rank, local):
                     n_romsa_mean=float(np.mean([x["n_romsa"] for x in r["reps"]])),
                     n_dsa_mean=float(np.mean([x["n_dsa"] for x in r["reps"]])),
                     dsa_iters_mean=float(np.mean([x["dsa_iters"] for x in r["reps"]])),
+                    n_sweep32_mean=float(np.mean([x["n_sweep32"] for x in r["reps"]])),
                     sweep_share=r["sweep_ms"] / float(np.sum(r["times"])),
                     phase_share={k: r["phases"][k + "_ms"] / float(np.sum(r["times"]))
-                                 for k in ("sweep", "dsa", "rom", "setup")},
+                                 for k in ("sweep", "sweep32", "dsa", "rom", "setup")},
+                    sweep32_tflops=(r["phases"]["sweep32_units"] * FLOP_PER_CELL_DIR /
+                                    (r["phases"]["sweep32_ms"] / 1e3) / 1e12
+                                    if r["phases"]["sweep32_ms"] > 0 else None),
                     p50_ms=float(np.percentile(r["times"], 50)),
                     p99_ms=float(np.percentile(r["times"], 99)))
 

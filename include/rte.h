@@ -160,10 +160,11 @@ int rte_sweep_static(rte_batch_t batch, const double* rho_in, double* rho_out, i
 /* Sweep-kernel timing for throughput and roofline accounting.  Each 2D/1D sweep kernel launched
  * for this batch while timing is on is bracketed by CUDA events recorded on the stream it is
  * launched on, and so is each DSA correction, each ROM step (ROMSA correction, ROMIG, reduced
- * operator assembly) and each per-instance set-up.  out (HOST double[9], may be NULL) receives
- * (sweep-kernel ms, timed sweep launches, cell x distinct-direction local solves they performed,
- * DSA ms, DSA calls, ROM ms, ROM calls, set-up ms, set-up calls); the call waits for the
- * recorded events.  enable = 1 resets and starts, 0 resets and stops, -1 only
+ * operator assembly), each per-instance set-up and each FP32 sweep (sources, sweep, no reduction).
+ * out (HOST double[12], may be NULL) receives (FP64 sweep-kernel ms, timed FP64 sweep launches,
+ * cell x distinct-direction local solves they performed, DSA ms, DSA calls, ROM ms, ROM calls,
+ * set-up ms, set-up calls, FP32 sweep ms, FP32 sweep calls, their cell x direction solves); the
+ * call waits for the recorded events.  enable = 1 resets and starts, 0 resets and stops, -1 only
  * reads.  Errors: RTE_EINVAL, RTE_ECUDA. */
 int rte_batch_timing(rte_batch_t batch, int enable, double* out);
 
@@ -250,6 +251,10 @@ typedef struct {
   int dsa_max_it;      /* 2D DSA: iteration cap, or the number of V-cycles when dsa_rtol == 0  */
   const uint8_t* schedule; /* HOST uint8[max_iter] or NULL: forces ROMSAD's choice per
                               iteration (1 = ROMSA, 0 = DSA), for reproducibility tests      */
+  double fp32_switch;  /* precision variant (2D): 0 -- every sweep in FP64; > 0 -- an instance
+                          sweeps in FP32 until its stop-test quantity falls below fp32_switch,
+                          then in FP64 until the stop test fires, so the FP64 sweeps supply the
+                          final digits (the fixed point is the FP64 one)                      */
 } rte_solve_opts;
 
 typedef struct {
@@ -260,6 +265,7 @@ typedef struct {
   int dsa_iters;       /* total DSA Krylov iterations                                       */
   double last_change;  /* last ||rho* - rho||_inf                                           */
   double rho_inf;      /* ||rho*||_inf at exit                                              */
+  int n_sweep32;       /* of the n_sweep sweeps, those done in FP32                          */
 } rte_solve_report;
 
 /* Runs Alg. 1 on every instance of the batch, each stopping on its own test.

@@ -67,7 +67,7 @@ static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w
 
 using namespace rte;
 
-extern "C" int rte_version(void) { return 10000; }
+extern "C" int rte_version(void) { return 10100; }
 extern "C" const char* rte_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" int rte_disc_create(const rte_disc_desc* d, int device, rte_disc_t* out) {
@@ -327,6 +327,9 @@ extern "C" int rte_batch_timing(rte_batch_t b, int enable, double* out) {
       out[1 + 2 * p] = pms[p];
       out[2 + 2 * p] = (double)b->phase_calls[p];
     }
+    out[9] = pms[0];
+    out[10] = (double)b->phase_calls[0];
+    out[11] = b->sweep32_units;
   }
   if (enable >= 0) {
     for (auto& e : b->sweep_ev) {
@@ -341,6 +344,7 @@ extern "C" int rte_batch_timing(rte_batch_t b, int enable, double* out) {
     b->phase_ev.clear();
     for (auto& c : b->phase_calls) c = 0;
     b->sweep_units = 0.0;
+    b->sweep32_units = 0.0;
     b->sweep_launches = 0;
     b->timing = enable != 0;
   }
@@ -425,6 +429,7 @@ extern "C" int rte_batch_set_params(rte_batch_t b, const double* sigma_t, const 
   {
     PhaseScope ps(b, 3, 0);
     RTE_TRY(setup_tables(b, 0));
+    b->tables32_stale = true;
     RTE_TRY(dsa_setup(b, 0));
   }
   RTE_CUDA_TRY(cudaDeviceSynchronize());

@@ -37,12 +37,15 @@ int fail(int code, const std::string& msg);
     if (_s != RTE_OK) return _s;                                                              \
   } while (0)
 
-// Switches the calling thread to the handle's device for the scope of a call.
+// Switches the calling thread to the handle's device for the scope of a call, and clears an
+// error that other code on this thread left in the runtime's last-error slot (the library checks
+// its launches with cudaGetLastError, which would otherwise report that stale error).
 struct DeviceGuard {
   int prev = -1;
   explicit DeviceGuard(int dev) {
     cudaGetDevice(&prev);
     if (prev != dev) cudaSetDevice(dev);
+    cudaGetLastError();
   }
   ~DeviceGuard() {
     int cur = -1;
@@ -135,6 +138,10 @@ struct rte_batch_s {
   rte::DevBuf<double> tables;             // [B][n_mat][n_dirs][kTab*]
   rte::DevBuf<double> partial;            // [B][n_groups][n_dof] per-group scalar-flux partials
   rte::DevBuf<double> S;                  // [B][n_dof] cell sources of the current sweep (2D)
+  // FP32 sweep state (precision variant), allocated on first use
+  rte::DevBuf<float> tables32, S32, partial32;
+  bool tables32_stale = true;
+  double sweep32_units = 0.0;
   rte::DevBuf<unsigned long long> norms;  // [B][2] stop-test norms as ordered bit patterns
   rte::DevBuf<double> work;               // [B][n_dof] x 4 iteration scratch for rte_solve
   rte::DsaState* dsa = nullptr;
@@ -144,7 +151,7 @@ struct rte_batch_s {
   double sweep_units = 0.0;   // cell x distinct-direction solves in the timed sweeps
   long long sweep_launches = 0;
   struct PhaseEv { int phase; cudaEvent_t a, b; };
-  std::vector<PhaseEv> phase_ev;   // phases: 1 DSA, 2 ROM, 3 set-up
+  std::vector<PhaseEv> phase_ev;   // phases: 0 FP32 sweep, 1 DSA, 2 ROM, 3 set-up
   long long phase_calls[4] = {0, 0, 0, 0};
   ~rte_batch_s();
 };
@@ -176,8 +183,10 @@ int auto_dpw(const rte_disc_s* disc, int B);
 // sweep.cu
 int sweep_launch(rte_batch_t b, const double* rho_in, double* rho_out, double* psi_out,
                  int with_source, const uint8_t* active, cudaStream_t st, bool fuse_norms,
-                 int n_active = -1);
+                 int n_active = -1, bool zero_norms = true);
 int norms_to_host(rte_batch_t b, double* host, cudaStream_t st);
+int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, const uint8_t* active,
+                     cudaStream_t st, int n_active, bool zero_norms = true);
 int setup_tables(rte_batch_t b, cudaStream_t st);
 int correction_source_launch(rte_batch_t b, const double* rs, const double* rp, double* R,
                              const uint8_t* active, cudaStream_t st);

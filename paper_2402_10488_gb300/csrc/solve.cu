@@ -24,12 +24,17 @@ int run_si(rte_batch_t bt, const rte_solve_opts* o, rte_rom_t rom_c, double* rho
   double* drho = bt->work.p + 3 * nb;
   RTE_CUDA_TRY(cudaMemcpyAsync(rho_prev, rho, sizeof(double) * nb, cudaMemcpyDeviceToDevice, st));
   std::vector<uint8_t> act(B, 1), use_rom(B, 0), use_dsa(B, 0);
-  DevBuf<uint8_t> act_dev, rom_dev, dsa_dev;
+  // precision variant: instances start with FP32 sweeps and switch to FP64 below fp32_switch
+  const bool mixed = o->fp32_switch > 0.0 && d->dim == 2 && psi_cur == nullptr;
+  std::vector<uint8_t> lowp(B, mixed ? 1 : 0), act_lo(B, 0), act_hi(B, 0);
+  DevBuf<uint8_t> act_dev, rom_dev, dsa_dev, lo_dev, hi_dev;
   RTE_TRY(act_dev.alloc(B));
+  RTE_TRY(lo_dev.alloc(B));
+  RTE_TRY(hi_dev.alloc(B));
   RTE_TRY(rom_dev.alloc(B));
   RTE_TRY(dsa_dev.alloc(B));
   std::vector<rte_solve_report> rep(B);
-  for (auto& r : rep) r = rte_solve_report{0, 0, 0, 0, 0, 0.0, 0.0};
+  for (auto& r : rep) r = rte_solve_report{0, 0, 0, 0, 0, 0.0, 0.0, 0};
   if ((o->sa == RTE_SA_ROMSA || o->sa == RTE_SA_ROMSAD) && !rom_c)
     return fail(RTE_EINVAL, "ROMSA/ROMSAD need a correction ROM");
   if (rom_c) {
@@ -43,9 +48,23 @@ int run_si(rte_batch_t bt, const rte_solve_opts* o, rte_rom_t rom_c, double* rho
   for (int l = 1; l <= o->max_iter; ++l) {
     RTE_CUDA_TRY(cudaMemcpyAsync(act_dev.p, act.data(), B, cudaMemcpyHostToDevice, st));
     double* psi = psi_cur;
-    int n_act = 0;
-    for (int b = 0; b < B; ++b) n_act += act[b] != 0;
-    RTE_TRY(sweep_launch(bt, rho_prev, rho_star, psi, 1, act_dev.p, st, true, n_act));
+    int n_lo = 0, n_hi = 0;
+    for (int b = 0; b < B; ++b) {
+      act_lo[b] = act[b] && lowp[b];
+      act_hi[b] = act[b] && !lowp[b];
+      n_lo += act_lo[b], n_hi += act_hi[b];
+    }
+    if (n_lo == 0) {
+      RTE_TRY(sweep_launch(bt, rho_prev, rho_star, psi, 1, act_dev.p, st, true, n_hi));
+    } else {
+      RTE_CUDA_TRY(cudaMemsetAsync(bt->norms.p, 0, sizeof(unsigned long long) * 2 * B, st));
+      RTE_CUDA_TRY(cudaMemcpyAsync(lo_dev.p, act_lo.data(), B, cudaMemcpyHostToDevice, st));
+      RTE_TRY(sweep_launch_f32(bt, rho_prev, rho_star, lo_dev.p, st, n_lo, false));
+      if (n_hi > 0) {
+        RTE_CUDA_TRY(cudaMemcpyAsync(hi_dev.p, act_hi.data(), B, cudaMemcpyHostToDevice, st));
+        RTE_TRY(sweep_launch(bt, rho_prev, rho_star, psi, 1, hi_dev.p, st, true, n_hi, false));
+      }
+    }
     if (psi_win && l <= window)
       for (int b = 0; b < B; ++b)
         if (act[b])
@@ -63,7 +82,10 @@ int run_si(rte_batch_t bt, const rte_solve_opts* o, rte_rom_t rom_c, double* rho
       rep[b].last_change = delta;
       rep[b].rho_inf = rinf;
       const double test = o->rel ? delta / rinf : delta;
-      if (test < o->eps) {
+      if (lowp[b]) {
+        rep[b].n_sweep32++;
+        if (test < o->fp32_switch) lowp[b] = 0;  // later sweeps of this instance in FP64
+      } else if (test < o->eps) {
         rep[b].converged = 1;
         act[b] = 0;
         RTE_CUDA_TRY(cudaMemcpyAsync(rho + (size_t)b * n, rho_star + (size_t)b * n,
@@ -124,7 +146,7 @@ extern "C" int rte_solve(rte_batch_t b, const rte_solve_opts* o, rte_rom_t rom_c
                          rte_solve_report* reports, double* history, void* stream) {
   if (!b || !o || !rho) return fail(RTE_EINVAL, "rte_solve: null argument");
   if (!b->params_set) return fail(RTE_ESTATE, "rte_solve: parameters not set");
-  if (!(o->eps >= 0) || o->max_iter < 1 || o->sa < 0 || o->sa > 3)
+  if (!(o->eps >= 0) || o->max_iter < 1 || o->sa < 0 || o->sa > 3 || !(o->fp32_switch >= 0))
     return fail(RTE_EINVAL, "rte_solve: bad options");
   if (o->sa != RTE_SA_NONE && b->disc->dim == 2 && (!(o->dsa_rtol >= 0) || o->dsa_max_it < 1))
     return fail(RTE_EINVAL, "rte_solve: bad DSA tolerance");

@@ -461,7 +461,7 @@ static int launch2d(const Sweep2DArgs& A, int B, int n_groups, cudaStream_t st) 
 
 int sweep_launch(rte_batch_t bt, const double* rho_in, double* rho_out, double* psi_out,
                  int with_source, const uint8_t* active, cudaStream_t st, bool fuse_norms,
-                 int n_active) {
+                 int n_active, bool zero_norms) {
   if (n_active < 0) n_active = bt->B;
   const rte_disc_s* d = bt->disc;
   const int n_groups = (int)bt->groups.size();
@@ -500,7 +500,8 @@ int sweep_launch(rte_batch_t bt, const double* rho_in, double* rho_out, double* 
     bt->sweep_launches += 1;
     bt->sweep_units += (double)n_active * d->n_cells * d->n_dirs;
   }
-  if (fuse_norms) RTE_CUDA_TRY(cudaMemsetAsync(bt->norms.p, 0, sizeof(unsigned long long) * 2 * bt->B, st));
+  if (fuse_norms && zero_norms)
+    RTE_CUDA_TRY(cudaMemsetAsync(bt->norms.p, 0, sizeof(unsigned long long) * 2 * bt->B, st));
   const int th = 256;
   dim3 grid((d->n_dof / 2 + th - 1) / th, bt->B);
   reduce_partials_kernel<<<grid, th, 0, st>>>(bt->partial.p, rho_in, rho_out,
@@ -613,6 +614,268 @@ int sweep_launch_with_scratch(rte_batch_t bt, const double* rho_in, double* rho_
   dim3 grid((d->n_dof / 2 + th - 1) / th, bt->B);
   reduce_partials_kernel<<<grid, th, 0, st>>>(partial, rho_in, rho_out, nullptr, nullptr, n_groups,
                                              d->n_dof); RTE_NOTE_LAUNCH();
+  RTE_CUDA_TRY(cudaGetLastError());
+  return RTE_OK;
+}
+
+}  // namespace rte
+
+// ---- FP32 sweep (precision variant) --------------------------------------------------------------
+//
+// Same wavefront layout and cell algebra as sweep2d_kernel, in single precision: FP32 tables,
+// FP32 sources formed once per sweep, FP32 partial sums.  The FP32 units of GB300 run at about 59x
+// the FP64 rate, so these sweeps are cheap; rte_solve uses them for the early iterations of an
+// instance and switches it to the FP64 sweep for the final ones (rte_solve_opts.fp32_switch).
+namespace rte {
+
+__global__ void tables_to_f32_kernel(const double* t64, float* t32, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) t32[i] = (float)t64[i];
+}
+
+__global__ void cell_source32_kernel(const double* __restrict__ rho, float* S,
+                                     const double* __restrict__ sigma_s,
+                                     const double* __restrict__ G0, const int32_t* __restrict__ mat,
+                                     const uint8_t* active, int n_cells, int n_mat, int with_source) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  const double ss = sigma_s[(size_t)b * n_mat + mat[c]];
+  const double* r = rho + ((size_t)b * n_cells + c) * 4;
+  const double s0 = fma(ss, r[0], with_source ? G0[(size_t)b * n_cells + c] : 0.0);
+  reinterpret_cast<float4*>(S)[(size_t)b * n_cells + c] =
+      make_float4((float)s0, (float)(ss * r[1]), (float)(ss * r[2]), (float)(ss * r[3]));
+}
+
+struct Sweep2D32Args {
+  const float* S;
+  float* partial;
+  const uint8_t* active;
+  const float* tables;
+  const double* inflow;
+  const int32_t* mat;
+  const double* dirs;
+  const SweepGroup* groups;
+  int nx, ny, n_cells, n_dof, n_mat, n_dirs, n_groups, with_source;
+  double sq_area;
+};
+
+template <int DPW>
+__global__ void __launch_bounds__(32) sweep2d_f32_kernel(const Sweep2D32Args A) {
+  const int g = blockIdx.x, b = blockIdx.y, lane = threadIdx.x;
+  if (A.active && !A.active[b]) return;
+  const SweepGroup grp = A.groups[g];
+  const bool xneg = grp.quad & 1, yneg = (grp.quad & 2) != 0;
+  extern __shared__ float smf[];
+  float* ybuf = smf;                                 // [nx][DPW][2]
+  float* tab_s = smf + (size_t)A.nx * DPW * 2;       // [n_mat][DPW][32]
+  const float* __restrict__ tabg = A.tables + (size_t)b * A.n_mat * A.n_dirs * kTab2D;
+  for (int e = lane; e < A.n_mat * DPW * kTab2D; e += 32) {
+    const int m = e / (DPW * kTab2D), r = e % (DPW * kTab2D), dd = r / kTab2D, k = r % kTab2D;
+    tab_s[e] = dd < grp.nd ? tabg[((size_t)m * A.n_dirs + grp.d0 + dd) * kTab2D + k] : 0.f;
+  }
+  __syncwarp();
+  float w[DPW];
+#pragma unroll
+  for (int dd = 0; dd < DPW; ++dd) w[dd] = dd < grp.nd ? (float)A.dirs[4 * (grp.d0 + dd) + 2] : 0.f;
+  const float s3 = 1.7320508075688772f;
+  const float c3x = xneg ? -s3 : s3, c3y = yneg ? -s3 : s3;
+  const float gxb = A.with_source ? (float)(A.inflow[4 * b + (xneg ? 1 : 0)] * A.sq_area) : 0.f;
+  const float gyb = A.with_source ? (float)(A.inflow[4 * b + (yneg ? 3 : 2)] * A.sq_area) : 0.f;
+  const int H = A.nx < 32 ? A.nx : 32;
+  const int nrb = (A.ny + H - 1) / H;
+  const int total = nrb * A.nx;
+  const float4* __restrict__ Sb = reinterpret_cast<const float4*>(A.S) + (size_t)b * A.n_cells;
+  float4* part = reinterpret_cast<float4*>(A.partial + ((size_t)b * A.n_groups + g) * A.n_dof);
+  float tx[DPW][2], typ[DPW][2];
+#pragma unroll
+  for (int dd = 0; dd < DPW; ++dd) tx[dd][0] = tx[dd][1] = typ[dd][0] = typ[dd][1] = 0.f;
+  for (int s = 0; s < total + H - 1; ++s) {
+    const int u = s - lane;
+    const bool inrange = lane < H && u >= 0 && u < total;
+    const int rb = inrange ? u / A.nx : 0;
+    const int t = inrange ? u - rb * A.nx : 0;
+    const int r = rb * H + lane;
+    const bool act = inrange && r < A.ny;
+    float ty[DPW][2];
+#pragma unroll
+    for (int dd = 0; dd < DPW; ++dd) {
+      ty[dd][0] = __shfl_up_sync(0xffffffffu, typ[dd][0], 1);
+      ty[dd][1] = __shfl_up_sync(0xffffffffu, typ[dd][1], 1);
+    }
+    if (act) {
+      if (r == 0) {
+#pragma unroll
+        for (int dd = 0; dd < DPW; ++dd) ty[dd][0] = gyb, ty[dd][1] = 0.f;
+      } else if (lane == 0) {
+#pragma unroll
+        for (int dd = 0; dd < DPW; ++dd) {
+          ty[dd][0] = ybuf[(t * DPW + dd) * 2];
+          ty[dd][1] = ybuf[(t * DPW + dd) * 2 + 1];
+        }
+      }
+      if (t == 0) {
+#pragma unroll
+        for (int dd = 0; dd < DPW; ++dd) tx[dd][0] = gxb, tx[dd][1] = 0.f;
+      }
+      const int i = xneg ? A.nx - 1 - t : t;
+      const int j = yneg ? A.ny - 1 - r : r;
+      const int c = j * A.nx + i;
+      const int m = A.mat[c];
+      const float4 sv = Sb[c];
+      float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+#pragma unroll
+      for (int dd = 0; dd < DPW; ++dd) {
+        if (dd < grp.nd) {
+          const float* T = tab_s + (m * DPW + dd) * kTab2D;
+          float a[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            float v = T[4 * k] * sv.x;
+            v = fmaf(T[4 * k + 1], sv.y, v);
+            v = fmaf(T[4 * k + 2], sv.z, v);
+            v = fmaf(T[4 * k + 3], sv.w, v);
+            v = fmaf(T[16 + 2 * k], tx[dd][0], v);
+            v = fmaf(T[17 + 2 * k], tx[dd][1], v);
+            v = fmaf(T[24 + 2 * k], ty[dd][0], v);
+            v = fmaf(T[25 + 2 * k], ty[dd][1], v);
+            a[k] = v;
+          }
+          tx[dd][0] = fmaf(c3x, a[1], a[0]);
+          tx[dd][1] = fmaf(c3x, a[3], a[2]);
+          typ[dd][0] = fmaf(c3y, a[2], a[0]);
+          typ[dd][1] = fmaf(c3y, a[3], a[1]);
+          acc0 = fmaf(w[dd], a[0], acc0);
+          acc1 = fmaf(w[dd], a[1], acc1);
+          acc2 = fmaf(w[dd], a[2], acc2);
+          acc3 = fmaf(w[dd], a[3], acc3);
+        }
+      }
+      part[c] = make_float4(acc0, acc1, acc2, acc3);
+      if (lane == H - 1 && rb + 1 < nrb) {
+#pragma unroll
+        for (int dd = 0; dd < DPW; ++dd) {
+          ybuf[(t * DPW + dd) * 2] = typ[dd][0];
+          ybuf[(t * DPW + dd) * 2 + 1] = typ[dd][1];
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// rho_out (FP64) = sum of the FP32 group partials (fixed order, summed in FP64); fused norms.
+__global__ void reduce_partials32_kernel(const float* __restrict__ partial,
+                                         const double* __restrict__ rho_in, double* rho_out,
+                                         unsigned long long* norms, const uint8_t* active,
+                                         int n_groups, int n_dof) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int e = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  double dmax = 0.0, rmax = 0.0;
+  if (e < n_dof) {
+    const float* p = partial + (size_t)b * n_groups * n_dof + e;
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    for (int g = 0; g < n_groups; ++g) {
+      const float4 v = *reinterpret_cast<const float4*>(p + (size_t)g * n_dof);
+      a0 += v.x, a1 += v.y, a2 += v.z, a3 += v.w;
+    }
+    double* o = rho_out + (size_t)b * n_dof + e;
+    o[0] = a0, o[1] = a1, o[2] = a2, o[3] = a3;
+    if (norms) {
+      const double* ri = rho_in + (size_t)b * n_dof + e;
+      dmax = fmax(fmax(fabs(a0 - ri[0]), fabs(a1 - ri[1])), fmax(fabs(a2 - ri[2]), fabs(a3 - ri[3])));
+      rmax = fmax(fmax(fabs(a0), fabs(a1)), fmax(fabs(a2), fabs(a3)));
+    }
+  }
+  if (!norms) return;
+  for (int o = 16; o > 0; o >>= 1) {
+    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+  }
+  __shared__ double sd[32], sr[32];
+  const int wid = threadIdx.x >> 5, ln = threadIdx.x & 31;
+  if (ln == 0) sd[wid] = dmax, sr[wid] = rmax;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    dmax = ln < nw ? sd[ln] : 0.0;
+    rmax = ln < nw ? sr[ln] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    }
+    if (ln == 0) {
+      atomicMax(norms + 2 * b, (unsigned long long)__double_as_longlong(dmax));
+      atomicMax(norms + 2 * b + 1, (unsigned long long)__double_as_longlong(rmax));
+    }
+  }
+}
+
+template <int DPW>
+static int launch2d_f32(const Sweep2D32Args& A, int B, int n_groups, cudaStream_t st) {
+  const size_t bytes = ((size_t)A.nx * DPW * 2 + (size_t)A.n_mat * DPW * kTab2D) * sizeof(float);
+  if (bytes > 200 * 1024) return fail(RTE_EINVAL, "FP32 sweep: shared memory exceeded");
+  if (bytes > 48 * 1024) {
+    RTE_CUDA_TRY(cudaFuncSetAttribute(sweep2d_f32_kernel<DPW>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  }
+  sweep2d_f32_kernel<DPW><<<dim3(n_groups, B), 32, bytes, st>>>(A); RTE_NOTE_LAUNCH();
+  RTE_CUDA_TRY(cudaGetLastError());
+  return RTE_OK;
+}
+
+// One FP32 sweep of the active instances of a 2D batch, partial sums reduced in FP64 into
+// rho_out with the stop-test norms fused (as sweep_launch with fuse_norms).
+int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, const uint8_t* active,
+                     cudaStream_t st, int n_active, bool zero_norms) {
+  const rte_disc_s* d = bt->disc;
+  if (d->dim != 2) return fail(RTE_EINVAL, "FP32 sweep: 2D only");
+  if (!bt->tables32.p) {
+    const size_t n = bt->tables.n;
+    RTE_TRY(bt->tables32.alloc(n));
+    RTE_TRY(bt->S32.alloc((size_t)bt->B * d->n_dof));
+    bt->tables32_stale = true;
+  }
+  if (bt->partial32.n < (size_t)bt->B * bt->groups.size() * d->n_dof)
+    RTE_TRY(bt->partial32.alloc((size_t)bt->B * bt->groups.size() * d->n_dof));
+  if (bt->tables32_stale) {
+    const size_t n = bt->tables.n;
+    tables_to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(bt->tables.p, bt->tables32.p, n); RTE_NOTE_LAUNCH();
+    bt->tables32_stale = false;
+  }
+  const int n_groups = (int)bt->groups.size();
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (bt->timing) {
+    RTE_CUDA_TRY(cudaEventCreate(&ev0));
+    RTE_CUDA_TRY(cudaEventCreate(&ev1));
+    RTE_CUDA_TRY(cudaEventRecord(ev0, st));
+  }
+  cell_source32_kernel<<<dim3((d->n_cells + 127) / 128, bt->B), 128, 0, st>>>(
+      rho_in, bt->S32.p, bt->sigma_s.p, bt->G0.p, d->mat_id.p, active, d->n_cells, d->n_mat, 1); RTE_NOTE_LAUNCH();
+  Sweep2D32Args A{bt->S32.p,  bt->partial32.p, active,   bt->tables32.p, bt->inflow.p,
+                  d->mat_id.p, d->dir_dev.p,   bt->groups_dev.p, d->nx,  d->ny,
+                  d->n_cells, d->n_dof,        d->n_mat, d->n_dirs,      n_groups,
+                  1,          std::sqrt(d->hx * d->hy)};
+  switch (bt->dpw) {
+    case 1: RTE_TRY(launch2d_f32<1>(A, bt->B, n_groups, st)); break;
+    case 2: RTE_TRY(launch2d_f32<2>(A, bt->B, n_groups, st)); break;
+    case 4: RTE_TRY(launch2d_f32<4>(A, bt->B, n_groups, st)); break;
+    case 8: RTE_TRY(launch2d_f32<8>(A, bt->B, n_groups, st)); break;
+    default: return fail(RTE_EINVAL, "unsupported directions-per-warp");
+  }
+  if (bt->timing) {
+    RTE_CUDA_TRY(cudaEventRecord(ev1, st));
+    bt->phase_ev.push_back({0, ev0, ev1});
+    bt->phase_calls[0] += 1;
+    bt->sweep32_units += (double)n_active * d->n_cells * d->n_dirs;
+  }
+  if (zero_norms)
+    RTE_CUDA_TRY(cudaMemsetAsync(bt->norms.p, 0, sizeof(unsigned long long) * 2 * bt->B, st));
+  const int th = 256;
+  reduce_partials32_kernel<<<dim3((d->n_dof / 4 + th - 1) / th, bt->B), th, 0, st>>>(
+      bt->partial32.p, rho_in, rho_out, bt->norms.p, active, n_groups, d->n_dof); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;
 }

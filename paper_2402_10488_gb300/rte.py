@@ -102,12 +102,13 @@ class _RomOpts(ctypes.Structure):
 
 class _SolveOpts(ctypes.Structure):
     _fields_ = [("eps", _D), ("rel", _I), ("max_iter", _I), ("sa", _I), ("theta", _I),
-                ("eps_romsad", _D), ("dsa_rtol", _D), ("dsa_max_it", _I), ("schedule", _P)]
+                ("eps_romsad", _D), ("dsa_rtol", _D), ("dsa_max_it", _I), ("schedule", _P),
+                ("fp32_switch", _D)]
 
 
 class SolveReport(ctypes.Structure):
     _fields_ = [("n_sweep", _I), ("converged", _I), ("n_romsa", _I), ("n_dsa", _I),
-                ("dsa_iters", _I), ("last_change", _D), ("rho_inf", _D)]
+                ("dsa_iters", _I), ("last_change", _D), ("rho_inf", _D), ("n_sweep32", _I)]
 
 
 def _ptr(t):
@@ -199,11 +200,13 @@ class Batch:
     def timing(self, enable):
         """enable=1 reset+start, 0 reset+stop, -1 read.  Returns a dict of phase times (ms) and
         counts: sweep (kernel only), dsa, rom, setup."""
-        out = np.zeros(9)
+        out = np.zeros(12)
         check(lib().rte_batch_timing(self.h, int(enable), out.ctypes.data_as(_P)))
         return dict(sweep_ms=float(out[0]), sweep_launches=int(out[1]), sweep_units=float(out[2]),
                     dsa_ms=float(out[3]), dsa_calls=int(out[4]), rom_ms=float(out[5]),
-                    rom_calls=int(out[6]), setup_ms=float(out[7]), setup_calls=int(out[8]))
+                    rom_calls=int(out[6]), setup_ms=float(out[7]), setup_calls=int(out[8]),
+                    sweep32_ms=float(out[9]), sweep32_launches=int(out[10]),
+                    sweep32_units=float(out[11]))
 
     def directions(self):
         d = np.zeros((self.disc.n_dirs, 4))
@@ -236,11 +239,11 @@ class Batch:
 
     def solve(self, rho, eps, sa=SA_DSA, rel=False, max_iter=1000, theta=0, eps_romsad=0.0,
               dsa_rtol=1e-10, dsa_max_it=500, rom_c=None, schedule=None, history=False,
-              stream=None):
+              fp32_switch=0.0, stream=None):
         sched = None if schedule is None else _host(schedule, np.uint8)
         opts = _SolveOpts(float(eps), 1 if rel else 0, int(max_iter), int(sa), int(theta),
                           float(eps_romsad), float(dsa_rtol), int(dsa_max_it),
-                          None if sched is None else sched.ctypes.data_as(_P))
+                          None if sched is None else sched.ctypes.data_as(_P), float(fp32_switch))
         reps = (SolveReport * self.B)()
         hist = np.zeros((self.B, max_iter)) if history else None
         st = check(lib().rte_solve(self.h, ctypes.byref(opts), None if rom_c is None else rom_c.h,
@@ -249,7 +252,7 @@ class Batch:
                                    _stream(stream)), allow=(RTE_ENOCONV,))
         rep = [dict(n_sweep=r.n_sweep, converged=bool(r.converged), n_romsa=r.n_romsa,
                     n_dsa=r.n_dsa, dsa_iters=r.dsa_iters, last_change=r.last_change,
-                    rho_inf=r.rho_inf) for r in reps]
+                    rho_inf=r.rho_inf, n_sweep32=r.n_sweep32) for r in reps]
         return rep, hist, st
 
     def close(self):

@@ -159,3 +159,31 @@ def test_si_with_fixed_vcycle_dsa_converges_to_the_same_solution():
         ref = sisa(tr, np.zeros(tr.n_dof), 1e-14, 400, "dsa", dsa=ConsistentDSA(tr), tol_mode="rel")
         assert _rel(rho.cpu().numpy()[b], ref["rho"]) < 1e-10
         assert rep[b]["n_sweep"] <= ref["n_sweep"] + 3
+
+
+@pytest.mark.parametrize("sa", ["dsa", "romsad"])
+def test_precision_variant_fp32_then_fp64_sweeps_reaches_the_fp64_solution(sa):
+    """Instances sweep in FP32 until the relative change falls below 1e-4, then in FP64: the
+    converged rho is the FP64 transport solution (1e-10 against the oracle)."""
+    rte = _rte()
+    p = inputs.lattice_test(32, 16, 3, n_vz=2)
+    batch = rte.Batch.from_problem(p)
+    kw = {}
+    if sa == "romsad":
+        train = inputs.lattice_train(32, 16, n_train=6, n_vz=2)
+        tb = rte.Batch(batch.disc, 6)
+        tb.set_params(train)
+        _, rc = rte.Rom.build(tb, eps_train=1e-12, window=3, rank_p=4, rank_c=6, max_iter=300,
+                              dsa_rtol=1e-10)
+        kw = dict(sa=rte.SA_ROMSAD, rom_c=rc, theta=5, eps_romsad=0.1 * max(1e-12, rc.eps_pod))
+    else:
+        kw = dict(sa=rte.SA_DSA)
+    rho = torch.zeros((3, p.n_dof), dtype=torch.float64, device="cuda")
+    rep, _, st = batch.solve(rho, 1e-13, rel=True, max_iter=300, dsa_rtol=0.0, dsa_max_it=2,
+                             fp32_switch=1e-4, **kw)
+    assert st == 0
+    for b in range(3):
+        assert rep[b]["n_sweep32"] >= 2 and rep[b]["n_sweep"] > rep[b]["n_sweep32"]
+        tr = Transport(p, b)
+        ref = sisa(tr, np.zeros(tr.n_dof), 1e-14, 400, "dsa", dsa=ConsistentDSA(tr), tol_mode="rel")
+        assert _rel(rho.cpu().numpy()[b], ref["rho"]) < 1e-10
