@@ -243,6 +243,44 @@ void make_groups(rte_batch_t b) {
   }
 }
 
+static std::vector<SweepGroup> groups_for(const rte_disc_s* disc, int dpw) {
+  std::vector<SweepGroup> g;
+  int d = 0;
+  while (d < disc->n_dirs) {
+    const int q = disc->dirs[d].quad;
+    int e = d;
+    while (e < disc->n_dirs && disc->dirs[e].quad == q && e - d < dpw) ++e;
+    g.push_back(SweepGroup{d, e - d, q, 0});
+    d = e;
+  }
+  return g;
+}
+
+void pick_groups(rte_batch_t b, int n_active, int* dpw, int* n_groups, const SweepGroup** dev) {
+  int use = b->dpw;
+  if (b->dpw_dynamic && b->disc->dim == 2) {
+    use = 1;
+    for (int k = 3; k >= 1; --k) {
+      const int cand = 1 << k;
+      if (cand > b->dpw) continue;
+      if ((long long)n_active * b->gcount[k] >= 4LL * b->n_sm) {
+        use = cand;
+        break;
+      }
+    }
+  }
+  const int k = use == 1 ? 0 : use == 2 ? 1 : use == 4 ? 2 : 3;
+  if (b->disc->dim == 2 && b->groups_all_dev.p) {
+    *dpw = use;
+    *n_groups = b->gcount[k];
+    *dev = b->groups_all_dev.p + b->goff[k];
+  } else {
+    *dpw = b->dpw;
+    *n_groups = (int)b->groups.size();
+    *dev = b->groups_dev.p;
+  }
+}
+
 // largest directions-per-warp giving >= 4 resident warps per SM (each SM sub-partition has its
 // own FP64 unit, so one warp per sub-partition is the minimum to use the SM's FP64 rate)
 int auto_dpw(const rte_disc_s* disc, int B) {
@@ -263,6 +301,7 @@ int auto_dpw(const rte_disc_s* disc, int B) {
 extern "C" int rte_batch_tune(rte_batch_t b, int dpw) {
   if (!b) return fail(RTE_EINVAL, "rte_batch_tune: null argument");
   if (b->disc->dim == 1) return RTE_OK;
+  b->dpw_dynamic = dpw == 0;
   if (dpw == 0) dpw = auto_dpw(b->disc, b->B);
   if (dpw != 1 && dpw != 2 && dpw != 4 && dpw != 8) return fail(RTE_EINVAL, "dirs_per_warp must be 0, 1, 2, 4 or 8");
   DeviceGuard g(b->disc->device);
@@ -360,6 +399,18 @@ extern "C" int rte_batch_create(rte_disc_t disc, int B, rte_batch_t* out) {
   b->B = B;
   b->dpw = disc->dim == 1 ? 1 : auto_dpw(disc, B);
   make_groups(b);
+  std::vector<SweepGroup> all;
+  if (disc->dim == 2) {
+    if (cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, disc->device) != cudaSuccess)
+      b->n_sm = 148;
+    for (int k = 0; k < 4; ++k) {
+      auto g = groups_for(disc, 1 << k);
+      b->goff[k] = (int)all.size();
+      b->gcount[k] = (int)g.size();
+      all.insert(all.end(), g.begin(), g.end());
+    }
+  }
+  const size_t max_groups = disc->dim == 2 ? (size_t)b->gcount[0] : b->groups.size();
   const size_t nb = (size_t)B;
   const size_t tab = disc->dim == 1 ? kTab1D : kTab2D;
   int st = RTE_OK;
@@ -369,7 +420,8 @@ extern "C" int rte_batch_create(rte_disc_t disc, int B, rte_batch_t* out) {
   if (st == RTE_OK) st = b->G0.alloc(nb * disc->n_cells);
   if (st == RTE_OK) st = b->inflow.alloc(nb * 4);
   if (st == RTE_OK) st = b->tables.alloc(nb * disc->n_mat * disc->n_dirs * tab);
-  if (st == RTE_OK) st = b->partial.alloc(nb * b->groups.size() * disc->n_dof);
+  if (st == RTE_OK) st = b->partial.alloc(nb * max_groups * disc->n_dof);
+  if (st == RTE_OK && !all.empty()) st = b->groups_all_dev.alloc(all.size());
   if (st == RTE_OK) st = b->norms.alloc(nb * 2);
   if (st == RTE_OK && disc->dim == 2) st = b->S.alloc(nb * disc->n_dof);
   if (st == RTE_OK) st = b->work.alloc(nb * disc->n_dof * 4);
@@ -377,7 +429,9 @@ extern "C" int rte_batch_create(rte_disc_t disc, int B, rte_batch_t* out) {
     delete b;
     return st;
   }
-  if (cudaMemcpy(b->groups_dev.p, b->groups.data(), sizeof(SweepGroup) * b->groups.size(),
+  if ((!all.empty() && cudaMemcpy(b->groups_all_dev.p, all.data(), sizeof(SweepGroup) * all.size(),
+                                  cudaMemcpyHostToDevice) != cudaSuccess) ||
+      cudaMemcpy(b->groups_dev.p, b->groups.data(), sizeof(SweepGroup) * b->groups.size(),
                  cudaMemcpyHostToDevice) != cudaSuccess) {
     delete b;
     return fail(RTE_ECUDA, "rte_batch_create: upload failed");

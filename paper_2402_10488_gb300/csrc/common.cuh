@@ -128,9 +128,15 @@ struct rte_batch_s {
   rte_disc_s* disc = nullptr;
   int B = 0;
   bool params_set = false;
-  int dpw = 4;                        // directions per warp in the 2D sweep
+  int dpw = 4;                        // directions per warp in the 2D sweep (preferred / fixed)
   std::vector<rte::SweepGroup> groups;
   rte::DevBuf<rte::SweepGroup> groups_dev;
+  // group tables for dpw = 1, 2, 4, 8; with dpw_dynamic each launch picks the largest dpw (up to
+  // the preferred one) that still keeps four warps per SM busy for its number of active instances
+  bool dpw_dynamic = true;
+  int n_sm = 148;
+  int gcount[4] = {0, 0, 0, 0}, goff[4] = {0, 0, 0, 0};
+  rte::DevBuf<rte::SweepGroup> groups_all_dev;
   std::vector<double> sigma_t_h, sigma_s_h, source_h, inflow_h;
   rte::DevBuf<double> sigma_t, sigma_s;   // [B][n_mat]
   rte::DevBuf<double> G0;                 // [B][n_cells] zeroth source moment int G phi_0
@@ -180,6 +186,8 @@ struct PhaseScope {
 };
 void make_groups(rte_batch_t b);
 int auto_dpw(const rte_disc_s* disc, int B);
+// groups of one launch: dpw, number of groups and their device table
+void pick_groups(rte_batch_t b, int n_active, int* dpw, int* n_groups, const SweepGroup** dev);
 // sweep.cu
 int sweep_launch(rte_batch_t b, const double* rho_in, double* rho_out, double* psi_out,
                  int with_source, const uint8_t* active, cudaStream_t st, bool fuse_norms,

@@ -464,7 +464,9 @@ int sweep_launch(rte_batch_t bt, const double* rho_in, double* rho_out, double* 
                  int n_active, bool zero_norms) {
   if (n_active < 0) n_active = bt->B;
   const rte_disc_s* d = bt->disc;
-  const int n_groups = (int)bt->groups.size();
+  int dpw = bt->dpw, n_groups = 0;
+  const SweepGroup* gdev = nullptr;
+  pick_groups(bt, n_active, &dpw, &n_groups, &gdev);
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   if (bt->timing) {
     RTE_CUDA_TRY(cudaEventCreate(&ev0));
@@ -477,9 +479,9 @@ int sweep_launch(rte_batch_t bt, const double* rho_in, double* rho_out, double* 
         with_source); RTE_NOTE_LAUNCH();
     Sweep2DArgs A{bt->S.p,      bt->partial.p, psi_out,        active,      bt->tables.p,
                   bt->sigma_s.p, bt->G0.p,     bt->inflow.p,   d->mat_id.p, d->dir_dev.p,
-                  bt->groups_dev.p, d->nx,     d->ny,          d->n_cells,  d->n_dof,
+                  gdev,         d->nx,         d->ny,          d->n_cells,  d->n_dof,
                   d->n_mat,     d->n_dirs,     n_groups,       with_source, std::sqrt(d->hx * d->hy)};
-    switch (bt->dpw) {
+    switch (dpw) {
       case 1: RTE_TRY((launch2d<1, true>(A, bt->B, n_groups, st))); break;
       case 2: RTE_TRY((launch2d<2, true>(A, bt->B, n_groups, st))); break;
       case 4: RTE_TRY((launch2d<4, true>(A, bt->B, n_groups, st))); break;
@@ -838,14 +840,16 @@ int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, cons
     RTE_TRY(bt->S32.alloc((size_t)bt->B * d->n_dof));
     bt->tables32_stale = true;
   }
-  if (bt->partial32.n < (size_t)bt->B * bt->groups.size() * d->n_dof)
-    RTE_TRY(bt->partial32.alloc((size_t)bt->B * bt->groups.size() * d->n_dof));
+  int dpw = bt->dpw, n_groups = 0;
+  const SweepGroup* gdev = nullptr;
+  pick_groups(bt, n_active, &dpw, &n_groups, &gdev);
+  const size_t need32 = (size_t)bt->B * std::max<size_t>(bt->gcount[0], bt->groups.size()) * d->n_dof;
+  if (bt->partial32.n < need32) RTE_TRY(bt->partial32.alloc(need32));
   if (bt->tables32_stale) {
     const size_t n = bt->tables.n;
     tables_to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(bt->tables.p, bt->tables32.p, n); RTE_NOTE_LAUNCH();
     bt->tables32_stale = false;
   }
-  const int n_groups = (int)bt->groups.size();
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   if (bt->timing) {
     RTE_CUDA_TRY(cudaEventCreate(&ev0));
@@ -855,10 +859,10 @@ int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, cons
   cell_source32_kernel<<<dim3((d->n_cells + 127) / 128, bt->B), 128, 0, st>>>(
       rho_in, bt->S32.p, bt->sigma_s.p, bt->G0.p, d->mat_id.p, active, d->n_cells, d->n_mat, 1); RTE_NOTE_LAUNCH();
   Sweep2D32Args A{bt->S32.p,  bt->partial32.p, active,   bt->tables32.p, bt->inflow.p,
-                  d->mat_id.p, d->dir_dev.p,   bt->groups_dev.p, d->nx,  d->ny,
+                  d->mat_id.p, d->dir_dev.p,   gdev,     d->nx,          d->ny,
                   d->n_cells, d->n_dof,        d->n_mat, d->n_dirs,      n_groups,
                   1,          std::sqrt(d->hx * d->hy)};
-  switch (bt->dpw) {
+  switch (dpw) {
     case 1: RTE_TRY(launch2d_f32<1>(A, bt->B, n_groups, st)); break;
     case 2: RTE_TRY(launch2d_f32<2>(A, bt->B, n_groups, st)); break;
     case 4: RTE_TRY(launch2d_f32<4>(A, bt->B, n_groups, st)); break;
