@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--batch", type=int, default=64, help="test instances per step per GPU")
+    ap.add_argument("--batch", type=int, default=128, help="test instances per step per GPU")
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--angles", type=int, default=64)
     ap.add_argument("--ntrain", type=int, default=32)
