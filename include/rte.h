@@ -115,6 +115,27 @@ int rte_batch_destroy(rte_batch_t batch);
 int rte_batch_set_params(rte_batch_t batch, const double* sigma_t, const double* sigma_s,
                          const double* source, const double* inflow);
 
+/* Sets the parameters of some instances (slots) only, leaving the others untouched -- the
+ * admission step of continuous batching.  Same meaning as rte_batch_set_params for n instances:
+ *   slots             HOST int[n], distinct, each in [0, B)
+ *   sigma_t, sigma_s  HOST double[n][n_mat]
+ *   source            HOST double[n][n_cells]
+ *   inflow            HOST double[n][2*dim]
+ * The host arrays may be reused when the call returns (they are staged in pinned memory).  The
+ * uploads and the per-slot set-up kernels are asynchronous on `stream`; a later call on the same
+ * batch waits until the previous call's staging has been consumed.  The batch counts as having
+ * parameters once every slot has been set (by this call or rte_batch_set_params).
+ * Errors: as rte_batch_set_params. */
+int rte_batch_set_slots(rte_batch_t batch, int n, const int* slots, const double* sigma_t,
+                        const double* sigma_s, const double* source, const double* inflow,
+                        void* stream);
+
+/* info (HOST int64[6]): B, device bytes held by the batch, directions per warp (preferred),
+ * the smallest directions per warp its sweep partial sums are sized for, 1 if the
+ * decomposition is picked per launch, 1 if every slot has parameters.  The device bytes of a
+ * one-instance batch bound the memory one more slot costs (used for admission by memory). */
+int rte_batch_info(rte_batch_t batch, int64_t* info);
+
 /* ---- hot path: one source iteration --------------------------------------------------- */
 
 /* Transport sweep fused with the scalar-flux reduction (Alg. 1; Eq. (transport_sweep)):
@@ -133,9 +154,10 @@ int rte_sweep(rte_batch_t batch, const double* rho_in, double* rho_out, double* 
 
 /* Work decomposition of the 2D sweep: dirs_per_warp in {1, 2, 4, 8} sets how many directions of
  * one quadrant a warp sweeps together (more directions: more instruction-level parallelism and
- * fewer partial sums; fewer: more warps in flight).  0 picks automatically the largest value that
- * still gives at least four resident warps per SM for this batch size.  Set before sweeping.
- * Errors: RTE_EINVAL. */
+ * fewer partial sums; fewer: more warps in flight).  0 (the default) picks per launch the largest
+ * value that still gives at least four resident warps per SM for the number of running
+ * instances, but never fewer directions per warp than keep one instance's partial sums within
+ * 64 MB (large meshes with many directions).  Set before sweeping.  Errors: RTE_EINVAL. */
 int rte_batch_tune(rte_batch_t batch, int dirs_per_warp);
 
 /* Allocation-free variant of rte_sweep (the paper has no counterpart: this is a library service).
@@ -210,9 +232,9 @@ typedef struct {
 } rte_rom_opts;
 
 /* Offline stage (Sec. 3.1.1, 3.2.1) on the GPU: SI-DSA solves of every training instance of
- * `train` (f stored), snapshot matrices F and delta F (window w), thin SVD via a stabilised
- * Gram-Schmidt QR and a Jacobi SVD of the small factor, truncation, U^rho, U^iso and the affine
- * reduced operators A_{k,r} = U^T A_k U.  Produces the parametric ROM (rom_p, for ROMIG) and
+ * `train` (f stored), snapshot matrices F and delta F (window w), thin SVD through the snapshot
+ * Gram matrix (FP64 on the device) and a Jacobi eigensolver of that small matrix, truncation,
+ * U^rho, U^iso and the affine reduced operators A_{k,r} = U^T A_k U.  Produces the parametric ROM (rom_p, for ROMIG) and
  * the correction ROM (rom_c, for ROMSA).  Either output pointer may be NULL.  Synchronous. */
 int rte_rom_build(rte_batch_t train, const rte_rom_opts* opts, rte_rom_t* rom_p,
                   rte_rom_t* rom_c, void* stream);
@@ -222,6 +244,14 @@ int rte_rom_destroy(rte_rom_t rom);
  * sum s_k), n_dirs, n_dof, sum of singular values.  sv (HOST double[n_snapshots] or NULL):
  * singular values of the snapshot matrix. */
 int rte_rom_info(rte_rom_t rom, double* info, double* sv);
+
+/* Writes the online part of a ROM (U^rho, U^iso, the reduced operators, singular values and the
+ * discretisation it was built on) to a file, and reads it back for a discretisation with the
+ * same mesh, domain, quadrature and material map.  The full basis U is not stored (the online
+ * stage never reads it).  Errors: RTE_EINVAL (path, mismatching discretisation, bad file),
+ * RTE_ENOMEM, RTE_ECUDA. */
+int rte_rom_save(rte_rom_t rom, const char* path);
+int rte_rom_load(rte_disc_t disc, const char* path, rte_rom_t* rom);
 
 /* ROMIG (Sec. 3.1.1): rho0 = U^rho c with (sum_k psi_k(mu) A_{k,r}) c = U^T b_mu, for every
  * instance of `batch` (same discretisation as the ROM).  rho0: DEVICE double[B][n_dof]. */
@@ -277,6 +307,61 @@ typedef struct {
  * Synchronous.  Returns RTE_ENOCONV if some instance hit max_iter. */
 int rte_solve(rte_batch_t batch, const rte_solve_opts* opts, rte_rom_t rom_c, double* rho,
               rte_solve_report* reports, double* history, void* stream);
+
+/* rte_solve on n batches at once (typically one per discretisation of a mixed-size workload),
+ * each on its own stream: one host thread keeps every batch's iteration going, relaunching a
+ * batch as soon as its stop-test norms are back, so the batches' kernels overlap on the device.
+ * Arrays of length n: batches (distinct), opts, roms (array or NULL; a ROM may serve one batch
+ * only), rho (DEVICE double[B_k][n_dof_k] each, in/out as in rte_solve), reports (HOST arrays of
+ * rte_solve_report[B_k], the array or an entry may be NULL), streams (array or NULL).
+ * Synchronous.  Returns RTE_ENOCONV if some instance hit its iteration cap. */
+int rte_solve_many(int n, const rte_batch_t* batches, const rte_solve_opts* opts,
+                   const rte_rom_t* roms, double* const* rho, rte_solve_report* const* reports,
+                   void* const* streams);
+
+/* ---- serving: continuous batching of parametric solves ---------------------------------- */
+
+typedef struct rte_server_s* rte_server_t;
+
+typedef struct {
+  rte_solve_report solve;  /* iteration report of the request's solve                         */
+  int status;              /* RTE_OK, RTE_ENOCONV, or the error that ended the request         */
+  int bucket, slot;        /* where it ran                                                    */
+  int pad;
+  double t_submit, t_admit, t_done;  /* seconds since rte_server_start (steady clock); t_done
+                                        is when the result was in host memory                 */
+} rte_serve_report;
+
+/* A server drives buckets -- one per discretisation -- from one worker thread, each bucket on its
+ * own stream.  A bucket's batch supplies its slots (B = the most requests of that bucket on the
+ * device at once; size it by device memory with rte_batch_info).  Requests queue per bucket; at
+ * every iteration boundary of a bucket its finished slots are returned and queued requests are
+ * admitted into free slots, so new requests join the running ones without waiting for them.
+ * Every slot runs Alg. 1 with the bucket's options (ROMSAD of Alg. 2 with rom_c, etc.) and the
+ * request's own tolerance; rom_p (or NULL for a zero initial iterate) gives the ROMIG guess.
+ * Handles passed to a bucket must outlive the server and not be used elsewhere meanwhile. */
+int rte_server_create(int device, rte_server_t* out);
+/* opts.schedule must be NULL; opts.eps is replaced by each request's tolerance. */
+int rte_server_add_bucket(rte_server_t server, rte_batch_t slots, rte_rom_t rom_p,
+                          rte_rom_t rom_c, const rte_solve_opts* opts, int* bucket);
+int rte_server_start(rte_server_t server);
+/* Queues one request (parameters as one instance of rte_batch_set_slots; host arrays copied
+ * before the call returns).  ticket: HOST uint64 out.  Thread-safe. */
+int rte_server_submit(rte_server_t server, int bucket, const double* sigma_t,
+                      const double* sigma_s, const double* source, const double* inflow,
+                      double eps, uint64_t* ticket);
+/* Waits up to timeout_s seconds for a request; on completion copies the solution (HOST
+ * double[n_dof], may be NULL) and the report, and releases the ticket.  RTE_ETIMEOUT if it has
+ * not finished (the ticket stays valid).  Thread-safe. */
+int rte_server_wait(rte_server_t server, uint64_t ticket, double timeout_s, double* rho,
+                    rte_serve_report* report);
+/* stats (HOST double[8]): sweep launches, admitted, completed, queued now, largest queue,
+ * largest number of running slots of one bucket, worker seconds with work in flight, seconds
+ * since start. */
+int rte_server_stats(rte_server_t server, double* stats);
+/* Drops queued requests, lets running ones finish, stops the worker and frees the server (not
+ * the batches or ROMs given to it). */
+int rte_server_destroy(rte_server_t server);
 
 #ifdef __cplusplus
 }

@@ -67,7 +67,7 @@ static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w
 
 using namespace rte;
 
-extern "C" int rte_version(void) { return 10100; }
+extern "C" int rte_version(void) { return 10200; }
 extern "C" const char* rte_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" int rte_disc_create(const rte_disc_desc* d, int device, rte_disc_t* out) {
@@ -268,6 +268,7 @@ void pick_groups(rte_batch_t b, int n_active, int* dpw, int* n_groups, const Swe
         break;
       }
     }
+    use = std::max(use, b->min_dpw);
   }
   const int k = use == 1 ? 0 : use == 2 ? 1 : use == 4 ? 2 : 3;
   if (b->disc->dim == 2 && b->groups_all_dev.p) {
@@ -302,7 +303,7 @@ extern "C" int rte_batch_tune(rte_batch_t b, int dpw) {
   if (!b) return fail(RTE_EINVAL, "rte_batch_tune: null argument");
   if (b->disc->dim == 1) return RTE_OK;
   b->dpw_dynamic = dpw == 0;
-  if (dpw == 0) dpw = auto_dpw(b->disc, b->B);
+  if (dpw == 0) dpw = std::max(auto_dpw(b->disc, b->B), b->min_dpw);
   if (dpw != 1 && dpw != 2 && dpw != 4 && dpw != 8) return fail(RTE_EINVAL, "dirs_per_warp must be 0, 1, 2, 4 or 8");
   DeviceGuard g(b->disc->device);
   const int old = b->dpw;
@@ -324,7 +325,17 @@ extern "C" int rte_batch_tune(rte_batch_t b, int dpw) {
   return RTE_OK;
 }
 
+size_t rte_batch_s::bytes() const {
+  size_t t = 8 * (sigma_t.n + sigma_s.n + G0.n + inflow.n + tables.n + partial.n + S.n + norms.n + work.n);
+  t += 4 * (tables32.n + S32.n + partial32.n);
+  t += sizeof(rte::SweepGroup) * (groups_dev.n + groups_all_dev.n) + slot_mask.n;
+  return t + rte::dsa_bytes(this);
+}
+
 rte_batch_s::~rte_batch_s() {
+  if (stage) cudaFreeHost(stage);
+  if (stage_mask) cudaFreeHost(stage_mask);
+  if (stage_ev) cudaEventDestroy(stage_ev);
   rte::dsa_state_free(dsa);
   for (auto& e : sweep_ev) {
     cudaEventDestroy(e.first);
@@ -397,8 +408,6 @@ extern "C" int rte_batch_create(rte_disc_t disc, int B, rte_batch_t* out) {
   auto* b = new rte_batch_s();
   b->disc = disc;
   b->B = B;
-  b->dpw = disc->dim == 1 ? 1 : auto_dpw(disc, B);
-  make_groups(b);
   std::vector<SweepGroup> all;
   if (disc->dim == 2) {
     if (cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, disc->device) != cudaSuccess)
@@ -409,8 +418,16 @@ extern "C" int rte_batch_create(rte_disc_t disc, int B, rte_batch_t* out) {
       b->gcount[k] = (int)g.size();
       all.insert(all.end(), g.begin(), g.end());
     }
+    // per-instance partial sums stay within kPartialBytes: large discretisations use wider groups
+    int k = 0;
+    while (k < 3 && (size_t)b->gcount[k] * disc->n_dof * sizeof(double) > kPartialBytes) ++k;
+    b->min_dpw = 1 << k;
   }
-  const size_t max_groups = disc->dim == 2 ? (size_t)b->gcount[0] : b->groups.size();
+  b->dpw = disc->dim == 1 ? 1 : std::max(auto_dpw(disc, B), b->min_dpw);
+  make_groups(b);
+  const size_t max_groups =
+      disc->dim == 2 ? (size_t)b->gcount[b->min_dpw == 1 ? 0 : b->min_dpw == 2 ? 1 : b->min_dpw == 4 ? 2 : 3]
+                     : b->groups.size();
   const size_t nb = (size_t)B;
   const size_t tab = disc->dim == 1 ? kTab1D : kTab2D;
   int st = RTE_OK;
@@ -487,7 +504,102 @@ extern "C" int rte_batch_set_params(rte_batch_t b, const double* sigma_t, const 
     RTE_TRY(dsa_setup(b, 0));
   }
   RTE_CUDA_TRY(cudaDeviceSynchronize());
+  b->slot_set.assign(b->B, 1);
   b->params_set = true;
+  return RTE_OK;
+}
+
+namespace rte {
+int set_slots(rte_batch_t b, int n, const int* slots, const double* sigma_t, const double* sigma_s,
+              const double* source, const double* inflow, cudaStream_t st) {
+  rte_disc_s* d = b->disc;
+  const int B = b->B, nm = d->n_mat, nc = d->n_cells, ni = 2 * d->dim;
+  const size_t per = 2 * (size_t)nm + nc + 4;
+  for (int i = 0; i < n; ++i) {
+    if (slots[i] < 0 || slots[i] >= B) return fail(RTE_EINVAL, "slot out of range");
+    for (int j = 0; j < i; ++j)
+      if (slots[j] == slots[i]) return fail(RTE_EINVAL, "slot listed twice");
+  }
+  for (size_t k = 0; k < (size_t)n * nm; ++k) {
+    if (!std::isfinite(sigma_t[k]) || !std::isfinite(sigma_s[k]))
+      return fail(RTE_EINVAL, "cross section is not finite");
+    if (!(sigma_t[k] > 0.0) || sigma_s[k] < 0.0 || sigma_s[k] > sigma_t[k])
+      return fail(RTE_EINVAL, "need sigma_t > 0 and 0 <= sigma_s <= sigma_t");
+  }
+  for (size_t k = 0; k < (size_t)n * nc; ++k)
+    if (!std::isfinite(source[k])) return fail(RTE_EINVAL, "source is not finite");
+  for (size_t k = 0; k < (size_t)n * ni; ++k)
+    if (!std::isfinite(inflow[k])) return fail(RTE_EINVAL, "inflow is not finite");
+  if (!b->stage) {
+    RTE_CUDA_TRY(cudaHostAlloc((void**)&b->stage, sizeof(double) * per * B, cudaHostAllocDefault));
+    RTE_CUDA_TRY(cudaHostAlloc((void**)&b->stage_mask, B, cudaHostAllocDefault));
+    RTE_CUDA_TRY(cudaEventCreateWithFlags(&b->stage_ev, cudaEventDisableTiming));
+    RTE_TRY(b->slot_mask.alloc(B));
+  } else {
+    RTE_CUDA_TRY(cudaEventSynchronize(b->stage_ev));  // the previous upload has been consumed
+  }
+  if (b->sigma_t_h.size() != (size_t)B * nm) {
+    b->sigma_t_h.assign((size_t)B * nm, 1.0);
+    b->sigma_s_h.assign((size_t)B * nm, 0.0);
+    b->source_h.assign((size_t)B * nc, 0.0);
+    b->inflow_h.assign(4 * (size_t)B, 0.0);
+  }
+  if (b->slot_set.size() != (size_t)B) b->slot_set.assign(B, 0);
+  std::memset(b->stage_mask, 0, B);
+  const double sq = std::sqrt(d->hx * d->hy);
+  for (int i = 0; i < n; ++i) {
+    const int sl = slots[i];
+    double* p = b->stage + per * sl;
+    for (int m = 0; m < nm; ++m) {
+      p[m] = b->sigma_t_h[(size_t)sl * nm + m] = sigma_t[(size_t)i * nm + m];
+      p[nm + m] = b->sigma_s_h[(size_t)sl * nm + m] = sigma_s[(size_t)i * nm + m];
+    }
+    for (int c = 0; c < nc; ++c) {
+      b->source_h[(size_t)sl * nc + c] = source[(size_t)i * nc + c];
+      p[2 * nm + c] = source[(size_t)i * nc + c] * sq;  // zeroth moment of the cell source
+    }
+    for (int k = 0; k < 4; ++k)
+      p[2 * nm + nc + k] = b->inflow_h[4 * (size_t)sl + k] = k < ni ? inflow[(size_t)i * ni + k] : 0.0;
+    b->stage_mask[sl] = 1;
+    b->slot_set[sl] = 1;
+    RTE_CUDA_TRY(cudaMemcpyAsync(b->sigma_t.p + (size_t)sl * nm, p, sizeof(double) * nm, cudaMemcpyHostToDevice, st));
+    RTE_CUDA_TRY(cudaMemcpyAsync(b->sigma_s.p + (size_t)sl * nm, p + nm, sizeof(double) * nm, cudaMemcpyHostToDevice, st));
+    RTE_CUDA_TRY(cudaMemcpyAsync(b->G0.p + (size_t)sl * nc, p + 2 * nm, sizeof(double) * nc, cudaMemcpyHostToDevice, st));
+    RTE_CUDA_TRY(cudaMemcpyAsync(b->inflow.p + 4 * (size_t)sl, p + 2 * nm + nc, sizeof(double) * 4, cudaMemcpyHostToDevice, st));
+  }
+  RTE_CUDA_TRY(cudaMemcpyAsync(b->slot_mask.p, b->stage_mask, B, cudaMemcpyHostToDevice, st));
+  {
+    PhaseScope ps(b, 3, st);
+    RTE_TRY(setup_tables(b, st, b->slot_mask.p));
+    b->tables32_stale = true;
+    RTE_TRY(dsa_setup(b, st, b->slot_mask.p));
+  }
+  RTE_CUDA_TRY(cudaEventRecord(b->stage_ev, st));
+  bool all = true;
+  for (int k = 0; k < B; ++k) all = all && b->slot_set[k];
+  if (all) b->params_set = true;
+  return RTE_OK;
+}
+}  // namespace rte
+
+extern "C" int rte_batch_set_slots(rte_batch_t b, int n, const int* slots, const double* sigma_t,
+                                   const double* sigma_s, const double* source,
+                                   const double* inflow, void* stream) {
+  if (!b || n < 0 || (n > 0 && (!slots || !sigma_t || !sigma_s || !source || !inflow)))
+    return fail(RTE_EINVAL, "rte_batch_set_slots: null argument");
+  if (n == 0) return RTE_OK;
+  DeviceGuard g(b->disc->device);
+  return set_slots(b, n, slots, sigma_t, sigma_s, source, inflow, (cudaStream_t)stream);
+}
+
+extern "C" int rte_batch_info(rte_batch_t b, int64_t* info) {
+  if (!b || !info) return fail(RTE_EINVAL, "rte_batch_info: null argument");
+  info[0] = b->B;
+  info[1] = (int64_t)b->bytes();
+  info[2] = b->dpw;
+  info[3] = b->min_dpw;
+  info[4] = b->dpw_dynamic ? 1 : 0;
+  info[5] = b->params_set ? 1 : 0;
   return RTE_OK;
 }
 

@@ -85,6 +85,7 @@ struct DevBuf {
 constexpr int kTab2D = 32;  // doubles per (material, direction) sweep table in 2D
 constexpr int kTab1D = 8;   // ... in 1D (Minv 2x2, Px 2x1, pad)
 constexpr int kMaxDirsPerWarp = 8;
+constexpr size_t kPartialBytes = size_t(64) << 20;  // per-instance sweep partial sums, upper bound
 
 // A distinct swept direction: X-Y geometry depends on (v_x, v_y) only.
 struct Dir {
@@ -121,7 +122,7 @@ struct rte_disc_s {
 namespace rte {
 struct DsaState;   // 2D/1D DSA per-batch state (dsa.cu)
 void dsa_state_free(DsaState*);
-int dsa_setup(rte_batch_t batch, cudaStream_t st);
+int dsa_setup(rte_batch_t batch, cudaStream_t st, const uint8_t* mask = nullptr);
 }
 
 struct rte_batch_s {
@@ -129,6 +130,7 @@ struct rte_batch_s {
   int B = 0;
   bool params_set = false;
   int dpw = 4;                        // directions per warp in the 2D sweep (preferred / fixed)
+  int min_dpw = 1;                    // smallest dpw the partial-sum buffer is sized for
   std::vector<rte::SweepGroup> groups;
   rte::DevBuf<rte::SweepGroup> groups_dev;
   // group tables for dpw = 1, 2, 4, 8; with dpw_dynamic each launch picks the largest dpw (up to
@@ -151,6 +153,12 @@ struct rte_batch_s {
   rte::DevBuf<unsigned long long> norms;  // [B][2] stop-test norms as ordered bit patterns
   rte::DevBuf<double> work;               // [B][n_dof] x 4 iteration scratch for rte_solve
   rte::DsaState* dsa = nullptr;
+  // pinned host staging for per-slot parameter uploads (rte_batch_set_slots), allocated on use
+  double* stage = nullptr;
+  uint8_t* stage_mask = nullptr;
+  rte::DevBuf<uint8_t> slot_mask;         // [B] instances touched by the last slot upload
+  std::vector<uint8_t> slot_set;          // parameters uploaded for this instance
+  cudaEvent_t stage_ev = nullptr;         // the last upload's copies have been issued before it
   // optional phase timing with CUDA events on the launching stream (rte_batch_timing)
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> sweep_ev;
@@ -159,6 +167,7 @@ struct rte_batch_s {
   struct PhaseEv { int phase; cudaEvent_t a, b; };
   std::vector<PhaseEv> phase_ev;   // phases: 0 FP32 sweep, 1 DSA, 2 ROM, 3 set-up
   long long phase_calls[4] = {0, 0, 0, 0};
+  size_t bytes() const;                   // device memory held by the batch
   ~rte_batch_s();
 };
 
@@ -195,11 +204,15 @@ int sweep_launch(rte_batch_t b, const double* rho_in, double* rho_out, double* p
 int norms_to_host(rte_batch_t b, double* host, cudaStream_t st);
 int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, const uint8_t* active,
                      cudaStream_t st, int n_active, bool zero_norms = true);
-int setup_tables(rte_batch_t b, cudaStream_t st);
+int setup_tables(rte_batch_t b, cudaStream_t st, const uint8_t* mask = nullptr);
+size_t dsa_bytes(const rte_batch_s* b);
+// per-slot parameter upload: instances slots[0..n) take the given parameters (host arrays)
+int set_slots(rte_batch_t b, int n, const int* slots, const double* sigma_t, const double* sigma_s,
+              const double* source, const double* inflow, cudaStream_t st);
 int correction_source_launch(rte_batch_t b, const double* rs, const double* rp, double* R,
                              const uint8_t* active, cudaStream_t st);
 int axpy_launch(rte_batch_t b, const double* x, const double* y, double* out,
-                const uint8_t* active, cudaStream_t st);  // out = x + y
+                const uint8_t* active, cudaStream_t st);  // out = x + y (x when y is null)
 int dsa_apply(rte_batch_t b, const double* R, double* drho, double rtol, int max_it,
               const uint8_t* active, int* iters, cudaStream_t st);
 }  // namespace rte
@@ -211,12 +224,53 @@ struct rte_rom_s {
   int r = 0, n_snap = 0;
   std::vector<double> sv;
   double eps_equiv = 0;
-  rte::DevBuf<double> U;       // [r][n_dirs][n_dof]: basis vectors, one row block per direction
+  rte::DevBuf<double> U;       // [r][n_dirs][n_dof]: basis vectors (offline only, then freed)
   rte::DevBuf<double> U_rho;   // [r][n_dof]
   rte::DevBuf<double> U_iso;   // [r][n_dof]
+  rte::DevBuf<double> U_iso0;  // [r][n_cells] zeroth-moment rows of U_iso
   std::vector<double> A0;      // [r][r]
   std::vector<double> Aa, As;  // [n_mat][r][r]
   rte::DevBuf<double> A0_dev, Aa_dev, As_dev;
   rte::RomOnline* online = nullptr;
   ~rte_rom_s();
 };
+
+namespace rte {
+int rom_prepare(rte_rom_t rom, rte_batch_t bt, cudaStream_t st, const uint8_t* mask = nullptr);
+int rom_correction(rte_rom_t rom, rte_batch_t bt, const double* R, double* drho,
+                   const uint8_t* active, cudaStream_t st);
+// ROMIG initial guess rho0 = U^rho A_{mu,r}^{-1} (U^iso)^T G for the instances in `mask`
+int rom_guess_launch(rte_rom_t rom, rte_batch_t bt, double* rho0, const uint8_t* mask,
+                     cudaStream_t st);
+
+// Per-batch state of Alg. 1 / Alg. 2 for instances that may start and finish at different
+// times: one instance is one slot of the batch, with its own iteration count, tolerance and
+// report.  si_launch issues one sweep of every running instance and the asynchronous copy of
+// the stop-test norms; si_finish waits for those norms, applies the stop test and issues the
+// corrections.  Both only enqueue work on the stream, so several batches on several streams
+// progress concurrently from one host thread.
+struct SiState {
+  rte_batch_t bt = nullptr;
+  int B = 0;
+  rte_solve_opts o{};
+  rte_rom_t rom = nullptr;
+  bool mixed = false;                 // FP32 sweeps until the change drops below fp32_switch
+  uint8_t* hm = nullptr;              // pinned [6][B]: act, lo, hi (sweep) | act, rom, dsa (correction)
+  unsigned long long* hn = nullptr;   // pinned [2B] stop-test norms (ordered bit patterns)
+  DevBuf<uint8_t> dm;                 // device copy of hm
+  cudaEvent_t ev = nullptr;           // recorded after the norms copy
+  std::vector<uint8_t> act, lowp, done;
+  std::vector<int> it, status;
+  std::vector<double> eps;
+  std::vector<rte_solve_report> rep;
+  bool in_flight = false;
+  double* result = nullptr;           // [B][n_dof] destination of finished instances (device or pinned host)
+  int init(rte_batch_t b, const rte_solve_opts& opts, rte_rom_t rom_c, double* result_dst);
+  void begin(int b, double eps_b);    // the instance's initial iterate is already in slot b of work
+  int n_active() const;
+  ~SiState();
+};
+int si_launch(SiState& s, cudaStream_t st, double* psi_cur);
+int event_ready(cudaEvent_t ev, bool* ready);
+int si_finish(SiState& s, cudaStream_t st, double* history);
+}  // namespace rte

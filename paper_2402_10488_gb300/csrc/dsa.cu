@@ -468,10 +468,12 @@ __global__ void __launch_bounds__(512) coarse_vcycle_kernel(const CoarseArgs A, 
 __global__ void class_mass_kernel(int l, int n_mat, int n_class, int n_class_f, int nxf, int nxc,
                                   const int32_t* mixed, const int32_t* cls_f,
                                   const double* sigma_t, const double* sigma_s, int B,
-                                  const double* Maf, const double* Mtf, double* Ma, double* Mt) {
+                                  const double* Maf, const double* Mtf, double* Ma, double* Mt,
+                                  const uint8_t* mask) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= B * n_class) return;
   const int b = t / n_class, k = t % n_class;
+  if (mask && !mask[b]) return;
   double ma[16] = {0}, mt[16] = {0};
   if (k < n_mat) {
     const double st = sigma_t[b * n_mat + k], sa = st - sigma_s[b * n_mat + k];
@@ -507,9 +509,11 @@ __global__ void class_mass_kernel(int l, int n_mat, int n_class, int n_class_f, 
 // D = geo + blockdiag(Ma, 3<vx^2> Mt, 3<vy^2> Mt) per (instance, class); store D, D^{-1} (FP32)
 // and, when diag64 != nullptr, D in FP64.
 __global__ void class_diag_kernel(const double* geo, const double* Ma, const double* Mt, double cx,
-                                  double cy, int n, float* diag, float* dinv, double* diag64) {
+                                  double cy, int n, float* diag, float* dinv, double* diag64,
+                                  int n_class, const uint8_t* mask) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
+  if (mask && !mask[t / n_class]) return;
   double a[NB * 24];
   for (int r = 0; r < NB; ++r)
     for (int c = 0; c < NB; ++c) {
@@ -657,9 +661,10 @@ struct Blocks1D {
 
 __global__ void dsa1d_factor_kernel(Blocks1D K, const double* sigma_t, const double* sigma_s,
                                     const int32_t* mat, int nx, int n_mat, int B, double* Dpinv,
-                                    double* Mfac) {
+                                    double* Mfac, const uint8_t* mask) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
+  if (mask && !mask[b]) return;
   double Dp[16], Di[16], tmp[16];
   for (int c = 0; c < nx; ++c) {
     const int m = mat[c];
@@ -891,15 +896,40 @@ static int dsa_build_levels(rte_batch_t bt) {
   const size_t n = (size_t)B * d->n_cells * NB;
   RTE_TRY(s->xtot.alloc(n));
   RTE_TRY(s->borig.alloc(n));
+  return RTE_OK;
+}
+
+// FGMRES bases and work vectors, allocated on the first Krylov solve of the batch
+static int dsa_krylov_alloc(rte_batch_t bt) {
+  DsaState* s = bt->dsa;
+  if (s->V.p) return RTE_OK;
+  const size_t n = (size_t)bt->B * bt->disc->n_cells * NB;
   RTE_TRY(s->V.alloc((size_t)(s->m + 1) * n));
   RTE_TRY(s->Z.alloc((size_t)s->m * n));
   RTE_TRY(s->w.alloc(n));
   RTE_TRY(s->xs.alloc(n));
-  RTE_TRY(s->dots_dev.alloc((size_t)B * (s->m + 1)));
+  RTE_TRY(s->dots_dev.alloc((size_t)bt->B * (s->m + 1)));
   return RTE_OK;
 }
 
-int dsa_setup(rte_batch_t bt, cudaStream_t st) {
+// device bytes held by the batch's DSA state
+size_t dsa_bytes(const rte_batch_s* b) {
+  const DsaState* s = b->dsa;
+  if (!s) return 0;
+  size_t t = 0;
+  auto add = [&](size_t n, size_t e) { t += n * e; };
+  add(s->Dpinv.n + s->Mfac.n + s->work1.n, 8);
+  add(s->off64.n + s->diag64.n + s->V.n + s->Z.n + s->w.n + s->xs.n + s->dots_dev.n, 8);
+  add(s->xtot.n + s->borig.n, 4);
+  for (size_t l = 0; l < s->Ma.size(); ++l) {
+    add(s->Ma[l]->n + s->Mt[l]->n + s->geo64[l]->n, 8);
+    add(s->diag32[l]->n + s->dinv32[l]->n + s->xl[l]->n + s->bl[l]->n + s->rl[l]->n, 4);
+    add(s->cls[l]->n + s->mixed[l]->n, 4);
+  }
+  return t;
+}
+
+int dsa_setup(rte_batch_t bt, cudaStream_t st, const uint8_t* mask) {
   const rte_disc_s* d = bt->disc;
   const int B = bt->B;
   if (!bt->dsa) bt->dsa = new DsaState();
@@ -927,12 +957,14 @@ int dsa_setup(rte_batch_t bt, cudaStream_t st) {
     fill(s->K1.Dd, o.DCd, o.DJd);
     fill(s->K1.Lw, o.DCw, o.DJw);
     fill(s->K1.Ue, o.DCe, o.DJe);
-    RTE_TRY(s->Dpinv.alloc((size_t)B * d->nx * 16));
-    RTE_TRY(s->Mfac.alloc((size_t)B * d->nx * 16));
-    RTE_TRY(s->work1.alloc((size_t)B * d->nx * 4));
+    if (!s->Dpinv.p) {
+      RTE_TRY(s->Dpinv.alloc((size_t)B * d->nx * 16));
+      RTE_TRY(s->Mfac.alloc((size_t)B * d->nx * 16));
+      RTE_TRY(s->work1.alloc((size_t)B * d->nx * 4));
+    }
     dsa1d_factor_kernel<<<(B + 63) / 64, 64, 0, st>>>(s->K1, bt->sigma_t.p, bt->sigma_s.p,
                                                       d->mat_id.p, d->nx, d->n_mat, B,
-                                                      s->Dpinv.p, s->Mfac.p); RTE_NOTE_LAUNCH();
+                                                      s->Dpinv.p, s->Mfac.p, mask); RTE_NOTE_LAUNCH();
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
   }
@@ -943,11 +975,13 @@ int dsa_setup(rte_batch_t bt, cudaStream_t st) {
     class_mass_kernel<<<(n + 127) / 128, 128, 0, st>>>(
         l, d->n_mat, s->ncls[l], l ? s->ncls[l - 1] : 0, l ? s->lnx[l - 1] : 0, s->lnx[l],
         s->mixed[l]->p, l ? s->cls[l - 1]->p : nullptr, bt->sigma_t.p, bt->sigma_s.p, B,
-        l ? s->Ma[l - 1]->p : nullptr, l ? s->Mt[l - 1]->p : nullptr, s->Ma[l]->p, s->Mt[l]->p); RTE_NOTE_LAUNCH();
+        l ? s->Ma[l - 1]->p : nullptr, l ? s->Mt[l - 1]->p : nullptr, s->Ma[l]->p, s->Mt[l]->p,
+        mask); RTE_NOTE_LAUNCH();
     class_diag_kernel<<<(n + 63) / 64, 64, 0, st>>>(s->geo64[l]->p, s->Ma[l]->p, s->Mt[l]->p,
                                                     3.0 * d->mom.xx, 3.0 * d->mom.yy, n,
                                                     s->diag32[l]->p, s->dinv32[l]->p,
-                                                    l == 0 ? s->diag64.p : nullptr); RTE_NOTE_LAUNCH();
+                                                    l == 0 ? s->diag64.p : nullptr, s->ncls[l],
+                                                    mask); RTE_NOTE_LAUNCH();
     RTE_CUDA_TRY(cudaGetLastError());
   }
   return RTE_OK;
@@ -1053,6 +1087,7 @@ static int dsa2d_fgmres(rte_batch_t bt, const double* R, double* drho, double rt
                         const uint8_t* active_in, int* iters_out, cudaStream_t st) {
   DsaState* s = bt->dsa;
   const rte_disc_s* d = bt->disc;
+  RTE_TRY(dsa_krylov_alloc(bt));
   const int B = bt->B, nc = d->n_cells, n = nc * NB, m = s->m;
   const size_t vstride = (size_t)B * n;
   const Fine F = fine_of(bt);

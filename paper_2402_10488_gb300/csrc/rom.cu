@@ -15,6 +15,8 @@
 // Online: ROMIG rho^(0) = U^rho A_{mu,r}^{-1} (U^iso)^T G (vacuum inflow); ROMSA
 // delta rho = dU^rho (dU^T A_mu dU)^{-1} (dU^iso)^T R (Eq. (rom_correction)).  The r x r systems
 // are assembled and LU-factored on the device once per parameter set.
+#include <cstdio>
+
 #include "common.cuh"
 
 namespace rte {
@@ -133,6 +135,14 @@ __global__ void rho_iso_kernel(const double* U, int r, int n_dirs, int n_dof, co
   U_iso[t] = si;
 }
 
+// U_iso0[i][c] = U_iso[i][c * P]: the zeroth-moment rows, contiguous for the ROMIG projection
+__global__ void iso0_kernel(const double* U_iso, int r, int n_cells, int P, double* U_iso0) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)r * n_cells) return;
+  const size_t i = t / n_cells, c = t % n_cells;
+  U_iso0[t] = U_iso[i * (size_t)n_cells * P + c * P];
+}
+
 // Y[i][d] = D_d U[i][d]: the upwind DG transport operator without Sigma_t (2D), with zero inflow.
 __global__ void transport_apply2d_kernel(const double* U, int r, int n_dirs, int nx, int ny,
                                          double hx, double hy, const double* dirs, double* Y) {
@@ -210,9 +220,11 @@ __global__ void transport_apply1d_kernel(const double* U, int r, int n_dirs, int
 // A_{mu,r} per instance and its LU factorisation with partial pivoting (one thread per instance).
 __global__ void rom_assemble_lu_kernel(const double* A0, const double* Aa, const double* As,
                                        int r, int n_mat, const double* sigma_t,
-                                       const double* sigma_s, int B, double* LU, int* piv) {
+                                       const double* sigma_s, int B, double* LU, int* piv,
+                                       const uint8_t* mask) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
+  if (mask && !mask[b]) return;
   double* A = LU + (size_t)b * r * r;
   for (int e = 0; e < r * r; ++e) {
     double v = A0[e];
@@ -464,6 +476,9 @@ static int reduce_operators(rte_rom_t rom, cudaStream_t st) {
   RTE_TRY(rom->U_iso.alloc((size_t)r * n));
   rho_iso_kernel<<<(unsigned)(((size_t)r * n + 255) / 256), 256, 0, st>>>(
       rom->U.p, r, d->n_dirs, n, d->dir_dev.p, rom->U_rho.p, rom->U_iso.p); RTE_NOTE_LAUNCH();
+  RTE_TRY(rom->U_iso0.alloc((size_t)r * d->n_cells));
+  iso0_kernel<<<(unsigned)(((size_t)r * d->n_cells + 255) / 256), 256, 0, st>>>(
+      rom->U_iso.p, r, d->n_cells, d->P, rom->U_iso0.p); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   // multiplicity per direction as the row weight
   std::vector<double> mult(d->n_dirs);
@@ -498,11 +513,13 @@ static int reduce_operators(rte_rom_t rom, cudaStream_t st) {
   RTE_CUDA_TRY(cudaMemcpyAsync(rom->Aa_dev.p, Aa.data(), 8 * Aa.size(), cudaMemcpyHostToDevice, st));
   RTE_CUDA_TRY(cudaMemcpyAsync(rom->As_dev.p, rom->As.data(), 8 * Aa.size(), cudaMemcpyHostToDevice, st));
   RTE_CUDA_TRY(cudaStreamSynchronize(st));
+  rom->U.release();  // the online stage needs U^rho, U^iso and the reduced operators only
   return RTE_OK;
 }
 
-// Assemble and factor A_{mu,r} for every instance of `bt` (cached per batch handle).
-int rom_prepare(rte_rom_t rom, rte_batch_t bt, cudaStream_t st) {
+// Assemble and factor A_{mu,r} for the instances of `bt` in `mask` (all when null); the factors
+// are cached in the ROM handle for that batch.
+int rom_prepare(rte_rom_t rom, rte_batch_t bt, cudaStream_t st, const uint8_t* mask) {
   if (!rom->online) rom->online = new RomOnline();
   RomOnline* o = rom->online;
   const int r = rom->r, B = bt->B;
@@ -513,9 +530,26 @@ int rom_prepare(rte_rom_t rom, rte_batch_t bt, cudaStream_t st) {
   }
   rom_assemble_lu_kernel<<<(B + 63) / 64, 64, 0, st>>>(rom->A0_dev.p, rom->Aa_dev.p, rom->As_dev.p,
                                                        r, bt->disc->n_mat, bt->sigma_t.p,
-                                                       bt->sigma_s.p, B, o->lu.p, o->piv.p); RTE_NOTE_LAUNCH();
+                                                       bt->sigma_s.p, B, o->lu.p, o->piv.p,
+                                                       mask); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   o->batch = bt;
+  return RTE_OK;
+}
+
+// ROMIG (Sec. 3.1.2): with vacuum inflow U^T b = (U^iso)^T G and G has only its zeroth moment per
+// cell, so the projection reads the k = 0 rows of U^iso, kept contiguous as U_iso0 [r][n_cells].
+int rom_guess_launch(rte_rom_t rom, rte_batch_t b, double* rho0, const uint8_t* mask,
+                     cudaStream_t st) {
+  RTE_TRY(rom_prepare(rom, b, st, mask));
+  const int r = rom->r, n = b->disc->n_dof, B = b->B, nc = b->disc->n_cells;
+  RomOnline* o = rom->online;
+  project_kernel<<<dim3(r, B), 256, 0, st>>>(rom->U_iso0.p, nc, b->G0.p, 1, 0, (size_t)nc,
+                                             o->proj.p, r, mask); RTE_NOTE_LAUNCH();
+  lu_solve_kernel<<<(B + 63) / 64, 64, 0, st>>>(o->lu.p, o->piv.p, o->proj.p, r, B, mask); RTE_NOTE_LAUNCH();
+  lift_kernel<<<dim3(std::min((n + 255) / 256, 1024), B), 256, 0, st>>>(rom->U_rho.p, n, o->proj.p, r,
+                                                                        rho0, mask); RTE_NOTE_LAUNCH();
+  RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;
 }
 
@@ -639,26 +673,7 @@ extern "C" int rte_rom_initial_guess(rte_rom_t rom, rte_batch_t b, double* rho0,
   DeviceGuard g(b->disc->device);
   cudaStream_t st = (cudaStream_t)stream;
   PhaseScope ps(b, 2, st);
-  RTE_TRY(rom_prepare(rom, b, st));
-  const int r = rom->r, n = b->disc->n_dof, B = b->B, P = b->disc->P;
-  // rhs_i = sum_c U_iso[i][c*P + 0] G0[c]: the source has only its zeroth moment
-  DevBuf<double> Ut0;
-  RTE_TRY(Ut0.alloc((size_t)r * b->disc->n_cells));
-  // gather the k = 0 rows of U_iso into a contiguous [r][n_cells] array
-  {
-    std::vector<double> h((size_t)r * n), h0((size_t)r * b->disc->n_cells);
-    RTE_CUDA_TRY(cudaMemcpy(h.data(), rom->U_iso.p, 8 * h.size(), cudaMemcpyDeviceToHost));
-    for (int i = 0; i < r; ++i)
-      for (int c = 0; c < b->disc->n_cells; ++c) h0[(size_t)i * b->disc->n_cells + c] = h[(size_t)i * n + (size_t)c * P];
-    RTE_CUDA_TRY(cudaMemcpy(Ut0.p, h0.data(), 8 * h0.size(), cudaMemcpyHostToDevice));
-  }
-  RomOnline* o = rom->online;
-  project_kernel<<<dim3(r, B), 256, 0, st>>>(Ut0.p, b->disc->n_cells, b->G0.p, 1, 0,
-                                             (size_t)b->disc->n_cells, o->proj.p, r, active); RTE_NOTE_LAUNCH();
-  lu_solve_kernel<<<(B + 63) / 64, 64, 0, st>>>(o->lu.p, o->piv.p, o->proj.p, r, B, active); RTE_NOTE_LAUNCH();
-  lift_kernel<<<dim3(std::min((n + 255) / 256, 1024), B), 256, 0, st>>>(rom->U_rho.p, n, o->proj.p, r,
-                                                                        rho0, active); RTE_NOTE_LAUNCH();
-  RTE_CUDA_TRY(cudaGetLastError());
+  RTE_TRY(rom_guess_launch(rom, b, rho0, active, st));
   RTE_CUDA_TRY(cudaStreamSynchronize(st));
   return RTE_OK;
 }
@@ -672,4 +687,115 @@ extern "C" int rte_romsa_correction(rte_rom_t rom, rte_batch_t b, const double* 
   cudaStream_t st = (cudaStream_t)stream;
   RTE_TRY(rom_prepare(rom, b, st));
   return rom_correction(rom, b, R, drho, active, st);
+}
+
+// ---- persistence of the online part of a ROM ------------------------------------------------
+// File layout (little-endian): magic "RTEROM01", int32 header {dim, nx, ny, n_phi, n_vz, n_mat,
+// r, n_snap, n_cells, P}, double {x0, x1, y0, y1, eps_equiv}, int32 mat_id[n_cells],
+// double sv[n_snap], A0[r][r], Aa[n_mat][r][r], As[n_mat][r][r], U_rho[r][n_dof], U_iso[r][n_dof].
+namespace {
+const char kRomMagic[8] = {'R', 'T', 'E', 'R', 'O', 'M', '0', '1'};
+
+struct FileCloser {
+  FILE* f;
+  ~FileCloser() {
+    if (f) fclose(f);
+  }
+};
+}  // namespace
+
+extern "C" int rte_rom_save(rte_rom_t rom, const char* path) {
+  if (!rom || !path) return fail(RTE_EINVAL, "rte_rom_save: null argument");
+  const rte_disc_s* d = rom->disc;
+  DeviceGuard g(d->device);
+  const int r = rom->r;
+  const size_t n = (size_t)r * d->n_dof;
+  std::vector<double> urho(n), uiso(n);
+  RTE_CUDA_TRY(cudaMemcpy(urho.data(), rom->U_rho.p, 8 * n, cudaMemcpyDeviceToHost));
+  RTE_CUDA_TRY(cudaMemcpy(uiso.data(), rom->U_iso.p, 8 * n, cudaMemcpyDeviceToHost));
+  FileCloser fc{fopen(path, "wb")};
+  if (!fc.f) return fail(RTE_EINVAL, std::string("rte_rom_save: cannot open ") + path);
+  const int32_t hdr[10] = {d->dim, d->nx, d->ny, d->n_phi, d->n_vz, d->n_mat, r, rom->n_snap,
+                           d->n_cells, d->P};
+  const double geo[5] = {d->x0, d->x1, d->y0, d->y1, rom->eps_equiv};
+  bool ok = fwrite(kRomMagic, 1, 8, fc.f) == 8 && fwrite(hdr, 4, 10, fc.f) == 10 &&
+            fwrite(geo, 8, 5, fc.f) == 5 &&
+            fwrite(d->mat_host.data(), 4, d->n_cells, fc.f) == (size_t)d->n_cells &&
+            fwrite(rom->sv.data(), 8, rom->sv.size(), fc.f) == rom->sv.size() &&
+            fwrite(rom->A0.data(), 8, rom->A0.size(), fc.f) == rom->A0.size() &&
+            fwrite(rom->Aa.data(), 8, rom->Aa.size(), fc.f) == rom->Aa.size() &&
+            fwrite(rom->As.data(), 8, rom->As.size(), fc.f) == rom->As.size() &&
+            fwrite(urho.data(), 8, n, fc.f) == n && fwrite(uiso.data(), 8, n, fc.f) == n;
+  if (!ok) return fail(RTE_EINVAL, std::string("rte_rom_save: write failed: ") + path);
+  return RTE_OK;
+}
+
+extern "C" int rte_rom_load(rte_disc_t disc, const char* path, rte_rom_t* out) {
+  if (!disc || !path || !out) return fail(RTE_EINVAL, "rte_rom_load: null argument");
+  *out = nullptr;
+  FileCloser fc{fopen(path, "rb")};
+  if (!fc.f) return fail(RTE_EINVAL, std::string("rte_rom_load: cannot open ") + path);
+  char magic[8];
+  int32_t hdr[10];
+  double geo[5];
+  if (fread(magic, 1, 8, fc.f) != 8 || std::memcmp(magic, kRomMagic, 8) != 0 ||
+      fread(hdr, 4, 10, fc.f) != 10 || fread(geo, 8, 5, fc.f) != 5)
+    return fail(RTE_EINVAL, "rte_rom_load: not a ROM file");
+  const rte_disc_s* d = disc;
+  if (hdr[0] != d->dim || hdr[1] != d->nx || hdr[2] != d->ny || hdr[3] != d->n_phi ||
+      hdr[4] != d->n_vz || hdr[5] != d->n_mat || hdr[8] != d->n_cells || hdr[9] != d->P ||
+      geo[0] != d->x0 || geo[1] != d->x1 || geo[2] != d->y0 || geo[3] != d->y1)
+    return fail(RTE_EINVAL, "rte_rom_load: the file was built on another discretisation");
+  const int r = hdr[6], n_snap = hdr[7];
+  if (r < 1 || n_snap < r || r > 4096 || n_snap > (1 << 20))
+    return fail(RTE_EINVAL, "rte_rom_load: bad ROM sizes");
+  std::vector<int32_t> mat(d->n_cells);
+  if (fread(mat.data(), 4, mat.size(), fc.f) != mat.size() || mat != d->mat_host)
+    return fail(RTE_EINVAL, "rte_rom_load: the file was built on another material map");
+  auto* rom = new rte_rom_s();
+  rom->disc = disc;
+  rom->r = r;
+  rom->n_snap = n_snap;
+  rom->eps_equiv = geo[4];
+  rom->sv.resize(n_snap);
+  rom->A0.resize((size_t)r * r);
+  rom->Aa.resize((size_t)d->n_mat * r * r);
+  rom->As.resize((size_t)d->n_mat * r * r);
+  const size_t n = (size_t)r * d->n_dof;
+  std::vector<double> urho(n), uiso(n);
+  bool ok = fread(rom->sv.data(), 8, rom->sv.size(), fc.f) == rom->sv.size() &&
+            fread(rom->A0.data(), 8, rom->A0.size(), fc.f) == rom->A0.size() &&
+            fread(rom->Aa.data(), 8, rom->Aa.size(), fc.f) == rom->Aa.size() &&
+            fread(rom->As.data(), 8, rom->As.size(), fc.f) == rom->As.size() &&
+            fread(urho.data(), 8, n, fc.f) == n && fread(uiso.data(), 8, n, fc.f) == n;
+  if (!ok) {
+    delete rom;
+    return fail(RTE_EINVAL, "rte_rom_load: truncated file");
+  }
+  DeviceGuard g(d->device);
+  int e = RTE_OK;
+  auto up = [&](DevBuf<double>& buf, const std::vector<double>& h) {
+    if (e != RTE_OK) return;
+    e = buf.alloc(h.size());
+    if (e == RTE_OK && cudaMemcpy(buf.p, h.data(), 8 * h.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      e = fail(RTE_ECUDA, "rte_rom_load: upload failed");
+  };
+  up(rom->U_rho, urho);
+  up(rom->U_iso, uiso);
+  up(rom->A0_dev, rom->A0);
+  up(rom->Aa_dev, rom->Aa);
+  up(rom->As_dev, rom->As);
+  if (e == RTE_OK) e = rom->U_iso0.alloc((size_t)r * d->n_cells);
+  if (e == RTE_OK) {
+    iso0_kernel<<<(unsigned)(((size_t)r * d->n_cells + 255) / 256), 256>>>(rom->U_iso.p, r, d->n_cells,
+                                                                          d->P, rom->U_iso0.p); RTE_NOTE_LAUNCH();
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+      e = fail(RTE_ECUDA, "rte_rom_load: set-up kernel failed");
+  }
+  if (e != RTE_OK) {
+    delete rom;
+    return e;
+  }
+  *out = rom;
+  return RTE_OK;
 }

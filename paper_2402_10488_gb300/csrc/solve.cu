@@ -5,152 +5,319 @@
 // (Eq. (rom_correction)) or, for ROMSAD, ROMSA iff 1 <= l <= theta and the change is at least
 // eps_ROMSAD.  Instances that have converged drop out of every later launch through a device
 // mask.  The only host round trip per iteration is the 2*B stop-test norms.
+//
+// The iteration is a small state machine per batch (SiState): instances are slots that may
+// start at different iterations (serving), and si_launch / si_finish only enqueue work, so one
+// host thread keeps several batches of different discretisations busy on their own streams
+// (rte_solve_many, the serving loop).
+#include <thread>
+
 #include "common.cuh"
 
 namespace rte {
-int rom_prepare(rte_rom_t rom, rte_batch_t bt, cudaStream_t st);
-int rom_correction(rte_rom_t rom, rte_batch_t bt, const double* R, double* drho,
-                   const uint8_t* active, cudaStream_t st);
 
+int SiState::init(rte_batch_t b, const rte_solve_opts& opts, rte_rom_t rom_c, double* result_dst) {
+  bt = b;
+  B = b->B;
+  o = opts;
+  rom = rom_c;
+  result = result_dst;
+  mixed = o.fp32_switch > 0.0 && b->disc->dim == 2;
+  if (!hm) {
+    RTE_CUDA_TRY(cudaHostAlloc((void**)&hm, 6 * (size_t)B, cudaHostAllocDefault));
+    RTE_CUDA_TRY(cudaHostAlloc((void**)&hn, sizeof(unsigned long long) * 2 * B, cudaHostAllocDefault));
+    RTE_TRY(dm.alloc(6 * (size_t)B));
+    RTE_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  }
+  std::memset(hm, 0, 6 * (size_t)B);
+  act.assign(B, 0);
+  lowp.assign(B, 0);
+  done.assign(B, 0);
+  it.assign(B, 0);
+  status.assign(B, RTE_OK);
+  eps.assign(B, o.eps);
+  rep.assign(B, rte_solve_report{0, 0, 0, 0, 0, 0.0, 0.0, 0});
+  in_flight = false;
+  return RTE_OK;
+}
+
+void SiState::begin(int b, double eps_b) {
+  act[b] = 1;
+  lowp[b] = mixed ? 1 : 0;
+  done[b] = 0;
+  it[b] = 0;
+  status[b] = RTE_OK;
+  eps[b] = eps_b;
+  rep[b] = rte_solve_report{0, 0, 0, 0, 0, 0.0, 0.0, 0};
+}
+
+int SiState::n_active() const {
+  int n = 0;
+  for (int b = 0; b < B; ++b) n += act[b];
+  return n;
+}
+
+SiState::~SiState() {
+  if (hm) cudaFreeHost(hm);
+  if (hn) cudaFreeHost(hn);
+  if (ev) cudaEventDestroy(ev);
+}
+
+// One sweep of every running instance: rho^(l,*) = L rho^(l-1) + b (FP32 for instances still in
+// the low-precision phase), then the asynchronous copy of the stop-test norms.
+int si_launch(SiState& s, cudaStream_t st, double* psi_cur) {
+  rte_batch_t bt = s.bt;
+  const int B = s.B;
+  const size_t nb = (size_t)B * bt->disc->n_dof;
+  double* rho_prev = bt->work.p;
+  double* rho_star = bt->work.p + nb;
+  uint8_t *h_act = s.hm, *h_lo = s.hm + B, *h_hi = s.hm + 2 * B;
+  int n_lo = 0, n_hi = 0;
+  for (int b = 0; b < B; ++b) {
+    const bool lo = s.act[b] && s.lowp[b] && psi_cur == nullptr;
+    h_act[b] = s.act[b];
+    h_lo[b] = lo;
+    h_hi[b] = s.act[b] && !lo;
+    n_lo += h_lo[b], n_hi += h_hi[b];
+  }
+  if (n_lo + n_hi == 0) return RTE_OK;
+  RTE_CUDA_TRY(cudaMemcpyAsync(s.dm.p, s.hm, 3 * (size_t)B, cudaMemcpyHostToDevice, st));
+  if (n_lo == 0) {
+    RTE_TRY(sweep_launch(bt, rho_prev, rho_star, psi_cur, 1, s.dm.p, st, true, n_hi));
+  } else {
+    RTE_CUDA_TRY(cudaMemsetAsync(bt->norms.p, 0, sizeof(unsigned long long) * 2 * B, st));
+    RTE_TRY(sweep_launch_f32(bt, rho_prev, rho_star, s.dm.p + B, st, n_lo, false));
+    if (n_hi > 0)
+      RTE_TRY(sweep_launch(bt, rho_prev, rho_star, psi_cur, 1, s.dm.p + 2 * B, st, true, n_hi, false));
+  }
+  RTE_CUDA_TRY(cudaMemcpyAsync(s.hn, bt->norms.p, sizeof(unsigned long long) * 2 * B,
+                               cudaMemcpyDeviceToHost, st));
+  RTE_CUDA_TRY(cudaEventRecord(s.ev, st));
+  s.in_flight = true;
+  return RTE_OK;
+}
+
+// Stop test and correction of the iteration launched by si_launch.  Finished instances (converged,
+// or at the iteration cap) have their result copied to s.result and are flagged in s.done.
+int si_finish(SiState& s, cudaStream_t st, double* history) {
+  if (!s.in_flight) return RTE_OK;
+  RTE_CUDA_TRY(cudaEventSynchronize(s.ev));
+  s.in_flight = false;
+  rte_batch_t bt = s.bt;
+  const rte_solve_opts& o = s.o;
+  const int B = s.B;
+  const size_t n = bt->disc->n_dof, nb = (size_t)B * n;
+  double* rho_prev = bt->work.p;
+  double* rho_star = bt->work.p + nb;
+  double* R = bt->work.p + 2 * nb;
+  double* drho = bt->work.p + 3 * nb;
+  uint8_t *h_corr = s.hm + 3 * B, *h_rom = s.hm + 4 * B, *h_dsa = s.hm + 5 * B;
+  std::vector<uint8_t> expire(B, 0);
+  bool any = false, anyd = false, anyr = false;
+  for (int b = 0; b < B; ++b) {
+    h_corr[b] = h_rom[b] = h_dsa[b] = 0;
+    if (!s.act[b]) continue;
+    const int l = ++s.it[b];
+    double delta, rinf;
+    std::memcpy(&delta, &s.hn[2 * b], sizeof(double));
+    std::memcpy(&rinf, &s.hn[2 * b + 1], sizeof(double));
+    if (history) history[(size_t)b * o.max_iter + (l - 1)] = delta;
+    rte_solve_report& rp = s.rep[b];
+    rp.n_sweep = l;
+    rp.last_change = delta;
+    rp.rho_inf = rinf;
+    const double test = o.rel ? delta / rinf : delta;
+    if (s.lowp[b]) {
+      rp.n_sweep32++;
+      if (test < o.fp32_switch) s.lowp[b] = 0;  // later sweeps of this instance in FP64
+    } else if (test < s.eps[b]) {
+      rp.converged = 1;
+      s.act[b] = 0;
+      s.done[b] = 1;
+      s.status[b] = RTE_OK;
+      RTE_CUDA_TRY(cudaMemcpyAsync(s.result + b * n, rho_star + b * n, sizeof(double) * n,
+                                   cudaMemcpyDefault, st));
+      continue;
+    }
+    if (l >= o.max_iter) expire[b] = 1;
+    any = true;
+    h_corr[b] = 1;
+    if (o.sa == RTE_SA_NONE) continue;
+    bool romsa = o.sa == RTE_SA_ROMSA;
+    if (o.sa == RTE_SA_ROMSAD)
+      romsa = o.schedule ? o.schedule[l - 1] != 0 : (l <= o.theta && delta >= o.eps_romsad);
+    if (romsa) h_rom[b] = 1, rp.n_romsa++, anyr = true;
+    else h_dsa[b] = 1, rp.n_dsa++, anyd = true;
+  }
+  if (any) {
+    RTE_CUDA_TRY(cudaMemcpyAsync(s.dm.p + 3 * B, h_corr, 3 * (size_t)B, cudaMemcpyHostToDevice, st));
+    const uint8_t* d_corr = s.dm.p + 3 * B;
+    if (o.sa == RTE_SA_NONE) {
+      // plain SI: rho^(l) = rho^(l,*)
+      RTE_TRY(axpy_launch(bt, rho_star, nullptr, rho_prev, d_corr, st));
+    } else {
+      RTE_TRY(correction_source_launch(bt, rho_star, rho_prev, R, d_corr, st));
+      if (anyd) {
+        std::vector<int> iters(B, 0);
+        PhaseScope ps(bt, 1, st);
+        int e = dsa_apply(bt, R, drho, o.dsa_rtol, o.dsa_max_it, s.dm.p + 5 * B, iters.data(), st);
+        if (e != RTE_OK && e != RTE_ENOCONV) return e;
+        for (int b = 0; b < B; ++b)
+          if (h_dsa[b]) s.rep[b].dsa_iters += iters[b];
+      }
+      if (anyr) {
+        PhaseScope ps(bt, 2, st);
+        RTE_TRY(rom_correction(s.rom, bt, R, drho, s.dm.p + 4 * B, st));
+      }
+      // rho^(l) = rho^(l,*) + delta rho^(l), written into the rho_prev slot
+      RTE_TRY(axpy_launch(bt, rho_star, drho, rho_prev, d_corr, st));
+    }
+  }
+  for (int b = 0; b < B; ++b)
+    if (expire[b]) {
+      s.act[b] = 0;
+      s.done[b] = 1;
+      s.status[b] = RTE_ENOCONV;
+      RTE_CUDA_TRY(cudaMemcpyAsync(s.result + b * n, rho_prev + b * n, sizeof(double) * n,
+                                   cudaMemcpyDefault, st));
+    }
+  return RTE_OK;
+}
+
+// All instances of the batch from the initial iterates in `rho` (overwritten with the results).
+// With psi_cur the angular flux of the latest sweep is kept, and the first `window` sweeps are
+// also copied to psi_win (training solves of the offline stage).
 int run_si(rte_batch_t bt, const rte_solve_opts* o, rte_rom_t rom_c, double* rho,
            rte_solve_report* reports, double* history, cudaStream_t st, double* psi_cur,
            double* psi_win, int window) {
   const rte_disc_s* d = bt->disc;
   const int B = bt->B;
-  const size_t n = d->n_dof, nb = (size_t)B * n;
-  double* rho_prev = bt->work.p;
-  double* rho_star = bt->work.p + nb;
-  double* R = bt->work.p + 2 * nb;
-  double* drho = bt->work.p + 3 * nb;
-  RTE_CUDA_TRY(cudaMemcpyAsync(rho_prev, rho, sizeof(double) * nb, cudaMemcpyDeviceToDevice, st));
-  std::vector<uint8_t> act(B, 1), use_rom(B, 0), use_dsa(B, 0);
-  // precision variant: instances start with FP32 sweeps and switch to FP64 below fp32_switch
-  const bool mixed = o->fp32_switch > 0.0 && d->dim == 2 && psi_cur == nullptr;
-  std::vector<uint8_t> lowp(B, mixed ? 1 : 0), act_lo(B, 0), act_hi(B, 0);
-  DevBuf<uint8_t> act_dev, rom_dev, dsa_dev, lo_dev, hi_dev;
-  RTE_TRY(act_dev.alloc(B));
-  RTE_TRY(lo_dev.alloc(B));
-  RTE_TRY(hi_dev.alloc(B));
-  RTE_TRY(rom_dev.alloc(B));
-  RTE_TRY(dsa_dev.alloc(B));
-  std::vector<rte_solve_report> rep(B);
-  for (auto& r : rep) r = rte_solve_report{0, 0, 0, 0, 0, 0.0, 0.0, 0};
+  const size_t n = d->n_dof;
   if ((o->sa == RTE_SA_ROMSA || o->sa == RTE_SA_ROMSAD) && !rom_c)
     return fail(RTE_EINVAL, "ROMSA/ROMSAD need a correction ROM");
+  SiState s;
+  rte_solve_opts oo = *o;
+  if (psi_cur) oo.fp32_switch = 0.0;
+  RTE_TRY(s.init(bt, oo, rom_c, rho));
+  RTE_CUDA_TRY(cudaMemcpyAsync(bt->work.p, rho, sizeof(double) * B * n, cudaMemcpyDeviceToDevice, st));
+  for (int b = 0; b < B; ++b) s.begin(b, o->eps);
   if (rom_c) {
     PhaseScope ps(bt, 2, st);
     RTE_TRY(rom_prepare(rom_c, bt, st));
   }
-  std::vector<double> norms(2 * B);
-  std::vector<int> iters(B);
-  int status = RTE_OK;
   const size_t psi_per = (size_t)d->n_dirs * n;
-  for (int l = 1; l <= o->max_iter; ++l) {
-    RTE_CUDA_TRY(cudaMemcpyAsync(act_dev.p, act.data(), B, cudaMemcpyHostToDevice, st));
-    double* psi = psi_cur;
-    int n_lo = 0, n_hi = 0;
-    for (int b = 0; b < B; ++b) {
-      act_lo[b] = act[b] && lowp[b];
-      act_hi[b] = act[b] && !lowp[b];
-      n_lo += act_lo[b], n_hi += act_hi[b];
-    }
-    if (n_lo == 0) {
-      RTE_TRY(sweep_launch(bt, rho_prev, rho_star, psi, 1, act_dev.p, st, true, n_hi));
-    } else {
-      RTE_CUDA_TRY(cudaMemsetAsync(bt->norms.p, 0, sizeof(unsigned long long) * 2 * B, st));
-      RTE_CUDA_TRY(cudaMemcpyAsync(lo_dev.p, act_lo.data(), B, cudaMemcpyHostToDevice, st));
-      RTE_TRY(sweep_launch_f32(bt, rho_prev, rho_star, lo_dev.p, st, n_lo, false));
-      if (n_hi > 0) {
-        RTE_CUDA_TRY(cudaMemcpyAsync(hi_dev.p, act_hi.data(), B, cudaMemcpyHostToDevice, st));
-        RTE_TRY(sweep_launch(bt, rho_prev, rho_star, psi, 1, hi_dev.p, st, true, n_hi, false));
-      }
-    }
+  for (int l = 1; s.n_active() > 0; ++l) {
+    RTE_TRY(si_launch(s, st, psi_cur));
     if (psi_win && l <= window)
       for (int b = 0; b < B; ++b)
-        if (act[b])
+        if (s.act[b])
           RTE_CUDA_TRY(cudaMemcpyAsync(psi_win + ((size_t)(l - 1) * B + b) * psi_per,
                                        psi_cur + (size_t)b * psi_per, sizeof(double) * psi_per,
                                        cudaMemcpyDeviceToDevice, st));
-    RTE_TRY(norms_to_host(bt, norms.data(), st));
-    bool any = false;
-    for (int b = 0; b < B; ++b) {
-      use_rom[b] = use_dsa[b] = 0;
-      if (!act[b]) continue;
-      const double delta = norms[2 * b], rinf = norms[2 * b + 1];
-      if (history) history[(size_t)b * o->max_iter + (l - 1)] = delta;
-      rep[b].n_sweep = l;
-      rep[b].last_change = delta;
-      rep[b].rho_inf = rinf;
-      const double test = o->rel ? delta / rinf : delta;
-      if (lowp[b]) {
-        rep[b].n_sweep32++;
-        if (test < o->fp32_switch) lowp[b] = 0;  // later sweeps of this instance in FP64
-      } else if (test < o->eps) {
-        rep[b].converged = 1;
-        act[b] = 0;
-        RTE_CUDA_TRY(cudaMemcpyAsync(rho + (size_t)b * n, rho_star + (size_t)b * n,
-                                     sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-        continue;
-      }
-      any = true;
-      bool romsa = o->sa == RTE_SA_ROMSA;
-      if (o->sa == RTE_SA_ROMSAD)
-        romsa = o->schedule ? o->schedule[l - 1] != 0 : (l <= o->theta && delta >= o->eps_romsad);
-      if (o->sa == RTE_SA_NONE) continue;
-      if (romsa) use_rom[b] = 1, rep[b].n_romsa++;
-      else use_dsa[b] = 1, rep[b].n_dsa++;
-    }
-    if (!any) break;
-    RTE_CUDA_TRY(cudaMemcpyAsync(act_dev.p, act.data(), B, cudaMemcpyHostToDevice, st));
-    if (o->sa == RTE_SA_NONE) {
-      // plain SI: rho^(l) = rho^(l,*)
-      std::swap(rho_prev, rho_star);
-      continue;
-    }
-    RTE_TRY(correction_source_launch(bt, rho_star, rho_prev, R, act_dev.p, st));
-    bool anyd = false, anyr = false;
-    for (int b = 0; b < B; ++b) anyd |= use_dsa[b] != 0, anyr |= use_rom[b] != 0;
-    if (anyd) {
-      RTE_CUDA_TRY(cudaMemcpyAsync(dsa_dev.p, use_dsa.data(), B, cudaMemcpyHostToDevice, st));
-      PhaseScope ps(bt, 1, st);
-      int s = dsa_apply(bt, R, drho, o->dsa_rtol, o->dsa_max_it, dsa_dev.p, iters.data(), st);
-      if (s != RTE_OK && s != RTE_ENOCONV) return s;
-      for (int b = 0; b < B; ++b)
-        if (use_dsa[b]) rep[b].dsa_iters += iters[b];
-    }
-    if (anyr) {
-      RTE_CUDA_TRY(cudaMemcpyAsync(rom_dev.p, use_rom.data(), B, cudaMemcpyHostToDevice, st));
-      PhaseScope ps(bt, 2, st);
-      RTE_TRY(rom_correction(rom_c, bt, R, drho, rom_dev.p, st));
-    }
-    // rho^(l) = rho^(l,*) + delta rho^(l), written into the rho_prev slot
-    RTE_TRY(axpy_launch(bt, rho_star, drho, rho_prev, act_dev.p, st));
+    RTE_TRY(si_finish(s, st, history));
   }
-  for (int b = 0; b < B; ++b)
-    if (act[b]) {
-      status = RTE_ENOCONV;
-      RTE_CUDA_TRY(cudaMemcpyAsync(rho + (size_t)b * n, rho_prev + (size_t)b * n,
-                                   sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-    }
   RTE_CUDA_TRY(cudaStreamSynchronize(st));
+  int status = RTE_OK;
+  for (int b = 0; b < B; ++b)
+    if (s.status[b] != RTE_OK) status = s.status[b];
   if (reports)
-    for (int b = 0; b < B; ++b) reports[b] = rep[b];
+    for (int b = 0; b < B; ++b) reports[b] = s.rep[b];
   return status;
+}
+
+// Readiness of an event without leaving cudaErrorNotReady in the thread's last-error slot.
+int event_ready(cudaEvent_t ev, bool* ready) {
+  const cudaError_t q = cudaEventQuery(ev);
+  if (q == cudaSuccess) {
+    *ready = true;
+    return RTE_OK;
+  }
+  if (q == cudaErrorNotReady) {
+    cudaGetLastError();
+    *ready = false;
+    return RTE_OK;
+  }
+  return fail(RTE_ECUDA, std::string("cudaEventQuery: ") + cudaGetErrorString(q));
 }
 
 }  // namespace rte
 
 using namespace rte;
 
-extern "C" int rte_solve(rte_batch_t b, const rte_solve_opts* o, rte_rom_t rom_c, double* rho,
-                         rte_solve_report* reports, double* history, void* stream) {
-  if (!b || !o || !rho) return fail(RTE_EINVAL, "rte_solve: null argument");
+static int check_opts(rte_batch_t b, const rte_solve_opts* o, rte_rom_t rom_c) {
   if (!b->params_set) return fail(RTE_ESTATE, "rte_solve: parameters not set");
   if (!(o->eps >= 0) || o->max_iter < 1 || o->sa < 0 || o->sa > 3 || !(o->fp32_switch >= 0))
     return fail(RTE_EINVAL, "rte_solve: bad options");
   if (o->sa != RTE_SA_NONE && b->disc->dim == 2 && (!(o->dsa_rtol >= 0) || o->dsa_max_it < 1))
     return fail(RTE_EINVAL, "rte_solve: bad DSA tolerance");
   if (rom_c && rom_c->disc != b->disc) return fail(RTE_EINVAL, "ROM built on another discretisation");
+  if ((o->sa == RTE_SA_ROMSA || o->sa == RTE_SA_ROMSAD) && !rom_c)
+    return fail(RTE_EINVAL, "ROMSA/ROMSAD need a correction ROM");
+  return RTE_OK;
+}
+
+extern "C" int rte_solve(rte_batch_t b, const rte_solve_opts* o, rte_rom_t rom_c, double* rho,
+                         rte_solve_report* reports, double* history, void* stream) {
+  if (!b || !o || !rho) return fail(RTE_EINVAL, "rte_solve: null argument");
+  RTE_TRY(check_opts(b, o, rom_c));
   DeviceGuard g(b->disc->device);
   return run_si(b, o, rom_c, rho, reports, history, (cudaStream_t)stream, nullptr, nullptr, 0);
+}
+
+extern "C" int rte_solve_many(int n, const rte_batch_t* batches, const rte_solve_opts* opts,
+                              const rte_rom_t* roms, double* const* rho,
+                              rte_solve_report* const* reports, void* const* streams) {
+  if (n < 1 || !batches || !opts || !rho) return fail(RTE_EINVAL, "rte_solve_many: null argument");
+  for (int k = 0; k < n; ++k) {
+    if (!batches[k] || !rho[k]) return fail(RTE_EINVAL, "rte_solve_many: null batch or rho");
+    if (batches[k]->disc->device != batches[0]->disc->device)
+      return fail(RTE_EINVAL, "rte_solve_many: batches on different devices");
+    for (int j = 0; j < k; ++j) {
+      if (batches[j] == batches[k]) return fail(RTE_EINVAL, "rte_solve_many: batch listed twice");
+      if (roms && roms[k] && roms[j] == roms[k])
+        return fail(RTE_EINVAL, "rte_solve_many: a ROM serves one batch at a time");
+    }
+    RTE_TRY(check_opts(batches[k], &opts[k], roms ? roms[k] : nullptr));
+  }
+  DeviceGuard g(batches[0]->disc->device);
+  std::vector<SiState> S(n);
+  std::vector<cudaStream_t> st(n);
+  for (int k = 0; k < n; ++k) {
+    rte_batch_t bt = batches[k];
+    rte_rom_t rom = roms ? roms[k] : nullptr;
+    st[k] = streams ? (cudaStream_t)streams[k] : nullptr;
+    RTE_TRY(S[k].init(bt, opts[k], rom, rho[k]));
+    RTE_CUDA_TRY(cudaMemcpyAsync(bt->work.p, rho[k], sizeof(double) * bt->B * bt->disc->n_dof,
+                                 cudaMemcpyDeviceToDevice, st[k]));
+    for (int b = 0; b < bt->B; ++b) S[k].begin(b, opts[k].eps);
+    if (rom) RTE_TRY(rom_prepare(rom, bt, st[k]));
+    RTE_TRY(si_launch(S[k], st[k], nullptr));
+  }
+  // event-driven round robin: whichever batch has its norms back is decided and relaunched
+  int running = n;
+  while (running > 0) {
+    bool progress = false;
+    running = 0;
+    for (int k = 0; k < n; ++k) {
+      if (!S[k].in_flight) continue;
+      bool ready = false;
+      RTE_TRY(event_ready(S[k].ev, &ready));
+      if (ready) {
+        RTE_TRY(si_finish(S[k], st[k], nullptr));
+        RTE_TRY(si_launch(S[k], st[k], nullptr));
+        progress = true;
+      }
+      running += S[k].in_flight;
+    }
+    if (!progress && running > 0) std::this_thread::yield();
+  }
+  int status = RTE_OK;
+  for (int k = 0; k < n; ++k) {
+    RTE_CUDA_TRY(cudaStreamSynchronize(st[k]));
+    for (int b = 0; b < S[k].B; ++b) {
+      if (S[k].status[b] != RTE_OK) status = S[k].status[b];
+      if (reports && reports[k]) reports[k][b] = S[k].rep[b];
+    }
+  }
+  return status;
 }

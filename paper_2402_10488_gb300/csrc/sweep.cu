@@ -50,12 +50,14 @@ __device__ __forceinline__ void inv4(double m[16]) {
 
 // One thread per (instance, material, direction): the cell tables.
 __global__ void tables2d_kernel(double* tables, const double* sigma_t, const double* dirs,
-                                int B, int n_mat, int n_dirs, double hx, double hy) {
+                                int B, int n_mat, int n_dirs, double hx, double hy,
+                                const uint8_t* mask) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= B * n_mat * n_dirs) return;
   const int d = idx % n_dirs;
   const int m = (idx / n_dirs) % n_mat;
   const int b = idx / (n_dirs * n_mat);
+  if (mask && !mask[b]) return;
   const double st = sigma_t[b * n_mat + m];
   const double vx = dirs[4 * d], vy = dirs[4 * d + 1];
   const double s3 = sqrt(3.0);
@@ -96,12 +98,13 @@ __global__ void tables2d_kernel(double* tables, const double* sigma_t, const dou
 }
 
 __global__ void tables1d_kernel(double* tables, const double* sigma_t, const double* dirs, int B,
-                                int n_mat, int n_dirs, double h) {
+                                int n_mat, int n_dirs, double h, const uint8_t* mask) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= B * n_mat * n_dirs) return;
   const int d = idx % n_dirs;
   const int m = (idx / n_dirs) % n_mat;
   const int b = idx / (n_dirs * n_mat);
+  if (mask && !mask[b]) return;
   const double st = sigma_t[b * n_mat + m];
   const double xi = dirs[4 * d];
   const double s3 = sqrt(3.0), sg = xi < 0 ? -1.0 : 1.0, a = fabs(xi) / h;
@@ -417,22 +420,22 @@ __global__ void add_kernel(const double* x, const double* y, double* out, const 
   if (active && !active[b]) return;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_dof; e += gridDim.x * blockDim.x) {
     const size_t o = (size_t)b * n_dof + e;
-    out[o] = x[o] + y[o];
+    out[o] = y ? x[o] + y[o] : x[o];
   }
 }
 
 // ---- host side ----------------------------------------------------------------------------
 
-int setup_tables(rte_batch_t bt, cudaStream_t st) {
+int setup_tables(rte_batch_t bt, cudaStream_t st, const uint8_t* mask) {
   const rte_disc_s* d = bt->disc;
   const int n = bt->B * d->n_mat * d->n_dirs;
   const int th = 128, bl = (n + th - 1) / th;
   if (d->dim == 2) {
     tables2d_kernel<<<bl, th, 0, st>>>(bt->tables.p, bt->sigma_t.p, d->dir_dev.p, bt->B, d->n_mat,
-                                       d->n_dirs, d->hx, d->hy); RTE_NOTE_LAUNCH();
+                                       d->n_dirs, d->hx, d->hy, mask); RTE_NOTE_LAUNCH();
   } else {
     tables1d_kernel<<<bl, th, 0, st>>>(bt->tables.p, bt->sigma_t.p, d->dir_dev.p, bt->B, d->n_mat,
-                                       d->n_dirs, d->hx); RTE_NOTE_LAUNCH();
+                                       d->n_dirs, d->hx, mask); RTE_NOTE_LAUNCH();
   }
   RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;

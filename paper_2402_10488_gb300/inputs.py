@@ -222,3 +222,24 @@ def mixed_batch_spec(n_instances: int = 256, seed: int = BATCH_SEED):
     mu = np.stack([rng.uniform(1.0, 100.0, n_instances), rng.uniform(0.1, 1.0, n_instances),
                    rng.uniform(0.01, 0.1, n_instances)], 1)
     return [(int(s), int(a), mu[k]) for k, (s, a) in enumerate(zip(sides, angles))]
+
+
+MESH_SIDES_SERVE = (64, 96, 128, 192, 256)
+ANGLES_SERVE = (32, 64, 128, 256)
+TOLS_SERVE = (1e-6, 1e-8)
+
+
+def serving_requests(n_requests: int, rate: float = 2000.0, seed: int = SERVE_SEED):
+    """Request stream of the serving workload: Poisson arrivals (exponential gaps, mean 1/rate
+    seconds), mesh side from {64,...,256}, angles from {32,...,256}, mu as in the lattice
+    workload, relative tolerance 1e-6 or 1e-8, all uniform.  Returns (t_arrival, side, angles,
+    mu, tol) per request."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, n_requests))
+    sides = rng.choice(MESH_SIDES_SERVE, n_requests)
+    angles = rng.choice(ANGLES_SERVE, n_requests)
+    tols = rng.choice(TOLS_SERVE, n_requests)
+    mu = np.stack([rng.uniform(1.0, 100.0, n_requests), rng.uniform(0.1, 1.0, n_requests),
+                   rng.uniform(0.01, 0.1, n_requests)], 1)
+    return [(float(t[k]), int(sides[k]), int(angles[k]), mu[k], float(tols[k]))
+            for k in range(n_requests)]

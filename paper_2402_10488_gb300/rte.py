@@ -48,6 +48,18 @@ SIGNATURES = {
     "rte_rom_initial_guess": (_I, [_P, _P, _P, _P, _P]),
     "rte_romsa_correction": (_I, [_P, _P, _P, _P, _P, _P]),
     "rte_solve": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+    "rte_batch_set_slots": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
+    "rte_batch_info": (_I, [_P, _P]),
+    "rte_rom_save": (_I, [_P, ctypes.c_char_p]),
+    "rte_rom_load": (_I, [_P, ctypes.c_char_p, _P]),
+    "rte_solve_many": (_I, [_I, _P, _P, _P, _P, _P, _P]),
+    "rte_server_create": (_I, [_I, _P]),
+    "rte_server_add_bucket": (_I, [_P, _P, _P, _P, _P, _P]),
+    "rte_server_start": (_I, [_P]),
+    "rte_server_submit": (_I, [_P, _I, _P, _P, _P, _P, _D, _P]),
+    "rte_server_wait": (_I, [_P, ctypes.c_uint64, _D, _P, _P]),
+    "rte_server_stats": (_I, [_P, _P]),
+    "rte_server_destroy": (_I, [_P]),
 }
 
 
@@ -109,6 +121,28 @@ class _SolveOpts(ctypes.Structure):
 class SolveReport(ctypes.Structure):
     _fields_ = [("n_sweep", _I), ("converged", _I), ("n_romsa", _I), ("n_dsa", _I),
                 ("dsa_iters", _I), ("last_change", _D), ("rho_inf", _D), ("n_sweep32", _I)]
+
+
+class ServeReport(ctypes.Structure):
+    _fields_ = [("solve", SolveReport), ("status", _I), ("bucket", _I), ("slot", _I), ("pad", _I),
+                ("t_submit", _D), ("t_admit", _D), ("t_done", _D)]
+
+
+def _report(r):
+    return dict(n_sweep=r.n_sweep, converged=bool(r.converged), n_romsa=r.n_romsa, n_dsa=r.n_dsa,
+                dsa_iters=r.dsa_iters, last_change=r.last_change, rho_inf=r.rho_inf,
+                n_sweep32=r.n_sweep32)
+
+
+def solve_opts(eps, sa=SA_DSA, rel=False, max_iter=1000, theta=0, eps_romsad=0.0, dsa_rtol=1e-10,
+               dsa_max_it=500, schedule=None, fp32_switch=0.0):
+    """rte_solve_opts; `schedule` (uint8 per iteration) is kept alive on the returned struct."""
+    sched = None if schedule is None else _host(schedule, np.uint8)
+    o = _SolveOpts(float(eps), 1 if rel else 0, int(max_iter), int(sa), int(theta),
+                   float(eps_romsad), float(dsa_rtol), int(dsa_max_it),
+                   None if sched is None else sched.ctypes.data_as(_P), float(fp32_switch))
+    o._sched = sched
+    return o
 
 
 def _ptr(t):
@@ -193,6 +227,22 @@ class Batch:
         check(lib().rte_batch_set_params(self.h, st.ctypes.data_as(_P), ss.ctypes.data_as(_P),
                                          src.ctypes.data_as(_P), inf.ctypes.data_as(_P)))
 
+    def set_slots(self, slots, sigma_t, sigma_s, source, inflow, stream=None):
+        """Parameters of instances `slots` only (rte_batch_set_slots)."""
+        sl = _host(slots, np.int32).reshape(-1)
+        n = len(sl)
+        st, ss = _host(sigma_t).reshape(n, -1), _host(sigma_s).reshape(n, -1)
+        src, inf = _host(source).reshape(n, -1), _host(inflow).reshape(n, -1)
+        check(lib().rte_batch_set_slots(self.h, n, sl.ctypes.data_as(_P), st.ctypes.data_as(_P),
+                                        ss.ctypes.data_as(_P), src.ctypes.data_as(_P),
+                                        inf.ctypes.data_as(_P), _stream(stream)))
+
+    def info(self):
+        out = np.zeros(6, np.int64)
+        check(lib().rte_batch_info(self.h, out.ctypes.data_as(_P)))
+        return dict(B=int(out[0]), bytes=int(out[1]), dirs_per_warp=int(out[2]),
+                    min_dirs_per_warp=int(out[3]), dynamic=bool(out[4]), params_set=bool(out[5]))
+
     def tune(self, dirs_per_warp=0):
         """Directions swept per warp in 2D (1, 2, 4, 8; 0 = automatic)."""
         check(lib().rte_batch_tune(self.h, int(dirs_per_warp)))
@@ -240,20 +290,15 @@ class Batch:
     def solve(self, rho, eps, sa=SA_DSA, rel=False, max_iter=1000, theta=0, eps_romsad=0.0,
               dsa_rtol=1e-10, dsa_max_it=500, rom_c=None, schedule=None, history=False,
               fp32_switch=0.0, stream=None):
-        sched = None if schedule is None else _host(schedule, np.uint8)
-        opts = _SolveOpts(float(eps), 1 if rel else 0, int(max_iter), int(sa), int(theta),
-                          float(eps_romsad), float(dsa_rtol), int(dsa_max_it),
-                          None if sched is None else sched.ctypes.data_as(_P), float(fp32_switch))
+        opts = solve_opts(eps, sa, rel, max_iter, theta, eps_romsad, dsa_rtol, dsa_max_it, schedule,
+                          fp32_switch)
         reps = (SolveReport * self.B)()
         hist = np.zeros((self.B, max_iter)) if history else None
         st = check(lib().rte_solve(self.h, ctypes.byref(opts), None if rom_c is None else rom_c.h,
                                    _ptr(rho), reps,
                                    None if hist is None else hist.ctypes.data_as(_P),
                                    _stream(stream)), allow=(RTE_ENOCONV,))
-        rep = [dict(n_sweep=r.n_sweep, converged=bool(r.converged), n_romsa=r.n_romsa,
-                    n_dsa=r.n_dsa, dsa_iters=r.dsa_iters, last_change=r.last_change,
-                    rho_inf=r.rho_inf, n_sweep32=r.n_sweep32) for r in reps]
-        return rep, hist, st
+        return [_report(r) for r in reps], hist, st
 
     def close(self):
         if self.h:
@@ -267,11 +312,28 @@ class Batch:
             pass
 
 
-class Rom:
-    """A POD reduced model built on the GPU (rte_rom_build)."""
+def solve_many(batches, rhos, opts, roms=None, streams=None):
+    """rte_solve_many: batches[k] solved from rhos[k] (device tensors, overwritten) with opts[k]
+    (rte_solve_opts from solve_opts()), optional roms[k] and streams[k].  Returns per-batch report
+    lists and the status."""
+    n = len(batches)
+    bh = (_P * n)(*[b.h for b in batches])
+    oa = (_SolveOpts * n)(*opts)
+    rh = (_P * n)(*[_ptr(r) for r in rhos])
+    reps = [(SolveReport * b.B)() for b in batches]
+    rp = (_P * n)(*[ctypes.cast(r, _P) for r in reps])
+    ro = None if roms is None else (_P * n)(*[None if r is None else r.h for r in roms])
+    sa = None if streams is None else (_P * n)(*[_stream(s) for s in streams])
+    st = check(lib().rte_solve_many(n, bh, oa, ro, rh, rp, sa), allow=(RTE_ENOCONV,))
+    return [[_report(r) for r in rr] for rr in reps], st
 
-    def __init__(self, h):
+
+class Rom:
+    """A POD reduced model built on the GPU (rte_rom_build) or loaded from a file."""
+
+    def __init__(self, h, disc=None):
         self.h = h
+        self.disc = disc  # keeps the discretisation alive as long as the model
         info = np.zeros(6)
         check(lib().rte_rom_info(h, info.ctypes.data_as(_P), None))
         self.r, self.n_snap = int(info[0]), int(info[1])
@@ -288,7 +350,16 @@ class Rom:
         hp, hc = _P(), _P()
         check(lib().rte_rom_build(train.h, ctypes.byref(o), ctypes.byref(hp), ctypes.byref(hc),
                                   _stream(stream)))
-        return Rom(hp), Rom(hc)
+        return Rom(hp, train.disc), Rom(hc, train.disc)
+
+    def save(self, path):
+        check(lib().rte_rom_save(self.h, os.fsencode(path)))
+
+    @staticmethod
+    def load(disc: Disc, path):
+        h = _P()
+        check(lib().rte_rom_load(disc.h, os.fsencode(path), ctypes.byref(h)))
+        return Rom(h, disc)
 
     def initial_guess(self, batch: Batch, rho0, active=None, stream=None):
         check(lib().rte_rom_initial_guess(self.h, batch.h, _ptr(rho0), _ptr(active),
@@ -301,6 +372,76 @@ class Rom:
     def close(self):
         if self.h:
             lib().rte_rom_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop (rte_server_*): buckets of slots, one worker thread."""
+
+    def __init__(self, device=0):
+        h = _P()
+        check(lib().rte_server_create(int(device), ctypes.byref(h)))
+        self.h = h
+        self._keep = []
+        self.buckets = []
+
+    def add_bucket(self, batch: Batch, rom_p=None, rom_c=None, **opts):
+        """Adds a bucket whose slots are `batch`'s instances; opts as solve_opts() (eps unused)."""
+        o = solve_opts(opts.pop("eps", 0.0), **opts)
+        k = _I()
+        check(lib().rte_server_add_bucket(self.h, batch.h, None if rom_p is None else rom_p.h,
+                                          None if rom_c is None else rom_c.h, ctypes.byref(o),
+                                          ctypes.byref(k)))
+        self._keep += [batch, rom_p, rom_c, o]
+        self.buckets.append(batch)
+        return int(k.value)
+
+    def start(self):
+        check(lib().rte_server_start(self.h))
+
+    def submit(self, bucket, sigma_t, sigma_s, source, inflow, eps):
+        st, ss, src, inf = _host(sigma_t), _host(sigma_s), _host(source), _host(inflow)
+        t = ctypes.c_uint64()
+        check(lib().rte_server_submit(self.h, int(bucket), st.ctypes.data_as(_P),
+                                      ss.ctypes.data_as(_P), src.ctypes.data_as(_P),
+                                      inf.ctypes.data_as(_P), float(eps), ctypes.byref(t)))
+        return int(t.value)
+
+    def wait(self, ticket, timeout=60.0, want_rho=True):
+        """(rho, report) once the request finished, or None on timeout."""
+        rep = ServeReport()
+        rho = None
+        if want_rho:
+            # the bucket is only known from the report; allocate for the largest bucket
+            rho = np.zeros(max(b.disc.n_dof for b in self.buckets))
+        st = lib().rte_server_wait(self.h, ctypes.c_uint64(ticket), float(timeout),
+                                   None if rho is None else rho.ctypes.data_as(_P), ctypes.byref(rep))
+        if st == RTE_ETIMEOUT:
+            return None
+        check(st, allow=(RTE_ENOCONV,))
+        r = _report(rep.solve)
+        r.update(status=rep.status, bucket=rep.bucket, slot=rep.slot, t_submit=rep.t_submit,
+                 t_admit=rep.t_admit, t_done=rep.t_done)
+        if rho is not None:
+            rho = rho[: self.buckets[rep.bucket].disc.n_dof]
+        return rho, r
+
+    def stats(self):
+        out = np.zeros(8)
+        check(lib().rte_server_stats(self.h, out.ctypes.data_as(_P)))
+        keys = ("launches", "admitted", "completed", "queued", "max_queue", "max_running",
+                "busy_s", "uptime_s")
+        return dict(zip(keys, (float(x) for x in out)))
+
+    def close(self):
+        if self.h:
+            lib().rte_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

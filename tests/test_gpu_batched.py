@@ -1,0 +1,269 @@
+"""Mixed-size batched solves and continuous-batching serving on the GPU, through the C ABI.
+
+What is checked:
+* per-slot parameter upload (rte_batch_set_slots) reproduces rte_batch_set_params bit for bit;
+* rte_solve_many over batches of different discretisations returns, for every batch, exactly
+  what rte_solve returns for that batch alone (the same kernels with the same decomposition);
+* the server: every request's result equals the same instance solved alone -- bit for bit when
+  the sweep decomposition is fixed, and within the stopping tolerance when it follows the number
+  of running slots -- and the converged results agree with the oracle's direct solve of
+  (I - L) rho = b (Eq. (rho_matrix_vec_def)) within the tolerance the stop test implies;
+* requests submitted while others run are admitted before those finish (continuous batching);
+* a saved ROM loads back to the same online operators.
+
+Tolerance for "alone vs in the mix" with a per-launch decomposition: both runs stop when the
+relative change drops below eps; with the DSA contraction c <= 0.5 measured on these problems,
+each result lies within eps * c / (1 - c) <= eps of the fixed point, so they agree to 2 eps
+(relative to ||rho||_inf) plus rounding."""
+import numpy as np
+import pytest
+
+from oracle.transport import Transport
+from paper_2402_10488_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _rte():
+    from paper_2402_10488_gb300 import build, rte
+    build.build()
+    return rte
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def test_set_slots_matches_set_params():
+    rte = _rte()
+    p = inputs.random_2d(20, 8, 2, 3, seed=11, B=4, inflow=(0.5, 0.0, 1.0, 0.25), ny=13)
+    disc = rte.Disc(p)
+    a = rte.Batch(disc, 4)
+    a.set_params(p)
+    b = rte.Batch(disc, 4)
+    for slots in ([2, 0], [3, 1]):
+        assert not b.info()["params_set"]
+        b.set_slots(slots, p.sigma_t[slots], p.sigma_s[slots], p.source[slots], p.inflow[slots])
+    torch.cuda.synchronize()
+    assert b.info()["params_set"]
+    rho = torch.tensor(np.random.default_rng(1).normal(size=(4, p.n_dof)), device="cuda")
+    oa, ob = torch.empty_like(rho), torch.empty_like(rho)
+    a.sweep(rho, oa)
+    b.sweep(rho, ob)
+    torch.cuda.synchronize()
+    assert torch.equal(oa, ob)
+    with pytest.raises(rte.RTEError):
+        b.set_slots([1, 1], p.sigma_t[:2], p.sigma_s[:2], p.source[:2], p.inflow[:2])
+    with pytest.raises(rte.RTEError):
+        b.set_slots([4], p.sigma_t[:1], p.sigma_s[:1], p.source[:1], p.inflow[:1])
+
+
+def test_batch_memory_info_is_per_slot_linear():
+    rte = _rte()
+    p1 = inputs.lattice_test(16, 16, 1)
+    p2 = inputs.lattice_test(16, 16, 2)
+    disc = rte.Disc(p1)
+    b1 = rte.Batch.from_problem(p1, disc)
+    b2 = rte.Batch.from_problem(p2, disc)
+    m1, m2 = b1.info()["bytes"], b2.info()["bytes"]
+    assert 0 < m2 - m1 <= m1
+    # large discretisations sweep with wider direction groups to bound the partial sums
+    big = inputs.lattice_test(256, 256, 1)
+    info = rte.Batch(rte.Disc(big), 1).info()
+    assert info["min_dirs_per_warp"] >= 4
+    assert info["bytes"] < 256 << 20
+
+
+def _buckets():
+    """Three discretisations of different sizes (lattice maps, vacuum inflow)."""
+    return [inputs.lattice_test(16, 16, 3), inputs.lattice_test(24, 32, 2),
+            inputs.lattice_test(12, 8, 4, n_vz=2)]
+
+
+def test_solve_many_matches_each_batch_alone():
+    rte = _rte()
+    probs = _buckets()
+    opts = [rte.solve_opts(1e-10, rte.SA_DSA, rel=True, max_iter=200, dsa_rtol=0.0, dsa_max_it=1)
+            for _ in probs]
+    opts[1] = rte.solve_opts(1e-9, rte.SA_DSA, rel=True, max_iter=200, dsa_rtol=1e-6, dsa_max_it=50)
+    batches = [rte.Batch.from_problem(p) for p in probs]
+    rhos = [torch.zeros((p.batch, p.n_dof), dtype=torch.float64, device="cuda") for p in probs]
+    streams = [torch.cuda.Stream() for _ in probs]
+    torch.cuda.synchronize()  # the initial iterates are ready before other streams read them
+    reps, st = rte.solve_many(batches, rhos, opts, streams=streams)
+    assert st == rte.RTE_OK
+    for k, p in enumerate(probs):
+        alone = rte.Batch.from_problem(p)
+        r = torch.zeros_like(rhos[k])
+        o = opts[k]
+        rep1, _, _ = alone.solve(r, o.eps, rte.SA_DSA, rel=True, max_iter=200, dsa_rtol=o.dsa_rtol,
+                                 dsa_max_it=o.dsa_max_it)
+        torch.cuda.synchronize()
+        assert torch.equal(r, rhos[k])
+        assert [x["n_sweep"] for x in rep1] == [x["n_sweep"] for x in reps[k]]
+        assert all(x["converged"] for x in reps[k])
+
+
+@pytest.fixture(scope="module")
+def served():
+    """A ROM for the 16x16 CL(4,4) lattice bucket (ROMSAD + ROMIG) and a DSA-only bucket."""
+    rte = _rte()
+    train = inputs.lattice_train(16, 16, n_train=8)
+    tb = rte.Batch.from_problem(train)
+    rp, rc = rte.Rom.build(tb, eps_train=1e-12, window=3, rank_p=6, rank_c=8, max_iter=300,
+                           dsa_rtol=1e-10)
+    return rte, tb.disc, rp, rc
+
+
+def _romsad_opts(rc):
+    return dict(sa=3, rel=True, max_iter=300, theta=5, eps_romsad=0.1 * rc.eps_pod,
+                dsa_rtol=0.0, dsa_max_it=1)
+
+
+def _requests(n, seed):
+    """Interleaved requests for bucket 0 (16x16 lattice) and bucket 1 (24x32 lattice)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        k = int(rng.integers(0, 2))
+        p = inputs.lattice_test(16, 16, 1, first=100 + i) if k == 0 else \
+            inputs.lattice_test(24, 32, 1, first=200 + i)
+        eps = float(rng.choice([1e-6, 1e-8, 1e-10]))
+        out.append((k, p, eps))
+    return out
+
+
+def _alone(rte, disc, p, eps, opts, rom_p=None, rom_c=None, dpw=0):
+    b = rte.Batch(disc, 1)
+    b.tune(dpw)
+    b.set_params(p)
+    r = torch.zeros((1, p.n_dof), dtype=torch.float64, device="cuda")
+    if rom_p is not None:
+        rom_p.initial_guess(b, r)
+    o = dict(opts)
+    rep, _, _ = b.solve(r, eps, rom_c=rom_c, **o)
+    torch.cuda.synchronize()
+    return r.cpu().numpy()[0], rep[0]
+
+
+@pytest.mark.parametrize("dpw", [2, 0])
+def test_server_results_equal_alone_and_oracle(served, dpw):
+    rte, disc0, rp, rc = served
+    disc1 = rte.Disc(inputs.lattice_test(24, 32, 1))
+    reqs = _requests(14, seed=5 + dpw)
+    b0 = rte.Batch(disc0, 3)
+    b1 = rte.Batch(disc1, 2)
+    for b, p in ((b0, inputs.lattice_test(16, 16, 3)), (b1, inputs.lattice_test(24, 32, 2))):
+        b.tune(dpw)
+        b.set_params(p)  # builds the DSA hierarchy; slots are overwritten at admission
+    o0 = _romsad_opts(rc)
+    o1 = dict(sa=1, rel=True, max_iter=300, dsa_rtol=0.0, dsa_max_it=1)
+    srv = rte.Server()
+    k0 = srv.add_bucket(b0, rp, rc, **o0)
+    k1 = srv.add_bucket(b1, None, None, **o1)
+    assert (k0, k1) == (0, 1)
+    srv.start()
+    tickets = [srv.submit(k, p.sigma_t[0], p.sigma_s[0], p.source[0], p.inflow[0], eps)
+               for k, p, eps in reqs]
+    results = [srv.wait(t, timeout=120.0) for t in tickets]
+    stats = srv.stats()
+    srv.close()
+    assert stats["completed"] == len(reqs) and stats["admitted"] == len(reqs)
+    assert stats["max_running"] >= 2
+    for (k, p, eps), res in zip(reqs, results):
+        assert res is not None
+        rho, rep = res
+        assert rep["status"] == rte.RTE_OK and rep["converged"] and rep["bucket"] == k
+        assert rep["t_submit"] <= rep["t_admit"] <= rep["t_done"]
+        if k == 0:
+            ref, rref = _alone(rte, disc0, p, eps, o0, rp, rc, dpw)
+        else:
+            ref, rref = _alone(rte, disc1, p, eps, o1, None, None, dpw)
+        if dpw:
+            assert np.array_equal(rho, ref), _rel(rho, ref)
+            assert rep["n_sweep"] == rref["n_sweep"]
+        else:
+            assert _rel(rho, ref) <= 2 * eps + 1e-13
+    # converged results against the oracle's direct solve, on the tightest requests
+    checked = 0
+    for (k, p, eps), res in zip(reqs, results):
+        if eps == 1e-10 and checked < 2:
+            exact = Transport(p, 0).solve_rho_direct()
+            assert _rel(res[0], exact) < 1e-8
+            checked += 1
+
+
+def test_server_admits_while_others_run(served):
+    rte, disc0, rp, rc = served
+    b0 = rte.Batch(disc0, 4)
+    b0.set_params(inputs.lattice_test(16, 16, 4))
+    srv = rte.Server()
+    srv.add_bucket(b0, rp, rc, **_romsad_opts(rc))
+    srv.start()
+    p = inputs.lattice_test(16, 16, 6, first=300)
+    # request 1 has tolerance 0: it runs to the iteration cap (300 iterations) and so is still
+    # on the device while the second wave arrives
+    quick = srv.submit(0, p.sigma_t[0], p.sigma_s[0], p.source[0], p.inflow[0], 1e-6)
+    slow = srv.submit(0, p.sigma_t[1], p.sigma_s[1], p.source[1], p.inflow[1], 0.0)
+    r0 = srv.wait(quick, timeout=60.0)
+    late = [srv.submit(0, p.sigma_t[i], p.sigma_s[i], p.source[i], p.inflow[i], 1e-6)
+            for i in range(2, 6)]
+    rl = [srv.wait(t, timeout=60.0) for t in late]
+    rs = srv.wait(slow, timeout=60.0)
+    srv.close()
+    assert r0 is not None and rs is not None and all(x is not None for x in rl)
+    assert r0[1]["converged"] and all(x[1]["converged"] for x in rl)
+    assert rs[1]["status"] == rte.RTE_ENOCONV and rs[1]["n_sweep"] == 300
+    # continuous batching: the late requests ran and finished while the slow one was running
+    assert max(x[1]["t_done"] for x in rl) < rs[1]["t_done"]
+    assert {x[1]["slot"] for x in rl} <= {0, 2, 3} | {r0[1]["slot"]}
+
+
+def test_server_rejects_bad_requests(served):
+    rte, disc0, rp, rc = served
+    b0 = rte.Batch(disc0, 2)
+    b0.set_params(inputs.lattice_test(16, 16, 2))
+    srv = rte.Server()
+    srv.add_bucket(b0, rp, rc, **_romsad_opts(rc))
+    p = inputs.lattice_test(16, 16, 1)
+    with pytest.raises(rte.RTEError):  # not started
+        srv.submit(0, p.sigma_t[0], p.sigma_s[0], p.source[0], p.inflow[0], 1e-6)
+    srv.start()
+    with pytest.raises(rte.RTEError):  # sigma_s > sigma_t
+        srv.submit(0, p.sigma_t[0], p.sigma_t[0] * 2, p.source[0], p.inflow[0], 1e-6)
+    with pytest.raises(rte.RTEError):  # ROMIG bucket takes vacuum inflow only
+        srv.submit(0, p.sigma_t[0], p.sigma_s[0], p.source[0], np.ones(4), 1e-6)
+    with pytest.raises(rte.RTEError):
+        srv.submit(5, p.sigma_t[0], p.sigma_s[0], p.source[0], p.inflow[0], 1e-6)
+    t = srv.submit(0, p.sigma_t[0], p.sigma_s[0], p.source[0], p.inflow[0], 1e-6)
+    assert srv.wait(t, timeout=60.0) is not None
+    srv.close()
+
+
+def test_rom_save_load_roundtrip(served, tmp_path):
+    rte, disc0, rp, rc = served
+    path = str(tmp_path / "rom_c.bin")
+    rc.save(path)
+    lc = rte.Rom.load(disc0, path)
+    assert lc.r == rc.r and lc.n_snap == rc.n_snap and np.array_equal(lc.sv, rc.sv)
+    test = inputs.lattice_test(16, 16, 2)
+    b = rte.Batch(disc0, 2)
+    b.set_params(test)
+    R = torch.tensor(np.random.default_rng(2).uniform(0, 1, (2, test.n_dof)), device="cuda")
+    d1, d2 = torch.zeros_like(R), torch.zeros_like(R)
+    rc.romsa_correction(b, R, d1)
+    lc.romsa_correction(b, R, d2)
+    torch.cuda.synchronize()
+    assert torch.equal(d1, d2)
+    pp = str(tmp_path / "rom_p.bin")
+    rp.save(pp)
+    lp = rte.Rom.load(disc0, pp)
+    g1 = torch.zeros_like(R)
+    g2 = torch.zeros_like(R)
+    rp.initial_guess(b, g1)
+    lp.initial_guess(b, g2)
+    assert torch.equal(g1, g2)
+    other = rte.Disc(inputs.lattice_test(24, 32, 1))
+    with pytest.raises(rte.RTEError):
+        rte.Rom.load(other, path)
