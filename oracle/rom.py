@@ -16,6 +16,9 @@
   delta f^{mu,(l)} = f^mu - f^{mu,(l)} for l <= w_mu = min(n_conv, w).
 * ROMSA (Eq. (rom_correction)): (dU^T A_mu dU) dc = (dU^iso)^T Sigma_s (rho* - rho_prev),
   delta rho = dU^rho dc.
+* ROMIG followed by ROMSAD (remark after Alg. 2): the correction snapshots must come from
+  training runs that start from the ROMIG guess, since the corrections such a run needs differ
+  from those of a run started at zero; correction_start="romig" collects them that way.
 """
 from __future__ import annotations
 
@@ -102,7 +105,8 @@ class OfflineROMs:
     """Offline stage: training SI-DSA solves, snapshot matrices F and delta F, two POD bases."""
 
     def __init__(self, train_problem, eps_train=1e-12, window=3, rank_p=None, rank_c=None,
-                 eps_pod=None, n_iter=2000, tol_mode="abs"):
+                 eps_pod=None, n_iter=2000, tol_mode="abs", correction_start="zero"):
+        assert correction_start in ("zero", "romig")
         F_cols, dF_cols, n_conv = [], [], []
         tr0 = None
         for b in range(train_problem.batch):
@@ -122,10 +126,23 @@ class OfflineROMs:
                 tr._lu = [None] * tr.n_angles  # free the factors of finished instances
         self.n_conv = n_conv
         self.F = np.stack(F_cols, 1)
-        self.dF = np.stack(dF_cols, 1)
         self.pod_p = POD(self.F, eps_pod, rank_p)
-        self.pod_c = POD(self.dF, eps_pod, rank_c)
         self.rom_p = ReducedModel(self.pod_p.U, tr0)
+        if correction_start == "romig":
+            # second pass: the same training solves started from the ROMIG guess
+            dF_cols, n_conv = [], []
+            for b in range(train_problem.batch):
+                tr = Transport(train_problem, b)
+                rho0 = self.rom_p.initial_guess(tr)
+                res = sisa(tr, rho0, eps_train, n_iter, "dsa", dsa=ConsistentDSA(tr),
+                           window=window, keep_f=True, tol_mode=tol_mode)
+                f = res["f"].reshape(-1)
+                n_conv.append(res["n_sweep"])
+                for l in range(min(res["n_sweep"], window)):
+                    dF_cols.append(f - res["f_window"][l].reshape(-1))
+            self.n_conv_romig = n_conv
+        self.dF = np.stack(dF_cols, 1)
+        self.pod_c = POD(self.dF, eps_pod, rank_c)
         self.rom_c = ReducedModel(self.pod_c.U, tr0)
         self.eps_train = eps_train
         self.eps_pod = self.pod_c.eps_equiv if eps_pod is None else eps_pod

@@ -92,3 +92,24 @@ def test_correction_rank_not_below_parametric_rank():
     train = inputs.lattice_train(6, 8, n_train=6, n_vz=2)
     off = OfflineROMs(train, eps_train=1e-13, window=3, eps_pod=1e-6)
     assert off.pod_p.r <= off.pod_c.r
+
+
+def test_romig_started_correction_snapshots_make_romig_romsa_exact():
+    """Remark after Alg. 2: for ROMIG followed by ROMSA the correction basis must come from
+    ROMIG-started training runs.  With window 1 and every snapshot kept, a training instance's
+    ROMIG-started trajectory has its own delta f^(1) in the basis, so ROMIG + ROMSA is exact after
+    the first correction and stops at the second sweep; the zero-started basis lacks that
+    correction and needs more sweeps."""
+    train = inputs.lattice_train(6, 8, n_train=3, n_vz=2)
+    kw = dict(eps_train=1e-14, window=1, rank_p=1, rank_c=3)
+    romig = OfflineROMs(train, correction_start="romig", **kw)
+    zero = OfflineROMs(train, correction_start="zero", **kw)
+    assert romig.dF.shape[1] == 3 and zero.dF.shape[1] == 3
+    tr = Transport(train, 1)
+    rho_exact = tr.solve_rho_direct()
+    rho0 = romig.rom_p.initial_guess(tr)
+    res = sisa(tr, rho0, 1e-11, 20, "romsa", rom_c=romig.rom_c)
+    assert res["converged"] and res["n_sweep"] == 2
+    np.testing.assert_allclose(res["rho"], rho_exact, atol=1e-10 * np.abs(rho_exact).max())
+    res0 = sisa(tr, rho0, 1e-11, 20, "romsa", rom_c=zero.rom_c)
+    assert res0["n_sweep"] > 2
