@@ -59,9 +59,11 @@ def parse():
     ap.add_argument("--dsa-vcycles", type=int, default=1)
     ap.add_argument("--fp32-switch", type=float, default=1e-5,
                     help="precision variant: FP32 sweeps until the relative change is below this")
-    ap.add_argument("--dpw", type=int, default=0, help="sweep directions per warp (0 = auto)")
+    ap.add_argument("--dpw", type=int, default=0,
+                    help="sweep directions per warp (0 = occupancy rule per launch, -1 = measured "
+                         "by the autotuner before timing)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--methods", default="romsad,si_dsa,romig,romsad_mixed")
+    ap.add_argument("--methods", default="romsad,si_dsa,romig,romig_romsad,romsad_mixed")
     ap.add_argument("--profile-window", action="store_true",
                     help="bracket the timed ROMSAD steps with cudaProfilerStart/Stop (for ncu)")
     ap.add_argument("--workload", default="lattice", choices=["lattice", "mixed", "serving"],
@@ -74,6 +76,8 @@ def parse():
     ap.add_argument("--mem-gb", type=float, default=96.0,
                     help="serving: device memory for slots, shared equally by the buckets")
     ap.add_argument("--max-slots", type=int, default=64, help="serving: slots per bucket at most")
+    ap.add_argument("--kappa", type=float, default=0.1,
+                    help="mixed/serving: stop at relative change kappa * error target")
     return ap.parse_args()
 
 
@@ -205,12 +209,19 @@ def run_ours(a, ws, rank, local):
     t0 = time.time()
     rom_p, rom_c = rte.Rom.build(tb, eps_train=1e-12, window=3, rank_p=a.rank, rank_c=a.rank,
                                  max_iter=500, dsa_rtol=1e-8)
+    methods = [m for m in a.methods.split(",") if m]
+    rom_ci = None
+    if "romig_romsad" in methods:  # correction ROM trained from ROMIG-started runs
+        _, rom_ci = rte.Rom.build(tb, eps_train=1e-12, window=3, rank_p=a.rank, rank_c=a.rank,
+                                  max_iter=500, dsa_rtol=1e-8, correction_start="romig")
     offline_s = time.time() - t0
     eps_train = 1e-12
     eps_romsad = 0.1 * max(eps_train, rom_c.eps_pod)
+    eps_romsad_i = 0.1 * max(eps_train, rom_ci.eps_pod) if rom_ci else None
     batch = rte.Batch(disc, B)
-    batch.tune(a.dpw)
+    batch.tune(max(a.dpw, 0))
     batch.set_params(test)
+    tuned = batch.autotune() if a.dpw < 0 else None
     n_dof = disc.n_dof
     # tightly converged references (untimed)
     ref = torch.zeros((B, n_dof), dtype=torch.float64, device="cuda")
@@ -230,6 +241,9 @@ def run_ours(a, ws, rank, local):
         elif method == "romsad_mixed":
             sa, kw = rte.SA_ROMSAD, dict(rom_c=rom_c, theta=5, eps_romsad=eps_romsad,
                                          fp32_switch=a.fp32_switch)
+        elif method == "romig_romsad":
+            rom_p.initial_guess(batch, rho)
+            sa, kw = rte.SA_ROMSAD, dict(rom_c=rom_ci, theta=5, eps_romsad=eps_romsad_i)
         else:
             sa, kw = rte.SA_DSA, {}
         rep, _, st = batch.solve(rho, a.eps, sa=sa, rel=True, max_iter=400, dsa_rtol=a.dsa_rtol,
@@ -237,8 +251,6 @@ def run_ours(a, ws, rank, local):
         if host_out is not None:
             host_out.copy_(rho, non_blocking=True)
         return rep
-
-    methods = [m for m in a.methods.split(",") if m]
 
     def measure(method, steps, warmup, host=False):
         rho = torch.zeros((B, n_dof), dtype=torch.float64, device="cuda")
@@ -328,7 +340,9 @@ def run_ours(a, ws, rank, local):
                    "eps_romsad": eps_romsad, "stop": f"relative change < {a.eps:g}",
                    "dsa": (f"{a.dsa_vcycles} FP32 multigrid V-cycles" if a.dsa_rtol == 0 else
                            f"FGMRES rtol {a.dsa_rtol}"), "error_target": 1e-6,
-                   "dirs_per_warp": a.dpw or "auto",
+                   "dirs_per_warp": (a.dpw if a.dpw > 0 else
+                                     f"measured per running count {tuned}" if tuned else
+                                     "occupancy rule per launch"),
                    "l2": "256 MB buffer written between timed steps",
                    "parallelism": "instances sharded across ranks, no collective"},
         "roofline": {"bound": "alu", "kernel": "sweep2d_kernel (FP64 DFMA)", "achieved": achieved,
@@ -345,7 +359,8 @@ def run_ours(a, ws, rank, local):
                        "note": "per batch of instances solved together"},
         "methods": summ,
         "offline_s": offline_s,
-        "rom": {"r_p": rom_p.r, "r_c": rom_c.r, "eps_pod_c": rom_c.eps_pod},
+        "rom": {"r_p": rom_p.r, "r_c": rom_c.r, "eps_pod_c": rom_c.eps_pod,
+                "eps_pod_c_romig_started": rom_ci.eps_pod if rom_ci else None},
     }
     return line, dict(n_sweep=summ["romsad"]["n_sweep_mean"], n_dsa=summ["romsad"]["n_dsa_mean"],
                       n_romsa=summ["romsad"]["n_romsa_mean"], n=a.n, angles=a.angles)
@@ -401,13 +416,15 @@ def run_mixed(a, ws, rank, local):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
+    eps = a.kappa * 1e-6
+
     def opts_for(method, k):
         kw = dict(rel=True, max_iter=400, dsa_rtol=a.dsa_rtol,
                   dsa_max_it=a.dsa_vcycles if a.dsa_rtol == 0 else 100)
         if method == "si_dsa":
-            return rte.solve_opts(a.eps, rte.SA_DSA, **kw), None
+            return rte.solve_opts(eps, rte.SA_DSA, **kw), None
         fp = a.fp32_switch if method == "romsad_mixed" else 0.0
-        return (rte.solve_opts(a.eps, rte.SA_ROMSAD, theta=5, eps_romsad=k["eps_romsad"],
+        return (rte.solve_opts(eps, rte.SA_ROMSAD, theta=5, eps_romsad=k["eps_romsad"],
                                fp32_switch=fp, **kw), k["rom_c"])
 
     def step(method):
@@ -469,7 +486,7 @@ def run_mixed(a, ws, rank, local):
                    "buckets": [f"{s_}x{s_}_CL({n_ // 4},4):{k['prob'].batch}"
                                for (s_, n_), k in zip(keys, B)],
                    "global_batch": a.instances * ws, "n_train": a.ntrain, "rank": a.rank,
-                   "stop": f"relative change < {a.eps:g}", "error_target": 1e-6,
+                   "stop": f"relative change < {eps:g}", "error_target": 1e-6,
                    "l2": "256 MB buffer written between timed steps",
                    "execution": "rte_solve_many: one stream per bucket, event-driven relaunch",
                    "parallelism": "instances sharded across ranks, no collective"},
@@ -548,7 +565,7 @@ def run_serving(a, ws, rank, local):
                 time.sleep(t_arr - now)
             p = inputs.lattice_from_params(side, ang // 4, 4, mu[None])
             tickets.append(srv.submit(ids[(side, ang)], p.sigma_t[0], p.sigma_s[0], p.source[0],
-                                      p.inflow[0], tol))
+                                      p.inflow[0], a.kappa * tol))
         out = [srv.wait(t, timeout=1800.0) for t in tickets]
         st1 = srv.stats()
         n_launch = rte.launch_count() - launches0
@@ -568,7 +585,7 @@ def run_serving(a, ws, rank, local):
         lat = np.array([r["t_done"] - r["t_submit"] for _, r in out]) * 1e3
         t_first = min(r["t_submit"] for _, r in out)
         t_last = max(r["t_done"] for _, r in out)
-        ok = [r["status"] == 0 and r["converged"] for _, r in out]
+        ok = [r["status"] == 0 and r["converged"] for _, r in out]  # stop test met (error: sample)
         results[m] = dict(solves_per_s=float(np.sum(ok)) / (t_last - t_first),
                           completed=len(out), converged=int(np.sum(ok)),
                           p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
@@ -599,6 +616,7 @@ def run_serving(a, ws, rank, local):
         "data": "synthetic (seeded Poisson request stream of lattice instances; no dataset)",
         "config": {"workload": f"serving_poisson{a.rate:g}_sides64-256_angles32-256_{head}",
                    "requests": a.requests, "rate_per_s": a.rate, "tolerances": [1e-6, 1e-8],
+                   "stop": f"relative change < {a.kappa:g} x the request's tolerance",
                    "buckets": {f"{k[0]}x{k[0]}_CL({k[1] // 4},4)": buckets[k]["slots"] for k in keys},
                    "slot_memory_gb": a.mem_gb, "n_train": a.ntrain, "rank": a.rank,
                    "parallelism": "one GPU, one worker thread, one stream per bucket"},

@@ -160,6 +160,15 @@ int rte_sweep(rte_batch_t batch, const double* rho_in, double* rho_out, double* 
  * 64 MB (large meshes with many directions).  Set before sweeping.  Errors: RTE_EINVAL. */
 int rte_batch_tune(rte_batch_t batch, int dirs_per_warp);
 
+/* Empirical autotuner of the same choice: for B, B/2, B/4, ..., 1 running instances it times one
+ * sweep with every allowed directions-per-warp value (CUDA events on `stream`, on the batch's
+ * current parameters) and keeps the fastest per count; later sweeps pick the entry for the
+ * smallest timed count >= their running instances.  Uses the batch's iteration scratch only.
+ *   n_entries  HOST int out (may be NULL); table HOST int[2*32] or NULL: (count, dirs_per_warp)
+ * Synchronous.  rte_batch_tune resets it.  1D batches: no-op.  Errors: RTE_ESTATE (no
+ * parameters), RTE_ECUDA. */
+int rte_batch_autotune(rte_batch_t batch, void* stream, int* n_entries, int* table);
+
 /* Allocation-free variant of rte_sweep (the paper has no counterpart: this is a library service).
  * For callers that cannot allocate device memory while they run (for example under a host
  * framework whose caching allocator has reserved the device's memory, or inside a latency-bound
@@ -229,6 +238,9 @@ typedef struct {
   double eps_pod;     /* truncation tolerance of Eq. (pod_truncation) when a rank is 0       */
   int max_iter;       /* iteration cap of the training solves                                */
   double dsa_rtol;    /* DSA solve tolerance used in the training solves                     */
+  int correction_start; /* 0: correction snapshots from training runs started at zero;
+                           1: from runs started at the ROMIG guess of the parametric ROM, for
+                           ROMIG followed by ROMSAD (remark after Alg. 2; vacuum inflow only)   */
 } rte_rom_opts;
 
 /* Offline stage (Sec. 3.1.1, 3.2.1) on the GPU: SI-DSA solves of every training instance of

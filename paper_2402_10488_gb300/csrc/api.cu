@@ -258,7 +258,17 @@ static std::vector<SweepGroup> groups_for(const rte_disc_s* disc, int dpw) {
 
 void pick_groups(rte_batch_t b, int n_active, int* dpw, int* n_groups, const SweepGroup** dev) {
   int use = b->dpw;
-  if (b->dpw_dynamic && b->disc->dim == 2) {
+  if (b->force_dpw && b->disc->dim == 2) {
+    use = b->force_dpw;
+  } else if (b->dpw_dynamic && b->disc->dim == 2 && !b->tuned.empty()) {
+    use = b->tuned.back().second;
+    for (const auto& e : b->tuned)
+      if (n_active <= e.first) {
+        use = e.second;
+        break;
+      }
+    use = std::max(use, b->min_dpw);
+  } else if (b->dpw_dynamic && b->disc->dim == 2) {
     use = 1;
     for (int k = 3; k >= 1; --k) {
       const int cand = 1 << k;
@@ -303,6 +313,7 @@ extern "C" int rte_batch_tune(rte_batch_t b, int dpw) {
   if (!b) return fail(RTE_EINVAL, "rte_batch_tune: null argument");
   if (b->disc->dim == 1) return RTE_OK;
   b->dpw_dynamic = dpw == 0;
+  b->tuned.clear();
   if (dpw == 0) dpw = std::max(auto_dpw(b->disc, b->B), b->min_dpw);
   if (dpw != 1 && dpw != 2 && dpw != 4 && dpw != 8) return fail(RTE_EINVAL, "dirs_per_warp must be 0, 1, 2, 4 or 8");
   DeviceGuard g(b->disc->device);

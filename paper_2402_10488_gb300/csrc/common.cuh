@@ -139,6 +139,10 @@ struct rte_batch_s {
   int n_sm = 148;
   int gcount[4] = {0, 0, 0, 0}, goff[4] = {0, 0, 0, 0};
   rte::DevBuf<rte::SweepGroup> groups_all_dev;
+  // measured choice of the empirical autotuner: (largest number of running instances, dpw),
+  // ascending; empty = the occupancy rule above
+  std::vector<std::pair<int, int>> tuned;
+  int force_dpw = 0;                  // autotuner trials: this dpw for every launch
   std::vector<double> sigma_t_h, sigma_s_h, source_h, inflow_h;
   rte::DevBuf<double> sigma_t, sigma_s;   // [B][n_mat]
   rte::DevBuf<double> G0;                 // [B][n_cells] zeroth source moment int G phi_0

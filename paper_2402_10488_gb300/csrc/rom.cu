@@ -577,10 +577,17 @@ extern "C" int rte_rom_build(rte_batch_t train, const rte_rom_opts* opts, rte_ro
                              rte_rom_t* rom_c, void* stream) {
   if (!train || !opts) return fail(RTE_EINVAL, "rte_rom_build: null argument");
   if (!train->params_set) return fail(RTE_ESTATE, "rte_rom_build: parameters not set");
-  if (opts->window < 1 || opts->max_iter < 1 || !(opts->eps_train > 0))
+  if (opts->window < 1 || opts->max_iter < 1 || !(opts->eps_train > 0) ||
+      (opts->correction_start != 0 && opts->correction_start != 1))
     return fail(RTE_EINVAL, "rte_rom_build: bad options");
   if ((opts->rank_p <= 0 || opts->rank_c <= 0) && !(opts->eps_pod > 0 && opts->eps_pod < 1))
     return fail(RTE_EINVAL, "rte_rom_build: need a rank or 0 < eps_pod < 1");
+  const bool romig_start = opts->correction_start == 1 && rom_c != nullptr;
+  if (romig_start)
+    for (double g : train->inflow_h)
+      if (g != 0.0) return fail(RTE_EINVAL, "ROMIG-started training needs vacuum inflow");
+  if (rom_p) *rom_p = nullptr;
+  if (rom_c) *rom_c = nullptr;
   rte_disc_s* d = train->disc;
   DeviceGuard g(d->device);
   cudaStream_t st = (cudaStream_t)stream;
@@ -596,25 +603,15 @@ extern "C" int rte_rom_build(rte_batch_t train, const rte_rom_opts* opts, rte_ro
   std::vector<rte_solve_report> rep(B);
   int s = run_si(train, &so, nullptr, rho.p, rep.data(), nullptr, st, psi_cur.p, psi_win.p, w);
   if (s != RTE_OK) return s == RTE_ENOCONV ? fail(RTE_ENOCONV, "training solve did not converge") : s;
-  // correction snapshots: (b, l) for l < min(n_conv, w)
-  std::vector<int> pairs;
-  for (int b = 0; b < B; ++b)
-    for (int l = 0; l < std::min(rep[b].n_sweep, w); ++l) pairs.push_back(b), pairs.push_back(l);
-  const int ndc = (int)pairs.size() / 2;
-  DevBuf<double> dF;
-  DevBuf<int> pairs_d;
-  RTE_TRY(dF.alloc((size_t)ndc * nrow));
-  RTE_TRY(pairs_d.alloc(pairs.size()));
-  RTE_CUDA_TRY(cudaMemcpyAsync(pairs_d.p, pairs.data(), sizeof(int) * pairs.size(), cudaMemcpyHostToDevice, st));
-  diff_kernel<<<dim3(1024, ndc), 256, 0, st>>>(psi_cur.p, psi_win.p, pairs_d.p, ndc, nrow, B, dF.p); RTE_NOTE_LAUNCH();
-  RTE_CUDA_TRY(cudaGetLastError());
   std::vector<double> mult(d->n_dirs);
   for (int k = 0; k < d->n_dirs; ++k) mult[k] = d->dirs[k].mult;
   DevBuf<double> multd;
   RTE_TRY(multd.alloc(d->n_dirs));
   RTE_CUDA_TRY(cudaMemcpyAsync(multd.p, mult.data(), 8 * mult.size(), cudaMemcpyHostToDevice, st));
-  if (rom_p) {
-    auto* rp = new rte_rom_s();
+  // parametric ROM from F = [f^mu] (needed first when the correction runs start from ROMIG)
+  rte_rom_s* rp = nullptr;
+  if (rom_p || romig_start) {
+    rp = new rte_rom_s();
     rp->disc = d;
     int e = pod(rp, psi_cur.p, B, nrow, opts->rank_p, opts->eps_pod, multd.p, st);
     if (e == RTE_OK) e = reduce_operators(rp, st);
@@ -622,23 +619,46 @@ extern "C" int rte_rom_build(rte_batch_t train, const rte_rom_opts* opts, rte_ro
       delete rp;
       return e;
     }
-    *rom_p = rp;
   }
+  if (romig_start) {
+    // remark after Alg. 2: the same training solves again, from the ROMIG guess
+    int e = rom_guess_launch(rp, train, rho.p, nullptr, st);
+    if (e == RTE_OK) e = run_si(train, &so, nullptr, rho.p, rep.data(), nullptr, st, psi_cur.p, psi_win.p, w);
+    if (e != RTE_OK) {
+      delete rp;
+      return e == RTE_ENOCONV ? fail(RTE_ENOCONV, "training solve did not converge") : e;
+    }
+  }
+  // correction snapshots: (b, l) for l < min(n_conv, w)
+  std::vector<int> pairs;
+  for (int b = 0; b < B; ++b)
+    for (int l = 0; l < std::min(rep[b].n_sweep, w); ++l) pairs.push_back(b), pairs.push_back(l);
+  const int ndc = (int)pairs.size() / 2;
   if (rom_c) {
+    DevBuf<double> dF;
+    DevBuf<int> pairs_d;
+    int e = dF.alloc((size_t)ndc * nrow);
+    if (e == RTE_OK) e = pairs_d.alloc(pairs.size());
+    if (e == RTE_OK && cudaMemcpyAsync(pairs_d.p, pairs.data(), sizeof(int) * pairs.size(),
+                                       cudaMemcpyHostToDevice, st) != cudaSuccess)
+      e = fail(RTE_ECUDA, "rte_rom_build: upload");
+    if (e == RTE_OK) {
+      diff_kernel<<<dim3(1024, ndc), 256, 0, st>>>(psi_cur.p, psi_win.p, pairs_d.p, ndc, nrow, B, dF.p); RTE_NOTE_LAUNCH();
+      if (cudaGetLastError() != cudaSuccess) e = fail(RTE_ECUDA, "rte_rom_build: diff kernel");
+    }
     auto* rc = new rte_rom_s();
     rc->disc = d;
-    int e = pod(rc, dF.p, ndc, nrow, opts->rank_c, opts->eps_pod, multd.p, st);
+    if (e == RTE_OK) e = pod(rc, dF.p, ndc, nrow, opts->rank_c, opts->eps_pod, multd.p, st);
     if (e == RTE_OK) e = reduce_operators(rc, st);
     if (e != RTE_OK) {
       delete rc;
-      if (rom_p && *rom_p) {
-        delete *rom_p;
-        *rom_p = nullptr;
-      }
+      delete rp;
       return e;
     }
     *rom_c = rc;
   }
+  if (rom_p) *rom_p = rp;
+  else delete rp;
   return RTE_OK;
 }
 

@@ -846,7 +846,8 @@ int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, cons
   int dpw = bt->dpw, n_groups = 0;
   const SweepGroup* gdev = nullptr;
   pick_groups(bt, n_active, &dpw, &n_groups, &gdev);
-  const size_t need32 = (size_t)bt->B * std::max<size_t>(bt->gcount[0], bt->groups.size()) * d->n_dof;
+  const int kmin = bt->min_dpw == 1 ? 0 : bt->min_dpw == 2 ? 1 : bt->min_dpw == 4 ? 2 : 3;
+  const size_t need32 = (size_t)bt->B * std::max<size_t>(bt->gcount[kmin], bt->groups.size()) * d->n_dof;
   if (bt->partial32.n < need32) RTE_TRY(bt->partial32.alloc(need32));
   if (bt->tables32_stale) {
     const size_t n = bt->tables.n;
@@ -888,3 +889,77 @@ int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, cons
 }
 
 }  // namespace rte
+
+namespace rte {
+// Empirical choice of the sweep decomposition: for running-instance counts B, B/2, B/4, ..., 1
+// (the first instances of the batch) every directions-per-warp value the partial-sum buffer
+// allows is timed with CUDA events on `st`, and the fastest is kept per count.
+static int autotune(rte_batch_t bt, cudaStream_t st, int* n_entries, int* table) {
+  const rte_disc_s* d = bt->disc;
+  const int B = bt->B;
+  const size_t nb = (size_t)B * d->n_dof;
+  std::vector<int> bands;
+  for (int n = B; n >= 1; n = n == 1 ? 0 : (n + 1) / 2) bands.push_back(n);
+  std::reverse(bands.begin(), bands.end());
+  DevBuf<uint8_t> mask;
+  RTE_TRY(mask.alloc(B));
+  std::vector<uint8_t> h(B);
+  cudaEvent_t e0, e1;
+  RTE_CUDA_TRY(cudaEventCreate(&e0));
+  RTE_CUDA_TRY(cudaEventCreate(&e1));
+  const bool timing = bt->timing;
+  bt->timing = false;
+  bt->tuned.clear();
+  int status = RTE_OK;
+  RTE_CUDA_TRY(cudaMemsetAsync(bt->work.p, 0, sizeof(double) * nb, st));
+  for (int n : bands) {
+    for (int b = 0; b < B; ++b) h[b] = b < n;
+    if (cudaMemcpyAsync(mask.p, h.data(), B, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      status = fail(RTE_ECUDA, "autotune: mask upload");
+      break;
+    }
+    float best_ms = 0.f;
+    int best = 0;
+    for (int dpw = bt->min_dpw; dpw <= kMaxDirsPerWarp && status == RTE_OK; dpw *= 2) {
+      bt->force_dpw = dpw;
+      float ms = 0.f;
+      status = sweep_launch(bt, bt->work.p, bt->work.p + nb, nullptr, 1, mask.p, st, true, n);
+      if (status == RTE_OK && cudaEventRecord(e0, st) != cudaSuccess) status = fail(RTE_ECUDA, "autotune: event");
+      for (int rep = 0; rep < 2 && status == RTE_OK; ++rep)
+        status = sweep_launch(bt, bt->work.p, bt->work.p + nb, nullptr, 1, mask.p, st, true, n);
+      if (status == RTE_OK && (cudaEventRecord(e1, st) != cudaSuccess ||
+                               cudaEventSynchronize(e1) != cudaSuccess ||
+                               cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        status = fail(RTE_ECUDA, "autotune: timing");
+      if (status == RTE_OK && (best == 0 || ms < best_ms)) best_ms = ms, best = dpw;
+    }
+    if (status != RTE_OK) break;
+    bt->tuned.emplace_back(n, best);
+  }
+  bt->force_dpw = 0;
+  bt->timing = timing;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (status != RTE_OK) {
+    bt->tuned.clear();
+    return status;
+  }
+  bt->dpw_dynamic = true;
+  if (n_entries) *n_entries = (int)bt->tuned.size();
+  if (table)
+    for (size_t k = 0; k < bt->tuned.size(); ++k) {
+      table[2 * k] = bt->tuned[k].first;
+      table[2 * k + 1] = bt->tuned[k].second;
+    }
+  return RTE_OK;
+}
+}  // namespace rte
+
+extern "C" int rte_batch_autotune(rte_batch_t b, void* stream, int* n_entries, int* table) {
+  if (!b) return fail(RTE_EINVAL, "rte_batch_autotune: null argument");
+  if (!b->params_set) return fail(RTE_ESTATE, "rte_batch_autotune: parameters not set");
+  if (n_entries) *n_entries = 0;
+  if (b->disc->dim != 2) return RTE_OK;
+  DeviceGuard g(b->disc->device);
+  return autotune(b, (cudaStream_t)stream, n_entries, table);
+}

@@ -29,6 +29,7 @@ SIGNATURES = {
     "rte_counters": (_I, [_P]),
     "rte_batch_timing": (_I, [_P, _I, _P]),
     "rte_batch_tune": (_I, [_P, _I]),
+    "rte_batch_autotune": (_I, [_P, _P, _P, _P]),
     "rte_disc_create": (_I, [_P, _I, _P]),
     "rte_disc_destroy": (_I, [_P]),
     "rte_disc_info": (_I, [_P, _P]),
@@ -109,7 +110,7 @@ class _DiscDesc(ctypes.Structure):
 
 class _RomOpts(ctypes.Structure):
     _fields_ = [("eps_train", _D), ("window", _I), ("rank_p", _I), ("rank_c", _I),
-                ("eps_pod", _D), ("max_iter", _I), ("dsa_rtol", _D)]
+                ("eps_pod", _D), ("max_iter", _I), ("dsa_rtol", _D), ("correction_start", _I)]
 
 
 class _SolveOpts(ctypes.Structure):
@@ -247,6 +248,15 @@ class Batch:
         """Directions swept per warp in 2D (1, 2, 4, 8; 0 = automatic)."""
         check(lib().rte_batch_tune(self.h, int(dirs_per_warp)))
 
+    def autotune(self, stream=None):
+        """Measured directions-per-warp per number of running instances (rte_batch_autotune).
+        Returns [(count, dirs_per_warp), ...] ascending."""
+        n = _I()
+        table = np.zeros(64, np.int32)
+        check(lib().rte_batch_autotune(self.h, _stream(stream), ctypes.byref(n),
+                                       table.ctypes.data_as(_P)))
+        return [(int(table[2 * k]), int(table[2 * k + 1])) for k in range(n.value)]
+
     def timing(self, enable):
         """enable=1 reset+start, 0 reset+stop, -1 read.  Returns a dict of phase times (ms) and
         counts: sweep (kernel only), dsa, rom, setup."""
@@ -344,9 +354,11 @@ class Rom:
 
     @staticmethod
     def build(train: Batch, eps_train=1e-12, window=3, rank_p=20, rank_c=20, eps_pod=1e-9,
-              max_iter=2000, dsa_rtol=1e-12, stream=None):
+              max_iter=2000, dsa_rtol=1e-12, correction_start="zero", stream=None):
+        """(rom_p, rom_c); correction_start="romig" takes the correction snapshots from training
+        runs started at the ROMIG guess (for ROMIG followed by ROMSAD)."""
         o = _RomOpts(float(eps_train), int(window), int(rank_p), int(rank_c), float(eps_pod),
-                     int(max_iter), float(dsa_rtol))
+                     int(max_iter), float(dsa_rtol), 1 if correction_start == "romig" else 0)
         hp, hc = _P(), _P()
         check(lib().rte_rom_build(train.h, ctypes.byref(o), ctypes.byref(hp), ctypes.byref(hc),
                                   _stream(stream)))

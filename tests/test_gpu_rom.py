@@ -110,3 +110,36 @@ def test_romsad_forced_schedule_iterates_and_converged(roms):
         eps_r = 0.1 * max(1e-13, rc.eps_pod)
         n_rom_expected = sum(1 for l, dl in enumerate(h[:-1], start=1) if l <= 5 and dl >= eps_r)
         assert rep2[b]["n_romsa"] == n_rom_expected
+
+
+def test_romig_started_correction_rom_matches_oracle():
+    """Correction snapshots from ROMIG-started training runs (remark after Alg. 2): same snapshot
+    count and leading singular values as the oracle, and ROMIG + ROMSAD on test instances under a
+    forced schedule agrees iterate by iterate.  The ROMIG guesses of the two sides differ at the
+    Gram-SVD level (~1e-9 relative), which carries into the snapshots: singular values are
+    compared at 1e-7 sigma_1."""
+    rte = _rte()
+    train = inputs.lattice_train(N, NA, n_train=6, n_vz=NVZ)
+    tb = rte.Batch.from_problem(train)
+    kw = dict(eps_train=1e-13, window=2, rank_p=3, rank_c=6)
+    rp, rc = rte.Rom.build(tb, max_iter=300, dsa_rtol=1e-13, correction_start="romig", **kw)
+    off = OfflineROMs(train, correction_start="romig", **kw)
+    assert rc.n_snap == off.dF.shape[1]
+    np.testing.assert_allclose(rc.sv[:6], off.pod_c.sv[:6], atol=1e-7 * off.pod_c.sv[0])
+    test = inputs.lattice_test(N, NA, 2, n_vz=NVZ)
+    batch = rte.Batch(tb.disc, 2)
+    batch.set_params(test)
+    rho = torch.zeros((2, test.n_dof), dtype=torch.float64, device="cuda")
+    rp.initial_guess(batch, rho)
+    sched = np.array([1, 1, 0, 0, 0, 0], np.uint8)
+    rep, _, _ = batch.solve(rho, 0.0, sa=rte.SA_ROMSAD, max_iter=6, rom_c=rc, schedule=sched,
+                            dsa_rtol=1e-13, dsa_max_it=3000)
+    got = rho.cpu().numpy()
+    names = ["romsa" if s else "dsa" for s in sched]
+    for b in range(2):
+        tr = Transport(test, b)
+        rho0 = off.rom_p.initial_guess(tr)
+        ref = sisa(tr, rho0, 0.0, 6, "romsad", dsa=ConsistentDSA(tr), rom_c=off.rom_c,
+                   schedule=names)
+        assert _rel(got[b], ref["rho"]) < 1e-6
+        assert rep[b]["n_romsa"] == 2 and rep[b]["n_dsa"] == 4
