@@ -35,7 +35,10 @@ FP64_PEAK_TFLOPS = 1.25     # GB300 FP64 rate from the profiling recipe's unit t
 FLOP_PER_CELL_DIR = 80      # 40 FMA per cell and distinct direction
 BYTES_PER_CELL_SWEEP = 76   # rho_in 32 B + G0 8 B + material id 4 B + rho_out 32 B
 # DRAM bytes per sweep launch from the committed ncu capture, valid only for this kernel source
-NCU_TRAFFIC = {"sha1": None, "bytes_per_launch": None, "workload": None}
+NCU_TRAFFIC = {"sha1": "4ae0cfbc012c24a503da42c8d4216cb3c1af0052", "bytes_per_launch": 544263723,
+               "batch": 128, "n": 128, "angles": 64,
+               "workload": "lattice128x128_CL(16,4) batch 128, mean of the 12 sweep launches of "
+                           "one ROMSAD step (profiles/sweep2d_traffic_lattice128_b128.md)"}
 
 
 def sweep_source_sha1():
@@ -63,7 +66,10 @@ def parse():
                     help="sweep directions per warp (0 = occupancy rule per launch, -1 = measured "
                          "by the autotuner before timing)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--methods", default="romsad,si_dsa,romig,romig_romsad,romsad_mixed")
+    ap.add_argument("--methods", default="romsad,si_dsa,romig,romig_romsad,romsad_mixed,pgmres,"
+                                         "romig_pgmres")
+    ap.add_argument("--gmres-rtol", type=float, default=1e-7,
+                    help="pgmres: relative residual of the preconditioned system")
     ap.add_argument("--profile-window", action="store_true",
                     help="bracket the timed ROMSAD steps with cudaProfilerStart/Stop (for ncu)")
     ap.add_argument("--workload", default="lattice", choices=["lattice", "mixed", "serving"],
@@ -244,6 +250,17 @@ def run_ours(a, ws, rank, local):
         elif method == "romig_romsad":
             rom_p.initial_guess(batch, rho)
             sa, kw = rte.SA_ROMSAD, dict(rom_c=rom_ci, theta=5, eps_romsad=eps_romsad_i)
+        elif method in ("pgmres", "romig_pgmres"):
+            # the paper's comparison system: DSA-preconditioned GMRES(25) on (I - L) rho = b-bar
+            if method == "romig_pgmres":
+                rom_p.initial_guess(batch, rho)
+            rep, _ = batch.pgmres(rho, a.gmres_rtol, restart=25, max_iter=400,
+                                  dsa_rtol=a.dsa_rtol,
+                                  dsa_max_it=a.dsa_vcycles if a.dsa_rtol == 0 else 100,
+                                  zero_start=method == "pgmres")
+            if host_out is not None:
+                host_out.copy_(rho, non_blocking=True)
+            return rep
         else:
             sa, kw = rte.SA_DSA, {}
         rep, _, st = batch.solve(rho, a.eps, sa=sa, rel=True, max_iter=400, dsa_rtol=a.dsa_rtol,
@@ -323,7 +340,8 @@ def run_ours(a, ws, rank, local):
     sweep_cells = head["sweep_units"] / disc.n_dirs
     sweep_gbs = sweep_cells * BYTES_PER_CELL_SWEEP / (head["sweep_ms"] / 1e3) / 1e9
     traffic = None
-    if NCU_TRAFFIC["sha1"] == sweep_source_sha1():
+    if (NCU_TRAFFIC["sha1"] == sweep_source_sha1() and (B, a.n, a.angles) ==
+            (NCU_TRAFFIC["batch"], NCU_TRAFFIC["n"], NCU_TRAFFIC["angles"]) and a.dpw <= 0):
         traffic = NCU_TRAFFIC["bytes_per_launch"]
     e2e_ms = float(np.mean(e2e["times"]))
     e2e_ok = int(np.sum(e2e["err"] <= 1e-6))
