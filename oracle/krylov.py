@@ -10,12 +10,16 @@ the first pin below checks exactly this identity against Alg. 1.
 
 GMRES with restart every m inner steps (App. A): Arnoldi with modified Gram-Schmidt on
 w = M^{-1} A v, Givens rotations that track the residual of the preconditioned system, and the
-update x = x0 + V y once that residual relative to ||M^{-1} b-bar|| is below rtol or at a restart,
-after which the residual is recomputed.  Inner products are Euclidean on the DG coefficient vectors
-(the basis is orthonormal, so this is the L2 inner product of the functions).
+update x = x0 + V y once that residual estimate relative to ||M^{-1} b-bar|| is below rtol or after
+m steps.  After every update the residual r = M^{-1}(b-bar - A x) is recomputed from x (App. A
+computes it in both places); the solve stops when that recomputed residual meets rtol, otherwise
+the next cycle starts from it.  (The recomputation matters when M^{-1} is applied inexactly: the
+Arnoldi estimate then drifts from the true residual.)  Inner products are Euclidean on the DG
+coefficient vectors (the basis is orthonormal, so this is the L2 inner product of the functions).
 
 Transport sweeps are counted as the paper does: one to form b-bar, one per application of
-A = I - L, and one per (re-)initialisation residual b-bar - A x when x is not zero.
+A = I - L, one per residual recomputation (end of every cycle) and one for the starting residual
+when x0 is not zero.
 """
 from __future__ import annotations
 
@@ -25,8 +29,8 @@ import numpy as np
 def pgmres(tr, rho0, rtol, m=25, max_outer=50, precond=None):
     """Solve (I - L) rho = b-bar for one instance.  precond(R) returns the correction for the
     source R = Sigma_s v (e.g. ConsistentDSA.correction) or None for no preconditioning.
-    Returns dict(rho, n_sweep, n_iter, converged, res) with res the relative preconditioned
-    residual after every Arnoldi step."""
+    Returns dict(rho, n_sweep, n_iter, n_cycles, converged, res) with res the relative
+    preconditioned residual estimate after every Arnoldi step."""
     n_sweep = 0
 
     def apply_A(v):
@@ -45,11 +49,13 @@ def pgmres(tr, rho0, rtol, m=25, max_outer=50, precond=None):
     ref = float(np.linalg.norm(apply_Minv(bbar)))
     r = apply_Minv(bbar - apply_A(x)) if np.any(x) else apply_Minv(bbar)
     res_hist = []
-    n_iter = 0
+    n_iter = n_cycles = 0
     for _ in range(max_outer):
         beta = float(np.linalg.norm(r))
         if ref == 0.0 or beta / ref <= rtol:
-            return dict(rho=x, n_sweep=n_sweep, n_iter=n_iter, converged=True, res=res_hist)
+            return dict(rho=x, n_sweep=n_sweep, n_iter=n_iter, n_cycles=n_cycles, converged=True,
+                        res=res_hist)
+        n_cycles += 1
         V = np.zeros((m + 1, x.size))
         H = np.zeros((m + 1, m))
         cs, sn = np.zeros(m), np.zeros(m)
@@ -57,7 +63,6 @@ def pgmres(tr, rho0, rtol, m=25, max_outer=50, precond=None):
         V[0] = r / beta
         g[0] = beta
         k = 0
-        done = False
         for i in range(m):
             w = apply_Minv(apply_A(V[i]))
             n_iter += 1
@@ -79,14 +84,13 @@ def pgmres(tr, rho0, rtol, m=25, max_outer=50, precond=None):
             k = i + 1
             res_hist.append(abs(g[i + 1]) / ref)
             if abs(g[i + 1]) / ref <= rtol:
-                done = True
                 break
         # x = x0 + V y with H y = g (upper triangular after the rotations)
         y = np.zeros(k)
         for i in range(k - 1, -1, -1):
             y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]
         x = x + V[:k].T @ y
-        if done:
-            return dict(rho=x, n_sweep=n_sweep, n_iter=n_iter, converged=True, res=res_hist)
-        r = apply_Minv(bbar - apply_A(x))               # re-initialisation before the restart
-    return dict(rho=x, n_sweep=n_sweep, n_iter=n_iter, converged=False, res=res_hist)
+        r = apply_Minv(bbar - apply_A(x))               # residual recomputed from the update
+    converged = ref == 0.0 or float(np.linalg.norm(r)) / ref <= rtol
+    return dict(rho=x, n_sweep=n_sweep, n_iter=n_iter, n_cycles=n_cycles, converged=converged,
+                res=res_hist)
