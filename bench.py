@@ -72,7 +72,7 @@ def parse():
                     help="pgmres: relative residual of the preconditioned system")
     ap.add_argument("--profile-window", action="store_true",
                     help="bracket the timed ROMSAD steps with cudaProfilerStart/Stop (for ncu)")
-    ap.add_argument("--workload", default="lattice", choices=["lattice", "mixed", "serving"],
+    ap.add_argument("--workload", default="lattice", choices=["lattice", "mixed", "serving", "paper"],
                     help="lattice: one discretisation, batches of --batch instances; mixed: 256 "
                          "instances over 12 (mesh, angles) buckets solved together; serving: a "
                          "Poisson request stream over 20 buckets through the serving loop")
@@ -648,6 +648,123 @@ def run_serving(a, ws, rank, local):
     return line
 
 
+# ---- the paper's own 2D test problems -------------------------------------------------------
+
+# n_sweep, T_rel and reduced dimensions printed in the paper: Tab. "Results for the problem with
+# homogeneous medium" (Sec. 4.2.1) and Tab. "Results for the pin-cell problem" (Sec. 4.2.3);
+# Matlab on the paper's hardware, averages over its own 10 random test parameters.
+PAPER_TABLES = {
+    "homogeneous": {"n_sweep": {"DSA": 14.6, "ROMIG": 3.0, "ROMSA": 2.9, "ROMSAD": 2.9,
+                                "PGMRES": 11.0, "PGMRES-ROMIG": 4.8},
+                    "T_rel": {"DSA": 1.0, "ROMIG": 0.19512, "ROMSA": 0.16578, "ROMSAD": 0.17853,
+                              "PGMRES": 0.78778, "PGMRES-ROMIG": 0.33966},
+                    "r_p": 5, "r_c": 14},
+    "pin_cell": {"n_sweep": {"DSA": 39.3, "ROMIG": 5.3, "ROMSAD": 4.0, "PGMRES": 16.2,
+                             "PGMRES-ROMIG": 5.6},
+                 "T_rel": {"DSA": 1.0, "ROMIG": 0.13143, "ROMSAD": 0.09336, "PGMRES": 0.40070,
+                           "PGMRES-ROMIG": 0.13781},
+                 "r_p": 21, "r_c": 59},
+}
+
+
+def run_paper(a, ws, rank, local):
+    """The paper's homogeneous-medium (Sec. 4.2.1) and pin-cell (Sec. 4.2.3) problems on the GPU:
+    80x80 mesh, CL(30,6), the paper's training sets, tolerances, eps_POD = 1e-9, window 3 and
+    theta; 10 seeded random test parameters.  Every method solves the 10 test instances as one
+    batch from its own start; n_sweep, the GPU time relative to SI-DSA, the residual
+    ||(I - L) rho - b-bar||_inf and the reduced dimensions are reported next to the paper's."""
+    import torch
+
+    import __graft_entry__
+    from paper_2402_10488_gb300 import inputs, rte
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    setups = {
+        "homogeneous": dict(make=inputs.homogeneous_medium, train=inputs.homogeneous_train(),
+                            test=inputs.homogeneous_test(10, seed=inputs.TEST_SEED0 + rank),
+                            eps=1e-12, gmres_rtol=1e-11, theta=3,
+                            methods=["DSA", "ROMIG", "ROMSA", "ROMSAD", "PGMRES", "PGMRES-ROMIG"]),
+        "pin_cell": dict(make=inputs.pin_cell, train=inputs.pin_cell_train(),
+                         test=inputs.pin_cell_test(10, seed=inputs.TEST_SEED0 + rank),
+                         eps=1e-11, gmres_rtol=2.5e-11, theta=5,
+                         methods=["DSA", "ROMIG", "ROMSAD", "PGMRES", "PGMRES-ROMIG"]),
+    }
+    dsa = dict(dsa_rtol=a.dsa_rtol if a.dsa_rtol > 0 else 1e-8, dsa_max_it=200)
+    out = {}
+    stream = torch.cuda.current_stream()
+    head_value = None
+    for name, S in setups.items():
+        train, test = S["make"](S["train"]), S["make"](S["test"])
+        disc = rte.Disc(train, device=local)
+        tb = rte.Batch(disc, train.batch)
+        tb.set_params(train)
+        t0 = time.time()
+        rom_p, rom_c = rte.Rom.build(tb, eps_train=S["eps"], window=3, rank_p=0, rank_c=0,
+                                     eps_pod=1e-9, max_iter=2000, dsa_rtol=1e-10)
+        offline_s = time.time() - t0
+        tb.close()
+        eps_rs = 0.1 * max(S["eps"], rom_c.eps_pod)
+        batch = rte.Batch(disc, test.batch)
+        batch.set_params(test)
+        rho = torch.zeros((test.batch, disc.n_dof), dtype=torch.float64, device="cuda")
+        chk = torch.empty_like(rho)
+
+        def run(m):
+            rho.zero_()
+            if m in ("ROMIG", "PGMRES-ROMIG"):
+                rom_p.initial_guess(batch, rho)
+            if m in ("PGMRES", "PGMRES-ROMIG"):
+                reps, _ = batch.pgmres(rho, S["gmres_rtol"], restart=25, max_iter=500,
+                                       zero_start=m == "PGMRES", **dsa)
+                return reps
+            sa = {"DSA": rte.SA_DSA, "ROMIG": rte.SA_DSA, "ROMSA": rte.SA_ROMSA,
+                  "ROMSAD": rte.SA_ROMSAD}[m]
+            reps, _, _ = batch.solve(rho, S["eps"], sa=sa, rel=False, max_iter=2000,
+                                     rom_c=rom_c if sa in (rte.SA_ROMSA, rte.SA_ROMSAD) else None,
+                                     theta=S["theta"], eps_romsad=eps_rs, **dsa)
+            return reps
+
+        res = {}
+        for m in S["methods"]:
+            for _ in range(max(1, a.warmup)):
+                run(m)
+            times = []
+            for _ in range(max(1, a.steps)):
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                reps = run(m)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            batch.sweep(rho, chk)
+            torch.cuda.synchronize()
+            resid = (rho - chk).abs().amax(1).cpu().numpy()
+            res[m] = dict(n_sweep=float(np.mean([r["n_sweep"] for r in reps])),
+                          converged=int(sum(r["converged"] for r in reps)),
+                          ms=float(np.mean(times)), residual_inf=float(np.mean(resid)),
+                          n_romsa=float(np.mean([r["n_romsa"] for r in reps])))
+        for m in res:
+            res[m]["T_rel"] = res[m]["ms"] / res["DSA"]["ms"]
+        out[name] = dict(ours=res, paper=PAPER_TABLES[name], r_p=rom_p.r, r_c=rom_c.r,
+                         offline_s=offline_s, eps_pod_c=rom_c.eps_pod)
+        if name == "pin_cell":
+            head_value = test.batch / (res["ROMSAD"]["ms"] / 1e3)
+    line = {
+        "metric": METRIC, "value": head_value, "unit": "solves/s", "n_gpus": ws,
+        "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": out["pin_cell"]["ours"]["ROMSAD"]["ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (the paper's parametric problems, seeded test parameters)",
+        "config": {"workload": "paper_2d_homogeneous_and_pin_cell_80x80_CL(30,6)",
+                   "dsa": f"FGMRES rtol {dsa['dsa_rtol']:g} (the paper: AMG)",
+                   "value": "ROMSAD solves/s on the 10 pin-cell test instances (one batch)"},
+        "problems": out,
+    }
+    return line
+
+
 # ---- CPU oracle (baseline leg and the reference arm) ------------------------------------------
 
 ORACLE_SAMPLE = r"""
@@ -752,7 +869,8 @@ def main():
             print(json.dumps(line), flush=True)
         return
     if a.workload != "lattice":
-        line = (run_mixed if a.workload == "mixed" else run_serving)(a, ws, rank, local)
+        line = {"mixed": run_mixed, "serving": run_serving, "paper": run_paper}[a.workload](
+            a, ws, rank, local)
         if rank == 0:
             print(json.dumps(line), flush=True)
         return

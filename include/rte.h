@@ -244,8 +244,9 @@ typedef struct {
 } rte_rom_opts;
 
 /* Offline stage (Sec. 3.1.1, 3.2.1) on the GPU: SI-DSA solves of every training instance of
- * `train` (f stored), snapshot matrices F and delta F (window w), thin SVD through the snapshot
- * Gram matrix (FP64 on the device) and a Jacobi eigensolver of that small matrix, truncation,
+ * `train` (f stored), snapshot matrices F and delta F (window w), thin SVD by a Gram-Schmidt QR
+ * on the device (applied twice per column) and a one-sided Jacobi SVD of the small factor R,
+ * truncation,
  * U^rho, U^iso and the affine reduced operators A_{k,r} = U^T A_k U.  Produces the parametric ROM (rom_p, for ROMIG) and
  * the correction ROM (rom_c, for ROMSA).  Either output pointer may be NULL.  Synchronous. */
 int rte_rom_build(rte_batch_t train, const rte_rom_opts* opts, rte_rom_t* rom_p,
@@ -319,6 +320,30 @@ typedef struct {
  * Synchronous.  Returns RTE_ENOCONV if some instance hit max_iter. */
 int rte_solve(rte_batch_t batch, const rte_solve_opts* opts, rte_rom_t rom_c, double* rho,
               rte_solve_report* reports, double* history, void* stream);
+
+/* ---- the paper's comparison system: DSA-preconditioned GMRES (Sec. 2.3, App. A) ---------- */
+
+typedef struct {
+  double rtol;      /* stop when ||M^{-1}(b-bar - (I - L) x)|| <= rtol ||M^{-1} b-bar||            */
+  int restart;      /* m: Arnoldi steps per cycle (the paper uses 25); 1..200                       */
+  int max_iter;     /* cap on the total Arnoldi steps per instance                                 */
+  int precond;      /* 1: left preconditioner M^{-1} = I + C Sigma_s (C: the DSA correction of
+                       Alg. 1, i.e. one SI-DSA step is a Richardson step); 0: none                */
+  double dsa_rtol;  /* 2D DSA inside M^{-1}, as in rte_solve_opts                                 */
+  int dsa_max_it;
+  int zero_start;   /* 1: start from x = 0 (rho is output only); 0: rho holds the start (one
+                       extra sweep for its residual), e.g. a ROMIG guess                           */
+} rte_gmres_opts;
+
+/* Restarted GMRES on (I - L) rho = b-bar for every instance of the batch (Eq. (rho_matrix_vec)),
+ * applying I - L by a transport sweep without source and b-bar by one sweep from rho = 0.
+ *   rho      DEVICE double[B][n_dof]: start (unless zero_start) and solution
+ *   reports  HOST rte_solve_report[B] or NULL: n_sweep (one for b-bar, one per Arnoldi step, one
+ *            per residual of a nonzero iterate -- the paper's count), converged, n_dsa = applications
+ *            of M^{-1}, dsa_iters, last_change = the final relative preconditioned residual
+ * Synchronous.  RTE_ENOCONV if an instance reached max_iter. */
+int rte_pgmres(rte_batch_t batch, const rte_gmres_opts* opts, double* rho,
+               rte_solve_report* reports, void* stream);
 
 /* rte_solve on n batches at once (typically one per discretisation of a mixed-size workload),
  * each on its own stream: one host thread keeps every batch's iteration going, relaunching a

@@ -4,11 +4,10 @@
 // angular flux f^mu and the first w iterates f^{mu,(l)}; F = [f^mu] and dF = [f^mu - f^{mu,(l)}].
 // In X-Y geometry the +-v_z copies of a direction carry identical rows, so snapshots are stored
 // once per distinct direction and every row-sum is weighted by the direction's multiplicity;
-// this leaves F^T F, the singular values and U unchanged.  The thin SVD is taken through the
-// snapshot Gram matrix (deterministic tiled FP64 reduction on the GPU) and a cyclic Jacobi
-// eigensolver on the small host matrix; U = X V Lambda^{-1/2}, re-orthonormalised once by a
-// Cholesky factor of its own Gram matrix.  Truncation: a fixed rank, or Eq. (pod_truncation)
-// with singular values.  Reduced operators (affine decomposition, cellwise materials m):
+// this leaves F^T F, the singular values and U unchanged.  The thin SVD: X = Q R by classical
+// Gram-Schmidt applied twice per column on the GPU (deterministic tiled FP64 inner products),
+// then a one-sided Jacobi SVD R = U_R Sigma V^T on the host, U = Q U_R.  Truncation: a fixed rank,
+// or Eq. (pod_truncation) with singular values.  Reduced operators (affine decomposition, cellwise materials m):
 //     A_0r = sum_j U_j^T D_j U_j,   A_{a,m} = sum_j U_j^T M_m U_j,
 //     A_{s,m} = A_{a,m} - (U^iso)^T M_m U^rho,   A_{mu,r} = A_0r + sum_m sigma_a,m A_{a,m} + sigma_s,m A_{s,m}
 // with U^rho = sum_j omega_j U_j and U^iso = sum_j U_j (Eq. (rho_basis)).
@@ -308,48 +307,6 @@ __global__ void lift_kernel(const double* Ut, int n, const double* c, int r, dou
 
 // ---- host helpers -----------------------------------------------------------------------------
 
-// Cyclic Jacobi eigen-decomposition of a symmetric n x n matrix (row-major, in place):
-// eigenvalues on return in lam, eigenvectors as columns of V.
-static void jacobi_eig(std::vector<double>& A, int n, std::vector<double>& lam, std::vector<double>& V) {
-  V.assign((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
-  for (int sweep = 0; sweep < 100; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int p = 0; p < n; ++p)
-      for (int q = 0; q < n; ++q) {
-        tot += A[(size_t)p * n + q] * A[(size_t)p * n + q];
-        if (p != q) off += A[(size_t)p * n + q] * A[(size_t)p * n + q];
-      }
-    if (off <= 1e-32 * tot) break;
-    for (int p = 0; p < n - 1; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        const double apq = A[(size_t)p * n + q];
-        if (std::fabs(apq) < 1e-300) continue;
-        const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
-        const double theta = (aqq - app) / (2.0 * apq);
-        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
-        for (int k = 0; k < n; ++k) {
-          const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
-          A[(size_t)k * n + p] = c * akp - s * akq;
-          A[(size_t)k * n + q] = s * akp + c * akq;
-        }
-        for (int k = 0; k < n; ++k) {
-          const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
-          A[(size_t)p * n + k] = c * apk - s * aqk;
-          A[(size_t)q * n + k] = s * apk + c * aqk;
-        }
-        for (int k = 0; k < n; ++k) {
-          const double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
-          V[(size_t)k * n + p] = c * vkp - s * vkq;
-          V[(size_t)k * n + q] = s * vkp + c * vkq;
-        }
-      }
-  }
-  lam.resize(n);
-  for (int i = 0; i < n; ++i) lam[i] = A[(size_t)i * n + i];
-}
-
 struct GramCtx {
   DevBuf<double> partial, out;
 };
@@ -379,25 +336,106 @@ static int cross_gram(const double* X, int nxc, const double* Y, int nyc, size_t
   return RTE_OK;
 }
 
+// q -= sum_{i<j} h[i] Q_i  (columns contiguous, length nrow)
+__global__ void sub_cols_kernel(double* q, const double* Q, int j, const double* h, size_t nrow) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nrow;
+       e += (size_t)gridDim.x * blockDim.x) {
+    double s = q[e];
+    for (int i = 0; i < j; ++i) s = fma(-h[i], Q[(size_t)i * nrow + e], s);
+    q[e] = s;
+  }
+}
+
+__global__ void scale_col_kernel(double* q, double c, size_t nrow) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nrow;
+       e += (size_t)gridDim.x * blockDim.x)
+    q[e] *= c;
+}
+
+// One-sided Jacobi SVD (Hestenes) of a small n x n matrix A (row-major): rotations orthogonalise
+// the columns of A; at convergence column k has norm sigma_k and direction u_k.  Returns the
+// singular values in descending order and U (row-major, column k = u_k).  Singular values come
+// out with an absolute error of a few ulps of ||A|| (no squaring of the matrix).
+static void jacobi_svd(std::vector<double> A, int n, std::vector<double>& sv, std::vector<double>& U) {
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    bool rotated = false;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double a = 0, b = 0, g = 0;
+        for (int k = 0; k < n; ++k) {
+          const double x = A[(size_t)k * n + p], y = A[(size_t)k * n + q];
+          a += x * x, b += y * y, g += x * y;
+        }
+        if (g == 0.0 || std::fabs(g) <= 1e-15 * std::sqrt(a * b)) continue;
+        rotated = true;
+        const double zeta = (b - a) / (2.0 * g);
+        const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), s = c * t;
+        for (int k = 0; k < n; ++k) {
+          const double x = A[(size_t)k * n + p], y = A[(size_t)k * n + q];
+          A[(size_t)k * n + p] = c * x - s * y;
+          A[(size_t)k * n + q] = s * x + c * y;
+        }
+      }
+    if (!rotated) break;
+  }
+  std::vector<double> nrm(n);
+  for (int j = 0; j < n; ++j) {
+    double t = 0;
+    for (int k = 0; k < n; ++k) t += A[(size_t)k * n + j] * A[(size_t)k * n + j];
+    nrm[j] = std::sqrt(t);
+  }
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return nrm[x] > nrm[y]; });
+  sv.resize(n);
+  U.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    const int j = order[i];
+    sv[i] = nrm[j];
+    for (int k = 0; k < n; ++k) U[(size_t)k * n + i] = nrm[j] > 0 ? A[(size_t)k * n + j] / nrm[j] : 0.0;
+  }
+}
+
 // POD of X [ncol][nrow] (columns contiguous): fills rom->U [r][nrow], sv, r, eps_equiv.
+// Thin SVD X = Q R = (Q U_R) Sigma V^T: Q from classical Gram-Schmidt applied twice per column on
+// the GPU (inner products weighted by direction multiplicity), then a one-sided Jacobi SVD of the
+// small R on the host.  Unlike an eigen-decomposition of X^T X this resolves singular values down
+// to a few ulps of sigma_1, which truncation tolerances like eps_POD = 1e-9 need.
 static int pod(rte_rom_t rom, const double* X, int ncol, size_t nrow, int rank, double eps_pod,
                const double* wdir, cudaStream_t st) {
   const rte_disc_s* d = rom->disc;
   if (ncol < 1) return fail(RTE_EINVAL, "ROM: no snapshots");
   if (ncol > 128) return fail(RTE_EINVAL, "ROM: at most 128 snapshots per basis");
-  std::vector<double> G;
-  RTE_TRY(cross_gram(X, ncol, X, ncol, nrow, d->n_dof, d->P, wdir, nullptr, 1, G, st));
-  std::vector<double> lam, V;
-  jacobi_eig(G, ncol, lam, V);
-  std::vector<int> order(ncol);
-  for (int i = 0; i < ncol; ++i) order[i] = i;
-  std::sort(order.begin(), order.end(), [&](int a, int b) { return lam[a] > lam[b]; });
-  rom->sv.resize(ncol);
-  double total = 0.0;
-  for (int i = 0; i < ncol; ++i) {
-    rom->sv[i] = std::sqrt(std::max(lam[order[i]], 0.0));
-    total += rom->sv[i];
+  DevBuf<double> Q, hdev;
+  RTE_TRY(Q.alloc((size_t)ncol * nrow));
+  RTE_TRY(hdev.alloc(ncol));
+  RTE_CUDA_TRY(cudaMemcpyAsync(Q.p, X, sizeof(double) * ncol * nrow, cudaMemcpyDeviceToDevice, st));
+  std::vector<double> R((size_t)ncol * ncol, 0.0), h, nn;
+  const unsigned grid = (unsigned)std::min<size_t>((nrow + 255) / 256, 4096);
+  for (int j = 0; j < ncol; ++j) {
+    double* qj = Q.p + (size_t)j * nrow;
+    RTE_TRY(cross_gram(qj, 1, qj, 1, nrow, d->n_dof, d->P, wdir, nullptr, 1, nn, st));
+    const double xnorm = std::sqrt(std::max(nn[0], 0.0));
+    for (int pass = 0; pass < 2 && j > 0; ++pass) {
+      RTE_TRY(cross_gram(qj, 1, Q.p, j, nrow, d->n_dof, d->P, wdir, nullptr, 1, h, st));
+      for (int i = 0; i < j; ++i) R[(size_t)i * ncol + j] += h[i];
+      RTE_CUDA_TRY(cudaMemcpyAsync(hdev.p, h.data(), sizeof(double) * j, cudaMemcpyHostToDevice, st));
+      sub_cols_kernel<<<grid, 256, 0, st>>>(qj, Q.p, j, hdev.p, nrow); RTE_NOTE_LAUNCH();
+      RTE_CUDA_TRY(cudaGetLastError());
+    }
+    RTE_TRY(cross_gram(qj, 1, qj, 1, nrow, d->n_dof, d->P, wdir, nullptr, 1, nn, st));
+    const double nrm = std::sqrt(std::max(nn[0], 0.0));
+    // a column already in the span of the previous ones (to rounding) contributes nothing new
+    const bool dependent = !(nrm > 1e-14 * xnorm) || nrm == 0.0;
+    R[(size_t)j * ncol + j] = dependent ? 0.0 : nrm;
+    scale_col_kernel<<<grid, 256, 0, st>>>(qj, dependent ? 0.0 : 1.0 / nrm, nrow); RTE_NOTE_LAUNCH();
+    RTE_CUDA_TRY(cudaGetLastError());
   }
+  std::vector<double> UR;
+  jacobi_svd(R, ncol, rom->sv, UR);
+  double total = 0.0;
+  for (double v : rom->sv) total += v;
   int r = rank;
   if (r <= 0) {  // Eq. (pod_truncation): smallest l with sum_{k<=l} s_k / trace >= 1 - eps
     double acc = 0.0;
@@ -411,7 +449,7 @@ static int pod(rte_rom_t rom, const double* X, int ncol, size_t nrow, int rank, 
     }
   }
   int nz = 0;
-  for (int i = 0; i < ncol; ++i) nz += rom->sv[i] > 1e-300 * std::max(1.0, rom->sv[0]);
+  for (int i = 0; i < ncol; ++i) nz += rom->sv[i] > 1e-14 * rom->sv[0];
   r = std::min(r, std::max(nz, 1));
   r = std::min(r, ncol);
   rom->r = r;
@@ -419,50 +457,16 @@ static int pod(rte_rom_t rom, const double* X, int ncol, size_t nrow, int rank, 
   double kept = 0.0;
   for (int i = 0; i < r; ++i) kept += rom->sv[i];
   rom->eps_equiv = total > 0 ? 1.0 - kept / total : 0.0;
-  // W = V_r Lambda_r^{-1/2}
+  // U = Q U_R[:, :r]
   std::vector<double> W((size_t)ncol * r);
   for (int k = 0; k < ncol; ++k)
-    for (int i = 0; i < r; ++i) W[(size_t)k * r + i] = V[(size_t)k * ncol + order[i]] / rom->sv[i];
+    for (int i = 0; i < r; ++i) W[(size_t)k * r + i] = UR[(size_t)k * ncol + i];
   DevBuf<double> Wd;
   RTE_TRY(Wd.alloc(W.size()));
   RTE_CUDA_TRY(cudaMemcpyAsync(Wd.p, W.data(), sizeof(double) * W.size(), cudaMemcpyHostToDevice, st));
   RTE_TRY(rom->U.alloc((size_t)r * nrow));
-  basis_kernel<<<(unsigned)((nrow + 127) / 128), 128, 0, st>>>(X, ncol, Wd.p, r, nrow, rom->U.p); RTE_NOTE_LAUNCH();
+  basis_kernel<<<(unsigned)((nrow + 127) / 128), 128, 0, st>>>(Q.p, ncol, Wd.p, r, nrow, rom->U.p); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
-  // re-orthonormalise: U <- U L^{-T},  L L^T = U^T diag(mult) U
-  std::vector<double> G2;
-  RTE_TRY(cross_gram(rom->U.p, r, rom->U.p, r, nrow, d->n_dof, d->P, wdir, nullptr, 1, G2, st));
-  std::vector<double> L((size_t)r * r, 0.0);
-  for (int i = 0; i < r; ++i)
-    for (int j = 0; j <= i; ++j) {
-      double s = G2[(size_t)i * r + j];
-      for (int k = 0; k < j; ++k) s -= L[(size_t)i * r + k] * L[(size_t)j * r + k];
-      if (i == j) {
-        if (!(s > 0)) return fail(RTE_EINVAL, "ROM: basis lost rank during orthonormalisation");
-        L[(size_t)i * r + i] = std::sqrt(s);
-      } else {
-        L[(size_t)i * r + j] = s / L[(size_t)j * r + j];
-      }
-    }
-  // M = L^{-T} (upper triangular): new U_i = sum_k U_k M[k][i]
-  std::vector<double> Minv((size_t)r * r, 0.0);
-  for (int c = 0; c < r; ++c) {  // solve L^T m = e_c
-    std::vector<double> m(r, 0.0);
-    for (int i = r - 1; i >= 0; --i) {
-      double s = i == c ? 1.0 : 0.0;
-      for (int k = i + 1; k < r; ++k) s -= L[(size_t)k * r + i] * m[k];
-      m[i] = s / L[(size_t)i * r + i];
-    }
-    for (int k = 0; k < r; ++k) Minv[(size_t)k * r + c] = m[k];
-  }
-  DevBuf<double> Md, Unew;
-  RTE_TRY(Md.alloc(Minv.size()));
-  RTE_TRY(Unew.alloc((size_t)r * nrow));
-  RTE_CUDA_TRY(cudaMemcpyAsync(Md.p, Minv.data(), sizeof(double) * Minv.size(), cudaMemcpyHostToDevice, st));
-  basis_kernel<<<(unsigned)((nrow + 127) / 128), 128, 0, st>>>(rom->U.p, r, Md.p, r, nrow, Unew.p); RTE_NOTE_LAUNCH();
-  RTE_CUDA_TRY(cudaGetLastError());
-  std::swap(rom->U.p, Unew.p);
-  std::swap(rom->U.n, Unew.n);
   RTE_CUDA_TRY(cudaStreamSynchronize(st));
   return RTE_OK;
 }

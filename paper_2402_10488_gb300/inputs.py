@@ -243,3 +243,72 @@ def serving_requests(n_requests: int, rate: float = 2000.0, seed: int = SERVE_SE
                    rng.uniform(0.01, 0.1, n_requests)], 1)
     return [(float(t[k]), int(sides[k]), int(angles[k]), mu[k], float(tols[k]))
             for k in range(n_requests)]
+
+
+# ---- the paper's 2D test problems (Sec. 4.2.1 homogeneous medium, Sec. 4.2.3 pin cell) --------
+
+def cell_average(fn, nx: int, ny: int, domain, order: int = 4) -> np.ndarray:
+    """Cell averages of a function on a uniform nx x ny mesh (cell index c = j*nx + i) by an
+    order x order tensor Gauss-Legendre rule per cell (numpy's nodes)."""
+    x0, x1, y0, y1 = domain
+    hx, hy = (x1 - x0) / nx, (y1 - y0) / ny
+    t, w = np.polynomial.legendre.leggauss(order)
+    xs = x0 + hx * (np.arange(nx)[:, None] + 0.5 + 0.5 * t[None, :])   # [nx, order]
+    ys = y0 + hy * (np.arange(ny)[:, None] + 0.5 + 0.5 * t[None, :])
+    X = xs[None, :, None, :]
+    Y = ys[:, None, :, None]
+    vals = fn(X, Y)                                                       # [ny, nx, order, order]
+    avg = 0.25 * np.einsum("jiab,a,b->ji", vals, w, w)
+    return avg.reshape(-1)
+
+
+def homogeneous_medium(mu_s, n: int = 80, n_phi: int = 30, n_vz: int = 6) -> Problem:
+    """Sec. 4.2.1: [0,1]^2, sigma_a = 0, sigma_s = mu_s (one material), zero inflow,
+    G = exp(-100((x-0.5)^2 + (y-0.5)^2)) taken cellwise constant (cell averages)."""
+    mu_s = np.atleast_1d(np.asarray(mu_s, dtype=np.float64))
+    B = mu_s.size
+    dom = (0.0, 1.0, 0.0, 1.0)
+    G = cell_average(lambda x, y: np.exp(-100.0 * ((x - 0.5) ** 2 + (y - 0.5) ** 2)), n, n, dom)
+    return Problem(2, n, n, dom, "cl", n_phi, n_vz, np.zeros(n * n, np.int32), mu_s[:, None].copy(),
+                   mu_s[:, None].copy(), np.tile(G, (B, 1)), np.zeros((B, 4)), mu_s[:, None].copy(),
+                   f"homogeneous{n}_CL({n_phi},{n_vz})")
+
+
+def homogeneous_train():
+    """21 training values mu_s = 0.9 + m/200, m = 0..20 (Sec. 4.2.1)."""
+    return 0.9 + np.arange(21) / 200.0
+
+
+def homogeneous_test(n_test: int = 10, seed: int = TEST_SEED0):
+    return np.random.default_rng(seed).uniform(0.9, 1.1, n_test)
+
+
+def pin_cell_map(n: int) -> np.ndarray:
+    """Material id on an n x n mesh of [-1,1]^2: 1 inside |x| <= 0.5 and |y| <= 0.5 (cell centre
+    inside; mesh-aligned when n is a multiple of 4), else 0."""
+    i = np.arange(n)
+    c = -1.0 + (i + 0.5) * 2.0 / n
+    inside = np.abs(c) <= 0.5
+    return (inside[None, :] & inside[:, None]).astype(np.int32).reshape(-1)
+
+
+def pin_cell(mu, n: int = 80, n_phi: int = 30, n_vz: int = 6) -> Problem:
+    """Sec. 4.2.3: [-1,1]^2, zero inflow, G = exp(-100(x^2 + y^2)) (cell averages); inside the
+    centre square sigma_a = mu_a, sigma_s = mu_s; outside sigma_a = 0, sigma_s = 100."""
+    mu = np.atleast_2d(np.asarray(mu, dtype=np.float64))   # rows (mu_a, mu_s)
+    B = mu.shape[0]
+    dom = (-1.0, 1.0, -1.0, 1.0)
+    G = cell_average(lambda x, y: np.exp(-100.0 * (x ** 2 + y ** 2)), n, n, dom)
+    sigma_s = np.stack([np.full(B, 100.0), mu[:, 1]], 1)    # material 0 = outside, 1 = pin
+    sigma_t = sigma_s + np.stack([np.zeros(B), mu[:, 0]], 1)
+    return Problem(2, n, n, dom, "cl", n_phi, n_vz, pin_cell_map(n), sigma_t, sigma_s,
+                   np.tile(G, (B, 1)), np.zeros((B, 4)), mu.copy(), f"pincell{n}_CL({n_phi},{n_vz})")
+
+
+def pin_cell_train():
+    """25 training pairs (mu_a, mu_s) = (0.05 i, 0.05 j), i, j = 1..5 (Sec. 4.2.3)."""
+    return np.array([(0.05 * i, 0.05 * j) for i in range(1, 6) for j in range(1, 6)])
+
+
+def pin_cell_test(n_test: int = 10, seed: int = TEST_SEED0):
+    return np.random.default_rng(seed).uniform(0.05, 0.5, (n_test, 2))

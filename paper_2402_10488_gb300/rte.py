@@ -61,6 +61,7 @@ SIGNATURES = {
     "rte_server_wait": (_I, [_P, ctypes.c_uint64, _D, _P, _P]),
     "rte_server_stats": (_I, [_P, _P]),
     "rte_server_destroy": (_I, [_P]),
+    "rte_pgmres": (_I, [_P, _P, _P, _P, _P]),
 }
 
 
@@ -122,6 +123,11 @@ class _SolveOpts(ctypes.Structure):
 class SolveReport(ctypes.Structure):
     _fields_ = [("n_sweep", _I), ("converged", _I), ("n_romsa", _I), ("n_dsa", _I),
                 ("dsa_iters", _I), ("last_change", _D), ("rho_inf", _D), ("n_sweep32", _I)]
+
+
+class _GmresOpts(ctypes.Structure):
+    _fields_ = [("rtol", _D), ("restart", _I), ("max_iter", _I), ("precond", _I),
+                ("dsa_rtol", _D), ("dsa_max_it", _I), ("zero_start", _I)]
 
 
 class ServeReport(ctypes.Structure):
@@ -309,6 +315,16 @@ class Batch:
                                    None if hist is None else hist.ctypes.data_as(_P),
                                    _stream(stream)), allow=(RTE_ENOCONV,))
         return [_report(r) for r in reps], hist, st
+
+    def pgmres(self, rho, rtol, restart=25, max_iter=500, precond=True, dsa_rtol=0.0,
+               dsa_max_it=1, zero_start=True, stream=None):
+        """DSA-preconditioned restarted GMRES on (I - L) rho = b-bar (rte_pgmres)."""
+        o = _GmresOpts(float(rtol), int(restart), int(max_iter), 1 if precond else 0,
+                       float(dsa_rtol), int(dsa_max_it), 1 if zero_start else 0)
+        reps = (SolveReport * self.B)()
+        st = check(lib().rte_pgmres(self.h, ctypes.byref(o), _ptr(rho), reps, _stream(stream)),
+                   allow=(RTE_ENOCONV,))
+        return [_report(r) for r in reps], st
 
     def close(self):
         if self.h:
