@@ -297,9 +297,8 @@ extern "C" int rte_server_add_bucket(rte_server_t sv, rte_batch_t slots, rte_rom
   const int B = slots->B;
   const size_t n = slots->disc->n_dof;
   int e = RTE_OK;
-  if (cudaStreamCreateWithFlags(&K->st, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaHostAlloc((void**)&K->out, sizeof(double) * n * B, cudaHostAllocDefault) != cudaSuccess)
-    e = fail(RTE_ENOMEM, "rte_server_add_bucket: stream or pinned buffer");
+  if (cudaHostAlloc((void**)&K->out, sizeof(double) * n * B, cudaHostAllocDefault) != cudaSuccess)
+    e = fail(RTE_ENOMEM, "rte_server_add_bucket: pinned buffer");
   if (e == RTE_OK) e = K->s.init(slots, *o, rom_c, K->out);
   K->slot_req.assign(B, nullptr);
   K->state.assign(B, kFree);
@@ -322,6 +321,24 @@ extern "C" int rte_server_start(rte_server_t sv) {
   if (!sv) return fail(RTE_EINVAL, "rte_server_start: null argument");
   if (sv->started) return fail(RTE_ESTATE, "rte_server_start: already started");
   if (sv->buckets.empty()) return fail(RTE_ESTATE, "rte_server_start: no bucket");
+  // one stream per bucket; cheaper buckets (fewer cell x direction solves per sweep) get higher
+  // stream priority, so their short kernels are not queued behind the block backlog of the
+  // expensive ones (priorities order pending blocks only; running blocks are not preempted)
+  DeviceGuard g(sv->device);
+  int least = 0, greatest = 0;
+  RTE_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  std::vector<std::pair<double, int>> cost;
+  for (int k = 0; k < (int)sv->buckets.size(); ++k) {
+    const rte_disc_s* d = sv->buckets[k]->bt->disc;
+    cost.emplace_back((double)d->n_cells * d->n_dirs, k);
+  }
+  std::sort(cost.begin(), cost.end());
+  const int levels = least - greatest + 1, nb = (int)cost.size();
+  for (int r = 0; r < nb; ++r) {
+    const int prio = greatest + (nb > 1 ? (r * (levels - 1) + (nb - 1) / 2) / (nb - 1) : 0);
+    Bucket* K = sv->buckets[cost[r].second];
+    RTE_CUDA_TRY(cudaStreamCreateWithPriority(&K->st, cudaStreamNonBlocking, prio));
+  }
   sv->started = true;
   sv->t0 = Clock::now();
   sv->worker = std::thread(worker_main, sv);

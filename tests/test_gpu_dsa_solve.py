@@ -187,3 +187,23 @@ def test_precision_variant_fp32_then_fp64_sweeps_reaches_the_fp64_solution(sa):
         tr = Transport(p, b)
         ref = sisa(tr, np.zeros(tr.n_dof), 1e-14, 400, "dsa", dsa=ConsistentDSA(tr), tol_mode="rel")
         assert _rel(rho.cpu().numpy()[b], ref["rho"]) < 1e-10
+
+
+def test_fully_fused_vcycle_equals_level_by_level():
+    """A batch with at least one instance per SM runs the whole V-cycle in one kernel per
+    instance; every cell update, residual, restriction and prolongation is the same function in
+    the same red-black order, so the DSA correction equals, bit for bit, that of a small batch
+    (level-by-level launches for the fine levels) holding the same instances."""
+    rte = _rte()
+    big = inputs.random_2d(64, 8, 2, 3, seed=61, B=160, inflow=(0.0, 0.0, 0.0, 0.0))
+    small = big.subset([0, 77, 159])
+    R = np.random.default_rng(8).uniform(-1, 1, (160, big.n_dof))
+    out = []
+    for p, rows in ((big, slice(None)), (small, [0, 77, 159])):
+        b = rte.Batch.from_problem(p)
+        Rt = torch.tensor(R[rows], device="cuda")
+        d = torch.zeros_like(Rt)
+        b.dsa_correction(Rt, d, rtol=0.0, max_it=2)
+        torch.cuda.synchronize()
+        out.append(d.cpu().numpy())
+    assert np.array_equal(out[0][[0, 77, 159]], out[1])
