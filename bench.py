@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--batch", type=int, default=128, help="test instances per step per GPU")
+    ap.add_argument("--batch", type=int, default=152,
+                    help="test instances per step per GPU (152 = one per SM: with 4 directions "
+                         "per warp, exactly two warps per SM sub-partition)")
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--angles", type=int, default=64)
     ap.add_argument("--ntrain", type=int, default=32)
@@ -62,7 +64,7 @@ def parse():
     ap.add_argument("--dsa-vcycles", type=int, default=1)
     ap.add_argument("--fp32-switch", type=float, default=1e-5,
                     help="precision variant: FP32 sweeps until the relative change is below this")
-    ap.add_argument("--dpw", type=int, default=0,
+    ap.add_argument("--dpw", type=int, default=-1,
                     help="sweep directions per warp (0 = occupancy rule per launch, -1 = measured "
                          "by the autotuner before timing)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
