@@ -35,10 +35,10 @@ FP64_PEAK_TFLOPS = 1.25     # GB300 FP64 rate from the profiling recipe's unit t
 FLOP_PER_CELL_DIR = 80      # 40 FMA per cell and distinct direction
 BYTES_PER_CELL_SWEEP = 76   # rho_in 32 B + G0 8 B + material id 4 B + rho_out 32 B
 # DRAM bytes per sweep launch from the committed ncu capture, valid only for this kernel source
-NCU_TRAFFIC = {"sha1": "4ae0cfbc012c24a503da42c8d4216cb3c1af0052", "bytes_per_launch": 544263723,
-               "batch": 128, "n": 128, "angles": 64,
-               "workload": "lattice128x128_CL(16,4) batch 128, mean of the 12 sweep launches of "
-                           "one ROMSAD step (profiles/sweep2d_traffic_lattice128_b128.md)"}
+NCU_TRAFFIC = {"sha1": "4ae0cfbc012c24a503da42c8d4216cb3c1af0052", "bytes_per_launch": 666794475,
+               "batch": 152, "n": 128, "angles": 64,
+               "workload": "lattice128x128_CL(16,4) batch 152, mean of the 12 sweep launches of "
+                           "one ROMSAD step (profiles/sweep2d_traffic_lattice128_b152.md)"}
 
 
 def sweep_source_sha1():

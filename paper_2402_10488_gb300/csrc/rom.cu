@@ -96,17 +96,31 @@ __global__ void sum_partials_kernel(const double* partial, int nparts, int n, do
 }
 
 // U[i][row] = sum_k X[k][row] W[k][i]
-__global__ void basis_kernel(const double* __restrict__ X, int ncol, const double* __restrict__ W,
-                             int r, size_t nrow, double* U) {
+// Columns k0 .. k0+nk of the sum (nk <= kBasisChunk); accumulate = add to U instead of storing.
+constexpr int kBasisChunk = 128;
+__global__ void basis_kernel(const double* __restrict__ X, int k0, int nk,
+                             const double* __restrict__ W, int r, size_t nrow, double* U,
+                             int accumulate) {
   const size_t row = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= nrow) return;
-  double x[128];
-  for (int k = 0; k < ncol; ++k) x[k] = X[(size_t)k * nrow + row];
+  double x[kBasisChunk];
+  for (int k = 0; k < nk; ++k) x[k] = X[(size_t)(k0 + k) * nrow + row];
   for (int i = 0; i < r; ++i) {
-    double s = 0.0;
-    for (int k = 0; k < ncol; ++k) s = fma(x[k], W[k * r + i], s);
+    double s = accumulate ? U[(size_t)i * nrow + row] : 0.0;
+    for (int k = 0; k < nk; ++k) s = fma(x[k], W[(size_t)(k0 + k) * r + i], s);
     U[(size_t)i * nrow + row] = s;
   }
+}
+
+// U [r][nrow] = sum_k X[k][row] W[k][i], in chunks of kBasisChunk snapshot columns
+static int basis_launch(const double* X, int ncol, const double* W, int r, size_t nrow, double* U,
+                        cudaStream_t st) {
+  for (int k0 = 0; k0 < ncol; k0 += kBasisChunk) {
+    const int nk = std::min(kBasisChunk, ncol - k0);
+    basis_kernel<<<(unsigned)((nrow + 127) / 128), 128, 0, st>>>(X, k0, nk, W, r, nrow, U, k0 > 0); RTE_NOTE_LAUNCH();
+    RTE_CUDA_TRY(cudaGetLastError());
+  }
+  return RTE_OK;
 }
 
 // column differences: out[col] = F[b] - win[l][b] for the listed (b, l)
@@ -312,27 +326,41 @@ struct GramCtx {
 };
 
 // Host: returns sum over rows (weighted/classified) of X_i Y_j -> out[cls][i][j]
+// The Y columns are processed in chunks that keep the kernel's shared memory within bounds.
 static int cross_gram(const double* X, int nxc, const double* Y, int nyc, size_t nrow, int n_dof,
                       int P, const double* wdir, const int32_t* mat, int n_class,
                       std::vector<double>& out, cudaStream_t st) {
   const int T = 16;
-  const size_t npairs = (size_t)nxc * nyc;
-  const size_t smem = ((size_t)(nxc + nyc) * T + n_class * npairs) * sizeof(double);
-  if (smem > 200 * 1024) return fail(RTE_EINVAL, "ROM: too many snapshots for the Gram kernel");
-  RTE_CUDA_TRY(cudaFuncSetAttribute(cross_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
+  const size_t budget = 200 * 1024 / sizeof(double);
+  // largest chunk c with (nxc + c) T + n_class nxc c <= budget
+  const size_t per = (size_t)T + (size_t)n_class * nxc;
+  if ((size_t)nxc * T + per > budget) return fail(RTE_EINVAL, "ROM: too many basis vectors for the Gram kernel");
+  const int chunk = (int)std::min<size_t>(nyc, (budget - (size_t)nxc * T) / per);
   int nblocks = (int)std::min<size_t>((nrow + T - 1) / T, 1024);
   GramCtx g;
-  RTE_TRY(g.partial.alloc((size_t)nblocks * n_class * npairs));
-  RTE_TRY(g.out.alloc((size_t)n_class * npairs));
-  cross_gram_kernel<<<nblocks, 256, smem, st>>>(X, nxc, Y, nyc, nrow, n_dof, P, wdir, mat, n_class,
-                                                g.partial.p); RTE_NOTE_LAUNCH();
-  RTE_CUDA_TRY(cudaGetLastError());
-  const int n = (int)(n_class * npairs);
-  sum_partials_kernel<<<(n + 255) / 256, 256, 0, st>>>(g.partial.p, nblocks, n, g.out.p); RTE_NOTE_LAUNCH();
-  out.resize(n);
-  RTE_CUDA_TRY(cudaMemcpyAsync(out.data(), g.out.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
-  RTE_CUDA_TRY(cudaStreamSynchronize(st));
+  RTE_TRY(g.partial.alloc((size_t)nblocks * n_class * nxc * chunk));
+  RTE_TRY(g.out.alloc((size_t)n_class * nxc * chunk));
+  out.assign((size_t)n_class * nxc * nyc, 0.0);
+  std::vector<double> part;
+  for (int j0 = 0; j0 < nyc; j0 += chunk) {
+    const int nc = std::min(chunk, nyc - j0);
+    const size_t npairs = (size_t)nxc * nc;
+    const size_t smem = ((size_t)(nxc + nc) * T + n_class * npairs) * sizeof(double);
+    RTE_CUDA_TRY(cudaFuncSetAttribute(cross_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    cross_gram_kernel<<<nblocks, 256, smem, st>>>(X, nxc, Y + (size_t)j0 * nrow, nc, nrow, n_dof, P,
+                                                  wdir, mat, n_class, g.partial.p); RTE_NOTE_LAUNCH();
+    RTE_CUDA_TRY(cudaGetLastError());
+    const int n = (int)(n_class * npairs);
+    sum_partials_kernel<<<(n + 255) / 256, 256, 0, st>>>(g.partial.p, nblocks, n, g.out.p); RTE_NOTE_LAUNCH();
+    part.resize(n);
+    RTE_CUDA_TRY(cudaMemcpyAsync(part.data(), g.out.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    RTE_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int c = 0; c < n_class; ++c)
+      for (int i = 0; i < nxc; ++i)
+        for (int j = 0; j < nc; ++j)
+          out[((size_t)c * nxc + i) * nyc + j0 + j] = part[((size_t)c * nxc + i) * nc + j];
+  }
   return RTE_OK;
 }
 
@@ -406,7 +434,7 @@ static int pod(rte_rom_t rom, const double* X, int ncol, size_t nrow, int rank, 
                const double* wdir, cudaStream_t st) {
   const rte_disc_s* d = rom->disc;
   if (ncol < 1) return fail(RTE_EINVAL, "ROM: no snapshots");
-  if (ncol > 128) return fail(RTE_EINVAL, "ROM: at most 128 snapshots per basis");
+  if (ncol > 1024) return fail(RTE_EINVAL, "ROM: at most 1024 snapshots per basis");
   DevBuf<double> Q, hdev;
   RTE_TRY(Q.alloc((size_t)ncol * nrow));
   RTE_TRY(hdev.alloc(ncol));
@@ -465,8 +493,7 @@ static int pod(rte_rom_t rom, const double* X, int ncol, size_t nrow, int rank, 
   RTE_TRY(Wd.alloc(W.size()));
   RTE_CUDA_TRY(cudaMemcpyAsync(Wd.p, W.data(), sizeof(double) * W.size(), cudaMemcpyHostToDevice, st));
   RTE_TRY(rom->U.alloc((size_t)r * nrow));
-  basis_kernel<<<(unsigned)((nrow + 127) / 128), 128, 0, st>>>(Q.p, ncol, Wd.p, r, nrow, rom->U.p); RTE_NOTE_LAUNCH();
-  RTE_CUDA_TRY(cudaGetLastError());
+  RTE_TRY(basis_launch(Q.p, ncol, Wd.p, r, nrow, rom->U.p, st));
   RTE_CUDA_TRY(cudaStreamSynchronize(st));
   return RTE_OK;
 }

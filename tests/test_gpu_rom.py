@@ -143,3 +143,48 @@ def test_romig_started_correction_rom_matches_oracle():
                    schedule=names)
         assert _rel(got[b], ref["rho"]) < 1e-6
         assert rep[b]["n_romsa"] == 2 and rep[b]["n_dsa"] == 4
+
+
+@pytest.mark.slow
+def test_full_size_romsad_solution_is_a_fixed_point_of_the_oracle_operator():
+    """The bench workload at full size in the bench's launch configuration (128^2 lattice,
+    CL(16,4), 152 instances, measured sweep decomposition, one FP32 V-cycle per DSA): sampled
+    instances of the GPU's ROMSAD solution are fixed points of the oracle's discrete operator,
+    rho = L rho + b-bar (Eq. (rho_matrix_vec)), to within what the stop test at a relative change
+    of 2e-7 allows: rho is the output of a sweep that changed its input by < 2e-7 ||rho||, so one
+    more exact sweep changes it by at most ||L|| times that (||L||_inf is near 1 for these
+    scattering ratios; the DG operator is not monotone, so 1e-6, the bench's error target, is
+    the bound checked)."""
+    rte = _rte()
+    train = inputs.lattice_train(128, 64)
+    tb = rte.Batch.from_problem(train)
+    rp, rc = rte.Rom.build(tb, eps_train=1e-12, window=3, rank_p=20, rank_c=20, max_iter=500,
+                           dsa_rtol=1e-8)
+    test = inputs.lattice_test(128, 64, 152)
+    batch = rte.Batch(tb.disc, 152)
+    batch.set_params(test)
+    batch.autotune()
+    rho = torch.zeros((152, test.n_dof), dtype=torch.float64, device="cuda")
+    reps, _, st = batch.solve(rho, 2e-7, sa=rte.SA_ROMSAD, rel=True, max_iter=400, rom_c=rc,
+                              theta=5, eps_romsad=0.1 * max(1e-12, rc.eps_pod), dsa_rtol=0.0,
+                              dsa_max_it=1)
+    assert st == rte.RTE_OK and all(r["converged"] for r in reps)
+    got = rho.cpu().numpy()
+    for b in (0, 151):
+        tr = Transport(test, b)
+        fixed = tr.sweep(got[b])
+        assert _rel(fixed, got[b]) < 1e-6
+
+
+def test_more_snapshots_than_one_kernel_chunk():
+    """Correction snapshot sets larger than one chunk of the device POD (60 training instances,
+    window 3: up to 180 columns): snapshot count and leading singular values as numpy's SVD."""
+    rte = _rte()
+    train = inputs.lattice_train(8, 8, n_train=60, n_vz=2)
+    tb = rte.Batch.from_problem(train)
+    rp, rc = rte.Rom.build(tb, eps_train=1e-12, window=3, rank_p=10, rank_c=30, max_iter=300,
+                           dsa_rtol=1e-13)
+    off = OfflineROMs(train, eps_train=1e-12, window=3, rank_p=10, rank_c=30)
+    assert rc.n_snap == off.dF.shape[1] and rc.n_snap > 128
+    np.testing.assert_allclose(rc.sv[:30], off.pod_c.sv[:30], atol=1e-10 * off.pod_c.sv[0])
+    np.testing.assert_allclose(rp.sv[:10], off.pod_p.sv[:10], atol=1e-10 * off.pod_p.sv[0])
