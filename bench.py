@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--eps", type=float, default=2e-7, help="relative stop tolerance")
     ap.add_argument("--dsa-rtol", type=float, default=0.0, help="0: fixed V-cycles")
     ap.add_argument("--dsa-vcycles", type=int, default=1)
+    ap.add_argument("--dsa-nu", type=int, default=2, help="DSA multigrid smoothing sweeps per level")
     ap.add_argument("--fp32-switch", type=float, default=1e-5,
                     help="precision variant: FP32 sweeps until the relative change is below this")
     ap.add_argument("--dpw", type=int, default=-1,
@@ -231,6 +232,7 @@ def run_ours(a, ws, rank, local):
     eps_romsad_i = 0.1 * max(eps_train, rom_ci.eps_pod) if rom_ci else None
     batch = rte.Batch(disc, B)
     batch.tune(max(a.dpw, 0))
+    batch.dsa_smoothing(a.dsa_nu)
     batch.set_params(test)
     tuned = batch.autotune() if a.dpw < 0 else None
     n_dof = disc.n_dof
@@ -361,7 +363,8 @@ def run_ours(a, ws, rank, local):
                    "angles": a.angles, "distinct_directions": disc.n_dirs, "global_batch": B * ws,
                    "n_train": a.ntrain, "rank": a.rank, "window": 3, "theta": 5,
                    "eps_romsad": eps_romsad, "stop": f"relative change < {a.eps:g}",
-                   "dsa": (f"{a.dsa_vcycles} FP32 multigrid V-cycles" if a.dsa_rtol == 0 else
+                   "dsa": (f"{a.dsa_vcycles} FP32 multigrid V-cycles, {a.dsa_nu} red-black "
+                           "smoothing sweeps per level" if a.dsa_rtol == 0 else
                            f"FGMRES rtol {a.dsa_rtol}"), "error_target": 1e-6,
                    "dirs_per_warp": (a.dpw if a.dpw > 0 else
                                      f"measured per running count {tuned}" if tuned else

@@ -130,6 +130,11 @@ int rte_batch_set_slots(rte_batch_t batch, int n, const int* slots, const double
                         const double* sigma_s, const double* source, const double* inflow,
                         void* stream);
 
+/* Red-black block Gauss-Seidel sweeps per level before and after the coarse correction in the
+ * 2D DSA multigrid (default 2; 1..8).  Changes only the convergence rate of the DSA solve (the
+ * fixed point of Alg. 1 does not depend on the DSA).  Errors: RTE_EINVAL. */
+int rte_batch_dsa_smoothing(rte_batch_t batch, int nu);
+
 /* info (HOST int64[6]): B, device bytes held by the batch, directions per warp (preferred),
  * the smallest directions per warp its sweep partial sums are sized for, 1 if the
  * decomposition is picked per launch, 1 if every slot has parameters.  The device bytes of a

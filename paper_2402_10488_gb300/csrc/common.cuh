@@ -157,6 +157,7 @@ struct rte_batch_s {
   rte::DevBuf<unsigned long long> norms;  // [B][2] stop-test norms as ordered bit patterns
   rte::DevBuf<double> work;               // [B][n_dof] x 4 iteration scratch for rte_solve
   rte::DsaState* dsa = nullptr;
+  int dsa_nu = 2;                         // red-black smoothing sweeps per multigrid level (2D DSA)
   // pinned host staging for per-slot parameter uploads (rte_batch_set_slots), allocated on use
   double* stage = nullptr;
   uint8_t* stage_mask = nullptr;

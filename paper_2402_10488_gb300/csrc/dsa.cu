@@ -1074,7 +1074,7 @@ static int dsa2d_vcycles(rte_batch_t bt, const double* R, double* drho, int k,
       residual_ext_kernel<<<dim3((nc + 127) / 128, B), 128, 0, st>>>(L0, s->K, s->borig.p, s->xtot.p,
                                                                    s->bl[0]->p, active); RTE_NOTE_LAUNCH();
     }
-    RTE_TRY(vcycle(bt, 0, active, st, 2));
+    RTE_TRY(vcycle(bt, 0, active, st, bt->dsa_nu));
     if (it == 0) {
       RTE_CUDA_TRY(cudaMemcpyAsync(s->xtot.p, s->xl[0]->p, sizeof(float) * (size_t)B * per,
                                    cudaMemcpyDeviceToDevice, st));
@@ -1162,7 +1162,7 @@ static int dsa2d_fgmres(rte_batch_t bt, const double* R, double* drho, double rt
       double* zk = s->Z.p + (size_t)k * vstride;
       // z_k = M^{-1} v_k (one FP32 V-cycle)
       to32_kernel<<<gvec_c, 256, 0, st>>>(vk, s->bl[0]->p, 0, n, act_dev.p); RTE_NOTE_LAUNCH();
-      RTE_TRY(vcycle(bt, 0, act_dev.p, st, 2));
+      RTE_TRY(vcycle(bt, 0, act_dev.p, st, bt->dsa_nu));
       to64_kernel<<<gvec_c, 256, 0, st>>>(s->xl[0]->p, zk, n, act_dev.p); RTE_NOTE_LAUNCH();
       // w = A z_k (FP64)
       fine_apply64_kernel<<<gvec, 256, 0, st>>>(F, d->nx, d->ny, B, zk, w, act_dev.p); RTE_NOTE_LAUNCH();
@@ -1307,4 +1307,10 @@ extern "C" int rte_dsa_correction(rte_batch_t b, const double* R, double* drho, 
   if (s != RTE_OK && s != RTE_ENOCONV) return s;
   RTE_CUDA_TRY(cudaStreamSynchronize(st));
   return s;
+}
+
+extern "C" int rte_batch_dsa_smoothing(rte_batch_t b, int nu) {
+  if (!b || nu < 1 || nu > 8) return fail(RTE_EINVAL, "rte_batch_dsa_smoothing: need 1 <= nu <= 8");
+  b->dsa_nu = nu;
+  return RTE_OK;
 }

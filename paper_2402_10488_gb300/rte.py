@@ -62,6 +62,7 @@ SIGNATURES = {
     "rte_server_stats": (_I, [_P, _P]),
     "rte_server_destroy": (_I, [_P]),
     "rte_pgmres": (_I, [_P, _P, _P, _P, _P]),
+    "rte_batch_dsa_smoothing": (_I, [_P, _I]),
 }
 
 
@@ -243,6 +244,10 @@ class Batch:
         check(lib().rte_batch_set_slots(self.h, n, sl.ctypes.data_as(_P), st.ctypes.data_as(_P),
                                         ss.ctypes.data_as(_P), src.ctypes.data_as(_P),
                                         inf.ctypes.data_as(_P), _stream(stream)))
+
+    def dsa_smoothing(self, nu):
+        """Red-black smoothing sweeps per multigrid level of the 2D DSA (rte_batch_dsa_smoothing)."""
+        check(lib().rte_batch_dsa_smoothing(self.h, int(nu)))
 
     def info(self):
         out = np.zeros(6, np.int64)
