@@ -75,7 +75,8 @@ def parse():
                     help="pgmres: relative residual of the preconditioned system")
     ap.add_argument("--profile-window", action="store_true",
                     help="bracket the timed ROMSAD steps with cudaProfilerStart/Stop (for ncu)")
-    ap.add_argument("--workload", default="lattice", choices=["lattice", "mixed", "serving", "paper"],
+    ap.add_argument("--workload", default="lattice",
+                    choices=["lattice", "mixed", "serving", "paper", "paper1d"],
                     help="lattice: one discretisation, batches of --batch instances; mixed: 256 "
                          "instances over 12 (mesh, angles) buckets solved together; serving: a "
                          "Poisson request stream over 20 buckets through the serving loop")
@@ -775,6 +776,86 @@ def run_paper(a, ws, rank, local):
     return line
 
 
+# n_sweep and reduced dimensions printed in the paper for the 1D cross-regime problem (Sec. 4.1.1:
+# Tab. of reduced dimensions and Tab. "Results for the cross-regime problem", eps_SISA = 1e-11).
+PAPER_TABLES_1D = {
+    1e-9: {"r_p": 6, "r_c": {1: 6, 3: 15},
+           "n_sweep": {"DSA": 15, "ROMIG": 9, "ROMSA-1": 23.75, "ROMSAD-1,3": 6.55,
+                       "ROMSA-3": 42.25, "ROMSAD-3,3": 6.85}},
+    1e-10: {"r_p": 6, "r_c": {1: 6, 3: 18},
+            "n_sweep": {"DSA": 15, "ROMIG": 9, "ROMSA-1": 23.75, "ROMSAD-1,3": 6.6,
+                        "ROMSA-3": 12.05, "ROMSAD-3,3": 5.8}},
+    1e-11: {"r_p": 7, "r_c": {1: 7, 3: 21},
+            "n_sweep": {"DSA": 15, "ROMIG": 9, "ROMSA-1": 7.05, "ROMSAD-1,3": 5.65,
+                        "ROMSA-3": 4.55, "ROMSAD-3,3": 4.5}},
+}
+
+
+def run_paper1d(a, ws, rank, local):
+    """The paper's 1D cross-regime problem (Sec. 4.1.1) on the GPU: 400 cells on [0,10], S_16,
+    41 training slopes, eps_SISA = 1e-11 (absolute), eps_POD in {1e-9, 1e-10, 1e-11}, windows 1
+    and 3, theta = 3; 20 seeded random test slopes solved as one batch per method.  Reports
+    n_sweep and the reduced dimensions next to the paper's tables."""
+    import torch
+
+    import __graft_entry__
+    from paper_2402_10488_gb300 import inputs, rte
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    train = inputs.cross_regime(inputs.cross_regime_train())
+    test = inputs.cross_regime(inputs.cross_regime_test(20, seed=inputs.TEST_SEED0 + rank))
+    disc = rte.Disc(train, device=local)
+    tb = rte.Batch(disc, train.batch)
+    tb.set_params(train)
+    batch = rte.Batch(disc, test.batch)
+    batch.set_params(test)
+    rho = torch.zeros((test.batch, disc.n_dof), dtype=torch.float64, device="cuda")
+    chk = torch.empty_like(rho)
+    eps = 1e-11
+    out = {}
+    t_all = time.time()
+
+    def run(sa, rom_c=None, rom_p=None, theta=0, eps_rs=0.0):
+        rho.zero_()
+        if rom_p is not None:
+            rom_p.initial_guess(batch, rho)
+        reps, _, _ = batch.solve(rho, eps, sa=sa, rel=False, max_iter=2000, rom_c=rom_c,
+                                 theta=theta, eps_romsad=eps_rs)
+        batch.sweep(rho, chk)
+        torch.cuda.synchronize()
+        return dict(n_sweep=float(np.mean([r["n_sweep"] for r in reps])),
+                    converged=int(sum(r["converged"] for r in reps)),
+                    residual_inf=float((rho - chk).abs().amax(1).mean().item()))
+
+    dsa = run(rte.SA_DSA)
+    for eps_pod in (1e-9, 1e-10, 1e-11):
+        res = {"DSA": dsa}
+        ranks = {}
+        for w in (1, 3):
+            rom_p, rom_c = rte.Rom.build(tb, eps_train=eps, window=w, rank_p=0, rank_c=0,
+                                         eps_pod=eps_pod, max_iter=2000, dsa_rtol=1e-10)
+            eps_rs = 0.1 * max(eps, rom_c.eps_pod)
+            ranks["r_p"] = rom_p.r
+            ranks[f"r_c(w={w})"] = rom_c.r
+            if w == 1:
+                res["ROMIG"] = run(rte.SA_DSA, rom_p=rom_p)
+            res[f"ROMSA-{w}"] = run(rte.SA_ROMSA, rom_c=rom_c)
+            res[f"ROMSAD-{w},3"] = run(rte.SA_ROMSAD, rom_c=rom_c, theta=3, eps_rs=eps_rs)
+        out[f"{eps_pod:g}"] = dict(ours=res, ranks=ranks, paper=PAPER_TABLES_1D[eps_pod])
+    line = {
+        "metric": METRIC, "value": None, "unit": "solves/s", "n_gpus": ws, "steps": 1, "warmup": 0,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (the paper's 1D cross-regime problem, seeded test slopes)",
+        "config": {"workload": "paper_1d_cross_regime_400_S16",
+                   "note": "sweep counts and reduced dimensions vs the paper; sigma_s cellwise "
+                           "constant (cell averages) where the paper has it linear in each cell",
+                   "wall_s": time.time() - t_all},
+        "eps_pod": out,
+    }
+    return line
+
+
 # ---- CPU oracle (baseline leg and the reference arm) ------------------------------------------
 
 ORACLE_SAMPLE = r"""
@@ -879,7 +960,8 @@ def main():
             print(json.dumps(line), flush=True)
         return
     if a.workload != "lattice":
-        line = {"mixed": run_mixed, "serving": run_serving, "paper": run_paper}[a.workload](
+        line = {"mixed": run_mixed, "serving": run_serving, "paper": run_paper,
+                "paper1d": run_paper1d}[a.workload](
             a, ws, rank, local)
         if rank == 0:
             print(json.dumps(line), flush=True)

@@ -258,29 +258,34 @@ static std::vector<SweepGroup> groups_for(const rte_disc_s* disc, int dpw) {
 
 void pick_groups(rte_batch_t b, int n_active, int* dpw, int* n_groups, const SweepGroup** dev) {
   int use = b->dpw;
+  auto kof = [](int v) { return v == 1 ? 0 : v == 2 ? 1 : v == 4 ? 2 : 3; };
   if (b->force_dpw && b->disc->dim == 2) {
     use = b->force_dpw;
-  } else if (b->dpw_dynamic && b->disc->dim == 2 && !b->tuned.empty()) {
-    use = b->tuned.back().second;
-    for (const auto& e : b->tuned)
-      if (n_active <= e.first) {
-        use = e.second;
-        break;
-      }
-    use = std::max(use, b->min_dpw);
   } else if (b->dpw_dynamic && b->disc->dim == 2) {
-    use = 1;
-    for (int k = 3; k >= 1; --k) {
-      const int cand = 1 << k;
-      if (cand > b->dpw) continue;
-      if ((long long)n_active * b->gcount[k] >= 4LL * b->n_sm) {
-        use = cand;
-        break;
+    if (!b->tuned.empty()) {
+      use = b->tuned.back().second;
+      for (const auto& e : b->tuned)
+        if (n_active <= e.first) {
+          use = e.second;
+          break;
+        }
+    } else {
+      use = 1;
+      for (int k = 3; k >= 1; --k) {
+        const int cand = 1 << k;
+        if (cand > b->dpw) continue;
+        if ((long long)n_active * b->gcount[k] >= 4LL * b->n_sm) {
+          use = cand;
+          break;
+        }
       }
     }
-    use = std::max(use, b->min_dpw);
+    // partial sums are indexed by the rank among running instances: a finer decomposition fits
+    // when few instances run; otherwise widen the groups until the buffer holds them
+    const size_t cap = b->partial.n / std::max(b->disc->n_dof, 1);
+    while (use < kMaxDirsPerWarp && (size_t)std::max(n_active, 1) * b->gcount[kof(use)] > cap) use *= 2;
   }
-  const int k = use == 1 ? 0 : use == 2 ? 1 : use == 4 ? 2 : 3;
+  const int k = kof(use);
   if (b->disc->dim == 2 && b->groups_all_dev.p) {
     *dpw = use;
     *n_groups = b->gcount[k];

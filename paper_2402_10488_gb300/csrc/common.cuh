@@ -143,6 +143,7 @@ struct rte_batch_s {
   // ascending; empty = the occupancy rule above
   std::vector<std::pair<int, int>> tuned;
   int force_dpw = 0;                  // autotuner trials: this dpw for every launch
+  bool kba = true;                    // several warps per direction group when warps are scarce
   std::vector<double> sigma_t_h, sigma_s_h, source_h, inflow_h;
   rte::DevBuf<double> sigma_t, sigma_s;   // [B][n_mat]
   rte::DevBuf<double> G0;                 // [B][n_cells] zeroth source moment int G phi_0

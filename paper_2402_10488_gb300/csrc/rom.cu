@@ -35,11 +35,12 @@ struct RomOnline {
 // ---- kernels ------------------------------------------------------------------------------
 
 // out[part][cls][i][j] = sum over this block's rows of w(row) X[i][row] Y[j][row], rows whose
-// class is cls.  Row index = d * n_dof + e; w = mult[d]; class = mat[e / P] (or 0).
+// class is cls0 + cls (other rows are skipped).  Row index = d * n_dof + e; w = mult[d];
+// class = mat[e / P] (or 0).
 __global__ void cross_gram_kernel(const double* __restrict__ X, int nx_cols,
                                   const double* __restrict__ Y, int ny_cols, size_t nrow,
                                   int n_dof, int P, const double* __restrict__ wdir,
-                                  const int32_t* __restrict__ mat, int n_class,
+                                  const int32_t* __restrict__ mat, int cls0, int n_class,
                                   double* partial) {
   extern __shared__ double sm[];
   const int T = 16;
@@ -68,7 +69,8 @@ __global__ void cross_gram_kernel(const double* __restrict__ X, int nx_cols,
       if (row < nrow) {
         const size_t d = row / n_dof, e = row % n_dof;
         w = wdir ? wdir[d] : 1.0;
-        c = mat ? mat[e / P] : 0;
+        c = (mat ? mat[e / P] : 0) - cls0;
+        if (c < 0 || c >= n_class) w = 0.0, c = 0;
       }
       ws[threadIdx.x] = w;
       cs[threadIdx.x] = c;
@@ -326,40 +328,47 @@ struct GramCtx {
 };
 
 // Host: returns sum over rows (weighted/classified) of X_i Y_j -> out[cls][i][j]
-// The Y columns are processed in chunks that keep the kernel's shared memory within bounds.
+// Classes and Y columns are processed in chunks that keep the kernel's shared memory within
+// bounds (many classes: e.g. one material per cell).
 static int cross_gram(const double* X, int nxc, const double* Y, int nyc, size_t nrow, int n_dof,
                       int P, const double* wdir, const int32_t* mat, int n_class,
                       std::vector<double>& out, cudaStream_t st) {
   const int T = 16;
   const size_t budget = 200 * 1024 / sizeof(double);
-  // largest chunk c with (nxc + c) T + n_class nxc c <= budget
-  const size_t per = (size_t)T + (size_t)n_class * nxc;
-  if ((size_t)nxc * T + per > budget) return fail(RTE_EINVAL, "ROM: too many basis vectors for the Gram kernel");
-  const int chunk = (int)std::min<size_t>(nyc, (budget - (size_t)nxc * T) / per);
+  auto fits = [&](int nc, int ncl) {
+    return (size_t)(nxc + nc) * T + (size_t)ncl * nxc * nc <= budget;
+  };
+  int ychunk = nyc, cchunk = n_class;
+  while (!fits(ychunk, cchunk) && cchunk > 1) cchunk = (cchunk + 1) / 2;
+  while (!fits(ychunk, cchunk) && ychunk > 1) ychunk = (ychunk + 1) / 2;
+  if (!fits(ychunk, cchunk)) return fail(RTE_EINVAL, "ROM: too many basis vectors for the Gram kernel");
   int nblocks = (int)std::min<size_t>((nrow + T - 1) / T, 1024);
   GramCtx g;
-  RTE_TRY(g.partial.alloc((size_t)nblocks * n_class * nxc * chunk));
-  RTE_TRY(g.out.alloc((size_t)n_class * nxc * chunk));
+  RTE_TRY(g.partial.alloc((size_t)nblocks * cchunk * nxc * ychunk));
+  RTE_TRY(g.out.alloc((size_t)cchunk * nxc * ychunk));
   out.assign((size_t)n_class * nxc * nyc, 0.0);
   std::vector<double> part;
-  for (int j0 = 0; j0 < nyc; j0 += chunk) {
-    const int nc = std::min(chunk, nyc - j0);
-    const size_t npairs = (size_t)nxc * nc;
-    const size_t smem = ((size_t)(nxc + nc) * T + n_class * npairs) * sizeof(double);
-    RTE_CUDA_TRY(cudaFuncSetAttribute(cross_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-    cross_gram_kernel<<<nblocks, 256, smem, st>>>(X, nxc, Y + (size_t)j0 * nrow, nc, nrow, n_dof, P,
-                                                  wdir, mat, n_class, g.partial.p); RTE_NOTE_LAUNCH();
-    RTE_CUDA_TRY(cudaGetLastError());
-    const int n = (int)(n_class * npairs);
-    sum_partials_kernel<<<(n + 255) / 256, 256, 0, st>>>(g.partial.p, nblocks, n, g.out.p); RTE_NOTE_LAUNCH();
-    part.resize(n);
-    RTE_CUDA_TRY(cudaMemcpyAsync(part.data(), g.out.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
-    RTE_CUDA_TRY(cudaStreamSynchronize(st));
-    for (int c = 0; c < n_class; ++c)
-      for (int i = 0; i < nxc; ++i)
-        for (int j = 0; j < nc; ++j)
-          out[((size_t)c * nxc + i) * nyc + j0 + j] = part[((size_t)c * nxc + i) * nc + j];
+  for (int c0 = 0; c0 < n_class; c0 += cchunk) {
+    const int ncl = std::min(cchunk, n_class - c0);
+    for (int j0 = 0; j0 < nyc; j0 += ychunk) {
+      const int nc = std::min(ychunk, nyc - j0);
+      const size_t npairs = (size_t)nxc * nc;
+      const size_t smem = ((size_t)(nxc + nc) * T + ncl * npairs) * sizeof(double);
+      RTE_CUDA_TRY(cudaFuncSetAttribute(cross_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+      cross_gram_kernel<<<nblocks, 256, smem, st>>>(X, nxc, Y + (size_t)j0 * nrow, nc, nrow, n_dof,
+                                                    P, wdir, mat, c0, ncl, g.partial.p); RTE_NOTE_LAUNCH();
+      RTE_CUDA_TRY(cudaGetLastError());
+      const int n = (int)(ncl * npairs);
+      sum_partials_kernel<<<(n + 255) / 256, 256, 0, st>>>(g.partial.p, nblocks, n, g.out.p); RTE_NOTE_LAUNCH();
+      part.resize(n);
+      RTE_CUDA_TRY(cudaMemcpyAsync(part.data(), g.out.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+      RTE_CUDA_TRY(cudaStreamSynchronize(st));
+      for (int c = 0; c < ncl; ++c)
+        for (int i = 0; i < nxc; ++i)
+          for (int j = 0; j < nc; ++j)
+            out[((size_t)(c0 + c) * nxc + i) * nyc + j0 + j] = part[((size_t)c * nxc + i) * nc + j];
+    }
   }
   return RTE_OK;
 }

@@ -48,6 +48,18 @@ __device__ __forceinline__ void inv4(double m[16]) {
     for (int c = 0; c < 4; ++c) m[4 * r + c] = a[r][c + 4];
 }
 
+// Position of instance b among the instances a launch runs (b itself without a mask).  Launches
+// index their per-instance partial sums by it, so a launch needs partial-sum space only for the
+// instances it runs; a batch with few running instances can then use finer direction groups.
+// Called by all 32 lanes of a warp.
+__device__ __forceinline__ int active_rank(const uint8_t* active, int b) {
+  if (!active) return b;
+  int c = 0;
+  for (int i = threadIdx.x & 31; i < b; i += 32) c += active[i] != 0;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  return c;
+}
+
 // One thread per (instance, material, direction): the cell tables.
 __global__ void tables2d_kernel(double* tables, const double* sigma_t, const double* dirs,
                                 int B, int n_mat, int n_dirs, double hx, double hy,
@@ -168,7 +180,7 @@ __global__ void __launch_bounds__(32) sweep2d_kernel(const Sweep2DArgs A) {
   const int total = nrb * A.nx;
   const double* __restrict__ rin = A.rho_in + (size_t)b * A.n_dof;
   const double* __restrict__ G0 = A.G0 + (size_t)b * A.n_cells;
-  double* part = A.partial + ((size_t)b * A.n_groups + g) * A.n_dof;
+  double* part = A.partial + ((size_t)active_rank(A.active, b) * A.n_groups + g) * A.n_dof;
   double* psi = A.psi_out ? A.psi_out + ((size_t)b * A.n_dirs + grp.d0) * A.n_dof : nullptr;
 
   double tx[DPW][2], typ[DPW][2];
@@ -266,6 +278,142 @@ __global__ void __launch_bounds__(32) sweep2d_kernel(const Sweep2DArgs A) {
   }
 }
 
+// Multi-warp variant for launches with too few (instance, group) pairs to give every SM
+// sub-partition a warp (the last iterations of a batch, a lone large request): NW warps of one CTA
+// share the row blocks of one direction group, warp w taking blocks w, w + NW, ...  Block rb starts
+// D steps after block rb - 1 (KBA-style pipelining); lane 0 of block rb reads the last row of
+// block rb - 1, written by another warp at least kKbaChunk + 1 steps earlier, and every warp passes
+// a block barrier every kKbaChunk steps, so that row is visible when read (no flags, no waits other
+// than the barriers, which every thread reaches the same number of times).  Blocks alternate
+// between two line buffers.  D >= H + kKbaChunk, and NW * D >= nx + H - 1 so that a warp has
+// finished a block before its next one starts.  Sources are the precomputed cell sources.
+constexpr int kKbaChunk = 8;
+
+template <int DPW, bool SMEM_TAB>
+__global__ void __launch_bounds__(256) sweep2d_kba_kernel(const Sweep2DArgs A, int D) {
+  const int g = blockIdx.x, b = blockIdx.y;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, NW = blockDim.x >> 5;
+  if (A.active && !A.active[b]) return;  // uniform over the CTA, before any barrier
+  const SweepGroup grp = A.groups[g];
+  const bool xneg = grp.quad & 1, yneg = (grp.quad & 2) != 0;
+  extern __shared__ double smem[];
+  double* ybuf = smem;                                       // [2][nx][DPW][2]
+  double* tab_s = smem + 2 * (size_t)A.nx * DPW * 2;         // [n_mat][DPW][32]
+  const double* __restrict__ tabg = A.tables + (size_t)b * A.n_mat * A.n_dirs * kTab2D;
+  if (SMEM_TAB) {
+    for (int e = threadIdx.x; e < A.n_mat * DPW * kTab2D; e += blockDim.x) {
+      const int m = e / (DPW * kTab2D), r = e % (DPW * kTab2D), dd = r / kTab2D, k = r % kTab2D;
+      tab_s[e] = dd < grp.nd ? tabg[((size_t)m * A.n_dirs + grp.d0 + dd) * kTab2D + k] : 0.0;
+    }
+  }
+  __syncthreads();
+  double w[DPW];
+#pragma unroll
+  for (int dd = 0; dd < DPW; ++dd) w[dd] = dd < grp.nd ? A.dirs[4 * (grp.d0 + dd) + 2] : 0.0;
+  const double s3 = sqrt(3.0);
+  const double c3x = xneg ? -s3 : s3, c3y = yneg ? -s3 : s3;
+  const double gxb = A.with_source ? A.inflow[4 * b + (xneg ? 1 : 0)] * A.sq_area : 0.0;
+  const double gyb = A.with_source ? A.inflow[4 * b + (yneg ? 3 : 2)] * A.sq_area : 0.0;
+  const int H = A.nx < 32 ? A.nx : 32;
+  const int nrb = (A.ny + H - 1) / H;
+  const int steps = (nrb - 1) * D + A.nx + H - 1;
+  const int padded = (steps + kKbaChunk - 1) / kKbaChunk * kKbaChunk;
+  const double* __restrict__ S = A.rho_in + (size_t)b * A.n_dof;
+  double* part = A.partial + ((size_t)active_rank(A.active, b) * A.n_groups + g) * A.n_dof;
+  double* psi = A.psi_out ? A.psi_out + ((size_t)b * A.n_dirs + grp.d0) * A.n_dof : nullptr;
+  double tx[DPW][2], typ[DPW][2];
+#pragma unroll
+  for (int dd = 0; dd < DPW; ++dd) tx[dd][0] = tx[dd][1] = typ[dd][0] = typ[dd][1] = 0.0;
+  for (int s = 0; s < padded; ++s) {
+    int rb = -1, u = -1;
+    if (s >= wid * D) {
+      rb = wid + NW * ((s - wid * D) / (NW * D));
+      u = s - rb * D - lane;
+    }
+    const bool inrange = lane < H && rb >= 0 && rb < nrb && u >= 0 && u < A.nx;
+    const int t = inrange ? u : 0;
+    const int r = rb * H + lane;
+    const bool act = inrange && r < A.ny;
+    double ty[DPW][2];
+#pragma unroll
+    for (int dd = 0; dd < DPW; ++dd) {
+      ty[dd][0] = __shfl_up_sync(0xffffffffu, typ[dd][0], 1);
+      ty[dd][1] = __shfl_up_sync(0xffffffffu, typ[dd][1], 1);
+    }
+    if (act) {
+      if (r == 0) {
+#pragma unroll
+        for (int dd = 0; dd < DPW; ++dd) ty[dd][0] = gyb, ty[dd][1] = 0.0;
+      } else if (lane == 0) {
+        const double* yb = ybuf + (size_t)((rb - 1) & 1) * A.nx * DPW * 2;
+#pragma unroll
+        for (int dd = 0; dd < DPW; ++dd) {
+          ty[dd][0] = yb[(t * DPW + dd) * 2];
+          ty[dd][1] = yb[(t * DPW + dd) * 2 + 1];
+        }
+      }
+      if (t == 0) {
+#pragma unroll
+        for (int dd = 0; dd < DPW; ++dd) tx[dd][0] = gxb, tx[dd][1] = 0.0;
+      }
+      const int i = xneg ? A.nx - 1 - t : t;
+      const int j = yneg ? A.ny - 1 - r : r;
+      const int c = j * A.nx + i;
+      const int m = A.mat[c];
+      const double2 r01 = reinterpret_cast<const double2*>(S + 4 * (size_t)c)[0];
+      const double2 r23 = reinterpret_cast<const double2*>(S + 4 * (size_t)c)[1];
+      const double s0 = r01.x, s1 = r01.y, s2 = r23.x, s3v = r23.y;
+      double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+#pragma unroll
+      for (int dd = 0; dd < DPW; ++dd) {
+        if (dd < grp.nd) {
+          const double* T = SMEM_TAB ? tab_s + (m * DPW + dd) * kTab2D
+                                     : tabg + ((size_t)m * A.n_dirs + grp.d0 + dd) * kTab2D;
+          double a[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            double v = T[4 * k] * s0;
+            v = fma(T[4 * k + 1], s1, v);
+            v = fma(T[4 * k + 2], s2, v);
+            v = fma(T[4 * k + 3], s3v, v);
+            v = fma(T[16 + 2 * k], tx[dd][0], v);
+            v = fma(T[17 + 2 * k], tx[dd][1], v);
+            v = fma(T[24 + 2 * k], ty[dd][0], v);
+            v = fma(T[25 + 2 * k], ty[dd][1], v);
+            a[k] = v;
+          }
+          tx[dd][0] = fma(c3x, a[1], a[0]);
+          tx[dd][1] = fma(c3x, a[3], a[2]);
+          typ[dd][0] = fma(c3y, a[2], a[0]);
+          typ[dd][1] = fma(c3y, a[3], a[1]);
+          acc0 = fma(w[dd], a[0], acc0);
+          acc1 = fma(w[dd], a[1], acc1);
+          acc2 = fma(w[dd], a[2], acc2);
+          acc3 = fma(w[dd], a[3], acc3);
+          if (psi) {
+            double2* p = reinterpret_cast<double2*>(psi + (size_t)dd * A.n_dof + 4 * (size_t)c);
+            p[0] = make_double2(a[0], a[1]);
+            p[1] = make_double2(a[2], a[3]);
+          }
+        }
+      }
+      double2* po = reinterpret_cast<double2*>(part + 4 * (size_t)c);
+      po[0] = make_double2(acc0, acc1);
+      po[1] = make_double2(acc2, acc3);
+      if (lane == H - 1 && rb + 1 < nrb) {
+        double* yb = ybuf + (size_t)(rb & 1) * A.nx * DPW * 2;
+#pragma unroll
+        for (int dd = 0; dd < DPW; ++dd) {
+          yb[(t * DPW + dd) * 2] = typ[dd][0];
+          yb[(t * DPW + dd) * 2 + 1] = typ[dd][1];
+        }
+      }
+    }
+    __syncwarp();
+    if ((s + 1) % kKbaChunk == 0) __syncthreads();
+  }
+}
+
 // S = Sigma_s rho + G (zeroth moment only; G omitted without source): the right-hand side shared
 // by all directions of a sweep, formed once per cell instead of once per direction warp.
 __global__ void cell_source_kernel(const double* __restrict__ rho, double* S,
@@ -310,7 +458,12 @@ __global__ void sweep1d_kernel(const Sweep1DArgs A) {
   const double c3 = neg ? -sqrt(3.0) : sqrt(3.0);
   double t = A.with_source ? A.inflow[4 * b + (neg ? 1 : 0)] * A.sq_h : 0.0;
   const double* rin = A.rho_in + (size_t)b * A.n_dof;
-  double* part = A.partial + ((size_t)b * A.n_dirs + d) * A.n_dof;
+  int rank = b;
+  if (A.active) {
+    rank = 0;
+    for (int i = 0; i < b; ++i) rank += A.active[i] != 0;
+  }
+  double* part = A.partial + ((size_t)rank * A.n_dirs + d) * A.n_dof;
   double* psi = A.psi_out ? A.psi_out + ((size_t)b * A.n_dirs + d) * A.n_dof : nullptr;
   const double* tab = A.tables + (size_t)b * A.n_mat * A.n_dirs * kTab1D;
   for (int step = 0; step < A.nx; ++step) {
@@ -336,10 +489,11 @@ __global__ void reduce_partials_kernel(const double* __restrict__ partial,
                                        int n_groups, int n_dof) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
+  const int rank = active_rank(active, b);
   const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   double dmax = 0.0, rmax = 0.0;
   if (e < n_dof) {
-    const double* p = partial + (size_t)b * n_groups * n_dof + e;
+    const double* p = partial + (size_t)rank * n_groups * n_dof + e;
     double2 acc = reinterpret_cast<const double2*>(p)[0];
     for (int g = 1; g < n_groups; ++g) {
       const double2 v = reinterpret_cast<const double2*>(p + (size_t)g * n_dof)[0];
@@ -462,6 +616,50 @@ static int launch2d(const Sweep2DArgs& A, int B, int n_groups, cudaStream_t st) 
   return RTE_OK;
 }
 
+template <int DPW>
+static int launch2d_kba(const Sweep2DArgs& A, int B, int n_groups, int NW, int D, cudaStream_t st) {
+  const size_t ybytes = 2 * (size_t)A.nx * DPW * 2 * sizeof(double);
+  const size_t tbytes = (size_t)A.n_mat * DPW * kTab2D * sizeof(double);
+  dim3 grid(n_groups, B);
+  if (ybytes + tbytes <= 48 * 1024) {
+    sweep2d_kba_kernel<DPW, true><<<grid, 32 * NW, ybytes + tbytes, st>>>(A, D); RTE_NOTE_LAUNCH();
+  } else {
+    if (ybytes > 200 * 1024) return fail(RTE_EINVAL, "sweep: mesh row too long for shared memory");
+    if (ybytes > 48 * 1024)
+      RTE_CUDA_TRY(cudaFuncSetAttribute(sweep2d_kba_kernel<DPW, false>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ybytes));
+    sweep2d_kba_kernel<DPW, false><<<grid, 32 * NW, ybytes, st>>>(A, D); RTE_NOTE_LAUNCH();
+  }
+  RTE_CUDA_TRY(cudaGetLastError());
+  return RTE_OK;
+}
+
+// Steps of the pipelined sweep with NW warps per direction group (D as in sweep_launch).
+static int kba_steps(int nx, int ny, int NW) {
+  const int H = nx < 32 ? nx : 32;
+  const int nrb = (ny + H - 1) / H;
+  const int D = std::max(H + kKbaChunk, (nx + H - 1 + NW - 1) / NW);
+  return (nrb - 1) * D + nx + H - 1;
+}
+
+// Warps per direction group for a launch: more than one only when the launch would leave SM
+// sub-partitions without a warp (each warp then has its sub-partition's FP64 unit to itself),
+// no more than there are row blocks to share, and only when the pipelined sweep is at least 10%
+// shorter than one warp walking all row blocks.
+static int kba_warps(const rte_disc_s* d, int n_sm, long long warps) {
+  const int H = d->nx < 32 ? d->nx : 32;
+  const int nrb = (d->ny + H - 1) / H;
+  if (nrb < 2 || warps <= 0 || 2 * warps > 4LL * n_sm) return 1;
+  const int max_nw = (int)std::min<long long>(std::min(nrb, 8), 4LL * n_sm / warps);
+  const int single = nrb * d->nx + H - 1;
+  int best = 1, best_steps = single;
+  for (int nw = 2; nw <= max_nw; ++nw) {
+    const int st = kba_steps(d->nx, d->ny, nw);
+    if (st < best_steps) best = nw, best_steps = st;
+  }
+  return best_steps < 0.9 * single ? best : 1;
+}
+
 int sweep_launch(rte_batch_t bt, const double* rho_in, double* rho_out, double* psi_out,
                  int with_source, const uint8_t* active, cudaStream_t st, bool fuse_norms,
                  int n_active, bool zero_norms) {
@@ -484,12 +682,25 @@ int sweep_launch(rte_batch_t bt, const double* rho_in, double* rho_out, double* 
                   bt->sigma_s.p, bt->G0.p,     bt->inflow.p,   d->mat_id.p, d->dir_dev.p,
                   gdev,         d->nx,         d->ny,          d->n_cells,  d->n_dof,
                   d->n_mat,     d->n_dirs,     n_groups,       with_source, std::sqrt(d->hx * d->hy)};
-    switch (dpw) {
-      case 1: RTE_TRY((launch2d<1, true>(A, bt->B, n_groups, st))); break;
-      case 2: RTE_TRY((launch2d<2, true>(A, bt->B, n_groups, st))); break;
-      case 4: RTE_TRY((launch2d<4, true>(A, bt->B, n_groups, st))); break;
-      case 8: RTE_TRY((launch2d<8, true>(A, bt->B, n_groups, st))); break;
-      default: return fail(RTE_EINVAL, "unsupported directions-per-warp");
+    const int NW = bt->kba ? kba_warps(d, bt->n_sm, (long long)n_active * n_groups) : 1;
+    if (NW >= 2) {
+      const int H = d->nx < 32 ? d->nx : 32;
+      const int D = std::max(H + kKbaChunk, (d->nx + H - 1 + NW - 1) / NW);  // as in kba_steps
+      switch (dpw) {
+        case 1: RTE_TRY(launch2d_kba<1>(A, bt->B, n_groups, NW, D, st)); break;
+        case 2: RTE_TRY(launch2d_kba<2>(A, bt->B, n_groups, NW, D, st)); break;
+        case 4: RTE_TRY(launch2d_kba<4>(A, bt->B, n_groups, NW, D, st)); break;
+        case 8: RTE_TRY(launch2d_kba<8>(A, bt->B, n_groups, NW, D, st)); break;
+        default: return fail(RTE_EINVAL, "unsupported directions-per-warp");
+      }
+    } else {
+      switch (dpw) {
+        case 1: RTE_TRY((launch2d<1, true>(A, bt->B, n_groups, st))); break;
+        case 2: RTE_TRY((launch2d<2, true>(A, bt->B, n_groups, st))); break;
+        case 4: RTE_TRY((launch2d<4, true>(A, bt->B, n_groups, st))); break;
+        case 8: RTE_TRY((launch2d<8, true>(A, bt->B, n_groups, st))); break;
+        default: return fail(RTE_EINVAL, "unsupported directions-per-warp");
+      }
     }
   } else {
     Sweep1DArgs A{rho_in,      bt->partial.p, psi_out,  active, bt->tables.p, bt->sigma_s.p,
@@ -692,7 +903,7 @@ __global__ void __launch_bounds__(32) sweep2d_f32_kernel(const Sweep2D32Args A) 
   const int nrb = (A.ny + H - 1) / H;
   const int total = nrb * A.nx;
   const float4* __restrict__ Sb = reinterpret_cast<const float4*>(A.S) + (size_t)b * A.n_cells;
-  float4* part = reinterpret_cast<float4*>(A.partial + ((size_t)b * A.n_groups + g) * A.n_dof);
+  float4* part = reinterpret_cast<float4*>(A.partial + ((size_t)active_rank(A.active, b) * A.n_groups + g) * A.n_dof);
   float tx[DPW][2], typ[DPW][2];
 #pragma unroll
   for (int dd = 0; dd < DPW; ++dd) tx[dd][0] = tx[dd][1] = typ[dd][0] = typ[dd][1] = 0.f;
@@ -777,10 +988,11 @@ __global__ void reduce_partials32_kernel(const float* __restrict__ partial,
                                          int n_groups, int n_dof) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
+  const int rank = active_rank(active, b);
   const int e = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
   double dmax = 0.0, rmax = 0.0;
   if (e < n_dof) {
-    const float* p = partial + (size_t)b * n_groups * n_dof + e;
+    const float* p = partial + (size_t)rank * n_groups * n_dof + e;
     double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     for (int g = 0; g < n_groups; ++g) {
       const float4 v = *reinterpret_cast<const float4*>(p + (size_t)g * n_dof);
@@ -846,8 +1058,7 @@ int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, cons
   int dpw = bt->dpw, n_groups = 0;
   const SweepGroup* gdev = nullptr;
   pick_groups(bt, n_active, &dpw, &n_groups, &gdev);
-  const int kmin = bt->min_dpw == 1 ? 0 : bt->min_dpw == 2 ? 1 : bt->min_dpw == 4 ? 2 : 3;
-  const size_t need32 = (size_t)bt->B * std::max<size_t>(bt->gcount[kmin], bt->groups.size()) * d->n_dof;
+  const size_t need32 = bt->partial.n;  // the same group-slice capacity as the FP64 partial sums
   if (bt->partial32.n < need32) RTE_TRY(bt->partial32.alloc(need32));
   if (bt->tables32_stale) {
     const size_t n = bt->tables.n;
@@ -920,7 +1131,9 @@ static int autotune(rte_batch_t bt, cudaStream_t st, int* n_entries, int* table)
     }
     float best_ms = 0.f;
     int best = 0;
-    for (int dpw = bt->min_dpw; dpw <= kMaxDirsPerWarp && status == RTE_OK; dpw *= 2) {
+    for (int dpw = 1; dpw <= kMaxDirsPerWarp && status == RTE_OK; dpw *= 2) {
+      const int k = dpw == 1 ? 0 : dpw == 2 ? 1 : dpw == 4 ? 2 : 3;
+      if ((size_t)n * bt->gcount[k] * d->n_dof > bt->partial.n) continue;  // no partial-sum space
       bt->force_dpw = dpw;
       float ms = 0.f;
       status = sweep_launch(bt, bt->work.p, bt->work.p + nb, nullptr, 1, mask.p, st, true, n);

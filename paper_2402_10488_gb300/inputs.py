@@ -312,3 +312,27 @@ def pin_cell_train():
 
 def pin_cell_test(n_test: int = 10, seed: int = TEST_SEED0):
     return np.random.default_rng(seed).uniform(0.05, 0.5, (n_test, 2))
+
+
+# ---- the paper's 1D cross-regime problem (Sec. 4.1.1) -----------------------------------------
+
+def cross_regime(mu_s, n: int = 400, n_angles: int = 16) -> Problem:
+    """Sec. 4.1.1: slab [0,10], sigma_a = 0, sigma_s(x) = 0.1 + mu_s x, G = 0.01, vacuum inflow,
+    n uniform cells, S_16.  sigma_s is taken cellwise constant at its cell average (the value at
+    the cell centre), so every cell is its own material: mat_id = cell index."""
+    mu_s = np.atleast_1d(np.asarray(mu_s, dtype=np.float64))
+    B = mu_s.size
+    xc = (np.arange(n) + 0.5) * 10.0 / n
+    sig = 0.1 + mu_s[:, None] * xc[None, :]
+    return Problem(1, n, 1, (0.0, 10.0), "gl", n_angles, 0, np.arange(n, dtype=np.int32), sig.copy(),
+                   sig.copy(), np.full((B, n), 0.01), np.zeros((B, 2)), mu_s[:, None].copy(),
+                   f"cross_regime{n}_S{n_angles}")
+
+
+def cross_regime_train():
+    """41 training slopes mu_s = 10 + j/4, j = 0..40 (Sec. 4.1.1)."""
+    return 10.0 + np.arange(41) / 4.0
+
+
+def cross_regime_test(n_test: int = 20, seed: int = TEST_SEED0):
+    return np.random.default_rng(seed).uniform(10.0, 20.0, n_test)

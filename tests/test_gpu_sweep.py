@@ -166,3 +166,59 @@ def test_autotuned_decomposition_keeps_results():
     torch.cuda.synchronize()
     ref, _ = _oracle_sweep(p, rho_in)
     _check(rout.cpu().numpy(), ref)
+
+
+def test_masked_2d_sweep_uses_compact_partials_and_finer_groups():
+    """With a mask the launch sums partials only for the running instances (indexed by their rank),
+    so a batch with few running instances may sweep with finer direction groups than its
+    partial-sum buffer holds for all instances: results of running instances match the oracle,
+    the others are untouched."""
+    rte = _rte()
+    p = inputs.random_2d(36, 16, 4, 2, seed=91, B=5, inflow=(0.3, 0.0, 0.8, 0.1), ny=40)
+    batch = rte.Batch.from_problem(p)
+    rho_in = np.random.default_rng(12).normal(size=(5, p.n_dof))
+    for mask in ([0, 1, 0, 1, 1], [0, 0, 0, 0, 1], [1, 1, 1, 1, 1]):
+        _, gpu, _ = _gpu_sweep(rte, p, rho_in, active=mask)
+        on = [b for b in range(5) if mask[b]]
+        ref, _ = _oracle_sweep(p.subset(on), rho_in[on])
+        _check(gpu[on], ref)
+        off = [b for b in range(5) if not mask[b]]
+        assert np.all(gpu[off] == 7.0)
+
+
+def test_finer_groups_than_the_buffer_holds_for_all_instances():
+    """136^2 with CL(64,4) (128 swept directions): one direction per warp needs 76 MB of partial
+    sums per instance, above the 64 MB bound, so the batch is sized for two directions per warp.
+    With one instance running, the launch sweeps one direction per warp (its partials fit in the
+    buffer by rank); the result equals the two-directions-per-warp sweep of all instances to
+    rounding (only the summation order of the partials differs)."""
+    rte = _rte()
+    p = inputs.lattice_test(136, 256, 4)
+    batch = rte.Batch.from_problem(p)
+    assert batch.info()["min_dirs_per_warp"] == 2
+    rho_in = torch.tensor(np.random.default_rng(13).uniform(0, 1, (4, p.n_dof)), device="cuda")
+    full = torch.empty_like(rho_in)
+    batch.sweep(rho_in, full)
+    one = torch.full_like(rho_in, 7.0)
+    batch.sweep(rho_in, one, active=torch.tensor([0, 0, 1, 0], dtype=torch.uint8, device="cuda"))
+    torch.cuda.synchronize()
+    f, o = full.cpu().numpy(), one.cpu().numpy()
+    assert np.abs(o[2] - f[2]).max() <= 1e-13 * np.abs(f[2]).max()
+    assert np.all(o[[0, 1, 3]] == 7.0)
+
+
+@pytest.mark.parametrize("nx,ny", [(96, 200), (130, 77)])
+def test_pipelined_multi_warp_sweep_matches_oracle(nx, ny):
+    """Launches with fewer (instance, group) warps than SM sub-partitions share each direction
+    group's row blocks among several warps of a CTA (pipelined, block barriers): one instance
+    here, 7 and 3 row blocks, inflow on every side, angular flux output included."""
+    rte = _rte()
+    p = inputs.random_2d(nx, 8, 2, 3, seed=nx + ny, B=1, inflow=(0.6, 0.2, 1.1, 0.4), ny=ny)
+    rho_in = np.random.default_rng(14).normal(size=(1, p.n_dof))
+    batch, gpu, psi = _gpu_sweep(rte, p, rho_in, psi=True)
+    ref, fs = _oracle_sweep(p, rho_in)
+    _check(gpu, ref)
+    tr, f = fs[0]
+    for k, (vx, vy, w, mult) in enumerate(batch.directions()):
+        j = int(np.argmin(np.abs(tr.v[:, 0] - vx) + np.abs(tr.v[:, 1] - vy)))
+        assert np.abs(psi[0, k] - f[j]).max() < RTOL * np.abs(f[j]).max() * 10
