@@ -714,7 +714,7 @@ def run_paper(a, ws, rank, local):
                                      eps_pod=1e-9, max_iter=2000, dsa_rtol=1e-10)
         offline_s = time.time() - t0
         tb.close()
-        eps_rs = 0.1 * max(S["eps"], rom_c.eps_pod)
+        eps_rs = 0.1 * max(S["eps"], 1e-9)  # eta max(eps_SISA, eps_POD), eps_POD = 1e-9 truncation
         batch = rte.Batch(disc, test.batch)
         batch.set_params(test)
         rho = torch.zeros((test.batch, disc.n_dof), dtype=torch.float64, device="cuda")
@@ -835,7 +835,7 @@ def run_paper1d(a, ws, rank, local):
         for w in (1, 3):
             rom_p, rom_c = rte.Rom.build(tb, eps_train=eps, window=w, rank_p=0, rank_c=0,
                                          eps_pod=eps_pod, max_iter=2000, dsa_rtol=1e-10)
-            eps_rs = 0.1 * max(eps, rom_c.eps_pod)
+            eps_rs = 0.1 * max(eps, eps_pod)  # Eq. (romsad_parameters) with the truncation tolerance
             ranks["r_p"] = rom_p.r
             ranks[f"r_c(w={w})"] = rom_c.r
             if w == 1:
