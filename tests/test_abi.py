@@ -36,3 +36,53 @@ def test_calls_without_gpu_fail_cleanly():
     with pytest.raises(rte.RTEError) as e:
         rte.Disc(inputs.slab(4, 2, 1.0, 0.5))
     assert e.value.status in (rte.RTE_ECUDA, rte.RTE_EINVAL)
+
+
+def test_boundary_rejects_bad_arguments_before_touching_the_device():
+    """Argument checks of the C ABI run on the host before any CUDA call: each bad input returns
+    RTE_EINVAL with a message (this runs with or without a GPU)."""
+    import ctypes
+
+    import numpy as np
+    L = rte.lib()
+    mat = np.zeros(4, np.int32)
+
+    def desc(**kw):
+        base = dict(dim=1, nx=4, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, n_phi=4, n_vz=0, n_mat=1,
+                    mat_id=mat.ctypes.data_as(ctypes.c_void_p))
+        base.update(kw)
+        return rte._DiscDesc(**base)
+
+    bad = [desc(dim=3), desc(nx=0), desc(ny=2), desc(x1=0.0), desc(n_mat=0), desc(n_phi=3),
+           desc(dim=2, ny=1, n_phi=5, n_vz=2), desc(dim=2, ny=1, n_phi=4, n_vz=0),
+           desc(mat_id=None)]
+    for d in bad:
+        h = ctypes.c_void_p()
+        assert L.rte_disc_create(ctypes.byref(d), 0, ctypes.byref(h)) == rte.RTE_EINVAL
+        assert L.rte_last_error()
+        assert not h.value
+    assert L.rte_disc_create(None, 0, None) == rte.RTE_EINVAL
+    null = ctypes.c_void_p()
+    assert L.rte_batch_create(None, 4, ctypes.byref(null)) == rte.RTE_EINVAL
+    assert L.rte_solve(None, None, None, None, None, None, None) == rte.RTE_EINVAL
+    assert L.rte_pgmres(None, None, None, None, None) == rte.RTE_EINVAL
+    assert L.rte_server_submit(None, 0, None, None, None, None, 1e-6, None) == rte.RTE_EINVAL
+    assert L.rte_server_wait(None, 1, 0.0, None, None) == rte.RTE_EINVAL
+    assert L.rte_rom_load(None, b"/nonexistent", ctypes.byref(null)) == rte.RTE_EINVAL
+    assert L.rte_batch_dsa_smoothing(None, 2) == rte.RTE_EINVAL
+    assert L.rte_solve_many(0, None, None, None, None, None, None) == rte.RTE_EINVAL
+    # destroying null handles is a no-op
+    for fn in (L.rte_disc_destroy, L.rte_batch_destroy, L.rte_rom_destroy, L.rte_server_destroy):
+        assert fn(None) == rte.RTE_OK
+
+
+def test_server_create_and_destroy_without_buckets():
+    """The serving loop's host object: created, refuses to start without a bucket, destroyed."""
+    import ctypes
+    L = rte.lib()
+    h = ctypes.c_void_p()
+    assert L.rte_server_create(0, ctypes.byref(h)) == rte.RTE_OK
+    assert L.rte_server_start(h) == rte.RTE_ESTATE
+    stats = (ctypes.c_double * 8)()
+    assert L.rte_server_stats(h, stats) == rte.RTE_OK and stats[2] == 0
+    assert L.rte_server_destroy(h) == rte.RTE_OK
