@@ -673,6 +673,12 @@ PAPER_TABLES = {
                  "T_rel": {"DSA": 1.0, "ROMIG": 0.13143, "ROMSAD": 0.09336, "PGMRES": 0.40070,
                            "PGMRES-ROMIG": 0.13781},
                  "r_p": 21, "r_c": 59},
+    # Tab. "Results for the variable scattering problem" (Sec. 4.2.4)
+    "variable_scattering": {"n_sweep": {"DSA": 17.0, "ROMIG": 2.6, "ROMSAD": 4.2, "PGMRES": 12.0,
+                                        "PGMRES-ROMIG": 3.8},
+                            "T_rel": {"DSA": 1.0, "ROMIG": 0.14357, "ROMSAD": 0.19879,
+                                      "PGMRES": 0.68760, "PGMRES-ROMIG": 0.20627},
+                            "r_p": 9, "r_c": 18},
 }
 
 
@@ -698,6 +704,11 @@ def run_paper(a, ws, rank, local):
                          test=inputs.pin_cell_test(10, seed=inputs.TEST_SEED0 + rank),
                          eps=1e-11, gmres_rtol=2.5e-11, theta=5,
                          methods=["DSA", "ROMIG", "ROMSAD", "PGMRES", "PGMRES-ROMIG"]),
+        "variable_scattering": dict(make=inputs.variable_scattering,
+                                    train=inputs.variable_scattering_train(),
+                                    test=inputs.variable_scattering_test(10, seed=inputs.TEST_SEED0 + rank),
+                                    eps=1e-12, gmres_rtol=2.5e-11, theta=5, eps_pod=1e-11,
+                                    methods=["DSA", "ROMIG", "ROMSAD", "PGMRES", "PGMRES-ROMIG"]),
     }
     dsa = (dict(dsa_rtol=1e-8, dsa_max_it=200) if a.paper_dsa == "fgmres" else
            dict(dsa_rtol=0.0, dsa_max_it=a.dsa_vcycles))
@@ -710,11 +721,12 @@ def run_paper(a, ws, rank, local):
         tb = rte.Batch(disc, train.batch)
         tb.set_params(train)
         t0 = time.time()
+        eps_pod = S.get("eps_pod", 1e-9)
         rom_p, rom_c = rte.Rom.build(tb, eps_train=S["eps"], window=3, rank_p=0, rank_c=0,
-                                     eps_pod=1e-9, max_iter=2000, dsa_rtol=1e-10)
+                                     eps_pod=eps_pod, max_iter=2000, dsa_rtol=1e-10)
         offline_s = time.time() - t0
         tb.close()
-        eps_rs = 0.1 * max(S["eps"], 1e-9)  # eta max(eps_SISA, eps_POD), eps_POD = 1e-9 truncation
+        eps_rs = 0.1 * max(S["eps"], eps_pod)  # eta max(eps_SISA, eps_POD), eps_POD the truncation tolerance
         batch = rte.Batch(disc, test.batch)
         batch.set_params(test)
         rho = torch.zeros((test.batch, disc.n_dof), dtype=torch.float64, device="cuda")
@@ -767,7 +779,7 @@ def run_paper(a, ws, rank, local):
         "ms_per_step": out["pin_cell"]["ours"]["ROMSAD"]["ms"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (the paper's parametric problems, seeded test parameters)",
-        "config": {"workload": "paper_2d_homogeneous_and_pin_cell_80x80_CL(30,6)",
+        "config": {"workload": "paper_2d_homogeneous_pin_cell_variable_scattering_80x80_CL(30,6)",
                    "dsa": (f"FGMRES rtol {dsa['dsa_rtol']:g} (the paper: AMG)" if dsa["dsa_rtol"] > 0
                            else f"{dsa['dsa_max_it']} FP32 multigrid V-cycles (the paper: AMG)"),
                    "value": "ROMSAD solves/s on the 10 pin-cell test instances (one batch)"},
@@ -789,6 +801,66 @@ PAPER_TABLES_1D = {
             "n_sweep": {"DSA": 15, "ROMIG": 9, "ROMSA-1": 7.05, "ROMSAD-1,3": 5.65,
                         "ROMSA-3": 4.55, "ROMSAD-3,3": 4.5}},
 }
+
+
+# The two-material problem (Sec. 4.1.2: Tab. "Results for the two-material problem"; ROMSAD with
+# theta = 1, 3, 5 performs identically there, window 3 and 5 too).
+PAPER_TABLES_1D_TWO = {
+    1e-6: {"r_p": 21, "r_c": {3: 49, 5: 54}, "n_sweep": {"DSA": 14.6, "ROMIG": 8.1, "ROMSAD-3,3": 8.9,
+                                                          "ROMSAD-5,3": 9.05}},
+    1e-9: {"r_p": 44, "r_c": {3: 101, 5: 120}, "n_sweep": {"DSA": 14.6, "ROMIG": 4.2, "ROMSAD-3,3": 5.35,
+                                                            "ROMSAD-5,3": 5.35}},
+    1e-10: {"r_p": 53, "r_c": {3: 123, 5: 147}, "n_sweep": {"DSA": 14.6, "ROMIG": 3.35, "ROMSAD-3,3": 4.25,
+                                                             "ROMSAD-5,3": 4.25}},
+}
+
+
+def run_two_material(rte, inputs, torch, local, rank):
+    """Sec. 4.1.2: two-material slab on the paper's non-uniform mesh, inflow 5 at x = 0, 451
+    training pairs, eps_SISA = 1e-12, eps_POD in {1e-6, 1e-9, 1e-10}, windows 3 and 5, theta 3;
+    20 seeded random test pairs."""
+    train = inputs.two_material(inputs.two_material_train())
+    test = inputs.two_material(inputs.two_material_test(20, seed=inputs.TEST_SEED0 + rank))
+    disc = rte.Disc(train, device=local)
+    tb = rte.Batch(disc, train.batch)
+    tb.set_params(train)
+    batch = rte.Batch(disc, test.batch)
+    batch.set_params(test)
+    rho = torch.zeros((test.batch, disc.n_dof), dtype=torch.float64, device="cuda")
+    chk = torch.empty_like(rho)
+    eps = 1e-12
+
+    def run(sa, rom_c=None, rom_p=None, theta=0, eps_rs=0.0):
+        rho.zero_()
+        if rom_p is not None:
+            rom_p.initial_guess(batch, rho)
+        reps, _, _ = batch.solve(rho, eps, sa=sa, rel=False, max_iter=2000, rom_c=rom_c,
+                                 theta=theta, eps_romsad=eps_rs)
+        batch.sweep(rho, chk)
+        torch.cuda.synchronize()
+        return dict(n_sweep=float(np.mean([r["n_sweep"] for r in reps])),
+                    converged=int(sum(r["converged"] for r in reps)),
+                    residual_inf=float((rho - chk).abs().amax(1).mean().item()))
+
+    out = {}
+    dsa = run(rte.SA_DSA)
+    for eps_pod in (1e-6, 1e-9, 1e-10):
+        res = {"DSA": dsa}
+        ranks = {}
+        t0 = time.time()
+        for w in (3, 5):
+            rom_p, rom_c = rte.Rom.build(tb, eps_train=eps, window=w, rank_p=0, rank_c=0,
+                                         eps_pod=eps_pod, max_iter=2000, dsa_rtol=1e-10)
+            ranks["r_p"] = rom_p.r
+            ranks[f"r_c(w={w})"] = rom_c.r
+            ranks[f"n_snap_c(w={w})"] = rom_c.n_snap
+            if w == 3:
+                res["ROMIG"] = run(rte.SA_DSA, rom_p=rom_p)
+            res[f"ROMSAD-{w},3"] = run(rte.SA_ROMSAD, rom_c=rom_c, theta=3,
+                                       eps_rs=0.1 * max(eps, eps_pod))
+        out[f"{eps_pod:g}"] = dict(ours=res, ranks=ranks, paper=PAPER_TABLES_1D_TWO[eps_pod],
+                                   offline_s=time.time() - t0)
+    return out
 
 
 def run_paper1d(a, ws, rank, local):
@@ -852,6 +924,7 @@ def run_paper1d(a, ws, rank, local):
                            "constant (cell averages) where the paper has it linear in each cell",
                    "wall_s": time.time() - t_all},
         "eps_pod": out,
+        "two_material": run_two_material(rte, inputs, torch, local, rank),
     }
     return line
 

@@ -80,6 +80,8 @@ typedef struct {
   int n_phi, n_vz;
   int n_mat;
   const int32_t* mat_id;
+  const double* dx;   /* 1D only, HOST double[nx] or NULL: cell widths of a non-uniform mesh
+                         (positive, summing to x1 - x0); NULL = uniform.  Ignored in 2D.         */
 } rte_disc_desc;
 
 /* Creates the discretisation on CUDA device `device`: builds the quadrature (Sec. 2.1), the
@@ -245,7 +247,7 @@ typedef struct {
   double dsa_rtol;    /* DSA solve tolerance used in the training solves                     */
   int correction_start; /* 0: correction snapshots from training runs started at zero;
                            1: from runs started at the ROMIG guess of the parametric ROM, for
-                           ROMIG followed by ROMSAD (remark after Alg. 2; vacuum inflow only)   */
+                           ROMIG followed by ROMSAD (remark after Alg. 2)                       */
 } rte_rom_opts;
 
 /* Offline stage (Sec. 3.1.1, 3.2.1) on the GPU: SI-DSA solves of every training instance of

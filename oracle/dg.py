@@ -358,6 +358,8 @@ class DG2D:
 def make_dg(problem):
     """DG object for a Problem description (paper's meshes are uniform; 1D may be non-uniform)."""
     if problem.dim == 1:
+        if getattr(problem, "edges", None) is not None:
+            return DG1D(problem.edges)
         x0, x1 = problem.domain[:2]
         return DG1D.uniform(problem.nx, x0, x1)
     x0, x1, y0, y1 = problem.domain

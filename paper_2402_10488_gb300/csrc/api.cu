@@ -67,7 +67,7 @@ static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w
 
 using namespace rte;
 
-extern "C" int rte_version(void) { return 10200; }
+extern "C" int rte_version(void) { return 10300; }
 extern "C" const char* rte_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" int rte_disc_create(const rte_disc_desc* d, int device, rte_disc_t* out) {
@@ -84,6 +84,15 @@ extern "C" int rte_disc_create(const rte_disc_desc* d, int device, rte_disc_t* o
   if (d->dim == 2 && (d->n_phi < 2 || d->n_phi % 2 || d->n_vz < 1))
     return fail(RTE_EINVAL, "2D: CL(n_phi, n_vz) needs even n_phi >= 2 and n_vz >= 1");
   if ((long long)d->nx * d->ny > (1LL << 28)) return fail(RTE_EINVAL, "mesh too large");
+  if (d->dim == 1 && d->dx) {
+    double tot = 0.0;
+    for (int c = 0; c < d->nx; ++c) {
+      if (!std::isfinite(d->dx[c]) || !(d->dx[c] > 0)) return fail(RTE_EINVAL, "cell widths must be positive");
+      tot += d->dx[c];
+    }
+    if (std::fabs(tot - (d->x1 - d->x0)) > 1e-12 * (d->x1 - d->x0))
+      return fail(RTE_EINVAL, "cell widths must sum to x1 - x0");
+  }
   int ndev = 0;
   RTE_CUDA_TRY(cudaGetDeviceCount(&ndev));
   if (device < 0 || device >= ndev) return fail(RTE_EINVAL, "bad device index");
@@ -99,6 +108,10 @@ extern "C" int rte_disc_create(const rte_disc_desc* d, int device, rte_disc_t* o
   disc->n_dof = disc->n_cells * disc->P;
   disc->x0 = d->x0, disc->x1 = d->x1, disc->y0 = d->y0, disc->y1 = d->y1;
   disc->hx = (d->x1 - d->x0) / d->nx;
+  if (d->dim == 1) {
+    if (d->dx) disc->dx.assign(d->dx, d->dx + d->nx);
+    else disc->dx.assign(d->nx, disc->hx);
+  }
   disc->hy = d->dim == 2 ? (d->y1 - d->y0) / d->ny : 1.0;
   disc->n_phi = d->n_phi;
   disc->n_vz = d->n_vz;
@@ -176,6 +189,7 @@ extern "C" int rte_disc_create(const rte_disc_desc* d, int device, rte_disc_t* o
 
   int st = disc->mat_id.alloc(disc->n_cells);
   if (st == RTE_OK) st = disc->dir_dev.alloc(4 * (size_t)disc->n_dirs);
+  if (st == RTE_OK && d->dim == 1) st = disc->dx_dev.alloc(disc->nx);
   if (st != RTE_OK) {
     delete disc;
     return st;
@@ -191,7 +205,10 @@ extern "C" int rte_disc_create(const rte_disc_desc* d, int device, rte_disc_t* o
                               sizeof(int32_t) * disc->n_cells, cudaMemcpyHostToDevice);
   cudaError_t e2 =
       cudaMemcpy(disc->dir_dev.p, dh.data(), sizeof(double) * dh.size(), cudaMemcpyHostToDevice);
-  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+  cudaError_t e3 = cudaSuccess;
+  if (d->dim == 1)
+    e3 = cudaMemcpy(disc->dx_dev.p, disc->dx.data(), sizeof(double) * disc->nx, cudaMemcpyHostToDevice);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
     delete disc;
     return fail(RTE_ECUDA, "rte_disc_create: upload failed");
   }
@@ -452,7 +469,10 @@ extern "C" int rte_batch_create(rte_disc_t disc, int B, rte_batch_t* out) {
   if (st == RTE_OK) st = b->sigma_s.alloc(nb * disc->n_mat);
   if (st == RTE_OK) st = b->G0.alloc(nb * disc->n_cells);
   if (st == RTE_OK) st = b->inflow.alloc(nb * 4);
-  if (st == RTE_OK) st = b->tables.alloc(nb * disc->n_mat * disc->n_dirs * tab);
+  // sweep tables per (instance, material, direction) in 2D; per (instance, cell, direction) in 1D
+  // (the cell width enters the table and 1D meshes may be non-uniform)
+  const size_t tab_units = disc->dim == 1 ? (size_t)disc->n_cells : (size_t)disc->n_mat;
+  if (st == RTE_OK) st = b->tables.alloc(nb * tab_units * disc->n_dirs * tab);
   if (st == RTE_OK) st = b->partial.alloc(nb * max_groups * disc->n_dof);
   if (st == RTE_OK && !all.empty()) st = b->groups_all_dev.alloc(all.size());
   if (st == RTE_OK) st = b->norms.alloc(nb * 2);
@@ -506,8 +526,8 @@ extern "C" int rte_batch_set_params(rte_batch_t b, const double* sigma_t, const 
     for (int s = 0; s < 2 * d->dim; ++s) b->inflow_h[4 * i + s] = inflow[2 * d->dim * i + s];
   // zeroth moment of a cellwise-constant source: int_T G phi_0 = G sqrt(|T|)
   std::vector<double> g0(nc);
-  const double sq = std::sqrt(d->hx * d->hy);
-  for (size_t k = 0; k < nc; ++k) g0[k] = source[k] * sq;
+  for (size_t k = 0; k < nc; ++k)
+    g0[k] = source[k] * (d->dim == 1 ? std::sqrt(d->dx[k % d->n_cells]) : std::sqrt(d->hx * d->hy));
   RTE_CUDA_TRY(cudaMemcpy(b->sigma_t.p, sigma_t, sizeof(double) * nm, cudaMemcpyHostToDevice));
   RTE_CUDA_TRY(cudaMemcpy(b->sigma_s.p, sigma_s, sizeof(double) * nm, cudaMemcpyHostToDevice));
   RTE_CUDA_TRY(cudaMemcpy(b->G0.p, g0.data(), sizeof(double) * nc, cudaMemcpyHostToDevice));
@@ -562,7 +582,6 @@ int set_slots(rte_batch_t b, int n, const int* slots, const double* sigma_t, con
   }
   if (b->slot_set.size() != (size_t)B) b->slot_set.assign(B, 0);
   std::memset(b->stage_mask, 0, B);
-  const double sq = std::sqrt(d->hx * d->hy);
   for (int i = 0; i < n; ++i) {
     const int sl = slots[i];
     double* p = b->stage + per * sl;
@@ -572,7 +591,8 @@ int set_slots(rte_batch_t b, int n, const int* slots, const double* sigma_t, con
     }
     for (int c = 0; c < nc; ++c) {
       b->source_h[(size_t)sl * nc + c] = source[(size_t)i * nc + c];
-      p[2 * nm + c] = source[(size_t)i * nc + c] * sq;  // zeroth moment of the cell source
+      p[2 * nm + c] = source[(size_t)i * nc + c] *   // zeroth moment of the cell source
+                      (d->dim == 1 ? std::sqrt(d->dx[c]) : std::sqrt(d->hx * d->hy));
     }
     for (int k = 0; k < 4; ++k)
       p[2 * nm + nc + k] = b->inflow_h[4 * (size_t)sl + k] = k < ni ? inflow[(size_t)i * ni + k] : 0.0;

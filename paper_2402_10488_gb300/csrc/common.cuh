@@ -83,7 +83,7 @@ struct DevBuf {
 };
 
 constexpr int kTab2D = 32;  // doubles per (material, direction) sweep table in 2D
-constexpr int kTab1D = 8;   // ... in 1D (Minv 2x2, Px 2x1, pad)
+constexpr int kTab1D = 8;   // ... in 1D, per (instance, cell, direction): Minv 2x2, inflow 2x1, 1/sqrt(h)
 constexpr int kMaxDirsPerWarp = 8;
 constexpr size_t kPartialBytes = size_t(64) << 20;  // per-instance sweep partial sums, upper bound
 
@@ -117,6 +117,8 @@ struct rte_disc_s {
   rte::DsaMoments mom{};
   rte::DevBuf<int32_t> mat_id;        // [n_cells]
   rte::DevBuf<double> dir_dev;        // [n_dirs][4] vx, vy, w, mult
+  std::vector<double> dx;             // 1D: cell widths (uniform: hx each)
+  rte::DevBuf<double> dx_dev;         // 1D: [nx]
 };
 
 namespace rte {
@@ -234,6 +236,7 @@ struct rte_rom_s {
   rte::DevBuf<double> U_rho;   // [r][n_dof]
   rte::DevBuf<double> U_iso;   // [r][n_dof]
   rte::DevBuf<double> U_iso0;  // [r][n_cells] zeroth-moment rows of U_iso
+  rte::DevBuf<double> a_side;  // [4][r] projection of a unit isotropic inflow through each side
   std::vector<double> A0;      // [r][r]
   std::vector<double> Aa, As;  // [n_mat][r][r]
   rte::DevBuf<double> A0_dev, Aa_dev, As_dev;

@@ -50,6 +50,24 @@ static Ops1D ops1d(double h) {
   return o;
 }
 
+// The same operators on a non-uniform 1D mesh for a cell of width h with west / east neighbours
+// of widths hw / he: the diagonal terms use h, each face coupling the traces of both cells.
+static Ops1D ops1d_cell(double hw, double h, double he) {
+  Ops1D o = ops1d(h);
+  const double s3 = std::sqrt(3.0), q = 1.0 / std::sqrt(h), qw = 1.0 / std::sqrt(hw),
+               qe = 1.0 / std::sqrt(he);
+  const double L[2] = {q, -s3 * q}, R[2] = {q, s3 * q};
+  const double Rw[2] = {qw, s3 * qw}, Le[2] = {qe, -s3 * qe};
+  for (int k = 0; k < 2; ++k)
+    for (int l = 0; l < 2; ++l) {
+      o.DCw[2 * k + l] = -0.5 * L[k] * Rw[l];
+      o.DCe[2 * k + l] = 0.5 * R[k] * Le[l];
+      o.DJw[2 * k + l] = L[k] * Rw[l];
+      o.DJe[2 * k + l] = R[k] * Le[l];
+    }
+  return o;
+}
+
 // 4x4 operator acting on the x-degree (k = a + 2b): (I_b (x) A)[a+2b][a'+2b'] = A[a][a'] d_bb'
 static void kron_x(const double A[4], double out[16]) {
   for (int k = 0; k < 16; ++k) out[k] = 0.0;
@@ -657,7 +675,7 @@ __device__ void inv4d(const double* A, double* Ai) {
 }
 
 struct Blocks1D {
-  double Dd[16], Lw[16], Ue[16];  // D without sigma terms; neighbour blocks
+  const double *Dd, *Lw, *Ue;  // [nx][16] per cell: D without sigma terms; west / east couplings
 };
 
 __global__ void dsa1d_factor_kernel(Blocks1D K, const double* sigma_t, const double* sigma_s,
@@ -670,7 +688,7 @@ __global__ void dsa1d_factor_kernel(Blocks1D K, const double* sigma_t, const dou
   for (int c = 0; c < nx; ++c) {
     const int m = mat[c];
     const double st = sigma_t[b * n_mat + m], sa = st - sigma_s[b * n_mat + m];
-    for (int e = 0; e < 16; ++e) Dp[e] = K.Dd[e];
+    for (int e = 0; e < 16; ++e) Dp[e] = K.Dd[16 * c + e];
     Dp[0] += sa, Dp[5] += sa, Dp[10] += st, Dp[15] += st;
     double* Mc = Mfac + ((size_t)b * nx + c) * 16;
     if (c > 0) {
@@ -678,13 +696,13 @@ __global__ void dsa1d_factor_kernel(Blocks1D K, const double* sigma_t, const dou
       for (int r = 0; r < 4; ++r)
         for (int q = 0; q < 4; ++q) {
           double s = 0.0;
-          for (int k = 0; k < 4; ++k) s += K.Lw[4 * r + k] * Dprev[4 * k + q];
+          for (int k = 0; k < 4; ++k) s += K.Lw[16 * c + 4 * r + k] * Dprev[4 * k + q];
           Mc[4 * r + q] = s;
         }
       for (int r = 0; r < 4; ++r)
         for (int q = 0; q < 4; ++q) {
           double s = 0.0;
-          for (int k = 0; k < 4; ++k) s += Mc[4 * r + k] * K.Ue[4 * k + q];
+          for (int k = 0; k < 4; ++k) s += Mc[4 * r + k] * K.Ue[16 * (c - 1) + 4 * k + q];
           tmp[4 * r + q] = s;
         }
       for (int e = 0; e < 16; ++e) Dp[e] -= tmp[e];
@@ -719,7 +737,7 @@ __global__ void dsa1d_solve_kernel(Blocks1D K, const double* Dpinv, const double
     for (int r = 0; r < 4; ++r) {
       double s = y[4 * c + r];
       if (c < nx - 1)
-        for (int k = 0; k < 4; ++k) s -= K.Ue[4 * r + k] * next[k];
+        for (int k = 0; k < 4; ++k) s -= K.Ue[16 * c + 4 * r + k] * next[k];
       t[r] = s;
     }
     const double* Di = Dpinv + ((size_t)b * nx + c) * 16;
@@ -739,6 +757,7 @@ struct DsaState {
   int dim = 2;
   // 1D
   Blocks1D K1{};
+  DevBuf<double> K1dev;                         // [3][nx][16] storage behind K1
   DevBuf<double> Dpinv, Mfac, work1;
   // 2D levels
   int n_levels = 0, lc = 0;                     // lc: first level of the fused coarse cycle
@@ -922,7 +941,7 @@ size_t dsa_bytes(const rte_batch_s* b) {
   if (!s) return 0;
   size_t t = 0;
   auto add = [&](size_t n, size_t e) { t += n * e; };
-  add(s->Dpinv.n + s->Mfac.n + s->work1.n, 8);
+  add(s->Dpinv.n + s->Mfac.n + s->work1.n + s->K1dev.n, 8);
   add(s->off64.n + s->diag64.n + s->V.n + s->Z.n + s->w.n + s->xs.n + s->dots_dev.n, 8);
   add(s->xtot.n + s->borig.n, 4);
   for (size_t l = 0; l < s->Ma.size(); ++l) {
@@ -947,7 +966,6 @@ int dsa_setup(rte_batch_t bt, cudaStream_t st, const uint8_t* mask) {
       c2 += w * v * v;
       if (v > 0) c1 += w * v, c3 += w * v * v * v;
     }
-    const Ops1D o = ops1d(d->hx);
     auto fill = [&](double* out, const double* DC, const double* DJ) {
       // rows (rho0, rho1, J0, J1): [[-c1 DJ, DC], [c2 DC, -3 c3 DJ]]
       for (int r = 0; r < 2; ++r)
@@ -958,9 +976,19 @@ int dsa_setup(rte_batch_t bt, cudaStream_t st, const uint8_t* mask) {
           out[4 * (r + 2) + c + 2] = -3.0 * c3 * DJ[2 * r + c];
         }
     };
-    fill(s->K1.Dd, o.DCd, o.DJd);
-    fill(s->K1.Lw, o.DCw, o.DJw);
-    fill(s->K1.Ue, o.DCe, o.DJe);
+    if (!s->K1dev.p) {  // per-cell blocks from the cell widths (fixed per discretisation)
+      const int nx = d->nx;
+      std::vector<double> K((size_t)3 * nx * 16);
+      for (int c = 0; c < nx; ++c) {
+        const double h = d->dx[c];
+        const Ops1D o = ops1d_cell(c > 0 ? d->dx[c - 1] : h, h, c + 1 < nx ? d->dx[c + 1] : h);
+        fill(&K[(size_t)16 * c], o.DCd, o.DJd);
+        fill(&K[(size_t)16 * (nx + c)], o.DCw, o.DJw);
+        fill(&K[(size_t)16 * (2 * nx + c)], o.DCe, o.DJe);
+      }
+      RTE_TRY(upload(s->K1dev, K));
+      s->K1 = Blocks1D{s->K1dev.p, s->K1dev.p + (size_t)16 * nx, s->K1dev.p + (size_t)32 * nx};
+    }
     if (!s->Dpinv.p) {
       RTE_TRY(s->Dpinv.alloc((size_t)B * d->nx * 16));
       RTE_TRY(s->Mfac.alloc((size_t)B * d->nx * 16));

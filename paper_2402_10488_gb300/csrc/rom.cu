@@ -11,7 +11,8 @@
 //     A_0r = sum_j U_j^T D_j U_j,   A_{a,m} = sum_j U_j^T M_m U_j,
 //     A_{s,m} = A_{a,m} - (U^iso)^T M_m U^rho,   A_{mu,r} = A_0r + sum_m sigma_a,m A_{a,m} + sigma_s,m A_{s,m}
 // with U^rho = sum_j omega_j U_j and U^iso = sum_j U_j (Eq. (rho_basis)).
-// Online: ROMIG rho^(0) = U^rho A_{mu,r}^{-1} (U^iso)^T G (vacuum inflow); ROMSA
+// Online: ROMIG rho^(0) = U^rho A_{mu,r}^{-1} U^T b_mu, U^T b_mu = (U^iso)^T G + sum over the
+// sides of g_side a_side (a_side = U^T of the unit isotropic inflow through that side); ROMSA
 // delta rho = dU^rho (dU^T A_mu dU)^{-1} (dU^iso)^T R (Eq. (rom_correction)).  The r x r systems
 // are assembled and LU-factored on the device once per parameter set.
 #include <cstdio>
@@ -158,6 +159,64 @@ __global__ void iso0_kernel(const double* U_iso, int r, int n_cells, int P, doub
   U_iso0[t] = U_iso[i * (size_t)n_cells * P + c * P];
 }
 
+// a_side[s][i] = U_i^T e_s: the right-hand side of a unit isotropic inflow through side s (1D: x-,
+// x+; 2D: x-, x+, y-, y+), summed over the directions entering through it with their
+// multiplicities.  In the orthonormal basis a unit inflow into a boundary cell contributes
+// |v_n| * sqrt(h_t / h_n) * (1, -+sqrt3) on the two modes constant along the face (2D; h_n the
+// width across the face, h_t along it) and |xi| / sqrt(h) * (1, -+sqrt3) in 1D.  One thread per
+// (side, i), fixed summation order.
+__global__ void inflow_basis_kernel(const double* U, int r, int n_dirs, int dim, int nx, int ny,
+                                    int n_dof, double hx, double hy, const double* dx,
+                                    const double* dirs, double* a_side) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 4 * r) return;
+  const int side = t / r, i = t % r;
+  const double s3 = sqrt(3.0);
+  double acc = 0.0;
+  if (dim == 1 && side >= 2) {
+    a_side[t] = 0.0;
+    return;
+  }
+  for (int d = 0; d < n_dirs; ++d) {
+    const double vx = dirs[4 * d], vy = dirs[4 * d + 1], mult = dirs[4 * d + 3];
+    const double* u = U + ((size_t)i * n_dirs + d) * n_dof;
+    if (dim == 1) {
+      const bool in = side == 0 ? vx > 0 : vx < 0;
+      if (!in) continue;
+      const int c = side == 0 ? 0 : nx - 1;
+      const double q = fabs(vx) / sqrt(dx[c]), sg = side == 0 ? -1.0 : 1.0;
+      acc += mult * q * (u[2 * c] + sg * s3 * u[2 * c + 1]);
+      continue;
+    }
+    const bool xside = side < 2;
+    const double vn = xside ? vx : vy;
+    const bool in = (side % 2 == 0) ? vn > 0 : vn < 0;
+    if (!in) continue;
+    const double q = xside ? fabs(vx) * sqrt(hy / hx) : fabs(vy) * sqrt(hx / hy);
+    const double sg = (side % 2 == 0) ? -1.0 : 1.0;
+    const int n_face = xside ? ny : nx;
+    for (int f = 0; f < n_face; ++f) {
+      const int c = xside ? f * nx + (side == 0 ? 0 : nx - 1) : (side == 2 ? 0 : ny - 1) * nx + f;
+      // modes constant along the face: k = 0 and k = 1 (x-faces) or k = 2 (y-faces)
+      const double m1 = xside ? u[4 * c + 1] : u[4 * c + 2];
+      acc += mult * q * (u[4 * c] + sg * s3 * m1);
+    }
+  }
+  a_side[t] = acc;
+}
+
+// proj[b][i] += sum_s g[b][s] a_side[s][i]
+__global__ void add_inflow_rhs_kernel(double* proj, const double* inflow, const double* a_side, int r,
+                                      int B, const uint8_t* mask) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= B * r) return;
+  const int b = t / r, i = t % r;
+  if (mask && !mask[b]) return;
+  double s = proj[t];
+  for (int side = 0; side < 4; ++side) s = fma(inflow[4 * b + side], a_side[(size_t)side * r + i], s);
+  proj[t] = s;
+}
+
 // Y[i][d] = D_d U[i][d]: the upwind DG transport operator without Sigma_t (2D), with zero inflow.
 __global__ void transport_apply2d_kernel(const double* U, int r, int n_dirs, int nx, int ny,
                                          double hx, double hy, const double* dirs, double* Y) {
@@ -212,20 +271,23 @@ __global__ void transport_apply2d_kernel(const double* U, int r, int n_dirs, int
   for (int k = 0; k < 4; ++k) out[k] = y[k];
 }
 
-__global__ void transport_apply1d_kernel(const double* U, int r, int n_dirs, int nx, double h,
-                                         const double* dirs, double* Y) {
+// 1D: own-cell terms scale with |xi| / h_c; the upwind face couples the upwind cell's outflow
+// trace (scaled 1/sqrt h_up) with this cell's inflow trace (scaled 1/sqrt h_c).
+__global__ void transport_apply1d_kernel(const double* U, int r, int n_dirs, int nx,
+                                         const double* dx, const double* dirs, double* Y) {
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)r * n_dirs * nx) return;
   const int c = t % nx, d = (t / nx) % n_dirs, i = t / ((size_t)nx * n_dirs);
-  const double xi = dirs[4 * d], s3 = sqrt(3.0), sg = xi < 0 ? -1.0 : 1.0, a = fabs(xi) / h;
+  const double xi = dirs[4 * d], s3 = sqrt(3.0), sg = xi < 0 ? -1.0 : 1.0, a = fabs(xi) / dx[c];
   const double* u = U + ((size_t)i * n_dirs + d) * nx * 2;
   const double a0 = u[2 * c], a1 = u[2 * c + 1];
   double y0 = a * (a0 + sg * s3 * a1), y1 = a * (-sg * s3 * a0 + 3.0 * a1);
   const int cu = c - (int)sg;
   if (cu >= 0 && cu < nx) {
+    const double au = fabs(xi) / sqrt(dx[c] * dx[cu]);
     const double tq = u[2 * cu] + sg * s3 * u[2 * cu + 1];
-    y0 -= a * tq;
-    y1 -= a * (-sg * s3) * tq;
+    y0 -= au * tq;
+    y1 -= au * (-sg * s3) * tq;
   }
   double* out = Y + ((size_t)i * n_dirs + d) * nx * 2;
   out[2 * c] = y0;
@@ -434,16 +496,238 @@ static void jacobi_svd(std::vector<double> A, int n, std::vector<double>& sv, st
   }
 }
 
+// One round of the parallel one-sided Jacobi SVD on the device: A is n x n, column-major (column
+// j at A + j n); block k rotates the disjoint column pair pairs[2k], pairs[2k+1] (-1: no partner)
+// so that the two columns become orthogonal.  rotated is set when some pair was not yet
+// orthogonal to the tolerance.  Dot products are reduced in a fixed order (deterministic).
+__global__ void jacobi_round_kernel(double* A, size_t n, const int* pairs, int npairs,
+                                    int* rotated) {
+  const int k = blockIdx.x;
+  if (k >= npairs) return;
+  const int p = pairs[2 * k], q = pairs[2 * k + 1];
+  if (p < 0 || q < 0) return;
+  double* ap = A + (size_t)p * n;
+  double* aq = A + (size_t)q * n;
+  double a = 0, b = 0, g = 0;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double x = ap[i], y = aq[i];
+    a = fma(x, x, a), b = fma(y, y, b), g = fma(x, y, g);
+  }
+  __shared__ double sa[256], sb[256], sg[256];
+  sa[threadIdx.x] = a, sb[threadIdx.x] = b, sg[threadIdx.x] = g;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      sa[threadIdx.x] += sa[threadIdx.x + h];
+      sb[threadIdx.x] += sb[threadIdx.x + h];
+      sg[threadIdx.x] += sg[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  a = sa[0], b = sb[0], g = sg[0];
+  if (g == 0.0 || fabs(g) <= 1e-15 * sqrt(a * b)) return;
+  const double zeta = (b - a) / (2.0 * g);
+  const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double x = ap[i], y = aq[i];
+    ap[i] = c * x - s * y;
+    aq[i] = s * x + c * y;
+  }
+  if (threadIdx.x == 0) atomicExch(rotated, 1);
+}
+
+// Round-robin (circle method) pairing: every two of n columns meet once per sweep, in n' - 1
+// rounds of n' / 2 disjoint pairs (n' = n rounded up to even; -1 marks the dummy column).
+static std::vector<int> round_robin_pairs(int n) {
+  const int m = n + (n & 1);
+  std::vector<int> order(m);
+  for (int i = 0; i < m; ++i) order[i] = i < n ? i : -1;
+  std::vector<int> pairs((size_t)(m - 1) * m);
+  for (int r = 0; r < m - 1; ++r) {
+    for (int k = 0; k < m / 2; ++k) {
+      pairs[((size_t)r * (m / 2) + k) * 2] = order[k];
+      pairs[((size_t)r * (m / 2) + k) * 2 + 1] = order[m - 1 - k];
+    }
+    const int last = order[m - 1];
+    for (int i = m - 1; i > 1; --i) order[i] = order[i - 1];
+    order[1] = last;
+  }
+  return pairs;
+}
+
+// Sweeps of the one-sided Jacobi method on the n columns (length len, contiguous) of A on the
+// device until no pair needs a rotation.
+static int jacobi_columns_device(double* A, size_t len, int n, cudaStream_t st) {
+  if (n < 2) return RTE_OK;
+  const int m = n + (n & 1);
+  const std::vector<int> pairs = round_robin_pairs(n);
+  DevBuf<int> P, flag;
+  RTE_TRY(P.alloc(pairs.size()));
+  RTE_TRY(flag.alloc(1));
+  RTE_CUDA_TRY(cudaMemcpyAsync(P.p, pairs.data(), sizeof(int) * pairs.size(), cudaMemcpyHostToDevice, st));
+  for (int sweep = 0; sweep < 80; ++sweep) {
+    RTE_CUDA_TRY(cudaMemsetAsync(flag.p, 0, sizeof(int), st));
+    for (int r = 0; r < m - 1; ++r) {
+      jacobi_round_kernel<<<m / 2, 256, 0, st>>>(A, len, P.p + (size_t)r * m, m / 2, flag.p); RTE_NOTE_LAUNCH();
+    }
+    RTE_CUDA_TRY(cudaGetLastError());
+    int h = 0;
+    RTE_CUDA_TRY(cudaMemcpyAsync(&h, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RTE_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!h) break;
+  }
+  return RTE_OK;
+}
+
+// One-sided Jacobi SVD of the n x n row-major matrix R on the device (for large snapshot counts):
+// the round-robin (circle) ordering pairs every two columns once per sweep in n - 1 rounds of
+// n / 2 disjoint pairs.  Same outputs as jacobi_svd.
+static int jacobi_svd_device(const std::vector<double>& R, int n, std::vector<double>& sv,
+                             std::vector<double>& U, cudaStream_t st) {
+  std::vector<double> Acm((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Acm[(size_t)j * n + i] = R[(size_t)i * n + j];
+  DevBuf<double> A;
+  RTE_TRY(A.alloc(Acm.size()));
+  RTE_CUDA_TRY(cudaMemcpyAsync(A.p, Acm.data(), sizeof(double) * Acm.size(), cudaMemcpyHostToDevice, st));
+  RTE_TRY(jacobi_columns_device(A.p, n, n, st));
+  RTE_CUDA_TRY(cudaMemcpyAsync(Acm.data(), A.p, sizeof(double) * Acm.size(), cudaMemcpyDeviceToHost, st));
+  RTE_CUDA_TRY(cudaStreamSynchronize(st));
+  std::vector<double> nrm(n);
+  for (int j = 0; j < n; ++j) {
+    double t = 0;
+    for (int i = 0; i < n; ++i) t += Acm[(size_t)j * n + i] * Acm[(size_t)j * n + i];
+    nrm[j] = std::sqrt(t);
+  }
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  std::sort(idx.begin(), idx.end(), [&](int x, int y) { return nrm[x] > nrm[y]; });
+  sv.resize(n);
+  U.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    const int j = idx[i];
+    sv[i] = nrm[j];
+    for (int k = 0; k < n; ++k) U[(size_t)k * n + i] = nrm[j] > 0 ? Acm[(size_t)j * n + k] / nrm[j] : 0.0;
+  }
+  return RTE_OK;
+}
+
+// rows of direction d (row = d * n_dof + e) scaled by w[d]^power (power = +-1/2)
+__global__ void scale_rows_kernel(double* A, int ncol, size_t nrow, int n_dof, const double* w,
+                                  double power) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)ncol * nrow) return;
+  const size_t row = t % nrow;
+  if (w) A[t] *= pow(w[row / n_dof], power);
+}
+
+// norms[j] = ||A_j|| for the n columns of length len (fixed-order block reduction)
+__global__ void col_norms_kernel(const double* A, size_t len, double* norms) {
+  const double* a = A + (size_t)blockIdx.x * len;
+  double s = 0.0;
+  for (size_t i = threadIdx.x; i < len; i += blockDim.x) s = fma(a[i], a[i], s);
+  __shared__ double sh[256];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) norms[blockIdx.x] = sqrt(sh[0]);
+}
+
+// U[i] = A[idx[i]] / sv[i], rows unweighted by w^-1/2
+__global__ void take_cols_kernel(const double* A, const int* idx, const double* sv, int r, size_t nrow,
+                                 int n_dof, const double* w, double* U) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)r * nrow) return;
+  const int i = t / nrow;
+  const size_t row = t % nrow;
+  const double sc = w ? 1.0 / sqrt(w[row / n_dof]) : 1.0;
+  U[t] = A[(size_t)idx[i] * nrow + row] / sv[i] * sc;
+}
+
+// Truncation rank: a fixed rank, or Eq. (pod_truncation) with singular values.
+static void pod_rank_of(rte_rom_t rom, int ncol, int rank, double eps_pod) {
+  double total = 0.0;
+  for (double v : rom->sv) total += v;
+  int r = rank;
+  if (r <= 0) {  // smallest l with sum_{k<=l} s_k / trace >= 1 - eps
+    double acc = 0.0;
+    r = ncol;
+    for (int i = 0; i < ncol; ++i) {
+      acc += rom->sv[i];
+      if (acc / total >= 1.0 - eps_pod) {
+        r = i + 1;
+        break;
+      }
+    }
+  }
+  int nz = 0;
+  for (int i = 0; i < ncol; ++i) nz += rom->sv[i] > 1e-14 * rom->sv[0];
+  r = std::min(r, std::max(nz, 1));
+  r = std::min(r, ncol);
+  rom->r = r;
+  rom->n_snap = ncol;
+  double kept = 0.0;
+  for (int i = 0; i < r; ++i) kept += rom->sv[i];
+  rom->eps_equiv = total > 0 ? 1.0 - kept / total : 0.0;
+}
+
+// POD of a snapshot matrix of moderate size by the one-sided Jacobi method applied to the
+// (row-weighted) snapshots themselves on the device: the columns are rotated until mutually
+// orthogonal; their norms are the singular values and their directions the left singular vectors.
+// No orthogonalisation of nearly dependent snapshots is involved, so large snapshot sets with many
+// tiny singular values keep their accuracy.
+static int pod_direct(rte_rom_t rom, const double* X, int ncol, size_t nrow, int rank,
+                      double eps_pod, const double* wdir, cudaStream_t st) {
+  const rte_disc_s* d = rom->disc;
+  DevBuf<double> A, nrmd, svd;
+  DevBuf<int> idxd;
+  RTE_TRY(A.alloc((size_t)ncol * nrow));
+  RTE_TRY(nrmd.alloc(ncol));
+  RTE_CUDA_TRY(cudaMemcpyAsync(A.p, X, sizeof(double) * ncol * nrow, cudaMemcpyDeviceToDevice, st));
+  const size_t tot = (size_t)ncol * nrow;
+  scale_rows_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(A.p, ncol, nrow, d->n_dof, wdir, 0.5); RTE_NOTE_LAUNCH();
+  RTE_TRY(jacobi_columns_device(A.p, nrow, ncol, st));
+  col_norms_kernel<<<ncol, 256, 0, st>>>(A.p, nrow, nrmd.p); RTE_NOTE_LAUNCH();
+  RTE_CUDA_TRY(cudaGetLastError());
+  std::vector<double> nrm(ncol);
+  RTE_CUDA_TRY(cudaMemcpyAsync(nrm.data(), nrmd.p, sizeof(double) * ncol, cudaMemcpyDeviceToHost, st));
+  RTE_CUDA_TRY(cudaStreamSynchronize(st));
+  std::vector<int> idx(ncol);
+  for (int i = 0; i < ncol; ++i) idx[i] = i;
+  std::sort(idx.begin(), idx.end(), [&](int x, int y) { return nrm[x] > nrm[y]; });
+  rom->sv.resize(ncol);
+  for (int i = 0; i < ncol; ++i) rom->sv[i] = nrm[idx[i]];
+  pod_rank_of(rom, ncol, rank, eps_pod);
+  const int r = rom->r;
+  RTE_TRY(idxd.alloc(r));
+  RTE_TRY(svd.alloc(r));
+  RTE_CUDA_TRY(cudaMemcpyAsync(idxd.p, idx.data(), sizeof(int) * r, cudaMemcpyHostToDevice, st));
+  RTE_CUDA_TRY(cudaMemcpyAsync(svd.p, rom->sv.data(), sizeof(double) * r, cudaMemcpyHostToDevice, st));
+  RTE_TRY(rom->U.alloc((size_t)r * nrow));
+  take_cols_kernel<<<(unsigned)(((size_t)r * nrow + 255) / 256), 256, 0, st>>>(
+      A.p, idxd.p, svd.p, r, nrow, d->n_dof, wdir, rom->U.p); RTE_NOTE_LAUNCH();
+  RTE_CUDA_TRY(cudaGetLastError());
+  RTE_CUDA_TRY(cudaStreamSynchronize(st));
+  return RTE_OK;
+}
+
 // POD of X [ncol][nrow] (columns contiguous): fills rom->U [r][nrow], sv, r, eps_equiv.
 // Thin SVD X = Q R = (Q U_R) Sigma V^T: Q from classical Gram-Schmidt applied twice per column on
 // the GPU (inner products weighted by direction multiplicity), then a one-sided Jacobi SVD of the
-// small R on the host.  Unlike an eigen-decomposition of X^T X this resolves singular values down
-// to a few ulps of sigma_1, which truncation tolerances like eps_POD = 1e-9 need.
+// small R.  Unlike an eigen-decomposition of X^T X this resolves singular values down to a few
+// ulps of sigma_1, which truncation tolerances like eps_POD = 1e-9 need.  Snapshot sets with more
+// than 256 columns and at most 4e8 entries go through pod_direct instead: orthogonalising many
+// nearly dependent snapshots one by one loses the small singular values.
 static int pod(rte_rom_t rom, const double* X, int ncol, size_t nrow, int rank, double eps_pod,
                const double* wdir, cudaStream_t st) {
   const rte_disc_s* d = rom->disc;
   if (ncol < 1) return fail(RTE_EINVAL, "ROM: no snapshots");
-  if (ncol > 1024) return fail(RTE_EINVAL, "ROM: at most 1024 snapshots per basis");
+  if (ncol > 4096) return fail(RTE_EINVAL, "ROM: at most 4096 snapshots per basis");
+  if (ncol > 256 && (double)ncol * nrow <= 4e8) return pod_direct(rom, X, ncol, nrow, rank, eps_pod, wdir, st);
   DevBuf<double> Q, hdev;
   RTE_TRY(Q.alloc((size_t)ncol * nrow));
   RTE_TRY(hdev.alloc(ncol));
@@ -470,30 +754,10 @@ static int pod(rte_rom_t rom, const double* X, int ncol, size_t nrow, int rank, 
     RTE_CUDA_TRY(cudaGetLastError());
   }
   std::vector<double> UR;
-  jacobi_svd(R, ncol, rom->sv, UR);
-  double total = 0.0;
-  for (double v : rom->sv) total += v;
-  int r = rank;
-  if (r <= 0) {  // Eq. (pod_truncation): smallest l with sum_{k<=l} s_k / trace >= 1 - eps
-    double acc = 0.0;
-    r = ncol;
-    for (int i = 0; i < ncol; ++i) {
-      acc += rom->sv[i];
-      if (acc / total >= 1.0 - eps_pod) {
-        r = i + 1;
-        break;
-      }
-    }
-  }
-  int nz = 0;
-  for (int i = 0; i < ncol; ++i) nz += rom->sv[i] > 1e-14 * rom->sv[0];
-  r = std::min(r, std::max(nz, 1));
-  r = std::min(r, ncol);
-  rom->r = r;
-  rom->n_snap = ncol;
-  double kept = 0.0;
-  for (int i = 0; i < r; ++i) kept += rom->sv[i];
-  rom->eps_equiv = total > 0 ? 1.0 - kept / total : 0.0;
+  if (ncol <= 256) jacobi_svd(R, ncol, rom->sv, UR);
+  else RTE_TRY(jacobi_svd_device(R, ncol, rom->sv, UR, st));
+  pod_rank_of(rom, ncol, rank, eps_pod);
+  const int r = rom->r;
   // U = Q U_R[:, :r]
   std::vector<double> W((size_t)ncol * r);
   for (int k = 0; k < ncol; ++k)
@@ -519,6 +783,10 @@ static int reduce_operators(rte_rom_t rom, cudaStream_t st) {
   RTE_TRY(rom->U_iso0.alloc((size_t)r * d->n_cells));
   iso0_kernel<<<(unsigned)(((size_t)r * d->n_cells + 255) / 256), 256, 0, st>>>(
       rom->U_iso.p, r, d->n_cells, d->P, rom->U_iso0.p); RTE_NOTE_LAUNCH();
+  RTE_TRY(rom->a_side.alloc((size_t)4 * r));
+  inflow_basis_kernel<<<(4 * r + 127) / 128, 128, 0, st>>>(
+      rom->U.p, r, d->n_dirs, d->dim, d->nx, d->ny, d->n_dof, d->hx, d->hy,
+      d->dim == 1 ? d->dx_dev.p : nullptr, d->dir_dev.p, rom->a_side.p); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   // multiplicity per direction as the row weight
   std::vector<double> mult(d->n_dirs);
@@ -534,7 +802,7 @@ static int reduce_operators(rte_rom_t rom, cudaStream_t st) {
   } else {
     const size_t tot = (size_t)r * d->n_dirs * d->nx;
     transport_apply1d_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
-        rom->U.p, r, d->n_dirs, d->nx, d->hx, d->dir_dev.p, Y.p); RTE_NOTE_LAUNCH();
+        rom->U.p, r, d->n_dirs, d->nx, d->dx_dev.p, d->dir_dev.p, Y.p); RTE_NOTE_LAUNCH();
   }
   RTE_CUDA_TRY(cudaGetLastError());
   std::vector<double> A0, Aa, C;
@@ -577,8 +845,8 @@ int rom_prepare(rte_rom_t rom, rte_batch_t bt, cudaStream_t st, const uint8_t* m
   return RTE_OK;
 }
 
-// ROMIG (Sec. 3.1.2): with vacuum inflow U^T b = (U^iso)^T G and G has only its zeroth moment per
-// cell, so the projection reads the k = 0 rows of U^iso, kept contiguous as U_iso0 [r][n_cells].
+// ROMIG (Sec. 3.1.2): U^T b = (U^iso)^T G + sum_s g_s a_side[s]; G has only its zeroth moment per
+// cell, so its projection reads the k = 0 rows of U^iso, kept contiguous as U_iso0 [r][n_cells].
 int rom_guess_launch(rte_rom_t rom, rte_batch_t b, double* rho0, const uint8_t* mask,
                      cudaStream_t st) {
   RTE_TRY(rom_prepare(rom, b, st, mask));
@@ -586,6 +854,8 @@ int rom_guess_launch(rte_rom_t rom, rte_batch_t b, double* rho0, const uint8_t* 
   RomOnline* o = rom->online;
   project_kernel<<<dim3(r, B), 256, 0, st>>>(rom->U_iso0.p, nc, b->G0.p, 1, 0, (size_t)nc,
                                              o->proj.p, r, mask); RTE_NOTE_LAUNCH();
+  add_inflow_rhs_kernel<<<(B * r + 127) / 128, 128, 0, st>>>(o->proj.p, b->inflow.p, rom->a_side.p, r,
+                                                             B, mask); RTE_NOTE_LAUNCH();
   lu_solve_kernel<<<(B + 63) / 64, 64, 0, st>>>(o->lu.p, o->piv.p, o->proj.p, r, B, mask); RTE_NOTE_LAUNCH();
   lift_kernel<<<dim3(std::min((n + 255) / 256, 1024), B), 256, 0, st>>>(rom->U_rho.p, n, o->proj.p, r,
                                                                         rho0, mask); RTE_NOTE_LAUNCH();
@@ -623,9 +893,6 @@ extern "C" int rte_rom_build(rte_batch_t train, const rte_rom_opts* opts, rte_ro
   if ((opts->rank_p <= 0 || opts->rank_c <= 0) && !(opts->eps_pod > 0 && opts->eps_pod < 1))
     return fail(RTE_EINVAL, "rte_rom_build: need a rank or 0 < eps_pod < 1");
   const bool romig_start = opts->correction_start == 1 && rom_c != nullptr;
-  if (romig_start)
-    for (double g : train->inflow_h)
-      if (g != 0.0) return fail(RTE_EINVAL, "ROMIG-started training needs vacuum inflow");
   if (rom_p) *rom_p = nullptr;
   if (rom_c) *rom_c = nullptr;
   rte_disc_s* d = train->disc;
@@ -728,8 +995,6 @@ extern "C" int rte_rom_initial_guess(rte_rom_t rom, rte_batch_t b, double* rho0,
   if (!rom || !b || !rho0) return fail(RTE_EINVAL, "rte_rom_initial_guess: null argument");
   if (!b->params_set) return fail(RTE_ESTATE, "parameters not set");
   if (rom->disc != b->disc) return fail(RTE_EINVAL, "ROM built on another discretisation");
-  for (double g : b->inflow_h)
-    if (g != 0.0) return fail(RTE_EINVAL, "ROMIG supports vacuum inflow only (U^T b = (U^iso)^T G)");
   DeviceGuard g(b->disc->device);
   cudaStream_t st = (cudaStream_t)stream;
   PhaseScope ps(b, 2, st);
@@ -750,11 +1015,12 @@ extern "C" int rte_romsa_correction(rte_rom_t rom, rte_batch_t b, const double* 
 }
 
 // ---- persistence of the online part of a ROM ------------------------------------------------
-// File layout (little-endian): magic "RTEROM01", int32 header {dim, nx, ny, n_phi, n_vz, n_mat,
+// File layout (little-endian): magic "RTEROM02", int32 header {dim, nx, ny, n_phi, n_vz, n_mat,
 // r, n_snap, n_cells, P}, double {x0, x1, y0, y1, eps_equiv}, int32 mat_id[n_cells],
-// double sv[n_snap], A0[r][r], Aa[n_mat][r][r], As[n_mat][r][r], U_rho[r][n_dof], U_iso[r][n_dof].
+// double dx[nx] (1D only), sv[n_snap], A0[r][r], Aa[n_mat][r][r], As[n_mat][r][r],
+// a_side[4][r], U_rho[r][n_dof], U_iso[r][n_dof].
 namespace {
-const char kRomMagic[8] = {'R', 'T', 'E', 'R', 'O', 'M', '0', '1'};
+const char kRomMagic[8] = {'R', 'T', 'E', 'R', 'O', 'M', '0', '2'};
 
 struct FileCloser {
   FILE* f;
@@ -770,9 +1036,10 @@ extern "C" int rte_rom_save(rte_rom_t rom, const char* path) {
   DeviceGuard g(d->device);
   const int r = rom->r;
   const size_t n = (size_t)r * d->n_dof;
-  std::vector<double> urho(n), uiso(n);
+  std::vector<double> urho(n), uiso(n), aside((size_t)4 * r);
   RTE_CUDA_TRY(cudaMemcpy(urho.data(), rom->U_rho.p, 8 * n, cudaMemcpyDeviceToHost));
   RTE_CUDA_TRY(cudaMemcpy(uiso.data(), rom->U_iso.p, 8 * n, cudaMemcpyDeviceToHost));
+  RTE_CUDA_TRY(cudaMemcpy(aside.data(), rom->a_side.p, 8 * aside.size(), cudaMemcpyDeviceToHost));
   FileCloser fc{fopen(path, "wb")};
   if (!fc.f) return fail(RTE_EINVAL, std::string("rte_rom_save: cannot open ") + path);
   const int32_t hdr[10] = {d->dim, d->nx, d->ny, d->n_phi, d->n_vz, d->n_mat, r, rom->n_snap,
@@ -781,10 +1048,12 @@ extern "C" int rte_rom_save(rte_rom_t rom, const char* path) {
   bool ok = fwrite(kRomMagic, 1, 8, fc.f) == 8 && fwrite(hdr, 4, 10, fc.f) == 10 &&
             fwrite(geo, 8, 5, fc.f) == 5 &&
             fwrite(d->mat_host.data(), 4, d->n_cells, fc.f) == (size_t)d->n_cells &&
+            (d->dim != 1 || fwrite(d->dx.data(), 8, d->dx.size(), fc.f) == d->dx.size()) &&
             fwrite(rom->sv.data(), 8, rom->sv.size(), fc.f) == rom->sv.size() &&
             fwrite(rom->A0.data(), 8, rom->A0.size(), fc.f) == rom->A0.size() &&
             fwrite(rom->Aa.data(), 8, rom->Aa.size(), fc.f) == rom->Aa.size() &&
             fwrite(rom->As.data(), 8, rom->As.size(), fc.f) == rom->As.size() &&
+            fwrite(aside.data(), 8, aside.size(), fc.f) == aside.size() &&
             fwrite(urho.data(), 8, n, fc.f) == n && fwrite(uiso.data(), 8, n, fc.f) == n;
   if (!ok) return fail(RTE_EINVAL, std::string("rte_rom_save: write failed: ") + path);
   return RTE_OK;
@@ -812,6 +1081,11 @@ extern "C" int rte_rom_load(rte_disc_t disc, const char* path, rte_rom_t* out) {
   std::vector<int32_t> mat(d->n_cells);
   if (fread(mat.data(), 4, mat.size(), fc.f) != mat.size() || mat != d->mat_host)
     return fail(RTE_EINVAL, "rte_rom_load: the file was built on another material map");
+  if (d->dim == 1) {
+    std::vector<double> dxf(d->nx);
+    if (fread(dxf.data(), 8, dxf.size(), fc.f) != dxf.size() || dxf != d->dx)
+      return fail(RTE_EINVAL, "rte_rom_load: the file was built on another mesh");
+  }
   auto* rom = new rte_rom_s();
   rom->disc = disc;
   rom->r = r;
@@ -822,11 +1096,12 @@ extern "C" int rte_rom_load(rte_disc_t disc, const char* path, rte_rom_t* out) {
   rom->Aa.resize((size_t)d->n_mat * r * r);
   rom->As.resize((size_t)d->n_mat * r * r);
   const size_t n = (size_t)r * d->n_dof;
-  std::vector<double> urho(n), uiso(n);
+  std::vector<double> urho(n), uiso(n), aside((size_t)4 * r);
   bool ok = fread(rom->sv.data(), 8, rom->sv.size(), fc.f) == rom->sv.size() &&
             fread(rom->A0.data(), 8, rom->A0.size(), fc.f) == rom->A0.size() &&
             fread(rom->Aa.data(), 8, rom->Aa.size(), fc.f) == rom->Aa.size() &&
             fread(rom->As.data(), 8, rom->As.size(), fc.f) == rom->As.size() &&
+            fread(aside.data(), 8, aside.size(), fc.f) == aside.size() &&
             fread(urho.data(), 8, n, fc.f) == n && fread(uiso.data(), 8, n, fc.f) == n;
   if (!ok) {
     delete rom;
@@ -845,6 +1120,7 @@ extern "C" int rte_rom_load(rte_disc_t disc, const char* path, rte_rom_t* out) {
   up(rom->A0_dev, rom->A0);
   up(rom->Aa_dev, rom->Aa);
   up(rom->As_dev, rom->As);
+  up(rom->a_side, aside);
   if (e == RTE_OK) e = rom->U_iso0.alloc((size_t)r * d->n_cells);
   if (e == RTE_OK) {
     iso0_kernel<<<(unsigned)(((size_t)r * d->n_cells + 255) / 256), 256>>>(rom->U_iso.p, r, d->n_cells,

@@ -361,11 +361,8 @@ extern "C" int rte_server_submit(rte_server_t sv, int bucket, const double* sigm
       return fail(RTE_EINVAL, "need finite sigma_t > 0 and 0 <= sigma_s <= sigma_t");
   for (int c = 0; c < nc; ++c)
     if (!std::isfinite(source[c])) return fail(RTE_EINVAL, "source is not finite");
-  for (int k = 0; k < ni; ++k) {
+  for (int k = 0; k < ni; ++k)
     if (!std::isfinite(inflow[k])) return fail(RTE_EINVAL, "inflow is not finite");
-    if (K.rom_p && inflow[k] != 0.0)
-      return fail(RTE_EINVAL, "a bucket with a ROM initial guess takes vacuum inflow only");
-  }
   auto* r = new Request();
   r->bucket = bucket;
   r->sigma_t.assign(sigma_t, sigma_t + nm);

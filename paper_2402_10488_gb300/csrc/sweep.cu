@@ -109,27 +109,32 @@ __global__ void tables2d_kernel(double* tables, const double* sigma_t, const dou
     }
 }
 
+// One thread per (instance, cell, direction), 1D: M = sigma_t I + (|xi|/h) [[1, s sqrt3],
+// [-s sqrt3, 3]] (s the sign of xi, h the cell's width) and the inflow coupling: a unit face value
+// u entering the cell contributes |xi| u phi_k(inflow face) = (|xi| / sqrt h) (1, -s sqrt3) to the
+// right-hand side.  T = {M^-1 (2x2), M^-1 (|xi| / sqrt h)(1, -s sqrt3), 1 / sqrt h}.
 __global__ void tables1d_kernel(double* tables, const double* sigma_t, const double* dirs, int B,
-                                int n_mat, int n_dirs, double h, const uint8_t* mask) {
+                                int n_mat, int n_cells, int n_dirs, const int32_t* mat,
+                                const double* dx, const uint8_t* mask) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= B * n_mat * n_dirs) return;
+  if (idx >= B * n_cells * n_dirs) return;
   const int d = idx % n_dirs;
-  const int m = (idx / n_dirs) % n_mat;
-  const int b = idx / (n_dirs * n_mat);
+  const int c = (idx / n_dirs) % n_cells;
+  const int b = idx / (n_dirs * n_cells);
   if (mask && !mask[b]) return;
-  const double st = sigma_t[b * n_mat + m];
-  const double xi = dirs[4 * d];
+  const double st = sigma_t[b * n_mat + mat[c]];
+  const double xi = dirs[4 * d], h = dx[c];
   const double s3 = sqrt(3.0), sg = xi < 0 ? -1.0 : 1.0, a = fabs(xi) / h;
-  // M = st I + a [[1, sg s3], [-sg s3, 3]]
   const double m00 = st + a, m01 = a * sg * s3, m10 = -a * sg * s3, m11 = st + 3.0 * a;
   const double det = m00 * m11 - m01 * m10;
   const double i00 = m11 / det, i01 = -m01 / det, i10 = -m10 / det, i11 = m00 / det;
+  const double q = 1.0 / sqrt(h), e0 = fabs(xi) * q, e1 = -sg * s3 * fabs(xi) * q;
   double* T = tables + (size_t)idx * kTab1D;
   T[0] = i00, T[1] = i01, T[2] = i10, T[3] = i11;
-  // inflow coupling E = a (1, -sg s3)
-  T[4] = i00 * a + i01 * (-sg * s3 * a);
-  T[5] = i10 * a + i11 * (-sg * s3 * a);
-  T[6] = T[7] = 0.0;
+  T[4] = i00 * e0 + i01 * e1;
+  T[5] = i10 * e0 + i11 * e1;
+  T[6] = q;
+  T[7] = 0.0;
 }
 
 struct Sweep2DArgs {
@@ -444,10 +449,11 @@ struct Sweep1DArgs {
   const int32_t* mat;
   const double* dirs;
   int B, nx, n_dof, n_mat, n_dirs, with_source;
-  double sq_h;
 };
 
 // 1D slab: one thread per (instance, direction), sequential in upwind order (2x2 cell solves).
+// The carried quantity is the angular flux's value u at the face between two cells (the inflow
+// value g at the boundary); per-cell tables hold the cell width's effect.
 __global__ void sweep1d_kernel(const Sweep1DArgs A) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= A.B * A.n_dirs) return;
@@ -456,7 +462,7 @@ __global__ void sweep1d_kernel(const Sweep1DArgs A) {
   const double xi = A.dirs[4 * d], w = A.dirs[4 * d + 2];
   const bool neg = xi < 0;
   const double c3 = neg ? -sqrt(3.0) : sqrt(3.0);
-  double t = A.with_source ? A.inflow[4 * b + (neg ? 1 : 0)] * A.sq_h : 0.0;
+  double u = A.with_source ? A.inflow[4 * b + (neg ? 1 : 0)] : 0.0;
   const double* rin = A.rho_in + (size_t)b * A.n_dof;
   int rank = b;
   if (A.active) {
@@ -465,17 +471,17 @@ __global__ void sweep1d_kernel(const Sweep1DArgs A) {
   }
   double* part = A.partial + ((size_t)rank * A.n_dirs + d) * A.n_dof;
   double* psi = A.psi_out ? A.psi_out + ((size_t)b * A.n_dirs + d) * A.n_dof : nullptr;
-  const double* tab = A.tables + (size_t)b * A.n_mat * A.n_dirs * kTab1D;
+  const double* tab = A.tables + (size_t)b * A.nx * A.n_dirs * kTab1D;
   for (int step = 0; step < A.nx; ++step) {
     const int c = neg ? A.nx - 1 - step : step;
     const int m = A.mat[c];
-    const double* T = tab + ((size_t)m * A.n_dirs + d) * kTab1D;
+    const double* T = tab + ((size_t)c * A.n_dirs + d) * kTab1D;
     const double ss = A.sigma_s[(size_t)b * A.n_mat + m];
     const double s0 = fma(ss, rin[2 * c], A.with_source ? A.G0[(size_t)b * A.nx + c] : 0.0);
     const double s1 = ss * rin[2 * c + 1];
-    const double a0 = fma(T[4], t, fma(T[1], s1, T[0] * s0));
-    const double a1 = fma(T[5], t, fma(T[3], s1, T[2] * s0));
-    t = fma(c3, a1, a0);
+    const double a0 = fma(T[4], u, fma(T[1], s1, T[0] * s0));
+    const double a1 = fma(T[5], u, fma(T[3], s1, T[2] * s0));
+    u = fma(c3, a1, a0) * T[6];
     part[2 * c] = w * a0;
     part[2 * c + 1] = w * a1;
     if (psi) psi[2 * c] = a0, psi[2 * c + 1] = a1;
@@ -588,8 +594,10 @@ int setup_tables(rte_batch_t bt, cudaStream_t st, const uint8_t* mask) {
     tables2d_kernel<<<bl, th, 0, st>>>(bt->tables.p, bt->sigma_t.p, d->dir_dev.p, bt->B, d->n_mat,
                                        d->n_dirs, d->hx, d->hy, mask); RTE_NOTE_LAUNCH();
   } else {
-    tables1d_kernel<<<bl, th, 0, st>>>(bt->tables.p, bt->sigma_t.p, d->dir_dev.p, bt->B, d->n_mat,
-                                       d->n_dirs, d->hx, mask); RTE_NOTE_LAUNCH();
+    const int n1 = bt->B * d->n_cells * d->n_dirs;
+    tables1d_kernel<<<(n1 + th - 1) / th, th, 0, st>>>(bt->tables.p, bt->sigma_t.p, d->dir_dev.p,
+                                                       bt->B, d->n_mat, d->n_cells, d->n_dirs,
+                                                       d->mat_id.p, d->dx_dev.p, mask); RTE_NOTE_LAUNCH();
   }
   RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;
@@ -705,7 +713,7 @@ int sweep_launch(rte_batch_t bt, const double* rho_in, double* rho_out, double* 
   } else {
     Sweep1DArgs A{rho_in,      bt->partial.p, psi_out,  active, bt->tables.p, bt->sigma_s.p,
                   bt->G0.p,    bt->inflow.p,  d->mat_id.p, d->dir_dev.p, bt->B, d->nx,
-                  d->n_dof,    d->n_mat,      d->n_dirs, with_source, std::sqrt(d->hx)};
+                  d->n_dof,    d->n_mat,      d->n_dirs, with_source};
     const int n = bt->B * d->n_dirs;
     sweep1d_kernel<<<(n + 63) / 64, 64, 0, st>>>(A); RTE_NOTE_LAUNCH();
     RTE_CUDA_TRY(cudaGetLastError());
@@ -821,7 +829,7 @@ int sweep_launch_with_scratch(rte_batch_t bt, const double* rho_in, double* rho_
   } else {
     Sweep1DArgs A{rho_in,      partial,       nullptr,  nullptr, bt->tables.p, bt->sigma_s.p,
                   bt->G0.p,    bt->inflow.p,  d->mat_id.p, d->dir_dev.p, bt->B, d->nx,
-                  d->n_dof,    d->n_mat,      d->n_dirs, with_source, std::sqrt(d->hx)};
+                  d->n_dof,    d->n_mat,      d->n_dirs, with_source};
     const int n = bt->B * d->n_dirs;
     sweep1d_kernel<<<(n + 63) / 64, 64, 0, st>>>(A); RTE_NOTE_LAUNCH();
     RTE_CUDA_TRY(cudaGetLastError());

@@ -48,6 +48,7 @@ class Problem:
     inflow: np.ndarray            # float64 [B, 2*dim], isotropic inflow per side
     params: np.ndarray = field(default=None)  # float64 [B, p], the mu that made each instance
     name: str = ""
+    edges: np.ndarray = field(default=None)   # 1D only: cell edges x_0 < ... < x_N (None: uniform)
 
     # ---- sizes -------------------------------------------------------------------------
     @property
@@ -336,3 +337,80 @@ def cross_regime_train():
 
 def cross_regime_test(n_test: int = 20, seed: int = TEST_SEED0):
     return np.random.default_rng(seed).uniform(10.0, 20.0, n_test)
+
+
+
+# ---- the paper's 1D two-material problem (Sec. 4.1.2) -----------------------------------------
+
+def two_material_edges():
+    """Non-uniform mesh of Sec. 4.1.2: width 1/100 on [0,1], 1/10 on [1,11] (200 cells)."""
+    return np.concatenate([np.arange(101) / 100.0, 1.0 + np.arange(1, 101) / 10.0])
+
+
+def two_material(mu, n_angles: int = 16) -> Problem:
+    """Sec. 4.1.2: slab [0,11]; on [0,1] sigma_a = mu_a, sigma_s = 0; on [1,11] sigma_a = 0,
+    sigma_s = mu_s; G = 0; isotropic inflow 5 at x = 0 and 0 at x = 11; S_16."""
+    mu = np.atleast_2d(np.asarray(mu, dtype=np.float64))   # rows (mu_a, mu_s)
+    B = mu.shape[0]
+    edges = two_material_edges()
+    n = edges.size - 1
+    mat = (edges[:-1] >= 1.0 - 1e-12).astype(np.int32)       # 0 absorber, 1 scatterer
+    sigma_s = np.stack([np.zeros(B), mu[:, 1]], 1)
+    sigma_t = sigma_s + np.stack([mu[:, 0], np.zeros(B)], 1)
+    inflow = np.tile(np.array([5.0, 0.0]), (B, 1))
+    return Problem(1, n, 1, (0.0, 11.0), "gl", n_angles, 0, mat, sigma_t, sigma_s,
+                   np.zeros((B, n)), inflow, mu.copy(), f"two_material{n}_S{n_angles}", edges)
+
+
+def two_material_train():
+    """451 training pairs (mu_a, mu_s) = (0.5 + 0.1 m, 10 + n), m = 0..10, n = 0..40."""
+    return np.array([(0.5 + 0.1 * m, 10.0 + k) for m in range(11) for k in range(41)])
+
+
+def two_material_test(n_test: int = 20, seed: int = TEST_SEED0):
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.uniform(0.5, 1.5, n_test), rng.uniform(10.0, 50.0, n_test)], 1)
+
+
+# ---- the paper's variable-scattering problem (Sec. 4.2.4) -----------------------------------
+
+def variable_scattering_map(n: int = 80, levels: int = 64):
+    """Material map and level values for sigma_s = mu_s f(x, y) + 0.1 on [-1,1]^2 with
+    f = r^4 (2 - r^2)^2 for r <= 1 and 1 outside: f is averaged over each cell (4x4 Gauss rule) and
+    the cell averages are grouped into `levels` equal-width bins of [0, 1] (f = 1 exactly, i.e.
+    cells entirely outside the unit disc, gets a material of its own); each bin is a material whose
+    f is the mean of its cells' averages."""
+    dom = (-1.0, 1.0, -1.0, 1.0)
+
+    def f(x, y):
+        r2 = x * x + y * y
+        return np.where(r2 <= 1.0, r2 * r2 * (2.0 - r2) ** 2, 1.0)
+
+    avg = cell_average(f, n, n, dom)
+    raw = np.where(avg >= 1.0 - 1e-15, levels, np.minimum((avg * levels).astype(int), levels - 1))
+    used = np.unique(raw)
+    mat = np.searchsorted(used, raw).astype(np.int32)
+    fval = np.array([avg[raw == u].mean() for u in used])
+    return mat, fval
+
+
+def variable_scattering(mu_s, n: int = 80, n_phi: int = 30, n_vz: int = 6, levels: int = 64) -> Problem:
+    """Sec. 4.2.4: [-1,1]^2, zero inflow, sigma_a = 0, sigma_s = mu_s f + 0.1 (levels of f as in
+    variable_scattering_map), G = (10 / pi) exp(-100 (x^2 + y^2)) (cell averages)."""
+    mu_s = np.atleast_1d(np.asarray(mu_s, dtype=np.float64))
+    B = mu_s.size
+    dom = (-1.0, 1.0, -1.0, 1.0)
+    mat, fval = variable_scattering_map(n, levels)
+    sig = mu_s[:, None] * fval[None, :] + 0.1
+    G = cell_average(lambda x, y: 10.0 / np.pi * np.exp(-100.0 * (x ** 2 + y ** 2)), n, n, dom)
+    return Problem(2, n, n, dom, "cl", n_phi, n_vz, mat, sig.copy(), sig.copy(), np.tile(G, (B, 1)),
+                   np.zeros((B, 4)), mu_s[:, None].copy(), f"variable_scattering{n}_CL({n_phi},{n_vz})")
+
+
+def variable_scattering_train():
+    """50 training values uniformly spread over [49.9, 99.9] (Sec. 4.2.4)."""
+    return np.linspace(49.9, 99.9, 50)
+
+
+def variable_scattering_test(n_test: int = 10, seed: int = TEST_SEED0):
+    return np.random.default_rng(seed).uniform(49.9, 99.9, n_test)

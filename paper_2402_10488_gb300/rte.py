@@ -107,7 +107,8 @@ def check(status, allow=()):
 
 class _DiscDesc(ctypes.Structure):
     _fields_ = [("dim", _I), ("nx", _I), ("ny", _I), ("x0", _D), ("x1", _D), ("y0", _D),
-                ("y1", _D), ("n_phi", _I), ("n_vz", _I), ("n_mat", _I), ("mat_id", _P)]
+                ("y1", _D), ("n_phi", _I), ("n_vz", _I), ("n_mat", _I), ("mat_id", _P),
+                ("dx", _P)]
 
 
 class _RomOpts(ctypes.Structure):
@@ -180,9 +181,12 @@ class Disc:
         L = lib()
         self._mat = _host(problem.mat_id, np.int32)
         dom = tuple(problem.domain) + ((0.0, 1.0) if problem.dim == 1 else ())
+        edges = getattr(problem, "edges", None)
+        self._dx = None if edges is None or problem.dim != 1 else _host(np.diff(edges))
         d = _DiscDesc(problem.dim, problem.nx, problem.ny, dom[0], dom[1], dom[2], dom[3],
                       problem.n_phi, problem.n_vz, problem.n_mat,
-                      self._mat.ctypes.data_as(_P))
+                      self._mat.ctypes.data_as(_P),
+                      None if self._dx is None else self._dx.ctypes.data_as(_P))
         h = _P()
         check(L.rte_disc_create(ctypes.byref(d), device, ctypes.byref(h)))
         self.h = h

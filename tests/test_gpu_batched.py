@@ -232,8 +232,8 @@ def test_server_rejects_bad_requests(served):
     srv.start()
     with pytest.raises(rte.RTEError):  # sigma_s > sigma_t
         srv.submit(0, p.sigma_t[0], p.sigma_t[0] * 2, p.source[0], p.inflow[0], 1e-6)
-    with pytest.raises(rte.RTEError):  # ROMIG bucket takes vacuum inflow only
-        srv.submit(0, p.sigma_t[0], p.sigma_s[0], p.source[0], np.ones(4), 1e-6)
+    with pytest.raises(rte.RTEError):  # inflow must be finite
+        srv.submit(0, p.sigma_t[0], p.sigma_s[0], p.source[0], np.full(4, np.nan), 1e-6)
     with pytest.raises(rte.RTEError):
         srv.submit(5, p.sigma_t[0], p.sigma_s[0], p.source[0], p.inflow[0], 1e-6)
     t = srv.submit(0, p.sigma_t[0], p.sigma_s[0], p.source[0], p.inflow[0], 1e-6)

@@ -57,3 +57,18 @@ def test_cross_regime_rom_and_solves_match_oracle():
             ref = sisa(tr, np.zeros(tr.n_dof), 1e-11, 2000, name, dsa=ConsistentDSA(tr),
                        rom_c=off.rom_c, theta=3, eps_romsad=romsad_eps(1e-11, off.eps_pod))
             assert abs(reps[b]["n_sweep"] - ref["n_sweep"]) <= 1
+
+
+def test_device_jacobi_svd_for_many_snapshots():
+    """More than 256 correction snapshots (90 training slopes, window 3): the small factor R of
+    the device QR is decomposed by the parallel one-sided Jacobi SVD on the GPU; singular values
+    and the eps_POD truncation rank as numpy's SVD."""
+    rte = _rte()
+    train = inputs.cross_regime(10.0 + np.arange(90) / 9.0, n=100)
+    tb = rte.Batch.from_problem(train)
+    rp, rc = rte.Rom.build(tb, eps_train=1e-11, window=3, rank_p=0, rank_c=0, eps_pod=1e-10,
+                           max_iter=2000, dsa_rtol=1e-10)
+    off = OfflineROMs(train, eps_train=1e-11, window=3, eps_pod=1e-10)
+    assert rc.n_snap == off.dF.shape[1] > 256
+    np.testing.assert_allclose(rc.sv, off.pod_c.sv[:rc.n_snap], atol=1e-10 * off.pod_c.sv[0])
+    assert abs(rc.r - off.pod_c.r) <= 1

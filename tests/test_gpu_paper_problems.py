@@ -1,8 +1,9 @@
 """The paper's own 2D test problems on the GPU at reduced size, against the oracle: the
 homogeneous medium of Sec. 4.2.1 (sigma_a = 0 everywhere: a pure scatterer, so only leakage
-makes the DSA system nonsingular) and the pin cell of Sec. 4.2.3 (sigma_s jumps from <= 0.5 to
-100 across the pin boundary, sigma_a = 0 outside), plus the CL(30,6) rule those problems use
-(it has directions with v_x = cos(pi/2), i.e. zero to rounding).
+makes the DSA system nonsingular), the pin cell of Sec. 4.2.3 (sigma_s jumps from <= 0.5 to
+100 across the pin boundary, sigma_a = 0 outside) and the variable-scattering problem of
+Sec. 4.2.4 (sigma_s levels as materials), plus the CL(30,6) rule those problems use (it has
+directions with v_x = cos(pi/2), i.e. zero to rounding).
 
 Tolerances: single sweeps 1e-12 relative (as the sweep parity tests); SI-DSA stopped at an
 absolute change of 1e-12 with a tight DSA lies within ~1e-11 of the fixed point, hence 1e-9
@@ -45,13 +46,15 @@ def test_cl_30_6_sweep_matches_oracle():
         assert _rel(out.cpu().numpy()[b], ref) < 1e-12
 
 
-@pytest.mark.parametrize("case", ["homogeneous", "pin_cell"])
+@pytest.mark.parametrize("case", ["homogeneous", "pin_cell", "variable_scattering"])
 def test_si_dsa_converges_to_the_direct_solution(case):
     rte = _rte()
     if case == "homogeneous":
         p = inputs.homogeneous_medium(inputs.homogeneous_test(2), n=10, n_phi=8, n_vz=2)
-    else:
+    elif case == "pin_cell":
         p = inputs.pin_cell(inputs.pin_cell_test(2), n=12, n_phi=8, n_vz=2)
+    else:  # sigma_s levels as materials (many materials, pure scatterer with sigma_s >= 0.1)
+        p = inputs.variable_scattering(inputs.variable_scattering_test(2), n=12, n_phi=8, n_vz=2)
     batch = rte.Batch.from_problem(p)
     rho = torch.zeros((2, p.n_dof), dtype=torch.float64, device="cuda")
     reps, _, st = batch.solve(rho, 1e-12, sa=rte.SA_DSA, max_iter=500, dsa_rtol=1e-12,
