@@ -114,9 +114,19 @@ class DG1D:
                           shape=(self.n_dof, self.n_dof))
         return A.tocsr()
 
-    def mass_matrix(self, sigma_cell) -> sp.csr_matrix:
-        """int sigma phi_k phi_l with cellwise-constant sigma (Sigma_t, Sigma_s)."""
-        blocks = [sp.csr_matrix(float(sigma_cell[c]) * self._mass(c)) for c in range(self.n_cells)]
+    def mass_matrix(self, sigma_cell, sigma_right=None) -> sp.csr_matrix:
+        """int sigma phi_k phi_l (Sigma_t, Sigma_s).  sigma cellwise constant, or -- with
+        sigma_right -- linear on every cell from sigma_cell[c] at its left end to sigma_right[c] at
+        its right end (the paper's cross-regime problem has sigma_s linear in x, Sec. 4.1.1)."""
+        if sigma_right is None:
+            blocks = [sp.csr_matrix(float(sigma_cell[c]) * self._mass(c)) for c in range(self.n_cells)]
+            return sp.csr_matrix(sp.block_diag(blocks, format="csr"))
+        blocks = []
+        for c in range(self.n_cells):
+            h = self.h[c]
+            vals, _ = basis_1d(h, _GX)
+            sig = float(sigma_cell[c]) * 0.5 * (1.0 - _GX) + float(sigma_right[c]) * 0.5 * (1.0 + _GX)
+            blocks.append(sp.csr_matrix((h / 2.0) * np.einsum("q,q,qk,ql->kl", _GW, sig, vals, vals)))
         return sp.csr_matrix(sp.block_diag(blocks, format="csr"))
 
     def source_vector(self, G_cell) -> np.ndarray:

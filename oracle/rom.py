@@ -5,11 +5,13 @@
   read literally with singular values: the smallest l with sum_{k<=l} lambda_k / trace >= 1 - eps;
   or a fixed rank.
 * Galerkin ROM (Eq. (rom_parametric)): U^T A_mu U c = U^T b_mu.
-* Affine precomputation (Sec. 3.1.1): with cellwise-constant materials m,
+* Affine precomputation (Sec. 3.1.1): with materials m (cellwise constant, or in 1D linear across
+  each cell between the materials of its two ends),
       A_mu = blockdiag_j(D_j + Sigma_t) - (1 omega^T) (x) Sigma_s
            = A_0 + sum_m sigma_{a,m} A_{a,m} + sum_m sigma_{s,m} A_{s,m},
       A_0 = blockdiag_j(D_j),  A_{a,m} = I (x) M_m,  A_{s,m} = I (x) M_m - (1 omega^T) (x) M_m,
-  M_m the mass matrix restricted to material m; A_{k,r} = U^T A_k U is stored.
+  M_m the mass matrix of material m's share of sigma (its indicator, or in 1D the linear function
+  that is 1 at the cell ends of material m and 0 at the others); A_{k,r} = U^T A_k U is stored.
 * U^rho = sum_j omega_j U_j and U^iso = sum_j U_j (Eq. (rho_basis)).
 * ROMIG (Sec. 3.1.1): rho^(0) = U^rho c with c the ROM solution.
 * Correction snapshots without solving the correction equation (Sec. 3.2.1):
@@ -62,10 +64,14 @@ class ReducedModel:
         self.U_iso = Uj.sum(0)
         self.A0 = sum(Uj[j].T @ (tr.D(j) @ Uj[j]) for j in range(self.Nv))
         mat = tr.problem.mat_id
+        mat_r = tr.problem.mat_id_right
         n_mat = tr.problem.n_mat
         self.Aa, self.As = [], []
         for m in range(n_mat):
-            Mm = tr.dg.mass_matrix((mat == m).astype(np.float64))
+            if mat_r is None:
+                Mm = tr.dg.mass_matrix((mat == m).astype(np.float64))
+            else:   # material m's share of a cell: its value at either end, linear in between
+                Mm = tr.dg.mass_matrix((mat == m).astype(np.float64), (mat_r == m).astype(np.float64))
             Aam = sum(Uj[j].T @ (Mm @ Uj[j]) for j in range(self.Nv))
             self.Aa.append(Aam)
             self.As.append(Aam - self.U_iso.T @ (Mm @ self.U_rho))

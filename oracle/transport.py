@@ -30,9 +30,20 @@ class Transport:
         self.sigma_t_cell = problem.sigma_t[b][mat]
         self.sigma_s_cell = problem.sigma_s[b][mat]
         self.sigma_a_cell = self.sigma_t_cell - self.sigma_s_cell
-        self.St = self.dg.mass_matrix(self.sigma_t_cell)
-        self.Ss = self.dg.mass_matrix(self.sigma_s_cell)
-        self.Sa = self.dg.mass_matrix(self.sigma_a_cell)
+        # 1D cross sections linear across each cell: the values at the cells' right ends
+        self.linear = problem.mat_id_right is not None
+        if self.linear:
+            mr = problem.mat_id_right
+            self.sigma_t_right = problem.sigma_t[b][mr]
+            self.sigma_s_right = problem.sigma_s[b][mr]
+            self.sigma_a_right = self.sigma_t_right - self.sigma_s_right
+            self.St = self.dg.mass_matrix(self.sigma_t_cell, self.sigma_t_right)
+            self.Ss = self.dg.mass_matrix(self.sigma_s_cell, self.sigma_s_right)
+            self.Sa = self.dg.mass_matrix(self.sigma_a_cell, self.sigma_a_right)
+        else:
+            self.St = self.dg.mass_matrix(self.sigma_t_cell)
+            self.Ss = self.dg.mass_matrix(self.sigma_s_cell)
+            self.Sa = self.dg.mass_matrix(self.sigma_a_cell)
         self.G = self.dg.source_vector(problem.source[b])
         self.inflow = problem.inflow[b]
         self.n_dof = self.dg.n_dof
@@ -152,9 +163,17 @@ def cell_balance(tr: Transport, rho_prev, f):
     rho_star = np.einsum("j,jn->n", tr.w, f)
     area = dg.h if tr.dim == 1 else np.full(n, dg.hx * dg.hy)
     sq = np.sqrt(area)           # int_T u = sqrt(|T|) u_0 for the orthonormal basis
-    bal = sq * (tr.sigma_t_cell * rho_star.reshape(n, P)[:, 0]
-                - tr.sigma_s_cell * rho_prev.reshape(n, P)[:, 0]
-                - tr.G.reshape(n, P)[:, 0])
+    rs, rp = rho_star.reshape(n, P), rho_prev.reshape(n, P)
+    if tr.linear:
+        # sigma = sbar + (sR - sL) xi / 2 and u = u_0 phi_0 + u_1 phi_1 on a cell of width h:
+        # int sigma u = sqrt(h) (sbar u_0 + (sR - sL) u_1 / (2 sqrt 3))
+        def moment(sl, sr, u):
+            return 0.5 * (sl + sr) * u[:, 0] + (sr - sl) / (2.0 * np.sqrt(3.0)) * u[:, 1]
+        bal = sq * (moment(tr.sigma_t_cell, tr.sigma_t_right, rs)
+                    - moment(tr.sigma_s_cell, tr.sigma_s_right, rp) - tr.G.reshape(n, P)[:, 0])
+    else:
+        bal = sq * (tr.sigma_t_cell * rs[:, 0] - tr.sigma_s_cell * rp[:, 0]
+                    - tr.G.reshape(n, P)[:, 0])
     for j in range(tr.n_angles):
         bal += tr.w[j] * dg.net_upwind_outflow(tr.v[j], f[j], tr.inflow)
     return bal

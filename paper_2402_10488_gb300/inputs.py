@@ -8,7 +8,9 @@ matrices), so that the oracle and the CUDA path share inputs but no computation.
 
 Problem statement: steady one-group RTE with isotropic scattering, isotropic source G and
 isotropic inflow g (paper Sec. 2, Eq. (1); slab form Eq. (2)).  Cross sections are cellwise
-constant: each cell carries a material id, each instance a table sigma_t[m], sigma_s[m].
+constant: each cell carries a material id, each instance a table sigma_t[m], sigma_s[m].  In 1D a
+second id per cell (``mat_id_right``) makes them linear across the cell, between the values of
+the two materials at its ends.
 
 Layout conventions (an interface, used identically by every consumer):
   * cell index ``c = j * nx + i`` (i along x, j along y; ny = 1 in 1D);
@@ -49,6 +51,10 @@ class Problem:
     params: np.ndarray = field(default=None)  # float64 [B, p], the mu that made each instance
     name: str = ""
     edges: np.ndarray = field(default=None)   # 1D only: cell edges x_0 < ... < x_N (None: uniform)
+    # 1D only: material at each cell's right end (None: mat_id).  Cross sections are then linear
+    # across every cell, from the value of material mat_id[c] at its left end to that of
+    # mat_id_right[c] at its right end.
+    mat_id_right: np.ndarray = field(default=None)
 
     # ---- sizes -------------------------------------------------------------------------
     @property
@@ -94,6 +100,9 @@ class Problem:
         assert self.dim in (1, 2)
         assert self.mat_id.shape == (self.n_cells,)
         assert self.mat_id.min() >= 0 and self.mat_id.max() < self.n_mat
+        if self.mat_id_right is not None:
+            assert self.dim == 1 and self.mat_id_right.shape == (self.n_cells,)
+            assert self.mat_id_right.min() >= 0 and self.mat_id_right.max() < self.n_mat
         B = self.batch
         assert self.sigma_s.shape == self.sigma_t.shape
         assert self.source.shape == (B, self.n_cells)
@@ -133,15 +142,19 @@ def slab_diffusive(n_cells: int = 128, n_angles: int = 16, eps: float = 0.01) ->
 
 
 def slab_random(n_cells: int, n_angles: int, n_mat: int, seed: int, B: int = 1,
-                inflow=(0.0, 0.0)) -> Problem:
-    """Slab with random per-cell materials (for parity tests): c = sigma_s/sigma_t in [0, 0.99]."""
+                inflow=(0.0, 0.0), linear: bool = False) -> Problem:
+    """Slab with random per-cell materials (for parity tests): c = sigma_s/sigma_t in [0, 0.99].
+    linear: a second random material per cell for its right end (cross sections linear across
+    the cell; c stays in [0, 0.99] everywhere since both ends satisfy it)."""
     rng = np.random.default_rng(seed)
     mat = rng.integers(0, n_mat, n_cells).astype(np.int32)
     st = rng.uniform(0.5, 20.0, (B, n_mat))
     ss = st * rng.uniform(0.0, 0.99, (B, n_mat))
     G = rng.uniform(0.0, 2.0, (B, n_cells))
+    mat_r = rng.integers(0, n_mat, n_cells).astype(np.int32) if linear else None
     return Problem(1, n_cells, 1, (0.0, 1.0), "gl", n_angles, 0, mat, st, ss, G,
-                   np.tile(_stack(inflow), (B, 1)), None, f"slab_random{seed}")
+                   np.tile(_stack(inflow), (B, 1)), None,
+                   f"slab_random{seed}" + ("_linear" if linear else ""), mat_id_right=mat_r)
 
 
 # ---- 2D lattice-cell workloads -------------------------------------------------------------
@@ -317,17 +330,26 @@ def pin_cell_test(n_test: int = 10, seed: int = TEST_SEED0):
 
 # ---- the paper's 1D cross-regime problem (Sec. 4.1.1) -----------------------------------------
 
-def cross_regime(mu_s, n: int = 400, n_angles: int = 16) -> Problem:
+def cross_regime(mu_s, n: int = 400, n_angles: int = 16, linear: bool = True) -> Problem:
     """Sec. 4.1.1: slab [0,10], sigma_a = 0, sigma_s(x) = 0.1 + mu_s x, G = 0.01, vacuum inflow,
-    n uniform cells, S_16.  sigma_s is taken cellwise constant at its cell average (the value at
-    the cell centre), so every cell is its own material: mat_id = cell index."""
+    n uniform cells, S_16.  linear: sigma_s is linear inside the cells as in the paper; the n + 1
+    cell edges are the materials (material m holds sigma_s(x_m)) and cell c runs from material c
+    to material c + 1.  Otherwise sigma_s is taken cellwise constant at its cell average (the
+    value at the cell centre), every cell its own material."""
     mu_s = np.atleast_1d(np.asarray(mu_s, dtype=np.float64))
     B = mu_s.size
+    name = f"cross_regime{n}_S{n_angles}"
+    if linear:
+        xe = np.arange(n + 1) * 10.0 / n
+        sig = 0.1 + mu_s[:, None] * xe[None, :]
+        return Problem(1, n, 1, (0.0, 10.0), "gl", n_angles, 0, np.arange(n, dtype=np.int32),
+                       sig.copy(), sig.copy(), np.full((B, n), 0.01), np.zeros((B, 2)),
+                       mu_s[:, None].copy(), name + "_linear",
+                       mat_id_right=np.arange(1, n + 1, dtype=np.int32))
     xc = (np.arange(n) + 0.5) * 10.0 / n
     sig = 0.1 + mu_s[:, None] * xc[None, :]
     return Problem(1, n, 1, (0.0, 10.0), "gl", n_angles, 0, np.arange(n, dtype=np.int32), sig.copy(),
-                   sig.copy(), np.full((B, n), 0.01), np.zeros((B, 2)), mu_s[:, None].copy(),
-                   f"cross_regime{n}_S{n_angles}")
+                   sig.copy(), np.full((B, n), 0.01), np.zeros((B, 2)), mu_s[:, None].copy(), name)
 
 
 def cross_regime_train():
