@@ -71,7 +71,7 @@ int rte_counters(int64_t* out);
  *   n_phi, n_vz    1D: n_phi = number of Gauss-Legendre points, n_vz = 0
  *                  2D: the CL(n_phi, n_vz) rule of Sec. 2.1; n_phi must be even (reflection
  *                  symmetry used by the 2D DSA moments)
- *   n_mat          number of materials (cross sections are constant per material)
+ *   n_mat          number of materials (a material's cross sections are one value per instance)
  *   mat_id         HOST int32[n_cells], material of each cell, copied during the call      */
 typedef struct {
   int dim;
@@ -82,6 +82,13 @@ typedef struct {
   const int32_t* mat_id;
   const double* dx;   /* 1D only, HOST double[nx] or NULL: cell widths of a non-uniform mesh
                          (positive, summing to x1 - x0); NULL = uniform.  Ignored in 2D.         */
+  const int32_t* mat_id_right;
+                      /* 1D only, HOST int32[nx] or NULL: the material at each cell's right
+                         end.  Cross sections are then linear across cell c, from the values of
+                         material mat_id[c] at its left end to those of mat_id_right[c] at its
+                         right end (the paper's cross-regime problem, Sec. 4.1.1, has sigma_s
+                         linear in x); NULL = mat_id (cellwise constant).  Must be NULL in 2D.
+                         Copied during the call.                                                */
 } rte_disc_desc;
 
 /* Creates the discretisation on CUDA device `device`: builds the quadrature (Sec. 2.1), the
@@ -116,6 +123,22 @@ int rte_batch_destroy(rte_batch_t batch);
  * Synchronous with respect to the host (returns after the set-up has run). */
 int rte_batch_set_params(rte_batch_t batch, const double* sigma_t, const double* sigma_s,
                          const double* source, const double* inflow);
+
+/* The same as rte_batch_set_params with the parameters already in DEVICE memory of the batch's
+ * device (for example tensors resident in HBM), in the same layouts:
+ *   sigma_t, sigma_s  DEVICE double[B][n_mat];  source DEVICE double[B][n_cells];
+ *   inflow            DEVICE double[B][2*dim]
+ * Asynchronous on `stream`: a kernel copies the tables, forms the source moments and checks every
+ * value (finite, sigma_t > 0, 0 <= sigma_s <= sigma_t) on the device, then the per-instance
+ * set-up kernels run; the call returns without waiting.  The check's outcome is read by the host
+ * in the next call that uses the parameters (rte_sweep, rte_solve, rte_pgmres, rte_dsa_correction,
+ * ...): that call waits for the set-up and returns RTE_EINVAL, leaving the batch without
+ * parameters, if a value was invalid.  Invalid values cause no fault (they only enter
+ * arithmetic).  The caller keeps the arrays unchanged until the stream has passed the call;
+ * work on other streams must be ordered after it by the caller.  Errors (immediate): RTE_EINVAL
+ * for null arguments, RTE_ECUDA. */
+int rte_batch_set_params_device(rte_batch_t batch, const double* sigma_t, const double* sigma_s,
+                                const double* source, const double* inflow, void* stream);
 
 /* Sets the parameters of some instances (slots) only, leaving the others untouched -- the
  * admission step of continuous batching.  Same meaning as rte_batch_set_params for n instances:

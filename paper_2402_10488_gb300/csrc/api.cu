@@ -67,7 +67,7 @@ static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w
 
 using namespace rte;
 
-extern "C" int rte_version(void) { return 10300; }
+extern "C" int rte_version(void) { return 10400; }
 extern "C" const char* rte_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" int rte_disc_create(const rte_disc_desc* d, int device, rte_disc_t* out) {
@@ -92,6 +92,12 @@ extern "C" int rte_disc_create(const rte_disc_desc* d, int device, rte_disc_t* o
     }
     if (std::fabs(tot - (d->x1 - d->x0)) > 1e-12 * (d->x1 - d->x0))
       return fail(RTE_EINVAL, "cell widths must sum to x1 - x0");
+  }
+  if (d->mat_id_right) {
+    if (d->dim != 1) return fail(RTE_EINVAL, "mat_id_right (linear cross sections) is 1D only");
+    for (int c = 0; c < d->nx; ++c)
+      if (d->mat_id_right[c] < 0 || d->mat_id_right[c] >= d->n_mat)
+        return fail(RTE_EINVAL, "material id out of range");
   }
   int ndev = 0;
   RTE_CUDA_TRY(cudaGetDeviceCount(&ndev));
@@ -122,6 +128,11 @@ extern "C" int rte_disc_create(const rte_disc_desc* d, int device, rte_disc_t* o
       delete disc;
       return fail(RTE_EINVAL, "material id out of range");
     }
+  if (d->dim == 1) {
+    disc->matr_host = d->mat_id_right ? std::vector<int32_t>(d->mat_id_right, d->mat_id_right + d->nx)
+                                      : disc->mat_host;
+    disc->linear = disc->matr_host != disc->mat_host;
+  }
 
   // ---- quadrature (Sec. 2.1) and distinct directions --------------------------------------
   if (d->dim == 1) {
@@ -190,6 +201,7 @@ extern "C" int rte_disc_create(const rte_disc_desc* d, int device, rte_disc_t* o
   int st = disc->mat_id.alloc(disc->n_cells);
   if (st == RTE_OK) st = disc->dir_dev.alloc(4 * (size_t)disc->n_dirs);
   if (st == RTE_OK && d->dim == 1) st = disc->dx_dev.alloc(disc->nx);
+  if (st == RTE_OK && disc->linear) st = disc->mat_r.alloc(disc->nx);
   if (st != RTE_OK) {
     delete disc;
     return st;
@@ -208,6 +220,9 @@ extern "C" int rte_disc_create(const rte_disc_desc* d, int device, rte_disc_t* o
   cudaError_t e3 = cudaSuccess;
   if (d->dim == 1)
     e3 = cudaMemcpy(disc->dx_dev.p, disc->dx.data(), sizeof(double) * disc->nx, cudaMemcpyHostToDevice);
+  if (e3 == cudaSuccess && disc->linear)
+    e3 = cudaMemcpy(disc->mat_r.p, disc->matr_host.data(), sizeof(int32_t) * disc->nx,
+                    cudaMemcpyHostToDevice);
   if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
     delete disc;
     return fail(RTE_ECUDA, "rte_disc_create: upload failed");
@@ -366,6 +381,8 @@ size_t rte_batch_s::bytes() const {
 }
 
 rte_batch_s::~rte_batch_s() {
+  if (param_bad_h) cudaFreeHost(param_bad_h);
+  if (param_ev) cudaEventDestroy(param_ev);
   if (stage) cudaFreeHost(stage);
   if (stage_mask) cudaFreeHost(stage_mask);
   if (stage_ev) cudaEventDestroy(stage_ev);
@@ -500,6 +517,100 @@ extern "C" int rte_batch_destroy(rte_batch_t b) {
   return RTE_OK;
 }
 
+namespace rte {
+// Parameters from device memory: the cross-section tables copied, G0 = G sqrt|T| per cell (the
+// zeroth moment of a cellwise-constant source on the orthonormal basis, as the host path computes
+// it), the inflow spread to the [B][4] layout, and `bad` set when a value is not finite or
+// violates sigma_t > 0, 0 <= sigma_s <= sigma_t.  Grid-stride over the largest of the three.
+__global__ void params_device_kernel(const double* __restrict__ sigma_t,
+                                     const double* __restrict__ sigma_s,
+                                     const double* __restrict__ source,
+                                     const double* __restrict__ inflow, double* st_out,
+                                     double* ss_out, double* G0, double* inflow_out,
+                                     const double* __restrict__ dx, double sq_area, int B,
+                                     int n_mat, int n_cells, int n_side, int* bad) {
+  const size_t nm = (size_t)B * n_mat, nc = (size_t)B * n_cells, ni = (size_t)B * 4;
+  const size_t n = nm > nc ? (nm > ni ? nm : ni) : (nc > ni ? nc : ni);
+  bool ok = true;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    if (k < nm) {
+      const double t = sigma_t[k], c = sigma_s[k];
+      ok = ok && isfinite(t) && isfinite(c) && t > 0.0 && c >= 0.0 && c <= t;
+      st_out[k] = t;
+      ss_out[k] = c;
+    }
+    if (k < nc) {
+      const double g = source[k];
+      ok = ok && isfinite(g);
+      G0[k] = g * (dx ? sqrt(dx[k % n_cells]) : sq_area);
+    }
+    if (k < ni) {
+      const int side = (int)(k % 4);
+      const double g = side < n_side ? inflow[(k / 4) * n_side + side] : 0.0;
+      ok = ok && isfinite(g);
+      inflow_out[k] = g;
+    }
+  }
+  if (!ok) atomicOr(bad, 1);
+}
+
+int params_ready(rte_batch_t b, const char* who) {
+  if (b->param_pending) {
+    RTE_CUDA_TRY(cudaEventSynchronize(b->param_ev));
+    b->param_pending = false;
+    if (*b->param_bad_h) {
+      b->params_set = false;
+      return fail(RTE_EINVAL, std::string(who) + ": the parameters set from device memory are "
+                  "invalid (need finite values, sigma_t > 0 and 0 <= sigma_s <= sigma_t)");
+    }
+  }
+  if (!b->params_set) return fail(RTE_ESTATE, std::string(who) + ": parameters not set");
+  return RTE_OK;
+}
+}  // namespace rte
+
+extern "C" int rte_batch_set_params_device(rte_batch_t b, const double* sigma_t,
+                                           const double* sigma_s, const double* source,
+                                           const double* inflow, void* stream) {
+  if (!b || !sigma_t || !sigma_s || !source || !inflow)
+    return fail(RTE_EINVAL, "rte_batch_set_params_device: null argument");
+  rte_disc_s* d = b->disc;
+  DeviceGuard g(d->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (b->param_pending) {       // a previous device upload's flag must be read before reuse
+    RTE_CUDA_TRY(cudaEventSynchronize(b->param_ev));
+    b->param_pending = false;
+  }
+  if (!b->param_bad.p) {
+    RTE_TRY(b->param_bad.alloc(1));
+    RTE_CUDA_TRY(cudaHostAlloc((void**)&b->param_bad_h, sizeof(int), cudaHostAllocDefault));
+    RTE_CUDA_TRY(cudaEventCreateWithFlags(&b->param_ev, cudaEventDisableTiming));
+  }
+  const size_t nm = (size_t)b->B * d->n_mat, nc = (size_t)b->B * d->n_cells;
+  const size_t n = std::max(std::max(nm, nc), (size_t)b->B * 4);
+  RTE_CUDA_TRY(cudaMemsetAsync(b->param_bad.p, 0, sizeof(int), st));
+  const int th = 256;
+  const unsigned bl = (unsigned)std::min<size_t>((n + th - 1) / th, 4096);
+  params_device_kernel<<<bl, th, 0, st>>>(sigma_t, sigma_s, source, inflow, b->sigma_t.p,
+                                          b->sigma_s.p, b->G0.p, b->inflow.p,
+                                          d->dim == 1 ? d->dx_dev.p : nullptr,
+                                          std::sqrt(d->hx * d->hy), b->B, d->n_mat, d->n_cells,
+                                          2 * d->dim, b->param_bad.p); RTE_NOTE_LAUNCH();
+  RTE_CUDA_TRY(cudaGetLastError());
+  {
+    PhaseScope ps(b, 3, st);
+    RTE_TRY(setup_tables(b, st));
+    b->tables32_stale = true;
+    RTE_TRY(dsa_setup(b, st));
+  }
+  RTE_CUDA_TRY(cudaMemcpyAsync(b->param_bad_h, b->param_bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RTE_CUDA_TRY(cudaEventRecord(b->param_ev, st));
+  b->param_pending = true;
+  b->slot_set.assign(b->B, 1);
+  b->params_set = true;
+  return RTE_OK;
+}
+
 extern "C" int rte_batch_set_params(rte_batch_t b, const double* sigma_t, const double* sigma_s,
                                     const double* source, const double* inflow) {
   if (!b || !sigma_t || !sigma_s || !source || !inflow)
@@ -518,6 +629,10 @@ extern "C" int rte_batch_set_params(rte_batch_t b, const double* sigma_t, const 
   for (size_t k = 0; k < ni; ++k)
     if (!std::isfinite(inflow[k])) return fail(RTE_EINVAL, "inflow is not finite");
   DeviceGuard g(d->device);
+  if (b->param_pending) {       // a device upload still in flight is superseded by this one
+    RTE_CUDA_TRY(cudaEventSynchronize(b->param_ev));
+    b->param_pending = false;
+  }
   b->sigma_t_h.assign(sigma_t, sigma_t + nm);
   b->sigma_s_h.assign(sigma_s, sigma_s + nm);
   b->source_h.assign(source, source + nc);

@@ -54,6 +54,15 @@ struct DeviceGuard {
   }
 };
 
+// A 1D cross section linear across a cell, from `left` at its left end to `right` at its right
+// end, acts on the cell's orthonormal P1 moments as the symmetric 2x2 [[mean, off], [off, mean]]
+// with mean = (left + right) / 2 and off = (right - left) / (2 sqrt 3).
+__host__ __device__ __forceinline__ void linear_sigma(double left, double right, double& mean,
+                                                      double& off) {
+  mean = 0.5 * (left + right);
+  off = (right - left) * 0.28867513459481288225;   // 1 / (2 sqrt 3)
+}
+
 // Device buffer owned by a handle.
 template <class T>
 struct DevBuf {
@@ -119,6 +128,11 @@ struct rte_disc_s {
   rte::DevBuf<double> dir_dev;        // [n_dirs][4] vx, vy, w, mult
   std::vector<double> dx;             // 1D: cell widths (uniform: hx each)
   rte::DevBuf<double> dx_dev;         // 1D: [nx]
+  // 1D cross sections linear across cells: material at each cell's right end (matr_host is
+  // mat_host when they are cellwise constant; mat_r is then not allocated and linear is false)
+  std::vector<int32_t> matr_host;
+  rte::DevBuf<int32_t> mat_r;         // 1D linear: [nx]
+  bool linear = false;
 };
 
 namespace rte {
@@ -147,6 +161,12 @@ struct rte_batch_s {
   int force_dpw = 0;                  // autotuner trials: this dpw for every launch
   bool kba = true;                    // several warps per direction group when warps are scarce
   std::vector<double> sigma_t_h, sigma_s_h, source_h, inflow_h;
+  // parameters taken from device memory (rte_batch_set_params_device) are validated on the device;
+  // the host reads the flag when a later call first needs them (params_ready)
+  rte::DevBuf<int> param_bad;
+  int* param_bad_h = nullptr;             // pinned copy of param_bad
+  cudaEvent_t param_ev = nullptr;         // recorded after the set-up and the flag copy
+  bool param_pending = false;
   rte::DevBuf<double> sigma_t, sigma_s;   // [B][n_mat]
   rte::DevBuf<double> G0;                 // [B][n_cells] zeroth source moment int G phi_0
   rte::DevBuf<double> inflow;             // [B][4] (2D) or [B][2] (1D)
@@ -180,6 +200,11 @@ struct rte_batch_s {
 };
 
 namespace rte {
+// RTE_OK when the batch has parameters; RTE_ESTATE ("<who>: parameters not set") otherwise.
+// Parameters set from device memory are checked here the first time: the host waits for their
+// set-up and reads the device's validation flag (RTE_EINVAL, and no parameters, if it failed).
+int params_ready(rte_batch_t b, const char* who);
+
 // Brackets one phase of work on `st` with CUDA events when the batch is timing (no-op otherwise).
 struct PhaseScope {
   rte_batch_t b;
@@ -264,7 +289,8 @@ struct SiState {
   rte_solve_opts o{};
   rte_rom_t rom = nullptr;
   bool mixed = false;                 // FP32 sweeps until the change drops below fp32_switch
-  uint8_t* hm = nullptr;              // pinned [6][B]: act, lo, hi (sweep) | act, rom, dsa (correction)
+  uint8_t* hm = nullptr;              // pinned [8][B]: act, lo, hi (sweep) | act, rom, dsa
+                                      // (correction) | converged, expired (result copies)
   unsigned long long* hn = nullptr;   // pinned [2B] stop-test norms (ordered bit patterns)
   DevBuf<uint8_t> dm;                 // device copy of hm
   cudaEvent_t ev = nullptr;           // recorded after the norms copy
@@ -274,6 +300,7 @@ struct SiState {
   std::vector<rte_solve_report> rep;
   bool in_flight = false;
   double* result = nullptr;           // [B][n_dof] destination of finished instances (device or pinned host)
+  bool result_dev = false;            // result is device memory: one masked copy kernel per iteration
   int init(rte_batch_t b, const rte_solve_opts& opts, rte_rom_t rom_c, double* result_dst);
   void begin(int b, double eps_b);    // the instance's initial iterate is already in slot b of work
   int n_active() const;

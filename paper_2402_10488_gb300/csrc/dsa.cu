@@ -678,18 +678,28 @@ struct Blocks1D {
   const double *Dd, *Lw, *Ue;  // [nx][16] per cell: D without sigma terms; west / east couplings
 };
 
+// Block LU of the 1D consistent-DSA system, cell blocks over the unknowns (drho_0, drho_1,
+// dJ_0, dJ_1): Sigma_a enters the (drho, drho) 2x2 and Sigma_t the (dJ, dJ) 2x2, each sigma I or,
+// with cross sections linear across cells (matr non-null), the 2x2 of linear_sigma.
 __global__ void dsa1d_factor_kernel(Blocks1D K, const double* sigma_t, const double* sigma_s,
-                                    const int32_t* mat, int nx, int n_mat, int B, double* Dpinv,
-                                    double* Mfac, const uint8_t* mask) {
+                                    const int32_t* mat, const int32_t* matr, int nx, int n_mat,
+                                    int B, double* Dpinv, double* Mfac, const uint8_t* mask) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   if (mask && !mask[b]) return;
   double Dp[16], Di[16], tmp[16];
   for (int c = 0; c < nx; ++c) {
     const int m = mat[c];
-    const double st = sigma_t[b * n_mat + m], sa = st - sigma_s[b * n_mat + m];
+    double st = sigma_t[b * n_mat + m], sa = st - sigma_s[b * n_mat + m], to = 0.0, ao = 0.0;
+    if (matr) {
+      const int mr = matr[c];
+      const double str = sigma_t[b * n_mat + mr], sar = str - sigma_s[b * n_mat + mr];
+      linear_sigma(st, str, st, to);
+      linear_sigma(sa, sar, sa, ao);
+    }
     for (int e = 0; e < 16; ++e) Dp[e] = K.Dd[16 * c + e];
     Dp[0] += sa, Dp[5] += sa, Dp[10] += st, Dp[15] += st;
+    Dp[1] += ao, Dp[4] += ao, Dp[11] += to, Dp[14] += to;
     double* Mc = Mfac + ((size_t)b * nx + c) * 16;
     if (c > 0) {
       const double* Dprev = Dpinv + ((size_t)b * nx + c - 1) * 16;
@@ -995,7 +1005,7 @@ int dsa_setup(rte_batch_t bt, cudaStream_t st, const uint8_t* mask) {
       RTE_TRY(s->work1.alloc((size_t)B * d->nx * 4));
     }
     dsa1d_factor_kernel<<<(B + 63) / 64, 64, 0, st>>>(s->K1, bt->sigma_t.p, bt->sigma_s.p,
-                                                      d->mat_id.p, d->nx, d->n_mat, B,
+                                                      d->mat_id.p, d->mat_r.p, d->nx, d->n_mat, B,
                                                       s->Dpinv.p, s->Mfac.p, mask); RTE_NOTE_LAUNCH();
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
@@ -1327,7 +1337,7 @@ using namespace rte;
 extern "C" int rte_dsa_correction(rte_batch_t b, const double* R, double* drho, double rtol,
                                   int max_it, const uint8_t* active, int* iters, void* stream) {
   if (!b || !R || !drho) return fail(RTE_EINVAL, "rte_dsa_correction: null argument");
-  if (!b->params_set) return fail(RTE_ESTATE, "parameters not set");
+  RTE_TRY(params_ready(b, "rte_dsa_correction"));
   if (!(rtol >= 0) || max_it < 1) return fail(RTE_EINVAL, "rte_dsa_correction: bad tolerance");
   DeviceGuard g(b->disc->device);
   cudaStream_t st = (cudaStream_t)stream;

@@ -17,12 +17,27 @@
 
 namespace rte {
 
-// w = v - Lv (or v when Lv is null); R = Sigma_s w
+// w = v - Lv (or v when Lv is null); R = Sigma_s w.  With 1D cross sections linear across cells
+// (matr non-null, P = 2) a thread takes one cell and applies the 2x2 of linear_sigma; both moments
+// are read before either is written, so w may alias v.
 __global__ void amv_kernel(const double* v, const double* Lv, double* w, double* R,
-                           const double* sigma_s, const int32_t* mat, const uint8_t* active,
-                           int n_dof, int P, int n_mat) {
+                           const double* sigma_s, const int32_t* mat, const int32_t* matr,
+                           const uint8_t* active, int n_dof, int P, int n_mat) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
+  if (matr) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_dof / 2; c += gridDim.x * blockDim.x) {
+      const size_t o = (size_t)b * n_dof + 2 * c;
+      const double t0 = Lv ? v[o] - Lv[o] : v[o], t1 = Lv ? v[o + 1] - Lv[o + 1] : v[o + 1];
+      double sb, so;
+      linear_sigma(sigma_s[(size_t)b * n_mat + mat[c]], sigma_s[(size_t)b * n_mat + matr[c]], sb, so);
+      w[o] = t0;
+      w[o + 1] = t1;
+      R[o] = fma(sb, t0, so * t1);
+      R[o + 1] = fma(so, t0, sb * t1);
+    }
+    return;
+  }
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_dof; e += gridDim.x * blockDim.x) {
     const size_t o = (size_t)b * n_dof + e;
     const double t = Lv ? v[o] - Lv[o] : v[o];
@@ -156,7 +171,8 @@ struct Gmres {
   }
   // out = M^{-1} in  (in may equal out)
   int apply_minv(const double* in, double* out, const uint8_t* act) {
-    amv_kernel<<<grid, 256, 0, st>>>(in, nullptr, out, R(), bt->sigma_s.p, bt->disc->mat_id.p, act,
+    amv_kernel<<<grid, 256, 0, st>>>(in, nullptr, out, R(), bt->sigma_s.p, bt->disc->mat_id.p,
+                                     bt->disc->mat_r.p, act,
                                      n, P, n_mat); RTE_NOTE_LAUNCH();
     RTE_CUDA_TRY(cudaGetLastError());
     if (o->precond) {
@@ -285,7 +301,7 @@ static int run_pgmres(rte_batch_t bt, const rte_gmres_opts* o, double* x,
       // w = M^{-1} (I - L) V_i
       RTE_TRY(sweep_launch(bt, G.Vj(i), G.lx(), nullptr, 0, m0, st, false, na));
       amv_kernel<<<G.grid, 256, 0, st>>>(G.Vj(i), G.lx(), G.w.p, G.R(), bt->sigma_s.p, d->mat_id.p,
-                                         m0, n, G.P, G.n_mat); RTE_NOTE_LAUNCH();
+                                         d->mat_r.p, m0, n, G.P, G.n_mat); RTE_NOTE_LAUNCH();
       RTE_CUDA_TRY(cudaGetLastError());
       if (o->precond) {
         PhaseScope ps(bt, 1, st);
@@ -386,7 +402,7 @@ using namespace rte;
 extern "C" int rte_pgmres(rte_batch_t b, const rte_gmres_opts* o, double* rho,
                           rte_solve_report* reports, void* stream) {
   if (!b || !o || !rho) return fail(RTE_EINVAL, "rte_pgmres: null argument");
-  if (!b->params_set) return fail(RTE_ESTATE, "rte_pgmres: parameters not set");
+  RTE_TRY(params_ready(b, "rte_pgmres"));
   if (!(o->rtol > 0) || o->restart < 1 || o->restart > 200 || o->max_iter < 1 ||
       (o->precond != 0 && o->precond != 1))
     return fail(RTE_EINVAL, "rte_pgmres: bad options");

@@ -49,7 +49,7 @@ using namespace rte;
 extern "C" int rte_sweep_static(rte_batch_t b, const double* rho_in, double* rho_out,
                                 int with_source, void* stream) {
   if (!b || !rho_in || !rho_out) return fail(RTE_EINVAL, "rte_sweep_static: null argument");
-  if (!b->params_set) return fail(RTE_ESTATE, "rte_sweep_static: parameters not set");
+  RTE_TRY(params_ready(b, "rte_sweep_static"));
   if (rho_in == rho_out) return fail(RTE_EINVAL, "rte_sweep_static: rho_out aliases rho_in");
   if (((uintptr_t)rho_in | (uintptr_t)rho_out) & 15)
     return fail(RTE_EINVAL, "rte_sweep_static: arrays must be 16-byte aligned");

@@ -10,7 +10,9 @@
 // or Eq. (pod_truncation) with singular values.  Reduced operators (affine decomposition, cellwise materials m):
 //     A_0r = sum_j U_j^T D_j U_j,   A_{a,m} = sum_j U_j^T M_m U_j,
 //     A_{s,m} = A_{a,m} - (U^iso)^T M_m U^rho,   A_{mu,r} = A_0r + sum_m sigma_a,m A_{a,m} + sigma_s,m A_{s,m}
-// with U^rho = sum_j omega_j U_j and U^iso = sum_j U_j (Eq. (rho_basis)).
+// with U^rho = sum_j omega_j U_j and U^iso = sum_j U_j (Eq. (rho_basis)); M_m is the mass matrix
+// of material m's share of the cross sections: its indicator, or in 1D with cross sections linear
+// across cells the function that is linear on each cell and 1 at the cell ends carrying m.
 // Online: ROMIG rho^(0) = U^rho A_{mu,r}^{-1} U^T b_mu, U^T b_mu = (U^iso)^T G + sum over the
 // sides of g_side a_side (a_side = U^T of the unit isotropic inflow through that side); ROMSA
 // delta rho = dU^rho (dU^T A_mu dU)^{-1} (dU^iso)^T R (Eq. (rom_correction)).  The r x r systems
@@ -41,15 +43,16 @@ struct RomOnline {
 __global__ void cross_gram_kernel(const double* __restrict__ X, int nx_cols,
                                   const double* __restrict__ Y, int ny_cols, size_t nrow,
                                   int n_dof, int P, const double* __restrict__ wdir,
-                                  const int32_t* __restrict__ mat, int cls0, int n_class,
+                                  const int32_t* __restrict__ mat,
+                                  const int32_t* __restrict__ matr, int cls0, int n_class,
                                   double* partial) {
   extern __shared__ double sm[];
   const int T = 16;
   double* Xs = sm;                        // [nx_cols][T]
   double* Ys = Xs + (size_t)nx_cols * T;  // [ny_cols][T]
   double* acc = Ys + (size_t)ny_cols * T; // [n_class][nx_cols*ny_cols]
-  __shared__ double ws[16];
-  __shared__ int cs[16];
+  __shared__ double ws[16], wr[16];
+  __shared__ int cs[16], cr[16];
   const int npairs = nx_cols * ny_cols;
   for (int p = threadIdx.x; p < n_class * npairs; p += blockDim.x) acc[p] = 0.0;
   const size_t ntiles = (nrow + T - 1) / T;
@@ -65,23 +68,47 @@ __global__ void cross_gram_kernel(const double* __restrict__ X, int nx_cols,
     }
     if (threadIdx.x < T) {
       const size_t row = r0 + threadIdx.x;
-      double w = 0.0;
-      int c = 0;
+      double w = 0.0, w2 = 0.0;
+      int c = 0, c2 = 0;
       if (row < nrow) {
         const size_t d = row / n_dof, e = row % n_dof;
         w = wdir ? wdir[d] : 1.0;
+        if (matr) {
+          w2 = w;
+          c2 = matr[e / P] - cls0;
+          if (c2 < 0 || c2 >= n_class) w2 = 0.0, c2 = 0;
+        }
         c = (mat ? mat[e / P] : 0) - cls0;
         if (c < 0 || c >= n_class) w = 0.0, c = 0;
       }
       ws[threadIdx.x] = w;
       cs[threadIdx.x] = c;
+      wr[threadIdx.x] = w2;
+      cr[threadIdx.x] = c2;
     }
     __syncthreads();
-    for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
-      const int i = p / ny_cols, j = p % ny_cols;
-      for (int rr = 0; rr < T; ++rr) {
-        const double v = ws[rr] * Xs[i * T + rr] * Ys[j * T + rr];
-        acc[cs[rr] * npairs + p] += v;
+    if (matr) {
+      // 1D, cross sections linear across cells (P = 2; a tile holds whole cells, rows rr and
+      // rr ^ 1 are one cell's two moments): material m's share of a cell is 1 at the ends that
+      // carry m, so a cell adds x^T [[1/2, -k], [-k, 1/2]] y to its left-end material and
+      // x^T [[1/2, k], [k, 1/2]] y to its right-end material, k = 1 / (2 sqrt 3).
+      const double k = 0.28867513459481288225;
+      for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+        const int i = p / ny_cols, j = p % ny_cols;
+        for (int rr = 0; rr < T; ++rr) {
+          const double x = Xs[i * T + rr];
+          const double vd = 0.5 * x * Ys[j * T + rr], vo = k * x * Ys[j * T + (rr ^ 1)];
+          acc[cs[rr] * npairs + p] += ws[rr] * (vd - vo);
+          acc[cr[rr] * npairs + p] += wr[rr] * (vd + vo);
+        }
+      }
+    } else {
+      for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+        const int i = p / ny_cols, j = p % ny_cols;
+        for (int rr = 0; rr < T; ++rr) {
+          const double v = ws[rr] * Xs[i * T + rr] * Ys[j * T + rr];
+          acc[cs[rr] * npairs + p] += v;
+        }
       }
     }
   }
@@ -394,7 +421,7 @@ struct GramCtx {
 // bounds (many classes: e.g. one material per cell).
 static int cross_gram(const double* X, int nxc, const double* Y, int nyc, size_t nrow, int n_dof,
                       int P, const double* wdir, const int32_t* mat, int n_class,
-                      std::vector<double>& out, cudaStream_t st) {
+                      std::vector<double>& out, cudaStream_t st, const int32_t* matr = nullptr) {
   const int T = 16;
   const size_t budget = 200 * 1024 / sizeof(double);
   auto fits = [&](int nc, int ncl) {
@@ -419,7 +446,7 @@ static int cross_gram(const double* X, int nxc, const double* Y, int nyc, size_t
       RTE_CUDA_TRY(cudaFuncSetAttribute(cross_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem));
       cross_gram_kernel<<<nblocks, 256, smem, st>>>(X, nxc, Y + (size_t)j0 * nrow, nc, nrow, n_dof,
-                                                    P, wdir, mat, c0, ncl, g.partial.p); RTE_NOTE_LAUNCH();
+                                                    P, wdir, mat, matr, c0, ncl, g.partial.p); RTE_NOTE_LAUNCH();
       RTE_CUDA_TRY(cudaGetLastError());
       const int n = (int)(ncl * npairs);
       sum_partials_kernel<<<(n + 255) / 256, 256, 0, st>>>(g.partial.p, nblocks, n, g.out.p); RTE_NOTE_LAUNCH();
@@ -808,8 +835,10 @@ static int reduce_operators(rte_rom_t rom, cudaStream_t st) {
   std::vector<double> A0, Aa, C;
   // A_0r[i][j] = sum_rows mult U_i (D U_j)
   RTE_TRY(cross_gram(rom->U.p, r, Y.p, r, nrow, n, d->P, multd.p, nullptr, 1, A0, st));
-  RTE_TRY(cross_gram(rom->U.p, r, rom->U.p, r, nrow, n, d->P, multd.p, d->mat_id.p, d->n_mat, Aa, st));
-  RTE_TRY(cross_gram(rom->U_iso.p, r, rom->U_rho.p, r, n, n, d->P, nullptr, d->mat_id.p, d->n_mat, C, st));
+  RTE_TRY(cross_gram(rom->U.p, r, rom->U.p, r, nrow, n, d->P, multd.p, d->mat_id.p, d->n_mat, Aa, st,
+                     d->mat_r.p));
+  RTE_TRY(cross_gram(rom->U_iso.p, r, rom->U_rho.p, r, n, n, d->P, nullptr, d->mat_id.p, d->n_mat, C,
+                     st, d->mat_r.p));
   rom->A0 = A0;
   rom->Aa = Aa;
   rom->As.resize(Aa.size());
@@ -886,7 +915,7 @@ using namespace rte;
 extern "C" int rte_rom_build(rte_batch_t train, const rte_rom_opts* opts, rte_rom_t* rom_p,
                              rte_rom_t* rom_c, void* stream) {
   if (!train || !opts) return fail(RTE_EINVAL, "rte_rom_build: null argument");
-  if (!train->params_set) return fail(RTE_ESTATE, "rte_rom_build: parameters not set");
+  RTE_TRY(params_ready(train, "rte_rom_build"));
   if (opts->window < 1 || opts->max_iter < 1 || !(opts->eps_train > 0) ||
       (opts->correction_start != 0 && opts->correction_start != 1))
     return fail(RTE_EINVAL, "rte_rom_build: bad options");
@@ -993,7 +1022,7 @@ extern "C" int rte_rom_info(rte_rom_t rom, double* info, double* sv) {
 extern "C" int rte_rom_initial_guess(rte_rom_t rom, rte_batch_t b, double* rho0,
                                      const uint8_t* active, void* stream) {
   if (!rom || !b || !rho0) return fail(RTE_EINVAL, "rte_rom_initial_guess: null argument");
-  if (!b->params_set) return fail(RTE_ESTATE, "parameters not set");
+  RTE_TRY(params_ready(b, "rte_rom_initial_guess"));
   if (rom->disc != b->disc) return fail(RTE_EINVAL, "ROM built on another discretisation");
   DeviceGuard g(b->disc->device);
   cudaStream_t st = (cudaStream_t)stream;
@@ -1006,7 +1035,7 @@ extern "C" int rte_rom_initial_guess(rte_rom_t rom, rte_batch_t b, double* rho0,
 extern "C" int rte_romsa_correction(rte_rom_t rom, rte_batch_t b, const double* R, double* drho,
                                     const uint8_t* active, void* stream) {
   if (!rom || !b || !R || !drho) return fail(RTE_EINVAL, "rte_romsa_correction: null argument");
-  if (!b->params_set) return fail(RTE_ESTATE, "parameters not set");
+  RTE_TRY(params_ready(b, "rte_romsa_correction"));
   if (rom->disc != b->disc) return fail(RTE_EINVAL, "ROM built on another discretisation");
   DeviceGuard g(b->disc->device);
   cudaStream_t st = (cudaStream_t)stream;
@@ -1015,12 +1044,13 @@ extern "C" int rte_romsa_correction(rte_rom_t rom, rte_batch_t b, const double* 
 }
 
 // ---- persistence of the online part of a ROM ------------------------------------------------
-// File layout (little-endian): magic "RTEROM02", int32 header {dim, nx, ny, n_phi, n_vz, n_mat,
+// File layout (little-endian): magic "RTEROM03", int32 header {dim, nx, ny, n_phi, n_vz, n_mat,
 // r, n_snap, n_cells, P}, double {x0, x1, y0, y1, eps_equiv}, int32 mat_id[n_cells],
-// double dx[nx] (1D only), sv[n_snap], A0[r][r], Aa[n_mat][r][r], As[n_mat][r][r],
+// 1D only: double dx[nx] and int32 mat_id_right[nx] (mat_id again when the cross sections are
+// cellwise constant), then double sv[n_snap], A0[r][r], Aa[n_mat][r][r], As[n_mat][r][r],
 // a_side[4][r], U_rho[r][n_dof], U_iso[r][n_dof].
 namespace {
-const char kRomMagic[8] = {'R', 'T', 'E', 'R', 'O', 'M', '0', '2'};
+const char kRomMagic[8] = {'R', 'T', 'E', 'R', 'O', 'M', '0', '3'};
 
 struct FileCloser {
   FILE* f;
@@ -1049,6 +1079,8 @@ extern "C" int rte_rom_save(rte_rom_t rom, const char* path) {
             fwrite(geo, 8, 5, fc.f) == 5 &&
             fwrite(d->mat_host.data(), 4, d->n_cells, fc.f) == (size_t)d->n_cells &&
             (d->dim != 1 || fwrite(d->dx.data(), 8, d->dx.size(), fc.f) == d->dx.size()) &&
+            (d->dim != 1 ||
+             fwrite(d->matr_host.data(), 4, d->matr_host.size(), fc.f) == d->matr_host.size()) &&
             fwrite(rom->sv.data(), 8, rom->sv.size(), fc.f) == rom->sv.size() &&
             fwrite(rom->A0.data(), 8, rom->A0.size(), fc.f) == rom->A0.size() &&
             fwrite(rom->Aa.data(), 8, rom->Aa.size(), fc.f) == rom->Aa.size() &&
@@ -1085,6 +1117,9 @@ extern "C" int rte_rom_load(rte_disc_t disc, const char* path, rte_rom_t* out) {
     std::vector<double> dxf(d->nx);
     if (fread(dxf.data(), 8, dxf.size(), fc.f) != dxf.size() || dxf != d->dx)
       return fail(RTE_EINVAL, "rte_rom_load: the file was built on another mesh");
+    std::vector<int32_t> matr(d->nx);
+    if (fread(matr.data(), 4, matr.size(), fc.f) != matr.size() || matr != d->matr_host)
+      return fail(RTE_EINVAL, "rte_rom_load: the file was built on another material map");
   }
   auto* rom = new rte_rom_s();
   rom->disc = disc;

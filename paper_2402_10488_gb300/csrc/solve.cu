@@ -24,12 +24,16 @@ int SiState::init(rte_batch_t b, const rte_solve_opts& opts, rte_rom_t rom_c, do
   result = result_dst;
   mixed = o.fp32_switch > 0.0 && b->disc->dim == 2;
   if (!hm) {
-    RTE_CUDA_TRY(cudaHostAlloc((void**)&hm, 6 * (size_t)B, cudaHostAllocDefault));
+    RTE_CUDA_TRY(cudaHostAlloc((void**)&hm, 8 * (size_t)B, cudaHostAllocDefault));
     RTE_CUDA_TRY(cudaHostAlloc((void**)&hn, sizeof(unsigned long long) * 2 * B, cudaHostAllocDefault));
-    RTE_TRY(dm.alloc(6 * (size_t)B));
+    RTE_TRY(dm.alloc(8 * (size_t)B));
     RTE_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   }
-  std::memset(hm, 0, 6 * (size_t)B);
+  std::memset(hm, 0, 8 * (size_t)B);
+  cudaPointerAttributes pa{};
+  result_dev = cudaPointerGetAttributes(&pa, result) == cudaSuccess &&
+               pa.type == cudaMemoryTypeDevice;
+  cudaGetLastError();   // a pointer the runtime does not know is not an error here
   act.assign(B, 0);
   lowp.assign(B, 0);
   done.assign(B, 0);
@@ -97,6 +101,34 @@ int si_launch(SiState& s, cudaStream_t st, double* psi_cur) {
   return RTE_OK;
 }
 
+// dst[b] = src[b] for the instances flagged in `mask` (results of finished instances).
+__global__ void copy_rows_kernel(double* dst, const double* src, const uint8_t* mask, int n_dof) {
+  const int b = blockIdx.y;
+  if (!mask[b]) return;
+  const size_t o = (size_t)b * n_dof;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_dof; e += gridDim.x * blockDim.x)
+    dst[o + e] = src[o + e];
+}
+
+// Copies the rows of the finished instances flagged in hflag (host) / dflag (device) from src to
+// s.result: one kernel when the result is in device memory, else one copy per instance.
+static int copy_finished(SiState& s, const double* src, const uint8_t* hflag, const uint8_t* dflag,
+                         int n_fin, cudaStream_t st) {
+  if (n_fin == 0) return RTE_OK;
+  const int n = s.bt->disc->n_dof;
+  if (s.result_dev) {
+    dim3 grid(std::min((n + 255) / 256, 256), s.B);
+    copy_rows_kernel<<<grid, 256, 0, st>>>(s.result, src, dflag, n); RTE_NOTE_LAUNCH();
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+  }
+  for (int b = 0; b < s.B; ++b)
+    if (hflag[b])
+      RTE_CUDA_TRY(cudaMemcpyAsync(s.result + (size_t)b * n, src + (size_t)b * n,
+                                   sizeof(double) * n, cudaMemcpyDefault, st));
+  return RTE_OK;
+}
+
 // Stop test and correction of the iteration launched by si_launch.  Finished instances (converged,
 // or at the iteration cap) have their result copied to s.result and are flagged in s.done.
 int si_finish(SiState& s, cudaStream_t st, double* history) {
@@ -112,10 +144,11 @@ int si_finish(SiState& s, cudaStream_t st, double* history) {
   double* R = bt->work.p + 2 * nb;
   double* drho = bt->work.p + 3 * nb;
   uint8_t *h_corr = s.hm + 3 * B, *h_rom = s.hm + 4 * B, *h_dsa = s.hm + 5 * B;
-  std::vector<uint8_t> expire(B, 0);
+  uint8_t *h_conv = s.hm + 6 * B, *h_exp = s.hm + 7 * B;
+  int n_conv = 0, n_exp = 0;
   bool any = false, anyd = false, anyr = false;
   for (int b = 0; b < B; ++b) {
-    h_corr[b] = h_rom[b] = h_dsa[b] = 0;
+    h_corr[b] = h_rom[b] = h_dsa[b] = h_conv[b] = h_exp[b] = 0;
     if (!s.act[b]) continue;
     const int l = ++s.it[b];
     double delta, rinf;
@@ -135,11 +168,10 @@ int si_finish(SiState& s, cudaStream_t st, double* history) {
       s.act[b] = 0;
       s.done[b] = 1;
       s.status[b] = RTE_OK;
-      RTE_CUDA_TRY(cudaMemcpyAsync(s.result + b * n, rho_star + b * n, sizeof(double) * n,
-                                   cudaMemcpyDefault, st));
+      h_conv[b] = 1, n_conv++;
       continue;
     }
-    if (l >= o.max_iter) expire[b] = 1;
+    if (l >= o.max_iter) h_exp[b] = 1, n_exp++;
     any = true;
     h_corr[b] = 1;
     if (o.sa == RTE_SA_NONE) continue;
@@ -149,8 +181,10 @@ int si_finish(SiState& s, cudaStream_t st, double* history) {
     if (romsa) h_rom[b] = 1, rp.n_romsa++, anyr = true;
     else h_dsa[b] = 1, rp.n_dsa++, anyd = true;
   }
+  if (any || n_conv || n_exp)
+    RTE_CUDA_TRY(cudaMemcpyAsync(s.dm.p + 3 * B, h_corr, 5 * (size_t)B, cudaMemcpyHostToDevice, st));
+  RTE_TRY(copy_finished(s, rho_star, h_conv, s.dm.p + 6 * B, n_conv, st));
   if (any) {
-    RTE_CUDA_TRY(cudaMemcpyAsync(s.dm.p + 3 * B, h_corr, 3 * (size_t)B, cudaMemcpyHostToDevice, st));
     const uint8_t* d_corr = s.dm.p + 3 * B;
     if (o.sa == RTE_SA_NONE) {
       // plain SI: rho^(l) = rho^(l,*)
@@ -174,13 +208,12 @@ int si_finish(SiState& s, cudaStream_t st, double* history) {
     }
   }
   for (int b = 0; b < B; ++b)
-    if (expire[b]) {
+    if (h_exp[b]) {
       s.act[b] = 0;
       s.done[b] = 1;
       s.status[b] = RTE_ENOCONV;
-      RTE_CUDA_TRY(cudaMemcpyAsync(s.result + b * n, rho_prev + b * n, sizeof(double) * n,
-                                   cudaMemcpyDefault, st));
     }
+  RTE_TRY(copy_finished(s, rho_prev, h_exp, s.dm.p + 7 * B, n_exp, st));
   return RTE_OK;
 }
 
@@ -245,7 +278,7 @@ int event_ready(cudaEvent_t ev, bool* ready) {
 using namespace rte;
 
 static int check_opts(rte_batch_t b, const rte_solve_opts* o, rte_rom_t rom_c) {
-  if (!b->params_set) return fail(RTE_ESTATE, "rte_solve: parameters not set");
+  RTE_TRY(params_ready(b, "rte_solve"));
   if (!(o->eps >= 0) || o->max_iter < 1 || o->sa < 0 || o->sa > 3 || !(o->fp32_switch >= 0))
     return fail(RTE_EINVAL, "rte_solve: bad options");
   if (o->sa != RTE_SA_NONE && b->disc->dim == 2 && (!(o->dsa_rtol >= 0) || o->dsa_max_it < 1))

@@ -109,23 +109,26 @@ __global__ void tables2d_kernel(double* tables, const double* sigma_t, const dou
     }
 }
 
-// One thread per (instance, cell, direction), 1D: M = sigma_t I + (|xi|/h) [[1, s sqrt3],
-// [-s sqrt3, 3]] (s the sign of xi, h the cell's width) and the inflow coupling: a unit face value
-// u entering the cell contributes |xi| u phi_k(inflow face) = (|xi| / sqrt h) (1, -s sqrt3) to the
-// right-hand side.  T = {M^-1 (2x2), M^-1 (|xi| / sqrt h)(1, -s sqrt3), 1 / sqrt h}.
+// One thread per (instance, cell, direction), 1D: M = Sigma_t + (|xi|/h) [[1, s sqrt3],
+// [-s sqrt3, 3]] (s the sign of xi, h the cell's width; Sigma_t = sigma_t I, or the 2x2 of
+// linear_sigma when the cross sections are linear across cells) and the inflow coupling: a unit
+// face value u entering the cell contributes |xi| u phi_k(inflow face) = (|xi| / sqrt h)
+// (1, -s sqrt3) to the right-hand side.  T = {M^-1 (2x2), M^-1 (|xi| / sqrt h)(1, -s sqrt3),
+// 1 / sqrt h}.
 __global__ void tables1d_kernel(double* tables, const double* sigma_t, const double* dirs, int B,
                                 int n_mat, int n_cells, int n_dirs, const int32_t* mat,
-                                const double* dx, const uint8_t* mask) {
+                                const int32_t* matr, const double* dx, const uint8_t* mask) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= B * n_cells * n_dirs) return;
   const int d = idx % n_dirs;
   const int c = (idx / n_dirs) % n_cells;
   const int b = idx / (n_dirs * n_cells);
   if (mask && !mask[b]) return;
-  const double st = sigma_t[b * n_mat + mat[c]];
+  double st = sigma_t[b * n_mat + mat[c]], to = 0.0;
+  if (matr) linear_sigma(st, sigma_t[b * n_mat + matr[c]], st, to);
   const double xi = dirs[4 * d], h = dx[c];
   const double s3 = sqrt(3.0), sg = xi < 0 ? -1.0 : 1.0, a = fabs(xi) / h;
-  const double m00 = st + a, m01 = a * sg * s3, m10 = -a * sg * s3, m11 = st + 3.0 * a;
+  const double m00 = st + a, m01 = to + a * sg * s3, m10 = to - a * sg * s3, m11 = st + 3.0 * a;
   const double det = m00 * m11 - m01 * m10;
   const double i00 = m11 / det, i01 = -m01 / det, i10 = -m10 / det, i11 = m00 / det;
   const double q = 1.0 / sqrt(h), e0 = fabs(xi) * q, e1 = -sg * s3 * fabs(xi) * q;
@@ -447,6 +450,7 @@ struct Sweep1DArgs {
   const double* G0;
   const double* inflow;
   const int32_t* mat;
+  const int32_t* matr;      // material at each cell's right end (linear cross sections) or null
   const double* dirs;
   int B, nx, n_dof, n_mat, n_dirs, with_source;
 };
@@ -477,8 +481,17 @@ __global__ void sweep1d_kernel(const Sweep1DArgs A) {
     const int m = A.mat[c];
     const double* T = tab + ((size_t)c * A.n_dirs + d) * kTab1D;
     const double ss = A.sigma_s[(size_t)b * A.n_mat + m];
-    const double s0 = fma(ss, rin[2 * c], A.with_source ? A.G0[(size_t)b * A.nx + c] : 0.0);
-    const double s1 = ss * rin[2 * c + 1];
+    const double g0 = A.with_source ? A.G0[(size_t)b * A.nx + c] : 0.0;
+    double s0, s1;
+    if (A.matr) {   // Sigma_s = [[sb, so], [so, sb]]
+      double sb, so;
+      linear_sigma(ss, A.sigma_s[(size_t)b * A.n_mat + A.matr[c]], sb, so);
+      s0 = fma(sb, rin[2 * c], fma(so, rin[2 * c + 1], g0));
+      s1 = fma(so, rin[2 * c], sb * rin[2 * c + 1]);
+    } else {
+      s0 = fma(ss, rin[2 * c], g0);
+      s1 = ss * rin[2 * c + 1];
+    }
     const double a0 = fma(T[4], u, fma(T[1], s1, T[0] * s0));
     const double a1 = fma(T[5], u, fma(T[3], s1, T[2] * s0));
     u = fma(c3, a1, a0) * T[6];
@@ -574,6 +587,24 @@ __global__ void correction_source_kernel(const double* rs, const double* rp, dou
   }
 }
 
+// The same in 1D with sigma_s linear across cells: one thread per cell applies the 2x2 of
+// linear_sigma (both moments read before either is written, so R may alias rs or rp).
+__global__ void correction_source1d_linear_kernel(const double* rs, const double* rp, double* R,
+                                                  const double* sigma_s, const int32_t* mat,
+                                                  const int32_t* matr, const uint8_t* active,
+                                                  int nx, int n_mat) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nx; c += gridDim.x * blockDim.x) {
+    const size_t o = (size_t)b * 2 * nx + 2 * c;
+    double sb, so;
+    linear_sigma(sigma_s[(size_t)b * n_mat + mat[c]], sigma_s[(size_t)b * n_mat + matr[c]], sb, so);
+    const double d0 = rs[o] - rp[o], d1 = rs[o + 1] - rp[o + 1];
+    R[o] = fma(sb, d0, so * d1);
+    R[o + 1] = fma(so, d0, sb * d1);
+  }
+}
+
 __global__ void add_kernel(const double* x, const double* y, double* out, const uint8_t* active,
                            int n_dof) {
   const int b = blockIdx.y;
@@ -597,7 +628,8 @@ int setup_tables(rte_batch_t bt, cudaStream_t st, const uint8_t* mask) {
     const int n1 = bt->B * d->n_cells * d->n_dirs;
     tables1d_kernel<<<(n1 + th - 1) / th, th, 0, st>>>(bt->tables.p, bt->sigma_t.p, d->dir_dev.p,
                                                        bt->B, d->n_mat, d->n_cells, d->n_dirs,
-                                                       d->mat_id.p, d->dx_dev.p, mask); RTE_NOTE_LAUNCH();
+                                                       d->mat_id.p, d->mat_r.p, d->dx_dev.p,
+                                                       mask); RTE_NOTE_LAUNCH();
   }
   RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;
@@ -712,7 +744,7 @@ int sweep_launch(rte_batch_t bt, const double* rho_in, double* rho_out, double* 
     }
   } else {
     Sweep1DArgs A{rho_in,      bt->partial.p, psi_out,  active, bt->tables.p, bt->sigma_s.p,
-                  bt->G0.p,    bt->inflow.p,  d->mat_id.p, d->dir_dev.p, bt->B, d->nx,
+                  bt->G0.p,    bt->inflow.p,  d->mat_id.p, d->mat_r.p, d->dir_dev.p, bt->B, d->nx,
                   d->n_dof,    d->n_mat,      d->n_dirs, with_source};
     const int n = bt->B * d->n_dirs;
     sweep1d_kernel<<<(n + 63) / 64, 64, 0, st>>>(A); RTE_NOTE_LAUNCH();
@@ -752,6 +784,13 @@ int norms_to_host(rte_batch_t bt, double* host, cudaStream_t st) {
 int correction_source_launch(rte_batch_t bt, const double* rs, const double* rp, double* R,
                              const uint8_t* active, cudaStream_t st) {
   const rte_disc_s* d = bt->disc;
+  if (d->linear) {
+    dim3 grid1(std::min((d->nx + 255) / 256, 1024), bt->B);
+    correction_source1d_linear_kernel<<<grid1, 256, 0, st>>>(rs, rp, R, bt->sigma_s.p, d->mat_id.p,
+                                                             d->mat_r.p, active, d->nx, d->n_mat); RTE_NOTE_LAUNCH();
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+  }
   dim3 grid(std::min((d->n_dof + 255) / 256, 1024), bt->B);
   correction_source_kernel<<<grid, 256, 0, st>>>(rs, rp, R, bt->sigma_s.p, d->mat_id.p, active,
                                                  d->n_dof, d->P, d->n_mat); RTE_NOTE_LAUNCH();
@@ -775,7 +814,7 @@ using namespace rte;
 extern "C" int rte_sweep(rte_batch_t b, const double* rho_in, double* rho_out, double* psi_out,
                          int with_source, const uint8_t* active, void* stream) {
   if (!b || !rho_in || !rho_out) return fail(RTE_EINVAL, "rte_sweep: null argument");
-  if (!b->params_set) return fail(RTE_ESTATE, "rte_sweep: parameters not set");
+  RTE_TRY(params_ready(b, "rte_sweep"));
   if (rho_in == rho_out) return fail(RTE_EINVAL, "rte_sweep: rho_out aliases rho_in");
   if (((uintptr_t)rho_in | (uintptr_t)rho_out | (uintptr_t)psi_out) & 15)
     return fail(RTE_EINVAL, "rte_sweep: arrays must be 16-byte aligned");
@@ -800,7 +839,7 @@ extern "C" int rte_change_norm(rte_batch_t b, const double* rho_star, const doub
 extern "C" int rte_correction_source(rte_batch_t b, const double* rho_star, const double* rho_prev,
                                      double* R, void* stream) {
   if (!b || !rho_star || !rho_prev || !R) return fail(RTE_EINVAL, "rte_correction_source: null");
-  if (!b->params_set) return fail(RTE_ESTATE, "parameters not set");
+  RTE_TRY(params_ready(b, "rte_correction_source"));
   DeviceGuard g(b->disc->device);
   return correction_source_launch(b, rho_star, rho_prev, R, nullptr, (cudaStream_t)stream);
 }
@@ -828,7 +867,7 @@ int sweep_launch_with_scratch(rte_batch_t bt, const double* rho_in, double* rho_
     }
   } else {
     Sweep1DArgs A{rho_in,      partial,       nullptr,  nullptr, bt->tables.p, bt->sigma_s.p,
-                  bt->G0.p,    bt->inflow.p,  d->mat_id.p, d->dir_dev.p, bt->B, d->nx,
+                  bt->G0.p,    bt->inflow.p,  d->mat_id.p, d->mat_r.p, d->dir_dev.p, bt->B, d->nx,
                   d->n_dof,    d->n_mat,      d->n_dirs, with_source};
     const int n = bt->B * d->n_dirs;
     sweep1d_kernel<<<(n + 63) / 64, 64, 0, st>>>(A); RTE_NOTE_LAUNCH();
@@ -1178,7 +1217,7 @@ static int autotune(rte_batch_t bt, cudaStream_t st, int* n_entries, int* table)
 
 extern "C" int rte_batch_autotune(rte_batch_t b, void* stream, int* n_entries, int* table) {
   if (!b) return fail(RTE_EINVAL, "rte_batch_autotune: null argument");
-  if (!b->params_set) return fail(RTE_ESTATE, "rte_batch_autotune: parameters not set");
+  RTE_TRY(params_ready(b, "rte_batch_autotune"));
   if (n_entries) *n_entries = 0;
   if (b->disc->dim != 2) return RTE_OK;
   DeviceGuard g(b->disc->device);

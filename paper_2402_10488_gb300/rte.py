@@ -37,6 +37,7 @@ SIGNATURES = {
     "rte_batch_create": (_I, [_P, _I, _P]),
     "rte_batch_destroy": (_I, [_P]),
     "rte_batch_set_params": (_I, [_P, _P, _P, _P, _P]),
+    "rte_batch_set_params_device": (_I, [_P, _P, _P, _P, _P, _P]),
     "rte_batch_directions": (_I, [_P, _P]),
     "rte_sweep": (_I, [_P, _P, _P, _P, _I, _P, _P]),
     "rte_sweep_static": (_I, [_P, _P, _P, _I, _P]),
@@ -108,7 +109,7 @@ def check(status, allow=()):
 class _DiscDesc(ctypes.Structure):
     _fields_ = [("dim", _I), ("nx", _I), ("ny", _I), ("x0", _D), ("x1", _D), ("y0", _D),
                 ("y1", _D), ("n_phi", _I), ("n_vz", _I), ("n_mat", _I), ("mat_id", _P),
-                ("dx", _P)]
+                ("dx", _P), ("mat_id_right", _P)]
 
 
 class _RomOpts(ctypes.Structure):
@@ -183,10 +184,13 @@ class Disc:
         dom = tuple(problem.domain) + ((0.0, 1.0) if problem.dim == 1 else ())
         edges = getattr(problem, "edges", None)
         self._dx = None if edges is None or problem.dim != 1 else _host(np.diff(edges))
+        mat_r = getattr(problem, "mat_id_right", None)
+        self._matr = None if mat_r is None else _host(mat_r, np.int32)
         d = _DiscDesc(problem.dim, problem.nx, problem.ny, dom[0], dom[1], dom[2], dom[3],
                       problem.n_phi, problem.n_vz, problem.n_mat,
                       self._mat.ctypes.data_as(_P),
-                      None if self._dx is None else self._dx.ctypes.data_as(_P))
+                      None if self._dx is None else self._dx.ctypes.data_as(_P),
+                      None if self._matr is None else self._matr.ctypes.data_as(_P))
         h = _P()
         check(L.rte_disc_create(ctypes.byref(d), device, ctypes.byref(h)))
         self.h = h
@@ -238,6 +242,17 @@ class Batch:
         inf = _host(problem.inflow)
         check(lib().rte_batch_set_params(self.h, st.ctypes.data_as(_P), ss.ctypes.data_as(_P),
                                          src.ctypes.data_as(_P), inf.ctypes.data_as(_P)))
+
+    def set_params_device(self, sigma_t, sigma_s, source, inflow, stream=None):
+        """rte_batch_set_params_device: parameters from float64 device tensors [B][n_mat],
+        [B][n_mat], [B][n_cells], [B][2*dim]; asynchronous on `stream`, validated on the device
+        (an invalid value makes the next call that uses the parameters raise)."""
+        for t, shape in ((sigma_t, (self.B, self.disc.n_mat)), (sigma_s, (self.B, self.disc.n_mat)),
+                         (source, (self.B, self.disc.n_cells)), (inflow, (self.B, 2 * self.disc.dim))):
+            if tuple(t.shape) != shape or str(t.dtype) != "torch.float64" or not t.is_cuda:
+                raise ValueError(f"expected a float64 CUDA tensor of shape {shape}")
+        check(lib().rte_batch_set_params_device(self.h, _ptr(sigma_t), _ptr(sigma_s), _ptr(source),
+                                                _ptr(inflow), _stream(stream)))
 
     def set_slots(self, slots, sigma_t, sigma_s, source, inflow, stream=None):
         """Parameters of instances `slots` only (rte_batch_set_slots)."""

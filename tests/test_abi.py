@@ -24,7 +24,7 @@ def test_library_builds_and_exports_every_declared_symbol():
     missing = [s for s in syms if not hasattr(L, s)]
     assert not missing, missing
     assert set(syms) == set(rte.SIGNATURES), set(syms) ^ set(rte.SIGNATURES)
-    assert L.rte_version() == 10300
+    assert L.rte_version() == 10400
 
 
 def test_calls_without_gpu_fail_cleanly():
@@ -46,6 +46,7 @@ def test_boundary_rejects_bad_arguments_before_touching_the_device():
     import numpy as np
     L = rte.lib()
     mat = np.zeros(4, np.int32)
+    right_bad = np.array([0, 0, 1, 0], np.int32)     # material 1 with n_mat = 1
 
     def desc(**kw):
         base = dict(dim=1, nx=4, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, n_phi=4, n_vz=0, n_mat=1,
@@ -55,7 +56,10 @@ def test_boundary_rejects_bad_arguments_before_touching_the_device():
 
     bad = [desc(dim=3), desc(nx=0), desc(ny=2), desc(x1=0.0), desc(n_mat=0), desc(n_phi=3),
            desc(dim=2, ny=1, n_phi=5, n_vz=2), desc(dim=2, ny=1, n_phi=4, n_vz=0),
-           desc(mat_id=None)]
+           desc(mat_id=None),
+           # linear cross sections: right-end material out of range; a right-end map in 2D
+           desc(mat_id_right=right_bad.ctypes.data_as(ctypes.c_void_p)),
+           desc(dim=2, nx=2, ny=2, n_phi=4, n_vz=2, mat_id_right=mat.ctypes.data_as(ctypes.c_void_p))]
     for d in bad:
         h = ctypes.c_void_p()
         assert L.rte_disc_create(ctypes.byref(d), 0, ctypes.byref(h)) == rte.RTE_EINVAL
