@@ -34,16 +34,21 @@ METRIC = "solves/s at 1e-6 φ error (ROMSAD vs SI-DSA, same GPU); sweep GB/s; p5
 FP64_PEAK_TFLOPS = 1.25     # GB300 FP64 rate from the profiling recipe's unit table (nominal)
 FLOP_PER_CELL_DIR = 80      # 40 FMA per cell and distinct direction
 BYTES_PER_CELL_SWEEP = 76   # rho_in 32 B + G0 8 B + material id 4 B + rho_out 32 B
-# DRAM bytes per sweep launch from the committed ncu capture, valid only for this kernel source
-NCU_TRAFFIC = {"sha1": "4ae0cfbc012c24a503da42c8d4216cb3c1af0052", "bytes_per_launch": 666794475,
+# DRAM bytes per sweep launch from the committed ncu capture, valid only for the 2D sweep
+# kernels' device code it was taken with (sha1 of that part of sweep.cu, sweep_source_sha1)
+NCU_TRAFFIC = {"sha1": "43f50fcc7cc28c1bd6f29d15beb2de4541d29128", "bytes_per_launch": 665419989,
                "batch": 152, "n": 128, "angles": 64,
                "workload": "lattice128x128_CL(16,4) batch 152, mean of the 12 sweep launches of "
                            "one ROMSAD step (profiles/sweep2d_traffic_lattice128_b152.md)"}
 
 
 def sweep_source_sha1():
+    """sha1 of the 2D sweep kernels' device code: sweep.cu from the kernels' argument struct to
+    the 1D sweep's, which holds sweep2d_kernel, sweep2d_kba_kernel and the cell-source kernel."""
     with open(os.path.join(ROOT, "paper_2402_10488_gb300", "csrc", "sweep.cu"), "rb") as fh:
-        return hashlib.sha1(fh.read()).hexdigest()
+        src = fh.read()
+    a, b = src.find(b"struct Sweep2DArgs {"), src.find(b"struct Sweep1DArgs {")
+    return hashlib.sha1(src[a:b] if 0 <= a < b else src).hexdigest()
 
 
 def parse():

@@ -682,22 +682,24 @@ static int kba_steps(int nx, int ny, int NW) {
   return (nrb - 1) * D + nx + H - 1;
 }
 
-// Warps per direction group for a launch: more than one only when the launch would leave SM
-// sub-partitions without a warp (each warp then has its sub-partition's FP64 unit to itself),
-// no more than there are row blocks to share, and only when the pipelined sweep is at least 10%
-// shorter than one warp walking all row blocks.
-static int kba_warps(const rte_disc_s* d, int n_sm, long long warps) {
+// Warps per direction group for a launch (one CTA per group).  Cost model: the launch takes the
+// pipelined sweep's steps times the warps sharing the busiest SM sub-partition's FP64 unit, with
+// the CTAs spread evenly over the SMs (ceil(ctas / n_sm) on the busiest) and each SM's warps over
+// its four sub-partitions.  More than one warp only when that cost is at least 10% below one warp
+// walking all row blocks, and no more warps than row blocks.
+static int kba_warps(const rte_disc_s* d, int n_sm, long long ctas) {
   const int H = d->nx < 32 ? d->nx : 32;
   const int nrb = (d->ny + H - 1) / H;
-  if (nrb < 2 || warps <= 0 || 2 * warps > 4LL * n_sm) return 1;
-  const int max_nw = (int)std::min<long long>(std::min(nrb, 8), 4LL * n_sm / warps);
-  const int single = nrb * d->nx + H - 1;
-  int best = 1, best_steps = single;
-  for (int nw = 2; nw <= max_nw; ++nw) {
-    const int st = kba_steps(d->nx, d->ny, nw);
-    if (st < best_steps) best = nw, best_steps = st;
+  if (nrb < 2 || ctas <= 0) return 1;
+  const long long per_sm = (ctas + n_sm - 1) / n_sm;
+  const long long single = (long long)(nrb * d->nx + H - 1) * ((per_sm + 3) / 4);
+  int best = 1;
+  long long best_cost = single;
+  for (int nw = 2; nw <= std::min(nrb, 8); ++nw) {
+    const long long cost = (long long)kba_steps(d->nx, d->ny, nw) * ((per_sm * nw + 3) / 4);
+    if (cost < best_cost) best = nw, best_cost = cost;
   }
-  return best_steps < 0.9 * single ? best : 1;
+  return best_cost < 0.9 * single ? best : 1;
 }
 
 int sweep_launch(rte_batch_t bt, const double* rho_in, double* rho_out, double* psi_out,
