@@ -222,3 +222,51 @@ def test_pipelined_multi_warp_sweep_matches_oracle(nx, ny):
     for k, (vx, vy, w, mult) in enumerate(batch.directions()):
         j = int(np.argmin(np.abs(tr.v[:, 0] - vx) + np.abs(tr.v[:, 1] - vy)))
         assert np.abs(psi[0, k] - f[j]).max() < RTOL * np.abs(f[j]).max() * 10
+
+
+def _corner(problem, b, i0, j0, k, rho):
+    """The k x k block of cells starting at (i0, j0) as a problem of its own, with the block's
+    materials, sources, incoming scalar flux and the domain's inflow values (only the sides that
+    are domain sides matter for the directions compared)."""
+    n = problem.nx
+    cells = np.array([(j0 + j) * n + (i0 + i) for j in range(k) for i in range(k)])
+    h = (problem.domain[1] - problem.domain[0]) / n
+    sub = inputs.Problem(2, k, k, (0.0, k * h, 0.0, k * h), "cl", problem.n_phi, problem.n_vz,
+                         problem.mat_id[cells].astype(np.int32), problem.sigma_t[b:b + 1].copy(),
+                         problem.sigma_s[b:b + 1].copy(), problem.source[b:b + 1, cells].copy(),
+                         problem.inflow[b:b + 1].copy(), None, "corner")
+    sub_rho = rho.reshape(-1, 4)[cells].reshape(-1)
+    return sub, cells, sub_rho
+
+
+@pytest.mark.slow
+def test_sweep_at_the_largest_serving_size_matches_oracle_in_the_inflow_corners():
+    """256 x 256 cells, CL(64,4) (128 distinct directions; the largest mesh and angle count of the
+    serving workload), random materials and inflow on every side, two instances.  A direction of
+    quadrant (sx, sy) sees, in the k x k block of cells at its inflow corner, only that block and
+    the inflow on the two domain sides it enters through, so the oracle solves that block alone and
+    its angular flux must equal the GPU's there, for every direction of the quadrant.  The scalar
+    flux is the weighted sum of the GPU's own angular fluxes (the fused reduction) everywhere."""
+    rte = _rte()
+    N, k = 256, 12
+    p = inputs.random_2d(N, 64, 4, 3, seed=23, B=2, inflow=(0.5, 1.0, 0.2, 0.7))
+    rho_in = np.random.default_rng(21).uniform(0, 1, size=(2, p.n_dof))
+    batch, rho_out, psi = _gpu_sweep(rte, p, rho_in, psi=True)
+    dirs = batch.directions()
+    w = np.array([d[2] for d in dirs])
+    recon = np.einsum("k,bkn->bn", w, psi)
+    assert np.abs(recon - rho_out).max() <= 1e-13 * np.abs(rho_out).max()
+    for b in range(2):
+        for sx, sy in ((1, 1), (-1, 1), (1, -1), (-1, -1)):
+            i0 = 0 if sx > 0 else N - k
+            j0 = 0 if sy > 0 else N - k
+            sub, cells, sub_rho = _corner(p, b, i0, j0, k, rho_in[b])
+            tr = Transport(sub, 0)
+            _, f = tr.sweep(sub_rho, store_f=True)
+            dof = (cells[:, None] * 4 + np.arange(4)[None, :]).reshape(-1)
+            for kd, (vx, vy, _, _) in enumerate(dirs):
+                if np.sign(vx) != sx or np.sign(vy) != sy:
+                    continue
+                j = int(np.argmin(np.abs(tr.v[:, 0] - vx) + np.abs(tr.v[:, 1] - vy)))
+                ref = f[j]
+                assert np.abs(psi[b, kd, dof] - ref).max() <= RTOL * np.abs(ref).max() * 10
