@@ -74,8 +74,19 @@ def parse():
                     help="sweep directions per warp (0 = occupancy rule per launch, -1 = measured "
                          "by the autotuner before timing)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--methods", default="romsad,si_dsa,romig,romig_romsad,romsad_mixed,pgmres,"
-                                         "romig_pgmres")
+    ap.add_argument("--refine-kappa", type=float, default=0.1,
+                    help="romsad_refine: FP32 correction sweeps after an FP64 sweep until their "
+                         "change is this fraction of the FP64 one")
+    ap.add_argument("--refine-inner", type=int, default=8,
+                    help="romsad_refine: at most this many FP32 correction sweeps per FP64 sweep")
+    ap.add_argument("--gang-wait", type=int, default=4,
+                    help="romsad_refine: an instance due for an FP64 sweep waits up to this many "
+                         "iterations while others still sweep in FP32 (fuller FP64 launches)")
+    ap.add_argument("--refine-switch", type=float, default=1e-5,
+                    help="romsad_refine: FP32 sweeps (with sources) until the relative change is "
+                         "below this, then the FP64 outer residual correction")
+    ap.add_argument("--methods", default="romsad,si_dsa,romig,romig_romsad,romsad_mixed,"
+                                         "romsad_refine,pgmres,romig_pgmres")
     ap.add_argument("--gmres-rtol", type=float, default=1e-7,
                     help="pgmres: relative residual of the preconditioned system")
     ap.add_argument("--profile-window", action="store_true",
@@ -100,6 +111,18 @@ def parse():
     ap.add_argument("--kappa", type=float, default=0.1,
                     help="mixed/serving: stop at relative change kappa * error target")
     return ap.parse_args()
+
+
+def precision_kw(method, a):
+    """Solver options of the precision variants: romsad_mixed sweeps in FP32 until the change is
+    below --fp32-switch and in FP64 afterwards; romsad_refine follows its FP32 phase with the FP64
+    outer residual correction (FP64 sweeps of the iterate, FP32 sweeps of the error equation)."""
+    if method == "romsad_mixed":
+        return dict(fp32_switch=a.fp32_switch)
+    if method == "romsad_refine":
+        return dict(fp32_switch=a.refine_switch, refine_kappa=a.refine_kappa,
+                    refine_inner=a.refine_inner, gang_wait=a.gang_wait)
+    return {}
 
 
 # ---- multi-process plumbing ----------------------------------------------------------------
@@ -271,9 +294,9 @@ def run_ours(a, ws, rank, local):
             sa, kw = rte.SA_DSA, {}
         elif method == "romsad":
             sa, kw = rte.SA_ROMSAD, dict(rom_c=rom_c, theta=5, eps_romsad=eps_romsad)
-        elif method == "romsad_mixed":
+        elif method in ("romsad_mixed", "romsad_refine"):
             sa, kw = rte.SA_ROMSAD, dict(rom_c=rom_c, theta=5, eps_romsad=eps_romsad,
-                                         fp32_switch=a.fp32_switch)
+                                         **precision_kw(method, a))
         elif method == "romig_romsad":
             rom_p.initial_guess(batch, rho)
             sa, kw = rte.SA_ROMSAD, dict(rom_c=rom_ci, theta=5, eps_romsad=eps_romsad_i)
@@ -471,9 +494,8 @@ def run_mixed(a, ws, rank, local):
                   dsa_max_it=a.dsa_vcycles if a.dsa_rtol == 0 else 100)
         if method == "si_dsa":
             return rte.solve_opts(eps, rte.SA_DSA, **kw), None
-        fp = a.fp32_switch if method == "romsad_mixed" else 0.0
         return (rte.solve_opts(eps, rte.SA_ROMSAD, theta=5, eps_romsad=k["eps_romsad"],
-                               fp32_switch=fp, **kw), k["rom_c"])
+                               **precision_kw(method, a), **kw), k["rom_c"])
 
     def step(method):
         for k in B:
@@ -486,7 +508,8 @@ def run_mixed(a, ws, rank, local):
                                   streams=[k["stream"] for k in B])
         return reps
 
-    methods = [m for m in a.methods.split(",") if m in ("romsad", "si_dsa", "romsad_mixed")]
+    methods = [m for m in a.methods.split(",")
+               if m in ("romsad", "si_dsa", "romsad_mixed", "romsad_refine")]
     results = {}
     clocks = ClockSampler(local)
     clocks.start()
@@ -591,9 +614,9 @@ def run_serving(a, ws, rank, local):
             if method == "si_dsa":
                 ids[key] = srv.add_bucket(bt, None, None, sa=rte.SA_DSA, **kw)
             else:
-                fp = a.fp32_switch if method == "romsad_mixed" else 0.0
                 ids[key] = srv.add_bucket(bt, None, b["rom_c"], sa=rte.SA_ROMSAD, theta=5,
-                                          eps_romsad=b["eps_romsad"], fp32_switch=fp, **kw)
+                                          eps_romsad=b["eps_romsad"], **precision_kw(method, a),
+                                          **kw)
             keep.append(bt)
         srv.start()
         # warm-up: one request per bucket
@@ -622,7 +645,8 @@ def run_serving(a, ws, rank, local):
             bt.close()
         return out, st0, st1, n_launch
 
-    methods = [m for m in a.methods.split(",") if m in ("romsad", "si_dsa", "romsad_mixed")]
+    methods = [m for m in a.methods.split(",")
+               if m in ("romsad", "si_dsa", "romsad_mixed", "romsad_refine")]
     results = {}
     clocks = ClockSampler(local)
     clocks.start()

@@ -328,6 +328,21 @@ typedef struct {
                           sweeps in FP32 until its stop-test quantity falls below fp32_switch,
                           then in FP64 until the stop test fires, so the FP64 sweeps supply the
                           final digits (the fixed point is the FP64 one)                      */
+  double refine_kappa; /* FP64 outer residual correction (2D): 0 -- off; > 0 -- an FP64 sweep
+                          of the iterate x0 that does not stop the instance gives y0 = L x0 + b
+                          and the residual r = y0 - x0 (Eq. (rho_matrix_vec): (I - L) e = r for
+                          the error e of x0).  The following sweeps iterate e alone in FP32
+                          (rho^(l,*) = y0 + L (rho^(l-1) - x0), so FP32 rounding only touches the
+                          small e; the corrections are Alg. 1's), until the change falls below
+                          refine_kappa x the FP64 change or refine_inner FP32 sweeps are done;
+                          then the next sweep is FP64 again.  Only FP64 sweeps take the stop
+                          test.  Combines with fp32_switch (its FP32 phase comes first).      */
+  int refine_inner;    /* cap on the FP32 sweeps per outer step (>= 1 when refine_kappa > 0) */
+  int gang_wait;       /* precision variant: 0 -- every instance sweeps at every iteration;
+                          > 0 -- an instance due for an FP64 sweep while other running instances
+                          still sweep in FP32 waits (no sweep, no correction) for up to gang_wait
+                          iterations, so that FP64 sweeps run in fewer, fuller launches.  Its
+                          own sequence of iterates is unchanged; only when it runs changes.   */
 } rte_solve_opts;
 
 typedef struct {

@@ -374,7 +374,8 @@ extern "C" int rte_batch_tune(rte_batch_t b, int dpw) {
 }
 
 size_t rte_batch_s::bytes() const {
-  size_t t = 8 * (sigma_t.n + sigma_s.n + G0.n + inflow.n + tables.n + partial.n + S.n + norms.n + work.n);
+  size_t t = 8 * (sigma_t.n + sigma_s.n + G0.n + inflow.n + tables.n + partial.n + S.n + norms.n + work.n +
+                  outer.n);
   t += 4 * (tables32.n + S32.n + partial32.n);
   t += sizeof(rte::SweepGroup) * (groups_dev.n + groups_all_dev.n) + slot_mask.n;
   return t + rte::dsa_bytes(this);

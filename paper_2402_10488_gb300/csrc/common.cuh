@@ -179,6 +179,8 @@ struct rte_batch_s {
   double sweep32_units = 0.0;
   rte::DevBuf<unsigned long long> norms;  // [B][2] stop-test norms as ordered bit patterns
   rte::DevBuf<double> work;               // [B][n_dof] x 4 iteration scratch for rte_solve
+  rte::DevBuf<double> outer;              // [2][B][n_dof] x0, y0 of the FP64 outer residual
+                                          // correction (rte_solve_opts.refine_kappa), on first use
   rte::DsaState* dsa = nullptr;
   int dsa_nu = 2;                         // red-black smoothing sweeps per multigrid level (2D DSA)
   // pinned host staging for per-slot parameter uploads (rte_batch_set_slots), allocated on use
@@ -235,8 +237,12 @@ int sweep_launch(rte_batch_t b, const double* rho_in, double* rho_out, double* p
                  int with_source, const uint8_t* active, cudaStream_t st, bool fuse_norms,
                  int n_active = -1, bool zero_norms = true);
 int norms_to_host(rte_batch_t b, double* host, cudaStream_t st);
+// FP32 sweep; the instances flagged in `inner` sweep the error rho_in - x0 without sources and
+// get y0 added in the reduction (the correction sweeps of the FP64 outer residual correction)
 int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, const uint8_t* active,
-                     cudaStream_t st, int n_active, bool zero_norms = true);
+                     cudaStream_t st, int n_active, bool zero_norms = true,
+                     const uint8_t* inner = nullptr, const double* x0 = nullptr,
+                     const double* y0 = nullptr);
 int setup_tables(rte_batch_t b, cudaStream_t st, const uint8_t* mask = nullptr);
 size_t dsa_bytes(const rte_batch_s* b);
 // per-slot parameter upload: instances slots[0..n) take the given parameters (host arrays)
@@ -289,14 +295,18 @@ struct SiState {
   rte_solve_opts o{};
   rte_rom_t rom = nullptr;
   bool mixed = false;                 // FP32 sweeps until the change drops below fp32_switch
-  uint8_t* hm = nullptr;              // pinned [8][B]: act, lo, hi (sweep) | act, rom, dsa
-                                      // (correction) | converged, expired (result copies)
+  bool refine = false;                // FP64 outer residual correction with FP32 inner sweeps
+  uint8_t* hm = nullptr;              // pinned [10][B]: act, lo, hi, inner (sweep) | act, rom,
+                                      // dsa, enter (correction) | converged, expired (result
+                                      // copies); enter = the FP64 sweep just done is an outer point
   unsigned long long* hn = nullptr;   // pinned [2B] stop-test norms (ordered bit patterns)
   DevBuf<uint8_t> dm;                 // device copy of hm
   cudaEvent_t ev = nullptr;           // recorded after the norms copy
   std::vector<uint8_t> act, lowp, done;
-  std::vector<int> it, status;
-  std::vector<double> eps;
+  std::vector<uint8_t> inner;         // the next sweep is an FP32 correction sweep
+  std::vector<uint8_t> swept;         // swept in the launch in flight (not waiting, gang_wait)
+  std::vector<int> it, status, n_inner, waited;
+  std::vector<double> eps, outer_test;  // outer_test: stop-test quantity of the last FP64 sweep
   std::vector<rte_solve_report> rep;
   bool in_flight = false;
   double* result = nullptr;           // [B][n_dof] destination of finished instances (device or pinned host)

@@ -935,7 +935,7 @@ extern "C" int rte_rom_build(rte_batch_t train, const rte_rom_opts* opts, rte_ro
   RTE_TRY(rho.alloc((size_t)B * d->n_dof));
   RTE_CUDA_TRY(cudaMemsetAsync(rho.p, 0, sizeof(double) * B * d->n_dof, st));
   rte_solve_opts so{opts->eps_train, 0, opts->max_iter, RTE_SA_DSA, 0, 0.0,
-                    opts->dsa_rtol > 0 ? opts->dsa_rtol : 1e-12, 2000, nullptr, 0.0};
+                    opts->dsa_rtol > 0 ? opts->dsa_rtol : 1e-12, 2000, nullptr, 0.0, 0.0, 0, 0};
   std::vector<rte_solve_report> rep(B);
   int s = run_si(train, &so, nullptr, rho.p, rep.data(), nullptr, st, psi_cur.p, psi_win.p, w);
   if (s != RTE_OK) return s == RTE_ENOCONV ? fail(RTE_ENOCONV, "training solve did not converge") : s;

@@ -6,6 +6,16 @@
 // eps_ROMSAD.  Instances that have converged drop out of every later launch through a device
 // mask.  The only host round trip per iteration is the 2*B stop-test norms.
 //
+// Precision variant: an instance may sweep in FP32 while its change is above fp32_switch, and with
+// refine_kappa > 0 every FP64 sweep that does not stop it opens an outer residual-correction step:
+// the FP64 sweep y0 = L x0 + b of the iterate x0 gives the residual r = y0 - x0 of
+// (I - L) rho = b (Eq. (rho_matrix_vec)), and the following sweeps solve (I - L) e = r for the
+// error e = rho - x0 by the same SI iterations (DSA / ROMSA corrections unchanged) with the sweep of
+// e in FP32, rho^(l,*) = y0 + L (rho^(l-1) - x0), until the change is refine_kappa times smaller
+// than the FP64 one; then the next FP64 sweep evaluates the new residual.  FP32 rounding thus only
+// enters through e, which shrinks from one outer step to the next, and the stop test sees FP64
+// sweeps only.
+//
 // The iteration is a small state machine per batch (SiState): instances are slots that may
 // start at different iterations (serving), and si_launch / si_finish only enqueue work, so one
 // host thread keeps several batches of different discretisations busy on their own streams
@@ -23,13 +33,16 @@ int SiState::init(rte_batch_t b, const rte_solve_opts& opts, rte_rom_t rom_c, do
   rom = rom_c;
   result = result_dst;
   mixed = o.fp32_switch > 0.0 && b->disc->dim == 2;
+  refine = o.refine_kappa > 0.0 && b->disc->dim == 2;
+  if (refine && b->outer.n < 2 * (size_t)B * b->disc->n_dof)
+    RTE_TRY(b->outer.alloc(2 * (size_t)B * b->disc->n_dof));
   if (!hm) {
-    RTE_CUDA_TRY(cudaHostAlloc((void**)&hm, 8 * (size_t)B, cudaHostAllocDefault));
+    RTE_CUDA_TRY(cudaHostAlloc((void**)&hm, 10 * (size_t)B, cudaHostAllocDefault));
     RTE_CUDA_TRY(cudaHostAlloc((void**)&hn, sizeof(unsigned long long) * 2 * B, cudaHostAllocDefault));
-    RTE_TRY(dm.alloc(8 * (size_t)B));
+    RTE_TRY(dm.alloc(10 * (size_t)B));
     RTE_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   }
-  std::memset(hm, 0, 8 * (size_t)B);
+  std::memset(hm, 0, 10 * (size_t)B);
   cudaPointerAttributes pa{};
   result_dev = cudaPointerGetAttributes(&pa, result) == cudaSuccess &&
                pa.type == cudaMemoryTypeDevice;
@@ -37,9 +50,14 @@ int SiState::init(rte_batch_t b, const rte_solve_opts& opts, rte_rom_t rom_c, do
   act.assign(B, 0);
   lowp.assign(B, 0);
   done.assign(B, 0);
+  inner.assign(B, 0);
+  swept.assign(B, 0);
   it.assign(B, 0);
+  n_inner.assign(B, 0);
+  waited.assign(B, 0);
   status.assign(B, RTE_OK);
   eps.assign(B, o.eps);
+  outer_test.assign(B, 0.0);
   rep.assign(B, rte_solve_report{0, 0, 0, 0, 0, 0.0, 0.0, 0});
   in_flight = false;
   return RTE_OK;
@@ -49,7 +67,11 @@ void SiState::begin(int b, double eps_b) {
   act[b] = 1;
   lowp[b] = mixed ? 1 : 0;
   done[b] = 0;
+  inner[b] = 0;
+  swept[b] = 0;
   it[b] = 0;
+  n_inner[b] = 0;
+  waited[b] = 0;
   status[b] = RTE_OK;
   eps[b] = eps_b;
   rep[b] = rte_solve_report{0, 0, 0, 0, 0, 0.0, 0.0, 0};
@@ -68,29 +90,47 @@ SiState::~SiState() {
 }
 
 // One sweep of every running instance: rho^(l,*) = L rho^(l-1) + b (FP32 for instances still in
-// the low-precision phase), then the asynchronous copy of the stop-test norms.
+// the low-precision phase or inside an outer residual-correction step), then the asynchronous copy
+// of the stop-test norms.
 int si_launch(SiState& s, cudaStream_t st, double* psi_cur) {
   rte_batch_t bt = s.bt;
   const int B = s.B;
   const size_t nb = (size_t)B * bt->disc->n_dof;
   double* rho_prev = bt->work.p;
   double* rho_star = bt->work.p + nb;
-  uint8_t *h_act = s.hm, *h_lo = s.hm + B, *h_hi = s.hm + 2 * B;
-  int n_lo = 0, n_hi = 0;
+  uint8_t *h_act = s.hm, *h_lo = s.hm + B, *h_hi = s.hm + 2 * B, *h_in = s.hm + 3 * B;
+  int n_lo = 0, n_hi = 0, n_in = 0;
   for (int b = 0; b < B; ++b) {
-    const bool lo = s.act[b] && s.lowp[b] && psi_cur == nullptr;
-    h_act[b] = s.act[b];
+    const bool in = s.act[b] && s.inner[b] && psi_cur == nullptr;
+    const bool lo = s.act[b] && (s.lowp[b] || in) && psi_cur == nullptr;
+    s.swept[b] = s.act[b];
     h_lo[b] = lo;
     h_hi[b] = s.act[b] && !lo;
-    n_lo += h_lo[b], n_hi += h_hi[b];
+    h_in[b] = in;
+    n_lo += h_lo[b], n_hi += h_hi[b], n_in += in;
+  }
+  if (s.o.gang_wait > 0 && n_lo > 0 && n_hi > 0) {
+    // instances due for an FP64 sweep wait while others still sweep in FP32 (bounded)
+    for (int b = 0; b < B; ++b)
+      if (h_hi[b] && s.waited[b] < s.o.gang_wait) {
+        h_hi[b] = 0, s.swept[b] = 0, n_hi--;
+        s.waited[b]++;
+      }
+  }
+  for (int b = 0; b < B; ++b) {
+    h_act[b] = s.swept[b];
+    if (h_hi[b]) s.waited[b] = 0;
   }
   if (n_lo + n_hi == 0) return RTE_OK;
-  RTE_CUDA_TRY(cudaMemcpyAsync(s.dm.p, s.hm, 3 * (size_t)B, cudaMemcpyHostToDevice, st));
+  RTE_CUDA_TRY(cudaMemcpyAsync(s.dm.p, s.hm, 4 * (size_t)B, cudaMemcpyHostToDevice, st));
   if (n_lo == 0) {
     RTE_TRY(sweep_launch(bt, rho_prev, rho_star, psi_cur, 1, s.dm.p, st, true, n_hi));
   } else {
     RTE_CUDA_TRY(cudaMemsetAsync(bt->norms.p, 0, sizeof(unsigned long long) * 2 * B, st));
-    RTE_TRY(sweep_launch_f32(bt, rho_prev, rho_star, s.dm.p + B, st, n_lo, false));
+    const double* x0 = bt->outer.p;
+    const double* y0 = bt->outer.p ? bt->outer.p + nb : nullptr;
+    RTE_TRY(sweep_launch_f32(bt, rho_prev, rho_star, s.dm.p + B, st, n_lo, false,
+                             n_in ? s.dm.p + 3 * B : nullptr, x0, y0));
     if (n_hi > 0)
       RTE_TRY(sweep_launch(bt, rho_prev, rho_star, psi_cur, 1, s.dm.p + 2 * B, st, true, n_hi, false));
   }
@@ -143,13 +183,13 @@ int si_finish(SiState& s, cudaStream_t st, double* history) {
   double* rho_star = bt->work.p + nb;
   double* R = bt->work.p + 2 * nb;
   double* drho = bt->work.p + 3 * nb;
-  uint8_t *h_corr = s.hm + 3 * B, *h_rom = s.hm + 4 * B, *h_dsa = s.hm + 5 * B;
-  uint8_t *h_conv = s.hm + 6 * B, *h_exp = s.hm + 7 * B;
-  int n_conv = 0, n_exp = 0;
+  uint8_t *h_corr = s.hm + 4 * B, *h_rom = s.hm + 5 * B, *h_dsa = s.hm + 6 * B;
+  uint8_t *h_enter = s.hm + 7 * B, *h_conv = s.hm + 8 * B, *h_exp = s.hm + 9 * B;
+  int n_conv = 0, n_exp = 0, n_enter = 0;
   bool any = false, anyd = false, anyr = false;
   for (int b = 0; b < B; ++b) {
-    h_corr[b] = h_rom[b] = h_dsa[b] = h_conv[b] = h_exp[b] = 0;
-    if (!s.act[b]) continue;
+    h_corr[b] = h_rom[b] = h_dsa[b] = h_enter[b] = h_conv[b] = h_exp[b] = 0;
+    if (!s.act[b] || !s.swept[b]) continue;
     const int l = ++s.it[b];
     double delta, rinf;
     std::memcpy(&delta, &s.hn[2 * b], sizeof(double));
@@ -163,6 +203,12 @@ int si_finish(SiState& s, cudaStream_t st, double* history) {
     if (s.lowp[b]) {
       rp.n_sweep32++;
       if (test < o.fp32_switch) s.lowp[b] = 0;  // later sweeps of this instance in FP64
+    } else if (s.inner[b]) {
+      // FP32 sweep of the correction equation: back to FP64 once the error equation's change is
+      // refine_kappa times below the outer residual, or after refine_inner sweeps
+      rp.n_sweep32++;
+      if (++s.n_inner[b] >= o.refine_inner || test < o.refine_kappa * s.outer_test[b])
+        s.inner[b] = 0;
     } else if (test < s.eps[b]) {
       rp.converged = 1;
       s.act[b] = 0;
@@ -170,6 +216,12 @@ int si_finish(SiState& s, cudaStream_t st, double* history) {
       s.status[b] = RTE_OK;
       h_conv[b] = 1, n_conv++;
       continue;
+    } else if (s.refine) {
+      // this FP64 sweep is the outer point: x0 = rho^(l-1), y0 = rho^(l,*)
+      s.inner[b] = 1;
+      s.n_inner[b] = 0;
+      s.outer_test[b] = test;
+      h_enter[b] = 1, n_enter++;
     }
     if (l >= o.max_iter) h_exp[b] = 1, n_exp++;
     any = true;
@@ -182,10 +234,18 @@ int si_finish(SiState& s, cudaStream_t st, double* history) {
     else h_dsa[b] = 1, rp.n_dsa++, anyd = true;
   }
   if (any || n_conv || n_exp)
-    RTE_CUDA_TRY(cudaMemcpyAsync(s.dm.p + 3 * B, h_corr, 5 * (size_t)B, cudaMemcpyHostToDevice, st));
-  RTE_TRY(copy_finished(s, rho_star, h_conv, s.dm.p + 6 * B, n_conv, st));
+    RTE_CUDA_TRY(cudaMemcpyAsync(s.dm.p + 4 * B, h_corr, 6 * (size_t)B, cudaMemcpyHostToDevice, st));
+  RTE_TRY(copy_finished(s, rho_star, h_conv, s.dm.p + 8 * B, n_conv, st));
+  if (n_enter) {
+    // keep the outer point and its FP64 sweep before the correction overwrites rho_prev
+    const int n = bt->disc->n_dof;
+    dim3 grid(std::min((n + 255) / 256, 256), B);
+    copy_rows_kernel<<<grid, 256, 0, st>>>(bt->outer.p, rho_prev, s.dm.p + 7 * B, n); RTE_NOTE_LAUNCH();
+    copy_rows_kernel<<<grid, 256, 0, st>>>(bt->outer.p + nb, rho_star, s.dm.p + 7 * B, n); RTE_NOTE_LAUNCH();
+    RTE_CUDA_TRY(cudaGetLastError());
+  }
   if (any) {
-    const uint8_t* d_corr = s.dm.p + 3 * B;
+    const uint8_t* d_corr = s.dm.p + 4 * B;
     if (o.sa == RTE_SA_NONE) {
       // plain SI: rho^(l) = rho^(l,*)
       RTE_TRY(axpy_launch(bt, rho_star, nullptr, rho_prev, d_corr, st));
@@ -194,14 +254,14 @@ int si_finish(SiState& s, cudaStream_t st, double* history) {
       if (anyd) {
         std::vector<int> iters(B, 0);
         PhaseScope ps(bt, 1, st);
-        int e = dsa_apply(bt, R, drho, o.dsa_rtol, o.dsa_max_it, s.dm.p + 5 * B, iters.data(), st);
+        int e = dsa_apply(bt, R, drho, o.dsa_rtol, o.dsa_max_it, s.dm.p + 6 * B, iters.data(), st);
         if (e != RTE_OK && e != RTE_ENOCONV) return e;
         for (int b = 0; b < B; ++b)
           if (h_dsa[b]) s.rep[b].dsa_iters += iters[b];
       }
       if (anyr) {
         PhaseScope ps(bt, 2, st);
-        RTE_TRY(rom_correction(s.rom, bt, R, drho, s.dm.p + 4 * B, st));
+        RTE_TRY(rom_correction(s.rom, bt, R, drho, s.dm.p + 5 * B, st));
       }
       // rho^(l) = rho^(l,*) + delta rho^(l), written into the rho_prev slot
       RTE_TRY(axpy_launch(bt, rho_star, drho, rho_prev, d_corr, st));
@@ -213,7 +273,7 @@ int si_finish(SiState& s, cudaStream_t st, double* history) {
       s.done[b] = 1;
       s.status[b] = RTE_ENOCONV;
     }
-  RTE_TRY(copy_finished(s, rho_prev, h_exp, s.dm.p + 7 * B, n_exp, st));
+  RTE_TRY(copy_finished(s, rho_prev, h_exp, s.dm.p + 9 * B, n_exp, st));
   return RTE_OK;
 }
 
@@ -230,7 +290,7 @@ int run_si(rte_batch_t bt, const rte_solve_opts* o, rte_rom_t rom_c, double* rho
     return fail(RTE_EINVAL, "ROMSA/ROMSAD need a correction ROM");
   SiState s;
   rte_solve_opts oo = *o;
-  if (psi_cur) oo.fp32_switch = 0.0;
+  if (psi_cur) oo.fp32_switch = 0.0, oo.refine_kappa = 0.0;
   RTE_TRY(s.init(bt, oo, rom_c, rho));
   RTE_CUDA_TRY(cudaMemcpyAsync(bt->work.p, rho, sizeof(double) * B * n, cudaMemcpyDeviceToDevice, st));
   for (int b = 0; b < B; ++b) s.begin(b, o->eps);
@@ -279,7 +339,8 @@ using namespace rte;
 
 static int check_opts(rte_batch_t b, const rte_solve_opts* o, rte_rom_t rom_c) {
   RTE_TRY(params_ready(b, "rte_solve"));
-  if (!(o->eps >= 0) || o->max_iter < 1 || o->sa < 0 || o->sa > 3 || !(o->fp32_switch >= 0))
+  if (!(o->eps >= 0) || o->max_iter < 1 || o->sa < 0 || o->sa > 3 || !(o->fp32_switch >= 0) ||
+      !(o->refine_kappa >= 0) || (o->refine_kappa > 0 && o->refine_inner < 1) || o->gang_wait < 0)
     return fail(RTE_EINVAL, "rte_solve: bad options");
   if (o->sa != RTE_SA_NONE && b->disc->dim == 2 && (!(o->dsa_rtol >= 0) || o->dsa_max_it < 1))
     return fail(RTE_EINVAL, "rte_solve: bad DSA tolerance");

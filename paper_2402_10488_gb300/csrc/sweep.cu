@@ -891,6 +891,12 @@ int sweep_launch_with_scratch(rte_batch_t bt, const double* rho_in, double* rho_
 // FP32 sources formed once per sweep, FP32 partial sums.  The FP32 units of GB300 run at about 59x
 // the FP64 rate, so these sweeps are cheap; rte_solve uses them for the early iterations of an
 // instance and switches it to the FP64 sweep for the final ones (rte_solve_opts.fp32_switch).
+//
+// Correction sweeps of the FP64 outer residual-correction loop (rte_solve_opts.refine_kappa): for
+// the instances flagged in `inner`, the sweep applies L to the error e = rho - x0 of the outer
+// point x0 alone -- cell sources Sigma_s (rho - x0), no volume source, no inflow -- and the FP64
+// reduction adds y0 = L x0 + b (the FP64 sweep of x0), so rho_out = y0 + L (rho - x0) = L rho + b
+// with FP32 rounding confined to the small e.
 namespace rte {
 
 __global__ void tables_to_f32_kernel(const double* t64, float* t32, size_t n) {
@@ -901,22 +907,32 @@ __global__ void tables_to_f32_kernel(const double* t64, float* t32, size_t n) {
 __global__ void cell_source32_kernel(const double* __restrict__ rho, float* S,
                                      const double* __restrict__ sigma_s,
                                      const double* __restrict__ G0, const int32_t* __restrict__ mat,
-                                     const uint8_t* active, int n_cells, int n_mat, int with_source) {
+                                     const uint8_t* active, int n_cells, int n_mat, int with_source,
+                                     const uint8_t* inner, const double* __restrict__ x0) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_cells) return;
   const double ss = sigma_s[(size_t)b * n_mat + mat[c]];
-  const double* r = rho + ((size_t)b * n_cells + c) * 4;
-  const double s0 = fma(ss, r[0], with_source ? G0[(size_t)b * n_cells + c] : 0.0);
+  const size_t o = ((size_t)b * n_cells + c) * 4;
+  const double* r = rho + o;
+  double4 v = make_double4(r[0], r[1], r[2], r[3]);
+  bool src = with_source;
+  if (inner && inner[b]) {
+    const double* x = x0 + o;
+    v.x -= x[0], v.y -= x[1], v.z -= x[2], v.w -= x[3];
+    src = false;
+  }
+  const double s0 = fma(ss, v.x, src ? G0[(size_t)b * n_cells + c] : 0.0);
   reinterpret_cast<float4*>(S)[(size_t)b * n_cells + c] =
-      make_float4((float)s0, (float)(ss * r[1]), (float)(ss * r[2]), (float)(ss * r[3]));
+      make_float4((float)s0, (float)(ss * v.y), (float)(ss * v.z), (float)(ss * v.w));
 }
 
 struct Sweep2D32Args {
   const float* S;
   float* partial;
   const uint8_t* active;
+  const uint8_t* inner;   // correction sweeps: no inflow
   const float* tables;
   const double* inflow;
   const int32_t* mat;
@@ -946,8 +962,9 @@ __global__ void __launch_bounds__(32) sweep2d_f32_kernel(const Sweep2D32Args A) 
   for (int dd = 0; dd < DPW; ++dd) w[dd] = dd < grp.nd ? (float)A.dirs[4 * (grp.d0 + dd) + 2] : 0.f;
   const float s3 = 1.7320508075688772f;
   const float c3x = xneg ? -s3 : s3, c3y = yneg ? -s3 : s3;
-  const float gxb = A.with_source ? (float)(A.inflow[4 * b + (xneg ? 1 : 0)] * A.sq_area) : 0.f;
-  const float gyb = A.with_source ? (float)(A.inflow[4 * b + (yneg ? 3 : 2)] * A.sq_area) : 0.f;
+  const bool src = A.with_source && !(A.inner && A.inner[b]);
+  const float gxb = src ? (float)(A.inflow[4 * b + (xneg ? 1 : 0)] * A.sq_area) : 0.f;
+  const float gyb = src ? (float)(A.inflow[4 * b + (yneg ? 3 : 2)] * A.sq_area) : 0.f;
   const int H = A.nx < 32 ? A.nx : 32;
   const int nrb = (A.ny + H - 1) / H;
   const int total = nrb * A.nx;
@@ -1030,11 +1047,13 @@ __global__ void __launch_bounds__(32) sweep2d_f32_kernel(const Sweep2D32Args A) 
   }
 }
 
-// rho_out (FP64) = sum of the FP32 group partials (fixed order, summed in FP64); fused norms.
+// rho_out (FP64) = sum of the FP32 group partials (fixed order, summed in FP64), plus y0 for the
+// instances flagged in `inner`; fused norms.
 __global__ void reduce_partials32_kernel(const float* __restrict__ partial,
                                          const double* __restrict__ rho_in, double* rho_out,
                                          unsigned long long* norms, const uint8_t* active,
-                                         int n_groups, int n_dof) {
+                                         int n_groups, int n_dof, const uint8_t* inner,
+                                         const double* __restrict__ y0) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   const int rank = active_rank(active, b);
@@ -1043,6 +1062,10 @@ __global__ void reduce_partials32_kernel(const float* __restrict__ partial,
   if (e < n_dof) {
     const float* p = partial + (size_t)rank * n_groups * n_dof + e;
     double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    if (inner && inner[b]) {
+      const double* y = y0 + (size_t)b * n_dof + e;
+      a0 = y[0], a1 = y[1], a2 = y[2], a3 = y[3];
+    }
     for (int g = 0; g < n_groups; ++g) {
       const float4 v = *reinterpret_cast<const float4*>(p + (size_t)g * n_dof);
       a0 += v.x, a1 += v.y, a2 += v.z, a3 += v.w;
@@ -1095,7 +1118,9 @@ static int launch2d_f32(const Sweep2D32Args& A, int B, int n_groups, cudaStream_
 // One FP32 sweep of the active instances of a 2D batch, partial sums reduced in FP64 into
 // rho_out with the stop-test norms fused (as sweep_launch with fuse_norms).
 int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, const uint8_t* active,
-                     cudaStream_t st, int n_active, bool zero_norms) {
+                     cudaStream_t st, int n_active, bool zero_norms, const uint8_t* inner,
+                     const double* x0, const double* y0) {
+  if (inner && (!x0 || !y0)) return fail(RTE_EINVAL, "FP32 correction sweep without x0, y0");
   const rte_disc_s* d = bt->disc;
   if (d->dim != 2) return fail(RTE_EINVAL, "FP32 sweep: 2D only");
   if (!bt->tables32.p) {
@@ -1121,8 +1146,9 @@ int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, cons
     RTE_CUDA_TRY(cudaEventRecord(ev0, st));
   }
   cell_source32_kernel<<<dim3((d->n_cells + 127) / 128, bt->B), 128, 0, st>>>(
-      rho_in, bt->S32.p, bt->sigma_s.p, bt->G0.p, d->mat_id.p, active, d->n_cells, d->n_mat, 1); RTE_NOTE_LAUNCH();
-  Sweep2D32Args A{bt->S32.p,  bt->partial32.p, active,   bt->tables32.p, bt->inflow.p,
+      rho_in, bt->S32.p, bt->sigma_s.p, bt->G0.p, d->mat_id.p, active, d->n_cells, d->n_mat, 1,
+      inner, x0); RTE_NOTE_LAUNCH();
+  Sweep2D32Args A{bt->S32.p,  bt->partial32.p, active,   inner,    bt->tables32.p, bt->inflow.p,
                   d->mat_id.p, d->dir_dev.p,   gdev,     d->nx,          d->ny,
                   d->n_cells, d->n_dof,        d->n_mat, d->n_dirs,      n_groups,
                   1,          std::sqrt(d->hx * d->hy)};
@@ -1143,7 +1169,7 @@ int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, cons
     RTE_CUDA_TRY(cudaMemsetAsync(bt->norms.p, 0, sizeof(unsigned long long) * 2 * bt->B, st));
   const int th = 256;
   reduce_partials32_kernel<<<dim3((d->n_dof / 4 + th - 1) / th, bt->B), th, 0, st>>>(
-      bt->partial32.p, rho_in, rho_out, bt->norms.p, active, n_groups, d->n_dof); RTE_NOTE_LAUNCH();
+      bt->partial32.p, rho_in, rho_out, bt->norms.p, active, n_groups, d->n_dof, inner, y0); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;
 }

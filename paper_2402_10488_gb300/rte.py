@@ -120,7 +120,8 @@ class _RomOpts(ctypes.Structure):
 class _SolveOpts(ctypes.Structure):
     _fields_ = [("eps", _D), ("rel", _I), ("max_iter", _I), ("sa", _I), ("theta", _I),
                 ("eps_romsad", _D), ("dsa_rtol", _D), ("dsa_max_it", _I), ("schedule", _P),
-                ("fp32_switch", _D)]
+                ("fp32_switch", _D), ("refine_kappa", _D), ("refine_inner", _I),
+                ("gang_wait", _I)]
 
 
 class SolveReport(ctypes.Structure):
@@ -145,12 +146,14 @@ def _report(r):
 
 
 def solve_opts(eps, sa=SA_DSA, rel=False, max_iter=1000, theta=0, eps_romsad=0.0, dsa_rtol=1e-10,
-               dsa_max_it=500, schedule=None, fp32_switch=0.0):
+               dsa_max_it=500, schedule=None, fp32_switch=0.0, refine_kappa=0.0, refine_inner=0,
+               gang_wait=0):
     """rte_solve_opts; `schedule` (uint8 per iteration) is kept alive on the returned struct."""
     sched = None if schedule is None else _host(schedule, np.uint8)
     o = _SolveOpts(float(eps), 1 if rel else 0, int(max_iter), int(sa), int(theta),
                    float(eps_romsad), float(dsa_rtol), int(dsa_max_it),
-                   None if sched is None else sched.ctypes.data_as(_P), float(fp32_switch))
+                   None if sched is None else sched.ctypes.data_as(_P), float(fp32_switch),
+                   float(refine_kappa), int(refine_inner), int(gang_wait))
     o._sched = sched
     return o
 
@@ -329,9 +332,9 @@ class Batch:
 
     def solve(self, rho, eps, sa=SA_DSA, rel=False, max_iter=1000, theta=0, eps_romsad=0.0,
               dsa_rtol=1e-10, dsa_max_it=500, rom_c=None, schedule=None, history=False,
-              fp32_switch=0.0, stream=None):
+              fp32_switch=0.0, refine_kappa=0.0, refine_inner=0, gang_wait=0, stream=None):
         opts = solve_opts(eps, sa, rel, max_iter, theta, eps_romsad, dsa_rtol, dsa_max_it, schedule,
-                          fp32_switch)
+                          fp32_switch, refine_kappa, refine_inner, gang_wait)
         reps = (SolveReport * self.B)()
         hist = np.zeros((self.B, max_iter)) if history else None
         st = check(lib().rte_solve(self.h, ctypes.byref(opts), None if rom_c is None else rom_c.h,

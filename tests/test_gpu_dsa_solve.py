@@ -189,6 +189,65 @@ def test_precision_variant_fp32_then_fp64_sweeps_reaches_the_fp64_solution(sa):
         assert _rel(rho.cpu().numpy()[b], ref["rho"]) < 1e-10
 
 
+@pytest.mark.parametrize("sa,switch", [("dsa", 1e-4), ("romsad", 1e-4), ("dsa", 0.0)])
+def test_fp64_outer_residual_correction_reaches_the_fp64_solution(sa, switch):
+    """FP64 outer residual correction: every FP64 sweep that does not stop an instance is followed
+    by FP32 sweeps of the error equation (I - L) e = r only.  The converged rho is the FP64
+    transport solution (1e-10 against the oracle, as for the FP64 path), and fewer FP64 sweeps are
+    needed than when the FP32 phase is followed by plain FP64 iterations.  switch = 0 starts with an
+    FP64 sweep (no FP32 phase before the first outer step)."""
+    rte = _rte()
+    p = inputs.lattice_test(32, 16, 3, n_vz=2)
+    batch = rte.Batch.from_problem(p)
+    if sa == "romsad":
+        train = inputs.lattice_train(32, 16, n_train=6, n_vz=2)
+        tb = rte.Batch(batch.disc, 6)
+        tb.set_params(train)
+        _, rc = rte.Rom.build(tb, eps_train=1e-12, window=3, rank_p=4, rank_c=6, max_iter=300,
+                              dsa_rtol=1e-10)
+        kw = dict(sa=rte.SA_ROMSAD, rom_c=rc, theta=5, eps_romsad=0.1 * max(1e-12, rc.eps_pod))
+    else:
+        kw = dict(sa=rte.SA_DSA)
+    common = dict(rel=True, max_iter=300, dsa_rtol=0.0, dsa_max_it=2, fp32_switch=switch, **kw)
+    rho = torch.zeros((3, p.n_dof), dtype=torch.float64, device="cuda")
+    rep, hist, st = batch.solve(rho, 1e-13, refine_kappa=0.05, refine_inner=8, history=True,
+                                **common)
+    assert st == 0
+    plain = torch.zeros_like(rho)
+    rep0, _, st0 = batch.solve(plain, 1e-13, **common)
+    assert st0 == 0
+    for b in range(3):
+        tr = Transport(p, b)
+        ref = sisa(tr, np.zeros(tr.n_dof), 1e-14, 400, "dsa", dsa=ConsistentDSA(tr), tol_mode="rel")
+        assert rep[b]["converged"] and rep[b]["n_sweep32"] >= 2
+        assert _rel(rho.cpu().numpy()[b], ref["rho"]) < 1e-10
+        n64 = rep[b]["n_sweep"] - rep[b]["n_sweep32"]
+        n64_plain = rep0[b]["n_sweep"] - rep0[b]["n_sweep32"]
+        assert n64 < n64_plain, (rep[b], rep0[b])
+        # the last change is an FP64 sweep's and passed the stop test
+        assert rep[b]["last_change"] / rep[b]["rho_inf"] < 1e-13
+
+
+def test_gang_wait_changes_when_instances_sweep_not_what_they_compute():
+    """With gang_wait an instance due for an FP64 sweep may wait while others still sweep in FP32;
+    its own iterates are unchanged, so with a fixed sweep decomposition every instance returns
+    bit for bit the same result, sweep counts and FP32 sweep counts as without waiting."""
+    rte = _rte()
+    p = inputs.lattice_test(32, 16, 6, n_vz=2)
+    out = []
+    for gang in (0, 3):
+        batch = rte.Batch.from_problem(p)
+        batch.tune(2)
+        rho = torch.zeros((6, p.n_dof), dtype=torch.float64, device="cuda")
+        rep, _, st = batch.solve(rho, 1e-12, sa=rte.SA_DSA, rel=True, max_iter=300, dsa_rtol=0.0,
+                                 dsa_max_it=1, fp32_switch=1e-3, refine_kappa=0.05,
+                                 refine_inner=6, gang_wait=gang)
+        assert st == 0
+        out.append((rho.cpu().numpy(), [(r["n_sweep"], r["n_sweep32"]) for r in rep]))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
+
+
 def test_dsa_correction_independent_of_batch_composition():
     """Every cell update, residual, restriction and prolongation of the V-cycle acts on one
     instance, so the DSA correction of an instance is bit for bit the same in a batch of 160 and
