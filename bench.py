@@ -82,6 +82,8 @@ def parse():
     ap.add_argument("--gang-wait", type=int, default=4,
                     help="romsad_refine: an instance due for an FP64 sweep waits up to this many "
                          "iterations while others still sweep in FP32 (fuller FP64 launches)")
+    ap.add_argument("--refine-rom-bf16", type=int, default=0,
+                    help="romsad_refine: ROMSA's project/lift products in BF16 on the tensor cores")
     ap.add_argument("--refine-switch", type=float, default=1e-5,
                     help="romsad_refine: FP32 sweeps (with sources) until the relative change is "
                          "below this, then the FP64 outer residual correction")
@@ -121,7 +123,8 @@ def precision_kw(method, a):
         return dict(fp32_switch=a.fp32_switch)
     if method == "romsad_refine":
         return dict(fp32_switch=a.refine_switch, refine_kappa=a.refine_kappa,
-                    refine_inner=a.refine_inner, gang_wait=a.gang_wait)
+                    refine_inner=a.refine_inner, gang_wait=a.gang_wait,
+                    rom_bf16=bool(a.refine_rom_bf16))
     return {}
 
 

@@ -306,6 +306,27 @@ int rte_rom_initial_guess(rte_rom_t rom_p, rte_batch_t batch, double* rho0,
 int rte_romsa_correction(rte_rom_t rom_c, rte_batch_t batch, const double* R, double* drho,
                          const uint8_t* active, void* stream);
 
+/* Dense POD projections on the tensor cores: the products behind ROMSA's and ROMIG's project and
+ * lift steps (Eq. (rom_correction); Sec. 3.1.2) for a basis of r <= 32 vectors of length n,
+ *   rte_pod_project_bf16:  out[b][i] = sum_e U[i][e] X[b][e]     (i < r, e < n, b < B)
+ *   rte_pod_lift_bf16:     Y[b][e]   = sum_i U[i][e] C[b][i]
+ * with U, X, C rounded to BF16 and products summed in FP32 (tcgen05.mma, accumulators in tensor
+ * memory); the projection sums its K chunks in FP64 in a fixed order, so results are
+ * deterministic.  Exact when the operands are BF16 values whose partial sums stay exact in FP32.
+ *   U    DEVICE double[r][n];  X DEVICE double[B][n];  C DEVICE double[B][r]
+ *   out  DEVICE double[B][r];  Y DEVICE double[B][n] (rows of inactive instances untouched)
+ *   active  DEVICE uint8[B] or NULL (instances with active[b] == 0 are skipped)
+ *   work DEVICE, 16-byte aligned, rte_pod_workspace_bytes(r, n, B) bytes (the lift uses its first
+ *        word only).  work's first int32 is a status word: a device-side wait that gave up sets it
+ *        to 1 (the result is then invalid); the caller zeroes it before the first call.
+ * Asynchronous on `stream`; calls sharing `work` must not overlap.  Errors: RTE_EINVAL (r > 32,
+ * bad sizes, null or misaligned pointers), RTE_ECUDA. */
+int rte_pod_workspace_bytes(int r, int n, int B, int64_t* bytes);
+int rte_pod_project_bf16(const double* U, int r, int n, const double* X, int B,
+                         const uint8_t* active, double* out, void* work, void* stream);
+int rte_pod_lift_bf16(const double* U, int r, int n, const double* C, int B, const uint8_t* active,
+                      double* Y, void* work, void* stream);
+
 /* ---- full solves (Alg. 1 with the SA of choice, Alg. 2) --------------------------------- */
 
 #define RTE_SA_NONE 0
@@ -338,6 +359,11 @@ typedef struct {
                           then the next sweep is FP64 again.  Only FP64 sweeps take the stop
                           test.  Combines with fp32_switch (its FP32 phase comes first).      */
   int refine_inner;    /* cap on the FP32 sweeps per outer step (>= 1 when refine_kappa > 0) */
+  int rom_bf16;        /* 1: ROMSA's project and lift products (Eq. (rom_correction)) in BF16
+                          on the tensor cores with FP32 accumulation (rte_pod_project_bf16,
+                          rte_pod_lift_bf16); the r x r solve stays FP64.  The correction is
+                          then accurate to ~1e-3 relative, which changes how fast the iteration
+                          converges, never its FP64 fixed point.  0: FP64.                    */
   int gang_wait;       /* precision variant: 0 -- every instance sweeps at every iteration;
                           > 0 -- an instance due for an FP64 sweep while other running instances
                           still sweep in FP32 waits (no sweep, no correction) for up to gang_wait

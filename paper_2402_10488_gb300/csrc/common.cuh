@@ -278,7 +278,16 @@ struct rte_rom_s {
 namespace rte {
 int rom_prepare(rte_rom_t rom, rte_batch_t bt, cudaStream_t st, const uint8_t* mask = nullptr);
 int rom_correction(rte_rom_t rom, rte_batch_t bt, const double* R, double* drho,
-                   const uint8_t* active, cudaStream_t st);
+                   const uint8_t* active, cudaStream_t st, bool bf16 = false);
+// status word of the BF16 tensor-core products of this ROM's online state (0 if never used):
+// nonzero when a device-side wait gave up; read after the stream is synchronised
+int rom_tc_status(rte_rom_t rom, int* status);
+// podtc.cu: BF16 tensor-core POD products (see rte_pod_project_bf16 / rte_pod_lift_bf16)
+size_t pod_project_ws_bytes(int n, int B, int n_sm);
+int pod_project_bf16(const double* U, int r, int n, const double* X, int B, const uint8_t* active,
+                     double* out, void* ws, int n_sm, cudaStream_t st);
+int pod_lift_bf16(const double* U, int r, int n, const double* C, int B, const uint8_t* active,
+                  double* Y, int* status, cudaStream_t st);
 // ROMIG initial guess rho0 = U^rho A_{mu,r}^{-1} (U^iso)^T G for the instances in `mask`
 int rom_guess_launch(rte_rom_t rom, rte_batch_t bt, double* rho0, const uint8_t* mask,
                      cudaStream_t st);

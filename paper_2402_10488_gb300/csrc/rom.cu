@@ -33,6 +33,7 @@ struct RomOnline {
   DevBuf<double> lu;    // [B][r][r]
   DevBuf<int> piv;      // [B][r]
   DevBuf<double> proj;  // [B][r]
+  DevBuf<uint8_t> tcws; // workspace of the BF16 tensor-core products (first word: status)
 };
 
 // ---- kernels ------------------------------------------------------------------------------
@@ -892,12 +893,32 @@ int rom_guess_launch(rte_rom_t rom, rte_batch_t b, double* rho0, const uint8_t* 
   return RTE_OK;
 }
 
+int rom_tc_status(rte_rom_t rom, int* status) {
+  *status = 0;
+  if (!rom->online || !rom->online->tcws.p) return RTE_OK;
+  RTE_CUDA_TRY(cudaMemcpy(status, rom->online->tcws.p, sizeof(int), cudaMemcpyDeviceToHost));
+  return RTE_OK;
+}
+
 int rom_correction(rte_rom_t rom, rte_batch_t bt, const double* R, double* drho,
-                   const uint8_t* active, cudaStream_t st) {
+                   const uint8_t* active, cudaStream_t st, bool bf16) {
   RomOnline* o = rom->online;
   if (!o || o->batch != bt) RTE_TRY(rom_prepare(rom, bt, st));
   o = rom->online;
   const int r = rom->r, n = bt->disc->n_dof, B = bt->B;
+  if (bf16 && r <= 32) {
+    const size_t need = pod_project_ws_bytes(n, B, bt->n_sm);
+    if (o->tcws.n < need) {
+      RTE_TRY(o->tcws.alloc(need));
+      RTE_CUDA_TRY(cudaMemsetAsync(o->tcws.p, 0, 256, st));
+    }
+    RTE_TRY(pod_project_bf16(rom->U_iso.p, r, n, R, B, active, o->proj.p, o->tcws.p, bt->n_sm, st));
+    lu_solve_kernel<<<(B + 63) / 64, 64, 0, st>>>(o->lu.p, o->piv.p, o->proj.p, r, B, active); RTE_NOTE_LAUNCH();
+    RTE_TRY(pod_lift_bf16(rom->U_rho.p, r, n, o->proj.p, B, active, drho,
+                          reinterpret_cast<int*>(o->tcws.p), st));
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+  }
   project_kernel<<<dim3(r, B), 256, 0, st>>>(rom->U_iso.p, n, R, 1, 0, (size_t)n, o->proj.p, r, active); RTE_NOTE_LAUNCH();
   lu_solve_kernel<<<(B + 63) / 64, 64, 0, st>>>(o->lu.p, o->piv.p, o->proj.p, r, B, active); RTE_NOTE_LAUNCH();
   lift_kernel<<<dim3(std::min((n + 255) / 256, 1024), B), 256, 0, st>>>(rom->U_rho.p, n, o->proj.p, r,
@@ -935,7 +956,7 @@ extern "C" int rte_rom_build(rte_batch_t train, const rte_rom_opts* opts, rte_ro
   RTE_TRY(rho.alloc((size_t)B * d->n_dof));
   RTE_CUDA_TRY(cudaMemsetAsync(rho.p, 0, sizeof(double) * B * d->n_dof, st));
   rte_solve_opts so{opts->eps_train, 0, opts->max_iter, RTE_SA_DSA, 0, 0.0,
-                    opts->dsa_rtol > 0 ? opts->dsa_rtol : 1e-12, 2000, nullptr, 0.0, 0.0, 0, 0};
+                    opts->dsa_rtol > 0 ? opts->dsa_rtol : 1e-12, 2000, nullptr, 0.0, 0.0, 0, 0, 0};
   std::vector<rte_solve_report> rep(B);
   int s = run_si(train, &so, nullptr, rho.p, rep.data(), nullptr, st, psi_cur.p, psi_win.p, w);
   if (s != RTE_OK) return s == RTE_ENOCONV ? fail(RTE_ENOCONV, "training solve did not converge") : s;

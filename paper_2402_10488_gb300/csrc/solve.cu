@@ -261,7 +261,7 @@ int si_finish(SiState& s, cudaStream_t st, double* history) {
       }
       if (anyr) {
         PhaseScope ps(bt, 2, st);
-        RTE_TRY(rom_correction(s.rom, bt, R, drho, s.dm.p + 5 * B, st));
+        RTE_TRY(rom_correction(s.rom, bt, R, drho, s.dm.p + 5 * B, st, o.rom_bf16 != 0));
       }
       // rho^(l) = rho^(l,*) + delta rho^(l), written into the rho_prev slot
       RTE_TRY(axpy_launch(bt, rho_star, drho, rho_prev, d_corr, st));
@@ -313,6 +313,11 @@ int run_si(rte_batch_t bt, const rte_solve_opts* o, rte_rom_t rom_c, double* rho
   int status = RTE_OK;
   for (int b = 0; b < B; ++b)
     if (s.status[b] != RTE_OK) status = s.status[b];
+  if (rom_c && o->rom_bf16) {
+    int tc = 0;
+    RTE_TRY(rom_tc_status(rom_c, &tc));
+    if (tc) return fail(RTE_ETIMEOUT, "BF16 ROM product: a device-side wait gave up");
+  }
   if (reports)
     for (int b = 0; b < B; ++b) reports[b] = s.rep[b];
   return status;
@@ -408,6 +413,11 @@ extern "C" int rte_solve_many(int n, const rte_batch_t* batches, const rte_solve
   int status = RTE_OK;
   for (int k = 0; k < n; ++k) {
     RTE_CUDA_TRY(cudaStreamSynchronize(st[k]));
+    if (roms && roms[k] && opts[k].rom_bf16) {
+      int tc = 0;
+      RTE_TRY(rom_tc_status(roms[k], &tc));
+      if (tc) return fail(RTE_ETIMEOUT, "BF16 ROM product: a device-side wait gave up");
+    }
     for (int b = 0; b < S[k].B; ++b) {
       if (S[k].status[b] != RTE_OK) status = S[k].status[b];
       if (reports && reports[k]) reports[k][b] = S[k].rep[b];

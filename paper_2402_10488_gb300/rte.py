@@ -64,7 +64,32 @@ SIGNATURES = {
     "rte_server_destroy": (_I, [_P]),
     "rte_pgmres": (_I, [_P, _P, _P, _P, _P]),
     "rte_batch_dsa_smoothing": (_I, [_P, _I]),
+    "rte_pod_workspace_bytes": (_I, [_I, _I, _I, _P]),
+    "rte_pod_project_bf16": (_I, [_P, _I, _I, _P, _I, _P, _P, _P, _P]),
+    "rte_pod_lift_bf16": (_I, [_P, _I, _I, _P, _I, _P, _P, _P, _P]),
 }
+
+
+def pod_workspace(r, n, B):
+    """A zeroed device workspace for pod_project_bf16 / pod_lift_bf16 (a torch uint8 tensor)."""
+    import torch
+    nb = np.zeros(1, np.int64)
+    check(lib().rte_pod_workspace_bytes(int(r), int(n), int(B), nb.ctypes.data_as(_P)))
+    return torch.zeros(int(nb[0]), dtype=torch.uint8, device="cuda")
+
+
+def pod_project_bf16(U, X, out, work, active=None, stream=None):
+    """out[b][i] = sum_e U[i][e] X[b][e] on the tensor cores (BF16 operands, FP32 sums)."""
+    r, n = U.shape
+    check(lib().rte_pod_project_bf16(_ptr(U), int(r), int(n), _ptr(X), int(X.shape[0]),
+                                     _ptr(active), _ptr(out), _ptr(work), _stream(stream)))
+
+
+def pod_lift_bf16(U, C, Y, work, active=None, stream=None):
+    """Y[b][e] = sum_i U[i][e] C[b][i] on the tensor cores (BF16 operands, FP32 sums)."""
+    r, n = U.shape
+    check(lib().rte_pod_lift_bf16(_ptr(U), int(r), int(n), _ptr(C), int(C.shape[0]),
+                                  _ptr(active), _ptr(Y), _ptr(work), _stream(stream)))
 
 
 def launch_count() -> int:
@@ -121,7 +146,7 @@ class _SolveOpts(ctypes.Structure):
     _fields_ = [("eps", _D), ("rel", _I), ("max_iter", _I), ("sa", _I), ("theta", _I),
                 ("eps_romsad", _D), ("dsa_rtol", _D), ("dsa_max_it", _I), ("schedule", _P),
                 ("fp32_switch", _D), ("refine_kappa", _D), ("refine_inner", _I),
-                ("gang_wait", _I)]
+                ("rom_bf16", _I), ("gang_wait", _I)]
 
 
 class SolveReport(ctypes.Structure):
@@ -147,13 +172,13 @@ def _report(r):
 
 def solve_opts(eps, sa=SA_DSA, rel=False, max_iter=1000, theta=0, eps_romsad=0.0, dsa_rtol=1e-10,
                dsa_max_it=500, schedule=None, fp32_switch=0.0, refine_kappa=0.0, refine_inner=0,
-               gang_wait=0):
+               gang_wait=0, rom_bf16=False):
     """rte_solve_opts; `schedule` (uint8 per iteration) is kept alive on the returned struct."""
     sched = None if schedule is None else _host(schedule, np.uint8)
     o = _SolveOpts(float(eps), 1 if rel else 0, int(max_iter), int(sa), int(theta),
                    float(eps_romsad), float(dsa_rtol), int(dsa_max_it),
                    None if sched is None else sched.ctypes.data_as(_P), float(fp32_switch),
-                   float(refine_kappa), int(refine_inner), int(gang_wait))
+                   float(refine_kappa), int(refine_inner), 1 if rom_bf16 else 0, int(gang_wait))
     o._sched = sched
     return o
 
@@ -332,9 +357,10 @@ class Batch:
 
     def solve(self, rho, eps, sa=SA_DSA, rel=False, max_iter=1000, theta=0, eps_romsad=0.0,
               dsa_rtol=1e-10, dsa_max_it=500, rom_c=None, schedule=None, history=False,
-              fp32_switch=0.0, refine_kappa=0.0, refine_inner=0, gang_wait=0, stream=None):
+              fp32_switch=0.0, refine_kappa=0.0, refine_inner=0, gang_wait=0, rom_bf16=False,
+              stream=None):
         opts = solve_opts(eps, sa, rel, max_iter, theta, eps_romsad, dsa_rtol, dsa_max_it, schedule,
-                          fp32_switch, refine_kappa, refine_inner, gang_wait)
+                          fp32_switch, refine_kappa, refine_inner, gang_wait, rom_bf16)
         reps = (SolveReport * self.B)()
         hist = np.zeros((self.B, max_iter)) if history else None
         st = check(lib().rte_solve(self.h, ctypes.byref(opts), None if rom_c is None else rom_c.h,
