@@ -160,6 +160,13 @@ int rte_batch_set_slots(rte_batch_t batch, int n, const int* slots, const double
  * fixed point of Alg. 1 does not depend on the DSA).  Errors: RTE_EINVAL. */
 int rte_batch_dsa_smoothing(rte_batch_t batch, int nu);
 
+/* on = 1: the nu smoothing sweeps of a multigrid level run as one launch that keeps a 16 x 16
+ * tile of cells and a halo of 2 nu cells in shared memory (temporal blocking, nu <= 4); 0 (the
+ * default): one launch per colour per sweep.  Both compute the same values bit for bit; the
+ * blocked form reads x and b once instead of 2 nu times but updates 1.4x as many cells (the
+ * shrinking halo), which on GB300 costs more than it saves.  Errors: RTE_EINVAL. */
+int rte_batch_dsa_blocking(rte_batch_t batch, int on);
+
 /* info (HOST int64[6]): B, device bytes held by the batch, directions per warp (preferred),
  * the smallest directions per warp its sweep partial sums are sized for, 1 if the
  * decomposition is picked per launch, 1 if every slot has parameters.  The device bytes of a

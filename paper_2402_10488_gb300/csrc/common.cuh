@@ -183,6 +183,7 @@ struct rte_batch_s {
                                           // correction (rte_solve_opts.refine_kappa), on first use
   rte::DsaState* dsa = nullptr;
   int dsa_nu = 2;                         // red-black smoothing sweeps per multigrid level (2D DSA)
+  bool dsa_blocking = false;              // smoothing sweeps of a level in one temporally blocked launch
   // pinned host staging for per-slot parameter uploads (rte_batch_set_slots), allocated on use
   double* stage = nullptr;
   uint8_t* stage_mask = nullptr;

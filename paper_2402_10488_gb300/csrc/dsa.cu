@@ -243,14 +243,15 @@ __device__ __forceinline__ void store12(float* p, const float v[NB]) {
   for (int k = 0; k < 3; ++k) q[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
 }
 
-// acc += sum over the existing face neighbours of their coupling to cell (i, j), via traces.
-__device__ __forceinline__ void nbr_trace_sum(const Coup& K, float qx, float qy,
-                                              const float* __restrict__ x, int i, int j, int nx,
-                                              int ny, float acc[NB]) {
+// acc += sum over the existing face neighbours of their coupling to a cell, via traces; w, e, s, n
+// point to the 12 values of the west, east, south and north neighbours (null where there is none).
+__device__ __forceinline__ void nbr_trace_sum_p(const Coup& K, float qx, float qy, const float* w,
+                                                const float* e, const float* s, const float* n,
+                                                float acc[NB]) {
   const float s3 = 1.7320508075688772f;
   float v[NB], t[3][2];
-  if (i > 0) {  // west neighbour: its right-face traces, own left-face values
-    load12(x + ((size_t)j * nx + i - 1) * NB, v);
+  if (w) {  // west neighbour: its right-face traces, own left-face values
+    load12(w, v);
 #pragma unroll
     for (int f = 0; f < 3; ++f)
 #pragma unroll
@@ -264,8 +265,8 @@ __device__ __forceinline__ void nbr_trace_sum(const Coup& K, float qx, float qy,
         acc[4 * f + 1 + 2 * q] -= s3 * u;
       }
   }
-  if (i + 1 < nx) {  // east neighbour: its left-face traces, own right-face values
-    load12(x + ((size_t)j * nx + i + 1) * NB, v);
+  if (e) {  // east neighbour: its left-face traces, own right-face values
+    load12(e, v);
 #pragma unroll
     for (int f = 0; f < 3; ++f)
 #pragma unroll
@@ -279,8 +280,8 @@ __device__ __forceinline__ void nbr_trace_sum(const Coup& K, float qx, float qy,
         acc[4 * f + 1 + 2 * q] += s3 * u;
       }
   }
-  if (j > 0) {  // south neighbour: its top-face traces (expanded along x), own bottom values
-    load12(x + ((size_t)(j - 1) * nx + i) * NB, v);
+  if (s) {  // south neighbour: its top-face traces (expanded along x), own bottom values
+    load12(s, v);
 #pragma unroll
     for (int f = 0; f < 3; ++f)
 #pragma unroll
@@ -294,8 +295,8 @@ __device__ __forceinline__ void nbr_trace_sum(const Coup& K, float qx, float qy,
         acc[4 * f + q + 2] -= s3 * u;
       }
   }
-  if (j + 1 < ny) {  // north neighbour: its bottom-face traces, own top values
-    load12(x + ((size_t)(j + 1) * nx + i) * NB, v);
+  if (n) {  // north neighbour: its bottom-face traces, own top values
+    load12(n, v);
 #pragma unroll
     for (int f = 0; f < 3; ++f)
 #pragma unroll
@@ -311,6 +312,16 @@ __device__ __forceinline__ void nbr_trace_sum(const Coup& K, float qx, float qy,
   }
 }
 
+// the same for cell (i, j) of a level vector x in global memory
+__device__ __forceinline__ void nbr_trace_sum(const Coup& K, float qx, float qy,
+                                              const float* __restrict__ x, int i, int j, int nx,
+                                              int ny, float acc[NB]) {
+  nbr_trace_sum_p(K, qx, qy, i > 0 ? x + ((size_t)j * nx + i - 1) * NB : nullptr,
+                  i + 1 < nx ? x + ((size_t)j * nx + i + 1) * NB : nullptr,
+                  j > 0 ? x + ((size_t)(j - 1) * nx + i) * NB : nullptr,
+                  j + 1 < ny ? x + ((size_t)(j + 1) * nx + i) * NB : nullptr, acc);
+}
+
 __device__ __forceinline__ void matvec12(const float* __restrict__ M, const float v[NB], float out[NB]) {
 #pragma unroll
   for (int r = 0; r < NB; ++r) {
@@ -321,8 +332,10 @@ __device__ __forceinline__ void matvec12(const float* __restrict__ M, const floa
   }
 }
 
-// one cell of a red-black block Gauss-Seidel half sweep: x_c = D_c^{-1} (b_c - sum_n O_n x_n)
-__device__ __forceinline__ void rbgs_cell(const LevelC& L, const Coup& K, int b, int c) {
+// one cell of a red-black block Gauss-Seidel half sweep: x_c = D_c^{-1} (b_c - sum_n O_n x_n);
+// dinv_b: the instance's D^-1 blocks [n_class][144] (global memory, or a shared-memory copy)
+__device__ __forceinline__ void rbgs_cell(const LevelC& L, const Coup& K, int b, int c,
+                                          const float* dinv_b) {
   const int i = c % L.nx, j = c / L.nx;
   float* xb = L.x + (size_t)b * L.nc * NB;
   float acc[NB];
@@ -334,7 +347,7 @@ __device__ __forceinline__ void rbgs_cell(const LevelC& L, const Coup& K, int b,
 #pragma unroll
   for (int r = 0; r < NB; ++r) res[r] -= acc[r];
   float out[NB];
-  matvec12(L.dinv + ((size_t)b * L.n_class + L.cls[c]) * NB2, res, out);
+  matvec12(dinv_b + (size_t)L.cls[c] * NB2, res, out);
   store12(xb + (size_t)c * NB, out);
 }
 
@@ -395,16 +408,106 @@ __device__ __forceinline__ void prolong_entry(const LevelC& F, const LevelC& Cl,
   F.x[(size_t)b * F.nc * NB + t] += s;
 }
 
+constexpr int kSmemClasses = 8;  // a level with at most this many classes has its D^-1 blocks
+                                 // staged in shared memory by the smoothing kernels
+
 __global__ void rbgs_kernel(LevelC L, Coup K, int color, const uint8_t* active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
+  __shared__ float4 dsh4[kSmemClasses * NB2 / 4];
+  const float* dg = L.dinv + (size_t)b * L.n_class * NB2;
+  const bool dsm = L.n_class <= kSmemClasses;
+  if (dsm) {
+    for (int t = threadIdx.x; t < L.n_class * NB2 / 4; t += blockDim.x)
+      dsh4[t] = reinterpret_cast<const float4*>(dg)[t];
+    __syncthreads();
+  }
   const int hx2 = (L.nx + 1) / 2;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= hx2 * L.ny) return;
   const int j = idx / hx2;
   const int i = 2 * (idx % hx2) + ((j + color) & 1);
   if (i >= L.nx) return;
-  rbgs_cell(L, K, b, j * L.nx + i);
+  rbgs_cell(L, K, b, j * L.nx + i, dsm ? reinterpret_cast<const float*>(dsh4) : dg);
+}
+
+// Red-black Gauss-Seidel with temporal blocking: H = 2 nu half sweeps of one level, colours c0,
+// 1 - c0, c0, ..., on a 16 x 16 tile per CTA, in shared memory.  The CTA loads x and b on the tile
+// and a halo of H cells, then half sweep h updates the cells of its colour within H - 1 - h cells
+// of the tile (their neighbours are exact after half sweep h - 1 there), so after H half sweeps
+// the tile holds exactly what H launches of rbgs_kernel give; only the tile is written, to xout
+// (not to L.x, whose halo cells other CTAs are still reading).  One pass over x and b instead of
+// H, for 1.4x the cell updates (the shrinking halo).  Each cell update is rbgs_cell's arithmetic
+// in the same order, so results are bit for bit those of rbgs_kernel.
+constexpr int kFT = 16;        // tile side
+constexpr int kFusedMaxH = 8;  // half sweeps per launch at most (nu <= 4)
+
+constexpr int kFusedClasses = kSmemClasses;
+
+__host__ __device__ constexpr size_t fused_smem_bytes(int H) {
+  return ((size_t)2 * (kFT + 2 * H) * (kFT + 2 * H) * NB + (size_t)kFusedClasses * NB2) * sizeof(float);
+}
+
+__global__ void __launch_bounds__(256) rbgs_fused_kernel(LevelC L, Coup K, int H, int c0,
+                                                         float* xout, const uint8_t* active) {
+  const int b = blockIdx.z;
+  if (active && !active[b]) return;
+  extern __shared__ float4 fsm4[];
+  const int R = kFT + 2 * H;
+  float* xs = reinterpret_cast<float*>(fsm4);  // [R * R][12] region, row-major
+  float* bs = xs + (size_t)R * R * NB;
+  float* ds = bs + (size_t)R * R * NB;         // [n_class][144] D^-1 blocks when few classes
+  const bool dsm = L.n_class <= kFusedClasses;
+  const float* dg = L.dinv + (size_t)b * L.n_class * NB2;
+  if (dsm)
+    for (int t = threadIdx.x; t < L.n_class * NB2 / 4; t += blockDim.x)
+      reinterpret_cast<float4*>(ds)[t] = reinterpret_cast<const float4*>(dg)[t];
+  const int i0 = blockIdx.x * kFT - H, j0 = blockIdx.y * kFT - H;  // region origin
+  const float* xg = L.x + (size_t)b * L.nc * NB;
+  const float* bg = L.b + (size_t)b * L.nc * NB;
+  float* xo = xout + (size_t)b * L.nc * NB;
+  for (int t = threadIdx.x; t < R * R * 3; t += blockDim.x) {
+    const int cell = t / 3, q = t % 3, gi = i0 + cell % R, gj = j0 + cell / R;
+    if (gi >= 0 && gi < L.nx && gj >= 0 && gj < L.ny) {
+      const size_t g = ((size_t)gj * L.nx + gi) * NB;
+      reinterpret_cast<float4*>(xs + (size_t)cell * NB)[q] = reinterpret_cast<const float4*>(xg + g)[q];
+      reinterpret_cast<float4*>(bs + (size_t)cell * NB)[q] = reinterpret_cast<const float4*>(bg + g)[q];
+    }
+  }
+  __syncthreads();
+  for (int h = 0; h < H; ++h) {
+    const int color = (c0 + h) & 1, d = H - 1 - h;
+    const int lo = H - d, W = kFT + 2 * d, half = (W + 1) / 2;  // region rows/cols [lo, lo + W)
+    for (int t = threadIdx.x; t < W * half; t += blockDim.x) {
+      const int rj = lo + t / half, gj = j0 + rj;
+      // first column of this row with (gi + gj) % 2 == color, then every second one
+      const int ri = lo + ((color - gj - (i0 + lo)) & 1) + 2 * (t % half), gi = i0 + ri;
+      if (ri >= lo + W || gi < 0 || gi >= L.nx || gj < 0 || gj >= L.ny) continue;
+      const int cell = rj * R + ri;
+      float acc[NB];
+#pragma unroll
+      for (int r = 0; r < NB; ++r) acc[r] = 0.f;
+      nbr_trace_sum_p(K, L.qx, L.qy, gi > 0 ? xs + (size_t)(cell - 1) * NB : nullptr,
+                      gi + 1 < L.nx ? xs + (size_t)(cell + 1) * NB : nullptr,
+                      gj > 0 ? xs + (size_t)(cell - R) * NB : nullptr,
+                      gj + 1 < L.ny ? xs + (size_t)(cell + R) * NB : nullptr, acc);
+      float res[NB];
+      load12(bs + (size_t)cell * NB, res);
+#pragma unroll
+      for (int r = 0; r < NB; ++r) res[r] -= acc[r];
+      float out[NB];
+      matvec12((dsm ? ds : dg) + (size_t)L.cls[gj * L.nx + gi] * NB2, res, out);
+      store12(xs + (size_t)cell * NB, out);
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < kFT * kFT * 3; t += blockDim.x) {
+    const int cell = t / 3, q = t % 3, ri = H + cell % kFT, rj = H + cell / kFT;
+    const int gi = i0 + ri, gj = j0 + rj;
+    if (gi < L.nx && gj < L.ny)
+      reinterpret_cast<float4*>(xo + ((size_t)gj * L.nx + gi) * NB)[q] =
+          reinterpret_cast<const float4*>(xs + (size_t)(rj * R + ri) * NB)[q];
+  }
 }
 
 __global__ void residual_kernel(LevelC L, Coup K, const uint8_t* active) {
@@ -448,7 +551,7 @@ __global__ void __launch_bounds__(512) coarse_vcycle_kernel(const CoarseArgs A, 
     const int hx2 = (L.nx + 1) / 2;
     for (int idx = tid; idx < hx2 * L.ny; idx += nt) {
       const int j = idx / hx2, i = 2 * (idx % hx2) + ((j + color) & 1);
-      if (i < L.nx) rbgs_cell(L, A.K, b, j * L.nx + i);
+      if (i < L.nx) rbgs_cell(L, A.K, b, j * L.nx + i, L.dinv + (size_t)b * L.n_class * NB2);
     }
     __syncthreads();
   };
@@ -1030,6 +1133,20 @@ int dsa_setup(rte_batch_t bt, cudaStream_t st, const uint8_t* mask) {
 }
 
 // One V-cycle from level l: x_l approximately solves A_l x = b_l (x_l starts at zero).
+// Opt-in to the temporally blocked smoother's shared memory once per device.
+static int fused_smem_attr(size_t bytes) {
+  static size_t done[64] = {};
+  int dev = 0;
+  RTE_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(RTE_EINVAL, "device index too large");
+  if (done[dev] >= bytes) return RTE_OK;
+  const size_t want = fused_smem_bytes(kFusedMaxH);
+  RTE_CUDA_TRY(cudaFuncSetAttribute(rbgs_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)want));
+  done[dev] = want;
+  return RTE_OK;
+}
+
 static int vcycle(rte_batch_t bt, int l, const uint8_t* active, cudaStream_t st, int nu) {
   DsaState* s = bt->dsa;
   const int B = bt->B;
@@ -1041,7 +1158,9 @@ static int vcycle(rte_batch_t bt, int l, const uint8_t* active, cudaStream_t st,
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
   }
-  const LevelC L = lvl_of(bt, l), Cl = lvl_of(bt, l + 1);
+  // the blocked smoother writes the level's residual buffer and then swaps it with x, so every
+  // LevelC is re-read after a step that may have swapped them
+  LevelC L = lvl_of(bt, l);
   RTE_CUDA_TRY(cudaMemsetAsync(L.x, 0, sizeof(float) * (size_t)B * L.nc * NB, st));
   const int ncol = ((L.nx + 1) / 2) * L.ny;
   const dim3 gcol((ncol + 127) / 128, B);
@@ -1049,12 +1168,29 @@ static int vcycle(rte_batch_t bt, int l, const uint8_t* active, cudaStream_t st,
     rbgs_kernel<<<gcol, 128, 0, st>>>(L, s->K, c0, active); RTE_NOTE_LAUNCH();
     rbgs_kernel<<<gcol, 128, 0, st>>>(L, s->K, 1 - c0, active); RTE_NOTE_LAUNCH();
   };
-  for (int k = 0; k < nu; ++k) smooth(0);
+  // nu sweeps starting with colour c0: one temporally blocked launch, or 2 nu launches
+  const bool blocked = bt->dsa_blocking && 2 * nu <= kFusedMaxH;
+  auto smooth_nu = [&](int c0) -> int {
+    if (blocked) {
+      const size_t bytes = fused_smem_bytes(2 * nu);
+      RTE_TRY(fused_smem_attr(bytes));
+      rbgs_fused_kernel<<<dim3((L.nx + kFT - 1) / kFT, (L.ny + kFT - 1) / kFT, B), 256, bytes, st>>>(
+          L, s->K, 2 * nu, c0, L.r, active); RTE_NOTE_LAUNCH();
+      std::swap(s->xl[l], s->rl[l]);  // the smoothed iterate is now the level's x
+      L = lvl_of(bt, l);
+    } else {
+      for (int k = 0; k < nu; ++k) smooth(c0);
+    }
+    return RTE_OK;
+  };
+  RTE_TRY(smooth_nu(0));
   residual_kernel<<<dim3((L.nc + 127) / 128, B), 128, 0, st>>>(L, s->K, active); RTE_NOTE_LAUNCH();
+  LevelC Cl = lvl_of(bt, l + 1);
   restrict_kernel<<<dim3((Cl.nc * NB + 255) / 256, B), 256, 0, st>>>(L, Cl, active); RTE_NOTE_LAUNCH();
   RTE_TRY(vcycle(bt, l + 1, active, st, nu));
+  Cl = lvl_of(bt, l + 1);
   prolong_add_kernel<<<dim3((L.nc * NB + 255) / 256, B), 256, 0, st>>>(L, Cl, active); RTE_NOTE_LAUNCH();
-  for (int k = 0; k < nu; ++k) smooth(1);
+  RTE_TRY(smooth_nu(1));
   RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;
 }
@@ -1345,6 +1481,12 @@ extern "C" int rte_dsa_correction(rte_batch_t b, const double* R, double* drho, 
   if (s != RTE_OK && s != RTE_ENOCONV) return s;
   RTE_CUDA_TRY(cudaStreamSynchronize(st));
   return s;
+}
+
+extern "C" int rte_batch_dsa_blocking(rte_batch_t b, int on) {
+  if (!b || (on != 0 && on != 1)) return fail(RTE_EINVAL, "rte_batch_dsa_blocking: need on = 0 or 1");
+  b->dsa_blocking = on != 0;
+  return RTE_OK;
 }
 
 extern "C" int rte_batch_dsa_smoothing(rte_batch_t b, int nu) {

@@ -502,6 +502,42 @@ __global__ void sweep1d_kernel(const Sweep1DArgs A) {
 }
 
 // rho_out = sum of the group partials (fixed order); optional stop-test norms per instance.
+// |x| as the bit pattern of a non-negative double: such patterns order like the values, so the
+// stop-test maxima are taken with integer max on the ALU instead of FP64 min/max instructions (a
+// NaN orders above +inf and so shows up in the norm).
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+  return a > b ? a : b;
+}
+
+// Block-wide maxima of (dmax, rmax) as bit patterns, folded into norms[2b], norms[2b + 1].
+__device__ __forceinline__ void block_norms(unsigned long long dmax, unsigned long long rmax,
+                                            unsigned long long* norms, int b) {
+  for (int o = 16; o > 0; o >>= 1) {
+    dmax = umax64(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    rmax = umax64(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+  }
+  __shared__ unsigned long long sd[32], sr[32];
+  const int wid = threadIdx.x >> 5, ln = threadIdx.x & 31;
+  if (ln == 0) sd[wid] = dmax, sr[wid] = rmax;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    dmax = ln < nw ? sd[ln] : 0ull;
+    rmax = ln < nw ? sr[ln] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+      dmax = umax64(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      rmax = umax64(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    }
+    if (ln == 0) {
+      atomicMax(norms + 2 * b, dmax);
+      atomicMax(norms + 2 * b + 1, rmax);
+    }
+  }
+}
+
 __global__ void reduce_partials_kernel(const double* __restrict__ partial,
                                        const double* __restrict__ rho_in, double* rho_out,
                                        unsigned long long* norms, const uint8_t* active,
@@ -510,7 +546,7 @@ __global__ void reduce_partials_kernel(const double* __restrict__ partial,
   if (active && !active[b]) return;
   const int rank = active_rank(active, b);
   const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-  double dmax = 0.0, rmax = 0.0;
+  unsigned long long dmax = 0ull, rmax = 0ull;
   if (e < n_dof) {
     const double* p = partial + (size_t)rank * n_groups * n_dof + e;
     double2 acc = reinterpret_cast<const double2*>(p)[0];
@@ -522,33 +558,12 @@ __global__ void reduce_partials_kernel(const double* __restrict__ partial,
     reinterpret_cast<double2*>(rho_out + (size_t)b * n_dof + e)[0] = acc;
     if (norms) {
       const double2 ri = reinterpret_cast<const double2*>(rho_in + (size_t)b * n_dof + e)[0];
-      dmax = fmax(fabs(acc.x - ri.x), fabs(acc.y - ri.y));
-      rmax = fmax(fabs(acc.x), fabs(acc.y));
+      dmax = umax64(abs_bits(acc.x - ri.x), abs_bits(acc.y - ri.y));
+      rmax = umax64(abs_bits(acc.x), abs_bits(acc.y));
     }
   }
   if (!norms) return;
-  for (int o = 16; o > 0; o >>= 1) {
-    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-    rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-  }
-  __shared__ double sd[32], sr[32];
-  const int wid = threadIdx.x >> 5, ln = threadIdx.x & 31;
-  if (ln == 0) sd[wid] = dmax, sr[wid] = rmax;
-  __syncthreads();
-  if (wid == 0) {
-    const int nw = blockDim.x >> 5;
-    dmax = ln < nw ? sd[ln] : 0.0;
-    rmax = ln < nw ? sr[ln] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) {
-      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-      rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-    }
-    if (ln == 0) {
-      // non-negative doubles order like their bit patterns: atomicMax on the bits is exact
-      atomicMax(norms + 2 * b, (unsigned long long)__double_as_longlong(dmax));
-      atomicMax(norms + 2 * b + 1, (unsigned long long)__double_as_longlong(rmax));
-    }
-  }
+  block_norms(dmax, rmax, norms, b);
 }
 
 __global__ void change_norm_kernel(const double* __restrict__ rs, const double* __restrict__ rp,
@@ -899,9 +914,22 @@ int sweep_launch_with_scratch(rte_batch_t bt, const double* rho_in, double* rho_
 // with FP32 rounding confined to the small e.
 namespace rte {
 
+// FP32 copy of the sweep tables, each table row-interleaved: row k (k < 4) is the 8 floats
+// {M^-1[k][0..3], (M^-1 E_x)[k][0..1], (M^-1 E_y)[k][0..1]}, so that the sweep reads a row with two
+// 16-byte shared-memory loads (the FP64 layout keeps the three blocks apart).
 __global__ void tables_to_f32_kernel(const double* t64, float* t32, size_t n) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) t32[i] = (float)t64[i];
+  if (i >= n) return;
+  const size_t base = i / kTab2D * kTab2D;
+  const int q = (int)(i % kTab2D), k = q / 8, j = q % 8;
+  const int src = j < 4 ? 4 * k + j : (j < 6 ? 16 + 2 * k + (j - 4) : 24 + 2 * k + (j - 6));
+  t32[i] = (float)t64[base + src];
+}
+
+// floats of the FP32 sweep's y-inflow line buffer, rounded up so that the tables behind it start
+// on a 16-byte boundary
+__host__ __device__ __forceinline__ int ybuf32_floats(int nx, int dpw) {
+  return (nx * dpw * 2 + 3) & ~3;
 }
 
 __global__ void cell_source32_kernel(const double* __restrict__ rho, float* S,
@@ -950,7 +978,7 @@ __global__ void __launch_bounds__(32) sweep2d_f32_kernel(const Sweep2D32Args A) 
   const bool xneg = grp.quad & 1, yneg = (grp.quad & 2) != 0;
   extern __shared__ float smf[];
   float* ybuf = smf;                                 // [nx][DPW][2]
-  float* tab_s = smf + (size_t)A.nx * DPW * 2;       // [n_mat][DPW][32]
+  float* tab_s = smf + ybuf32_floats(A.nx, DPW);     // [n_mat][DPW][32], 16-byte aligned
   const float* __restrict__ tabg = A.tables + (size_t)b * A.n_mat * A.n_dirs * kTab2D;
   for (int e = lane; e < A.n_mat * DPW * kTab2D; e += 32) {
     const int m = e / (DPW * kTab2D), r = e % (DPW * kTab2D), dd = r / kTab2D, k = r % kTab2D;
@@ -1010,18 +1038,19 @@ __global__ void __launch_bounds__(32) sweep2d_f32_kernel(const Sweep2D32Args A) 
 #pragma unroll
       for (int dd = 0; dd < DPW; ++dd) {
         if (dd < grp.nd) {
-          const float* T = tab_s + (m * DPW + dd) * kTab2D;
+          const float4* T = reinterpret_cast<const float4*>(tab_s + (m * DPW + dd) * kTab2D);
           float a[4];
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            float v = T[4 * k] * sv.x;
-            v = fmaf(T[4 * k + 1], sv.y, v);
-            v = fmaf(T[4 * k + 2], sv.z, v);
-            v = fmaf(T[4 * k + 3], sv.w, v);
-            v = fmaf(T[16 + 2 * k], tx[dd][0], v);
-            v = fmaf(T[17 + 2 * k], tx[dd][1], v);
-            v = fmaf(T[24 + 2 * k], ty[dd][0], v);
-            v = fmaf(T[25 + 2 * k], ty[dd][1], v);
+            const float4 mr = T[2 * k], er = T[2 * k + 1];  // M^-1 row k | inflow rows k
+            float v = mr.x * sv.x;
+            v = fmaf(mr.y, sv.y, v);
+            v = fmaf(mr.z, sv.z, v);
+            v = fmaf(mr.w, sv.w, v);
+            v = fmaf(er.x, tx[dd][0], v);
+            v = fmaf(er.y, tx[dd][1], v);
+            v = fmaf(er.z, ty[dd][0], v);
+            v = fmaf(er.w, ty[dd][1], v);
             a[k] = v;
           }
           tx[dd][0] = fmaf(c3x, a[1], a[0]);
@@ -1047,8 +1076,9 @@ __global__ void __launch_bounds__(32) sweep2d_f32_kernel(const Sweep2D32Args A) 
   }
 }
 
-// rho_out (FP64) = sum of the FP32 group partials (fixed order, summed in FP64), plus y0 for the
-// instances flagged in `inner`; fused norms.
+// rho_out (FP64) = sum of the FP32 group partials (fixed order, summed in FP32: the partials carry
+// FP32 rounding already, and FP64 additions would bind on GB300's FP64 pipe), plus y0 in FP64 for
+// the instances flagged in `inner`; fused norms (the change itself is formed in FP64).
 __global__ void reduce_partials32_kernel(const float* __restrict__ partial,
                                          const double* __restrict__ rho_in, double* rho_out,
                                          unsigned long long* norms, const uint8_t* active,
@@ -1058,53 +1088,36 @@ __global__ void reduce_partials32_kernel(const float* __restrict__ partial,
   if (active && !active[b]) return;
   const int rank = active_rank(active, b);
   const int e = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
-  double dmax = 0.0, rmax = 0.0;
+  unsigned long long dmax = 0ull, rmax = 0ull;
   if (e < n_dof) {
     const float* p = partial + (size_t)rank * n_groups * n_dof + e;
-    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    float4 s = *reinterpret_cast<const float4*>(p);
+    for (int g = 1; g < n_groups; ++g) {
+      const float4 v = *reinterpret_cast<const float4*>(p + (size_t)g * n_dof);
+      s.x += v.x, s.y += v.y, s.z += v.z, s.w += v.w;
+    }
+    double a0 = s.x, a1 = s.y, a2 = s.z, a3 = s.w;
     if (inner && inner[b]) {
       const double* y = y0 + (size_t)b * n_dof + e;
-      a0 = y[0], a1 = y[1], a2 = y[2], a3 = y[3];
-    }
-    for (int g = 0; g < n_groups; ++g) {
-      const float4 v = *reinterpret_cast<const float4*>(p + (size_t)g * n_dof);
-      a0 += v.x, a1 += v.y, a2 += v.z, a3 += v.w;
+      a0 += y[0], a1 += y[1], a2 += y[2], a3 += y[3];
     }
     double* o = rho_out + (size_t)b * n_dof + e;
     o[0] = a0, o[1] = a1, o[2] = a2, o[3] = a3;
     if (norms) {
       const double* ri = rho_in + (size_t)b * n_dof + e;
-      dmax = fmax(fmax(fabs(a0 - ri[0]), fabs(a1 - ri[1])), fmax(fabs(a2 - ri[2]), fabs(a3 - ri[3])));
-      rmax = fmax(fmax(fabs(a0), fabs(a1)), fmax(fabs(a2), fabs(a3)));
+      dmax = umax64(umax64(abs_bits(a0 - ri[0]), abs_bits(a1 - ri[1])),
+                    umax64(abs_bits(a2 - ri[2]), abs_bits(a3 - ri[3])));
+      rmax = umax64(umax64(abs_bits(a0), abs_bits(a1)), umax64(abs_bits(a2), abs_bits(a3)));
     }
   }
   if (!norms) return;
-  for (int o = 16; o > 0; o >>= 1) {
-    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-    rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-  }
-  __shared__ double sd[32], sr[32];
-  const int wid = threadIdx.x >> 5, ln = threadIdx.x & 31;
-  if (ln == 0) sd[wid] = dmax, sr[wid] = rmax;
-  __syncthreads();
-  if (wid == 0) {
-    const int nw = blockDim.x >> 5;
-    dmax = ln < nw ? sd[ln] : 0.0;
-    rmax = ln < nw ? sr[ln] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) {
-      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-      rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-    }
-    if (ln == 0) {
-      atomicMax(norms + 2 * b, (unsigned long long)__double_as_longlong(dmax));
-      atomicMax(norms + 2 * b + 1, (unsigned long long)__double_as_longlong(rmax));
-    }
-  }
+  block_norms(dmax, rmax, norms, b);
 }
 
 template <int DPW>
 static int launch2d_f32(const Sweep2D32Args& A, int B, int n_groups, cudaStream_t st) {
-  const size_t bytes = ((size_t)A.nx * DPW * 2 + (size_t)A.n_mat * DPW * kTab2D) * sizeof(float);
+  const size_t bytes =
+      ((size_t)ybuf32_floats(A.nx, DPW) + (size_t)A.n_mat * DPW * kTab2D) * sizeof(float);
   if (bytes > 200 * 1024) return fail(RTE_EINVAL, "FP32 sweep: shared memory exceeded");
   if (bytes > 48 * 1024) {
     RTE_CUDA_TRY(cudaFuncSetAttribute(sweep2d_f32_kernel<DPW>,

@@ -64,6 +64,7 @@ SIGNATURES = {
     "rte_server_destroy": (_I, [_P]),
     "rte_pgmres": (_I, [_P, _P, _P, _P, _P]),
     "rte_batch_dsa_smoothing": (_I, [_P, _I]),
+    "rte_batch_dsa_blocking": (_I, [_P, _I]),
     "rte_pod_workspace_bytes": (_I, [_I, _I, _I, _P]),
     "rte_pod_project_bf16": (_I, [_P, _I, _I, _P, _I, _P, _P, _P, _P]),
     "rte_pod_lift_bf16": (_I, [_P, _I, _I, _P, _I, _P, _P, _P, _P]),
@@ -295,6 +296,10 @@ class Batch:
     def dsa_smoothing(self, nu):
         """Red-black smoothing sweeps per multigrid level of the 2D DSA (rte_batch_dsa_smoothing)."""
         check(lib().rte_batch_dsa_smoothing(self.h, int(nu)))
+
+    def dsa_blocking(self, on):
+        """Temporally blocked smoothing launches in the 2D DSA multigrid (rte_batch_dsa_blocking)."""
+        check(lib().rte_batch_dsa_blocking(self.h, 1 if on else 0))
 
     def info(self):
         out = np.zeros(6, np.int64)
