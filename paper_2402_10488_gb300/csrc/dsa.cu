@@ -127,28 +127,6 @@ static void invert_host(const double* A, double* Ai, int n) {
 
 // ---- device helpers -------------------------------------------------------------------------
 
-template <class T>
-__device__ __forceinline__ void inv12(T* a /*[12][24] scratch*/) {
-  for (int k = 0; k < NB; ++k) {
-    int p = k;
-    for (int r = k + 1; r < NB; ++r)
-      if (fabs((double)a[r * 24 + k]) > fabs((double)a[p * 24 + k])) p = r;
-    if (p != k)
-      for (int c = 0; c < 24; ++c) {
-        T t = a[k * 24 + c];
-        a[k * 24 + c] = a[p * 24 + c];
-        a[p * 24 + c] = t;
-      }
-    const T piv = (T)1 / a[k * 24 + k];
-    for (int c = 0; c < 24; ++c) a[k * 24 + c] *= piv;
-    for (int r = 0; r < NB; ++r)
-      if (r != k) {
-        const T f = a[r * 24 + k];
-        for (int c = 0; c < 24; ++c) a[r * 24 + c] -= f * a[k * 24 + c];
-      }
-  }
-}
-
 // ---- multigrid levels ----------------------------------------------------------------------------
 //
 // The Galerkin coarse operator P^T A P of this DG moment system is the same system on the coarse
@@ -629,31 +607,65 @@ __global__ void class_mass_kernel(int l, int n_mat, int n_class, int n_class_f, 
 }
 
 // D = geo + blockdiag(Ma, 3<vx^2> Mt, 3<vy^2> Mt) per (instance, class); store D, D^{-1} (FP32)
-// and, when diag64 != nullptr, D in FP64.
+// and, when diag64 != nullptr, D in FP64.  One warp per block: lane c < 24 holds column c of the
+// augmented matrix [D | I] in registers, and the Gauss-Jordan elimination with partial pivoting of
+// inv12 runs column-parallel (the pivot column's lane picks the pivot row and broadcasts the
+// scaling and elimination factors); every element sees inv12's operations in inv12's order.
 __global__ void class_diag_kernel(const double* geo, const double* Ma, const double* Mt, double cx,
                                   double cy, int n, float* diag, float* dinv, double* diag64,
                                   int n_class, const uint8_t* mask) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (t >= n) return;
   if (mask && !mask[t / n_class]) return;
-  double a[NB * 24];
-  for (int r = 0; r < NB; ++r)
-    for (int c = 0; c < NB; ++c) {
-      double v = geo[r * NB + c];
+  double col[NB];
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+    double v = 0.0;
+    if (lane < NB) {
+      const int c = lane;
+      v = geo[r * NB + c];
       const int fr = r / 4, fc = c / 4;
       if (fr == fc) {
         const double m = fr == 0 ? Ma[(size_t)t * 16 + 4 * (r % 4) + (c % 4)]
                                  : (fr == 1 ? cx : cy) * Mt[(size_t)t * 16 + 4 * (r % 4) + (c % 4)];
         v += m;
       }
-      a[r * 24 + c] = v;
-      a[r * 24 + NB + c] = r == c ? 1.0 : 0.0;
       diag[(size_t)t * NB2 + r * NB + c] = (float)v;
       if (diag64) diag64[(size_t)t * NB2 + r * NB + c] = v;
+    } else if (lane < 2 * NB) {
+      v = r == lane - NB ? 1.0 : 0.0;
     }
-  inv12<double>(a);
-  for (int r = 0; r < NB; ++r)
-    for (int c = 0; c < NB; ++c) dinv[(size_t)t * NB2 + r * NB + c] = (float)a[r * 24 + NB + c];
+    col[r] = v;
+  }
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    // pivot row: the first largest |a[r][k]|, r >= k (lane k owns column k)
+    int p = k;
+    double best = fabs(col[k]);
+#pragma unroll
+    for (int r = k + 1; r < NB; ++r)
+      if (fabs(col[r]) > best) best = fabs(col[r]), p = r;
+    p = __shfl_sync(0xffffffffu, p, k);
+    if (p != k) {
+      double tk = col[k], tp = tk;
+#pragma unroll
+      for (int r = k + 1; r < NB; ++r) tp = r == p ? col[r] : tp;
+#pragma unroll
+      for (int r = k + 1; r < NB; ++r) col[r] = r == p ? tk : col[r];
+      col[k] = tp;
+    }
+    const double piv = 1.0 / __shfl_sync(0xffffffffu, col[k], k);
+    col[k] *= piv;
+#pragma unroll
+    for (int r = 0; r < NB; ++r)
+      if (r != k) {
+        const double f = __shfl_sync(0xffffffffu, col[r], k);
+        col[r] -= f * col[k];
+      }
+  }
+  if (lane >= NB && lane < 2 * NB)
+#pragma unroll
+    for (int r = 0; r < NB; ++r) dinv[(size_t)t * NB2 + r * NB + (lane - NB)] = (float)col[r];
 }
 
 // ---- vector helpers (FGMRES, FP64) ---------------------------------------------------------
@@ -1122,7 +1134,7 @@ int dsa_setup(rte_batch_t bt, cudaStream_t st, const uint8_t* mask) {
         s->mixed[l]->p, l ? s->cls[l - 1]->p : nullptr, bt->sigma_t.p, bt->sigma_s.p, B,
         l ? s->Ma[l - 1]->p : nullptr, l ? s->Mt[l - 1]->p : nullptr, s->Ma[l]->p, s->Mt[l]->p,
         mask); RTE_NOTE_LAUNCH();
-    class_diag_kernel<<<(n + 63) / 64, 64, 0, st>>>(s->geo64[l]->p, s->Ma[l]->p, s->Mt[l]->p,
+    class_diag_kernel<<<(n + 3) / 4, 128, 0, st>>>(s->geo64[l]->p, s->Ma[l]->p, s->Mt[l]->p,
                                                     3.0 * d->mom.xx, 3.0 * d->mom.yy, n,
                                                     s->diag32[l]->p, s->dinv32[l]->p,
                                                     l == 0 ? s->diag64.p : nullptr, s->ncls[l],

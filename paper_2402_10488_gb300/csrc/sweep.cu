@@ -1001,6 +1001,24 @@ __global__ void __launch_bounds__(32) sweep2d_f32_kernel(const Sweep2D32Args A) 
   float tx[DPW][2], typ[DPW][2];
 #pragma unroll
   for (int dd = 0; dd < DPW; ++dd) tx[dd][0] = tx[dd][1] = typ[dd][0] = typ[dd][1] = 0.f;
+  // cell of this lane at wavefront step s_ (false when the lane is idle there)
+  auto cell_at = [&](int s_, int& c_) -> bool {
+    const int u_ = s_ - lane;
+    const bool in_ = lane < H && u_ >= 0 && u_ < total;
+    const int rb_ = in_ ? u_ / A.nx : 0;
+    const int t_ = in_ ? u_ - rb_ * A.nx : 0;
+    const int r_ = rb_ * H + lane;
+    c_ = (yneg ? A.ny - 1 - r_ : r_) * A.nx + (xneg ? A.nx - 1 - t_ : t_);
+    return in_ && r_ < A.ny;
+  };
+  // the next step's material and cell source are loaded while this step computes, so the
+  // global-memory latency is off the wavefront's critical path
+  int m_next = 0;
+  float4 sv_next = make_float4(0.f, 0.f, 0.f, 0.f);
+  {
+    int c0;
+    if (cell_at(0, c0)) m_next = A.mat[c0], sv_next = Sb[c0];
+  }
   for (int s = 0; s < total + H - 1; ++s) {
     const int u = s - lane;
     const bool inrange = lane < H && u >= 0 && u < total;
@@ -1008,6 +1026,12 @@ __global__ void __launch_bounds__(32) sweep2d_f32_kernel(const Sweep2D32Args A) 
     const int t = inrange ? u - rb * A.nx : 0;
     const int r = rb * H + lane;
     const bool act = inrange && r < A.ny;
+    const int m_cur = m_next;
+    const float4 sv_cur = sv_next;
+    {
+      int c1;
+      if (cell_at(s + 1, c1)) m_next = A.mat[c1], sv_next = Sb[c1];
+    }
     float ty[DPW][2];
 #pragma unroll
     for (int dd = 0; dd < DPW; ++dd) {
@@ -1032,8 +1056,8 @@ __global__ void __launch_bounds__(32) sweep2d_f32_kernel(const Sweep2D32Args A) 
       const int i = xneg ? A.nx - 1 - t : t;
       const int j = yneg ? A.ny - 1 - r : r;
       const int c = j * A.nx + i;
-      const int m = A.mat[c];
-      const float4 sv = Sb[c];
+      const int m = m_cur;
+      const float4 sv = sv_cur;
       float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
 #pragma unroll
       for (int dd = 0; dd < DPW; ++dd) {
