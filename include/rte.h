@@ -200,7 +200,9 @@ int rte_batch_tune(rte_batch_t batch, int dirs_per_warp);
 /* Empirical autotuner of the same choice: for B, B/2, B/4, ..., 1 running instances it times one
  * sweep with every allowed directions-per-warp value (CUDA events on `stream`, on the batch's
  * current parameters) and keeps the fastest per count; later sweeps pick the entry for the
- * smallest timed count >= their running instances.  Uses the batch's iteration scratch only.
+ * smallest timed count >= their running instances.  2D batches get a second table, measured the
+ * same way with the FP32 sweep of the precision variant (kept internally).  Uses the batch's
+ * iteration scratch only.
  *   n_entries  HOST int out (may be NULL); table HOST int[2*32] or NULL: (count, dirs_per_warp)
  * Synchronous.  rte_batch_tune resets it.  1D batches: no-op.  Errors: RTE_ESTATE (no
  * parameters), RTE_ECUDA. */

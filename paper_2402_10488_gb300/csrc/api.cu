@@ -288,15 +288,17 @@ static std::vector<SweepGroup> groups_for(const rte_disc_s* disc, int dpw) {
   return g;
 }
 
-void pick_groups(rte_batch_t b, int n_active, int* dpw, int* n_groups, const SweepGroup** dev) {
+void pick_groups(rte_batch_t b, int n_active, int* dpw, int* n_groups, const SweepGroup** dev,
+                 bool f32) {
   int use = b->dpw;
   auto kof = [](int v) { return v == 1 ? 0 : v == 2 ? 1 : v == 4 ? 2 : 3; };
+  const auto& tuned = f32 && !b->tuned32.empty() ? b->tuned32 : b->tuned;
   if (b->force_dpw && b->disc->dim == 2) {
     use = b->force_dpw;
   } else if (b->dpw_dynamic && b->disc->dim == 2) {
-    if (!b->tuned.empty()) {
-      use = b->tuned.back().second;
-      for (const auto& e : b->tuned)
+    if (!tuned.empty()) {
+      use = tuned.back().second;
+      for (const auto& e : tuned)
         if (n_active <= e.first) {
           use = e.second;
           break;
@@ -351,6 +353,7 @@ extern "C" int rte_batch_tune(rte_batch_t b, int dpw) {
   if (b->disc->dim == 1) return RTE_OK;
   b->dpw_dynamic = dpw == 0;
   b->tuned.clear();
+  b->tuned32.clear();
   if (dpw == 0) dpw = std::max(auto_dpw(b->disc, b->B), b->min_dpw);
   if (dpw != 1 && dpw != 2 && dpw != 4 && dpw != 8) return fail(RTE_EINVAL, "dirs_per_warp must be 0, 1, 2, 4 or 8");
   DeviceGuard g(b->disc->device);

@@ -158,6 +158,7 @@ struct rte_batch_s {
   // measured choice of the empirical autotuner: (largest number of running instances, dpw),
   // ascending; empty = the occupancy rule above
   std::vector<std::pair<int, int>> tuned;
+  std::vector<std::pair<int, int>> tuned32;   // the same, measured with the FP32 sweep
   int force_dpw = 0;                  // autotuner trials: this dpw for every launch
   bool kba = true;                    // several warps per direction group when warps are scarce
   std::vector<double> sigma_t_h, sigma_s_h, source_h, inflow_h;
@@ -232,7 +233,8 @@ struct PhaseScope {
 void make_groups(rte_batch_t b);
 int auto_dpw(const rte_disc_s* disc, int B);
 // groups of one launch: dpw, number of groups and their device table
-void pick_groups(rte_batch_t b, int n_active, int* dpw, int* n_groups, const SweepGroup** dev);
+void pick_groups(rte_batch_t b, int n_active, int* dpw, int* n_groups, const SweepGroup** dev,
+                 bool f32 = false);
 // sweep.cu
 int sweep_launch(rte_batch_t b, const double* rho_in, double* rho_out, double* psi_out,
                  int with_source, const uint8_t* active, cudaStream_t st, bool fuse_norms,

@@ -1250,6 +1250,14 @@ static int dsa2d_vcycles(rte_batch_t bt, const double* R, double* drho, int k,
   DsaState* s = bt->dsa;
   const int B = bt->B, nc = bt->disc->n_cells, per = nc * NB;
   const dim3 gv((per + 255) / 256, B), gvc(std::min((per + 255) / 256, 1024), B);
+  if (k == 1) {
+    // one cycle: pack the right-hand side straight into level 0 and read the result from there
+    pack_rhs32_kernel<<<gv, 256, 0, st>>>(R, s->bl[0]->p, nc, active); RTE_NOTE_LAUNCH();
+    RTE_TRY(vcycle(bt, 0, active, st, bt->dsa_nu));
+    extract_rho32_kernel<<<dim3((nc * 4 + 255) / 256, B), 256, 0, st>>>(s->xl[0]->p, drho, nc, active); RTE_NOTE_LAUNCH();
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+  }
   pack_rhs32_kernel<<<gv, 256, 0, st>>>(R, s->borig.p, nc, active); RTE_NOTE_LAUNCH();
   const LevelC L0 = lvl_of(bt, 0);
   for (int it = 0; it < k; ++it) {

@@ -1168,7 +1168,7 @@ int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, cons
   }
   int dpw = bt->dpw, n_groups = 0;
   const SweepGroup* gdev = nullptr;
-  pick_groups(bt, n_active, &dpw, &n_groups, &gdev);
+  pick_groups(bt, n_active, &dpw, &n_groups, &gdev, true);
   const size_t need32 = bt->partial.n;  // the same group-slice capacity as the FP64 partial sums
   if (bt->partial32.n < need32) RTE_TRY(bt->partial32.alloc(need32));
   if (bt->tables32_stale) {
@@ -1216,7 +1216,9 @@ int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, cons
 namespace rte {
 // Empirical choice of the sweep decomposition: for running-instance counts B, B/2, B/4, ..., 1
 // (the first instances of the batch) every directions-per-warp value the partial-sum buffer
-// allows is timed with CUDA events on `st`, and the fastest is kept per count.
+// allows is timed with CUDA events on `st`, and the fastest is kept per count -- separately for
+// the FP64 sweep and for the FP32 sweep of the precision variant (which is bound by the latency of
+// its wavefront rather than by the FP64 pipe, so it may want more, narrower warps).
 static int autotune(rte_batch_t bt, cudaStream_t st, int* n_entries, int* table) {
   const rte_disc_s* d = bt->disc;
   const int B = bt->B;
@@ -1233,6 +1235,7 @@ static int autotune(rte_batch_t bt, cudaStream_t st, int* n_entries, int* table)
   const bool timing = bt->timing;
   bt->timing = false;
   bt->tuned.clear();
+  bt->tuned32.clear();
   int status = RTE_OK;
   RTE_CUDA_TRY(cudaMemsetAsync(bt->work.p, 0, sizeof(double) * nb, st));
   for (int n : bands) {
@@ -1241,25 +1244,31 @@ static int autotune(rte_batch_t bt, cudaStream_t st, int* n_entries, int* table)
       status = fail(RTE_ECUDA, "autotune: mask upload");
       break;
     }
-    float best_ms = 0.f;
-    int best = 0;
-    for (int dpw = 1; dpw <= kMaxDirsPerWarp && status == RTE_OK; dpw *= 2) {
-      const int k = dpw == 1 ? 0 : dpw == 2 ? 1 : dpw == 4 ? 2 : 3;
-      if ((size_t)n * bt->gcount[k] * d->n_dof > bt->partial.n) continue;  // no partial-sum space
-      bt->force_dpw = dpw;
-      float ms = 0.f;
-      status = sweep_launch(bt, bt->work.p, bt->work.p + nb, nullptr, 1, mask.p, st, true, n);
-      if (status == RTE_OK && cudaEventRecord(e0, st) != cudaSuccess) status = fail(RTE_ECUDA, "autotune: event");
-      for (int rep = 0; rep < 2 && status == RTE_OK; ++rep)
-        status = sweep_launch(bt, bt->work.p, bt->work.p + nb, nullptr, 1, mask.p, st, true, n);
-      if (status == RTE_OK && (cudaEventRecord(e1, st) != cudaSuccess ||
-                               cudaEventSynchronize(e1) != cudaSuccess ||
-                               cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-        status = fail(RTE_ECUDA, "autotune: timing");
-      if (status == RTE_OK && (best == 0 || ms < best_ms)) best_ms = ms, best = dpw;
+    for (int prec = 0; prec < (d->dim == 2 ? 2 : 1) && status == RTE_OK; ++prec) {
+      float best_ms = 0.f;
+      int best = 0;
+      auto launch = [&]() {
+        return prec == 0 ? sweep_launch(bt, bt->work.p, bt->work.p + nb, nullptr, 1, mask.p, st, true, n)
+                         : sweep_launch_f32(bt, bt->work.p, bt->work.p + nb, mask.p, st, n);
+      };
+      for (int dpw = 1; dpw <= kMaxDirsPerWarp && status == RTE_OK; dpw *= 2) {
+        const int k = dpw == 1 ? 0 : dpw == 2 ? 1 : dpw == 4 ? 2 : 3;
+        if ((size_t)n * bt->gcount[k] * d->n_dof > bt->partial.n) continue;  // no partial-sum space
+        bt->force_dpw = dpw;
+        float ms = 0.f;
+        status = launch();
+        if (status == RTE_OK && cudaEventRecord(e0, st) != cudaSuccess) status = fail(RTE_ECUDA, "autotune: event");
+        for (int rep = 0; rep < 2 && status == RTE_OK; ++rep) status = launch();
+        if (status == RTE_OK && (cudaEventRecord(e1, st) != cudaSuccess ||
+                                 cudaEventSynchronize(e1) != cudaSuccess ||
+                                 cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+          status = fail(RTE_ECUDA, "autotune: timing");
+        if (status == RTE_OK && (best == 0 || ms < best_ms)) best_ms = ms, best = dpw;
+      }
+      if (status != RTE_OK) break;
+      (prec == 0 ? bt->tuned : bt->tuned32).emplace_back(n, best);
     }
     if (status != RTE_OK) break;
-    bt->tuned.emplace_back(n, best);
   }
   bt->force_dpw = 0;
   bt->timing = timing;
@@ -1267,6 +1276,7 @@ static int autotune(rte_batch_t bt, cudaStream_t st, int* n_entries, int* table)
   cudaEventDestroy(e1);
   if (status != RTE_OK) {
     bt->tuned.clear();
+    bt->tuned32.clear();
     return status;
   }
   bt->dpw_dynamic = true;
