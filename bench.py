@@ -68,9 +68,9 @@ def parse():
     ap.add_argument("--dsa-rtol", type=float, default=0.0, help="0: fixed V-cycles")
     ap.add_argument("--dsa-vcycles", type=int, default=1)
     ap.add_argument("--dsa-nu", type=int, default=2, help="DSA multigrid smoothing sweeps per level")
-    ap.add_argument("--dsa-blocking", type=int, default=-1,
-                    help="1: temporally blocked DSA smoother, 0: one launch per half sweep, "
-                         "-1: the library default")
+    ap.add_argument("--dsa-smoother", type=int, default=-1,
+                    help="DSA smoother form: 0 global, 1 shared-memory tiles, 2 temporally "
+                         "blocked, -1 the library default")
     ap.add_argument("--fp32-switch", type=float, default=1e-5,
                     help="precision variant: FP32 sweeps until the relative change is below this")
     ap.add_argument("--dpw", type=int, default=-1,
@@ -271,8 +271,8 @@ def run_ours(a, ws, rank, local):
     batch = rte.Batch(disc, B)
     batch.tune(max(a.dpw, 0))
     batch.dsa_smoothing(a.dsa_nu)
-    if a.dsa_blocking >= 0:
-        batch.dsa_blocking(a.dsa_blocking)
+    if a.dsa_smoother >= 0:
+        batch.dsa_smoother(a.dsa_smoother)
     batch.set_params(test)
     tuned = batch.autotune() if a.dpw < 0 else None
     n_dof = disc.n_dof

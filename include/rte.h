@@ -160,12 +160,21 @@ int rte_batch_set_slots(rte_batch_t batch, int n, const int* slots, const double
  * fixed point of Alg. 1 does not depend on the DSA).  Errors: RTE_EINVAL. */
 int rte_batch_dsa_smoothing(rte_batch_t batch, int nu);
 
-/* on = 1: the nu smoothing sweeps of a multigrid level run as one launch that keeps a 16 x 16
- * tile of cells and a halo of 2 nu cells in shared memory (temporal blocking, nu <= 4); 0 (the
- * default): one launch per colour per sweep.  Both compute the same values bit for bit; the
- * blocked form reads x and b once instead of 2 nu times but updates 1.4x as many cells (the
- * shrinking halo), which on GB300 costs more than it saves.  Errors: RTE_EINVAL. */
-int rte_batch_dsa_blocking(rte_batch_t batch, int on);
+/* Form of the red-black smoother on the multigrid levels that run one launch per step (the
+ * levels coarser than 32 x 32 cells run inside one fused kernel per instance).  All three compute
+ * the same values bit for bit:
+ *   RTE_SMOOTHER_GLOBAL   one launch per half sweep, each cell reading its neighbours from global
+ *                         memory
+ *   RTE_SMOOTHER_TILED    one launch per half sweep on 16 x 16 tiles: the other colour's cells of a
+ *                         tile and a one-cell halo are loaded into shared memory once
+ *   RTE_SMOOTHER_BLOCKED  the nu sweeps in one launch on 16 x 16 tiles with a halo of 2 nu cells
+ *                         in shared memory (temporal blocking, nu <= 4): x and b read once, but
+ *                         1.4x the cell updates (the shrinking halo)
+ * Default: the measured fastest on GB300 (see the library's design notes).  Errors: RTE_EINVAL. */
+#define RTE_SMOOTHER_GLOBAL 0
+#define RTE_SMOOTHER_TILED 1
+#define RTE_SMOOTHER_BLOCKED 2
+int rte_batch_dsa_smoother(rte_batch_t batch, int kind);
 
 /* info (HOST int64[6]): B, device bytes held by the batch, directions per warp (preferred),
  * the smallest directions per warp its sweep partial sums are sized for, 1 if the

@@ -185,6 +185,7 @@ struct rte_batch_s {
   rte::DsaState* dsa = nullptr;
   int dsa_nu = 2;                         // red-black smoothing sweeps per multigrid level (2D DSA)
   bool dsa_blocking = false;              // smoothing sweeps of a level in one temporally blocked launch
+  bool dsa_tiled = false;                 // half sweeps on shared-memory tiles (rbgs_tiled_kernel)
   // pinned host staging for per-slot parameter uploads (rte_batch_set_slots), allocated on use
   double* stage = nullptr;
   uint8_t* stage_mask = nullptr;

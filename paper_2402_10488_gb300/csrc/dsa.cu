@@ -488,6 +488,56 @@ __global__ void __launch_bounds__(256) rbgs_fused_kernel(LevelC L, Coup K, int H
   }
 }
 
+// One red-black half sweep on 16 x 16 tiles: the CTA first loads the cells of the other colour
+// on its tile and a one-cell halo into shared memory with coalesced 16-byte loads (each such cell
+// once, instead of once per neighbour that reads it), then each of its 128 threads updates one
+// cell of `color` from there.  Cells of `color` are only written and cells of the other colour
+// only read, so the update is in place.  Same arithmetic as rbgs_kernel, bit for bit.
+constexpr int kTT = 16;  // tile side
+
+__global__ void __launch_bounds__(128) rbgs_tiled_kernel(LevelC L, Coup K, int color,
+                                                         const uint8_t* active) {
+  const int b = blockIdx.z;
+  if (active && !active[b]) return;
+  constexpr int R = kTT + 2;
+  __shared__ float4 xs4[R * R * 3];
+  __shared__ float4 dsh4[kSmemClasses * NB2 / 4];
+  float* xs = reinterpret_cast<float*>(xs4);
+  float* xg = L.x + (size_t)b * L.nc * NB;
+  const int i0 = blockIdx.x * kTT - 1, j0 = blockIdx.y * kTT - 1;  // region origin
+  for (int t = threadIdx.x; t < R * R * 3; t += blockDim.x) {
+    const int cell = t / 3, q = t % 3, gi = i0 + cell % R, gj = j0 + cell / R;
+    if (gi >= 0 && gi < L.nx && gj >= 0 && gj < L.ny && ((gi + gj) & 1) != color)
+      xs4[t] = reinterpret_cast<const float4*>(xg + ((size_t)gj * L.nx + gi) * NB)[q];
+  }
+  const float* dg = L.dinv + (size_t)b * L.n_class * NB2;
+  const bool dsm = L.n_class <= kSmemClasses;
+  if (dsm)
+    for (int t = threadIdx.x; t < L.n_class * NB2 / 4; t += blockDim.x)
+      dsh4[t] = reinterpret_cast<const float4*>(dg)[t];
+  __syncthreads();
+  // thread k: tile row k / 8, the (k % 8)-th cell of `color` in that row
+  const int rr = threadIdx.x >> 3, gj = j0 + 1 + rr;
+  const int ci = 2 * (threadIdx.x & 7) + ((color - gj - (i0 + 1)) & 1), gi = i0 + 1 + ci;
+  if (gi >= L.nx || gj >= L.ny) return;
+  const int cell = (rr + 1) * R + ci + 1;
+  float acc[NB];
+#pragma unroll
+  for (int r = 0; r < NB; ++r) acc[r] = 0.f;
+  nbr_trace_sum_p(K, L.qx, L.qy, gi > 0 ? xs + (size_t)(cell - 1) * NB : nullptr,
+                  gi + 1 < L.nx ? xs + (size_t)(cell + 1) * NB : nullptr,
+                  gj > 0 ? xs + (size_t)(cell - R) * NB : nullptr,
+                  gj + 1 < L.ny ? xs + (size_t)(cell + R) * NB : nullptr, acc);
+  const int c = gj * L.nx + gi;
+  float res[NB];
+  load12(L.b + ((size_t)b * L.nc + c) * NB, res);
+#pragma unroll
+  for (int r = 0; r < NB; ++r) res[r] -= acc[r];
+  float out[NB];
+  matvec12((dsm ? reinterpret_cast<const float*>(dsh4) : dg) + (size_t)L.cls[c] * NB2, res, out);
+  store12(xg + (size_t)c * NB, out);
+}
+
 __global__ void residual_kernel(LevelC L, Coup K, const uint8_t* active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
@@ -1176,9 +1226,15 @@ static int vcycle(rte_batch_t bt, int l, const uint8_t* active, cudaStream_t st,
   RTE_CUDA_TRY(cudaMemsetAsync(L.x, 0, sizeof(float) * (size_t)B * L.nc * NB, st));
   const int ncol = ((L.nx + 1) / 2) * L.ny;
   const dim3 gcol((ncol + 127) / 128, B);
+  const dim3 gtile((L.nx + kTT - 1) / kTT, (L.ny + kTT - 1) / kTT, B);
   auto smooth = [&](int c0) {
-    rbgs_kernel<<<gcol, 128, 0, st>>>(L, s->K, c0, active); RTE_NOTE_LAUNCH();
-    rbgs_kernel<<<gcol, 128, 0, st>>>(L, s->K, 1 - c0, active); RTE_NOTE_LAUNCH();
+    if (bt->dsa_tiled) {
+      rbgs_tiled_kernel<<<gtile, 128, 0, st>>>(L, s->K, c0, active); RTE_NOTE_LAUNCH();
+      rbgs_tiled_kernel<<<gtile, 128, 0, st>>>(L, s->K, 1 - c0, active); RTE_NOTE_LAUNCH();
+    } else {
+      rbgs_kernel<<<gcol, 128, 0, st>>>(L, s->K, c0, active); RTE_NOTE_LAUNCH();
+      rbgs_kernel<<<gcol, 128, 0, st>>>(L, s->K, 1 - c0, active); RTE_NOTE_LAUNCH();
+    }
   };
   // nu sweeps starting with colour c0: one temporally blocked launch, or 2 nu launches
   const bool blocked = bt->dsa_blocking && 2 * nu <= kFusedMaxH;
@@ -1503,9 +1559,11 @@ extern "C" int rte_dsa_correction(rte_batch_t b, const double* R, double* drho, 
   return s;
 }
 
-extern "C" int rte_batch_dsa_blocking(rte_batch_t b, int on) {
-  if (!b || (on != 0 && on != 1)) return fail(RTE_EINVAL, "rte_batch_dsa_blocking: need on = 0 or 1");
-  b->dsa_blocking = on != 0;
+extern "C" int rte_batch_dsa_smoother(rte_batch_t b, int kind) {
+  if (!b || kind < RTE_SMOOTHER_GLOBAL || kind > RTE_SMOOTHER_BLOCKED)
+    return fail(RTE_EINVAL, "rte_batch_dsa_smoother: unknown smoother");
+  b->dsa_tiled = kind == RTE_SMOOTHER_TILED;
+  b->dsa_blocking = kind == RTE_SMOOTHER_BLOCKED;
   return RTE_OK;
 }
 

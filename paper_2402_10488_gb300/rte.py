@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "librte_gb300.so")
 
 RTE_OK, RTE_EINVAL, RTE_ENOMEM, RTE_ENOCONV, RTE_ETIMEOUT, RTE_ECUDA, RTE_ESTATE = 0, -1, -2, -3, -4, -5, -6
 SA_NONE, SA_DSA, SA_ROMSA, SA_ROMSAD = 0, 1, 2, 3
+SMOOTHER_GLOBAL, SMOOTHER_TILED, SMOOTHER_BLOCKED = 0, 1, 2
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -64,7 +65,7 @@ SIGNATURES = {
     "rte_server_destroy": (_I, [_P]),
     "rte_pgmres": (_I, [_P, _P, _P, _P, _P]),
     "rte_batch_dsa_smoothing": (_I, [_P, _I]),
-    "rte_batch_dsa_blocking": (_I, [_P, _I]),
+    "rte_batch_dsa_smoother": (_I, [_P, _I]),
     "rte_pod_workspace_bytes": (_I, [_I, _I, _I, _P]),
     "rte_pod_project_bf16": (_I, [_P, _I, _I, _P, _I, _P, _P, _P, _P]),
     "rte_pod_lift_bf16": (_I, [_P, _I, _I, _P, _I, _P, _P, _P, _P]),
@@ -297,9 +298,10 @@ class Batch:
         """Red-black smoothing sweeps per multigrid level of the 2D DSA (rte_batch_dsa_smoothing)."""
         check(lib().rte_batch_dsa_smoothing(self.h, int(nu)))
 
-    def dsa_blocking(self, on):
-        """Temporally blocked smoothing launches in the 2D DSA multigrid (rte_batch_dsa_blocking)."""
-        check(lib().rte_batch_dsa_blocking(self.h, 1 if on else 0))
+    def dsa_smoother(self, kind):
+        """Form of the 2D DSA multigrid smoother: SMOOTHER_GLOBAL / _TILED / _BLOCKED
+        (rte_batch_dsa_smoother)."""
+        check(lib().rte_batch_dsa_smoother(self.h, int(kind)))
 
     def info(self):
         out = np.zeros(6, np.int64)

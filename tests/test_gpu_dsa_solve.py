@@ -249,11 +249,12 @@ def test_gang_wait_changes_when_instances_sweep_not_what_they_compute():
 
 
 @pytest.mark.parametrize("case,nu", [("lattice", 2), ("lattice", 1), ("ragged", 3), ("ragged", 2)])
-def test_blocked_smoother_is_bit_identical_to_one_launch_per_half_sweep(case, nu):
-    """The temporally blocked smoother (nu sweeps of a level in one launch on shared-memory tiles
-    with a shrinking halo) computes every cell update as the one-launch-per-colour smoother does,
-    in the same order: the DSA corrections (fixed V-cycles) agree bit for bit, with an active mask,
-    on a mesh whose levels have partial tiles."""
+def test_smoother_forms_are_bit_identical(case, nu):
+    """The three forms of the red-black smoother -- one launch per half sweep reading neighbours
+    from global memory, half sweeps on shared-memory tiles, and nu sweeps in one temporally blocked
+    launch with a shrinking halo -- compute every cell update with the same arithmetic in the same
+    order: the DSA corrections (fixed V-cycles) agree bit for bit, with an active mask, on a mesh
+    whose levels have partial tiles, on two calls in a row."""
     rte = _rte()
     if case == "lattice":
         p = inputs.lattice_test(128, 16, 5, n_vz=2)
@@ -262,17 +263,17 @@ def test_blocked_smoother_is_bit_identical_to_one_launch_per_half_sweep(case, nu
     R = np.random.default_rng(9).uniform(-1, 1, (p.batch, p.n_dof))
     act = torch.tensor(np.array([1, 0, 1, 1, 1][:p.batch], np.uint8), device="cuda")
     out = []
-    for blocked in (False, True):
+    for kind in (rte.SMOOTHER_GLOBAL, rte.SMOOTHER_TILED, rte.SMOOTHER_BLOCKED):
         b = rte.Batch.from_problem(p)
         b.dsa_smoothing(nu)
-        b.dsa_blocking(blocked)
+        b.dsa_smoother(kind)
         Rt = _dev(R)
         d = torch.full_like(Rt, 7.0)
-        for _ in range(2):   # twice: the second call starts from the swapped buffers
+        for _ in range(2):   # twice: the second call starts from the buffers the first left
             b.dsa_correction(Rt, d, rtol=0.0, max_it=2, active=act)
         torch.cuda.synchronize()
         out.append(d.cpu().numpy())
-    assert np.array_equal(out[0], out[1])
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
     assert np.all(out[1][1] == 7.0) and np.isfinite(out[1]).all()
 
 
