@@ -194,6 +194,38 @@ def test_server_results_equal_alone_and_oracle(served, dpw):
             checked += 1
 
 
+def test_server_precision_variant_equals_alone_and_oracle(served):
+    """A bucket served with the precision variant (FP32 sweeps, then the FP64 outer residual
+    correction with gang waiting): with a fixed sweep decomposition every request returns bit for
+    bit what the same instance gives solved alone with the same options (waiting changes when an
+    instance sweeps, not what it computes), and the tightest ones match the oracle's direct solve."""
+    rte, disc0, rp, rc = served
+    b0 = rte.Batch(disc0, 3)
+    b0.tune(2)
+    b0.set_params(inputs.lattice_test(16, 16, 3))
+    o0 = dict(_romsad_opts(rc), fp32_switch=1e-4, refine_kappa=0.1, refine_inner=8, gang_wait=4)
+    rng = np.random.default_rng(17)
+    reqs = [(inputs.lattice_test(16, 16, 1, first=300 + i), float(rng.choice([1e-8, 1e-10])))
+            for i in range(8)]
+    srv = rte.Server()
+    srv.add_bucket(b0, None, rc, **o0)
+    srv.start()
+    tickets = [srv.submit(0, p.sigma_t[0], p.sigma_s[0], p.source[0], p.inflow[0], eps)
+               for p, eps in reqs]
+    results = [srv.wait(t, timeout=120.0) for t in tickets]
+    srv.close()
+    checked = 0
+    for (p, eps), (rho, rep) in zip(reqs, results):
+        assert rep["status"] == rte.RTE_OK and rep["converged"] and rep["n_sweep32"] > 0
+        ref, rref = _alone(rte, disc0, p, eps, o0, None, rc, 2)
+        assert np.array_equal(rho, ref), _rel(rho, ref)
+        assert rep["n_sweep"] == rref["n_sweep"] and rep["n_sweep32"] == rref["n_sweep32"]
+        if eps == 1e-10 and checked < 2:
+            assert _rel(rho, Transport(p, 0).solve_rho_direct()) < 1e-8
+            checked += 1
+    assert checked >= 1
+
+
 def test_server_admits_while_others_run(served):
     rte, disc0, rp, rc = served
     b0 = rte.Batch(disc0, 4)
