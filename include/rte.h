@@ -345,6 +345,15 @@ int rte_pod_project_bf16(const double* U, int r, int n, const double* X, int B,
 int rte_pod_lift_bf16(const double* U, int r, int n, const double* C, int B, const uint8_t* active,
                       double* Y, void* work, void* stream);
 
+/* Fault injection for tests of the failure path (no counterpart in the paper).  The device-side
+ * waits of the library (the tensor-core products' mbarrier waits) give up after about one second
+ * and set the caller's status word instead of hanging.  RTE_FAULT_LIFT_NO_MMA makes the next
+ * rte_pod_lift_bf16 launch (directly or inside a ROMSA correction with rom_bf16) issue no MMA, so
+ * its wait runs out: its status word becomes 1, its output is invalid, nothing is left in flight
+ * and the context stays usable.  One-shot; 0 clears.  Errors: RTE_EINVAL. */
+#define RTE_FAULT_LIFT_NO_MMA 1
+int rte_fault_inject(int what);
+
 /* ---- full solves (Alg. 1 with the SA of choice, Alg. 2) --------------------------------- */
 
 #define RTE_SA_NONE 0

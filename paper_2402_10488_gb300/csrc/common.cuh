@@ -284,7 +284,7 @@ int rom_prepare(rte_rom_t rom, rte_batch_t bt, cudaStream_t st, const uint8_t* m
 int rom_correction(rte_rom_t rom, rte_batch_t bt, const double* R, double* drho,
                    const uint8_t* active, cudaStream_t st, bool bf16 = false);
 // status word of the BF16 tensor-core products of this ROM's online state (0 if never used):
-// nonzero when a device-side wait gave up; read after the stream is synchronised
+// nonzero when a device-side wait gave up; read after the stream is synchronised, then cleared
 int rom_tc_status(rte_rom_t rom, int* status);
 // podtc.cu: BF16 tensor-core POD products (see rte_pod_project_bf16 / rte_pod_lift_bf16)
 size_t pod_project_ws_bytes(int n, int B, int n_sm);

@@ -34,7 +34,8 @@ constexpr int kProjK = 64;       // K elements per shared-memory stage of the pr
 constexpr int kProjN = 32;       // basis vectors per projection tile (r <= 32)
 constexpr int kLiftK = 32;       // r padded to the MMA's K granularity (2 x 16)
 constexpr int kLiftN = 256;      // instances per lift tile (the largest N of one MMA)
-constexpr long long kSpinLimit = 1ll << 22;  // polls of mbarrier.try_wait before giving up
+constexpr long long kSpinLimit = 1ll << 26;  // polls of mbarrier.try_wait at most
+constexpr uint64_t kWaitNs = 1000000000ull;   // and at most about one second of waiting
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -61,9 +62,18 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar) {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Bounded wait for the completion of phase `parity` of an mbarrier; false after kSpinLimit polls.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for the completion of phase `parity` of an mbarrier: false once about kWaitNs
+// nanoseconds (or kSpinLimit polls) have passed without it.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
   for (long long it = 0; it < kSpinLimit; ++it) {
+    if ((it & 255) == 255 && global_ns() - t0 > kWaitNs) return false;
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -255,6 +265,7 @@ struct LiftArgs {
   double* Y;        // [B][n]
   int* status;
   int r, n, B;
+  int no_mma;       // injected fault (tests of the failure path): issue no MMA, so the wait runs out
 };
 
 // One (128 entries of e, <= 256 instances) tile of the lift: Y[b][e] = sum_i U[i][e] C[b][i].
@@ -311,7 +322,7 @@ __global__ void __launch_bounds__(kTcThreads) pod_lift_tc_kernel(const LiftArgs 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tslot;
-  if (tid == 0) {
+  if (tid == 0 && !A.no_mma) {
     const uint32_t a0 = smem_addr(As), bb0 = smem_addr(Bs), idesc = idesc_bf16(128, npad);
 #pragma unroll
     for (int kk = 0; kk < kLiftK / 16; ++kk)
@@ -345,6 +356,9 @@ constexpr size_t kLiftSmemReq = kLiftSmem > 80 * 1024 ? kLiftSmem : 80 * 1024;
 }  // namespace
 
 // ---- host side -------------------------------------------------------------------------------
+
+// one-shot injected fault of the tensor-core products (rte_fault_inject)
+static std::atomic<int> g_fault{0};
 
 // Chunking of the projection's K range: about two CTAs per SM over all instance tiles.
 static void proj_chunks(int n, int B, int n_sm, int* kc, int* n_chunks, int* mt) {
@@ -391,7 +405,7 @@ int pod_lift_bf16(const double* U, int r, int n, const double* C, int B, const u
                                       (int)kLiftSmemReq));
     attr_set[dev] = true;
   }
-  LiftArgs A{U, C, active, Y, status, r, n, B};
+  LiftArgs A{U, C, active, Y, status, r, n, B, g_fault.exchange(0) == RTE_FAULT_LIFT_NO_MMA ? 1 : 0};
   pod_lift_tc_kernel<<<dim3((n + 127) / 128, (B + kLiftN - 1) / kLiftN), kTcThreads, kLiftSmemReq,
                        st>>>(A); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
@@ -407,6 +421,12 @@ static int sm_count() {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
   return n;
+}
+
+extern "C" int rte_fault_inject(int what) {
+  if (what != 0 && what != RTE_FAULT_LIFT_NO_MMA) return fail(RTE_EINVAL, "rte_fault_inject: unknown fault");
+  g_fault.store(what);
+  return RTE_OK;
 }
 
 extern "C" int rte_pod_workspace_bytes(int r, int n, int B, int64_t* bytes) {

@@ -897,6 +897,7 @@ int rom_tc_status(rte_rom_t rom, int* status) {
   *status = 0;
   if (!rom->online || !rom->online->tcws.p) return RTE_OK;
   RTE_CUDA_TRY(cudaMemcpy(status, rom->online->tcws.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (*status) RTE_CUDA_TRY(cudaMemset(rom->online->tcws.p, 0, sizeof(int)));  // reported once
   return RTE_OK;
 }
 

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "librte_gb300.so")
 RTE_OK, RTE_EINVAL, RTE_ENOMEM, RTE_ENOCONV, RTE_ETIMEOUT, RTE_ECUDA, RTE_ESTATE = 0, -1, -2, -3, -4, -5, -6
 SA_NONE, SA_DSA, SA_ROMSA, SA_ROMSAD = 0, 1, 2, 3
 SMOOTHER_GLOBAL, SMOOTHER_TILED, SMOOTHER_BLOCKED = 0, 1, 2
+FAULT_LIFT_NO_MMA = 1
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -69,6 +70,7 @@ SIGNATURES = {
     "rte_pod_workspace_bytes": (_I, [_I, _I, _I, _P]),
     "rte_pod_project_bf16": (_I, [_P, _I, _I, _P, _I, _P, _P, _P, _P]),
     "rte_pod_lift_bf16": (_I, [_P, _I, _I, _P, _I, _P, _P, _P, _P]),
+    "rte_fault_inject": (_I, [_I]),
 }
 
 
@@ -92,6 +94,11 @@ def pod_lift_bf16(U, C, Y, work, active=None, stream=None):
     r, n = U.shape
     check(lib().rte_pod_lift_bf16(_ptr(U), int(r), int(n), _ptr(C), int(C.shape[0]),
                                   _ptr(active), _ptr(Y), _ptr(work), _stream(stream)))
+
+
+def fault_inject(what):
+    """One-shot injected fault for tests of the failure path (rte_fault_inject)."""
+    check(lib().rte_fault_inject(int(what)))
 
 
 def launch_count() -> int:

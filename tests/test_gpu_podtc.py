@@ -14,6 +14,8 @@ Pins, derived:
     ROM products converges to the oracle's solution at the FP64 tolerance (1e-10) and needs at most
     two more sweeps than with FP64 products.
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -140,3 +142,45 @@ def test_romsad_with_bf16_rom_products_reaches_the_fp64_solution(refine):
         tr = Transport(p, b)
         ref = sisa(tr, np.zeros(tr.n_dof), 1e-14, 400, "dsa", dsa=ConsistentDSA(tr), tol_mode="rel")
         assert np.abs(rho.cpu().numpy()[b] - ref["rho"]).max() / np.abs(ref["rho"]).max() < 1e-10
+
+
+def test_injected_wait_timeout_sets_status_and_leaves_the_context_usable():
+    """Failure path of the device-side waits: an injected fault makes the next lift launch issue no
+    MMA, so its bounded mbarrier wait runs out (about a second); the status word reports it, nothing
+    is left in flight, and the next call on the same context is exact again.  Inside a solve with
+    BF16 ROM products the same fault ends the solve with RTE_ETIMEOUT, and the following solve on
+    the same batch and ROM succeeds."""
+    rte = _rte()
+    rng = np.random.default_rng(5)
+    r, n, B = 8, 256, 4
+    U, C = _ints(rng, (r, n)), _ints(rng, (B, r))
+    Y = torch.zeros((B, n), dtype=torch.float64, device="cuda")
+    work = rte.pod_workspace(r, n, B)
+    rte.fault_inject(rte.FAULT_LIFT_NO_MMA)
+    t0 = time.perf_counter()
+    rte.pod_lift_bf16(U, C, Y, work)
+    torch.cuda.synchronize()
+    assert time.perf_counter() - t0 < 30.0
+    assert int(work[:4].view(torch.int32)[0]) == 1
+    work.zero_()
+    rte.pod_lift_bf16(U, C, Y, work)   # one-shot: this call is clean
+    torch.cuda.synchronize()
+    assert torch.equal(Y, C @ U) and int(work[:4].view(torch.int32)[0]) == 0
+
+    p = inputs.lattice_test(16, 16, 2, n_vz=2)
+    batch = rte.Batch.from_problem(p)
+    train = inputs.lattice_train(16, 16, n_train=4, n_vz=2)
+    tb = rte.Batch(batch.disc, 4)
+    tb.set_params(train)
+    _, rc = rte.Rom.build(tb, eps_train=1e-12, window=2, rank_p=3, rank_c=4, max_iter=300,
+                          dsa_rtol=1e-10)
+    kw = dict(sa=rte.SA_ROMSAD, rom_c=rc, theta=5, eps_romsad=0.1 * max(1e-12, rc.eps_pod),
+              rel=True, max_iter=300, dsa_rtol=0.0, dsa_max_it=2, rom_bf16=True)
+    rho = torch.zeros((2, p.n_dof), dtype=torch.float64, device="cuda")
+    rte.fault_inject(rte.FAULT_LIFT_NO_MMA)
+    with pytest.raises(rte.RTEError) as e:
+        batch.solve(rho, 1e-12, **kw)
+    assert e.value.status == rte.RTE_ETIMEOUT
+    rho.zero_()
+    rep, _, st = batch.solve(rho, 1e-12, **kw)
+    assert st == rte.RTE_OK and all(x["converged"] and x["n_romsa"] >= 1 for x in rep)
