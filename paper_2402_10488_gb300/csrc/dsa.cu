@@ -409,6 +409,67 @@ __global__ void rbgs_kernel(LevelC L, Coup K, int color, const uint8_t* active) 
   rbgs_cell(L, K, b, j * L.nx + i, dsm ? reinterpret_cast<const float*>(dsh4) : dg);
 }
 
+// The first half sweep of post-smoothing with the prolongation x += P x_coarse folded in.  That
+// half sweep overwrites the cells of `color` without reading them, so their prolongation is never
+// needed, and the other colour's cells enter only as its neighbours: each neighbour's 12 values are
+// corrected in registers with prolong_entry's arithmetic (the same single rounding as the stored
+// sum) and the stored x of the other colour is left as it was -- the next half sweep recomputes
+// those cells from scratch.  Saves the separate pass of prolong_add_kernel over x; bit for bit the
+// same results.
+__device__ __forceinline__ void nbr_prolonged(const float* __restrict__ xb, const LevelC& Cl, int b,
+                                              int ii, int jj, int nx, float v[NB]) {
+  load12(xb + ((size_t)jj * nx + ii) * NB, v);
+  const int C = (jj / 2) * Cl.nx + ii / 2, dx = ii & 1, dy = jj & 1;
+  const float* xc = Cl.x + ((size_t)b * Cl.nc + C) * NB;
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+#pragma unroll
+    for (int kf = 0; kf < 4; ++kf) {
+      float s = 0.f;
+#pragma unroll
+      for (int kc = 0; kc < 4; ++kc) s = fmaf(pk(dx, dy, kf, kc), xc[4 * f + kc], s);
+      v[4 * f + kf] += s;
+    }
+}
+
+__global__ void rbgs_prolong_kernel(LevelC L, LevelC Cl, Coup K, int color, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  __shared__ float4 dsh4[kSmemClasses * NB2 / 4];
+  const float* dg = L.dinv + (size_t)b * L.n_class * NB2;
+  const bool dsm = L.n_class <= kSmemClasses;
+  if (dsm) {
+    for (int t = threadIdx.x; t < L.n_class * NB2 / 4; t += blockDim.x)
+      dsh4[t] = reinterpret_cast<const float4*>(dg)[t];
+    __syncthreads();
+  }
+  const int hx2 = (L.nx + 1) / 2;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= hx2 * L.ny) return;
+  const int j = idx / hx2;
+  const int i = 2 * (idx % hx2) + ((j + color) & 1);
+  if (i >= L.nx) return;
+  const int c = j * L.nx + i;
+  float* xb = L.x + (size_t)b * L.nc * NB;
+  float vw[NB], ve[NB], vs[NB], vn[NB];
+  if (i > 0) nbr_prolonged(xb, Cl, b, i - 1, j, L.nx, vw);
+  if (i + 1 < L.nx) nbr_prolonged(xb, Cl, b, i + 1, j, L.nx, ve);
+  if (j > 0) nbr_prolonged(xb, Cl, b, i, j - 1, L.nx, vs);
+  if (j + 1 < L.ny) nbr_prolonged(xb, Cl, b, i, j + 1, L.nx, vn);
+  float acc[NB];
+#pragma unroll
+  for (int r = 0; r < NB; ++r) acc[r] = 0.f;
+  nbr_trace_sum_p(K, L.qx, L.qy, i > 0 ? vw : nullptr, i + 1 < L.nx ? ve : nullptr,
+                  j > 0 ? vs : nullptr, j + 1 < L.ny ? vn : nullptr, acc);
+  float res[NB];
+  load12(L.b + ((size_t)b * L.nc + c) * NB, res);
+#pragma unroll
+  for (int r = 0; r < NB; ++r) res[r] -= acc[r];
+  float out[NB];
+  matvec12((dsm ? reinterpret_cast<const float*>(dsh4) : dg) + (size_t)L.cls[c] * NB2, res, out);
+  store12(xb + (size_t)c * NB, out);
+}
+
 // Red-black Gauss-Seidel with temporal blocking: H = 2 nu half sweeps of one level, colours c0,
 // 1 - c0, c0, ..., on a 16 x 16 tile per CTA, in shared memory.  The CTA loads x and b on the tile
 // and a halo of H cells, then half sweep h updates the cells of its colour within H - 1 - h cells
@@ -1238,7 +1299,8 @@ static int vcycle(rte_batch_t bt, int l, const uint8_t* active, cudaStream_t st,
   };
   // nu sweeps starting with colour c0: one temporally blocked launch, or 2 nu launches
   const bool blocked = bt->dsa_blocking && 2 * nu <= kFusedMaxH;
-  auto smooth_nu = [&](int c0) -> int {
+  // pro: the coarse level whose prolongation is folded into the first half sweep (global form)
+  auto smooth_nu = [&](int c0, const LevelC* pro) -> int {
     if (blocked) {
       const size_t bytes = fused_smem_bytes(2 * nu);
       RTE_TRY(fused_smem_attr(bytes));
@@ -1246,19 +1308,26 @@ static int vcycle(rte_batch_t bt, int l, const uint8_t* active, cudaStream_t st,
           L, s->K, 2 * nu, c0, L.r, active); RTE_NOTE_LAUNCH();
       std::swap(s->xl[l], s->rl[l]);  // the smoothed iterate is now the level's x
       L = lvl_of(bt, l);
+    } else if (pro) {
+      rbgs_prolong_kernel<<<gcol, 128, 0, st>>>(L, *pro, s->K, c0, active); RTE_NOTE_LAUNCH();
+      rbgs_kernel<<<gcol, 128, 0, st>>>(L, s->K, 1 - c0, active); RTE_NOTE_LAUNCH();
+      for (int k = 1; k < nu; ++k) smooth(c0);
     } else {
       for (int k = 0; k < nu; ++k) smooth(c0);
     }
     return RTE_OK;
   };
-  RTE_TRY(smooth_nu(0));
+  RTE_TRY(smooth_nu(0, nullptr));
   residual_kernel<<<dim3((L.nc + 127) / 128, B), 128, 0, st>>>(L, s->K, active); RTE_NOTE_LAUNCH();
   LevelC Cl = lvl_of(bt, l + 1);
   restrict_kernel<<<dim3((Cl.nc * NB + 255) / 256, B), 256, 0, st>>>(L, Cl, active); RTE_NOTE_LAUNCH();
   RTE_TRY(vcycle(bt, l + 1, active, st, nu));
   Cl = lvl_of(bt, l + 1);
-  prolong_add_kernel<<<dim3((L.nc * NB + 255) / 256, B), 256, 0, st>>>(L, Cl, active); RTE_NOTE_LAUNCH();
-  RTE_TRY(smooth_nu(1));
+  const bool fold = !blocked && !bt->dsa_tiled;  // the global form folds the prolongation in
+  if (!fold) {
+    prolong_add_kernel<<<dim3((L.nc * NB + 255) / 256, B), 256, 0, st>>>(L, Cl, active); RTE_NOTE_LAUNCH();
+  }
+  RTE_TRY(smooth_nu(1, fold ? &Cl : nullptr));
   RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;
 }
