@@ -90,3 +90,33 @@ def test_server_create_and_destroy_without_buckets():
     stats = (ctypes.c_double * 8)()
     assert L.rte_server_stats(h, stats) == rte.RTE_OK and stats[2] == 0
     assert L.rte_server_destroy(h) == rte.RTE_OK
+
+
+def test_tensor_core_products_and_service_calls_check_arguments_on_the_host():
+    """The BF16 POD products, the workspace query, the smoother choice and the fault hook reject bad
+    arguments with RTE_EINVAL on the host, before any device memory is touched (the pointers below
+    are never dereferenced)."""
+    import ctypes
+
+    import numpy as np
+    L = rte.lib()
+    out = np.zeros(1, np.int64)
+    p_out = out.ctypes.data_as(ctypes.c_void_p)
+    assert L.rte_pod_workspace_bytes(20, 65536, 152, p_out) == rte.RTE_OK and out[0] > 256
+    small = int(out[0])
+    assert L.rte_pod_workspace_bytes(20, 4096, 152, p_out) == rte.RTE_OK and 0 < out[0] <= small
+    for r, n, B in ((33, 64, 2), (0, 64, 2), (20, 0, 2), (20, 64, 0)):
+        assert L.rte_pod_workspace_bytes(r, n, B, p_out) == rte.RTE_EINVAL
+    assert L.rte_pod_workspace_bytes(20, 64, 2, None) == rte.RTE_EINVAL
+    fake = ctypes.c_void_p(0x10000)          # 16-byte aligned, never dereferenced
+    odd = ctypes.c_void_p(0x10008)           # not 16-byte aligned
+    assert L.rte_pod_project_bf16(None, 20, 64, fake, 2, None, fake, fake, None) == rte.RTE_EINVAL
+    assert L.rte_pod_project_bf16(fake, 20, 64, fake, 2, None, fake, odd, None) == rte.RTE_EINVAL
+    assert "aligned" in L.rte_last_error().decode()
+    assert L.rte_pod_project_bf16(fake, 33, 64, fake, 2, None, fake, fake, None) == rte.RTE_EINVAL
+    assert L.rte_pod_lift_bf16(fake, 0, 64, fake, 2, None, fake, fake, None) == rte.RTE_EINVAL
+    assert L.rte_pod_lift_bf16(fake, 20, 64, fake, 0, None, fake, fake, None) == rte.RTE_EINVAL
+    assert L.rte_pod_lift_bf16(fake, 20, 64, None, 2, None, fake, fake, None) == rte.RTE_EINVAL
+    assert L.rte_batch_dsa_smoother(None, rte.SMOOTHER_GLOBAL) == rte.RTE_EINVAL
+    assert L.rte_fault_inject(7) == rte.RTE_EINVAL
+    assert L.rte_fault_inject(0) == rte.RTE_OK
