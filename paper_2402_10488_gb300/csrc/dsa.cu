@@ -102,29 +102,6 @@ static void field_block(const DsaMoments& m, const double DCx[16], const double 
     }
 }
 
-static void invert_host(const double* A, double* Ai, int n) {
-  std::vector<double> a(2 * n * n);
-  for (int r = 0; r < n; ++r)
-    for (int c = 0; c < 2 * n; ++c) a[r * 2 * n + c] = c < n ? A[r * n + c] : (c - n == r ? 1.0 : 0.0);
-  for (int k = 0; k < n; ++k) {
-    int p = k;
-    for (int r = k + 1; r < n; ++r)
-      if (std::fabs(a[r * 2 * n + k]) > std::fabs(a[p * 2 * n + k])) p = r;
-    if (p != k)
-      for (int c = 0; c < 2 * n; ++c) std::swap(a[k * 2 * n + c], a[p * 2 * n + c]);
-    const double piv = 1.0 / a[k * 2 * n + k];
-    for (int c = 0; c < 2 * n; ++c) a[k * 2 * n + c] *= piv;
-    for (int r = 0; r < n; ++r)
-      if (r != k) {
-        const double f = a[r * 2 * n + k];
-        if (f != 0.0)
-          for (int c = 0; c < 2 * n; ++c) a[r * 2 * n + c] -= f * a[k * 2 * n + c];
-      }
-  }
-  for (int r = 0; r < n; ++r)
-    for (int c = 0; c < n; ++c) Ai[r * n + c] = a[r * 2 * n + n + c];
-}
-
 // ---- device helpers -------------------------------------------------------------------------
 
 // ---- multigrid levels ----------------------------------------------------------------------------

@@ -270,7 +270,7 @@ struct LiftArgs {
 
 // One (128 entries of e, <= 256 instances) tile of the lift: Y[b][e] = sum_i U[i][e] C[b][i].
 __global__ void __launch_bounds__(kTcThreads) pod_lift_tc_kernel(const LiftArgs A) {
-  constexpr int kAbytes = 128 * kLiftK * 2, kBbytes = kLiftN * kLiftK * 2;
+  constexpr int kAbytes = 128 * kLiftK * 2;
   extern __shared__ __align__(1024) uint8_t dsm[];
   uint8_t* As = dsm;
   uint8_t* Bs = dsm + kAbytes;

@@ -944,16 +944,16 @@ __global__ void cell_source32_kernel(const double* __restrict__ rho, float* S,
   const double ss = sigma_s[(size_t)b * n_mat + mat[c]];
   const size_t o = ((size_t)b * n_cells + c) * 4;
   const double* r = rho + o;
-  double4 v = make_double4(r[0], r[1], r[2], r[3]);
+  double v0 = r[0], v1 = r[1], v2 = r[2], v3 = r[3];
   bool src = with_source;
   if (inner && inner[b]) {
     const double* x = x0 + o;
-    v.x -= x[0], v.y -= x[1], v.z -= x[2], v.w -= x[3];
+    v0 -= x[0], v1 -= x[1], v2 -= x[2], v3 -= x[3];
     src = false;
   }
-  const double s0 = fma(ss, v.x, src ? G0[(size_t)b * n_cells + c] : 0.0);
+  const double s0 = fma(ss, v0, src ? G0[(size_t)b * n_cells + c] : 0.0);
   reinterpret_cast<float4*>(S)[(size_t)b * n_cells + c] =
-      make_float4((float)s0, (float)(ss * v.y), (float)(ss * v.z), (float)(ss * v.w));
+      make_float4((float)s0, (float)(ss * v1), (float)(ss * v2), (float)(ss * v3));
 }
 
 struct Sweep2D32Args {
