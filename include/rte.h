@@ -160,9 +160,10 @@ int rte_batch_set_slots(rte_batch_t batch, int n, const int* slots, const double
  * fixed point of Alg. 1 does not depend on the DSA).  Errors: RTE_EINVAL. */
 int rte_batch_dsa_smoothing(rte_batch_t batch, int nu);
 
-/* Form of the red-black smoother on the multigrid levels that run one launch per step (the
- * levels coarser than 32 x 32 cells run inside one fused kernel per instance).  All three compute
- * the same values bit for bit:
+/* Form of the red-black block Gauss-Seidel smoother of the 2D DSA multigrid -- the solver of the
+ * consistent DSA system (App. B, carried to X-Y geometry) -- on the levels that run one launch per
+ * step (levels of at most 32 x 32 cells run inside one fused kernel per instance).  Changes only
+ * how the same sweeps are scheduled: all three compute the same values bit for bit:
  *   RTE_SMOOTHER_GLOBAL   one launch per half sweep, each cell reading its neighbours from global
  *                         memory
  *   RTE_SMOOTHER_TILED    one launch per half sweep on 16 x 16 tiles: the other colour's cells of a
