@@ -107,31 +107,40 @@ class ReducedModel:
         return self.U_rho @ dc
 
 
+def training_snapshots(train_problem, eps_train, window, n_iter=2000, tol_mode="abs"):
+    """The training solves of the offline stage: SI-DSA from rho = 0 for every training parameter,
+    the converged angular flux f^mu as a column of F (Sec. 3.1.1) and the correction snapshots
+    f^mu - f^{mu,(l)}, l < w_mu = min(n_conv, window), as columns of delta F (Sec. 3.2.1).
+    Returns (F, dF, n_conv, tr0) with tr0 the first instance's Transport."""
+    F_cols, dF_cols, n_conv = [], [], []
+    tr0 = None
+    for b in range(train_problem.batch):
+        tr = Transport(train_problem, b)
+        if tr0 is None:
+            tr0 = tr
+        dsa = ConsistentDSA(tr)
+        res = sisa(tr, np.zeros(tr.n_dof), eps_train, n_iter, "dsa", dsa=dsa,
+                   window=window, keep_f=True, tol_mode=tol_mode)
+        f = res["f"].reshape(-1)
+        F_cols.append(f)
+        n_conv.append(res["n_sweep"])
+        w_mu = min(res["n_sweep"], window)
+        for l in range(w_mu):
+            dF_cols.append(f - res["f_window"][l].reshape(-1))
+        if b > 0:
+            tr._lu = [None] * tr.n_angles  # free the factors of finished instances
+    return np.stack(F_cols, 1), np.stack(dF_cols, 1), n_conv, tr0
+
+
 class OfflineROMs:
     """Offline stage: training SI-DSA solves, snapshot matrices F and delta F, two POD bases."""
 
     def __init__(self, train_problem, eps_train=1e-12, window=3, rank_p=None, rank_c=None,
                  eps_pod=None, n_iter=2000, tol_mode="abs", correction_start="zero"):
         assert correction_start in ("zero", "romig")
-        F_cols, dF_cols, n_conv = [], [], []
-        tr0 = None
-        for b in range(train_problem.batch):
-            tr = Transport(train_problem, b)
-            if tr0 is None:
-                tr0 = tr
-            dsa = ConsistentDSA(tr)
-            res = sisa(tr, np.zeros(tr.n_dof), eps_train, n_iter, "dsa", dsa=dsa,
-                       window=window, keep_f=True, tol_mode=tol_mode)
-            f = res["f"].reshape(-1)
-            F_cols.append(f)
-            n_conv.append(res["n_sweep"])
-            w_mu = min(res["n_sweep"], window)
-            for l in range(w_mu):
-                dF_cols.append(f - res["f_window"][l].reshape(-1))
-            if b > 0:
-                tr._lu = [None] * tr.n_angles  # free the factors of finished instances
+        self.F, self.dF, n_conv, tr0 = training_snapshots(train_problem, eps_train, window, n_iter,
+                                                          tol_mode)
         self.n_conv = n_conv
-        self.F = np.stack(F_cols, 1)
         self.pod_p = POD(self.F, eps_pod, rank_p)
         self.rom_p = ReducedModel(self.pod_p.U, tr0)
         if correction_start == "romig":
@@ -147,7 +156,7 @@ class OfflineROMs:
                 for l in range(min(res["n_sweep"], window)):
                     dF_cols.append(f - res["f_window"][l].reshape(-1))
             self.n_conv_romig = n_conv
-        self.dF = np.stack(dF_cols, 1)
+            self.dF = np.stack(dF_cols, 1)
         self.pod_c = POD(self.dF, eps_pod, rank_c)
         self.rom_c = ReducedModel(self.pod_c.U, tr0)
         self.eps_train = eps_train
