@@ -222,20 +222,49 @@ int rte_batch_autotune(rte_batch_t batch, void* stream, int* n_entries, int* tab
  * For callers that cannot allocate device memory while they run (for example under a host
  * framework whose caching allocator has reserved the device's memory, or inside a latency-bound
  * service loop where an allocation, which may synchronise the device, is not allowed).  Computes
- * exactly what rte_sweep computes for every instance (no active mask, no psi output), but keeps
- * the partial scalar-flux sums in one fixed 16 MiB device array that belongs to the library image
- * instead of memory owned by the batch; the call itself allocates nothing.
+ * the same sweep and scalar-flux reduction as rte_sweep for every instance (no active mask, no psi
+ * output), equal to rounding: it always uses the batch's preferred directions per warp and one
+ * warp per direction group, while rte_sweep may group directions per launch, so the partial sums
+ * can be added in another order (1e-12 relative).  It keeps the partial scalar-flux sums in one
+ * fixed 16 MiB device array that belongs to the library image instead of memory owned by the
+ * batch.  The array is taken on a device when the first batch is created there
+ * (rte_batch_create loads it and looks up its address); the call itself allocates nothing and
+ * looks the address up again each time.
  *   rho_in, rho_out  DEVICE double[B][n_dof], 16-byte aligned, not aliased
  * Limit: B * (number of sweep work groups) * n_dof <= 2^21 doubles, else RTE_EINVAL (e.g. at most
  * 4 instances of a 128x128 CL(16,4) batch swept with 4 directions per warp, see
  * rte_batch_tune; any 1D slab batch of moderate size).
- * Every GPU that loads the library holds the 16 MiB array until the process exits.  The first
- * call on a device looks up the array's device address (once per device); make that first call
- * before capturing streams.  All calls share the one array: calls that overlap on the GPU (on
- * different streams, or from different threads) race and give wrong results; serialise them.
+ * Every GPU that loads the library's device code holds the 16 MiB array until the process exits.
+ * All calls share the one array: calls that overlap on the GPU (on different streams, or from
+ * different threads) race and give wrong results; serialise them.
  * Asynchronous on `stream`.  Errors: RTE_EINVAL, RTE_ESTATE, RTE_ECUDA. */
 int rte_sweep_static(rte_batch_t batch, const double* rho_in, double* rho_out, int with_source,
                      void* stream);
+
+/* Residual and particle balance of a solution, in FP64 (one extra sweep; no counterpart call in
+ * the paper, which reports the residual R^rho_inf = ||(I - L) rho - b-bar||_inf of Eq.
+ * (rho_matrix_vec) averaged over its test sets, the notation table of Sec. 4).  For every instance
+ * b (in `active`, or all when NULL) one FP64 sweep rho* = L rho + b-bar of rho gives
+ *   out[b][0] = ||rho - rho*||_inf                          (R^rho_inf of this instance)
+ *   out[b][1] = max_T |bal_T|, bal_T = net outflow_T + int_T sigma_t rho* - int_T sigma_s rho
+ *               - int_T G: the particle balance of the sweep in cell T (the DG equation tested
+ *               with T's indicator function), the net outflow summed over directions with their
+ *               weights from the upwind face traces the sweep passes between cells; it vanishes
+ *               for an exact sweep whatever rho is
+ *   out[b][2] = leakage + int sigma_a rho* - int G over the domain (absorption + net leakage =
+ *               source), which tends to 0 as rho converges: it equals sum_T bal_T minus
+ *               int sigma_s (rho* - rho)
+ *   out[b][3] = int G over the domain
+ *   rho           DEVICE double[B][n_dof], 16-byte aligned
+ *   out           DEVICE double[B][4]
+ *   cell_balance  DEVICE double[B][n_cells] or NULL: bal_T per cell
+ *   active        DEVICE uint8[B] or NULL
+ * Uses the batch's iteration scratch (not to overlap rte_solve on the same batch) and, from the
+ * first call, B x (directions / 8 in 2D, directions in 1D) x n_cells doubles the batch keeps for
+ * the face outflows.  Asynchronous on `stream`.  Errors: RTE_ESTATE, RTE_EINVAL, RTE_ENOMEM,
+ * RTE_ECUDA. */
+int rte_residual(rte_batch_t batch, const double* rho, double* out, double* cell_balance,
+                 const uint8_t* active, void* stream);
 
 /* Sweep-kernel timing for throughput and roofline accounting.  Each 2D/1D sweep kernel launched
  * for this batch while timing is on is bracketed by CUDA events recorded on the stream it is
@@ -397,6 +426,13 @@ typedef struct {
                           still sweep in FP32 waits (no sweep, no correction) for up to gang_wait
                           iterations, so that FP64 sweeps run in fewer, fuller launches.  Its
                           own sequence of iterates is unchanged; only when it runs changes.   */
+  int verify;          /* 1: after the solve, one more FP64 sweep of each result gives its
+                          residual R^rho_inf and particle balance (rte_residual) in the report;
+                          the result must be in device memory.  0: not computed (zeros).      */
+  uint8_t* sa_history; /* HOST uint8[B][max_iter] or NULL, written: per sweep l of an instance,
+                          the correction that followed it -- RTE_SA_NONE (none: plain SI, or the
+                          stop test fired), RTE_SA_DSA or RTE_SA_ROMSA (Alg. 2's choice) --
+                          plus 0x10 when sweep l ran in FP32.  Entries past n_sweep untouched. */
 } rte_solve_opts;
 
 typedef struct {
@@ -408,6 +444,13 @@ typedef struct {
   double last_change;  /* last ||rho* - rho||_inf                                           */
   double rho_inf;      /* ||rho*||_inf at exit                                              */
   int n_sweep32;       /* of the n_sweep sweeps, those done in FP32                          */
+  int pad;
+  /* with rte_solve_opts.verify (else 0), from one FP64 sweep rho* of the result rho:          */
+  double r_inf;        /* ||(I - L) rho - b-bar||_inf = ||rho - rho*||_inf (R^rho_inf, Sec. 4) */
+  double balance_cell; /* max over cells of |net outflow + int sigma_t rho* - int sigma_s rho
+                          - int G| (zero for an exact sweep; see rte_residual)               */
+  double balance;      /* leakage + int sigma_a rho* - int G (absorption + net leakage =
+                          source; -> 0 as rho converges)                                      */
 } rte_solve_report;
 
 /* Runs Alg. 1 on every instance of the batch, each stopping on its own test.
@@ -477,7 +520,8 @@ typedef struct {
  * request's own tolerance; rom_p (or NULL for a zero initial iterate) gives the ROMIG guess.
  * Handles passed to a bucket must outlive the server and not be used elsewhere meanwhile. */
 int rte_server_create(int device, rte_server_t* out);
-/* opts.schedule must be NULL; opts.eps is replaced by each request's tolerance. */
+/* opts.schedule and opts.sa_history must be NULL and opts.verify 0; opts.eps is replaced by each
+ * request's tolerance. */
 int rte_server_add_bucket(rte_server_t server, rte_batch_t slots, rte_rom_t rom_p,
                           rte_rom_t rom_c, const rte_solve_opts* opts, int* bucket);
 int rte_server_start(rte_server_t server);

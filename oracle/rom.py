@@ -110,7 +110,8 @@ class ReducedModel:
 def training_snapshots(train_problem, eps_train, window, n_iter=2000, tol_mode="abs"):
     """The training solves of the offline stage: SI-DSA from rho = 0 for every training parameter,
     the converged angular flux f^mu as a column of F (Sec. 3.1.1) and the correction snapshots
-    f^mu - f^{mu,(l)}, l < w_mu = min(n_conv, window), as columns of delta F (Sec. 3.2.1).
+    f^mu - f^{mu,(l)} for l = 1, ..., w_mu = min(n_conv, window), f^{mu,(l)} the angular flux of
+    sweep l, as columns of delta F (Sec. 3.2.1).
     Returns (F, dF, n_conv, tr0) with tr0 the first instance's Transport."""
     F_cols, dF_cols, n_conv = [], [], []
     tr0 = None
@@ -125,8 +126,8 @@ def training_snapshots(train_problem, eps_train, window, n_iter=2000, tol_mode="
         F_cols.append(f)
         n_conv.append(res["n_sweep"])
         w_mu = min(res["n_sweep"], window)
-        for l in range(w_mu):
-            dF_cols.append(f - res["f_window"][l].reshape(-1))
+        for l in range(1, w_mu + 1):   # f_window[l - 1] is the angular flux of sweep l
+            dF_cols.append(f - res["f_window"][l - 1].reshape(-1))
         if b > 0:
             tr._lu = [None] * tr.n_angles  # free the factors of finished instances
     return np.stack(F_cols, 1), np.stack(dF_cols, 1), n_conv, tr0
@@ -153,8 +154,8 @@ class OfflineROMs:
                            window=window, keep_f=True, tol_mode=tol_mode)
                 f = res["f"].reshape(-1)
                 n_conv.append(res["n_sweep"])
-                for l in range(min(res["n_sweep"], window)):
-                    dF_cols.append(f - res["f_window"][l].reshape(-1))
+                for l in range(1, min(res["n_sweep"], window) + 1):
+                    dF_cols.append(f - res["f_window"][l - 1].reshape(-1))
             self.n_conv_romig = n_conv
             self.dF = np.stack(dF_cols, 1)
         self.pod_c = POD(self.dF, eps_pod, rank_c)

@@ -67,7 +67,7 @@ static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w
 
 using namespace rte;
 
-extern "C" int rte_version(void) { return 10500; }
+extern "C" int rte_version(void) { return 10600; }
 extern "C" const char* rte_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" int rte_disc_create(const rte_disc_desc* d, int device, rte_disc_t* out) {
@@ -378,7 +378,7 @@ extern "C" int rte_batch_tune(rte_batch_t b, int dpw) {
 
 size_t rte_batch_s::bytes() const {
   size_t t = 8 * (sigma_t.n + sigma_s.n + G0.n + inflow.n + tables.n + partial.n + S.n + norms.n + work.n +
-                  outer.n);
+                  outer.n + leak.n + vout.n);
   t += 4 * (tables32.n + S32.n + partial32.n);
   t += sizeof(rte::SweepGroup) * (groups_dev.n + groups_all_dev.n) + slot_mask.n;
   return t + rte::dsa_bytes(this);
@@ -499,6 +499,9 @@ extern "C" int rte_batch_create(rte_disc_t disc, int B, rte_batch_t* out) {
   if (st == RTE_OK) st = b->norms.alloc(nb * 2);
   if (st == RTE_OK && disc->dim == 2) st = b->S.alloc(nb * disc->n_dof);
   if (st == RTE_OK) st = b->work.alloc(nb * disc->n_dof * 4);
+  // the allocation-free sweep's static scratch is loaded on this device now, at set-up, so that
+  // rte_sweep_static itself never triggers the load (and its allocation)
+  if (st == RTE_OK) st = rte::static_scratch_preload();
   if (st != RTE_OK) {
     delete b;
     return st;

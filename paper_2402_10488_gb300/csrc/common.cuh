@@ -182,6 +182,9 @@ struct rte_batch_s {
   rte::DevBuf<double> work;               // [B][n_dof] x 4 iteration scratch for rte_solve
   rte::DevBuf<double> outer;              // [2][B][n_dof] x0, y0 of the FP64 outer residual
                                           // correction (rte_solve_opts.refine_kappa), on first use
+  rte::DevBuf<double> leak;               // [B][groups][n_cells] net face outflow partials and
+  rte::DevBuf<double> vout;               // [B][4] outputs of the residual / balance check
+                                          // (rte_residual, rte_solve_opts.verify), on first use
   rte::DsaState* dsa = nullptr;
   int dsa_nu = 2;                         // red-black smoothing sweeps per multigrid level (2D DSA)
   bool dsa_blocking = false;              // smoothing sweeps of a level in one temporally blocked launch
@@ -248,7 +251,17 @@ int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, cons
                      const uint8_t* inner = nullptr, const double* x0 = nullptr,
                      const double* y0 = nullptr);
 int setup_tables(rte_batch_t b, cudaStream_t st, const uint8_t* mask = nullptr);
+// one FP64 sweep with source that also records each cell's net face outflow (bt->leak)
+int sweep_launch_leak(rte_batch_t bt, const double* rho_in, double* rho_out, const uint8_t* active,
+                      cudaStream_t st, int* n_groups);
+// verify.cu: residual ||(I - L) rho - b||_inf and particle balance of every instance in `active`
+// (all when null): out DEVICE double[B][4], cell_balance DEVICE double[B][n_cells] or null
+int residual_launch(rte_batch_t bt, const double* rho, double* out, double* cell_balance,
+                    const uint8_t* active, cudaStream_t st);
 size_t dsa_bytes(const rte_batch_s* b);
+// noalloc.cu: looks up the allocation-free sweep's static scratch on the current device, which
+// loads (and allocates) it there if it was not loaded yet; called when a batch is created
+int static_scratch_preload();
 // per-slot parameter upload: instances slots[0..n) take the given parameters (host arrays)
 int set_slots(rte_batch_t b, int n, const int* slots, const double* sigma_t, const double* sigma_s,
               const double* source, const double* inflow, cudaStream_t st);

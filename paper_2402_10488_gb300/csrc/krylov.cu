@@ -214,7 +214,7 @@ static int run_pgmres(rte_batch_t bt, const rte_gmres_opts* o, double* x,
   RTE_CUDA_TRY(cudaHostAlloc((void**)&G.hy, sizeof(double) * B * (m + 1), cudaHostAllocDefault));
   RTE_TRY(G.init_events());
   G.dsa_iters.assign(B, 0);
-  std::vector<rte_solve_report> rep(B, rte_solve_report{0, 0, 0, 0, 0, 0.0, 0.0, 0});
+  std::vector<rte_solve_report> rep(B, rte_solve_report{});
   std::vector<uint8_t> act(B, 1);
   RTE_TRY(G.upload_mask(0, act));
   const uint8_t* m0 = G.mask.p;

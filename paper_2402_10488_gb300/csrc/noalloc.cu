@@ -6,8 +6,6 @@
 // bound service loop where a cudaMalloc (which can synchronise the device and fragment memory)
 // is not allowed.  They create and parameterise a batch once at set-up, then call this entry
 // point as often as they like without the library allocating anything.
-#include <mutex>
-
 #include "common.cuh"
 
 namespace rte {
@@ -20,26 +18,25 @@ int sweep_launch_with_scratch(rte_batch_t bt, const double* rho_in, double* rho_
 constexpr size_t kStaticScratchDoubles = size_t(1) << 21;
 static __device__ __align__(256) double g_sweep_scratch[kStaticScratchDoubles];
 
-constexpr int kMaxDevices = 64;
-static std::mutex g_scratch_mu;
-static double* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the static array on `device` (the caller has made `device` current).  In host
-// code the symbol name only stands for the array; its device address has to be looked up, once
-// per device.
-static int static_scratch(int device, double** out) {
-  if (device < 0 || device >= kMaxDevices) return fail(RTE_EINVAL, "device index too large");
-  std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_ptr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_sweep_scratch);
-    if (e != cudaSuccess || !p)
-      return fail(RTE_ECUDA, std::string("cudaGetSymbolAddress(static sweep scratch): ") +
-                                 cudaGetErrorString(e));
-    g_scratch_ptr[device] = static_cast<double*>(p);
-  }
-  *out = g_scratch_ptr[device];
+// Device address of the static array on the current device.  In host code the symbol name only
+// stands for the array; its device address has to be looked up.  The lookup is repeated on every
+// call (no cached address can outlive a device reset).  Under lazy module loading (the CUDA
+// default) the first lookup on a device loads this file's device code and with it allocates the
+// 16 MiB array; batch creation makes that first lookup (static_scratch_preload), so the
+// allocation happens at set-up and never inside rte_sweep_static.
+static int static_scratch(double** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_sweep_scratch);
+  if (e != cudaSuccess || !p)
+    return fail(e == cudaErrorMemoryAllocation ? RTE_ENOMEM : RTE_ECUDA,
+                std::string("cudaGetSymbolAddress(static sweep scratch): ") + cudaGetErrorString(e));
+  *out = static_cast<double*>(p);
   return RTE_OK;
+}
+
+int static_scratch_preload() {
+  double* p = nullptr;
+  return static_scratch(&p);
 }
 
 }  // namespace rte
@@ -60,7 +57,7 @@ extern "C" int rte_sweep_static(rte_batch_t b, const double* rho_in, double* rho
                                 std::to_string(kStaticScratchDoubles) + "); use rte_sweep");
   DeviceGuard g(b->disc->device);
   double* scratch = nullptr;
-  RTE_TRY(static_scratch(b->disc->device, &scratch));
+  RTE_TRY(static_scratch(&scratch));
   // every partial of every instance is written by the sweep before the reduction reads it, so the
   // previous call's contents never leak into this one and nothing needs clearing
   return sweep_launch_with_scratch(b, rho_in, rho_out, with_source, (cudaStream_t)stream, scratch);

@@ -58,7 +58,7 @@ int SiState::init(rte_batch_t b, const rte_solve_opts& opts, rte_rom_t rom_c, do
   status.assign(B, RTE_OK);
   eps.assign(B, o.eps);
   outer_test.assign(B, 0.0);
-  rep.assign(B, rte_solve_report{0, 0, 0, 0, 0, 0.0, 0.0, 0});
+  rep.assign(B, rte_solve_report{});
   in_flight = false;
   return RTE_OK;
 }
@@ -74,7 +74,7 @@ void SiState::begin(int b, double eps_b) {
   waited[b] = 0;
   status[b] = RTE_OK;
   eps[b] = eps_b;
-  rep[b] = rte_solve_report{0, 0, 0, 0, 0, 0.0, 0.0, 0};
+  rep[b] = rte_solve_report{};
 }
 
 int SiState::n_active() const {
@@ -195,6 +195,7 @@ int si_finish(SiState& s, cudaStream_t st, double* history) {
     std::memcpy(&delta, &s.hn[2 * b], sizeof(double));
     std::memcpy(&rinf, &s.hn[2 * b + 1], sizeof(double));
     if (history) history[(size_t)b * o.max_iter + (l - 1)] = delta;
+    if (o.sa_history) o.sa_history[(size_t)b * o.max_iter + (l - 1)] = s.hm[B + b] ? 0x10 : 0;
     rte_solve_report& rp = s.rep[b];
     rp.n_sweep = l;
     rp.last_change = delta;
@@ -226,12 +227,18 @@ int si_finish(SiState& s, cudaStream_t st, double* history) {
     if (l >= o.max_iter) h_exp[b] = 1, n_exp++;
     any = true;
     h_corr[b] = 1;
-    if (o.sa == RTE_SA_NONE) continue;
+    if (o.sa == RTE_SA_NONE) {
+      if (o.sa_history) o.sa_history[(size_t)b * o.max_iter + (l - 1)] = s.hm[B + b] ? 0x10 : 0;
+      continue;
+    }
     bool romsa = o.sa == RTE_SA_ROMSA;
     if (o.sa == RTE_SA_ROMSAD)
       romsa = o.schedule ? o.schedule[l - 1] != 0 : (l <= o.theta && delta >= o.eps_romsad);
     if (romsa) h_rom[b] = 1, rp.n_romsa++, anyr = true;
     else h_dsa[b] = 1, rp.n_dsa++, anyd = true;
+    if (o.sa_history)   // the correction that follows sweep l; 0x10 marks an FP32 sweep
+      o.sa_history[(size_t)b * o.max_iter + (l - 1)] =
+          (uint8_t)((romsa ? RTE_SA_ROMSA : RTE_SA_DSA) | (s.hm[B + b] ? 0x10 : 0));
   }
   if (any || n_conv || n_exp)
     RTE_CUDA_TRY(cudaMemcpyAsync(s.dm.p + 4 * B, h_corr, 6 * (size_t)B, cudaMemcpyHostToDevice, st));
@@ -277,6 +284,25 @@ int si_finish(SiState& s, cudaStream_t st, double* history) {
   return RTE_OK;
 }
 
+// rte_solve_opts.verify: R^rho_inf and the particle balance of every instance's result (in DEVICE
+// memory) into its report.  Synchronises the stream.
+static int verify_results(SiState& s, cudaStream_t st) {
+  rte_batch_t bt = s.bt;
+  if (!s.result_dev) return fail(RTE_EINVAL, "verify: the result must be in device memory");
+  if (bt->vout.n < 4 * (size_t)s.B) RTE_TRY(bt->vout.alloc(4 * (size_t)s.B));
+  RTE_TRY(residual_launch(bt, s.result, bt->vout.p, nullptr, nullptr, st));
+  std::vector<double> v(4 * (size_t)s.B);
+  RTE_CUDA_TRY(cudaMemcpyAsync(v.data(), bt->vout.p, sizeof(double) * v.size(),
+                               cudaMemcpyDeviceToHost, st));
+  RTE_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int b = 0; b < s.B; ++b) {
+    s.rep[b].r_inf = v[4 * b];
+    s.rep[b].balance_cell = v[4 * b + 1];
+    s.rep[b].balance = v[4 * b + 2];
+  }
+  return RTE_OK;
+}
+
 // All instances of the batch from the initial iterates in `rho` (overwritten with the results).
 // With psi_cur the angular flux of the latest sweep is kept, and the first `window` sweeps are
 // also copied to psi_win (training solves of the offline stage).
@@ -309,6 +335,7 @@ int run_si(rte_batch_t bt, const rte_solve_opts* o, rte_rom_t rom_c, double* rho
                                        cudaMemcpyDeviceToDevice, st));
     RTE_TRY(si_finish(s, st, history));
   }
+  if (o->verify) RTE_TRY(verify_results(s, st));
   RTE_CUDA_TRY(cudaStreamSynchronize(st));
   int status = RTE_OK;
   for (int b = 0; b < B; ++b)
@@ -345,7 +372,8 @@ using namespace rte;
 static int check_opts(rte_batch_t b, const rte_solve_opts* o, rte_rom_t rom_c) {
   RTE_TRY(params_ready(b, "rte_solve"));
   if (!(o->eps >= 0) || o->max_iter < 1 || o->sa < 0 || o->sa > 3 || !(o->fp32_switch >= 0) ||
-      !(o->refine_kappa >= 0) || (o->refine_kappa > 0 && o->refine_inner < 1) || o->gang_wait < 0)
+      !(o->refine_kappa >= 0) || (o->refine_kappa > 0 && o->refine_inner < 1) || o->gang_wait < 0 ||
+      o->verify < 0 || o->verify > 1)
     return fail(RTE_EINVAL, "rte_solve: bad options");
   if (o->sa != RTE_SA_NONE && b->disc->dim == 2 && (!(o->dsa_rtol >= 0) || o->dsa_max_it < 1))
     return fail(RTE_EINVAL, "rte_solve: bad DSA tolerance");
@@ -412,6 +440,7 @@ extern "C" int rte_solve_many(int n, const rte_batch_t* batches, const rte_solve
   }
   int status = RTE_OK;
   for (int k = 0; k < n; ++k) {
+    if (opts[k].verify) RTE_TRY(verify_results(S[k], st[k]));
     RTE_CUDA_TRY(cudaStreamSynchronize(st[k]));
     if (roms && roms[k] && opts[k].rom_bf16) {
       int tc = 0;

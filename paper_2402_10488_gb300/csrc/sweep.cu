@@ -154,9 +154,19 @@ struct Sweep2DArgs {
   const SweepGroup* groups;
   int nx, ny, n_cells, n_dof, n_mat, n_dirs, n_groups, with_source;
   double sq_area;
+  // balance accounting (kernels instantiated with LEAK only): per (running instance, group, cell)
+  // the omega-weighted net outflow through the cell's faces; lx = sqrt(h_y / h_x) and
+  // ly = sqrt(h_x / h_y) turn a face trace's zeroth coefficient into the face integral
+  double* leak = nullptr;
+  double lx = 0.0, ly = 0.0;
 };
 
-template <int DPW, bool SMEM_TAB, bool PRESRC = false>
+// With LEAK the kernel also records, per cell, sum over its directions of
+//     omega_j ( |v_x| int_{x-outflow face} f - |v_x| int_{x-inflow face} f + the same along y ),
+// the net upwind outflow that enters the cell's particle balance (the DG equation tested with the
+// cell's indicator function): with t the face traces above, int_face f = t[0] sqrt(h_face / h_n),
+// h_n the cell's extent normal to the face.
+template <int DPW, bool SMEM_TAB, bool PRESRC = false, bool LEAK = false>
 __global__ void __launch_bounds__(32) sweep2d_kernel(const Sweep2DArgs A) {
   const int g = blockIdx.x, b = blockIdx.y, lane = threadIdx.x;
   if (A.active && !A.active[b]) return;
@@ -194,6 +204,16 @@ __global__ void __launch_bounds__(32) sweep2d_kernel(const Sweep2DArgs A) {
   double tx[DPW][2], typ[DPW][2];
 #pragma unroll
   for (int dd = 0; dd < DPW; ++dd) tx[dd][0] = tx[dd][1] = typ[dd][0] = typ[dd][1] = 0.0;
+  double lkx[DPW], lky[DPW];
+  double* lkp = nullptr;
+  if (LEAK) {
+#pragma unroll
+    for (int dd = 0; dd < DPW; ++dd) {
+      lkx[dd] = dd < grp.nd ? w[dd] * fabs(A.dirs[4 * (grp.d0 + dd)]) * A.lx : 0.0;
+      lky[dd] = dd < grp.nd ? w[dd] * fabs(A.dirs[4 * (grp.d0 + dd) + 1]) * A.ly : 0.0;
+    }
+    lkp = A.leak + ((size_t)active_rank(A.active, b) * A.n_groups + g) * A.n_cells;
+  }
 
   for (int s = 0; s < total + H - 1; ++s) {
     const int u = s - lane;
@@ -237,7 +257,7 @@ __global__ void __launch_bounds__(32) sweep2d_kernel(const Sweep2DArgs A) {
         s0 = fma(ss, r01.x, A.with_source ? G0[c] : 0.0);
         s1 = ss * r01.y, s2 = ss * r23.x, s3v = ss * r23.y;
       }
-      double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+      double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0, lk = 0.0;
 #pragma unroll
       for (int dd = 0; dd < DPW; ++dd) {
         if (dd < grp.nd) {
@@ -256,10 +276,12 @@ __global__ void __launch_bounds__(32) sweep2d_kernel(const Sweep2DArgs A) {
             v = fma(T[25 + 2 * k], ty[dd][1], v);
             a[k] = v;
           }
+          const double txin = tx[dd][0];
           tx[dd][0] = fma(c3x, a[1], a[0]);
           tx[dd][1] = fma(c3x, a[3], a[2]);
           typ[dd][0] = fma(c3y, a[2], a[0]);
           typ[dd][1] = fma(c3y, a[3], a[1]);
+          if (LEAK) lk = fma(lkx[dd], tx[dd][0] - txin, fma(lky[dd], typ[dd][0] - ty[dd][0], lk));
           acc0 = fma(w[dd], a[0], acc0);
           acc1 = fma(w[dd], a[1], acc1);
           acc2 = fma(w[dd], a[2], acc2);
@@ -274,6 +296,7 @@ __global__ void __launch_bounds__(32) sweep2d_kernel(const Sweep2DArgs A) {
       double2* po = reinterpret_cast<double2*>(part + 4 * (size_t)c);
       po[0] = make_double2(acc0, acc1);
       po[1] = make_double2(acc2, acc3);
+      if (LEAK) lkp[c] = lk;
       if (lane == H - 1 && rb + 1 < nrb) {
 #pragma unroll
         for (int dd = 0; dd < DPW; ++dd) {
@@ -453,6 +476,7 @@ struct Sweep1DArgs {
   const int32_t* matr;      // material at each cell's right end (linear cross sections) or null
   const double* dirs;
   int B, nx, n_dof, n_mat, n_dirs, with_source;
+  double* leak = nullptr;   // or [rank][n_dirs][nx]: omega |xi| (u_out - u_in) per cell (balance)
 };
 
 // 1D slab: one thread per (instance, direction), sequential in upwind order (2x2 cell solves).
@@ -494,10 +518,12 @@ __global__ void sweep1d_kernel(const Sweep1DArgs A) {
     }
     const double a0 = fma(T[4], u, fma(T[1], s1, T[0] * s0));
     const double a1 = fma(T[5], u, fma(T[3], s1, T[2] * s0));
+    const double uin = u;
     u = fma(c3, a1, a0) * T[6];
     part[2 * c] = w * a0;
     part[2 * c + 1] = w * a1;
     if (psi) psi[2 * c] = a0, psi[2 * c + 1] = a1;
+    if (A.leak) A.leak[((size_t)rank * A.n_dirs + d) * A.nx + c] = w * fabs(xi) * (u - uin);
   }
 }
 
@@ -650,22 +676,22 @@ int setup_tables(rte_batch_t bt, cudaStream_t st, const uint8_t* mask) {
   return RTE_OK;
 }
 
-template <int DPW, bool PRESRC = false>
+template <int DPW, bool PRESRC = false, bool LEAK = false>
 static int launch2d(const Sweep2DArgs& A, int B, int n_groups, cudaStream_t st) {
   const size_t ybytes = (size_t)A.nx * DPW * 2 * sizeof(double);
   const size_t tbytes = (size_t)A.n_mat * DPW * kTab2D * sizeof(double);
   const size_t sbytes = (size_t)A.n_mat * sizeof(double);
   dim3 grid(n_groups, B);
   if (ybytes + tbytes + sbytes <= 48 * 1024) {
-    sweep2d_kernel<DPW, true, PRESRC><<<grid, 32, ybytes + tbytes + sbytes, st>>>(A); RTE_NOTE_LAUNCH();
+    sweep2d_kernel<DPW, true, PRESRC, LEAK><<<grid, 32, ybytes + tbytes + sbytes, st>>>(A); RTE_NOTE_LAUNCH();
   } else {
     const size_t bytes = ybytes + sbytes;
     if (bytes > 200 * 1024) return fail(RTE_EINVAL, "sweep: mesh row too long for shared memory");
     if (bytes > 48 * 1024) {
-      RTE_CUDA_TRY(cudaFuncSetAttribute(sweep2d_kernel<DPW, false, PRESRC>,
+      RTE_CUDA_TRY(cudaFuncSetAttribute(sweep2d_kernel<DPW, false, PRESRC, LEAK>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
     }
-    sweep2d_kernel<DPW, false, PRESRC><<<grid, 32, bytes, st>>>(A); RTE_NOTE_LAUNCH();
+    sweep2d_kernel<DPW, false, PRESRC, LEAK><<<grid, 32, bytes, st>>>(A); RTE_NOTE_LAUNCH();
   }
   RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;
@@ -895,6 +921,50 @@ int sweep_launch_with_scratch(rte_batch_t bt, const double* rho_in, double* rho_
   reduce_partials_kernel<<<grid, th, 0, st>>>(partial, rho_in, rho_out, nullptr, nullptr, n_groups,
                                              d->n_dof); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
+  return RTE_OK;
+}
+
+// One FP64 sweep with source of the instances in `active` (every instance when null) that also
+// records each cell's net face outflow per work group in bt->leak (allocated here on first use:
+// B x groups x n_cells doubles).  2D sweeps use the widest direction groups (8 per warp), which
+// need the fewest leak partials and fit every batch's partial-sum buffer.  *n_groups receives the
+// number of groups whose leak partials the caller sums.
+int sweep_launch_leak(rte_batch_t bt, const double* rho_in, double* rho_out, const uint8_t* active,
+                      cudaStream_t st, int* n_groups_out) {
+  const rte_disc_s* d = bt->disc;
+  int n_groups = 0;
+  const SweepGroup* gdev = nullptr;
+  if (d->dim == 2) {
+    n_groups = bt->gcount[3];
+    gdev = bt->groups_all_dev.p + bt->goff[3];
+  } else {
+    n_groups = d->n_dirs;
+  }
+  const size_t need = (size_t)bt->B * n_groups * d->n_cells;
+  if (bt->leak.n < need) RTE_TRY(bt->leak.alloc(need));
+  if (d->dim == 2) {
+    cell_source_kernel<<<dim3((d->n_cells + 127) / 128, bt->B), 128, 0, st>>>(
+        rho_in, bt->S.p, bt->sigma_s.p, bt->G0.p, d->mat_id.p, active, d->n_cells, d->n_mat, 1); RTE_NOTE_LAUNCH();
+    Sweep2DArgs A{bt->S.p,      bt->partial.p, nullptr,        active,      bt->tables.p,
+                  bt->sigma_s.p, bt->G0.p,     bt->inflow.p,   d->mat_id.p, d->dir_dev.p,
+                  gdev,         d->nx,         d->ny,          d->n_cells,  d->n_dof,
+                  d->n_mat,     d->n_dirs,     n_groups,       1,           std::sqrt(d->hx * d->hy),
+                  bt->leak.p,   std::sqrt(d->hy / d->hx),      std::sqrt(d->hx / d->hy)};
+    RTE_TRY((launch2d<8, true, true>(A, bt->B, n_groups, st)));
+  } else {
+    Sweep1DArgs A{rho_in,      bt->partial.p, nullptr,  active, bt->tables.p, bt->sigma_s.p,
+                  bt->G0.p,    bt->inflow.p,  d->mat_id.p, d->mat_r.p, d->dir_dev.p, bt->B, d->nx,
+                  d->n_dof,    d->n_mat,      d->n_dirs, 1,      bt->leak.p};
+    const int n = bt->B * d->n_dirs;
+    sweep1d_kernel<<<(n + 63) / 64, 64, 0, st>>>(A); RTE_NOTE_LAUNCH();
+    RTE_CUDA_TRY(cudaGetLastError());
+  }
+  const int th = 256;
+  dim3 grid((d->n_dof / 2 + th - 1) / th, bt->B);
+  reduce_partials_kernel<<<grid, th, 0, st>>>(bt->partial.p, rho_in, rho_out, nullptr, active,
+                                             n_groups, d->n_dof); RTE_NOTE_LAUNCH();
+  RTE_CUDA_TRY(cudaGetLastError());
+  *n_groups_out = n_groups;
   return RTE_OK;
 }
 

@@ -43,6 +43,7 @@ SIGNATURES = {
     "rte_batch_directions": (_I, [_P, _P]),
     "rte_sweep": (_I, [_P, _P, _P, _P, _I, _P, _P]),
     "rte_sweep_static": (_I, [_P, _P, _P, _I, _P]),
+    "rte_residual": (_I, [_P, _P, _P, _P, _P, _P]),
     "rte_change_norm": (_I, [_P, _P, _P, _P, _P]),
     "rte_dsa_correction": (_I, [_P, _P, _P, _D, _I, _P, _P, _P]),
     "rte_correction_source": (_I, [_P, _P, _P, _P, _P]),
@@ -155,12 +156,13 @@ class _SolveOpts(ctypes.Structure):
     _fields_ = [("eps", _D), ("rel", _I), ("max_iter", _I), ("sa", _I), ("theta", _I),
                 ("eps_romsad", _D), ("dsa_rtol", _D), ("dsa_max_it", _I), ("schedule", _P),
                 ("fp32_switch", _D), ("refine_kappa", _D), ("refine_inner", _I),
-                ("rom_bf16", _I), ("gang_wait", _I)]
+                ("rom_bf16", _I), ("gang_wait", _I), ("verify", _I), ("sa_history", _P)]
 
 
 class SolveReport(ctypes.Structure):
     _fields_ = [("n_sweep", _I), ("converged", _I), ("n_romsa", _I), ("n_dsa", _I),
-                ("dsa_iters", _I), ("last_change", _D), ("rho_inf", _D), ("n_sweep32", _I)]
+                ("dsa_iters", _I), ("last_change", _D), ("rho_inf", _D), ("n_sweep32", _I),
+                ("pad", _I), ("r_inf", _D), ("balance_cell", _D), ("balance", _D)]
 
 
 class _GmresOpts(ctypes.Structure):
@@ -176,19 +178,26 @@ class ServeReport(ctypes.Structure):
 def _report(r):
     return dict(n_sweep=r.n_sweep, converged=bool(r.converged), n_romsa=r.n_romsa, n_dsa=r.n_dsa,
                 dsa_iters=r.dsa_iters, last_change=r.last_change, rho_inf=r.rho_inf,
-                n_sweep32=r.n_sweep32)
+                n_sweep32=r.n_sweep32, r_inf=r.r_inf, balance_cell=r.balance_cell,
+                balance=r.balance)
 
 
 def solve_opts(eps, sa=SA_DSA, rel=False, max_iter=1000, theta=0, eps_romsad=0.0, dsa_rtol=1e-10,
                dsa_max_it=500, schedule=None, fp32_switch=0.0, refine_kappa=0.0, refine_inner=0,
-               gang_wait=0, rom_bf16=False):
-    """rte_solve_opts; `schedule` (uint8 per iteration) is kept alive on the returned struct."""
+               gang_wait=0, rom_bf16=False, verify=False, sa_history=None):
+    """rte_solve_opts; `schedule` (uint8 per iteration) and `sa_history` (a writable uint8 numpy
+    array [B][max_iter]) are kept alive on the returned struct."""
     sched = None if schedule is None else _host(schedule, np.uint8)
+    if sa_history is not None and (sa_history.dtype != np.uint8 or not sa_history.flags.c_contiguous):
+        raise ValueError("sa_history must be a C-contiguous uint8 array")
     o = _SolveOpts(float(eps), 1 if rel else 0, int(max_iter), int(sa), int(theta),
                    float(eps_romsad), float(dsa_rtol), int(dsa_max_it),
                    None if sched is None else sched.ctypes.data_as(_P), float(fp32_switch),
-                   float(refine_kappa), int(refine_inner), 1 if rom_bf16 else 0, int(gang_wait))
+                   float(refine_kappa), int(refine_inner), 1 if rom_bf16 else 0, int(gang_wait),
+                   1 if verify else 0,
+                   None if sa_history is None else sa_history.ctypes.data_as(_P))
     o._sched = sched
+    o._hist = sa_history
     return o
 
 
@@ -372,16 +381,30 @@ class Batch:
     def solve(self, rho, eps, sa=SA_DSA, rel=False, max_iter=1000, theta=0, eps_romsad=0.0,
               dsa_rtol=1e-10, dsa_max_it=500, rom_c=None, schedule=None, history=False,
               fp32_switch=0.0, refine_kappa=0.0, refine_inner=0, gang_wait=0, rom_bf16=False,
-              stream=None):
+              verify=False, stream=None):
+        """rte_solve.  Returns (reports, hist, status); with history=True, hist is the change per
+        sweep [B][max_iter] and each report also carries "sa_history", the codes of
+        rte_solve_opts.sa_history for its n_sweep sweeps."""
+        sah = np.zeros((self.B, max_iter), np.uint8) if history else None
         opts = solve_opts(eps, sa, rel, max_iter, theta, eps_romsad, dsa_rtol, dsa_max_it, schedule,
-                          fp32_switch, refine_kappa, refine_inner, gang_wait, rom_bf16)
+                          fp32_switch, refine_kappa, refine_inner, gang_wait, rom_bf16, verify, sah)
         reps = (SolveReport * self.B)()
         hist = np.zeros((self.B, max_iter)) if history else None
         st = check(lib().rte_solve(self.h, ctypes.byref(opts), None if rom_c is None else rom_c.h,
                                    _ptr(rho), reps,
                                    None if hist is None else hist.ctypes.data_as(_P),
                                    _stream(stream)), allow=(RTE_ENOCONV,))
-        return [_report(r) for r in reps], hist, st
+        out = [_report(r) for r in reps]
+        if history:
+            for b, r in enumerate(out):
+                r["sa_history"] = sah[b, : r["n_sweep"]].copy()
+        return out, hist, st
+
+    def residual(self, rho, out, cell_balance=None, active=None, stream=None):
+        """rte_residual: out [B][4] = (||(I - L) rho - b-bar||_inf, max per-cell balance, global
+        balance defect, int G), device tensors; cell_balance [B][n_cells] optional."""
+        check(lib().rte_residual(self.h, _ptr(rho), _ptr(out), _ptr(cell_balance), _ptr(active),
+                                 _stream(stream)))
 
     def pgmres(self, rho, rtol, restart=25, max_iter=500, precond=True, dsa_rtol=0.0,
                dsa_max_it=1, zero_start=True, stream=None):

@@ -4,8 +4,16 @@ rte_sweep_static exists for callers that cannot allocate device memory while the
 its partial sums in a fixed array of the library instead of memory owned by the batch.  Both
 entry points run the same kernels on the same inputs, so their outputs are compared at the
 sweep-parity tolerance of the other tests (1e-12 relative), on two calls in a row (the second
-call must not see anything left over from the first).  This file is collected last so that a
-run that stops at the first failure has already run every other test."""
+call must not see anything left over from the first).  The entry point's defining property --
+it allocates no device memory -- is checked by the device's free memory (cudaMemGetInfo) around
+repeated calls, in this process and in a fresh one with lazy module loading, where the static
+array is allocated when the library's device code that holds it is first loaded (batch creation
+does that).  This file is collected last so that a run that stops at the first failure has
+already run every other test."""
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
@@ -63,3 +71,52 @@ def test_static_sweep_rejects_batches_beyond_its_scratch():
     with pytest.raises(rte.RTEError) as e:
         batch.sweep_static(rin, out)
     assert e.value.status == rte.RTE_EINVAL and "static scratch" in str(e.value)
+
+
+def test_static_sweep_allocates_no_device_memory():
+    rte = _rte()
+    p = inputs.lattice_test(64, 32, 2)
+    batch = rte.Batch(rte.Disc(p), 2)
+    batch.set_params(p)
+    rin = torch.rand((2, p.n_dof), dtype=torch.float64, device="cuda")
+    out = torch.empty_like(rin)
+    batch.sweep(rin, out)                 # loads the sweep kernels
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        batch.sweep_static(rin, out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
+_LAZY_SCRIPT = r"""
+import sys, torch
+sys.path.insert(0, sys.argv[1])
+from paper_2402_10488_gb300 import inputs, rte
+p = inputs.slab_random(40, 16, 3, seed=4, B=2, inflow=(1.0, 0.0))
+batch = rte.Batch(rte.Disc(p), 2)
+batch.set_params(p)
+rin = torch.rand((2, p.n_dof), dtype=torch.float64, device="cuda")
+ref, out = torch.empty_like(rin), torch.empty_like(rin)
+batch.sweep(rin, ref)
+torch.cuda.synchronize()
+free0 = torch.cuda.mem_get_info()[0]
+batch.sweep_static(rin, out)
+batch.sweep_static(rin, out)
+torch.cuda.synchronize()
+free1 = torch.cuda.mem_get_info()[0]
+err = float((out - ref).abs().max() / ref.abs().max())
+print("FREE", free0, free1, "ERR", err)
+sys.exit(0 if free0 == free1 and err < 1e-12 else 1)
+"""
+
+
+def test_static_sweep_allocates_nothing_under_lazy_module_loading():
+    """A fresh process with CUDA_MODULE_LOADING=LAZY: the static array's device code is loaded when
+    the batch is created, so the first rte_sweep_static calls leave free device memory unchanged."""
+    _rte()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, CUDA_MODULE_LOADING="LAZY")
+    r = subprocess.run([sys.executable, "-c", _LAZY_SCRIPT, root], env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
