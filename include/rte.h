@@ -277,6 +277,13 @@ int rte_residual(rte_batch_t batch, const double* rho, double* out, double* cell
  * reads.  Errors: RTE_EINVAL, RTE_ECUDA. */
 int rte_batch_timing(rte_batch_t batch, int enable, double* out);
 
+/* Measured FMA throughput of the device's arithmetic pipes, for roofline accounting (a library
+ * service; the paper has no counterpart): kind 0 = FP64 DFMA (the 2D FP64 sweep's bound), 1 = FP32
+ * FFMA (the FP32 sweep's).  Independent FMA chains in 4 blocks of 256 threads per SM; best of five
+ * launches of a few milliseconds, timed with CUDA events on `stream` after two untimed ones.
+ * tflops: HOST double out (2 FLOP per FMA).  Synchronous.  Errors: RTE_EINVAL, RTE_ECUDA. */
+int rte_fma_peak(int device, int kind, double* tflops, void* stream);
+
 /* The distinct swept directions: dirs (HOST double[n_dirs][4]) = (v_x, v_y, summed weight,
  * multiplicity), in the order used by psi_out and the ROM bases. */
 int rte_batch_directions(rte_batch_t batch, double* dirs);

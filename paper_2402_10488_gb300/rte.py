@@ -44,6 +44,7 @@ SIGNATURES = {
     "rte_sweep": (_I, [_P, _P, _P, _P, _I, _P, _P]),
     "rte_sweep_static": (_I, [_P, _P, _P, _I, _P]),
     "rte_residual": (_I, [_P, _P, _P, _P, _P, _P]),
+    "rte_fma_peak": (_I, [_I, _I, _P, _P]),
     "rte_change_norm": (_I, [_P, _P, _P, _P, _P]),
     "rte_dsa_correction": (_I, [_P, _P, _P, _D, _I, _P, _P, _P]),
     "rte_correction_source": (_I, [_P, _P, _P, _P, _P]),
@@ -95,6 +96,14 @@ def pod_lift_bf16(U, C, Y, work, active=None, stream=None):
     r, n = U.shape
     check(lib().rte_pod_lift_bf16(_ptr(U), int(r), int(n), _ptr(C), int(C.shape[0]),
                                   _ptr(active), _ptr(Y), _ptr(work), _stream(stream)))
+
+
+def fma_peak(kind="fp64", device=0, stream=None):
+    """Measured FMA throughput of the device in TFLOP/s (rte_fma_peak): kind "fp64" or "fp32"."""
+    out = ctypes.c_double()
+    check(lib().rte_fma_peak(int(device), 0 if kind == "fp64" else 1, ctypes.byref(out),
+                             _stream(stream)))
+    return float(out.value)
 
 
 def fault_inject(what):

@@ -33,3 +33,38 @@ def test_default_bench_runs_every_method_on_one_sm_per_instance(monkeypatch):
     assert methods[0] == "romsad"
     assert {"si_dsa", "romig", "romsad_mixed", "romsad_refine", "pgmres"} <= set(methods)
     assert a.warmup >= 3 and a.dsa_smoother == -1
+
+
+def _tiny(monkeypatch, steps=3, warmup=1):
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--n", "8", "--angles", "8",
+                                      "--ntrain", "4", "--rank", "3", "--steps", str(steps),
+                                      "--warmup", str(warmup), "--eps", "1e-8"])
+    return bench, bench.parse()
+
+
+def test_reference_arm_times_whole_oracle_solves(monkeypatch):
+    """The reference arm on a tiny lattice: the oracle's own offline stage, then K complete ROMSAD
+    solves timed as one concurrent region; the timed region is the steps' wall time (so K x
+    ms_per_step is inside the run), every solve converges and the counts are the oracle's own."""
+    import time
+    bench, a = _tiny(monkeypatch)
+    t0 = time.perf_counter()
+    line = bench.run_reference(a, 1, 0)
+    total = time.perf_counter() - t0
+    assert line["impl"] == "reference" and line["steps"] == 3 and line["warmup"] == 1
+    assert line["steps"] * line["ms_per_step"] / 1e3 <= total
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == min(bench.oracle_workers(), 3)
+    assert line["value"] == cb["value"] == line["e2e"]["value"] > 0
+    # a correction follows every sweep but the one that stopped the solve
+    assert cb["n_romsa_mean"] >= 1
+    assert abs(cb["n_sweep_mean"] - (cb["n_romsa_mean"] + cb["n_dsa_mean"] + 1)) < 1e-12
+    assert bench.run_reference(a, 2, 1) is None   # other ranks do no work
+
+
+def test_cpu_baseline_leg_runs_one_instance_per_core(monkeypatch):
+    bench, a = _tiny(monkeypatch)
+    cb = bench.cpu_baseline_leg(a, dict(n_sweep=4.4))
+    assert cb["cores"] == bench.oracle_workers() and cb["value"] > 0
+    assert "4 iterations" in cb["sample"]
