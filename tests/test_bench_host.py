@@ -55,7 +55,8 @@ def test_reference_arm_times_whole_oracle_solves(monkeypatch):
     assert line["impl"] == "reference" and line["steps"] == 3 and line["warmup"] == 1
     assert line["steps"] * line["ms_per_step"] / 1e3 <= total
     cb = line["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == min(bench.oracle_workers(), 3)
+    assert cb["kind"] == "oracle" and cb["cores"] == bench.oracle_workers()
+    assert line["config"]["global_batch"] == max(3, bench.oracle_workers())
     assert line["value"] == cb["value"] == line["e2e"]["value"] > 0
     # a correction follows every sweep but the one that stopped the solve
     assert cb["n_romsa_mean"] >= 1
