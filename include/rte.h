@@ -199,6 +199,26 @@ int rte_batch_info(rte_batch_t batch, int64_t* info);
 int rte_sweep(rte_batch_t batch, const double* rho_in, double* rho_out, double* psi_out,
               int with_source, const uint8_t* active, void* stream);
 
+/* One FP32 sweep (the precision variant's sweep, rte_solve_opts.fp32_switch): the operator of
+ * rte_sweep with source, evaluated with FP32 sweep tables, FP32 cell sources Sigma_s rho_in + G, FP32
+ * cell solves and FP32 per-group partial sums, which are added in FP32 and returned in FP64:
+ *     rho_out ~ sum_j omega_j (D_j + Sigma_t)^{-1} (Sigma_s rho_in + G + g^bc_j)
+ * to FP32 rounding (a few 1e-7 relative per cell solve, carried along the sweep).
+ *   rho_in, rho_out  DEVICE double[B][n_dof], not aliased
+ *   active           DEVICE uint8[B] or NULL (instances with active[b] == 0 are skipped)
+ * 2D only.  Asynchronous on `stream`.  Errors: RTE_ESTATE, RTE_EINVAL, RTE_ECUDA. */
+int rte_sweep_f32(rte_batch_t batch, const double* rho_in, double* rho_out, const uint8_t* active,
+                  void* stream);
+
+/* Form of the FP32 sweep kernel: 0 -- one warp per group of directions (the group's directions
+ * give each lane independent work per step); 1 -- one warp per direction, the warps of a group in
+ * one thread block, which adds their contributions to each cell in shared memory in a fixed order
+ * before writing one partial sum per group (more warps in flight for the same partial-sum
+ * traffic); -1 (default) -- chosen by rte_batch_autotune per number of running instances, form 1
+ * until it has run.  Both give the same sweep up to FP32 rounding (the partial sums are grouped
+ * differently); each is deterministic.  Errors: RTE_EINVAL. */
+int rte_batch_f32_form(rte_batch_t batch, int form);
+
 /* Work decomposition of the 2D sweep: dirs_per_warp in {1, 2, 4, 8} sets how many directions of
  * one quadrant a warp sweeps together (more directions: more instruction-level parallelism and
  * fewer partial sums; fewer: more warps in flight).  0 (the default) picks per launch the largest

@@ -1170,6 +1170,146 @@ __global__ void __launch_bounds__(32) sweep2d_f32_kernel(const Sweep2D32Args A) 
   }
 }
 
+// FP32 sweep, cooperative form: a CTA of NW warps sweeps the (at most NW) directions of one group,
+// one warp per direction.  The directions of a group share a quadrant, so every warp visits the same
+// cell at the same step; each warp leaves its omega-weighted cell solution in a shared-memory
+// buffer, and every kChunk32 steps the CTA adds the buffer over its warps in warp order and writes
+// one partial per cell and group.  This gives the occupancy of one warp per direction (the FP32
+// wavefront is bound by latency, not by the FP32 pipe, so it needs many warps in flight) with the
+// partial-sum traffic of the wide groups.  The buffer is double-buffered: chunk j is summed right
+// after the barrier that ends it and is overwritten only by chunk j + 2, after the next barrier.
+constexpr int kChunk32 = 4;
+
+__host__ __device__ __forceinline__ size_t cta32_smem_bytes(int nw, int nx, int n_mat) {
+  return sizeof(float4) * 2 * kChunk32 * nw * 32 +           // partial-sum buffer
+         sizeof(float) * ((size_t)nw * ybuf32_floats(nx, 1) + (size_t)n_mat * nw * kTab2D);
+}
+
+template <int NW>
+__global__ void __launch_bounds__(32 * NW, 32 / NW) sweep2d_f32_cta_kernel(const Sweep2D32Args A) {
+  const int g = blockIdx.x, b = blockIdx.y;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (A.active && !A.active[b]) return;   // the same for every thread of the CTA: no barrier skipped
+  const SweepGroup grp = A.groups[g];
+  const bool xneg = grp.quad & 1, yneg = (grp.quad & 2) != 0;
+  const bool live = wid < grp.nd;         // surplus warps only take part in the barriers and sums
+  extern __shared__ float4 smq[];
+  float4* accb = smq;                                                  // [2][kChunk32][NW][32]
+  float* ybuf = reinterpret_cast<float*>(smq + 2 * kChunk32 * NW * 32)
+                + (size_t)wid * ybuf32_floats(A.nx, 1);                // this warp's [nx][2]
+  float* tab_s = reinterpret_cast<float*>(smq + 2 * kChunk32 * NW * 32)
+                 + (size_t)NW * ybuf32_floats(A.nx, 1);                // [n_mat][NW][32]
+  const float* __restrict__ tabg = A.tables + (size_t)b * A.n_mat * A.n_dirs * kTab2D;
+  for (int e = threadIdx.x; e < A.n_mat * NW * kTab2D; e += 32 * NW) {
+    const int m = e / (NW * kTab2D), r = e % (NW * kTab2D), dd = r / kTab2D, k = r % kTab2D;
+    tab_s[e] = dd < grp.nd ? tabg[((size_t)m * A.n_dirs + grp.d0 + dd) * kTab2D + k] : 0.f;
+  }
+  __syncthreads();
+  const float wd = live ? (float)A.dirs[4 * (grp.d0 + wid) + 2] : 0.f;
+  const float s3 = 1.7320508075688772f;
+  const float c3x = xneg ? -s3 : s3, c3y = yneg ? -s3 : s3;
+  const bool src = A.with_source && !(A.inner && A.inner[b]);
+  const float gxb = src ? (float)(A.inflow[4 * b + (xneg ? 1 : 0)] * A.sq_area) : 0.f;
+  const float gyb = src ? (float)(A.inflow[4 * b + (yneg ? 3 : 2)] * A.sq_area) : 0.f;
+  const int H = A.nx < 32 ? A.nx : 32;
+  const int nrb = (A.ny + H - 1) / H;
+  const int total = nrb * A.nx;
+  const int steps = total + H - 1;
+  const int padded = (steps + kChunk32 - 1) / kChunk32 * kChunk32;
+  const float4* __restrict__ Sb = reinterpret_cast<const float4*>(A.S) + (size_t)b * A.n_cells;
+  float4* part = reinterpret_cast<float4*>(A.partial + ((size_t)active_rank(A.active, b) * A.n_groups + g) * A.n_dof);
+  const float4* tab_w = reinterpret_cast<const float4*>(tab_s) + (size_t)wid * (kTab2D / 4);
+  // cell of lane l at wavefront step s_ (false when the lane is idle there); the same for every warp
+  auto cell_at = [&](int s_, int l, int& c_) -> bool {
+    const int u_ = s_ - l;
+    const bool in_ = l < H && u_ >= 0 && u_ < total;
+    const int rb_ = in_ ? u_ / A.nx : 0;
+    const int t_ = in_ ? u_ - rb_ * A.nx : 0;
+    const int r_ = rb_ * H + l;
+    c_ = (yneg ? A.ny - 1 - r_ : r_) * A.nx + (xneg ? A.nx - 1 - t_ : t_);
+    return in_ && r_ < A.ny;
+  };
+  float tx0 = 0.f, tx1 = 0.f, typ0 = 0.f, typ1 = 0.f;
+  int m_next = 0;
+  float4 sv_next = make_float4(0.f, 0.f, 0.f, 0.f);
+  {
+    int c0;
+    if (live && cell_at(0, lane, c0)) m_next = A.mat[c0], sv_next = Sb[c0];
+  }
+  for (int s = 0; s < padded; ++s) {
+    const int q = s % kChunk32;
+    float4* acc_slot = accb + ((size_t)(((s / kChunk32) & 1) * kChunk32 + q) * NW + wid) * 32 + lane;
+    if (live) {
+      const int u = s - lane;
+      const bool inrange = lane < H && u >= 0 && u < total;
+      const int rb = inrange ? u / A.nx : 0;
+      const int t = inrange ? u - rb * A.nx : 0;
+      const int r = rb * H + lane;
+      const bool act = inrange && r < A.ny;
+      const int m = m_next;
+      const float4 sv = sv_next;
+      {
+        int c1;
+        if (cell_at(s + 1, lane, c1)) m_next = A.mat[c1], sv_next = Sb[c1];
+      }
+      float ty0 = __shfl_up_sync(0xffffffffu, typ0, 1);
+      float ty1 = __shfl_up_sync(0xffffffffu, typ1, 1);
+      if (act) {
+        if (r == 0) {
+          ty0 = gyb, ty1 = 0.f;
+        } else if (lane == 0) {
+          ty0 = ybuf[2 * t];
+          ty1 = ybuf[2 * t + 1];
+        }
+        if (t == 0) tx0 = gxb, tx1 = 0.f;
+        const float4* T = tab_w + (size_t)m * NW * (kTab2D / 4);
+        float a[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float4 mr = T[2 * k], er = T[2 * k + 1];  // M^-1 row k | inflow rows k
+          float v = mr.x * sv.x;
+          v = fmaf(mr.y, sv.y, v);
+          v = fmaf(mr.z, sv.z, v);
+          v = fmaf(mr.w, sv.w, v);
+          v = fmaf(er.x, tx0, v);
+          v = fmaf(er.y, tx1, v);
+          v = fmaf(er.z, ty0, v);
+          v = fmaf(er.w, ty1, v);
+          a[k] = v;
+        }
+        tx0 = fmaf(c3x, a[1], a[0]);
+        tx1 = fmaf(c3x, a[3], a[2]);
+        typ0 = fmaf(c3y, a[2], a[0]);
+        typ1 = fmaf(c3y, a[3], a[1]);
+        *acc_slot = make_float4(wd * a[0], wd * a[1], wd * a[2], wd * a[3]);
+        if (lane == H - 1 && rb + 1 < nrb) {
+          ybuf[2 * t] = typ0;
+          ybuf[2 * t + 1] = typ1;
+        }
+      }
+      __syncwarp();
+    }
+    if (q == kChunk32 - 1) {
+      __syncthreads();
+      // sum the chunk's contributions over the warps, in warp order, one (step, lane) per thread
+      const int s0 = s - (kChunk32 - 1);
+      const float4* chunk = accb + (size_t)((s / kChunk32) & 1) * kChunk32 * NW * 32;
+      for (int i = threadIdx.x; i < kChunk32 * 32; i += 32 * NW) {
+        const int qq = i >> 5, l = i & 31;
+        int c;
+        if (!cell_at(s0 + qq, l, c)) continue;
+        const float4* p = chunk + (size_t)qq * NW * 32 + l;
+        float4 sum = p[0];
+        for (int w2 = 1; w2 < grp.nd; ++w2) {
+          const float4 v = p[(size_t)w2 * 32];
+          sum.x += v.x, sum.y += v.y, sum.z += v.z, sum.w += v.w;
+        }
+        part[c] = sum;
+      }
+    }
+  }
+}
+
 // rho_out (FP64) = sum of the FP32 group partials (fixed order, summed in FP32: the partials carry
 // FP32 rounding already, and FP64 additions would bind on GB300's FP64 pipe), plus y0 in FP64 for
 // the instances flagged in `inner`; fused norms (the change itself is formed in FP64).
@@ -1222,6 +1362,19 @@ static int launch2d_f32(const Sweep2D32Args& A, int B, int n_groups, cudaStream_
   return RTE_OK;
 }
 
+template <int NW>
+static int launch2d_f32_cta(const Sweep2D32Args& A, int B, int n_groups, cudaStream_t st) {
+  const size_t bytes = cta32_smem_bytes(NW, A.nx, A.n_mat);
+  if (bytes > 200 * 1024) return fail(RTE_EINVAL, "FP32 sweep: shared memory exceeded");
+  if (bytes > 48 * 1024) {
+    RTE_CUDA_TRY(cudaFuncSetAttribute(sweep2d_f32_cta_kernel<NW>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  }
+  sweep2d_f32_cta_kernel<NW><<<dim3(n_groups, B), 32 * NW, bytes, st>>>(A); RTE_NOTE_LAUNCH();
+  RTE_CUDA_TRY(cudaGetLastError());
+  return RTE_OK;
+}
+
 // One FP32 sweep of the active instances of a 2D batch, partial sums reduced in FP64 into
 // rho_out with the stop-test norms fused (as sweep_launch with fuse_norms).
 int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, const uint8_t* active,
@@ -1236,9 +1389,9 @@ int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, cons
     RTE_TRY(bt->S32.alloc((size_t)bt->B * d->n_dof));
     bt->tables32_stale = true;
   }
-  int dpw = bt->dpw, n_groups = 0;
+  int dpw = bt->dpw, n_groups = 0, form = 1;
   const SweepGroup* gdev = nullptr;
-  pick_groups(bt, n_active, &dpw, &n_groups, &gdev, true);
+  pick_groups(bt, n_active, &dpw, &n_groups, &gdev, true, &form);
   const size_t need32 = bt->partial.n;  // the same group-slice capacity as the FP64 partial sums
   if (bt->partial32.n < need32) RTE_TRY(bt->partial32.alloc(need32));
   if (bt->tables32_stale) {
@@ -1259,12 +1412,22 @@ int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, cons
                   d->mat_id.p, d->dir_dev.p,   gdev,     d->nx,          d->ny,
                   d->n_cells, d->n_dof,        d->n_mat, d->n_dirs,      n_groups,
                   1,          std::sqrt(d->hx * d->hy)};
-  switch (dpw) {
-    case 1: RTE_TRY(launch2d_f32<1>(A, bt->B, n_groups, st)); break;
-    case 2: RTE_TRY(launch2d_f32<2>(A, bt->B, n_groups, st)); break;
-    case 4: RTE_TRY(launch2d_f32<4>(A, bt->B, n_groups, st)); break;
-    case 8: RTE_TRY(launch2d_f32<8>(A, bt->B, n_groups, st)); break;
-    default: return fail(RTE_EINVAL, "unsupported directions-per-warp");
+  if (form == 1) {   // one warp per direction, the group's warps in one CTA
+    switch (dpw) {
+      case 1: RTE_TRY(launch2d_f32_cta<1>(A, bt->B, n_groups, st)); break;
+      case 2: RTE_TRY(launch2d_f32_cta<2>(A, bt->B, n_groups, st)); break;
+      case 4: RTE_TRY(launch2d_f32_cta<4>(A, bt->B, n_groups, st)); break;
+      case 8: RTE_TRY(launch2d_f32_cta<8>(A, bt->B, n_groups, st)); break;
+      default: return fail(RTE_EINVAL, "unsupported directions-per-warp");
+    }
+  } else {
+    switch (dpw) {
+      case 1: RTE_TRY(launch2d_f32<1>(A, bt->B, n_groups, st)); break;
+      case 2: RTE_TRY(launch2d_f32<2>(A, bt->B, n_groups, st)); break;
+      case 4: RTE_TRY(launch2d_f32<4>(A, bt->B, n_groups, st)); break;
+      case 8: RTE_TRY(launch2d_f32<8>(A, bt->B, n_groups, st)); break;
+      default: return fail(RTE_EINVAL, "unsupported directions-per-warp");
+    }
   }
   if (bt->timing) {
     RTE_CUDA_TRY(cudaEventRecord(ev1, st));
@@ -1282,6 +1445,17 @@ int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, cons
 }
 
 }  // namespace rte
+
+extern "C" int rte_sweep_f32(rte_batch_t b, const double* rho_in, double* rho_out,
+                             const uint8_t* active, void* stream) {
+  if (!b || !rho_in || !rho_out) return fail(RTE_EINVAL, "rte_sweep_f32: null argument");
+  RTE_TRY(params_ready(b, "rte_sweep_f32"));
+  if (b->disc->dim != 2) return fail(RTE_EINVAL, "rte_sweep_f32: 2D batches only");
+  if (rho_in == rho_out) return fail(RTE_EINVAL, "rte_sweep_f32: rho_out aliases rho_in");
+  DeviceGuard g(b->disc->device);
+  // the group choice is sized for every instance running (the mask is device memory)
+  return sweep_launch_f32(b, rho_in, rho_out, active, (cudaStream_t)stream, b->B);
+}
 
 namespace rte {
 // Empirical choice of the sweep decomposition: for running-instance counts B, B/2, B/4, ..., 1
@@ -1321,10 +1495,15 @@ static int autotune(rte_batch_t bt, cudaStream_t st, int* n_entries, int* table)
         return prec == 0 ? sweep_launch(bt, bt->work.p, bt->work.p + nb, nullptr, 1, mask.p, st, true, n)
                          : sweep_launch_f32(bt, bt->work.p, bt->work.p + nb, mask.p, st, n);
       };
+      // FP32: both forms of the kernel unless the batch fixes one (entries dpw | form << 8)
+      const int f_lo = prec == 0 || !bt->f32_form_auto ? bt->f32_form : 0;
+      const int f_hi = prec == 0 || !bt->f32_form_auto ? bt->f32_form : 1;
+      for (int form = f_lo; form <= f_hi && status == RTE_OK; ++form)
       for (int dpw = 1; dpw <= kMaxDirsPerWarp && status == RTE_OK; dpw *= 2) {
         const int k = dpw == 1 ? 0 : dpw == 2 ? 1 : dpw == 4 ? 2 : 3;
         if ((size_t)n * bt->gcount[k] * d->n_dof > bt->partial.n) continue;  // no partial-sum space
         bt->force_dpw = dpw;
+        bt->force_form = prec == 1 ? form : -1;
         float ms = 0.f;
         status = launch();
         if (status == RTE_OK && cudaEventRecord(e0, st) != cudaSuccess) status = fail(RTE_ECUDA, "autotune: event");
@@ -1333,7 +1512,8 @@ static int autotune(rte_batch_t bt, cudaStream_t st, int* n_entries, int* table)
                                  cudaEventSynchronize(e1) != cudaSuccess ||
                                  cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
           status = fail(RTE_ECUDA, "autotune: timing");
-        if (status == RTE_OK && (best == 0 || ms < best_ms)) best_ms = ms, best = dpw;
+        if (status == RTE_OK && (best == 0 || ms < best_ms))
+          best_ms = ms, best = prec == 1 ? (dpw | form << 8) : dpw;
       }
       if (status != RTE_OK) break;
       (prec == 0 ? bt->tuned : bt->tuned32).emplace_back(n, best);
@@ -1341,6 +1521,7 @@ static int autotune(rte_batch_t bt, cudaStream_t st, int* n_entries, int* table)
     if (status != RTE_OK) break;
   }
   bt->force_dpw = 0;
+  bt->force_form = -1;
   bt->timing = timing;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
