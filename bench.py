@@ -32,9 +32,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "solves/s at 1e-6 φ error (ROMSAD vs SI-DSA, same GPU); sweep GB/s; p50/p99 ms"
 FP64_PEAK_NOMINAL = 1.25    # GB300 FP64 rate from the unit table (used only if the probe fails)
-# 40 FMA per cell and distinct direction: 8 per unknown for the 4 unknowns (M^-1 s and the two
-# inflow couplings), 4 for the outflow traces, 4 for the scalar-flux accumulation
-FLOP_PER_CELL_DIR = 80
+# 32 FMA per cell and distinct direction: 8 to form the right-hand side s + E_x t_x + E_y t_y, 16
+# to apply M^-1, 4 for the outflow traces, 4 for the scalar-flux accumulation
+FLOP_PER_CELL_DIR = 64
 BYTES_PER_CELL_SWEEP = 76   # rho_in 32 B + G0 8 B + material id 4 B + rho_out 32 B
 # DRAM bytes per sweep launch from the committed ncu capture, valid only for the 2D sweep
 # kernels' device code it was taken with (sha1 of that part of sweep.cu, sweep_source_sha1)

@@ -210,15 +210,6 @@ int rte_sweep(rte_batch_t batch, const double* rho_in, double* rho_out, double* 
 int rte_sweep_f32(rte_batch_t batch, const double* rho_in, double* rho_out, const uint8_t* active,
                   void* stream);
 
-/* Form of the FP32 sweep kernel: 0 -- one warp per group of directions (the group's directions
- * give each lane independent work per step); 1 -- one warp per direction, the warps of a group in
- * one thread block, which adds their contributions to each cell in shared memory in a fixed order
- * before writing one partial sum per group (more warps in flight for the same partial-sum
- * traffic); -1 (default) -- chosen by rte_batch_autotune per number of running instances, form 1
- * until it has run.  Both give the same sweep up to FP32 rounding (the partial sums are grouped
- * differently); each is deterministic.  Errors: RTE_EINVAL. */
-int rte_batch_f32_form(rte_batch_t batch, int form);
-
 /* Work decomposition of the 2D sweep: dirs_per_warp in {1, 2, 4, 8} sets how many directions of
  * one quadrant a warp sweeps together (more directions: more instruction-level parallelism and
  * fewer partial sums; fewer: more warps in flight).  0 (the default) picks per launch the largest

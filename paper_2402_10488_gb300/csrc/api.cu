@@ -289,12 +289,10 @@ static std::vector<SweepGroup> groups_for(const rte_disc_s* disc, int dpw) {
 }
 
 void pick_groups(rte_batch_t b, int n_active, int* dpw, int* n_groups, const SweepGroup** dev,
-                 bool f32, int* f32_form) {
+                 bool f32) {
   int use = b->dpw;
   auto kof = [](int v) { return v == 1 ? 0 : v == 2 ? 1 : v == 4 ? 2 : 3; };
-  const bool t32 = f32 && !b->tuned32.empty();
-  const auto& tuned = t32 ? b->tuned32 : b->tuned;
-  if (f32_form) *f32_form = b->force_form >= 0 ? b->force_form : b->f32_form;
+  const auto& tuned = f32 && !b->tuned32.empty() ? b->tuned32 : b->tuned;
   if (b->force_dpw && b->disc->dim == 2) {
     use = b->force_dpw;
   } else if (b->dpw_dynamic && b->disc->dim == 2) {
@@ -305,10 +303,6 @@ void pick_groups(rte_batch_t b, int n_active, int* dpw, int* n_groups, const Swe
           use = e.second;
           break;
         }
-      if (t32) {   // FP32 entries carry the measured form in their high bits
-        if (f32_form && b->force_form < 0) *f32_form = use >> 8;
-        use &= 0xFF;
-      }
     } else {
       use = 1;
       for (int k = 3; k >= 1; --k) {
@@ -353,15 +347,6 @@ int auto_dpw(const rte_disc_s* disc, int B) {
   return 1;
 }
 }  // namespace rte
-
-extern "C" int rte_batch_f32_form(rte_batch_t b, int form) {
-  if (!b) return fail(RTE_EINVAL, "rte_batch_f32_form: null argument");
-  if (form < -1 || form > 1) return fail(RTE_EINVAL, "rte_batch_f32_form: form must be -1, 0 or 1");
-  b->f32_form_auto = form < 0;
-  if (form >= 0) b->f32_form = form;
-  b->tuned32.clear();
-  return RTE_OK;
-}
 
 extern "C" int rte_batch_tune(rte_batch_t b, int dpw) {
   if (!b) return fail(RTE_EINVAL, "rte_batch_tune: null argument");

@@ -91,7 +91,7 @@ struct DevBuf {
   DevBuf& operator=(const DevBuf&) = delete;
 };
 
-constexpr int kTab2D = 32;  // doubles per (material, direction) sweep table in 2D
+constexpr int kTab2D = 16;  // doubles per (material, direction) sweep table in 2D: M^-1 (4x4)
 constexpr int kTab1D = 8;   // ... in 1D, per (instance, cell, direction): Minv 2x2, inflow 2x1, 1/sqrt(h)
 constexpr int kMaxDirsPerWarp = 8;
 constexpr size_t kPartialBytes = size_t(64) << 20;  // per-instance sweep partial sums, upper bound
@@ -160,12 +160,6 @@ struct rte_batch_s {
   std::vector<std::pair<int, int>> tuned;
   std::vector<std::pair<int, int>> tuned32;   // the same, measured with the FP32 sweep
   int force_dpw = 0;                  // autotuner trials: this dpw for every launch
-  // form of the FP32 sweep (rte_batch_f32_form): 0 -- one warp per group of directions; 1 -- one
-  // warp per direction, a group's warps in one CTA summing their contributions in shared memory.
-  // With f32_form_auto the autotuner measures both (its FP32 table entries are dpw | form << 8).
-  int f32_form = 1;
-  bool f32_form_auto = true;
-  int force_form = -1;                // autotuner trials: this FP32 form for every launch
   bool kba = true;                    // several warps per direction group when warps are scarce
   std::vector<double> sigma_t_h, sigma_s_h, source_h, inflow_h;
   // parameters taken from device memory (rte_batch_set_params_device) are validated on the device;
@@ -244,7 +238,7 @@ void make_groups(rte_batch_t b);
 int auto_dpw(const rte_disc_s* disc, int B);
 // groups of one launch: dpw, number of groups and their device table
 void pick_groups(rte_batch_t b, int n_active, int* dpw, int* n_groups, const SweepGroup** dev,
-                 bool f32 = false, int* f32_form = nullptr);
+                 bool f32 = false);
 // sweep.cu
 int sweep_launch(rte_batch_t b, const double* rho_in, double* rho_out, double* psi_out,
                  int with_source, const uint8_t* active, cudaStream_t st, bool fuse_norms,

@@ -2,12 +2,17 @@
 //
 // 2D: upwind DG-Q^1 on a uniform Cartesian mesh.  In every cell and direction the local system
 //     M a = s + E_x t_x + E_y t_y,   M = sigma_t I + a_x (K_x (x) I) + a_y (I (x) K_y)
-// is solved with a per-(material, direction) table {M^-1, M^-1 E_x, M^-1 E_y} computed once per
-// parameter set, where a_x = |v_x|/h_x, K_x = [[1, s_x sqrt3], [-s_x sqrt3, 3]] (s_x the sign
-// of v_x), s = Sigma_s rho + G are the cell's source moments and t_x, t_y the upwind traces
+// is solved with a per-(material, direction) table M^-1 computed once per parameter set, where
+// a_x = |v_x|/h_x, K_x = [[1, s_x sqrt3], [-s_x sqrt3, 3]] (s_x the sign of v_x), s = Sigma_s rho
+// + G are the cell's source moments and t_x, t_y the upwind traces
 //     t_x[b] = a_{0b} + s_x sqrt3 a_{1b}   (x-outflow face, expanded along y),
 //     t_y[a] = a_{a0} + s_y sqrt3 a_{a1}   (y-outflow face, expanded along x).
-// On an inflow boundary t = g sqrt(h_x h_y) (isotropic inflow g, zeroth moment only).
+// On an inflow boundary t = g sqrt(h_x h_y) (isotropic inflow g, zeroth moment only).  The inflow
+// couplings have two distinct entries per direction, E_x t_x = (a_x t_x0, b_x t_x0, a_x t_x1,
+// b_x t_x1) and E_y t_y = (a_y t_y0, a_y t_y1, b_y t_y0, b_y t_y1) with b = -s sqrt3 a, so the
+// right-hand side is formed first (8 FMA) and M^-1 applied to it (16): 32 FMA per cell and
+// direction with the traces and the scalar-flux accumulation, against 40 with M^-1 E_x, M^-1 E_y
+// tabulated.
 //
 // Parallel layout (GB300): one warp per (instance, quadrant, group of <= DPW directions).  The
 // warp sweeps the mesh in blocks of H = min(32, n_x) rows; lane l owns row l of the block and
@@ -88,25 +93,40 @@ __global__ void tables2d_kernel(double* tables, const double* sigma_t, const dou
           M[4 * (aa + 2 * bb) + (a2 + 2 * b2)] = v;
         }
   inv4(M);
-  double Ex[4][2] = {{0}}, Ey[4][2] = {{0}};
-  for (int q = 0; q < 2; ++q) {
-    Ex[0 + 2 * q][q] = ax;
-    Ex[1 + 2 * q][q] = -sx * s3 * ax;
-    Ey[q][q] = ay;
-    Ey[q + 2][q] = -sy * s3 * ay;
-  }
   double* T = tables + (size_t)idx * kTab2D;
   for (int k = 0; k < 16; ++k) T[k] = M[k];
-  for (int k = 0; k < 4; ++k)
-    for (int q = 0; q < 2; ++q) {
-      double px = 0.0, py = 0.0;
-      for (int l = 0; l < 4; ++l) {
-        px += M[4 * k + l] * Ex[l][q];
-        py += M[4 * k + l] * Ey[l][q];
-      }
-      T[16 + 2 * k + q] = px;
-      T[24 + 2 * k + q] = py;
-    }
+}
+
+// Per-direction inflow couplings of the 2D cell solve (see the file header): a = |v|/h and
+// b = -s sqrt3 a along x and y.
+struct InflowCoef {
+  double ax, bx, ay, by;
+};
+__device__ __forceinline__ InflowCoef inflow_coef(const double* dirs, int d, double ihx, double ihy) {
+  const double s3 = 1.7320508075688772;
+  const double vx = dirs[4 * d], vy = dirs[4 * d + 1];
+  InflowCoef c;
+  c.ax = fabs(vx) * ihx;
+  c.ay = fabs(vy) * ihy;
+  c.bx = (vx < 0 ? s3 : -s3) * c.ax;
+  c.by = (vy < 0 ? s3 : -s3) * c.ay;
+  return c;
+}
+
+// One cell of one direction: a = M^-1 (s + E_x t_x + E_y t_y), T the direction's M^-1 (row-major).
+__device__ __forceinline__ void cell_solve(const double* T, const InflowCoef& e, double s0, double s1,
+                                           double s2, double s3v, const double tx[2],
+                                           const double ty[2], double a[4]) {
+  const double r0 = fma(e.ay, ty[0], fma(e.ax, tx[0], s0));
+  const double r1 = fma(e.ay, ty[1], fma(e.bx, tx[0], s1));
+  const double r2 = fma(e.by, ty[0], fma(e.ax, tx[1], s2));
+  const double r3 = fma(e.by, ty[1], fma(e.bx, tx[1], s3v));
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double2 m01 = reinterpret_cast<const double2*>(T + 4 * k)[0];
+    const double2 m23 = reinterpret_cast<const double2*>(T + 4 * k)[1];
+    a[k] = fma(m23.y, r3, fma(m23.x, r2, fma(m01.y, r1, m01.x * r0)));
+  }
 }
 
 // One thread per (instance, cell, direction), 1D: M = Sigma_t + (|xi|/h) [[1, s sqrt3],
@@ -154,6 +174,7 @@ struct Sweep2DArgs {
   const SweepGroup* groups;
   int nx, ny, n_cells, n_dof, n_mat, n_dirs, n_groups, with_source;
   double sq_area;
+  double ihx, ihy;          // 1 / h_x, 1 / h_y
   // balance accounting (kernels instantiated with LEAK only): per (running instance, group, cell)
   // the omega-weighted net outflow through the cell's faces; lx = sqrt(h_y / h_x) and
   // ly = sqrt(h_x / h_y) turn a face trace's zeroth coefficient into the face integral
@@ -187,8 +208,12 @@ __global__ void __launch_bounds__(32) sweep2d_kernel(const Sweep2DArgs A) {
   __syncwarp();
 
   double w[DPW];
+  InflowCoef ec[DPW];
 #pragma unroll
-  for (int dd = 0; dd < DPW; ++dd) w[dd] = dd < grp.nd ? A.dirs[4 * (grp.d0 + dd) + 2] : 0.0;
+  for (int dd = 0; dd < DPW; ++dd) {
+    w[dd] = dd < grp.nd ? A.dirs[4 * (grp.d0 + dd) + 2] : 0.0;
+    ec[dd] = inflow_coef(A.dirs, grp.d0 + (dd < grp.nd ? dd : 0), A.ihx, A.ihy);
+  }
   const double s3 = sqrt(3.0);
   const double c3x = xneg ? -s3 : s3, c3y = yneg ? -s3 : s3;
   const double gxb = A.with_source ? A.inflow[4 * b + (xneg ? 1 : 0)] * A.sq_area : 0.0;
@@ -264,18 +289,7 @@ __global__ void __launch_bounds__(32) sweep2d_kernel(const Sweep2DArgs A) {
           const double* T = SMEM_TAB ? tab_s + (m * DPW + dd) * kTab2D
                                      : tabg + ((size_t)m * A.n_dirs + grp.d0 + dd) * kTab2D;
           double a[4];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            double v = T[4 * k] * s0;
-            v = fma(T[4 * k + 1], s1, v);
-            v = fma(T[4 * k + 2], s2, v);
-            v = fma(T[4 * k + 3], s3v, v);
-            v = fma(T[16 + 2 * k], tx[dd][0], v);
-            v = fma(T[17 + 2 * k], tx[dd][1], v);
-            v = fma(T[24 + 2 * k], ty[dd][0], v);
-            v = fma(T[25 + 2 * k], ty[dd][1], v);
-            a[k] = v;
-          }
+          cell_solve(T, ec[dd], s0, s1, s2, s3v, tx[dd], ty[dd], a);
           const double txin = tx[dd][0];
           tx[dd][0] = fma(c3x, a[1], a[0]);
           tx[dd][1] = fma(c3x, a[3], a[2]);
@@ -339,8 +353,12 @@ __global__ void __launch_bounds__(256) sweep2d_kba_kernel(const Sweep2DArgs A, i
   }
   __syncthreads();
   double w[DPW];
+  InflowCoef ec[DPW];
 #pragma unroll
-  for (int dd = 0; dd < DPW; ++dd) w[dd] = dd < grp.nd ? A.dirs[4 * (grp.d0 + dd) + 2] : 0.0;
+  for (int dd = 0; dd < DPW; ++dd) {
+    w[dd] = dd < grp.nd ? A.dirs[4 * (grp.d0 + dd) + 2] : 0.0;
+    ec[dd] = inflow_coef(A.dirs, grp.d0 + (dd < grp.nd ? dd : 0), A.ihx, A.ihy);
+  }
   const double s3 = sqrt(3.0);
   const double c3x = xneg ? -s3 : s3, c3y = yneg ? -s3 : s3;
   const double gxb = A.with_source ? A.inflow[4 * b + (xneg ? 1 : 0)] * A.sq_area : 0.0;
@@ -401,18 +419,7 @@ __global__ void __launch_bounds__(256) sweep2d_kba_kernel(const Sweep2DArgs A, i
           const double* T = SMEM_TAB ? tab_s + (m * DPW + dd) * kTab2D
                                      : tabg + ((size_t)m * A.n_dirs + grp.d0 + dd) * kTab2D;
           double a[4];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            double v = T[4 * k] * s0;
-            v = fma(T[4 * k + 1], s1, v);
-            v = fma(T[4 * k + 2], s2, v);
-            v = fma(T[4 * k + 3], s3v, v);
-            v = fma(T[16 + 2 * k], tx[dd][0], v);
-            v = fma(T[17 + 2 * k], tx[dd][1], v);
-            v = fma(T[24 + 2 * k], ty[dd][0], v);
-            v = fma(T[25 + 2 * k], ty[dd][1], v);
-            a[k] = v;
-          }
+          cell_solve(T, ec[dd], s0, s1, s2, s3v, tx[dd], ty[dd], a);
           tx[dd][0] = fma(c3x, a[1], a[0]);
           tx[dd][1] = fma(c3x, a[3], a[2]);
           typ[dd][0] = fma(c3y, a[2], a[0]);
@@ -764,7 +771,8 @@ int sweep_launch(rte_batch_t bt, const double* rho_in, double* rho_out, double* 
     Sweep2DArgs A{bt->S.p,      bt->partial.p, psi_out,        active,      bt->tables.p,
                   bt->sigma_s.p, bt->G0.p,     bt->inflow.p,   d->mat_id.p, d->dir_dev.p,
                   gdev,         d->nx,         d->ny,          d->n_cells,  d->n_dof,
-                  d->n_mat,     d->n_dirs,     n_groups,       with_source, std::sqrt(d->hx * d->hy)};
+                  d->n_mat,     d->n_dirs,     n_groups,       with_source, std::sqrt(d->hx * d->hy),
+                  1.0 / d->hx,  1.0 / d->hy};
     const int NW = bt->kba ? kba_warps(d, bt->n_sm, (long long)n_active * n_groups) : 1;
     if (NW >= 2) {
       const int H = d->nx < 32 ? d->nx : 32;
@@ -900,7 +908,8 @@ int sweep_launch_with_scratch(rte_batch_t bt, const double* rho_in, double* rho_
     Sweep2DArgs A{rho_in,       partial,       nullptr,        nullptr,     bt->tables.p,
                   bt->sigma_s.p, bt->G0.p,     bt->inflow.p,   d->mat_id.p, d->dir_dev.p,
                   bt->groups_dev.p, d->nx,     d->ny,          d->n_cells,  d->n_dof,
-                  d->n_mat,     d->n_dirs,     n_groups,       with_source, std::sqrt(d->hx * d->hy)};
+                  d->n_mat,     d->n_dirs,     n_groups,       with_source, std::sqrt(d->hx * d->hy),
+                  1.0 / d->hx,  1.0 / d->hy};
     switch (bt->dpw) {
       case 1: RTE_TRY(launch2d<1>(A, bt->B, n_groups, st)); break;
       case 2: RTE_TRY(launch2d<2>(A, bt->B, n_groups, st)); break;
@@ -949,7 +958,8 @@ int sweep_launch_leak(rte_batch_t bt, const double* rho_in, double* rho_out, con
                   bt->sigma_s.p, bt->G0.p,     bt->inflow.p,   d->mat_id.p, d->dir_dev.p,
                   gdev,         d->nx,         d->ny,          d->n_cells,  d->n_dof,
                   d->n_mat,     d->n_dirs,     n_groups,       1,           std::sqrt(d->hx * d->hy),
-                  bt->leak.p,   std::sqrt(d->hy / d->hx),      std::sqrt(d->hx / d->hy)};
+                  1.0 / d->hx,  1.0 / d->hy,   bt->leak.p,     std::sqrt(d->hy / d->hx),
+                  std::sqrt(d->hx / d->hy)};
     RTE_TRY((launch2d<8, true, true>(A, bt->B, n_groups, st)));
   } else {
     Sweep1DArgs A{rho_in,      bt->partial.p, nullptr,  active, bt->tables.p, bt->sigma_s.p,
@@ -984,16 +994,11 @@ int sweep_launch_leak(rte_batch_t bt, const double* rho_in, double* rho_out, con
 // with FP32 rounding confined to the small e.
 namespace rte {
 
-// FP32 copy of the sweep tables, each table row-interleaved: row k (k < 4) is the 8 floats
-// {M^-1[k][0..3], (M^-1 E_x)[k][0..1], (M^-1 E_y)[k][0..1]}, so that the sweep reads a row with two
-// 16-byte shared-memory loads (the FP64 layout keeps the three blocks apart).
+// FP32 copy of the sweep tables (M^-1 of each (instance, material, direction), row-major, so that a
+// row is one 16-byte word).
 __global__ void tables_to_f32_kernel(const double* t64, float* t32, size_t n) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const size_t base = i / kTab2D * kTab2D;
-  const int q = (int)(i % kTab2D), k = q / 8, j = q % 8;
-  const int src = j < 4 ? 4 * k + j : (j < 6 ? 16 + 2 * k + (j - 4) : 24 + 2 * k + (j - 6));
-  t32[i] = (float)t64[base + src];
+  if (i < n) t32[i] = (float)t64[i];
 }
 
 // floats of the FP32 sweep's y-inflow line buffer, rounded up so that the tables behind it start
@@ -1038,7 +1043,13 @@ struct Sweep2D32Args {
   const SweepGroup* groups;
   int nx, ny, n_cells, n_dof, n_mat, n_dirs, n_groups, with_source;
   double sq_area;
+  double ihx, ihy;          // 1 / h_x, 1 / h_y
 };
+
+// Per-material stride of the FP32 kernel's shared-memory tables: a group's DPW tables of 16 floats,
+// padded by 4 floats so that rows of consecutive materials fall into different banks (a warp's
+// lanes on either side of a material interface then read their rows without a bank conflict).
+__host__ __device__ __forceinline__ int tab32_stride(int dpw) { return dpw * kTab2D + 4; }
 
 template <int DPW>
 __global__ void __launch_bounds__(32) sweep2d_f32_kernel(const Sweep2D32Args A) {
@@ -1048,16 +1059,25 @@ __global__ void __launch_bounds__(32) sweep2d_f32_kernel(const Sweep2D32Args A) 
   const bool xneg = grp.quad & 1, yneg = (grp.quad & 2) != 0;
   extern __shared__ float smf[];
   float* ybuf = smf;                                 // [nx][DPW][2]
-  float* tab_s = smf + ybuf32_floats(A.nx, DPW);     // [n_mat][DPW][32], 16-byte aligned
+  float* tab_s = smf + ybuf32_floats(A.nx, DPW);     // [n_mat][tab32_stride], 16-byte aligned
+  const int mstride = tab32_stride(DPW);
   const float* __restrict__ tabg = A.tables + (size_t)b * A.n_mat * A.n_dirs * kTab2D;
   for (int e = lane; e < A.n_mat * DPW * kTab2D; e += 32) {
     const int m = e / (DPW * kTab2D), r = e % (DPW * kTab2D), dd = r / kTab2D, k = r % kTab2D;
-    tab_s[e] = dd < grp.nd ? tabg[((size_t)m * A.n_dirs + grp.d0 + dd) * kTab2D + k] : 0.f;
+    tab_s[m * mstride + r] = dd < grp.nd ? tabg[((size_t)m * A.n_dirs + grp.d0 + dd) * kTab2D + k] : 0.f;
   }
   __syncwarp();
-  float w[DPW];
+  float w[DPW], ax[DPW], bx[DPW], ay[DPW], by[DPW];
 #pragma unroll
-  for (int dd = 0; dd < DPW; ++dd) w[dd] = dd < grp.nd ? (float)A.dirs[4 * (grp.d0 + dd) + 2] : 0.f;
+  for (int dd = 0; dd < DPW; ++dd) {
+    const bool in = dd < grp.nd;
+    w[dd] = in ? (float)A.dirs[4 * (grp.d0 + dd) + 2] : 0.f;
+    const double vx = in ? A.dirs[4 * (grp.d0 + dd)] : 0.0, vy = in ? A.dirs[4 * (grp.d0 + dd) + 1] : 0.0;
+    const double axd = fabs(vx) * A.ihx, ayd = fabs(vy) * A.ihy;
+    ax[dd] = (float)axd, ay[dd] = (float)ayd;
+    bx[dd] = (float)((vx < 0 ? 1.7320508075688772 : -1.7320508075688772) * axd);
+    by[dd] = (float)((vy < 0 ? 1.7320508075688772 : -1.7320508075688772) * ayd);
+  }
   const float s3 = 1.7320508075688772f;
   const float c3x = xneg ? -s3 : s3, c3y = yneg ? -s3 : s3;
   const bool src = A.with_source && !(A.inner && A.inner[b]);
@@ -1071,36 +1091,38 @@ __global__ void __launch_bounds__(32) sweep2d_f32_kernel(const Sweep2D32Args A) 
   float tx[DPW][2], typ[DPW][2];
 #pragma unroll
   for (int dd = 0; dd < DPW; ++dd) tx[dd][0] = tx[dd][1] = typ[dd][0] = typ[dd][1] = 0.f;
-  // cell of this lane at wavefront step s_ (false when the lane is idle there)
-  auto cell_at = [&](int s_, int& c_) -> bool {
-    const int u_ = s_ - lane;
-    const bool in_ = lane < H && u_ >= 0 && u_ < total;
-    const int rb_ = in_ ? u_ / A.nx : 0;
-    const int t_ = in_ ? u_ - rb_ * A.nx : 0;
+  // A lane handles u = s - lane, u = 0, 1, ..., total - 1, at column t = u mod nx of row block
+  // rb = u / nx; both are kept as counters (tn, rbn: the position of u + 1) instead of being
+  // divided out at every step.  Its cell is c = j nx + i with i, j the mirrored t and rb H + lane.
+  auto cell_of = [&](int t_, int rb_) {
     const int r_ = rb_ * H + lane;
-    c_ = (yneg ? A.ny - 1 - r_ : r_) * A.nx + (xneg ? A.nx - 1 - t_ : t_);
-    return in_ && r_ < A.ny;
+    return (yneg ? A.ny - 1 - r_ : r_) * A.nx + (xneg ? A.nx - 1 - t_ : t_);
   };
+  int tn = 0, rbn = 0;
   // the next step's material and cell source are loaded while this step computes, so the
   // global-memory latency is off the wavefront's critical path
   int m_next = 0;
   float4 sv_next = make_float4(0.f, 0.f, 0.f, 0.f);
-  {
-    int c0;
-    if (cell_at(0, c0)) m_next = A.mat[c0], sv_next = Sb[c0];
+  if (lane == 0 && H > 0 && A.ny > 0) {   // lane 0's first cell (u = 0 at step 0)
+    const int c0 = cell_of(0, 0);
+    m_next = A.mat[c0], sv_next = Sb[c0];
   }
   for (int s = 0; s < total + H - 1; ++s) {
     const int u = s - lane;
+    int t = 0, rb = 0;
+    if (u >= 0) {   // this step's position; advance the next one
+      t = tn, rb = rbn;
+      if (++tn == A.nx) tn = 0, ++rbn;
+    }
     const bool inrange = lane < H && u >= 0 && u < total;
-    const int rb = inrange ? u / A.nx : 0;
-    const int t = inrange ? u - rb * A.nx : 0;
     const int r = rb * H + lane;
     const bool act = inrange && r < A.ny;
-    const int m_cur = m_next;
-    const float4 sv_cur = sv_next;
-    {
-      int c1;
-      if (cell_at(s + 1, c1)) m_next = A.mat[c1], sv_next = Sb[c1];
+    const int m = m_next;
+    const float4 sv = sv_next;
+    // u + 1 sits at (tn, rbn)
+    if (lane < H && u + 1 >= 0 && u + 1 < total && rbn * H + lane < A.ny) {
+      const int c1 = cell_of(tn, rbn);
+      m_next = A.mat[c1], sv_next = Sb[c1];
     }
     float ty[DPW][2];
 #pragma unroll
@@ -1123,39 +1145,34 @@ __global__ void __launch_bounds__(32) sweep2d_f32_kernel(const Sweep2D32Args A) 
 #pragma unroll
         for (int dd = 0; dd < DPW; ++dd) tx[dd][0] = gxb, tx[dd][1] = 0.f;
       }
-      const int i = xneg ? A.nx - 1 - t : t;
-      const int j = yneg ? A.ny - 1 - r : r;
-      const int c = j * A.nx + i;
-      const int m = m_cur;
-      const float4 sv = sv_cur;
+      const int c = cell_of(t, rb);
       float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+      // every slot of the group is computed without a branch, so the DPW directions' FMA chains
+      // can be interleaved: a slot beyond the group's directions has zero tables and weight and
+      // adds nothing
+      const float4* Tm = reinterpret_cast<const float4*>(tab_s + m * mstride);
 #pragma unroll
       for (int dd = 0; dd < DPW; ++dd) {
-        if (dd < grp.nd) {
-          const float4* T = reinterpret_cast<const float4*>(tab_s + (m * DPW + dd) * kTab2D);
-          float a[4];
+        const float4* T = Tm + dd * (kTab2D / 4);
+        // right-hand side s + E_x t_x + E_y t_y, then the rows of M^-1
+        const float r0 = fmaf(ay[dd], ty[dd][0], fmaf(ax[dd], tx[dd][0], sv.x));
+        const float r1 = fmaf(ay[dd], ty[dd][1], fmaf(bx[dd], tx[dd][0], sv.y));
+        const float r2 = fmaf(by[dd], ty[dd][0], fmaf(ax[dd], tx[dd][1], sv.z));
+        const float r3 = fmaf(by[dd], ty[dd][1], fmaf(bx[dd], tx[dd][1], sv.w));
+        float a[4];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const float4 mr = T[2 * k], er = T[2 * k + 1];  // M^-1 row k | inflow rows k
-            float v = mr.x * sv.x;
-            v = fmaf(mr.y, sv.y, v);
-            v = fmaf(mr.z, sv.z, v);
-            v = fmaf(mr.w, sv.w, v);
-            v = fmaf(er.x, tx[dd][0], v);
-            v = fmaf(er.y, tx[dd][1], v);
-            v = fmaf(er.z, ty[dd][0], v);
-            v = fmaf(er.w, ty[dd][1], v);
-            a[k] = v;
-          }
-          tx[dd][0] = fmaf(c3x, a[1], a[0]);
-          tx[dd][1] = fmaf(c3x, a[3], a[2]);
-          typ[dd][0] = fmaf(c3y, a[2], a[0]);
-          typ[dd][1] = fmaf(c3y, a[3], a[1]);
-          acc0 = fmaf(w[dd], a[0], acc0);
-          acc1 = fmaf(w[dd], a[1], acc1);
-          acc2 = fmaf(w[dd], a[2], acc2);
-          acc3 = fmaf(w[dd], a[3], acc3);
+        for (int k = 0; k < 4; ++k) {
+          const float4 mr = T[k];
+          a[k] = fmaf(mr.w, r3, fmaf(mr.z, r2, fmaf(mr.y, r1, mr.x * r0)));
         }
+        tx[dd][0] = fmaf(c3x, a[1], a[0]);
+        tx[dd][1] = fmaf(c3x, a[3], a[2]);
+        typ[dd][0] = fmaf(c3y, a[2], a[0]);
+        typ[dd][1] = fmaf(c3y, a[3], a[1]);
+        acc0 = fmaf(w[dd], a[0], acc0);
+        acc1 = fmaf(w[dd], a[1], acc1);
+        acc2 = fmaf(w[dd], a[2], acc2);
+        acc3 = fmaf(w[dd], a[3], acc3);
       }
       part[c] = make_float4(acc0, acc1, acc2, acc3);
       if (lane == H - 1 && rb + 1 < nrb) {
@@ -1167,146 +1184,6 @@ __global__ void __launch_bounds__(32) sweep2d_f32_kernel(const Sweep2D32Args A) 
       }
     }
     __syncwarp();
-  }
-}
-
-// FP32 sweep, cooperative form: a CTA of NW warps sweeps the (at most NW) directions of one group,
-// one warp per direction.  The directions of a group share a quadrant, so every warp visits the same
-// cell at the same step; each warp leaves its omega-weighted cell solution in a shared-memory
-// buffer, and every kChunk32 steps the CTA adds the buffer over its warps in warp order and writes
-// one partial per cell and group.  This gives the occupancy of one warp per direction (the FP32
-// wavefront is bound by latency, not by the FP32 pipe, so it needs many warps in flight) with the
-// partial-sum traffic of the wide groups.  The buffer is double-buffered: chunk j is summed right
-// after the barrier that ends it and is overwritten only by chunk j + 2, after the next barrier.
-constexpr int kChunk32 = 4;
-
-__host__ __device__ __forceinline__ size_t cta32_smem_bytes(int nw, int nx, int n_mat) {
-  return sizeof(float4) * 2 * kChunk32 * nw * 32 +           // partial-sum buffer
-         sizeof(float) * ((size_t)nw * ybuf32_floats(nx, 1) + (size_t)n_mat * nw * kTab2D);
-}
-
-template <int NW>
-__global__ void __launch_bounds__(32 * NW, 32 / NW) sweep2d_f32_cta_kernel(const Sweep2D32Args A) {
-  const int g = blockIdx.x, b = blockIdx.y;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (A.active && !A.active[b]) return;   // the same for every thread of the CTA: no barrier skipped
-  const SweepGroup grp = A.groups[g];
-  const bool xneg = grp.quad & 1, yneg = (grp.quad & 2) != 0;
-  const bool live = wid < grp.nd;         // surplus warps only take part in the barriers and sums
-  extern __shared__ float4 smq[];
-  float4* accb = smq;                                                  // [2][kChunk32][NW][32]
-  float* ybuf = reinterpret_cast<float*>(smq + 2 * kChunk32 * NW * 32)
-                + (size_t)wid * ybuf32_floats(A.nx, 1);                // this warp's [nx][2]
-  float* tab_s = reinterpret_cast<float*>(smq + 2 * kChunk32 * NW * 32)
-                 + (size_t)NW * ybuf32_floats(A.nx, 1);                // [n_mat][NW][32]
-  const float* __restrict__ tabg = A.tables + (size_t)b * A.n_mat * A.n_dirs * kTab2D;
-  for (int e = threadIdx.x; e < A.n_mat * NW * kTab2D; e += 32 * NW) {
-    const int m = e / (NW * kTab2D), r = e % (NW * kTab2D), dd = r / kTab2D, k = r % kTab2D;
-    tab_s[e] = dd < grp.nd ? tabg[((size_t)m * A.n_dirs + grp.d0 + dd) * kTab2D + k] : 0.f;
-  }
-  __syncthreads();
-  const float wd = live ? (float)A.dirs[4 * (grp.d0 + wid) + 2] : 0.f;
-  const float s3 = 1.7320508075688772f;
-  const float c3x = xneg ? -s3 : s3, c3y = yneg ? -s3 : s3;
-  const bool src = A.with_source && !(A.inner && A.inner[b]);
-  const float gxb = src ? (float)(A.inflow[4 * b + (xneg ? 1 : 0)] * A.sq_area) : 0.f;
-  const float gyb = src ? (float)(A.inflow[4 * b + (yneg ? 3 : 2)] * A.sq_area) : 0.f;
-  const int H = A.nx < 32 ? A.nx : 32;
-  const int nrb = (A.ny + H - 1) / H;
-  const int total = nrb * A.nx;
-  const int steps = total + H - 1;
-  const int padded = (steps + kChunk32 - 1) / kChunk32 * kChunk32;
-  const float4* __restrict__ Sb = reinterpret_cast<const float4*>(A.S) + (size_t)b * A.n_cells;
-  float4* part = reinterpret_cast<float4*>(A.partial + ((size_t)active_rank(A.active, b) * A.n_groups + g) * A.n_dof);
-  const float4* tab_w = reinterpret_cast<const float4*>(tab_s) + (size_t)wid * (kTab2D / 4);
-  // cell of lane l at wavefront step s_ (false when the lane is idle there); the same for every warp
-  auto cell_at = [&](int s_, int l, int& c_) -> bool {
-    const int u_ = s_ - l;
-    const bool in_ = l < H && u_ >= 0 && u_ < total;
-    const int rb_ = in_ ? u_ / A.nx : 0;
-    const int t_ = in_ ? u_ - rb_ * A.nx : 0;
-    const int r_ = rb_ * H + l;
-    c_ = (yneg ? A.ny - 1 - r_ : r_) * A.nx + (xneg ? A.nx - 1 - t_ : t_);
-    return in_ && r_ < A.ny;
-  };
-  float tx0 = 0.f, tx1 = 0.f, typ0 = 0.f, typ1 = 0.f;
-  int m_next = 0;
-  float4 sv_next = make_float4(0.f, 0.f, 0.f, 0.f);
-  {
-    int c0;
-    if (live && cell_at(0, lane, c0)) m_next = A.mat[c0], sv_next = Sb[c0];
-  }
-  for (int s = 0; s < padded; ++s) {
-    const int q = s % kChunk32;
-    float4* acc_slot = accb + ((size_t)(((s / kChunk32) & 1) * kChunk32 + q) * NW + wid) * 32 + lane;
-    if (live) {
-      const int u = s - lane;
-      const bool inrange = lane < H && u >= 0 && u < total;
-      const int rb = inrange ? u / A.nx : 0;
-      const int t = inrange ? u - rb * A.nx : 0;
-      const int r = rb * H + lane;
-      const bool act = inrange && r < A.ny;
-      const int m = m_next;
-      const float4 sv = sv_next;
-      {
-        int c1;
-        if (cell_at(s + 1, lane, c1)) m_next = A.mat[c1], sv_next = Sb[c1];
-      }
-      float ty0 = __shfl_up_sync(0xffffffffu, typ0, 1);
-      float ty1 = __shfl_up_sync(0xffffffffu, typ1, 1);
-      if (act) {
-        if (r == 0) {
-          ty0 = gyb, ty1 = 0.f;
-        } else if (lane == 0) {
-          ty0 = ybuf[2 * t];
-          ty1 = ybuf[2 * t + 1];
-        }
-        if (t == 0) tx0 = gxb, tx1 = 0.f;
-        const float4* T = tab_w + (size_t)m * NW * (kTab2D / 4);
-        float a[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const float4 mr = T[2 * k], er = T[2 * k + 1];  // M^-1 row k | inflow rows k
-          float v = mr.x * sv.x;
-          v = fmaf(mr.y, sv.y, v);
-          v = fmaf(mr.z, sv.z, v);
-          v = fmaf(mr.w, sv.w, v);
-          v = fmaf(er.x, tx0, v);
-          v = fmaf(er.y, tx1, v);
-          v = fmaf(er.z, ty0, v);
-          v = fmaf(er.w, ty1, v);
-          a[k] = v;
-        }
-        tx0 = fmaf(c3x, a[1], a[0]);
-        tx1 = fmaf(c3x, a[3], a[2]);
-        typ0 = fmaf(c3y, a[2], a[0]);
-        typ1 = fmaf(c3y, a[3], a[1]);
-        *acc_slot = make_float4(wd * a[0], wd * a[1], wd * a[2], wd * a[3]);
-        if (lane == H - 1 && rb + 1 < nrb) {
-          ybuf[2 * t] = typ0;
-          ybuf[2 * t + 1] = typ1;
-        }
-      }
-      __syncwarp();
-    }
-    if (q == kChunk32 - 1) {
-      __syncthreads();
-      // sum the chunk's contributions over the warps, in warp order, one (step, lane) per thread
-      const int s0 = s - (kChunk32 - 1);
-      const float4* chunk = accb + (size_t)((s / kChunk32) & 1) * kChunk32 * NW * 32;
-      for (int i = threadIdx.x; i < kChunk32 * 32; i += 32 * NW) {
-        const int qq = i >> 5, l = i & 31;
-        int c;
-        if (!cell_at(s0 + qq, l, c)) continue;
-        const float4* p = chunk + (size_t)qq * NW * 32 + l;
-        float4 sum = p[0];
-        for (int w2 = 1; w2 < grp.nd; ++w2) {
-          const float4 v = p[(size_t)w2 * 32];
-          sum.x += v.x, sum.y += v.y, sum.z += v.z, sum.w += v.w;
-        }
-        part[c] = sum;
-      }
-    }
   }
 }
 
@@ -1351,26 +1228,13 @@ __global__ void reduce_partials32_kernel(const float* __restrict__ partial,
 template <int DPW>
 static int launch2d_f32(const Sweep2D32Args& A, int B, int n_groups, cudaStream_t st) {
   const size_t bytes =
-      ((size_t)ybuf32_floats(A.nx, DPW) + (size_t)A.n_mat * DPW * kTab2D) * sizeof(float);
+      ((size_t)ybuf32_floats(A.nx, DPW) + (size_t)A.n_mat * tab32_stride(DPW)) * sizeof(float);
   if (bytes > 200 * 1024) return fail(RTE_EINVAL, "FP32 sweep: shared memory exceeded");
   if (bytes > 48 * 1024) {
     RTE_CUDA_TRY(cudaFuncSetAttribute(sweep2d_f32_kernel<DPW>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   }
   sweep2d_f32_kernel<DPW><<<dim3(n_groups, B), 32, bytes, st>>>(A); RTE_NOTE_LAUNCH();
-  RTE_CUDA_TRY(cudaGetLastError());
-  return RTE_OK;
-}
-
-template <int NW>
-static int launch2d_f32_cta(const Sweep2D32Args& A, int B, int n_groups, cudaStream_t st) {
-  const size_t bytes = cta32_smem_bytes(NW, A.nx, A.n_mat);
-  if (bytes > 200 * 1024) return fail(RTE_EINVAL, "FP32 sweep: shared memory exceeded");
-  if (bytes > 48 * 1024) {
-    RTE_CUDA_TRY(cudaFuncSetAttribute(sweep2d_f32_cta_kernel<NW>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  }
-  sweep2d_f32_cta_kernel<NW><<<dim3(n_groups, B), 32 * NW, bytes, st>>>(A); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;
 }
@@ -1389,9 +1253,9 @@ int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, cons
     RTE_TRY(bt->S32.alloc((size_t)bt->B * d->n_dof));
     bt->tables32_stale = true;
   }
-  int dpw = bt->dpw, n_groups = 0, form = 1;
+  int dpw = bt->dpw, n_groups = 0;
   const SweepGroup* gdev = nullptr;
-  pick_groups(bt, n_active, &dpw, &n_groups, &gdev, true, &form);
+  pick_groups(bt, n_active, &dpw, &n_groups, &gdev, true);
   const size_t need32 = bt->partial.n;  // the same group-slice capacity as the FP64 partial sums
   if (bt->partial32.n < need32) RTE_TRY(bt->partial32.alloc(need32));
   if (bt->tables32_stale) {
@@ -1411,23 +1275,13 @@ int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, cons
   Sweep2D32Args A{bt->S32.p,  bt->partial32.p, active,   inner,    bt->tables32.p, bt->inflow.p,
                   d->mat_id.p, d->dir_dev.p,   gdev,     d->nx,          d->ny,
                   d->n_cells, d->n_dof,        d->n_mat, d->n_dirs,      n_groups,
-                  1,          std::sqrt(d->hx * d->hy)};
-  if (form == 1) {   // one warp per direction, the group's warps in one CTA
-    switch (dpw) {
-      case 1: RTE_TRY(launch2d_f32_cta<1>(A, bt->B, n_groups, st)); break;
-      case 2: RTE_TRY(launch2d_f32_cta<2>(A, bt->B, n_groups, st)); break;
-      case 4: RTE_TRY(launch2d_f32_cta<4>(A, bt->B, n_groups, st)); break;
-      case 8: RTE_TRY(launch2d_f32_cta<8>(A, bt->B, n_groups, st)); break;
-      default: return fail(RTE_EINVAL, "unsupported directions-per-warp");
-    }
-  } else {
-    switch (dpw) {
-      case 1: RTE_TRY(launch2d_f32<1>(A, bt->B, n_groups, st)); break;
-      case 2: RTE_TRY(launch2d_f32<2>(A, bt->B, n_groups, st)); break;
-      case 4: RTE_TRY(launch2d_f32<4>(A, bt->B, n_groups, st)); break;
-      case 8: RTE_TRY(launch2d_f32<8>(A, bt->B, n_groups, st)); break;
-      default: return fail(RTE_EINVAL, "unsupported directions-per-warp");
-    }
+                  1,          std::sqrt(d->hx * d->hy), 1.0 / d->hx, 1.0 / d->hy};
+  switch (dpw) {
+    case 1: RTE_TRY(launch2d_f32<1>(A, bt->B, n_groups, st)); break;
+    case 2: RTE_TRY(launch2d_f32<2>(A, bt->B, n_groups, st)); break;
+    case 4: RTE_TRY(launch2d_f32<4>(A, bt->B, n_groups, st)); break;
+    case 8: RTE_TRY(launch2d_f32<8>(A, bt->B, n_groups, st)); break;
+    default: return fail(RTE_EINVAL, "unsupported directions-per-warp");
   }
   if (bt->timing) {
     RTE_CUDA_TRY(cudaEventRecord(ev1, st));
@@ -1495,15 +1349,10 @@ static int autotune(rte_batch_t bt, cudaStream_t st, int* n_entries, int* table)
         return prec == 0 ? sweep_launch(bt, bt->work.p, bt->work.p + nb, nullptr, 1, mask.p, st, true, n)
                          : sweep_launch_f32(bt, bt->work.p, bt->work.p + nb, mask.p, st, n);
       };
-      // FP32: both forms of the kernel unless the batch fixes one (entries dpw | form << 8)
-      const int f_lo = prec == 0 || !bt->f32_form_auto ? bt->f32_form : 0;
-      const int f_hi = prec == 0 || !bt->f32_form_auto ? bt->f32_form : 1;
-      for (int form = f_lo; form <= f_hi && status == RTE_OK; ++form)
       for (int dpw = 1; dpw <= kMaxDirsPerWarp && status == RTE_OK; dpw *= 2) {
         const int k = dpw == 1 ? 0 : dpw == 2 ? 1 : dpw == 4 ? 2 : 3;
         if ((size_t)n * bt->gcount[k] * d->n_dof > bt->partial.n) continue;  // no partial-sum space
         bt->force_dpw = dpw;
-        bt->force_form = prec == 1 ? form : -1;
         float ms = 0.f;
         status = launch();
         if (status == RTE_OK && cudaEventRecord(e0, st) != cudaSuccess) status = fail(RTE_ECUDA, "autotune: event");
@@ -1512,8 +1361,7 @@ static int autotune(rte_batch_t bt, cudaStream_t st, int* n_entries, int* table)
                                  cudaEventSynchronize(e1) != cudaSuccess ||
                                  cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
           status = fail(RTE_ECUDA, "autotune: timing");
-        if (status == RTE_OK && (best == 0 || ms < best_ms))
-          best_ms = ms, best = prec == 1 ? (dpw | form << 8) : dpw;
+        if (status == RTE_OK && (best == 0 || ms < best_ms)) best_ms = ms, best = dpw;
       }
       if (status != RTE_OK) break;
       (prec == 0 ? bt->tuned : bt->tuned32).emplace_back(n, best);
@@ -1521,7 +1369,6 @@ static int autotune(rte_batch_t bt, cudaStream_t st, int* n_entries, int* table)
     if (status != RTE_OK) break;
   }
   bt->force_dpw = 0;
-  bt->force_form = -1;
   bt->timing = timing;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -46,7 +46,6 @@ SIGNATURES = {
     "rte_residual": (_I, [_P, _P, _P, _P, _P, _P]),
     "rte_fma_peak": (_I, [_I, _I, _P, _P]),
     "rte_sweep_f32": (_I, [_P, _P, _P, _P, _P]),
-    "rte_batch_f32_form": (_I, [_P, _I]),
     "rte_change_norm": (_I, [_P, _P, _P, _P, _P]),
     "rte_dsa_correction": (_I, [_P, _P, _P, _D, _I, _P, _P, _P]),
     "rte_correction_source": (_I, [_P, _P, _P, _P, _P]),
@@ -373,11 +372,6 @@ class Batch:
         """rte_sweep_f32: one FP32 sweep with source (2D), result in FP64."""
         check(lib().rte_sweep_f32(self.h, _ptr(rho_in), _ptr(rho_out), _ptr(active),
                                   _stream(stream)))
-
-    def f32_form(self, form):
-        """Form of the FP32 sweep kernel: 0 warp per direction group, 1 warp per direction with a
-        block-wide sum, -1 measured by autotune() (rte_batch_f32_form)."""
-        check(lib().rte_batch_f32_form(self.h, int(form)))
 
     def sweep_static(self, rho_in, rho_out, with_source=True, stream=None):
         """rte_sweep_static: the same sweep with the library's fixed scratch (no allocation)."""

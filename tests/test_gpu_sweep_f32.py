@@ -1,6 +1,5 @@
 """GPU parity of the FP32 sweep of the precision variant (rte_sweep_f32) against the oracle's FP64
-sweep (Eq. (transport_sweep)), through the C ABI, for both forms of the FP32 kernel (one warp per
-group of directions; one warp per direction with a block-wide sum) and every work decomposition.
+sweep (Eq. (transport_sweep)), through the C ABI, for every work decomposition.
 
 Tolerance, derived: the sources and sweep tables are rounded to FP32 (relative u = 2^-24 ~ 6e-8
 each) and each cell solve adds ~10 roundings of a chain of FMAs, so one cell's solution carries
@@ -8,8 +7,8 @@ each) and each cell solve adds ~10 roundings of a chain of FMAs, so one cell's s
 per cell crossed, i.e. <= (n_x + n_y) * 16u along a characteristic (2e-4 for the largest mesh
 here); the partial sums over directions add ~n_dirs u.  Rounding errors of independent cells
 largely cancel, so the test bounds the error by 3e-5 ||rho*||_inf, well inside the worst case.  The
-two forms add the same FP32 terms in different groupings, so they agree to the same bound; each is
-deterministic (bit-identical on a second call)."""
+decompositions add the same FP32 terms in different groupings, so they agree to the same bound;
+each is deterministic (bit-identical on a second call)."""
 import numpy as np
 import pytest
 
@@ -37,7 +36,7 @@ def _rte():
 
 
 @pytest.mark.parametrize("nx,ny,nphi,nvz", CASES)
-def test_fp32_sweep_matches_oracle_every_form_and_decomposition(nx, ny, nphi, nvz):
+def test_fp32_sweep_matches_oracle_every_decomposition(nx, ny, nphi, nvz):
     rte = _rte()
     p = inputs.random_2d(nx, nphi, nvz, 3, seed=nx + ny, B=3, inflow=(0.4, 1.1, 0.0, 0.6), ny=ny)
     rho = np.random.default_rng(nx).uniform(0.0, 1.0, (3, p.n_dof))
@@ -46,28 +45,26 @@ def test_fp32_sweep_matches_oracle_every_form_and_decomposition(nx, ny, nphi, nv
     batch = rte.Batch.from_problem(p)
     rin = torch.tensor(rho, device="cuda")
     outs = {}
-    for form in (0, 1):
-        batch.f32_form(form)
-        for dpw in (1, 2, 4, 8):
-            batch.tune(dpw)
-            out = torch.full_like(rin, float("nan"))
-            batch.sweep_f32(rin, out)
-            again = torch.full_like(rin, float("nan"))
-            batch.sweep_f32(rin, again)
-            torch.cuda.synchronize()
-            assert torch.equal(out, again), (form, dpw)
-            got = out.cpu().numpy()
-            err = np.abs(got - ref).max() / scale
-            assert err < TOL32, (form, dpw, err)
-            outs[(form, dpw)] = got
-    base = outs[(0, 1)]
+    for dpw in (1, 2, 4, 8):
+        batch.tune(dpw)
+        out = torch.full_like(rin, float("nan"))
+        batch.sweep_f32(rin, out)
+        again = torch.full_like(rin, float("nan"))
+        batch.sweep_f32(rin, again)
+        torch.cuda.synchronize()
+        assert torch.equal(out, again), dpw
+        got = out.cpu().numpy()
+        err = np.abs(got - ref).max() / scale
+        assert err < TOL32, (dpw, err)
+        outs[dpw] = got
+    base = outs[1]
     for k, v in outs.items():
         assert np.abs(v - base).max() / scale < TOL32, k
 
 
-def test_fp32_sweep_masked_instances_untouched_and_autotuned_forms():
+def test_fp32_sweep_masked_instances_untouched_and_autotuned():
     """The active mask leaves skipped instances' outputs untouched; after the autotuner has chosen a
-    form per running count, the FP32 sweep still matches the oracle."""
+    decomposition per running count, the FP32 sweep still matches the oracle."""
     rte = _rte()
     p = inputs.lattice_test(48, 32, 4)
     rho = np.random.default_rng(5).uniform(0.0, 1.0, (4, p.n_dof))
