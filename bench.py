@@ -38,10 +38,10 @@ FLOP_PER_CELL_DIR = 64
 BYTES_PER_CELL_SWEEP = 76   # rho_in 32 B + G0 8 B + material id 4 B + rho_out 32 B
 # DRAM bytes per sweep launch from the committed ncu capture, valid only for the 2D sweep
 # kernels' device code it was taken with (sha1 of that part of sweep.cu, sweep_source_sha1)
-NCU_TRAFFIC = {"sha1": "43f50fcc7cc28c1bd6f29d15beb2de4541d29128", "bytes_per_launch": 665419989,
+NCU_TRAFFIC = {"sha1": "9f7572895d1ea71c649e97ea9837ba3485344491", "bytes_per_launch": 715564940,
                "batch": 152, "n": 128, "angles": 64,
-               "workload": "lattice128x128_CL(16,4) batch 152, mean of the 12 sweep launches of "
-                           "one ROMSAD step"}
+               "workload": "lattice128x128_CL(16,4) batch 152, mean of the 11 sweep2d_kernel launches "
+                           "of one ROMSAD step"}
 
 
 def sweep_source_sha1():

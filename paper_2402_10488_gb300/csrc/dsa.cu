@@ -1247,7 +1247,11 @@ static int fused_smem_attr(size_t bytes) {
   return RTE_OK;
 }
 
-static int vcycle(rte_batch_t bt, int l, const uint8_t* active, cudaStream_t st, int nu) {
+// first_done: level l's x holds the first half sweep of pre-smoothing from x = 0 already (colour 0
+// cells set, colour 1 cells stale; pack_first_half_kernel), so the cycle neither clears x nor repeats
+// that half sweep.  Only with the one-launch-per-half-sweep smoother forms.
+static int vcycle(rte_batch_t bt, int l, const uint8_t* active, cudaStream_t st, int nu,
+                  bool first_done = false) {
   DsaState* s = bt->dsa;
   const int B = bt->B;
   if (l >= s->lc) {  // the rest of the cycle in one launch, one CTA per instance
@@ -1261,7 +1265,7 @@ static int vcycle(rte_batch_t bt, int l, const uint8_t* active, cudaStream_t st,
   // the blocked smoother writes the level's residual buffer and then swaps it with x, so every
   // LevelC is re-read after a step that may have swapped them
   LevelC L = lvl_of(bt, l);
-  RTE_CUDA_TRY(cudaMemsetAsync(L.x, 0, sizeof(float) * (size_t)B * L.nc * NB, st));
+  if (!first_done) RTE_CUDA_TRY(cudaMemsetAsync(L.x, 0, sizeof(float) * (size_t)B * L.nc * NB, st));
   const int ncol = ((L.nx + 1) / 2) * L.ny;
   const dim3 gcol((ncol + 127) / 128, B);
   const dim3 gtile((L.nx + kTT - 1) / kTT, (L.ny + kTT - 1) / kTT, B);
@@ -1294,7 +1298,16 @@ static int vcycle(rte_batch_t bt, int l, const uint8_t* active, cudaStream_t st,
     }
     return RTE_OK;
   };
-  RTE_TRY(smooth_nu(0, nullptr));
+  if (first_done) {   // the rest of the first sweep (colour 1), then nu - 1 full sweeps
+    if (bt->dsa_tiled) {
+      rbgs_tiled_kernel<<<gtile, 128, 0, st>>>(L, s->K, 1, active); RTE_NOTE_LAUNCH();
+    } else {
+      rbgs_kernel<<<gcol, 128, 0, st>>>(L, s->K, 1, active); RTE_NOTE_LAUNCH();
+    }
+    for (int k = 1; k < nu; ++k) smooth(0);
+  } else {
+    RTE_TRY(smooth_nu(0, nullptr));
+  }
   residual_kernel<<<dim3((L.nc + 127) / 128, B), 128, 0, st>>>(L, s->K, active); RTE_NOTE_LAUNCH();
   LevelC Cl = lvl_of(bt, l + 1);
   restrict_kernel<<<dim3((Cl.nc * NB + 255) / 256, B), 256, 0, st>>>(L, Cl, active); RTE_NOTE_LAUNCH();
@@ -1316,6 +1329,37 @@ __global__ void pack_rhs32_kernel(const double* R, float* v, int nc, const uint8
   if (t >= nc * NB) return;
   const int c = t / NB, k = t % NB;
   v[(size_t)b * nc * NB + t] = k < 4 ? (float)R[(size_t)b * nc * 4 + 4 * c + k] : 0.f;
+}
+
+// The right-hand side R (FP64, 4 moments per cell) packed into level 0's b (the delta-rho block; the
+// current blocks are zero) together with the first half sweep of pre-smoothing from x = 0: every
+// neighbour of a cell of colour 0 is then zero, so that half sweep sets x_c = D_c^-1 b_c -- the
+// same operations, in the same order, as rbgs_cell with zero neighbours, bit for bit.  The cells of
+// colour 1 are left as they are: the next half sweep overwrites them without reading them.  Saves
+// the separate pass that cleared x and one half sweep's neighbour reads.
+__global__ void pack_first_half_kernel(LevelC L, const double* __restrict__ R, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  __shared__ float4 dsh4[kSmemClasses * NB2 / 4];
+  const float* dg = L.dinv + (size_t)b * L.n_class * NB2;
+  const bool dsm = L.n_class <= kSmemClasses;
+  if (dsm) {
+    for (int t = threadIdx.x; t < L.n_class * NB2 / 4; t += blockDim.x)
+      dsh4[t] = reinterpret_cast<const float4*>(dg)[t];
+    __syncthreads();
+  }
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.nc) return;
+  const double* rc = R + ((size_t)b * L.nc + c) * 4;
+  float v[NB];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) v[k] = k < 4 ? (float)rc[k] : 0.f;
+  store12(L.b + ((size_t)b * L.nc + c) * NB, v);
+  const int i = c % L.nx, j = c / L.nx;
+  if (((i + j) & 1) != 0) return;
+  float out[NB];
+  matvec12((dsm ? reinterpret_cast<const float*>(dsh4) : dg) + (size_t)L.cls[c] * NB2, v, out);
+  store12(L.x + ((size_t)b * L.nc + c) * NB, out);
 }
 
 __global__ void add32_kernel(const float* x, float* y, int per, const uint8_t* active) {
@@ -1353,9 +1397,15 @@ static int dsa2d_vcycles(rte_batch_t bt, const double* R, double* drho, int k,
   const int B = bt->B, nc = bt->disc->n_cells, per = nc * NB;
   const dim3 gv((per + 255) / 256, B), gvc(std::min((per + 255) / 256, 1024), B);
   if (k == 1) {
-    // one cycle: pack the right-hand side straight into level 0 and read the result from there
-    pack_rhs32_kernel<<<gv, 256, 0, st>>>(R, s->bl[0]->p, nc, active); RTE_NOTE_LAUNCH();
-    RTE_TRY(vcycle(bt, 0, active, st, bt->dsa_nu));
+    // one cycle: pack the right-hand side straight into level 0 and read the result from there; with
+    // a one-launch-per-half-sweep smoother the packing also does the first half sweep
+    const bool fuse = !bt->dsa_blocking && s->lc > 0;
+    if (fuse) {
+      pack_first_half_kernel<<<dim3((nc + 127) / 128, B), 128, 0, st>>>(lvl_of(bt, 0), R, active); RTE_NOTE_LAUNCH();
+    } else {
+      pack_rhs32_kernel<<<gv, 256, 0, st>>>(R, s->bl[0]->p, nc, active); RTE_NOTE_LAUNCH();
+    }
+    RTE_TRY(vcycle(bt, 0, active, st, bt->dsa_nu, fuse));
     extract_rho32_kernel<<<dim3((nc * 4 + 255) / 256, B), 256, 0, st>>>(s->xl[0]->p, drho, nc, active); RTE_NOTE_LAUNCH();
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
