@@ -104,6 +104,10 @@ def parse():
                          "instances over 12 (mesh, angles) buckets solved together; serving: a "
                          "Poisson request stream over 20 buckets through the serving loop")
     ap.add_argument("--instances", type=int, default=256, help="mixed: instances per step per GPU")
+    ap.add_argument("--mixed-exec", default="streams", choices=["lockstep", "streams"],
+                    help="mixed: FP64 methods iterate all buckets in lockstep with one sweep launch "
+                         "per iteration (rte_solve_lockstep), or each bucket on its own stream "
+                         "(rte_solve_many); the precision variants always use the streams")
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the stream")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean arrivals per second")
     ap.add_argument("--mem-gb", type=float, default=96.0,
@@ -560,8 +564,11 @@ def run_mixed(a, ws, rank, local):
         oo = [opts_for(method, k) for k in B]
         reps, st = rte.solve_many([k["batch"] for k in B], [k["rho"] for k in B],
                                   [o for o, _ in oo], roms=[r for _, r in oo],
-                                  streams=[k["stream"] for k in B])
+                                  streams=[k["stream"] for k in B], lockstep=lockstep(method))
         return reps
+
+    def lockstep(method):
+        return a.mixed_exec == "lockstep" and method in ("romsad", "si_dsa")
 
     methods = [m for m in a.methods.split(",")
                if m in ("romsad", "si_dsa", "romsad_mixed", "romsad_refine")]
@@ -592,7 +599,8 @@ def run_mixed(a, ws, rank, local):
                               np.abs(refs[i]).max(1) for i, k in enumerate(B)])
         ns = np.concatenate([[x["n_sweep"] for x in rr] for rr in reps])
         ms = float(np.mean(times))
-        results[m] = dict(ms_per_step=ms, solves_ok=int(np.sum(err <= 1e-6)),
+        results[m] = dict(exec="lockstep" if lockstep(m) else "streams",
+                          ms_per_step=ms, solves_ok=int(np.sum(err <= 1e-6)),
                           solves_per_s=float(np.sum(err <= 1e-6)) / (ms / 1e3),
                           err_max=float(err.max()), n_sweep_mean=float(ns.mean()),
                           launches_per_step=n_launch / a.steps,
@@ -615,7 +623,10 @@ def run_mixed(a, ws, rank, local):
                    "global_batch": a.instances * ws, "n_train": a.ntrain, "rank": a.rank,
                    "stop": f"relative change < {eps:g}", "error_target": 1e-6,
                    "l2": "256 MB buffer written between timed steps",
-                   "execution": "rte_solve_many: one stream per bucket, event-driven relaunch",
+                   "execution": ("FP64 methods: rte_solve_lockstep, one work-queue sweep launch over "
+                                 "every bucket per iteration; precision variants: rte_solve_many, one "
+                                 "stream per bucket" if a.mixed_exec == "lockstep" else
+                                 "rte_solve_many: one stream per bucket, event-driven relaunch"),
                    "parallelism": "instances sharded across ranks, no collective"},
         "roofline": {"bound": "alu", "kernel": "sweep2d_kernel (FP64 DFMA), whole step",
                      "achieved": head["sweep_tflops_whole_step"], "peak": peaks["fp64"],

@@ -516,6 +516,20 @@ int rte_solve_many(int n, const rte_batch_t* batches, const rte_solve_opts* opts
                    const rte_rom_t* roms, double* const* rho, rte_solve_report* const* reports,
                    void* const* streams);
 
+/* rte_solve_many with the batches iterating in lockstep, for mixed-size workloads: at every iteration
+ * ONE sweep launch covers the running instances of all batches -- a persistent grid of warps taking
+ * (batch, instance, direction group) work items from a shared counter, longest sweeps first -- so
+ * that instances of every mesh and quadrature size fill the GPU together and the launch's tail is
+ * short; then each batch's stop test and corrections (Alg. 1 / Alg. 2) run on its own stream, and
+ * the next sweep waits for them all.  Every batch sweeps 4 directions per warp (8 where its partial
+ * sums need wider groups); with the same decomposition (rte_batch_tune) the results equal
+ * rte_solve_many's bit for bit.  The sweeps run on the first batch's stream.  Arguments as in
+ * rte_solve_many; 2D batches and FP64 sweeps only (no fp32_switch / refine_kappa).  Synchronous.
+ * Errors: RTE_EINVAL, RTE_ENOCONV (some instance hit its cap), RTE_ECUDA. */
+int rte_solve_lockstep(int n, const rte_batch_t* batches, const rte_solve_opts* opts,
+                       const rte_rom_t* roms, double* const* rho, rte_solve_report* const* reports,
+                       void* const* streams);
+
 /* ---- serving: continuous batching of parametric solves ---------------------------------- */
 
 typedef struct rte_server_s* rte_server_t;

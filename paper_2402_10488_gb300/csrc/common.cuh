@@ -244,6 +244,46 @@ int sweep_launch(rte_batch_t b, const double* rho_in, double* rho_out, double* p
                  int with_source, const uint8_t* active, cudaStream_t st, bool fuse_norms,
                  int n_active = -1, bool zero_norms = true);
 int norms_to_host(rte_batch_t b, double* host, cudaStream_t st);
+// Arguments of the 2D FP64 sweep kernels (sweep.cu): one batch's arrays and sizes for one launch.
+struct Sweep2DArgs {
+  const double* rho_in;     // or, when the kernel is instantiated with PRESRC, the sources S
+  double* partial;
+  double* psi_out;
+  const uint8_t* active;
+  const double* tables;
+  const double* sigma_s;
+  const double* G0;
+  const double* inflow;
+  const int32_t* mat;
+  const double* dirs;
+  const SweepGroup* groups;
+  int nx, ny, n_cells, n_dof, n_mat, n_dirs, n_groups, with_source;
+  double sq_area;
+  double ihx, ihy;          // 1 / h_x, 1 / h_y
+  // balance accounting (kernels instantiated with LEAK only): per (running instance, group, cell)
+  // the omega-weighted net outflow through the cell's faces; lx = sqrt(h_y / h_x) and
+  // ly = sqrt(h_x / h_y) turn a face trace's zeroth coefficient into the face integral
+  double* leak = nullptr;
+  double lx = 0.0, ly = 0.0;
+};
+
+// A work item of the multi-batch sweep: one direction group of one instance of one batch.
+struct SweepItem {
+  int batch, group, inst, pad;
+};
+
+// one FP64 sweep of several 2D batches in one work-queue launch (sweep.cu)
+struct MultiSweepScratch {
+  DevBuf<Sweep2DArgs> descs;
+  DevBuf<SweepItem> items;
+  DevBuf<int> counter;
+  std::vector<Sweep2DArgs> h_descs;
+  std::vector<SweepItem> h_items;
+};
+int sweep_launch_multi(const std::vector<rte_batch_t>& bts, const std::vector<const double*>& rho_in,
+                       const std::vector<double*>& rho_out, const std::vector<const uint8_t*>& act,
+                       const std::vector<const uint8_t*>& host_act, MultiSweepScratch& ws,
+                       cudaStream_t st);
 // FP32 sweep; the instances flagged in `inner` sweep the error rho_in - x0 without sources and
 // get y0 added in the reduction (the correction sweeps of the FP64 outer residual correction)
 int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, const uint8_t* active,

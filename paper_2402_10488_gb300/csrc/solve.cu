@@ -454,3 +454,107 @@ extern "C" int rte_solve_many(int n, const rte_batch_t* batches, const rte_solve
   }
   return status;
 }
+
+// rte_solve_many with every batch iterating in lockstep: at each iteration one sweep launch covers
+// the running instances of all batches (sweep_launch_multi: a work queue over (batch, instance,
+// direction group), longest first), so that instances of any size fill the GPU together; then each
+// batch's stop test and corrections run on its own stream, and the next sweep waits for all of
+// them.  FP64 sweeps (no precision variant) and 2D batches only.
+extern "C" int rte_solve_lockstep(int n, const rte_batch_t* batches, const rte_solve_opts* opts,
+                                  const rte_rom_t* roms, double* const* rho,
+                                  rte_solve_report* const* reports, void* const* streams) {
+  if (n < 1 || !batches || !opts || !rho) return fail(RTE_EINVAL, "rte_solve_lockstep: null argument");
+  for (int k = 0; k < n; ++k) {
+    if (!batches[k] || !rho[k]) return fail(RTE_EINVAL, "rte_solve_lockstep: null batch or rho");
+    if (batches[k]->disc->device != batches[0]->disc->device)
+      return fail(RTE_EINVAL, "rte_solve_lockstep: batches on different devices");
+    if (batches[k]->disc->dim != 2) return fail(RTE_EINVAL, "rte_solve_lockstep: 2D batches only");
+    if (opts[k].fp32_switch > 0.0 || opts[k].refine_kappa > 0.0)
+      return fail(RTE_EINVAL, "rte_solve_lockstep: FP64 sweeps only (no precision variant)");
+    for (int j = 0; j < k; ++j) {
+      if (batches[j] == batches[k]) return fail(RTE_EINVAL, "rte_solve_lockstep: batch listed twice");
+      if (roms && roms[k] && roms[j] == roms[k])
+        return fail(RTE_EINVAL, "rte_solve_lockstep: a ROM serves one batch at a time");
+    }
+    RTE_TRY(check_opts(batches[k], &opts[k], roms ? roms[k] : nullptr));
+  }
+  DeviceGuard g(batches[0]->disc->device);
+  std::vector<SiState> S(n);
+  std::vector<cudaStream_t> st(n);
+  std::vector<cudaEvent_t> done(n, nullptr);
+  struct EvGuard {
+    std::vector<cudaEvent_t>& e;
+    ~EvGuard() {
+      for (auto x : e)
+        if (x) cudaEventDestroy(x);
+    }
+  } evg{done};
+  for (int k = 0; k < n; ++k) {
+    rte_batch_t bt = batches[k];
+    rte_rom_t rom = roms ? roms[k] : nullptr;
+    st[k] = streams ? (cudaStream_t)streams[k] : nullptr;
+    RTE_CUDA_TRY(cudaEventCreateWithFlags(&done[k], cudaEventDisableTiming));
+    RTE_TRY(S[k].init(bt, opts[k], rom, rho[k]));
+    RTE_CUDA_TRY(cudaMemcpyAsync(bt->work.p, rho[k], sizeof(double) * bt->B * bt->disc->n_dof,
+                                 cudaMemcpyDeviceToDevice, st[k]));
+    for (int b = 0; b < bt->B; ++b) S[k].begin(b, opts[k].eps);
+    if (rom) RTE_TRY(rom_prepare(rom, bt, st[k]));
+    RTE_CUDA_TRY(cudaEventRecord(done[k], st[k]));
+  }
+  // the sweeps run on the first batch's stream, after every batch's set-up and corrections
+  cudaStream_t s0 = st[0];
+  MultiSweepScratch ws;
+  for (;;) {
+    std::vector<int> run;
+    for (int k = 0; k < n; ++k)
+      if (S[k].n_active() > 0) run.push_back(k);
+    if (run.empty()) break;
+    std::vector<rte_batch_t> bts;
+    std::vector<const double*> rin;
+    std::vector<double*> rout;
+    std::vector<const uint8_t*> act, hact;
+    for (int k : run) {
+      SiState& s = S[k];
+      rte_batch_t bt = batches[k];
+      const size_t nb = (size_t)bt->B * bt->disc->n_dof;
+      RTE_CUDA_TRY(cudaStreamWaitEvent(s0, done[k], 0));
+      for (int b = 0; b < s.B; ++b) {
+        s.swept[b] = s.act[b];
+        s.hm[b] = s.act[b];
+      }
+      RTE_CUDA_TRY(cudaMemcpyAsync(s.dm.p, s.hm, (size_t)s.B, cudaMemcpyHostToDevice, s0));
+      bts.push_back(bt);
+      rin.push_back(bt->work.p);
+      rout.push_back(bt->work.p + nb);
+      act.push_back(s.dm.p);
+      hact.push_back(s.hm);
+    }
+    RTE_TRY(sweep_launch_multi(bts, rin, rout, act, hact, ws, s0));
+    for (int k : run) {
+      SiState& s = S[k];
+      RTE_CUDA_TRY(cudaMemcpyAsync(s.hn, batches[k]->norms.p, sizeof(unsigned long long) * 2 * s.B,
+                                   cudaMemcpyDeviceToHost, s0));
+      RTE_CUDA_TRY(cudaEventRecord(s.ev, s0));
+      s.in_flight = true;
+    }
+    for (int k : run) {
+      RTE_TRY(si_finish(S[k], st[k], nullptr));
+      RTE_CUDA_TRY(cudaEventRecord(done[k], st[k]));
+    }
+  }
+  int status = RTE_OK;
+  for (int k = 0; k < n; ++k) {
+    if (opts[k].verify) RTE_TRY(verify_results(S[k], st[k]));
+    RTE_CUDA_TRY(cudaStreamSynchronize(st[k]));
+    if (roms && roms[k] && opts[k].rom_bf16) {
+      int tc = 0;
+      RTE_TRY(rom_tc_status(roms[k], &tc));
+      if (tc) return fail(RTE_ETIMEOUT, "BF16 ROM product: a device-side wait gave up");
+    }
+    for (int b = 0; b < S[k].B; ++b) {
+      if (S[k].status[b] != RTE_OK) status = S[k].status[b];
+      if (reports && reports[k]) reports[k][b] = S[k].rep[b];
+    }
+  }
+  return status;
+}

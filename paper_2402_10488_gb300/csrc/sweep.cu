@@ -160,36 +160,17 @@ __global__ void tables1d_kernel(double* tables, const double* sigma_t, const dou
   T[7] = 0.0;
 }
 
-struct Sweep2DArgs {
-  const double* rho_in;     // or, when the kernel is instantiated with PRESRC, the sources S
-  double* partial;
-  double* psi_out;
-  const uint8_t* active;
-  const double* tables;
-  const double* sigma_s;
-  const double* G0;
-  const double* inflow;
-  const int32_t* mat;
-  const double* dirs;
-  const SweepGroup* groups;
-  int nx, ny, n_cells, n_dof, n_mat, n_dirs, n_groups, with_source;
-  double sq_area;
-  double ihx, ihy;          // 1 / h_x, 1 / h_y
-  // balance accounting (kernels instantiated with LEAK only): per (running instance, group, cell)
-  // the omega-weighted net outflow through the cell's faces; lx = sqrt(h_y / h_x) and
-  // ly = sqrt(h_x / h_y) turn a face trace's zeroth coefficient into the face integral
-  double* leak = nullptr;
-  double lx = 0.0, ly = 0.0;
-};
 
 // With LEAK the kernel also records, per cell, sum over its directions of
 //     omega_j ( |v_x| int_{x-outflow face} f - |v_x| int_{x-inflow face} f + the same along y ),
 // the net upwind outflow that enters the cell's particle balance (the DG equation tested with the
 // cell's indicator function): with t the face traces above, int_face f = t[0] sqrt(h_face / h_n),
 // h_n the cell's extent normal to the face.
-template <int DPW, bool SMEM_TAB, bool PRESRC = false, bool LEAK = false>
-__global__ void __launch_bounds__(32) sweep2d_kernel(const Sweep2DArgs A) {
-  const int g = blockIdx.x, b = blockIdx.y, lane = threadIdx.x;
+// One warp sweeps direction group g of instance b (the body of sweep2d_kernel and of the
+// work-queue sweep over several batches, sweep2d_multi_kernel).
+template <int DPW, bool SMEM_TAB, bool PRESRC, bool LEAK>
+__device__ __forceinline__ void sweep2d_warp(const Sweep2DArgs& A, int g, int b) {
+  const int lane = threadIdx.x & 31;
   if (A.active && !A.active[b]) return;
   const SweepGroup grp = A.groups[g];
   const bool xneg = grp.quad & 1, yneg = (grp.quad & 2) != 0;
@@ -320,6 +301,34 @@ __global__ void __launch_bounds__(32) sweep2d_kernel(const Sweep2DArgs A) {
       }
     }
     __syncwarp();
+  }
+}
+
+template <int DPW, bool SMEM_TAB, bool PRESRC = false, bool LEAK = false>
+__global__ void __launch_bounds__(32) sweep2d_kernel(const Sweep2DArgs A) {
+  sweep2d_warp<DPW, SMEM_TAB, PRESRC, LEAK>(A, blockIdx.x, blockIdx.y);
+}
+
+// One sweep of several batches (different meshes and quadratures) in one launch: a persistent grid
+// of one-warp blocks takes work items (batch, instance, direction group) from a shared counter in
+// the order of the list -- longest sweeps first, so that the launch's tail is short -- and sweeps
+// each with the batch's own arguments.  Every item writes only its own partial sums, so the result
+// does not depend on which warp took which item.  The shared memory is sized for the largest batch.
+
+template <int DPW>
+__global__ void __launch_bounds__(32) sweep2d_multi_kernel(const Sweep2DArgs* __restrict__ descs,
+                                                           const SweepItem* __restrict__ items,
+                                                           int n_items, int* counter) {
+  const int lane = threadIdx.x;
+  for (;;) {
+    int i = 0;
+    if (lane == 0) i = atomicAdd(counter, 1);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    if (i >= n_items) return;
+    const SweepItem it = items[i];
+    const Sweep2DArgs A = descs[it.batch];
+    sweep2d_warp<DPW, true, true, false>(A, it.group, it.inst);
+    __syncwarp();   // the next item restages the shared memory
   }
 }
 
@@ -814,6 +823,95 @@ int sweep_launch(rte_batch_t bt, const double* rho_in, double* rho_out, double* 
   reduce_partials_kernel<<<grid, th, 0, st>>>(bt->partial.p, rho_in, rho_out,
                                              fuse_norms ? bt->norms.p : nullptr, active, n_groups,
                                              d->n_dof); RTE_NOTE_LAUNCH();
+  RTE_CUDA_TRY(cudaGetLastError());
+  return RTE_OK;
+}
+
+// One FP64 sweep with source of the running instances of several 2D batches, in one launch of
+// sweep2d_multi_kernel (see there), each batch's cell sources and partial-sum reduction (with the
+// stop-test norms) launched per batch around it, all on `st`.  host_act[k]: batch k's running
+// instances (host copy of its device mask act[k]).  Every batch sweeps DPW directions per warp,
+// DPW = 4 or, when a batch's partial sums need wider groups, 8.  `ws` is scratch the call owns:
+// descriptors, work list and counter.
+int sweep_launch_multi(const std::vector<rte_batch_t>& bts, const std::vector<const double*>& rho_in,
+                       const std::vector<double*>& rho_out, const std::vector<const uint8_t*>& act,
+                       const std::vector<const uint8_t*>& host_act, MultiSweepScratch& ws,
+                       cudaStream_t st) {
+  const int n = (int)bts.size();
+  int dpw = 4;
+  for (rte_batch_t bt : bts) dpw = std::max(dpw, bt->min_dpw);
+  const int k = dpw == 4 ? 2 : 3;
+  std::vector<Sweep2DArgs> descs(n);
+  std::vector<std::pair<long long, SweepItem>> work;
+  size_t smem = 0;
+  for (int q = 0; q < n; ++q) {
+    rte_batch_t bt = bts[q];
+    const rte_disc_s* d = bt->disc;
+    if (d->dim != 2) return fail(RTE_EINVAL, "multi-batch sweep: 2D batches only");
+    int n_act = 0;
+    for (int b = 0; b < bt->B; ++b) n_act += host_act[q][b] != 0;
+    if ((size_t)n_act * bt->gcount[k] * d->n_dof > bt->partial.n)
+      return fail(RTE_EINVAL, "multi-batch sweep: partial sums do not fit");
+    cell_source_kernel<<<dim3((d->n_cells + 127) / 128, bt->B), 128, 0, st>>>(
+        rho_in[q], bt->S.p, bt->sigma_s.p, bt->G0.p, d->mat_id.p, act[q], d->n_cells, d->n_mat, 1); RTE_NOTE_LAUNCH();
+    descs[q] = Sweep2DArgs{bt->S.p,      bt->partial.p, nullptr,      act[q],      bt->tables.p,
+                           bt->sigma_s.p, bt->G0.p,     bt->inflow.p, d->mat_id.p, d->dir_dev.p,
+                           bt->groups_all_dev.p + bt->goff[k], d->nx, d->ny, d->n_cells, d->n_dof,
+                           d->n_mat,     d->n_dirs,     bt->gcount[k], 1,       std::sqrt(d->hx * d->hy),
+                           1.0 / d->hx,  1.0 / d->hy};
+    const int H = d->nx < 32 ? d->nx : 32;
+    const long long steps = (long long)((d->ny + H - 1) / H) * d->nx + H - 1;
+    for (int b = 0; b < bt->B; ++b)
+      if (host_act[q][b])
+        for (int g = 0; g < bt->gcount[k]; ++g) work.push_back({steps, SweepItem{q, g, b, 0}});
+    smem = std::max(smem, ((size_t)d->nx * dpw * 2 + (size_t)d->n_mat * dpw * kTab2D + d->n_mat) *
+                              sizeof(double));
+    if (bt->timing) bt->sweep_units += (double)n_act * d->n_cells * d->n_dirs;
+  }
+  RTE_CUDA_TRY(cudaGetLastError());
+  // longest sweeps first; ties keep the batch / instance / group order
+  std::stable_sort(work.begin(), work.end(),
+                   [](const auto& a, const auto& b) { return a.first > b.first; });
+  const int n_items = (int)work.size();
+  if (n_items > 0) {
+    if (ws.descs.n < (size_t)n) RTE_TRY(ws.descs.alloc(n));
+    if (ws.items.n < (size_t)n_items) RTE_TRY(ws.items.alloc(n_items));
+    if (!ws.counter.p) RTE_TRY(ws.counter.alloc(1));
+    ws.h_items.resize(n_items);
+    for (int i = 0; i < n_items; ++i) ws.h_items[i] = work[i].second;
+    ws.h_descs = descs;
+    RTE_CUDA_TRY(cudaMemcpyAsync(ws.descs.p, ws.h_descs.data(), sizeof(Sweep2DArgs) * n,
+                                 cudaMemcpyHostToDevice, st));
+    RTE_CUDA_TRY(cudaMemcpyAsync(ws.items.p, ws.h_items.data(), sizeof(SweepItem) * n_items,
+                                 cudaMemcpyHostToDevice, st));
+    RTE_CUDA_TRY(cudaMemsetAsync(ws.counter.p, 0, sizeof(int), st));
+    if (smem > 200 * 1024) return fail(RTE_EINVAL, "multi-batch sweep: shared memory exceeded");
+    int n_sm = 0, dev = 0;
+    RTE_CUDA_TRY(cudaGetDevice(&dev));
+    RTE_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = std::min(n_items, 16 * n_sm);   // a persistent grid: warps take items in turn
+    if (dpw == 4) {
+      if (smem > 48 * 1024)
+        RTE_CUDA_TRY(cudaFuncSetAttribute(sweep2d_multi_kernel<4>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      sweep2d_multi_kernel<4><<<grid, 32, smem, st>>>(ws.descs.p, ws.items.p, n_items, ws.counter.p); RTE_NOTE_LAUNCH();
+    } else {
+      if (smem > 48 * 1024)
+        RTE_CUDA_TRY(cudaFuncSetAttribute(sweep2d_multi_kernel<8>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      sweep2d_multi_kernel<8><<<grid, 32, smem, st>>>(ws.descs.p, ws.items.p, n_items, ws.counter.p); RTE_NOTE_LAUNCH();
+    }
+    RTE_CUDA_TRY(cudaGetLastError());
+  }
+  const int th = 256;
+  for (int q = 0; q < n; ++q) {
+    rte_batch_t bt = bts[q];
+    const rte_disc_s* d = bt->disc;
+    RTE_CUDA_TRY(cudaMemsetAsync(bt->norms.p, 0, sizeof(unsigned long long) * 2 * bt->B, st));
+    dim3 grid((d->n_dof / 2 + th - 1) / th, bt->B);
+    reduce_partials_kernel<<<grid, th, 0, st>>>(bt->partial.p, rho_in[q], rho_out[q], bt->norms.p,
+                                               act[q], bt->gcount[k], d->n_dof); RTE_NOTE_LAUNCH();
+  }
   RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;
 }

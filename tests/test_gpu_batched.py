@@ -105,6 +105,48 @@ def test_solve_many_matches_each_batch_alone():
         assert all(x["converged"] for x in reps[k])
 
 
+def test_lockstep_equals_solve_many_and_the_direct_solve():
+    """rte_solve_lockstep (one sweep launch over every running instance of all three discretisations
+    per iteration, as a work queue) returns bit for bit what rte_solve_many returns when both use
+    the same sweep decomposition (4 directions per warp), with the same sweep counts; the tightly
+    converged results agree with the oracle's direct solve of (I - L) rho = b-bar."""
+    rte = _rte()
+    probs = _buckets()
+    opts = [rte.solve_opts(1e-12, rte.SA_DSA, rel=True, max_iter=300, dsa_rtol=0.0, dsa_max_it=1)
+            for _ in probs]
+    out = {}
+    for lock in (False, True):
+        batches = [rte.Batch.from_problem(p) for p in probs]
+        for b in batches:
+            b.tune(4)
+        rhos = [torch.zeros((p.batch, p.n_dof), dtype=torch.float64, device="cuda") for p in probs]
+        streams = [torch.cuda.Stream() for _ in probs]
+        torch.cuda.synchronize()
+        reps, st = rte.solve_many(batches, rhos, opts, streams=streams, lockstep=lock)
+        torch.cuda.synchronize()
+        assert st == rte.RTE_OK and all(x["converged"] for rr in reps for x in rr)
+        out[lock] = ([r.cpu().numpy() for r in rhos], [[x["n_sweep"] for x in rr] for rr in reps])
+    for k in range(len(probs)):
+        assert np.array_equal(out[True][0][k], out[False][0][k]), k
+        assert out[True][1][k] == out[False][1][k], k
+    p = probs[2]
+    for b in range(p.batch):
+        exact = Transport(p, b).solve_rho_direct()
+        assert _rel(out[True][0][2][b], exact) < 1e-9
+
+
+def test_lockstep_rejects_the_precision_variant():
+    rte = _rte()
+    p = inputs.lattice_test(12, 8, 2, n_vz=2)
+    b = rte.Batch.from_problem(p)
+    rho = torch.zeros((2, p.n_dof), dtype=torch.float64, device="cuda")
+    o = rte.solve_opts(1e-8, rte.SA_DSA, rel=True, max_iter=100, dsa_rtol=0.0, dsa_max_it=1,
+                       fp32_switch=1e-4)
+    with pytest.raises(rte.RTEError) as e:
+        rte.solve_many([b], [rho], [o], lockstep=True)
+    assert e.value.status == rte.RTE_EINVAL
+
+
 @pytest.fixture(scope="module")
 def served():
     """A ROM for the 16x16 CL(4,4) lattice bucket (ROMSAD + ROMIG) and a DSA-only bucket."""
