@@ -653,19 +653,28 @@ __global__ void __launch_bounds__(512) coarse_vcycle_kernel(const CoarseArgs A, 
 
 // Masses of level l per (instance, class): materials sigma I; mixed cells sum_children P^T M P with
 // the children's masses taken from level l-1 by their classes.
+// Mass blocks of every (instance, class) of level l, one thread per (instance, class, entry): a
+// material class holds sigma_a I and sigma_t I; a mixed class of a coarse level the Galerkin
+// projection sum over its 2 x 2 children of P_c^T M_child P_c (the children's blocks from level
+// l - 1).  Each entry is summed over the children and the P coefficients in a fixed order.
 __global__ void class_mass_kernel(int l, int n_mat, int n_class, int n_class_f, int nxf, int nxc,
                                   const int32_t* mixed, const int32_t* cls_f,
                                   const double* sigma_t, const double* sigma_s, int B,
                                   const double* Maf, const double* Mtf, double* Ma, double* Mt,
                                   const uint8_t* mask) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= B * n_class) return;
-  const int b = t / n_class, k = t % n_class;
+  if (t >= B * n_class * 16) return;
+  const int e = t % 16, bk = t / 16;
+  const int b = bk / n_class, k = bk % n_class;
   if (mask && !mask[b]) return;
-  double ma[16] = {0}, mt[16] = {0};
+  const int r = e / 4, q = e % 4;
+  double ma = 0.0, mt = 0.0;
   if (k < n_mat) {
-    const double st = sigma_t[b * n_mat + k], sa = st - sigma_s[b * n_mat + k];
-    for (int q = 0; q < 4; ++q) ma[5 * q] = sa, mt[5 * q] = st;
+    if (r == q) {
+      const double st = sigma_t[b * n_mat + k];
+      ma = st - sigma_s[b * n_mat + k];
+      mt = st;
+    }
   } else {
     const int C = mixed[k - n_mat];
     const int I = C % nxc, J = C / nxc;
@@ -674,24 +683,22 @@ __global__ void class_mass_kernel(int l, int n_mat, int n_class, int n_class_f, 
         const int c = (2 * J + dy) * nxf + 2 * I + dx;
         const double* fa = Maf + ((size_t)b * n_class_f + cls_f[c]) * 16;
         const double* ft = Mtf + ((size_t)b * n_class_f + cls_f[c]) * 16;
-        for (int r = 0; r < 4; ++r)
-          for (int q = 0; q < 4; ++q) {
-            double sa = 0.0, stt = 0.0;
-            for (int kk = 0; kk < 4; ++kk) {
-              const double pr = pk(dx, dy, kk, r);
-              if (pr == 0.0) continue;
-              for (int ll = 0; ll < 4; ++ll) {
-                const double pq = pk(dx, dy, ll, q);
-                sa += pr * fa[4 * kk + ll] * pq;
-                stt += pr * ft[4 * kk + ll] * pq;
-              }
-            }
-            ma[4 * r + q] += sa;
-            mt[4 * r + q] += stt;
+        double sa = 0.0, stt = 0.0;
+        for (int kk = 0; kk < 4; ++kk) {
+          const double pr = pk(dx, dy, kk, r);
+          if (pr == 0.0) continue;
+          for (int ll = 0; ll < 4; ++ll) {
+            const double pq = pk(dx, dy, ll, q);
+            sa += pr * fa[4 * kk + ll] * pq;
+            stt += pr * ft[4 * kk + ll] * pq;
           }
+        }
+        ma += sa;
+        mt += stt;
       }
   }
-  for (int e = 0; e < 16; ++e) Ma[(size_t)t * 16 + e] = ma[e], Mt[(size_t)t * 16 + e] = mt[e];
+  Ma[(size_t)bk * 16 + e] = ma;
+  Mt[(size_t)bk * 16 + e] = mt;
 }
 
 // D = geo + blockdiag(Ma, 3<vx^2> Mt, 3<vy^2> Mt) per (instance, class); store D, D^{-1} (FP32)
@@ -1217,7 +1224,7 @@ int dsa_setup(rte_batch_t bt, cudaStream_t st, const uint8_t* mask) {
   // per parameter set: masses and diagonal blocks of every (instance, class), level by level
   for (int l = 0; l < s->n_levels; ++l) {
     const int n = B * s->ncls[l];
-    class_mass_kernel<<<(n + 127) / 128, 128, 0, st>>>(
+    class_mass_kernel<<<(16 * n + 127) / 128, 128, 0, st>>>(
         l, d->n_mat, s->ncls[l], l ? s->ncls[l - 1] : 0, l ? s->lnx[l - 1] : 0, s->lnx[l],
         s->mixed[l]->p, l ? s->cls[l - 1]->p : nullptr, bt->sigma_t.p, bt->sigma_s.p, B,
         l ? s->Ma[l - 1]->p : nullptr, l ? s->Mt[l - 1]->p : nullptr, s->Ma[l]->p, s->Mt[l]->p,

@@ -322,16 +322,19 @@ __global__ void transport_apply1d_kernel(const double* U, int r, int n_dirs, int
   out[2 * c + 1] = y1;
 }
 
-// A_{mu,r} per instance and its LU factorisation with partial pivoting (one thread per instance).
-__global__ void rom_assemble_lu_kernel(const double* A0, const double* Aa, const double* As,
-                                       int r, int n_mat, const double* sigma_t,
-                                       const double* sigma_s, int B, double* LU, int* piv,
-                                       const uint8_t* mask) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B) return;
+// A_{mu,r} per instance and its LU factorisation with partial pivoting, one warp per instance: lane l
+// assembles the entries e = l, l + 32, ... and owns the rows q = l, l + 32, ... in the elimination.
+// Every entry gets the same operations in the same order as a sequential Doolittle elimination, and
+// the pivot is the first row of largest magnitude (a warp arg-max with ties to the lower row).
+__global__ void rom_assemble_lu_warp_kernel(const double* A0, const double* Aa, const double* As,
+                                            int r, int n_mat, const double* sigma_t,
+                                            const double* sigma_s, int B, double* LU, int* piv,
+                                            const uint8_t* mask) {
+  const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (b >= B) return;                     // uniform over the warp
   if (mask && !mask[b]) return;
   double* A = LU + (size_t)b * r * r;
-  for (int e = 0; e < r * r; ++e) {
+  for (int e = lane; e < r * r; e += 32) {
     double v = A0[e];
     for (int m = 0; m < n_mat; ++m) {
       const double st = sigma_t[b * n_mat + m], ss = sigma_s[b * n_mat + m];
@@ -339,25 +342,37 @@ __global__ void rom_assemble_lu_kernel(const double* A0, const double* Aa, const
     }
     A[e] = v;
   }
+  __syncwarp();
   for (int k = 0; k < r; ++k) {
-    int p = k;
-    for (int q = k + 1; q < r; ++q)
-      if (fabs(A[q * r + k]) > fabs(A[p * r + k])) p = q;
-    piv[b * r + k] = p;
+    double best = -1.0;
+    int p = r;
+    for (int q = k + lane; q < r; q += 32) {
+      const double v = fabs(A[q * r + k]);
+      if (v > best) best = v, p = q;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int op = __shfl_xor_sync(0xffffffffu, p, o);
+      if (ob > best || (ob == best && op < p)) best = ob, p = op;
+    }
+    if (lane == 0) piv[b * r + k] = p;
     if (p != k)
-      for (int c = 0; c < r; ++c) {
+      for (int c = lane; c < r; c += 32) {
         const double t = A[k * r + c];
         A[k * r + c] = A[p * r + c];
         A[p * r + c] = t;
       }
+    __syncwarp();
     const double inv = 1.0 / A[k * r + k];
-    for (int q = k + 1; q < r; ++q) {
+    for (int q = k + 1 + lane; q < r; q += 32) {
       const double f = A[q * r + k] * inv;
       A[q * r + k] = f;
       for (int c = k + 1; c < r; ++c) A[q * r + c] -= f * A[k * r + c];
     }
+    __syncwarp();
   }
 }
+
 
 // proj[b][i] = sum_e Ut[i][e] v[b][e * stride + off]  (one block per (i, b))
 __global__ void project_kernel(const double* Ut, int n, const double* v, int stride, int off,
@@ -866,10 +881,10 @@ int rom_prepare(rte_rom_t rom, rte_batch_t bt, cudaStream_t st, const uint8_t* m
     RTE_TRY(o->piv.alloc((size_t)B * r));
     RTE_TRY(o->proj.alloc((size_t)B * r));
   }
-  rom_assemble_lu_kernel<<<(B + 63) / 64, 64, 0, st>>>(rom->A0_dev.p, rom->Aa_dev.p, rom->As_dev.p,
-                                                       r, bt->disc->n_mat, bt->sigma_t.p,
-                                                       bt->sigma_s.p, B, o->lu.p, o->piv.p,
-                                                       mask); RTE_NOTE_LAUNCH();
+  rom_assemble_lu_warp_kernel<<<(B + 3) / 4, 128, 0, st>>>(rom->A0_dev.p, rom->Aa_dev.p, rom->As_dev.p,
+                                                           r, bt->disc->n_mat, bt->sigma_t.p,
+                                                           bt->sigma_s.p, B, o->lu.p, o->piv.p,
+                                                           mask); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   o->batch = bt;
   return RTE_OK;
