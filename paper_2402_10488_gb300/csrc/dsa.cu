@@ -198,83 +198,129 @@ __device__ __forceinline__ void store12(float* p, const float v[NB]) {
   for (int k = 0; k < 3; ++k) q[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
 }
 
-// acc += sum over the existing face neighbours of their coupling to a cell, via traces; w, e, s, n
-// point to the 12 values of the west, east, south and north neighbours (null where there is none).
+// ---- level vectors in HBM ------------------------------------------------------------------------
+// Per instance [2 colours][3 fields][half][4] floats, half = ceil(nc / 2): the cells of colour
+// (i + j) & 1 in the order of c / 2 (which numbers each colour's cells without gaps for either parity
+// of nx), each field's 4 moments one 16-byte word.  A warp updating consecutive cells of one colour
+// then reads each field of their neighbours -- consecutive cells of the other colour -- as one
+// contiguous span of 16-byte words, and writes its own cells the same way (a cell's 12 values side
+// by side would put consecutive cells of a colour 96 bytes apart).
+__host__ __device__ __forceinline__ int lhalf(int nc) { return (nc + 1) / 2; }
+__host__ __device__ __forceinline__ size_t lstride(int nc) { return (size_t)24 * lhalf(nc); }
+__device__ __forceinline__ size_t lword(int half, int c, int col, int f) {
+  return ((size_t)(col * 3 + f) * half + (c >> 1)) * 4;
+}
+__device__ __forceinline__ int lcolour(int c, int nx) {
+  const int j = c / nx;
+  return (c - j * nx + j) & 1;
+}
+// the 12 values of cell c (colour col) of one instance's vector v
+__device__ __forceinline__ void lload(const float* v, int half, int c, int col, float out[NB]) {
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    const float4 u = *reinterpret_cast<const float4*>(v + lword(half, c, col, f));
+    out[4 * f] = u.x, out[4 * f + 1] = u.y, out[4 * f + 2] = u.z, out[4 * f + 3] = u.w;
+  }
+}
+__device__ __forceinline__ void lstore(float* v, int half, int c, int col, const float in[NB]) {
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+    *reinterpret_cast<float4*>(v + lword(half, c, col, f)) =
+        make_float4(in[4 * f], in[4 * f + 1], in[4 * f + 2], in[4 * f + 3]);
+}
+
+// The coupling of one face neighbour to a cell, added to acc, from the neighbour's 12 values v via
+// its traces on the shared face: west (its right-face traces, the cell's left-face values), east,
+// south (traces expanded along x) and north.
+__device__ __forceinline__ void side_w(const Coup& K, float qx, const float v[NB], float acc[NB]) {
+  const float s3 = 1.7320508075688772f;
+  float t[3][2];
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) t[f][q] = qx * fmaf(s3, v[4 * f + 1 + 2 * q], v[4 * f + 2 * q]);
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float u = qx * (K.W[3 * f] * t[0][q] + K.W[3 * f + 1] * t[1][q] + K.W[3 * f + 2] * t[2][q]);
+      acc[4 * f + 2 * q] += u;
+      acc[4 * f + 1 + 2 * q] -= s3 * u;
+    }
+}
+__device__ __forceinline__ void side_e(const Coup& K, float qx, const float v[NB], float acc[NB]) {
+  const float s3 = 1.7320508075688772f;
+  float t[3][2];
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) t[f][q] = qx * fmaf(-s3, v[4 * f + 1 + 2 * q], v[4 * f + 2 * q]);
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float u = qx * (K.E[3 * f] * t[0][q] + K.E[3 * f + 1] * t[1][q] + K.E[3 * f + 2] * t[2][q]);
+      acc[4 * f + 2 * q] += u;
+      acc[4 * f + 1 + 2 * q] += s3 * u;
+    }
+}
+__device__ __forceinline__ void side_s(const Coup& K, float qy, const float v[NB], float acc[NB]) {
+  const float s3 = 1.7320508075688772f;
+  float t[3][2];
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) t[f][q] = qy * fmaf(s3, v[4 * f + q + 2], v[4 * f + q]);
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float u = qy * (K.S[3 * f] * t[0][q] + K.S[3 * f + 1] * t[1][q] + K.S[3 * f + 2] * t[2][q]);
+      acc[4 * f + q] += u;
+      acc[4 * f + q + 2] -= s3 * u;
+    }
+}
+__device__ __forceinline__ void side_n(const Coup& K, float qy, const float v[NB], float acc[NB]) {
+  const float s3 = 1.7320508075688772f;
+  float t[3][2];
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) t[f][q] = qy * fmaf(-s3, v[4 * f + q + 2], v[4 * f + q]);
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float u = qy * (K.N[3 * f] * t[0][q] + K.N[3 * f + 1] * t[1][q] + K.N[3 * f + 2] * t[2][q]);
+      acc[4 * f + q] += u;
+      acc[4 * f + q + 2] += s3 * u;
+    }
+}
+
+// acc += sum over the existing face neighbours of their coupling to a cell; w, e, s, n point to the
+// 12 values of the west, east, south and north neighbours (null where there is none), in shared
+// memory or registers.
 __device__ __forceinline__ void nbr_trace_sum_p(const Coup& K, float qx, float qy, const float* w,
                                                 const float* e, const float* s, const float* n,
                                                 float acc[NB]) {
-  const float s3 = 1.7320508075688772f;
-  float v[NB], t[3][2];
-  if (w) {  // west neighbour: its right-face traces, own left-face values
-    load12(w, v);
-#pragma unroll
-    for (int f = 0; f < 3; ++f)
-#pragma unroll
-      for (int q = 0; q < 2; ++q) t[f][q] = qx * fmaf(s3, v[4 * f + 1 + 2 * q], v[4 * f + 2 * q]);
-#pragma unroll
-    for (int f = 0; f < 3; ++f)
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const float u = qx * (K.W[3 * f] * t[0][q] + K.W[3 * f + 1] * t[1][q] + K.W[3 * f + 2] * t[2][q]);
-        acc[4 * f + 2 * q] += u;
-        acc[4 * f + 1 + 2 * q] -= s3 * u;
-      }
-  }
-  if (e) {  // east neighbour: its left-face traces, own right-face values
-    load12(e, v);
-#pragma unroll
-    for (int f = 0; f < 3; ++f)
-#pragma unroll
-      for (int q = 0; q < 2; ++q) t[f][q] = qx * fmaf(-s3, v[4 * f + 1 + 2 * q], v[4 * f + 2 * q]);
-#pragma unroll
-    for (int f = 0; f < 3; ++f)
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const float u = qx * (K.E[3 * f] * t[0][q] + K.E[3 * f + 1] * t[1][q] + K.E[3 * f + 2] * t[2][q]);
-        acc[4 * f + 2 * q] += u;
-        acc[4 * f + 1 + 2 * q] += s3 * u;
-      }
-  }
-  if (s) {  // south neighbour: its top-face traces (expanded along x), own bottom values
-    load12(s, v);
-#pragma unroll
-    for (int f = 0; f < 3; ++f)
-#pragma unroll
-      for (int q = 0; q < 2; ++q) t[f][q] = qy * fmaf(s3, v[4 * f + q + 2], v[4 * f + q]);
-#pragma unroll
-    for (int f = 0; f < 3; ++f)
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const float u = qy * (K.S[3 * f] * t[0][q] + K.S[3 * f + 1] * t[1][q] + K.S[3 * f + 2] * t[2][q]);
-        acc[4 * f + q] += u;
-        acc[4 * f + q + 2] -= s3 * u;
-      }
-  }
-  if (n) {  // north neighbour: its bottom-face traces, own top values
-    load12(n, v);
-#pragma unroll
-    for (int f = 0; f < 3; ++f)
-#pragma unroll
-      for (int q = 0; q < 2; ++q) t[f][q] = qy * fmaf(-s3, v[4 * f + q + 2], v[4 * f + q]);
-#pragma unroll
-    for (int f = 0; f < 3; ++f)
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const float u = qy * (K.N[3 * f] * t[0][q] + K.N[3 * f + 1] * t[1][q] + K.N[3 * f + 2] * t[2][q]);
-        acc[4 * f + q] += u;
-        acc[4 * f + q + 2] += s3 * u;
-      }
-  }
+  float v[NB];
+  if (w) load12(w, v), side_w(K, qx, v, acc);
+  if (e) load12(e, v), side_e(K, qx, v, acc);
+  if (s) load12(s, v), side_s(K, qy, v, acc);
+  if (n) load12(n, v), side_n(K, qy, v, acc);
 }
 
-// the same for cell (i, j) of a level vector x in global memory
+// the same for cell (i, j) of one instance's level vector x in global memory (its neighbours have
+// the other colour)
 __device__ __forceinline__ void nbr_trace_sum(const Coup& K, float qx, float qy,
-                                              const float* __restrict__ x, int i, int j, int nx,
-                                              int ny, float acc[NB]) {
-  nbr_trace_sum_p(K, qx, qy, i > 0 ? x + ((size_t)j * nx + i - 1) * NB : nullptr,
-                  i + 1 < nx ? x + ((size_t)j * nx + i + 1) * NB : nullptr,
-                  j > 0 ? x + ((size_t)(j - 1) * nx + i) * NB : nullptr,
-                  j + 1 < ny ? x + ((size_t)(j + 1) * nx + i) * NB : nullptr, acc);
+                                              const float* __restrict__ x, int half, int i, int j,
+                                              int nx, int ny, float acc[NB]) {
+  const int nc = 1 - ((i + j) & 1);
+  float v[NB];
+  if (i > 0) lload(x, half, j * nx + i - 1, nc, v), side_w(K, qx, v, acc);
+  if (i + 1 < nx) lload(x, half, j * nx + i + 1, nc, v), side_e(K, qx, v, acc);
+  if (j > 0) lload(x, half, (j - 1) * nx + i, nc, v), side_s(K, qy, v, acc);
+  if (j + 1 < ny) lload(x, half, (j + 1) * nx + i, nc, v), side_n(K, qy, v, acc);
 }
 
 __device__ __forceinline__ void matvec12(const float* __restrict__ M, const float v[NB], float out[NB]) {
@@ -291,34 +337,35 @@ __device__ __forceinline__ void matvec12(const float* __restrict__ M, const floa
 // dinv_b: the instance's D^-1 blocks [n_class][144] (global memory, or a shared-memory copy)
 __device__ __forceinline__ void rbgs_cell(const LevelC& L, const Coup& K, int b, int c,
                                           const float* dinv_b) {
-  const int i = c % L.nx, j = c / L.nx;
-  float* xb = L.x + (size_t)b * L.nc * NB;
+  const int i = c % L.nx, j = c / L.nx, col = (i + j) & 1, half = lhalf(L.nc);
+  float* xb = L.x + (size_t)b * lstride(L.nc);
   float acc[NB];
 #pragma unroll
   for (int r = 0; r < NB; ++r) acc[r] = 0.f;
-  nbr_trace_sum(K, L.qx, L.qy, xb, i, j, L.nx, L.ny, acc);
+  nbr_trace_sum(K, L.qx, L.qy, xb, half, i, j, L.nx, L.ny, acc);
   float res[NB];
-  load12(L.b + ((size_t)b * L.nc + c) * NB, res);
+  lload(L.b + (size_t)b * lstride(L.nc), half, c, col, res);
 #pragma unroll
   for (int r = 0; r < NB; ++r) res[r] -= acc[r];
   float out[NB];
   matvec12(dinv_b + (size_t)L.cls[c] * NB2, res, out);
-  store12(xb + (size_t)c * NB, out);
+  lstore(xb, half, c, col, out);
 }
 
 // one cell of r = b - A x
 __device__ __forceinline__ void residual_cell(const LevelC& L, const Coup& K, int b, int c) {
-  const int i = c % L.nx, j = c / L.nx;
-  const float* xb = L.x + (size_t)b * L.nc * NB;
+  const int i = c % L.nx, j = c / L.nx, col = (i + j) & 1, half = lhalf(L.nc);
+  const size_t off = (size_t)b * lstride(L.nc);
+  const float* xb = L.x + off;
   float xl[NB], acc[NB];
-  load12(xb + (size_t)c * NB, xl);
+  lload(xb, half, c, col, xl);
   matvec12(L.diag + ((size_t)b * L.n_class + L.cls[c]) * NB2, xl, acc);
-  nbr_trace_sum(K, L.qx, L.qy, xb, i, j, L.nx, L.ny, acc);
+  nbr_trace_sum(K, L.qx, L.qy, xb, half, i, j, L.nx, L.ny, acc);
   float bl[NB];
-  load12(L.b + ((size_t)b * L.nc + c) * NB, bl);
+  lload(L.b + off, half, c, col, bl);
 #pragma unroll
   for (int k = 0; k < NB; ++k) bl[k] -= acc[k];
-  store12(L.r + ((size_t)b * L.nc + c) * NB, bl);
+  lstore(L.r + off, half, c, col, bl);
 }
 
 // Prolongation coefficients: fine basis a_f in the coarse basis a_c restricted to child o (-1/+1):
@@ -340,15 +387,17 @@ __host__ __device__ __forceinline__ float pk(int dx, int dy, int kf, int kc) {
 __device__ __forceinline__ void restrict_entry(const LevelC& F, const LevelC& Cl, int b, int t) {
   const int C = t / NB, row = t % NB, f = row / 4, kc = row % 4;
   const int I = C % Cl.nx, J = C / Cl.nx;
+  const int fh = lhalf(F.nc);
+  const float* rb = F.r + (size_t)b * lstride(F.nc);
   float s = 0.f;
   for (int dy = 0; dy < 2; ++dy)
     for (int dx = 0; dx < 2; ++dx) {
       const int c = (2 * J + dy) * F.nx + 2 * I + dx;
-      const float* rv = F.r + ((size_t)b * F.nc + c) * NB + 4 * f;
+      const float* rv = rb + lword(fh, c, (dx + dy) & 1, f);   // (2I + dx) + (2J + dy) has dx + dy's parity
 #pragma unroll
       for (int kf = 0; kf < 4; ++kf) s = fmaf(pk(dx, dy, kf, kc), rv[kf], s);
     }
-  Cl.b[((size_t)b * Cl.nc) * NB + t] = s;
+  Cl.b[(size_t)b * lstride(Cl.nc) + lword(lhalf(Cl.nc), C, (I + J) & 1, f) + kc] = s;
 }
 
 // one entry t = (c, row) of x_fine += P_c x_coarse[C]
@@ -356,11 +405,12 @@ __device__ __forceinline__ void prolong_entry(const LevelC& F, const LevelC& Cl,
   const int c = t / NB, row = t % NB, f = row / 4, kf = row % 4;
   const int i = c % F.nx, j = c / F.nx;
   const int C = (j / 2) * Cl.nx + i / 2, dx = i & 1, dy = j & 1;
-  const float* xv = Cl.x + ((size_t)b * Cl.nc + C) * NB + 4 * f;
+  const float* xv = Cl.x + (size_t)b * lstride(Cl.nc) +
+                    lword(lhalf(Cl.nc), C, (i / 2 + j / 2) & 1, f);
   float s = 0.f;
 #pragma unroll
   for (int kc = 0; kc < 4; ++kc) s = fmaf(pk(dx, dy, kf, kc), xv[kc], s);
-  F.x[(size_t)b * F.nc * NB + t] += s;
+  F.x[(size_t)b * lstride(F.nc) + lword(lhalf(F.nc), c, (i + j) & 1, f) + kf] += s;
 }
 
 constexpr int kSmemClasses = 8;  // a level with at most this many classes has its D^-1 blocks
@@ -393,11 +443,12 @@ __global__ void rbgs_kernel(LevelC L, Coup K, int color, const uint8_t* active) 
 // sum) and the stored x of the other colour is left as it was -- the next half sweep recomputes
 // those cells from scratch.  Saves the separate pass of prolong_add_kernel over x; bit for bit the
 // same results.
-__device__ __forceinline__ void nbr_prolonged(const float* __restrict__ xb, const LevelC& Cl, int b,
-                                              int ii, int jj, int nx, float v[NB]) {
-  load12(xb + ((size_t)jj * nx + ii) * NB, v);
+__device__ __forceinline__ void nbr_prolonged(const float* __restrict__ xb, int half, const LevelC& Cl,
+                                              int b, int ii, int jj, int nx, float v[NB]) {
+  lload(xb, half, jj * nx + ii, (ii + jj) & 1, v);
   const int C = (jj / 2) * Cl.nx + ii / 2, dx = ii & 1, dy = jj & 1;
-  const float* xc = Cl.x + ((size_t)b * Cl.nc + C) * NB;
+  float xc[NB];
+  lload(Cl.x + (size_t)b * lstride(Cl.nc), lhalf(Cl.nc), C, (ii / 2 + jj / 2) & 1, xc);
 #pragma unroll
   for (int f = 0; f < 3; ++f)
 #pragma unroll
@@ -426,25 +477,25 @@ __global__ void rbgs_prolong_kernel(LevelC L, LevelC Cl, Coup K, int color, cons
   const int j = idx / hx2;
   const int i = 2 * (idx % hx2) + ((j + color) & 1);
   if (i >= L.nx) return;
-  const int c = j * L.nx + i;
-  float* xb = L.x + (size_t)b * L.nc * NB;
+  const int c = j * L.nx + i, half = lhalf(L.nc);
+  float* xb = L.x + (size_t)b * lstride(L.nc);
   float vw[NB], ve[NB], vs[NB], vn[NB];
-  if (i > 0) nbr_prolonged(xb, Cl, b, i - 1, j, L.nx, vw);
-  if (i + 1 < L.nx) nbr_prolonged(xb, Cl, b, i + 1, j, L.nx, ve);
-  if (j > 0) nbr_prolonged(xb, Cl, b, i, j - 1, L.nx, vs);
-  if (j + 1 < L.ny) nbr_prolonged(xb, Cl, b, i, j + 1, L.nx, vn);
+  if (i > 0) nbr_prolonged(xb, half, Cl, b, i - 1, j, L.nx, vw);
+  if (i + 1 < L.nx) nbr_prolonged(xb, half, Cl, b, i + 1, j, L.nx, ve);
+  if (j > 0) nbr_prolonged(xb, half, Cl, b, i, j - 1, L.nx, vs);
+  if (j + 1 < L.ny) nbr_prolonged(xb, half, Cl, b, i, j + 1, L.nx, vn);
   float acc[NB];
 #pragma unroll
   for (int r = 0; r < NB; ++r) acc[r] = 0.f;
   nbr_trace_sum_p(K, L.qx, L.qy, i > 0 ? vw : nullptr, i + 1 < L.nx ? ve : nullptr,
                   j > 0 ? vs : nullptr, j + 1 < L.ny ? vn : nullptr, acc);
   float res[NB];
-  load12(L.b + ((size_t)b * L.nc + c) * NB, res);
+  lload(L.b + (size_t)b * lstride(L.nc), half, c, color, res);
 #pragma unroll
   for (int r = 0; r < NB; ++r) res[r] -= acc[r];
   float out[NB];
   matvec12((dsm ? reinterpret_cast<const float*>(dsh4) : dg) + (size_t)L.cls[c] * NB2, res, out);
-  store12(xb + (size_t)c * NB, out);
+  lstore(xb, half, c, color, out);
 }
 
 // Red-black Gauss-Seidel with temporal blocking: H = 2 nu half sweeps of one level, colours c0,
@@ -479,15 +530,16 @@ __global__ void __launch_bounds__(256) rbgs_fused_kernel(LevelC L, Coup K, int H
     for (int t = threadIdx.x; t < L.n_class * NB2 / 4; t += blockDim.x)
       reinterpret_cast<float4*>(ds)[t] = reinterpret_cast<const float4*>(dg)[t];
   const int i0 = blockIdx.x * kFT - H, j0 = blockIdx.y * kFT - H;  // region origin
-  const float* xg = L.x + (size_t)b * L.nc * NB;
-  const float* bg = L.b + (size_t)b * L.nc * NB;
-  float* xo = xout + (size_t)b * L.nc * NB;
+  const int lh = lhalf(L.nc);
+  const float* xg = L.x + (size_t)b * lstride(L.nc);
+  const float* bg = L.b + (size_t)b * lstride(L.nc);
+  float* xo = xout + (size_t)b * lstride(L.nc);
   for (int t = threadIdx.x; t < R * R * 3; t += blockDim.x) {
     const int cell = t / 3, q = t % 3, gi = i0 + cell % R, gj = j0 + cell / R;
     if (gi >= 0 && gi < L.nx && gj >= 0 && gj < L.ny) {
-      const size_t g = ((size_t)gj * L.nx + gi) * NB;
-      reinterpret_cast<float4*>(xs + (size_t)cell * NB)[q] = reinterpret_cast<const float4*>(xg + g)[q];
-      reinterpret_cast<float4*>(bs + (size_t)cell * NB)[q] = reinterpret_cast<const float4*>(bg + g)[q];
+      const size_t g = lword(lh, gj * L.nx + gi, (gi + gj) & 1, q);
+      reinterpret_cast<float4*>(xs + (size_t)cell * NB)[q] = *reinterpret_cast<const float4*>(xg + g);
+      reinterpret_cast<float4*>(bs + (size_t)cell * NB)[q] = *reinterpret_cast<const float4*>(bg + g);
     }
   }
   __syncthreads();
@@ -521,7 +573,7 @@ __global__ void __launch_bounds__(256) rbgs_fused_kernel(LevelC L, Coup K, int H
     const int cell = t / 3, q = t % 3, ri = H + cell % kFT, rj = H + cell / kFT;
     const int gi = i0 + ri, gj = j0 + rj;
     if (gi < L.nx && gj < L.ny)
-      reinterpret_cast<float4*>(xo + ((size_t)gj * L.nx + gi) * NB)[q] =
+      *reinterpret_cast<float4*>(xo + lword(lh, gj * L.nx + gi, (gi + gj) & 1, q)) =
           reinterpret_cast<const float4*>(xs + (size_t)(rj * R + ri) * NB)[q];
   }
 }
@@ -541,12 +593,13 @@ __global__ void __launch_bounds__(128) rbgs_tiled_kernel(LevelC L, Coup K, int c
   __shared__ float4 xs4[R * R * 3];
   __shared__ float4 dsh4[kSmemClasses * NB2 / 4];
   float* xs = reinterpret_cast<float*>(xs4);
-  float* xg = L.x + (size_t)b * L.nc * NB;
+  const int lh = lhalf(L.nc);
+  float* xg = L.x + (size_t)b * lstride(L.nc);
   const int i0 = blockIdx.x * kTT - 1, j0 = blockIdx.y * kTT - 1;  // region origin
   for (int t = threadIdx.x; t < R * R * 3; t += blockDim.x) {
     const int cell = t / 3, q = t % 3, gi = i0 + cell % R, gj = j0 + cell / R;
     if (gi >= 0 && gi < L.nx && gj >= 0 && gj < L.ny && ((gi + gj) & 1) != color)
-      xs4[t] = reinterpret_cast<const float4*>(xg + ((size_t)gj * L.nx + gi) * NB)[q];
+      xs4[t] = *reinterpret_cast<const float4*>(xg + lword(lh, gj * L.nx + gi, 1 - color, q));
   }
   const float* dg = L.dinv + (size_t)b * L.n_class * NB2;
   const bool dsm = L.n_class <= kSmemClasses;
@@ -568,12 +621,12 @@ __global__ void __launch_bounds__(128) rbgs_tiled_kernel(LevelC L, Coup K, int c
                   gj + 1 < L.ny ? xs + (size_t)(cell + R) * NB : nullptr, acc);
   const int c = gj * L.nx + gi;
   float res[NB];
-  load12(L.b + ((size_t)b * L.nc + c) * NB, res);
+  lload(L.b + (size_t)b * lstride(L.nc), lh, c, color, res);
 #pragma unroll
   for (int r = 0; r < NB; ++r) res[r] -= acc[r];
   float out[NB];
   matvec12((dsm ? reinterpret_cast<const float*>(dsh4) : dg) + (size_t)L.cls[c] * NB2, res, out);
-  store12(xg + (size_t)c * NB, out);
+  lstore(xg, lh, c, color, out);
 }
 
 __global__ void residual_kernel(LevelC L, Coup K, const uint8_t* active) {
@@ -624,7 +677,7 @@ __global__ void __launch_bounds__(512) coarse_vcycle_kernel(const CoarseArgs A, 
   int l = A.lc;
   for (;; ++l) {  // down
     const LevelC& L = A.lv[l];
-    for (int e = tid; e < L.nc * NB; e += nt) L.x[(size_t)b * L.nc * NB + e] = 0.f;
+    for (size_t e = tid; e < lstride(L.nc); e += nt) L.x[(size_t)b * lstride(L.nc) + e] = 0.f;
     __syncthreads();
     if (l == A.nL - 1) {  // coarsest: exact for one cell, else many sweeps
       const int n = L.nc == 1 ? 1 : 30;
@@ -836,17 +889,26 @@ __global__ void combine_kernel(const double* Z, size_t zstride, double* x, const
   }
 }
 
-__global__ void to32_kernel(const double* in, float* out, size_t n, int per, const uint8_t* active) {
+// FP64 Krylov vectors ([nc][12] per instance) to and from FP32 level-0 vectors (colour-split)
+__global__ void to32_kernel(const double* in, float* out, int nc, int nx, const uint8_t* active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
-  for (size_t e = blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)per; e += gridDim.x * blockDim.x)
-    out[(size_t)b * per + e] = (float)in[(size_t)b * per + e];
+  const int half = lhalf(nc);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nc * NB; e += gridDim.x * blockDim.x) {
+    const int c = e / NB, k = e % NB;
+    out[(size_t)b * lstride(nc) + lword(half, c, lcolour(c, nx), k / 4) + k % 4] =
+        (float)in[(size_t)b * nc * NB + e];
+  }
 }
-__global__ void to64_kernel(const float* in, double* out, int per, const uint8_t* active) {
+__global__ void to64_kernel(const float* in, double* out, int nc, int nx, const uint8_t* active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < per; e += gridDim.x * blockDim.x)
-    out[(size_t)b * per + e] = (double)in[(size_t)b * per + e];
+  const int half = lhalf(nc);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nc * NB; e += gridDim.x * blockDim.x) {
+    const int c = e / NB, k = e % NB;
+    out[(size_t)b * nc * NB + e] =
+        (double)in[(size_t)b * lstride(nc) + lword(half, c, lcolour(c, nx), k / 4) + k % 4];
+  }
 }
 __global__ void zero32_kernel(float* x, int per, const uint8_t* active) {
   const int b = blockIdx.y;
@@ -1132,11 +1194,11 @@ static int dsa_build_levels(rte_batch_t bt) {
     }
     for (auto* v : {&s->xl, &s->bl, &s->rl}) {
       v->push_back(new DevBuf<float>());
-      RTE_TRY(v->back()->alloc((size_t)B * nc * NB));
+      RTE_TRY(v->back()->alloc((size_t)B * lstride(nc)));
     }
   }
   RTE_TRY(s->diag64.alloc((size_t)B * d->n_mat * NB2));
-  const size_t n = (size_t)B * d->n_cells * NB;
+  const size_t n = (size_t)B * lstride(d->n_cells);
   RTE_TRY(s->xtot.alloc(n));
   RTE_TRY(s->borig.alloc(n));
   return RTE_OK;
@@ -1272,7 +1334,7 @@ static int vcycle(rte_batch_t bt, int l, const uint8_t* active, cudaStream_t st,
   // the blocked smoother writes the level's residual buffer and then swaps it with x, so every
   // LevelC is re-read after a step that may have swapped them
   LevelC L = lvl_of(bt, l);
-  if (!first_done) RTE_CUDA_TRY(cudaMemsetAsync(L.x, 0, sizeof(float) * (size_t)B * L.nc * NB, st));
+  if (!first_done) RTE_CUDA_TRY(cudaMemsetAsync(L.x, 0, sizeof(float) * (size_t)B * lstride(L.nc), st));
   const int ncol = ((L.nx + 1) / 2) * L.ny;
   const dim3 gcol((ncol + 127) / 128, B);
   const dim3 gtile((L.nx + kTT - 1) / kTT, (L.ny + kTT - 1) / kTT, B);
@@ -1329,13 +1391,17 @@ static int vcycle(rte_batch_t bt, int l, const uint8_t* active, cudaStream_t st,
   return RTE_OK;
 }
 
-__global__ void pack_rhs32_kernel(const double* R, float* v, int nc, const uint8_t* active) {
+// R (FP64, 4 moments per cell) into a level-0 vector: the delta-rho field, the current fields zero.
+__global__ void pack_rhs32_kernel(const double* R, float* v, int nc, int nx, const uint8_t* active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nc * NB) return;
-  const int c = t / NB, k = t % NB;
-  v[(size_t)b * nc * NB + t] = k < 4 ? (float)R[(size_t)b * nc * 4 + 4 * c + k] : 0.f;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const double* rc = R + ((size_t)b * nc + c) * 4;
+  float u[NB];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) u[k] = k < 4 ? (float)rc[k] : 0.f;
+  lstore(v + (size_t)b * lstride(nc), lhalf(nc), c, lcolour(c, nx), u);
 }
 
 // The right-hand side R (FP64, 4 moments per cell) packed into level 0's b (the delta-rho block; the
@@ -1361,12 +1427,12 @@ __global__ void pack_first_half_kernel(LevelC L, const double* __restrict__ R, c
   float v[NB];
 #pragma unroll
   for (int k = 0; k < NB; ++k) v[k] = k < 4 ? (float)rc[k] : 0.f;
-  store12(L.b + ((size_t)b * L.nc + c) * NB, v);
-  const int i = c % L.nx, j = c / L.nx;
-  if (((i + j) & 1) != 0) return;
+  const int i = c % L.nx, j = c / L.nx, col = (i + j) & 1, half = lhalf(L.nc);
+  lstore(L.b + (size_t)b * lstride(L.nc), half, c, col, v);
+  if (col != 0) return;
   float out[NB];
   matvec12((dsm ? reinterpret_cast<const float*>(dsh4) : dg) + (size_t)L.cls[c] * NB2, v, out);
-  store12(L.x + ((size_t)b * L.nc + c) * NB, out);
+  lstore(L.x + (size_t)b * lstride(L.nc), half, c, col, out);
 }
 
 __global__ void add32_kernel(const float* x, float* y, int per, const uint8_t* active) {
@@ -1376,13 +1442,18 @@ __global__ void add32_kernel(const float* x, float* y, int per, const uint8_t* a
     y[(size_t)b * per + e] += x[(size_t)b * per + e];
 }
 
-__global__ void extract_rho32_kernel(const float* x, double* drho, int nc, const uint8_t* active) {
+// the delta-rho field of a level-0 vector, in FP64 (4 moments per cell)
+__global__ void extract_rho32_kernel(const float* x, double* drho, int nc, int nx,
+                                     const uint8_t* active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nc * 4) return;
-  const int c = t / 4, k = t % 4;
-  drho[(size_t)b * nc * 4 + t] = (double)x[((size_t)b * nc + c) * NB + k];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const float4 u = *reinterpret_cast<const float4*>(x + (size_t)b * lstride(nc) +
+                                                    lword(lhalf(nc), c, lcolour(c, nx), 0));
+  double2* o = reinterpret_cast<double2*>(drho + ((size_t)b * nc + c) * 4);
+  o[0] = make_double2((double)u.x, (double)u.y);
+  o[1] = make_double2((double)u.z, (double)u.w);
 }
 
 // residual on level 0 against an explicit right-hand side and iterate: r0 = borig - A0 xtot
@@ -1401,8 +1472,9 @@ __global__ void residual_ext_kernel(LevelC L, Coup K, const float* bvec, const f
 static int dsa2d_vcycles(rte_batch_t bt, const double* R, double* drho, int k,
                          const uint8_t* active, cudaStream_t st) {
   DsaState* s = bt->dsa;
-  const int B = bt->B, nc = bt->disc->n_cells, per = nc * NB;
-  const dim3 gv((per + 255) / 256, B), gvc(std::min((per + 255) / 256, 1024), B);
+  const int B = bt->B, nc = bt->disc->n_cells, nx = bt->disc->nx;
+  const size_t per = lstride(nc);
+  const dim3 gv((nc + 255) / 256, B), gvc((unsigned)std::min<size_t>((per + 255) / 256, 1024), B);
   if (k == 1) {
     // one cycle: pack the right-hand side straight into level 0 and read the result from there; with
     // a one-launch-per-half-sweep smoother the packing also does the first half sweep
@@ -1410,14 +1482,14 @@ static int dsa2d_vcycles(rte_batch_t bt, const double* R, double* drho, int k,
     if (fuse) {
       pack_first_half_kernel<<<dim3((nc + 127) / 128, B), 128, 0, st>>>(lvl_of(bt, 0), R, active); RTE_NOTE_LAUNCH();
     } else {
-      pack_rhs32_kernel<<<gv, 256, 0, st>>>(R, s->bl[0]->p, nc, active); RTE_NOTE_LAUNCH();
+      pack_rhs32_kernel<<<gv, 256, 0, st>>>(R, s->bl[0]->p, nc, nx, active); RTE_NOTE_LAUNCH();
     }
     RTE_TRY(vcycle(bt, 0, active, st, bt->dsa_nu, fuse));
-    extract_rho32_kernel<<<dim3((nc * 4 + 255) / 256, B), 256, 0, st>>>(s->xl[0]->p, drho, nc, active); RTE_NOTE_LAUNCH();
+    extract_rho32_kernel<<<gv, 256, 0, st>>>(s->xl[0]->p, drho, nc, nx, active); RTE_NOTE_LAUNCH();
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
   }
-  pack_rhs32_kernel<<<gv, 256, 0, st>>>(R, s->borig.p, nc, active); RTE_NOTE_LAUNCH();
+  pack_rhs32_kernel<<<gv, 256, 0, st>>>(R, s->borig.p, nc, nx, active); RTE_NOTE_LAUNCH();
   const LevelC L0 = lvl_of(bt, 0);
   for (int it = 0; it < k; ++it) {
     if (it == 0) {
@@ -1432,10 +1504,10 @@ static int dsa2d_vcycles(rte_batch_t bt, const double* R, double* drho, int k,
       RTE_CUDA_TRY(cudaMemcpyAsync(s->xtot.p, s->xl[0]->p, sizeof(float) * (size_t)B * per,
                                    cudaMemcpyDeviceToDevice, st));
     } else {
-      add32_kernel<<<gvc, 256, 0, st>>>(s->xl[0]->p, s->xtot.p, per, active); RTE_NOTE_LAUNCH();
+      add32_kernel<<<gvc, 256, 0, st>>>(s->xl[0]->p, s->xtot.p, (int)per, active); RTE_NOTE_LAUNCH();
     }
   }
-  extract_rho32_kernel<<<dim3((nc * 4 + 255) / 256, B), 256, 0, st>>>(s->xtot.p, drho, nc, active); RTE_NOTE_LAUNCH();
+  extract_rho32_kernel<<<gv, 256, 0, st>>>(s->xtot.p, drho, nc, nx, active); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;
 }
@@ -1514,9 +1586,9 @@ static int dsa2d_fgmres(rte_batch_t bt, const double* R, double* drho, double rt
       double* vk = s->V.p + (size_t)k * vstride;
       double* zk = s->Z.p + (size_t)k * vstride;
       // z_k = M^{-1} v_k (one FP32 V-cycle)
-      to32_kernel<<<gvec_c, 256, 0, st>>>(vk, s->bl[0]->p, 0, n, act_dev.p); RTE_NOTE_LAUNCH();
+      to32_kernel<<<gvec_c, 256, 0, st>>>(vk, s->bl[0]->p, nc, d->nx, act_dev.p); RTE_NOTE_LAUNCH();
       RTE_TRY(vcycle(bt, 0, act_dev.p, st, bt->dsa_nu));
-      to64_kernel<<<gvec_c, 256, 0, st>>>(s->xl[0]->p, zk, n, act_dev.p); RTE_NOTE_LAUNCH();
+      to64_kernel<<<gvec_c, 256, 0, st>>>(s->xl[0]->p, zk, nc, d->nx, act_dev.p); RTE_NOTE_LAUNCH();
       // w = A z_k (FP64)
       fine_apply64_kernel<<<gvec, 256, 0, st>>>(F, d->nx, d->ny, B, zk, w, act_dev.p); RTE_NOTE_LAUNCH();
       // classical Gram-Schmidt, twice
