@@ -45,12 +45,18 @@ NCU_TRAFFIC = {"sha1": "9f7572895d1ea71c649e97ea9837ba3485344491", "bytes_per_la
 
 
 def sweep_source_sha1():
-    """sha1 of the 2D sweep kernels' device code: sweep.cu from the kernels' argument struct to
-    the 1D sweep's, which holds sweep2d_kernel, sweep2d_kba_kernel and the cell-source kernel."""
-    with open(os.path.join(ROOT, "paper_2402_10488_gb300", "csrc", "sweep.cu"), "rb") as fh:
+    """sha1 of the 2D sweep kernels' device code: sweep.cu up to the 1D sweep's argument struct
+    (the cell solve, sweep2d_warp and the kernels built on it) and the 2D argument struct in
+    common.cuh."""
+    csrc = os.path.join(ROOT, "paper_2402_10488_gb300", "csrc")
+    with open(os.path.join(csrc, "sweep.cu"), "rb") as fh:
         src = fh.read()
-    a, b = src.find(b"struct Sweep2DArgs {"), src.find(b"struct Sweep1DArgs {")
-    return hashlib.sha1(src[a:b] if 0 <= a < b else src).hexdigest()
+    with open(os.path.join(csrc, "common.cuh"), "rb") as fh:
+        hdr = fh.read()
+    b = src.find(b"struct Sweep1DArgs {")
+    a0, a1 = hdr.find(b"struct Sweep2DArgs {"), hdr.find(b"struct SweepItem {")
+    part = (src[:b] if b > 0 else src) + (hdr[a0:a1] if 0 <= a0 < a1 else hdr)
+    return hashlib.sha1(part).hexdigest()
 
 
 def parse():

@@ -125,19 +125,25 @@ static void field_block(const DsaMoments& m, const double DCx[16], const double 
 constexpr int kMaxLevels = 16;
 constexpr int kFuseCells = 1024;  // levels this small run inside one fused kernel per instance
 
+// Row-major 3x3 field couplings of the W, E, S, N faces of one level, divided by the cell size
+// normal to the face (h_x for W, E and h_y for S, N): the neighbour's face traces and the cell's own
+// face values each carry a factor 1 / sqrt(h).  Entries (0,2), (1,2), (2,0), (2,1) of W and E and
+// (0,1), (1,0), (1,2), (2,1) of S and N are zero (an x face couples J_y only to J_y, a y face J_x
+// only to J_x); the trace products skip them.
+struct Coup {
+  float W[9], E[9], S[9], N[9];
+};
+
 struct LevelC {
   int nx, ny, nc, n_class;
+  int n_pure;          // classes 0 .. n_pure - 1 are single-material cells (parity-block D)
   const int32_t* cls;  // [nc] class of each cell (material map at level 0)
   const float* diag;   // [B][n_class][144]
   const float* dinv;   // [B][n_class][144]
-  float qx, qy;        // 1/sqrt(h_x), 1/sqrt(h_y) of this level
-  float* x;            // [B][nc][12]
+  Coup K;              // this level's face couplings
+  float* x;            // per instance [2][3][half][4] (see lword)
   float* b;
   float* r;
-};
-
-struct Coup {  // row-major 3x3 field couplings of the W, E, S, N faces
-  float W[9], E[9], S[9], N[9];
 };
 
 struct Fine {  // level 0 in FP64, for the Krylov operator
@@ -231,96 +237,76 @@ __device__ __forceinline__ void lstore(float* v, int half, int c, int col, const
 
 // The coupling of one face neighbour to a cell, added to acc, from the neighbour's 12 values v via
 // its traces on the shared face: west (its right-face traces, the cell's left-face values), east,
-// south (traces expanded along x) and north.
-__device__ __forceinline__ void side_w(const Coup& K, float qx, const float v[NB], float acc[NB]) {
+// south (traces expanded along x) and north.  t[f][q]: trace of field f, q the moment along the
+// face; u = K t the field couplings; the cell's face values expand u into its moments (1, -+sqrt3).
+__device__ __forceinline__ void side_x(const float* __restrict__ Km, float sg, const float v[NB],
+                                       float acc[NB]) {
   const float s3 = 1.7320508075688772f;
-  float t[3][2];
 #pragma unroll
-  for (int f = 0; f < 3; ++f)
+  for (int q = 0; q < 2; ++q) {
+    const float t0 = fmaf(sg * s3, v[1 + 2 * q], v[2 * q]);
+    const float t1 = fmaf(sg * s3, v[5 + 2 * q], v[4 + 2 * q]);
+    const float t2 = fmaf(sg * s3, v[9 + 2 * q], v[8 + 2 * q]);
+    const float u[3] = {fmaf(Km[1], t1, Km[0] * t0), fmaf(Km[4], t1, Km[3] * t0), Km[8] * t2};
 #pragma unroll
-    for (int q = 0; q < 2; ++q) t[f][q] = qx * fmaf(s3, v[4 * f + 1 + 2 * q], v[4 * f + 2 * q]);
-#pragma unroll
-  for (int f = 0; f < 3; ++f)
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const float u = qx * (K.W[3 * f] * t[0][q] + K.W[3 * f + 1] * t[1][q] + K.W[3 * f + 2] * t[2][q]);
-      acc[4 * f + 2 * q] += u;
-      acc[4 * f + 1 + 2 * q] -= s3 * u;
+    for (int f = 0; f < 3; ++f) {
+      acc[4 * f + 2 * q] += u[f];
+      acc[4 * f + 1 + 2 * q] = fmaf(-sg * s3, u[f], acc[4 * f + 1 + 2 * q]);
     }
+  }
 }
-__device__ __forceinline__ void side_e(const Coup& K, float qx, const float v[NB], float acc[NB]) {
+__device__ __forceinline__ void side_y(const float* __restrict__ Km, float sg, const float v[NB],
+                                       float acc[NB]) {
   const float s3 = 1.7320508075688772f;
-  float t[3][2];
 #pragma unroll
-  for (int f = 0; f < 3; ++f)
+  for (int q = 0; q < 2; ++q) {
+    const float t0 = fmaf(sg * s3, v[q + 2], v[q]);
+    const float t1 = fmaf(sg * s3, v[4 + q + 2], v[4 + q]);
+    const float t2 = fmaf(sg * s3, v[8 + q + 2], v[8 + q]);
+    const float u[3] = {fmaf(Km[2], t2, Km[0] * t0), Km[4] * t1, fmaf(Km[8], t2, Km[6] * t0)};
 #pragma unroll
-    for (int q = 0; q < 2; ++q) t[f][q] = qx * fmaf(-s3, v[4 * f + 1 + 2 * q], v[4 * f + 2 * q]);
-#pragma unroll
-  for (int f = 0; f < 3; ++f)
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const float u = qx * (K.E[3 * f] * t[0][q] + K.E[3 * f + 1] * t[1][q] + K.E[3 * f + 2] * t[2][q]);
-      acc[4 * f + 2 * q] += u;
-      acc[4 * f + 1 + 2 * q] += s3 * u;
+    for (int f = 0; f < 3; ++f) {
+      acc[4 * f + q] += u[f];
+      acc[4 * f + q + 2] = fmaf(-sg * s3, u[f], acc[4 * f + q + 2]);
     }
+  }
 }
-__device__ __forceinline__ void side_s(const Coup& K, float qy, const float v[NB], float acc[NB]) {
-  const float s3 = 1.7320508075688772f;
-  float t[3][2];
-#pragma unroll
-  for (int f = 0; f < 3; ++f)
-#pragma unroll
-    for (int q = 0; q < 2; ++q) t[f][q] = qy * fmaf(s3, v[4 * f + q + 2], v[4 * f + q]);
-#pragma unroll
-  for (int f = 0; f < 3; ++f)
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const float u = qy * (K.S[3 * f] * t[0][q] + K.S[3 * f + 1] * t[1][q] + K.S[3 * f + 2] * t[2][q]);
-      acc[4 * f + q] += u;
-      acc[4 * f + q + 2] -= s3 * u;
-    }
+// west: the neighbour's right-face trace a0 + sqrt3 a1, the cell's left-face values (1, -sqrt3)
+__device__ __forceinline__ void side_w(const Coup& K, const float v[NB], float acc[NB]) {
+  side_x(K.W, 1.f, v, acc);
 }
-__device__ __forceinline__ void side_n(const Coup& K, float qy, const float v[NB], float acc[NB]) {
-  const float s3 = 1.7320508075688772f;
-  float t[3][2];
-#pragma unroll
-  for (int f = 0; f < 3; ++f)
-#pragma unroll
-    for (int q = 0; q < 2; ++q) t[f][q] = qy * fmaf(-s3, v[4 * f + q + 2], v[4 * f + q]);
-#pragma unroll
-  for (int f = 0; f < 3; ++f)
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const float u = qy * (K.N[3 * f] * t[0][q] + K.N[3 * f + 1] * t[1][q] + K.N[3 * f + 2] * t[2][q]);
-      acc[4 * f + q] += u;
-      acc[4 * f + q + 2] += s3 * u;
-    }
+__device__ __forceinline__ void side_e(const Coup& K, const float v[NB], float acc[NB]) {
+  side_x(K.E, -1.f, v, acc);
+}
+__device__ __forceinline__ void side_s(const Coup& K, const float v[NB], float acc[NB]) {
+  side_y(K.S, 1.f, v, acc);
+}
+__device__ __forceinline__ void side_n(const Coup& K, const float v[NB], float acc[NB]) {
+  side_y(K.N, -1.f, v, acc);
 }
 
 // acc += sum over the existing face neighbours of their coupling to a cell; w, e, s, n point to the
 // 12 values of the west, east, south and north neighbours (null where there is none), in shared
 // memory or registers.
-__device__ __forceinline__ void nbr_trace_sum_p(const Coup& K, float qx, float qy, const float* w,
-                                                const float* e, const float* s, const float* n,
-                                                float acc[NB]) {
+__device__ __forceinline__ void nbr_trace_sum_p(const Coup& K, const float* w, const float* e,
+                                                const float* s, const float* n, float acc[NB]) {
   float v[NB];
-  if (w) load12(w, v), side_w(K, qx, v, acc);
-  if (e) load12(e, v), side_e(K, qx, v, acc);
-  if (s) load12(s, v), side_s(K, qy, v, acc);
-  if (n) load12(n, v), side_n(K, qy, v, acc);
+  if (w) load12(w, v), side_w(K, v, acc);
+  if (e) load12(e, v), side_e(K, v, acc);
+  if (s) load12(s, v), side_s(K, v, acc);
+  if (n) load12(n, v), side_n(K, v, acc);
 }
 
 // the same for cell (i, j) of one instance's level vector x in global memory (its neighbours have
 // the other colour)
-__device__ __forceinline__ void nbr_trace_sum(const Coup& K, float qx, float qy,
-                                              const float* __restrict__ x, int half, int i, int j,
-                                              int nx, int ny, float acc[NB]) {
+__device__ __forceinline__ void nbr_trace_sum(const Coup& K, const float* __restrict__ x, int half,
+                                              int i, int j, int nx, int ny, float acc[NB]) {
   const int nc = 1 - ((i + j) & 1);
   float v[NB];
-  if (i > 0) lload(x, half, j * nx + i - 1, nc, v), side_w(K, qx, v, acc);
-  if (i + 1 < nx) lload(x, half, j * nx + i + 1, nc, v), side_e(K, qx, v, acc);
-  if (j > 0) lload(x, half, (j - 1) * nx + i, nc, v), side_s(K, qy, v, acc);
-  if (j + 1 < ny) lload(x, half, (j + 1) * nx + i, nc, v), side_n(K, qy, v, acc);
+  if (i > 0) lload(x, half, j * nx + i - 1, nc, v), side_w(K, v, acc);
+  if (i + 1 < nx) lload(x, half, j * nx + i + 1, nc, v), side_e(K, v, acc);
+  if (j > 0) lload(x, half, (j - 1) * nx + i, nc, v), side_s(K, v, acc);
+  if (j + 1 < ny) lload(x, half, (j + 1) * nx + i, nc, v), side_n(K, v, acc);
 }
 
 __device__ __forceinline__ void matvec12(const float* __restrict__ M, const float v[NB], float out[NB]) {
@@ -333,34 +319,63 @@ __device__ __forceinline__ void matvec12(const float* __restrict__ M, const floa
   }
 }
 
+// The 12 unknowns (field f, moment k = kx + 2 ky) of a cell have parities (kx xor [f = 1],
+// ky xor [f = 2]) under the reflections x -> -x and y -> -y.  The diagonal block of a single-
+// material cell (geometric part plus sigma I mass blocks) is invariant under both, so it couples only
+// unknowns of equal parities: D and D^-1 are four 3 x 3 blocks, 36 of the 144 entries, the others
+// exact zeros.  Each row is summed in matvec12's order over its nonzero entries.
+__device__ __forceinline__ void matvec12_parity(const float* __restrict__ M, const float v[NB],
+                                                float out[NB]) {
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const int px = p & 1, py = p >> 1;
+    const int g[3] = {px + 2 * py, 5 - px + 2 * py, 10 + px - 2 * py};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float s = 0.f;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) s = fmaf(M[g[a] * NB + g[q]], v[g[q]], s);
+      out[g[a]] = s;
+    }
+  }
+}
+
+// D (or D^-1) of class k times v: the parity blocks for a single-material class, else dense
+__device__ __forceinline__ void apply_block(const LevelC& L, const float* __restrict__ M, int k,
+                                            const float v[NB], float out[NB]) {
+  if (k < L.n_pure) matvec12_parity(M, v, out);
+  else matvec12(M, v, out);
+}
+
 // one cell of a red-black block Gauss-Seidel half sweep: x_c = D_c^{-1} (b_c - sum_n O_n x_n);
 // dinv_b: the instance's D^-1 blocks [n_class][144] (global memory, or a shared-memory copy)
-__device__ __forceinline__ void rbgs_cell(const LevelC& L, const Coup& K, int b, int c,
-                                          const float* dinv_b) {
+__device__ __forceinline__ void rbgs_cell(const LevelC& L, int b, int c, const float* dinv_b) {
   const int i = c % L.nx, j = c / L.nx, col = (i + j) & 1, half = lhalf(L.nc);
   float* xb = L.x + (size_t)b * lstride(L.nc);
   float acc[NB];
 #pragma unroll
   for (int r = 0; r < NB; ++r) acc[r] = 0.f;
-  nbr_trace_sum(K, L.qx, L.qy, xb, half, i, j, L.nx, L.ny, acc);
+  nbr_trace_sum(L.K, xb, half, i, j, L.nx, L.ny, acc);
   float res[NB];
   lload(L.b + (size_t)b * lstride(L.nc), half, c, col, res);
 #pragma unroll
   for (int r = 0; r < NB; ++r) res[r] -= acc[r];
   float out[NB];
-  matvec12(dinv_b + (size_t)L.cls[c] * NB2, res, out);
+  const int k = L.cls[c];
+  apply_block(L, dinv_b + (size_t)k * NB2, k, res, out);
   lstore(xb, half, c, col, out);
 }
 
 // one cell of r = b - A x
-__device__ __forceinline__ void residual_cell(const LevelC& L, const Coup& K, int b, int c) {
+__device__ __forceinline__ void residual_cell(const LevelC& L, int b, int c) {
   const int i = c % L.nx, j = c / L.nx, col = (i + j) & 1, half = lhalf(L.nc);
   const size_t off = (size_t)b * lstride(L.nc);
   const float* xb = L.x + off;
   float xl[NB], acc[NB];
   lload(xb, half, c, col, xl);
-  matvec12(L.diag + ((size_t)b * L.n_class + L.cls[c]) * NB2, xl, acc);
-  nbr_trace_sum(K, L.qx, L.qy, xb, half, i, j, L.nx, L.ny, acc);
+  const int k = L.cls[c];
+  apply_block(L, L.diag + ((size_t)b * L.n_class + k) * NB2, k, xl, acc);
+  nbr_trace_sum(L.K, xb, half, i, j, L.nx, L.ny, acc);
   float bl[NB];
   lload(L.b + off, half, c, col, bl);
 #pragma unroll
@@ -416,7 +431,7 @@ __device__ __forceinline__ void prolong_entry(const LevelC& F, const LevelC& Cl,
 constexpr int kSmemClasses = 8;  // a level with at most this many classes has its D^-1 blocks
                                  // staged in shared memory by the smoothing kernels
 
-__global__ void rbgs_kernel(LevelC L, Coup K, int color, const uint8_t* active) {
+__global__ void rbgs_kernel(LevelC L, int color, const uint8_t* active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   __shared__ float4 dsh4[kSmemClasses * NB2 / 4];
@@ -433,7 +448,7 @@ __global__ void rbgs_kernel(LevelC L, Coup K, int color, const uint8_t* active) 
   const int j = idx / hx2;
   const int i = 2 * (idx % hx2) + ((j + color) & 1);
   if (i >= L.nx) return;
-  rbgs_cell(L, K, b, j * L.nx + i, dsm ? reinterpret_cast<const float*>(dsh4) : dg);
+  rbgs_cell(L, b, j * L.nx + i, dsm ? reinterpret_cast<const float*>(dsh4) : dg);
 }
 
 // The first half sweep of post-smoothing with the prolongation x += P x_coarse folded in.  That
@@ -460,7 +475,7 @@ __device__ __forceinline__ void nbr_prolonged(const float* __restrict__ xb, int 
     }
 }
 
-__global__ void rbgs_prolong_kernel(LevelC L, LevelC Cl, Coup K, int color, const uint8_t* active) {
+__global__ void rbgs_prolong_kernel(LevelC L, LevelC Cl, int color, const uint8_t* active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   __shared__ float4 dsh4[kSmemClasses * NB2 / 4];
@@ -487,14 +502,15 @@ __global__ void rbgs_prolong_kernel(LevelC L, LevelC Cl, Coup K, int color, cons
   float acc[NB];
 #pragma unroll
   for (int r = 0; r < NB; ++r) acc[r] = 0.f;
-  nbr_trace_sum_p(K, L.qx, L.qy, i > 0 ? vw : nullptr, i + 1 < L.nx ? ve : nullptr,
-                  j > 0 ? vs : nullptr, j + 1 < L.ny ? vn : nullptr, acc);
+  nbr_trace_sum_p(L.K, i > 0 ? vw : nullptr, i + 1 < L.nx ? ve : nullptr, j > 0 ? vs : nullptr,
+                  j + 1 < L.ny ? vn : nullptr, acc);
   float res[NB];
   lload(L.b + (size_t)b * lstride(L.nc), half, c, color, res);
 #pragma unroll
   for (int r = 0; r < NB; ++r) res[r] -= acc[r];
   float out[NB];
-  matvec12((dsm ? reinterpret_cast<const float*>(dsh4) : dg) + (size_t)L.cls[c] * NB2, res, out);
+  const int k = L.cls[c];
+  apply_block(L, (dsm ? reinterpret_cast<const float*>(dsh4) : dg) + (size_t)k * NB2, k, res, out);
   lstore(xb, half, c, color, out);
 }
 
@@ -515,8 +531,8 @@ __host__ __device__ constexpr size_t fused_smem_bytes(int H) {
   return ((size_t)2 * (kFT + 2 * H) * (kFT + 2 * H) * NB + (size_t)kFusedClasses * NB2) * sizeof(float);
 }
 
-__global__ void __launch_bounds__(256) rbgs_fused_kernel(LevelC L, Coup K, int H, int c0,
-                                                         float* xout, const uint8_t* active) {
+__global__ void __launch_bounds__(256) rbgs_fused_kernel(LevelC L, int H, int c0, float* xout,
+                                                         const uint8_t* active) {
   const int b = blockIdx.z;
   if (active && !active[b]) return;
   extern __shared__ float4 fsm4[];
@@ -555,7 +571,7 @@ __global__ void __launch_bounds__(256) rbgs_fused_kernel(LevelC L, Coup K, int H
       float acc[NB];
 #pragma unroll
       for (int r = 0; r < NB; ++r) acc[r] = 0.f;
-      nbr_trace_sum_p(K, L.qx, L.qy, gi > 0 ? xs + (size_t)(cell - 1) * NB : nullptr,
+      nbr_trace_sum_p(L.K, gi > 0 ? xs + (size_t)(cell - 1) * NB : nullptr,
                       gi + 1 < L.nx ? xs + (size_t)(cell + 1) * NB : nullptr,
                       gj > 0 ? xs + (size_t)(cell - R) * NB : nullptr,
                       gj + 1 < L.ny ? xs + (size_t)(cell + R) * NB : nullptr, acc);
@@ -564,7 +580,8 @@ __global__ void __launch_bounds__(256) rbgs_fused_kernel(LevelC L, Coup K, int H
 #pragma unroll
       for (int r = 0; r < NB; ++r) res[r] -= acc[r];
       float out[NB];
-      matvec12((dsm ? ds : dg) + (size_t)L.cls[gj * L.nx + gi] * NB2, res, out);
+      const int k = L.cls[gj * L.nx + gi];
+      apply_block(L, (dsm ? ds : dg) + (size_t)k * NB2, k, res, out);
       store12(xs + (size_t)cell * NB, out);
     }
     __syncthreads();
@@ -585,8 +602,7 @@ __global__ void __launch_bounds__(256) rbgs_fused_kernel(LevelC L, Coup K, int H
 // only read, so the update is in place.  Same arithmetic as rbgs_kernel, bit for bit.
 constexpr int kTT = 16;  // tile side
 
-__global__ void __launch_bounds__(128) rbgs_tiled_kernel(LevelC L, Coup K, int color,
-                                                         const uint8_t* active) {
+__global__ void __launch_bounds__(128) rbgs_tiled_kernel(LevelC L, int color, const uint8_t* active) {
   const int b = blockIdx.z;
   if (active && !active[b]) return;
   constexpr int R = kTT + 2;
@@ -615,7 +631,7 @@ __global__ void __launch_bounds__(128) rbgs_tiled_kernel(LevelC L, Coup K, int c
   float acc[NB];
 #pragma unroll
   for (int r = 0; r < NB; ++r) acc[r] = 0.f;
-  nbr_trace_sum_p(K, L.qx, L.qy, gi > 0 ? xs + (size_t)(cell - 1) * NB : nullptr,
+  nbr_trace_sum_p(L.K, gi > 0 ? xs + (size_t)(cell - 1) * NB : nullptr,
                   gi + 1 < L.nx ? xs + (size_t)(cell + 1) * NB : nullptr,
                   gj > 0 ? xs + (size_t)(cell - R) * NB : nullptr,
                   gj + 1 < L.ny ? xs + (size_t)(cell + R) * NB : nullptr, acc);
@@ -625,16 +641,17 @@ __global__ void __launch_bounds__(128) rbgs_tiled_kernel(LevelC L, Coup K, int c
 #pragma unroll
   for (int r = 0; r < NB; ++r) res[r] -= acc[r];
   float out[NB];
-  matvec12((dsm ? reinterpret_cast<const float*>(dsh4) : dg) + (size_t)L.cls[c] * NB2, res, out);
+  const int k = L.cls[c];
+  apply_block(L, (dsm ? reinterpret_cast<const float*>(dsh4) : dg) + (size_t)k * NB2, k, res, out);
   lstore(xg, lh, c, color, out);
 }
 
-__global__ void residual_kernel(LevelC L, Coup K, const uint8_t* active) {
+__global__ void residual_kernel(LevelC L, const uint8_t* active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.nc) return;
-  residual_cell(L, K, b, c);
+  residual_cell(L, b, c);
 }
 
 __global__ void restrict_kernel(LevelC F, LevelC Cl, const uint8_t* active) {
@@ -656,7 +673,6 @@ __global__ void prolong_add_kernel(LevelC F, LevelC Cl, const uint8_t* active) {
 struct CoarseArgs {
   int lc, nL, nu;
   LevelC lv[kMaxLevels];
-  Coup K;
 };
 
 // The V-cycle from level lc down to the coarsest and back, one CTA per instance; phases are
@@ -670,7 +686,7 @@ __global__ void __launch_bounds__(512) coarse_vcycle_kernel(const CoarseArgs A, 
     const int hx2 = (L.nx + 1) / 2;
     for (int idx = tid; idx < hx2 * L.ny; idx += nt) {
       const int j = idx / hx2, i = 2 * (idx % hx2) + ((j + color) & 1);
-      if (i < L.nx) rbgs_cell(L, A.K, b, j * L.nx + i, L.dinv + (size_t)b * L.n_class * NB2);
+      if (i < L.nx) rbgs_cell(L, b, j * L.nx + i, L.dinv + (size_t)b * L.n_class * NB2);
     }
     __syncthreads();
   };
@@ -688,7 +704,7 @@ __global__ void __launch_bounds__(512) coarse_vcycle_kernel(const CoarseArgs A, 
       break;
     }
     for (int k = 0; k < A.nu; ++k) half_sweep(L, 0), half_sweep(L, 1);
-    for (int c = tid; c < L.nc; c += nt) residual_cell(L, A.K, b, c);
+    for (int c = tid; c < L.nc; c += nt) residual_cell(L, b, c);
     __syncthreads();
     const LevelC& Cl = A.lv[l + 1];
     for (int t = tid; t < Cl.nc * NB; t += nt) restrict_entry(L, Cl, b, t);
@@ -1045,7 +1061,6 @@ struct DsaState {
   int n_levels = 0, lc = 0;                     // lc: first level of the fused coarse cycle
   std::vector<int> lnx, lny, ncls;
   std::vector<std::vector<int32_t>> cls_h, mixed_h;
-  Coup K{};
   DevBuf<double> off64, diag64;                 // level 0 in FP64 (Krylov operator)
   std::vector<DevBuf<int32_t>*> cls, mixed;     // class per cell; mixed cells of each level
   std::vector<DevBuf<double>*> geo64;           // [144] per level
@@ -1073,15 +1088,17 @@ static Fine fine_of(rte_batch_t bt) {
   return Fine{s->off64.p, s->diag64.p, bt->disc->mat_id.p, bt->disc->n_mat};
 }
 
+static Coup couplings(const DsaMoments& m, double hx, double hy);
+
 static LevelC lvl_of(rte_batch_t bt, int l) {
   DsaState* s = bt->dsa;
   const rte_disc_s* d = bt->disc;
   LevelC L{};
   L.nx = s->lnx[l], L.ny = s->lny[l], L.nc = L.nx * L.ny, L.n_class = s->ncls[l];
+  L.n_pure = d->n_mat;
   L.cls = s->cls[l]->p;
   L.diag = s->diag32[l]->p, L.dinv = s->dinv32[l]->p;
-  L.qx = (float)(1.0 / std::sqrt(d->hx * (1 << l)));
-  L.qy = (float)(1.0 / std::sqrt(d->hy * (1 << l)));
+  L.K = couplings(d->mom, d->hx * (1 << l), d->hy * (1 << l));
   L.x = s->xl[l]->p, L.b = s->bl[l]->p, L.r = s->rl[l]->p;
   return L;
 }
@@ -1102,22 +1119,26 @@ static void level_blocks(const DsaMoments& mom, double hx, double hy, double off
   field_block(mom, DCx[0], DJx[0], DCy[0], DJy[0], 0.0, 0.0, true, geo);
 }
 
-// field couplings of the trace form of the neighbour blocks (level independent)
-static Coup couplings(const DsaMoments& m) {
+// field couplings of the trace form of the neighbour blocks on cells of size hx x hy: the
+// quadrature moments' 3 x 3 couplings divided by the cell size normal to the face
+static Coup couplings(const DsaMoments& m, double hx, double hy) {
   Coup K{};
-  const float W[9] = {(float)(-0.5 * m.abs_x), (float)(-1.5 * m.xx), 0.f,
-                      (float)(-0.5 * m.xx), (float)(-1.5 * m.abs3_x), 0.f,
-                      0.f, 0.f, (float)(-1.5 * m.yy_absx)};
-  const float E[9] = {(float)(-0.5 * m.abs_x), (float)(1.5 * m.xx), 0.f,
-                      (float)(0.5 * m.xx), (float)(-1.5 * m.abs3_x), 0.f,
-                      0.f, 0.f, (float)(-1.5 * m.yy_absx)};
-  const float S[9] = {(float)(-0.5 * m.abs_y), 0.f, (float)(-1.5 * m.yy),
-                      0.f, (float)(-1.5 * m.xx_absy), 0.f,
-                      (float)(-0.5 * m.yy), 0.f, (float)(-1.5 * m.abs3_y)};
-  const float N[9] = {(float)(-0.5 * m.abs_y), 0.f, (float)(1.5 * m.yy),
-                      0.f, (float)(-1.5 * m.xx_absy), 0.f,
-                      (float)(0.5 * m.yy), 0.f, (float)(-1.5 * m.abs3_y)};
-  for (int k = 0; k < 9; ++k) K.W[k] = W[k], K.E[k] = E[k], K.S[k] = S[k], K.N[k] = N[k];
+  const double W[9] = {-0.5 * m.abs_x, -1.5 * m.xx, 0.0,
+                       -0.5 * m.xx, -1.5 * m.abs3_x, 0.0,
+                       0.0, 0.0, -1.5 * m.yy_absx};
+  const double E[9] = {-0.5 * m.abs_x, 1.5 * m.xx, 0.0,
+                       0.5 * m.xx, -1.5 * m.abs3_x, 0.0,
+                       0.0, 0.0, -1.5 * m.yy_absx};
+  const double S[9] = {-0.5 * m.abs_y, 0.0, -1.5 * m.yy,
+                       0.0, -1.5 * m.xx_absy, 0.0,
+                       -0.5 * m.yy, 0.0, -1.5 * m.abs3_y};
+  const double N[9] = {-0.5 * m.abs_y, 0.0, 1.5 * m.yy,
+                       0.0, -1.5 * m.xx_absy, 0.0,
+                       0.5 * m.yy, 0.0, -1.5 * m.abs3_y};
+  for (int k = 0; k < 9; ++k) {
+    K.W[k] = (float)(W[k] / hx), K.E[k] = (float)(E[k] / hx);
+    K.S[k] = (float)(S[k] / hy), K.N[k] = (float)(N[k] / hy);
+  }
   return K;
 }
 
@@ -1147,7 +1168,6 @@ static int dsa_build_levels(rte_batch_t bt) {
   // (Running the whole cycle fused, one 512-thread CTA per instance, was measured slower than
   // level-by-level launches for the fine levels even with an instance per SM: 152 lattice
   // instances, DSA share 16% vs 14.5% of a step.)
-  s->K = couplings(d->mom);
   for (int l = 0; l < s->n_levels; ++l) {
     const int nx = s->lnx[l], ny = s->lny[l], nc = nx * ny;
     std::vector<int32_t> cls(nc), mixed;
@@ -1325,7 +1345,7 @@ static int vcycle(rte_batch_t bt, int l, const uint8_t* active, cudaStream_t st,
   const int B = bt->B;
   if (l >= s->lc) {  // the rest of the cycle in one launch, one CTA per instance
     CoarseArgs A{};
-    A.lc = l, A.nL = s->n_levels, A.nu = nu, A.K = s->K;
+    A.lc = l, A.nL = s->n_levels, A.nu = nu;
     for (int k = 0; k < s->n_levels; ++k) A.lv[k] = lvl_of(bt, k);
     coarse_vcycle_kernel<<<B, 512, 0, st>>>(A, active); RTE_NOTE_LAUNCH();
     RTE_CUDA_TRY(cudaGetLastError());
@@ -1340,11 +1360,11 @@ static int vcycle(rte_batch_t bt, int l, const uint8_t* active, cudaStream_t st,
   const dim3 gtile((L.nx + kTT - 1) / kTT, (L.ny + kTT - 1) / kTT, B);
   auto smooth = [&](int c0) {
     if (bt->dsa_tiled) {
-      rbgs_tiled_kernel<<<gtile, 128, 0, st>>>(L, s->K, c0, active); RTE_NOTE_LAUNCH();
-      rbgs_tiled_kernel<<<gtile, 128, 0, st>>>(L, s->K, 1 - c0, active); RTE_NOTE_LAUNCH();
+      rbgs_tiled_kernel<<<gtile, 128, 0, st>>>(L, c0, active); RTE_NOTE_LAUNCH();
+      rbgs_tiled_kernel<<<gtile, 128, 0, st>>>(L, 1 - c0, active); RTE_NOTE_LAUNCH();
     } else {
-      rbgs_kernel<<<gcol, 128, 0, st>>>(L, s->K, c0, active); RTE_NOTE_LAUNCH();
-      rbgs_kernel<<<gcol, 128, 0, st>>>(L, s->K, 1 - c0, active); RTE_NOTE_LAUNCH();
+      rbgs_kernel<<<gcol, 128, 0, st>>>(L, c0, active); RTE_NOTE_LAUNCH();
+      rbgs_kernel<<<gcol, 128, 0, st>>>(L, 1 - c0, active); RTE_NOTE_LAUNCH();
     }
   };
   // nu sweeps starting with colour c0: one temporally blocked launch, or 2 nu launches
@@ -1355,12 +1375,12 @@ static int vcycle(rte_batch_t bt, int l, const uint8_t* active, cudaStream_t st,
       const size_t bytes = fused_smem_bytes(2 * nu);
       RTE_TRY(fused_smem_attr(bytes));
       rbgs_fused_kernel<<<dim3((L.nx + kFT - 1) / kFT, (L.ny + kFT - 1) / kFT, B), 256, bytes, st>>>(
-          L, s->K, 2 * nu, c0, L.r, active); RTE_NOTE_LAUNCH();
+          L, 2 * nu, c0, L.r, active); RTE_NOTE_LAUNCH();
       std::swap(s->xl[l], s->rl[l]);  // the smoothed iterate is now the level's x
       L = lvl_of(bt, l);
     } else if (pro) {
-      rbgs_prolong_kernel<<<gcol, 128, 0, st>>>(L, *pro, s->K, c0, active); RTE_NOTE_LAUNCH();
-      rbgs_kernel<<<gcol, 128, 0, st>>>(L, s->K, 1 - c0, active); RTE_NOTE_LAUNCH();
+      rbgs_prolong_kernel<<<gcol, 128, 0, st>>>(L, *pro, c0, active); RTE_NOTE_LAUNCH();
+      rbgs_kernel<<<gcol, 128, 0, st>>>(L, 1 - c0, active); RTE_NOTE_LAUNCH();
       for (int k = 1; k < nu; ++k) smooth(c0);
     } else {
       for (int k = 0; k < nu; ++k) smooth(c0);
@@ -1369,15 +1389,15 @@ static int vcycle(rte_batch_t bt, int l, const uint8_t* active, cudaStream_t st,
   };
   if (first_done) {   // the rest of the first sweep (colour 1), then nu - 1 full sweeps
     if (bt->dsa_tiled) {
-      rbgs_tiled_kernel<<<gtile, 128, 0, st>>>(L, s->K, 1, active); RTE_NOTE_LAUNCH();
+      rbgs_tiled_kernel<<<gtile, 128, 0, st>>>(L, 1, active); RTE_NOTE_LAUNCH();
     } else {
-      rbgs_kernel<<<gcol, 128, 0, st>>>(L, s->K, 1, active); RTE_NOTE_LAUNCH();
+      rbgs_kernel<<<gcol, 128, 0, st>>>(L, 1, active); RTE_NOTE_LAUNCH();
     }
     for (int k = 1; k < nu; ++k) smooth(0);
   } else {
     RTE_TRY(smooth_nu(0, nullptr));
   }
-  residual_kernel<<<dim3((L.nc + 127) / 128, B), 128, 0, st>>>(L, s->K, active); RTE_NOTE_LAUNCH();
+  residual_kernel<<<dim3((L.nc + 127) / 128, B), 128, 0, st>>>(L, active); RTE_NOTE_LAUNCH();
   LevelC Cl = lvl_of(bt, l + 1);
   restrict_kernel<<<dim3((Cl.nc * NB + 255) / 256, B), 256, 0, st>>>(L, Cl, active); RTE_NOTE_LAUNCH();
   RTE_TRY(vcycle(bt, l + 1, active, st, nu));
@@ -1431,7 +1451,8 @@ __global__ void pack_first_half_kernel(LevelC L, const double* __restrict__ R, c
   lstore(L.b + (size_t)b * lstride(L.nc), half, c, col, v);
   if (col != 0) return;
   float out[NB];
-  matvec12((dsm ? reinterpret_cast<const float*>(dsh4) : dg) + (size_t)L.cls[c] * NB2, v, out);
+  const int k = L.cls[c];
+  apply_block(L, (dsm ? reinterpret_cast<const float*>(dsh4) : dg) + (size_t)k * NB2, k, v, out);
   lstore(L.x + (size_t)b * lstride(L.nc), half, c, col, out);
 }
 
@@ -1457,7 +1478,7 @@ __global__ void extract_rho32_kernel(const float* x, double* drho, int nc, int n
 }
 
 // residual on level 0 against an explicit right-hand side and iterate: r0 = borig - A0 xtot
-__global__ void residual_ext_kernel(LevelC L, Coup K, const float* bvec, const float* xv, float* r,
+__global__ void residual_ext_kernel(LevelC L, const float* bvec, const float* xv, float* r,
                                     const uint8_t* active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
@@ -1465,7 +1486,7 @@ __global__ void residual_ext_kernel(LevelC L, Coup K, const float* bvec, const f
   if (c >= L.nc) return;
   LevelC M = L;
   M.b = const_cast<float*>(bvec), M.x = const_cast<float*>(xv), M.r = r;
-  residual_cell(M, K, b, c);
+  residual_cell(M, b, c);
 }
 
 // Stationary multigrid: k V-cycles on the FP32 system, x <- x + V(b - A x), no host round trip.
@@ -1496,7 +1517,7 @@ static int dsa2d_vcycles(rte_batch_t bt, const double* R, double* drho, int k,
       RTE_CUDA_TRY(cudaMemcpyAsync(s->bl[0]->p, s->borig.p, sizeof(float) * (size_t)B * per,
                                    cudaMemcpyDeviceToDevice, st));
     } else {
-      residual_ext_kernel<<<dim3((nc + 127) / 128, B), 128, 0, st>>>(L0, s->K, s->borig.p, s->xtot.p,
+      residual_ext_kernel<<<dim3((nc + 127) / 128, B), 128, 0, st>>>(L0, s->borig.p, s->xtot.p,
                                                                    s->bl[0]->p, active); RTE_NOTE_LAUNCH();
     }
     RTE_TRY(vcycle(bt, 0, active, st, bt->dsa_nu));
