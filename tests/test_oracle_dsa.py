@@ -86,3 +86,29 @@ def test_converged_solution_independent_of_correction():
         r = sisa(tr, np.zeros(tr.n_dof), 1e-14, 3000, sa, dsa=ConsistentDSA(tr))
         assert r["converged"]
         np.testing.assert_allclose(r["rho"], ref, atol=1e-11 * np.abs(ref).max())
+
+
+def test_2d_diagonal_blocks_couple_only_equal_parities():
+    """Every cell's 12 x 12 diagonal block of the 2D DSA system (fields drho, dJx, dJy; moments
+    k = kx + 2 ky) couples only unknowns of equal parities (kx xor [J_x], ky xor [J_y]) -- four
+    3 x 3 blocks -- on a random material map and a non-square mesh, for interior, edge and corner
+    cells, and so does its inverse.  The GPU smoother applies single-material blocks that way."""
+    p = inputs.random_2d(6, 8, 2, 3, seed=9, ny=5)
+    tr = Transport(p)
+    M = ConsistentDSA(tr).M.tocsr()
+    N = tr.n_dof
+
+    def par(f, k):
+        return ((k & 1) ^ (f == 1), (k >> 1) ^ (f == 2))
+
+    unk = [(f, k) for f in range(3) for k in range(4)]
+    same = np.array([[par(*a) == par(*b) for b in unk] for a in unk])
+    assert same.sum() == 36
+    for c in range(tr.n_dof // 4):
+        idx = [f * N + 4 * c + k for f, k in unk]
+        D = M[idx][:, idx].toarray()
+        Di = np.linalg.inv(D)
+        # zero up to the rounding of the oracle's quadrature-built operators
+        assert np.abs(D[~same]).max() <= 1e-14 * np.abs(D).max(), c
+        assert np.abs(Di[~same]).max() <= 1e-14 * np.abs(Di).max(), c
+        assert np.count_nonzero(np.abs(D[same]) > 1e-8 * np.abs(D).max()) > 12   # not diagonal
