@@ -530,6 +530,23 @@ int rte_solve_lockstep(int n, const rte_batch_t* batches, const rte_solve_opts* 
                        const rte_rom_t* roms, double* const* rho, rte_solve_report* const* reports,
                        void* const* streams);
 
+/* rte_solve_many with the SWEEPS of all batches on one internal stream of the highest priority, one
+ * after another in the order the batches' stop tests come back, and each batch's stop test and
+ * corrections (Alg. 1 / Alg. 2: DSA V-cycles, ROM products) on its own stream: while one batch
+ * sweeps, the corrections of the others run beside it.  The FP64 sweep is bound by the FP64 pipe and
+ * leaves the FP32 pipe and the memory system mostly idle, so splitting one batch of instances into
+ * sub-batches (separate rte_batch_t of one discretisation, each with its own ROM handle, e.g. from
+ * rte_rom_save / rte_rom_load) and solving them this way hides most of the correction time.  A
+ * batch's corrections are issued only after the sweep queued behind its own has been dispatched
+ * (sweeps placed on a GPU busy with other kernels crowd onto some SM sub-partitions and run up to
+ * 3x slower).  Every batch runs exactly the iterations it runs under rte_solve_many; the results
+ * equal rte_solve_many's bit for bit.  Arguments and errors as in rte_solve_many; streams: n
+ * distinct streams for the corrections (NULL: the legacy default stream, which serialises them
+ * with everything else and gives no overlap).  Synchronous. */
+int rte_solve_interleaved(int n, const rte_batch_t* batches, const rte_solve_opts* opts,
+                          const rte_rom_t* roms, double* const* rho, rte_solve_report* const* reports,
+                          void* const* streams);
+
 /* ---- serving: continuous batching of parametric solves ---------------------------------- */
 
 typedef struct rte_server_s* rte_server_t;

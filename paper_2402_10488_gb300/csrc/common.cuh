@@ -195,6 +195,9 @@ struct rte_batch_s {
   rte::DevBuf<uint8_t> slot_mask;         // [B] instances touched by the last slot upload
   std::vector<uint8_t> slot_set;          // parameters uploaded for this instance
   cudaEvent_t stage_ev = nullptr;         // the last upload's copies have been issued before it
+  // when set, the next sweep launch records it on its stream right before its first sweep kernel
+  // and clears it (rte_solve_interleaved: the host learns that the sweep has been dispatched)
+  cudaEvent_t started_ev = nullptr;
   // optional phase timing with CUDA events on the launching stream (rte_batch_timing)
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> sweep_ev;
@@ -368,6 +371,8 @@ struct SiState {
   unsigned long long* hn = nullptr;   // pinned [2B] stop-test norms (ordered bit patterns)
   DevBuf<uint8_t> dm;                 // device copy of hm
   cudaEvent_t ev = nullptr;           // recorded after the norms copy
+  cudaEvent_t started = nullptr;      // rte_solve_interleaved: recorded before the sweep kernel
+  cudaEvent_t corr = nullptr;         // rte_solve_interleaved: recorded after the corrections
   std::vector<uint8_t> act, lowp, done;
   std::vector<uint8_t> inner;         // the next sweep is an FP32 correction sweep
   std::vector<uint8_t> swept;         // swept in the launch in flight (not waiting, gang_wait)
@@ -382,7 +387,7 @@ struct SiState {
   int n_active() const;
   ~SiState();
 };
-int si_launch(SiState& s, cudaStream_t st, double* psi_cur);
+int si_launch(SiState& s, cudaStream_t st, double* psi_cur, cudaEvent_t wait_ev = nullptr);
 int event_ready(cudaEvent_t ev, bool* ready);
 int si_finish(SiState& s, cudaStream_t st, double* history);
 }  // namespace rte

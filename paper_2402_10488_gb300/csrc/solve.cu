@@ -20,6 +20,7 @@
 // start at different iterations (serving), and si_launch / si_finish only enqueue work, so one
 // host thread keeps several batches of different discretisations busy on their own streams
 // (rte_solve_many, the serving loop).
+#include <deque>
 #include <thread>
 
 #include "common.cuh"
@@ -87,12 +88,16 @@ SiState::~SiState() {
   if (hm) cudaFreeHost(hm);
   if (hn) cudaFreeHost(hn);
   if (ev) cudaEventDestroy(ev);
+  if (started) cudaEventDestroy(started);
+  if (corr) cudaEventDestroy(corr);
 }
 
 // One sweep of every running instance: rho^(l,*) = L rho^(l-1) + b (FP32 for instances still in
 // the low-precision phase or inside an outer residual-correction step), then the asynchronous copy
-// of the stop-test norms.
-int si_launch(SiState& s, cudaStream_t st, double* psi_cur) {
+// of the stop-test norms.  With wait_ev the stream first waits for that event (the batch's
+// corrections when they run on another stream); with s.started set, that event is recorded right
+// before the first sweep kernel.
+int si_launch(SiState& s, cudaStream_t st, double* psi_cur, cudaEvent_t wait_ev) {
   rte_batch_t bt = s.bt;
   const int B = s.B;
   const size_t nb = (size_t)B * bt->disc->n_dof;
@@ -122,7 +127,9 @@ int si_launch(SiState& s, cudaStream_t st, double* psi_cur) {
     if (h_hi[b]) s.waited[b] = 0;
   }
   if (n_lo + n_hi == 0) return RTE_OK;
+  if (wait_ev) RTE_CUDA_TRY(cudaStreamWaitEvent(st, wait_ev, 0));
   RTE_CUDA_TRY(cudaMemcpyAsync(s.dm.p, s.hm, 4 * (size_t)B, cudaMemcpyHostToDevice, st));
+  bt->started_ev = s.started;
   if (n_lo == 0) {
     RTE_TRY(sweep_launch(bt, rho_prev, rho_star, psi_cur, 1, s.dm.p, st, true, n_hi));
   } else {
@@ -134,6 +141,7 @@ int si_launch(SiState& s, cudaStream_t st, double* psi_cur) {
     if (n_hi > 0)
       RTE_TRY(sweep_launch(bt, rho_prev, rho_star, psi_cur, 1, s.dm.p + 2 * B, st, true, n_hi, false));
   }
+  bt->started_ev = nullptr;
   RTE_CUDA_TRY(cudaMemcpyAsync(s.hn, bt->norms.p, sizeof(unsigned long long) * 2 * B,
                                cudaMemcpyDeviceToHost, st));
   RTE_CUDA_TRY(cudaEventRecord(s.ev, st));
@@ -391,21 +399,150 @@ extern "C" int rte_solve(rte_batch_t b, const rte_solve_opts* o, rte_rom_t rom_c
   return run_si(b, o, rom_c, rho, reports, history, (cudaStream_t)stream, nullptr, nullptr, 0);
 }
 
-extern "C" int rte_solve_many(int n, const rte_batch_t* batches, const rte_solve_opts* opts,
-                              const rte_rom_t* roms, double* const* rho,
-                              rte_solve_report* const* reports, void* const* streams) {
-  if (n < 1 || !batches || !opts || !rho) return fail(RTE_EINVAL, "rte_solve_many: null argument");
+// Arguments of rte_solve_many / rte_solve_interleaved.
+static int check_many(const char* who, int n, const rte_batch_t* batches, const rte_solve_opts* opts,
+                      const rte_rom_t* roms, double* const* rho) {
+  const std::string w(who);
+  if (n < 1 || !batches || !opts || !rho) return fail(RTE_EINVAL, w + ": null argument");
   for (int k = 0; k < n; ++k) {
-    if (!batches[k] || !rho[k]) return fail(RTE_EINVAL, "rte_solve_many: null batch or rho");
+    if (!batches[k] || !rho[k]) return fail(RTE_EINVAL, w + ": null batch or rho");
     if (batches[k]->disc->device != batches[0]->disc->device)
-      return fail(RTE_EINVAL, "rte_solve_many: batches on different devices");
+      return fail(RTE_EINVAL, w + ": batches on different devices");
     for (int j = 0; j < k; ++j) {
-      if (batches[j] == batches[k]) return fail(RTE_EINVAL, "rte_solve_many: batch listed twice");
+      if (batches[j] == batches[k]) return fail(RTE_EINVAL, w + ": batch listed twice");
       if (roms && roms[k] && roms[j] == roms[k])
-        return fail(RTE_EINVAL, "rte_solve_many: a ROM serves one batch at a time");
+        return fail(RTE_EINVAL, w + ": a ROM serves one batch at a time");
     }
     RTE_TRY(check_opts(batches[k], &opts[k], roms ? roms[k] : nullptr));
   }
+  return RTE_OK;
+}
+
+// The end of a multi-batch solve: verification, stream synchronisation, reports, status.
+static int finish_many(std::vector<SiState>& S, const std::vector<cudaStream_t>& st,
+                       const rte_solve_opts* opts, const rte_rom_t* roms,
+                       rte_solve_report* const* reports) {
+  const int n = (int)S.size();
+  int status = RTE_OK;
+  for (int k = 0; k < n; ++k) {
+    if (opts[k].verify) RTE_TRY(verify_results(S[k], st[k]));
+    RTE_CUDA_TRY(cudaStreamSynchronize(st[k]));
+    if (roms && roms[k] && opts[k].rom_bf16) {
+      int tc = 0;
+      RTE_TRY(rom_tc_status(roms[k], &tc));
+      if (tc) return fail(RTE_ETIMEOUT, "BF16 ROM product: a device-side wait gave up");
+    }
+    for (int b = 0; b < S[k].B; ++b) {
+      if (S[k].status[b] != RTE_OK) status = S[k].status[b];
+      if (reports && reports[k]) reports[k][b] = S[k].rep[b];
+    }
+  }
+  return status;
+}
+
+// Whether the next sweep of s is a wide FP64 launch: every running instance sweeps in FP64 and at
+// least half the batch is running.  Such launches keep every SM sub-partition's FP64 pipe busy on
+// their own; narrower ones (the convergence tail) and FP32 sweeps are latency-bound.
+static bool wide_fp64(const SiState& s) {
+  int hi = 0;
+  for (int b = 0; b < s.B; ++b) {
+    if (!s.act[b]) continue;
+    if (s.lowp[b] || s.inner[b]) return false;
+    ++hi;
+  }
+  return 2 * hi >= s.B;
+}
+
+// rte_solve_many with the wide FP64 sweeps of all batches on one stream of the highest priority,
+// one after another, and each batch's stop test and corrections on its own stream: while one batch
+// sweeps, the others' corrections (DSA V-cycles on the FP32 pipe and the memory system, ROM
+// products) run beside it on the SMs that the FP64-bound sweep leaves idle.  Narrow and FP32
+// sweeps, latency-bound, run on the batch's own stream, concurrently with the others.  A sweep's
+// one-warp CTAs must be placed on an idle GPU -- dispatched while other kernels fill the SMs they
+// crowd onto some SM sub-partitions, whose FP64 pipes then carry two to three times their share
+// (measured: a half-batch sweep 2.45 ms alone, 7.1 ms dispatched together with a V-cycle) -- so
+// a batch's corrections are issued only once the wide sweep queued next on the priority stream
+// has recorded `started` (after its cell sources, before its sweep kernel).
+extern "C" int rte_solve_interleaved(int n, const rte_batch_t* batches, const rte_solve_opts* opts,
+                                     const rte_rom_t* roms, double* const* rho,
+                                     rte_solve_report* const* reports, void* const* streams) {
+  RTE_TRY(check_many("rte_solve_interleaved", n, batches, opts, roms, rho));
+  DeviceGuard g(batches[0]->disc->device);
+  int prio_low = 0, prio_high = 0;
+  RTE_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+  cudaStream_t sw = nullptr;
+  RTE_CUDA_TRY(cudaStreamCreateWithPriority(&sw, cudaStreamNonBlocking, prio_high));
+  struct StreamGuard {
+    cudaStream_t s;
+    ~StreamGuard() {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+  } sg{sw};
+  std::vector<SiState> S(n);
+  std::vector<cudaStream_t> st(n);
+  std::deque<int> wide;   // batches whose sweep in flight is queued on sw, in queue order
+  // queue the next sweep of batch k behind its corrections: wide FP64 sweeps on sw, others on st[k]
+  auto launch = [&](int k) -> int {
+    if (wide_fp64(S[k])) {
+      RTE_CUDA_TRY(cudaEventRecord(S[k].corr, st[k]));
+      RTE_TRY(si_launch(S[k], sw, nullptr, S[k].corr));
+      if (S[k].in_flight) wide.push_back(k);
+    } else {
+      RTE_TRY(si_launch(S[k], st[k], nullptr));
+    }
+    return RTE_OK;
+  };
+  for (int k = 0; k < n; ++k) {
+    rte_batch_t bt = batches[k];
+    rte_rom_t rom = roms ? roms[k] : nullptr;
+    st[k] = streams ? (cudaStream_t)streams[k] : nullptr;
+    RTE_TRY(S[k].init(bt, opts[k], rom, rho[k]));
+    if (!S[k].started) RTE_CUDA_TRY(cudaEventCreateWithFlags(&S[k].started, cudaEventDisableTiming));
+    if (!S[k].corr) RTE_CUDA_TRY(cudaEventCreateWithFlags(&S[k].corr, cudaEventDisableTiming));
+    RTE_CUDA_TRY(cudaMemcpyAsync(bt->work.p, rho[k], sizeof(double) * bt->B * bt->disc->n_dof,
+                                 cudaMemcpyDeviceToDevice, st[k]));
+    for (int b = 0; b < bt->B; ++b) S[k].begin(b, opts[k].eps);
+    if (rom) RTE_TRY(rom_prepare(rom, bt, st[k]));
+    RTE_TRY(launch(k));
+  }
+  int running = n;
+  while (running > 0) {
+    bool progress = false;
+    running = 0;
+    for (int k = 0; k < n; ++k) {
+      if (!S[k].in_flight) continue;
+      bool ready = false;
+      RTE_TRY(event_ready(S[k].ev, &ready));
+      if (ready) {
+        // the wide sweep that runs next on sw -- the one queued after k's, or the oldest one when
+        // k swept on its own stream (sw runs in order, so the ones before k's have finished) --
+        // is dispatched before these corrections are issued; it waits only for work already
+        // issued, so this wait ends
+        int next = -1;
+        for (auto it = wide.begin(); it != wide.end(); ++it)
+          if (*it == k) {
+            it = wide.erase(it);
+            if (it != wide.end()) next = *it;
+            break;
+          }
+        if (next < 0 && !wide.empty() && wide.front() != k) next = wide.front();
+        if (next >= 0) RTE_CUDA_TRY(cudaEventSynchronize(S[next].started));
+        RTE_TRY(si_finish(S[k], st[k], nullptr));
+        RTE_TRY(launch(k));
+        progress = true;
+      }
+      running += S[k].in_flight;
+    }
+    if (!progress && running > 0) std::this_thread::yield();
+  }
+  return finish_many(S, st, opts, roms, reports);
+}
+
+extern "C" int rte_solve_many(int n, const rte_batch_t* batches, const rte_solve_opts* opts,
+                              const rte_rom_t* roms, double* const* rho,
+                              rte_solve_report* const* reports, void* const* streams) {
+  RTE_TRY(check_many("rte_solve_many", n, batches, opts, roms, rho));
   DeviceGuard g(batches[0]->disc->device);
   std::vector<SiState> S(n);
   std::vector<cudaStream_t> st(n);
@@ -438,21 +575,7 @@ extern "C" int rte_solve_many(int n, const rte_batch_t* batches, const rte_solve
     }
     if (!progress && running > 0) std::this_thread::yield();
   }
-  int status = RTE_OK;
-  for (int k = 0; k < n; ++k) {
-    if (opts[k].verify) RTE_TRY(verify_results(S[k], st[k]));
-    RTE_CUDA_TRY(cudaStreamSynchronize(st[k]));
-    if (roms && roms[k] && opts[k].rom_bf16) {
-      int tc = 0;
-      RTE_TRY(rom_tc_status(roms[k], &tc));
-      if (tc) return fail(RTE_ETIMEOUT, "BF16 ROM product: a device-side wait gave up");
-    }
-    for (int b = 0; b < S[k].B; ++b) {
-      if (S[k].status[b] != RTE_OK) status = S[k].status[b];
-      if (reports && reports[k]) reports[k][b] = S[k].rep[b];
-    }
-  }
-  return status;
+  return finish_many(S, st, opts, roms, reports);
 }
 
 // rte_solve_many with every batch iterating in lockstep: at each iteration one sweep launch covers
@@ -463,20 +586,11 @@ extern "C" int rte_solve_many(int n, const rte_batch_t* batches, const rte_solve
 extern "C" int rte_solve_lockstep(int n, const rte_batch_t* batches, const rte_solve_opts* opts,
                                   const rte_rom_t* roms, double* const* rho,
                                   rte_solve_report* const* reports, void* const* streams) {
-  if (n < 1 || !batches || !opts || !rho) return fail(RTE_EINVAL, "rte_solve_lockstep: null argument");
+  RTE_TRY(check_many("rte_solve_lockstep", n, batches, opts, roms, rho));
   for (int k = 0; k < n; ++k) {
-    if (!batches[k] || !rho[k]) return fail(RTE_EINVAL, "rte_solve_lockstep: null batch or rho");
-    if (batches[k]->disc->device != batches[0]->disc->device)
-      return fail(RTE_EINVAL, "rte_solve_lockstep: batches on different devices");
     if (batches[k]->disc->dim != 2) return fail(RTE_EINVAL, "rte_solve_lockstep: 2D batches only");
     if (opts[k].fp32_switch > 0.0 || opts[k].refine_kappa > 0.0)
       return fail(RTE_EINVAL, "rte_solve_lockstep: FP64 sweeps only (no precision variant)");
-    for (int j = 0; j < k; ++j) {
-      if (batches[j] == batches[k]) return fail(RTE_EINVAL, "rte_solve_lockstep: batch listed twice");
-      if (roms && roms[k] && roms[j] == roms[k])
-        return fail(RTE_EINVAL, "rte_solve_lockstep: a ROM serves one batch at a time");
-    }
-    RTE_TRY(check_opts(batches[k], &opts[k], roms ? roms[k] : nullptr));
   }
   DeviceGuard g(batches[0]->disc->device);
   std::vector<SiState> S(n);
@@ -542,19 +656,5 @@ extern "C" int rte_solve_lockstep(int n, const rte_batch_t* batches, const rte_s
       RTE_CUDA_TRY(cudaEventRecord(done[k], st[k]));
     }
   }
-  int status = RTE_OK;
-  for (int k = 0; k < n; ++k) {
-    if (opts[k].verify) RTE_TRY(verify_results(S[k], st[k]));
-    RTE_CUDA_TRY(cudaStreamSynchronize(st[k]));
-    if (roms && roms[k] && opts[k].rom_bf16) {
-      int tc = 0;
-      RTE_TRY(rom_tc_status(roms[k], &tc));
-      if (tc) return fail(RTE_ETIMEOUT, "BF16 ROM product: a device-side wait gave up");
-    }
-    for (int b = 0; b < S[k].B; ++b) {
-      if (S[k].status[b] != RTE_OK) status = S[k].status[b];
-      if (reports && reports[k]) reports[k][b] = S[k].rep[b];
-    }
-  }
-  return status;
+  return finish_many(S, st, opts, roms, reports);
 }

@@ -759,6 +759,14 @@ static int kba_warps(const rte_disc_s* d, int n_sm, long long ctas) {
   return best_cost < 0.9 * single ? best : 1;
 }
 
+// Records bt->started_ev (when set) on the sweep's stream and clears it (see rte_batch_s).
+static int note_started(rte_batch_t bt, cudaStream_t st) {
+  if (!bt->started_ev) return RTE_OK;
+  RTE_CUDA_TRY(cudaEventRecord(bt->started_ev, st));
+  bt->started_ev = nullptr;
+  return RTE_OK;
+}
+
 int sweep_launch(rte_batch_t bt, const double* rho_in, double* rho_out, double* psi_out,
                  int with_source, const uint8_t* active, cudaStream_t st, bool fuse_norms,
                  int n_active, bool zero_norms) {
@@ -777,6 +785,7 @@ int sweep_launch(rte_batch_t bt, const double* rho_in, double* rho_out, double* 
     cell_source_kernel<<<dim3((d->n_cells + 127) / 128, bt->B), 128, 0, st>>>(
         rho_in, bt->S.p, bt->sigma_s.p, bt->G0.p, d->mat_id.p, active, d->n_cells, d->n_mat,
         with_source); RTE_NOTE_LAUNCH();
+    RTE_TRY(note_started(bt, st));
     Sweep2DArgs A{bt->S.p,      bt->partial.p, psi_out,        active,      bt->tables.p,
                   bt->sigma_s.p, bt->G0.p,     bt->inflow.p,   d->mat_id.p, d->dir_dev.p,
                   gdev,         d->nx,         d->ny,          d->n_cells,  d->n_dof,
@@ -807,6 +816,7 @@ int sweep_launch(rte_batch_t bt, const double* rho_in, double* rho_out, double* 
                   bt->G0.p,    bt->inflow.p,  d->mat_id.p, d->mat_r.p, d->dir_dev.p, bt->B, d->nx,
                   d->n_dof,    d->n_mat,      d->n_dirs, with_source};
     const int n = bt->B * d->n_dirs;
+    RTE_TRY(note_started(bt, st));
     sweep1d_kernel<<<(n + 63) / 64, 64, 0, st>>>(A); RTE_NOTE_LAUNCH();
     RTE_CUDA_TRY(cudaGetLastError());
   }
@@ -1370,6 +1380,7 @@ int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, cons
   cell_source32_kernel<<<dim3((d->n_cells + 127) / 128, bt->B), 128, 0, st>>>(
       rho_in, bt->S32.p, bt->sigma_s.p, bt->G0.p, d->mat_id.p, active, d->n_cells, d->n_mat, 1,
       inner, x0); RTE_NOTE_LAUNCH();
+  RTE_TRY(note_started(bt, st));
   Sweep2D32Args A{bt->S32.p,  bt->partial32.p, active,   inner,    bt->tables32.p, bt->inflow.p,
                   d->mat_id.p, d->dir_dev.p,   gdev,     d->nx,          d->ny,
                   d->n_cells, d->n_dof,        d->n_mat, d->n_dirs,      n_groups,

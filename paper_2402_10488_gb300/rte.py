@@ -61,6 +61,7 @@ SIGNATURES = {
     "rte_rom_load": (_I, [_P, ctypes.c_char_p, _P]),
     "rte_solve_many": (_I, [_I, _P, _P, _P, _P, _P, _P]),
     "rte_solve_lockstep": (_I, [_I, _P, _P, _P, _P, _P, _P]),
+    "rte_solve_interleaved": (_I, [_I, _P, _P, _P, _P, _P, _P]),
     "rte_server_create": (_I, [_I, _P]),
     "rte_server_add_bucket": (_I, [_P, _P, _P, _P, _P, _P]),
     "rte_server_start": (_I, [_P]),
@@ -444,11 +445,14 @@ class Batch:
             pass
 
 
-def solve_many(batches, rhos, opts, roms=None, streams=None, lockstep=False):
+def solve_many(batches, rhos, opts, roms=None, streams=None, lockstep=False, interleaved=False):
     """rte_solve_many: batches[k] solved from rhos[k] (device tensors, overwritten) with opts[k]
     (rte_solve_opts from solve_opts()), optional roms[k] and streams[k].  lockstep=True runs
-    rte_solve_lockstep instead (one sweep launch over all batches per iteration).  Returns per-batch
-    report lists and the status."""
+    rte_solve_lockstep instead (one sweep launch over all batches per iteration), interleaved=True
+    rte_solve_interleaved (the sweeps one after another on a priority stream, each batch's
+    corrections beside the next batch's sweep).  Returns per-batch report lists and the status."""
+    if lockstep and interleaved:
+        raise ValueError("lockstep and interleaved exclude each other")
     n = len(batches)
     bh = (_P * n)(*[b.h for b in batches])
     oa = (_SolveOpts * n)(*opts)
@@ -457,7 +461,8 @@ def solve_many(batches, rhos, opts, roms=None, streams=None, lockstep=False):
     rp = (_P * n)(*[ctypes.cast(r, _P) for r in reps])
     ro = None if roms is None else (_P * n)(*[None if r is None else r.h for r in roms])
     sa = None if streams is None else (_P * n)(*[_stream(s) for s in streams])
-    fn = lib().rte_solve_lockstep if lockstep else lib().rte_solve_many
+    fn = (lib().rte_solve_lockstep if lockstep else
+          lib().rte_solve_interleaved if interleaved else lib().rte_solve_many)
     st = check(fn(n, bh, oa, ro, rh, rp, sa), allow=(RTE_ENOCONV,))
     return [[_report(r) for r in rr] for rr in reps], st
 

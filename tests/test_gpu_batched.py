@@ -341,3 +341,58 @@ def test_rom_save_load_roundtrip(served, tmp_path):
     other = rte.Disc(inputs.lattice_test(24, 32, 1))
     with pytest.raises(rte.RTEError):
         rte.Rom.load(other, path)
+
+
+@pytest.mark.parametrize("variant", ["romsad", "refine"])
+def test_interleaved_sub_batches_equal_the_whole_batch(served, variant, tmp_path):
+    """rte_solve_interleaved over sub-batches of one discretisation (each with its own copy of the
+    correction ROM) returns bit for bit what rte_solve_many returns for them, and what rte_solve
+    returns for the whole batch: every instance runs its own Alg. 1 / Alg. 2 iterations, the sweeps
+    on the priority stream only change when they run.  Fixed decomposition (4 directions per warp);
+    the precision variant without gang waits, which couple the instances of one batch."""
+    rte, disc0, rp, rc = served
+    path = str(tmp_path / "rom_c.bin")
+    rc.save(path)
+    roms = [rc, rte.Rom.load(disc0, path), rte.Rom.load(disc0, path)]
+    test = inputs.lattice_test(16, 16, 7)
+    kw = _romsad_opts(rc)
+    if variant == "refine":
+        kw.update(fp32_switch=1e-5, refine_kappa=0.1, refine_inner=8, gang_wait=0)
+    whole = rte.Batch(disc0, 7)
+    whole.tune(4)
+    whole.set_params(test)
+    r_whole = torch.zeros((7, test.n_dof), dtype=torch.float64, device="cuda")
+    rep_whole, _, _ = whole.solve(r_whole, 1e-10, rom_c=rc, **kw)
+    torch.cuda.synchronize()
+    splits = [(0, 3), (3, 5), (5, 7)]
+    for inter in (False, True):
+        subs, rhos = [], []
+        for lo, hi in splits:
+            b = rte.Batch(disc0, hi - lo)
+            b.tune(4)
+            b.set_params(inputs.lattice_test(16, 16, hi - lo, first=lo))
+            subs.append(b)
+            rhos.append(torch.zeros((hi - lo, test.n_dof), dtype=torch.float64, device="cuda"))
+        opts = [rte.solve_opts(1e-10, **kw) for _ in splits]
+        streams = [torch.cuda.Stream() for _ in splits]
+        torch.cuda.synchronize()
+        reps, st = rte.solve_many(subs, rhos, opts, roms=roms, streams=streams, interleaved=inter)
+        torch.cuda.synchronize()
+        assert st == rte.RTE_OK
+        rho = torch.cat(rhos).cpu().numpy()
+        assert np.array_equal(rho, r_whole.cpu().numpy()), inter
+        for x, y in zip([x for rr in reps for x in rr], rep_whole):
+            assert all(x[k] == y[k] for k in ("n_sweep", "n_romsa", "n_dsa", "n_sweep32",
+                                               "converged")), (inter, x, y)
+
+
+def test_interleaved_rejects_bad_arguments(served):
+    rte, disc0, rp, rc = served
+    b = rte.Batch(disc0, 2)
+    b.set_params(inputs.lattice_test(16, 16, 2))
+    rho = torch.zeros((2, b.disc.n_dof), dtype=torch.float64, device="cuda")
+    o = rte.solve_opts(1e-8, rte.SA_DSA, rel=True, max_iter=50, dsa_rtol=0.0, dsa_max_it=1)
+    with pytest.raises(rte.RTEError):
+        rte.solve_many([b, b], [rho, rho], [o, o], interleaved=True)
+    with pytest.raises(ValueError):
+        rte.solve_many([b], [rho], [o], lockstep=True, interleaved=True)
