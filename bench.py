@@ -22,6 +22,7 @@ import hashlib
 import json
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -98,8 +99,8 @@ def parse():
     ap.add_argument("--refine-switch", type=float, default=1e-5,
                     help="romsad_refine: FP32 sweeps (with sources) until the relative change is "
                          "below this, then the FP64 outer residual correction")
-    ap.add_argument("--methods", default="romsad,si_dsa,romig,romig_romsad,romsad_mixed,"
-                                         "romsad_refine,pgmres,romig_pgmres")
+    ap.add_argument("--methods", default="romsad,romsad_interleaved,si_dsa,romig,romig_romsad,"
+                                         "romsad_mixed,romsad_refine,pgmres,romig_pgmres")
     ap.add_argument("--gmres-rtol", type=float, default=1e-7,
                     help="pgmres: relative residual of the preconditioned system")
     ap.add_argument("--profile-window", action="store_true",
@@ -312,6 +313,26 @@ def run_ours(a, ws, rank, local):
     batch.set_params(test)
     tuned = batch.autotune() if a.dpw < 0 else None
     n_dof = disc.n_dof
+    # romsad_interleaved: the same instances as two halves (separate batches, each with its own copy
+    # of the correction ROM) solved by rte_solve_interleaved
+    halves, half_roms, half_streams = [], [], []
+    if "romsad_interleaved" in methods:
+        h = B // 2
+        seeds = test_seeds(rank, B)
+        with tempfile.TemporaryDirectory() as tmp:
+            rom_c.save(os.path.join(tmp, "rom_c.bin"))
+            half_roms = [rom_c, rte.Rom.load(disc, os.path.join(tmp, "rom_c.bin"))]
+        for lo, hi in ((0, h), (h, B)):
+            hb = rte.Batch(disc, hi - lo)
+            hb.tune(max(a.dpw, 0))
+            hb.dsa_smoothing(a.dsa_nu)
+            if a.dsa_smoother >= 0:
+                hb.dsa_smoother(a.dsa_smoother)
+            hb.set_params(inputs.lattice(a.n, a.angles, seeds[lo:hi], nvz))
+            if a.dpw < 0:
+                hb.autotune()
+            halves.append((lo, hi, hb))
+        half_streams = [torch.cuda.Stream() for _ in halves]
     # tightly converged references (untimed)
     ref = torch.zeros((B, n_dof), dtype=torch.float64, device="cuda")
     rep_ref, _, _ = batch.solve(ref, 1e-13, sa=rte.SA_DSA, rel=True, max_iter=400, dsa_rtol=1e-3)
@@ -325,7 +346,25 @@ def run_ours(a, ws, rank, local):
     par_host = [t.cpu().pin_memory() for t in par_dev]
     par_in = [torch.empty_like(t) for t in par_dev]
 
+    def step_interleaved(rho):
+        # the halves' parameters from the same resident tensors, then both halves solved together
+        for lo, hi, hb in halves:
+            hb.set_params_device(*[t[lo:hi] for t in par_dev])
+        rho.zero_()
+        cur = torch.cuda.current_stream()
+        for s_ in half_streams:
+            s_.wait_stream(cur)
+        opts = [rte.solve_opts(a.eps, rte.SA_ROMSAD, rel=True, max_iter=400, theta=5,
+                               eps_romsad=eps_romsad, dsa_rtol=a.dsa_rtol,
+                               dsa_max_it=a.dsa_vcycles if a.dsa_rtol == 0 else 100)
+                for _ in halves]
+        reps, _ = rte.solve_many([hb for _, _, hb in halves], [rho[lo:hi] for lo, hi, _ in halves],
+                                 opts, roms=half_roms, streams=half_streams, interleaved=True)
+        return [x for rr in reps for x in rr]
+
     def step(method, rho, host_out=None):
+        if method == "romsad_interleaved":
+            return step_interleaved(rho)
         if host_out is not None:
             for d, h in zip(par_in, par_host):
                 d.copy_(h, non_blocking=True)
@@ -371,7 +410,9 @@ def run_ours(a, ws, rank, local):
         torch.cuda.synchronize()
         times, reps = [], []
         launches0 = rte.launch_count()
-        batch.timing(1)
+        timed = [hb for _, _, hb in halves] if method == "romsad_interleaved" else [batch]
+        for tb_ in timed:
+            tb_.timing(1)
         barrier(ws)
         prof = a.profile_window and method == methods[0] and not host
         if prof:
@@ -389,7 +430,8 @@ def run_ours(a, ws, rank, local):
         if prof:
             torch.cuda.profiler.stop()
         barrier(ws)
-        ph = batch.timing(0)
+        phs = [tb_.timing(0) for tb_ in timed]
+        ph = {k: sum(p_[k] for p_ in phs) for k in phs[0]}
         sweep_ms, launches, units = ph["sweep_ms"], ph["sweep_launches"], ph["sweep_units"]
         n_launch = rte.launch_count() - launches0
         got = (hbuf.numpy() if host else rho.cpu().numpy())
