@@ -26,6 +26,8 @@ CASES = [
     (37, 19, 8, 4),     # nx > 32, ny not a multiple of the block height
     (33, 70, 4, 2),     # several row blocks with a ragged tail
     (64, 64, 16, 4),    # 32 distinct directions
+    (70, 100, 8, 2),    # two row blocks per warp, a ragged last row block
+    (96, 80, 4, 2),     # two row blocks per warp, an odd number of row blocks
 ]
 
 
