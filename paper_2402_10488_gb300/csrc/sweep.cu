@@ -1102,11 +1102,34 @@ int sweep_launch_leak(rte_batch_t bt, const double* rho_in, double* rho_out, con
 // with FP32 rounding confined to the small e.
 namespace rte {
 
-// FP32 copy of the sweep tables (M^-1 of each (instance, material, direction), row-major, so that a
-// row is one 16-byte word).
+// FP32 copy of the sweep tables, M^-1 of each (instance, material, direction) in pair-major order:
+// the column entries of rows (0, 1) side by side, then those of rows (2, 3) --
+// (m00, m10, m01, m11, m02, m12, m03, m13, m20, m30, m21, m31, m22, m32, m23, m33) -- so that one
+// packed FMA applies a column to two rows (f32_cell).
 __global__ void tables_to_f32_kernel(const double* t64, float* t32, size_t n) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) t32[i] = (float)t64[i];
+  if (i >= n) return;
+  const int k = (int)(i % kTab2D), row = k / 4, col = k % 4, pr = row / 2;
+  t32[i - k + 8 * pr + 2 * col + (row - 2 * pr)] = (float)t64[i];
+}
+
+// Packed single-precision pairs (PTX fma.rn.f32x2 / mul.rn.f32x2, sm_100 and later): one
+// instruction for two FP32 operations, each rounded exactly as the scalar fmaf / multiply.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
 }
 
 // floats of the FP32 sweep's y-inflow line buffer, rounded up so that the tables behind it start
@@ -1259,30 +1282,39 @@ __global__ void __launch_bounds__(32) sweep2d_f32_kernel(const Sweep2D32Args A) 
       // can be interleaved: a slot beyond the group's directions has zero tables and weight and
       // adds nothing
       const float4* Tm = reinterpret_cast<const float4*>(tab_s + m * mstride);
+      float2 acc01 = make_float2(acc0, acc1), acc23 = make_float2(acc2, acc3);
 #pragma unroll
       for (int dd = 0; dd < DPW; ++dd) {
         const float4* T = Tm + dd * (kTab2D / 4);
-        // right-hand side s + E_x t_x + E_y t_y, then the rows of M^-1
-        const float r0 = fmaf(ay[dd], ty[dd][0], fmaf(ax[dd], tx[dd][0], sv.x));
-        const float r1 = fmaf(ay[dd], ty[dd][1], fmaf(bx[dd], tx[dd][0], sv.y));
-        const float r2 = fmaf(by[dd], ty[dd][0], fmaf(ax[dd], tx[dd][1], sv.z));
-        const float r3 = fmaf(by[dd], ty[dd][1], fmaf(bx[dd], tx[dd][1], sv.w));
-        float a[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const float4 mr = T[k];
-          a[k] = fmaf(mr.w, r3, fmaf(mr.z, r2, fmaf(mr.y, r1, mr.x * r0)));
-        }
-        tx[dd][0] = fmaf(c3x, a[1], a[0]);
-        tx[dd][1] = fmaf(c3x, a[3], a[2]);
-        typ[dd][0] = fmaf(c3y, a[2], a[0]);
-        typ[dd][1] = fmaf(c3y, a[3], a[1]);
-        acc0 = fmaf(w[dd], a[0], acc0);
-        acc1 = fmaf(w[dd], a[1], acc1);
-        acc2 = fmaf(w[dd], a[2], acc2);
-        acc3 = fmaf(w[dd], a[3], acc3);
+        // right-hand side s + E_x t_x + E_y t_y as the pairs (r0, r1), (r2, r3), then M^-1 applied
+        // column by column to the row pairs (a0, a1), (a2, a3) (pair-major tables): the same
+        // roundings in the same order as one fmaf per entry
+        const float2 exb = make_float2(ax[dd], bx[dd]);
+        const float2 tyv = make_float2(ty[dd][0], ty[dd][1]);
+        const float2 r01 = fma2(make_float2(ay[dd], ay[dd]), tyv,
+                                fma2(exb, make_float2(tx[dd][0], tx[dd][0]), make_float2(sv.x, sv.y)));
+        const float2 r23 = fma2(make_float2(by[dd], by[dd]), tyv,
+                                fma2(exb, make_float2(tx[dd][1], tx[dd][1]), make_float2(sv.z, sv.w)));
+        const float4 q0 = T[0], q1 = T[1], q2 = T[2], q3 = T[3];
+        const float2 rr0 = make_float2(r01.x, r01.x), rr1 = make_float2(r01.y, r01.y);
+        const float2 rr2 = make_float2(r23.x, r23.x), rr3 = make_float2(r23.y, r23.y);
+        float2 a01 = mul2(make_float2(q0.x, q0.y), rr0);
+        a01 = fma2(make_float2(q0.z, q0.w), rr1, a01);
+        a01 = fma2(make_float2(q1.x, q1.y), rr2, a01);
+        a01 = fma2(make_float2(q1.z, q1.w), rr3, a01);
+        float2 a23 = mul2(make_float2(q2.x, q2.y), rr0);
+        a23 = fma2(make_float2(q2.z, q2.w), rr1, a23);
+        a23 = fma2(make_float2(q3.x, q3.y), rr2, a23);
+        a23 = fma2(make_float2(q3.z, q3.w), rr3, a23);
+        tx[dd][0] = fmaf(c3x, a01.y, a01.x);
+        tx[dd][1] = fmaf(c3x, a23.y, a23.x);
+        const float2 tyo = fma2(make_float2(c3y, c3y), a23, a01);
+        typ[dd][0] = tyo.x, typ[dd][1] = tyo.y;
+        const float2 ww = make_float2(w[dd], w[dd]);
+        acc01 = fma2(ww, a01, acc01);
+        acc23 = fma2(ww, a23, acc23);
       }
-      part[c] = make_float4(acc0, acc1, acc2, acc3);
+      part[c] = make_float4(acc01.x, acc01.y, acc23.x, acc23.y);
       if (lane == H - 1 && rb + 1 < nrb) {
 #pragma unroll
         for (int dd = 0; dd < DPW; ++dd) {
