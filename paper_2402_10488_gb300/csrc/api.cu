@@ -354,6 +354,7 @@ extern "C" int rte_batch_tune(rte_batch_t b, int dpw) {
   b->dpw_dynamic = dpw == 0;
   b->tuned.clear();
   b->tuned32.clear();
+  b->tuned_nw.clear();
   if (dpw == 0) dpw = std::max(auto_dpw(b->disc, b->B), b->min_dpw);
   if (dpw != 1 && dpw != 2 && dpw != 4 && dpw != 8) return fail(RTE_EINVAL, "dirs_per_warp must be 0, 1, 2, 4 or 8");
   DeviceGuard g(b->disc->device);

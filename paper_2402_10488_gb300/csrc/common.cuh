@@ -160,6 +160,10 @@ struct rte_batch_s {
   std::vector<std::pair<int, int>> tuned;
   std::vector<std::pair<int, int>> tuned32;   // the same, measured with the FP32 sweep
   int force_dpw = 0;                  // autotuner trials: this dpw for every launch
+  int force_nw = 0;                   // autotuner trials: this many warps per direction group
+  // measured warps per direction group of the FP64 sweep for each entry of `tuned` (1: one warp
+  // walks all row blocks; more: the pipelined sweep2d_kba_kernel); empty = the cost model
+  std::vector<int> tuned_nw;
   bool kba = true;                    // several warps per direction group when warps are scarce
   std::vector<double> sigma_t_h, sigma_s_h, source_h, inflow_h;
   // parameters taken from device memory (rte_batch_set_params_device) are validated on the device;

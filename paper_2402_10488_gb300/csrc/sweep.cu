@@ -791,7 +791,22 @@ int sweep_launch(rte_batch_t bt, const double* rho_in, double* rho_out, double* 
                   gdev,         d->nx,         d->ny,          d->n_cells,  d->n_dof,
                   d->n_mat,     d->n_dirs,     n_groups,       with_source, std::sqrt(d->hx * d->hy),
                   1.0 / d->hx,  1.0 / d->hy};
-    const int NW = bt->kba ? kba_warps(d, bt->n_sm, (long long)n_active * n_groups) : 1;
+    const int H0 = d->nx < 32 ? d->nx : 32;
+    const int nrb = (d->ny + H0 - 1) / H0;
+    int NW = 1;
+    if (bt->force_nw > 0) {
+      NW = bt->force_nw;
+    } else if (!bt->tuned_nw.empty() && bt->tuned_nw.size() == bt->tuned.size() && !bt->force_dpw) {
+      NW = bt->tuned_nw.back();   // the measured choice for this running count
+      for (size_t e = 0; e < bt->tuned.size(); ++e)
+        if (n_active <= bt->tuned[e].first) {
+          NW = bt->tuned_nw[e];
+          break;
+        }
+    } else if (bt->kba) {
+      NW = kba_warps(d, bt->n_sm, (long long)n_active * n_groups);
+    }
+    NW = std::max(1, std::min(NW, std::min(nrb, 8)));
     if (NW >= 2) {
       const int H = d->nx < 32 ? d->nx : 32;
       const int D = std::max(H + kKbaChunk, (d->nx + H - 1 + NW - 1) / NW);  // as in kba_steps
@@ -1475,6 +1490,7 @@ static int autotune(rte_batch_t bt, cudaStream_t st, int* n_entries, int* table)
   bt->timing = false;
   bt->tuned.clear();
   bt->tuned32.clear();
+  bt->tuned_nw.clear();
   int status = RTE_OK;
   RTE_CUDA_TRY(cudaMemsetAsync(bt->work.p, 0, sizeof(double) * nb, st));
   for (int n : bands) {
@@ -1490,32 +1506,43 @@ static int autotune(rte_batch_t bt, cudaStream_t st, int* n_entries, int* table)
         return prec == 0 ? sweep_launch(bt, bt->work.p, bt->work.p + nb, nullptr, 1, mask.p, st, true, n)
                          : sweep_launch_f32(bt, bt->work.p, bt->work.p + nb, mask.p, st, n);
       };
+      int best_nw = 1;
+      // FP64: also the pipelined sweep with 2, 4 or 8 warps per direction group (row blocks
+      // permitting); the FP32 sweep has one form
+      const int H0 = d->nx < 32 ? d->nx : 32;
+      const int nw_max = prec == 0 ? std::min(8, (d->ny + H0 - 1) / H0) : 1;
       for (int dpw = 1; dpw <= kMaxDirsPerWarp && status == RTE_OK; dpw *= 2) {
         const int k = dpw == 1 ? 0 : dpw == 2 ? 1 : dpw == 4 ? 2 : 3;
         if ((size_t)n * bt->gcount[k] * d->n_dof > bt->partial.n) continue;  // no partial-sum space
-        bt->force_dpw = dpw;
-        float ms = 0.f;
-        status = launch();
-        if (status == RTE_OK && cudaEventRecord(e0, st) != cudaSuccess) status = fail(RTE_ECUDA, "autotune: event");
-        for (int rep = 0; rep < 2 && status == RTE_OK; ++rep) status = launch();
-        if (status == RTE_OK && (cudaEventRecord(e1, st) != cudaSuccess ||
-                                 cudaEventSynchronize(e1) != cudaSuccess ||
-                                 cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-          status = fail(RTE_ECUDA, "autotune: timing");
-        if (status == RTE_OK && (best == 0 || ms < best_ms)) best_ms = ms, best = dpw;
+        for (int nw = 1; nw <= nw_max && status == RTE_OK; nw *= 2) {
+          bt->force_dpw = dpw;
+          bt->force_nw = prec == 0 ? nw : 0;
+          float ms = 0.f;
+          status = launch();
+          if (status == RTE_OK && cudaEventRecord(e0, st) != cudaSuccess) status = fail(RTE_ECUDA, "autotune: event");
+          for (int rep = 0; rep < 2 && status == RTE_OK; ++rep) status = launch();
+          if (status == RTE_OK && (cudaEventRecord(e1, st) != cudaSuccess ||
+                                   cudaEventSynchronize(e1) != cudaSuccess ||
+                                   cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            status = fail(RTE_ECUDA, "autotune: timing");
+          if (status == RTE_OK && (best == 0 || ms < best_ms)) best_ms = ms, best = dpw, best_nw = nw;
+        }
       }
       if (status != RTE_OK) break;
       (prec == 0 ? bt->tuned : bt->tuned32).emplace_back(n, best);
+      if (prec == 0) bt->tuned_nw.push_back(best_nw);
     }
     if (status != RTE_OK) break;
   }
   bt->force_dpw = 0;
+  bt->force_nw = 0;
   bt->timing = timing;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (status != RTE_OK) {
     bt->tuned.clear();
     bt->tuned32.clear();
+    bt->tuned_nw.clear();
     return status;
   }
   bt->dpw_dynamic = true;
