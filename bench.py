@@ -312,6 +312,8 @@ def run_ours(a, ws, rank, local):
         batch.dsa_smoother(a.dsa_smoother)
     batch.set_params(test)
     tuned = batch.autotune() if a.dpw < 0 else None
+    if tuned:   # (count, dirs per warp, warps per direction group) of the FP64 sweep
+        tuned = batch.tuned() or tuned
     n_dof = disc.n_dof
     # romsad_interleaved: the same instances as two halves (separate batches, each with its own copy
     # of the correction ROM) solved by rte_solve_interleaved
@@ -505,7 +507,8 @@ def run_ours(a, ws, rank, local):
                            "smoothing sweeps per level" if a.dsa_rtol == 0 else
                            f"FGMRES rtol {a.dsa_rtol}"), "error_target": 1e-6,
                    "dirs_per_warp": (a.dpw if a.dpw > 0 else
-                                     f"measured per running count {tuned}" if tuned else
+                                     "measured per running count (count, directions per warp, "
+                                     f"warps per direction group) {tuned}" if tuned else
                                      "occupancy rule per launch"),
                    "l2": "256 MB buffer written between timed steps",
                    "parallelism": "instances sharded across ranks, no collective"},

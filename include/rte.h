@@ -220,7 +220,9 @@ int rte_batch_tune(rte_batch_t batch, int dirs_per_warp);
 
 /* Empirical autotuner of the same choice: for B, B/2, B/4, ..., 1 running instances it times one
  * sweep with every allowed directions-per-warp value (CUDA events on `stream`, on the batch's
- * current parameters) and keeps the fastest per count; later sweeps pick the entry for the
+ * current parameters) and keeps the fastest per count; for the FP64 sweep every value is also
+ * timed with 2, 4 and 8 warps per direction group (the pipelined form, row blocks shared
+ * round-robin, as far as the mesh has row blocks of 32 rows).  Later sweeps pick the entry for the
  * smallest timed count >= their running instances.  2D batches get a second table, measured the
  * same way with the FP32 sweep of the precision variant (kept internally).  Uses the batch's
  * iteration scratch only.
@@ -228,6 +230,12 @@ int rte_batch_tune(rte_batch_t batch, int dirs_per_warp);
  * Synchronous.  rte_batch_tune resets it.  1D batches: no-op.  Errors: RTE_ESTATE (no
  * parameters), RTE_ECUDA. */
 int rte_batch_autotune(rte_batch_t batch, void* stream, int* n_entries, int* table);
+
+/* The FP64 sweep decomposition rte_batch_autotune chose, per timed count of running instances:
+ *   n_entries  HOST int out: 0 when the batch is not autotuned
+ *   table      HOST int[3*32] or NULL: (count, dirs_per_warp, warps per direction group)
+ * Errors: RTE_EINVAL (null batch). */
+int rte_batch_tuned(rte_batch_t batch, int* n_entries, int* table);
 
 /* Allocation-free variant of rte_sweep (the paper has no counterpart: this is a library service).
  * For callers that cannot allocate device memory while they run (for example under a host

@@ -67,7 +67,7 @@ static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w
 
 using namespace rte;
 
-extern "C" int rte_version(void) { return 10700; }
+extern "C" int rte_version(void) { return 10800; }
 extern "C" const char* rte_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" int rte_disc_create(const rte_disc_desc* d, int device, rte_disc_t* out) {

@@ -1556,6 +1556,19 @@ static int autotune(rte_batch_t bt, cudaStream_t st, int* n_entries, int* table)
 }
 }  // namespace rte
 
+extern "C" int rte_batch_tuned(rte_batch_t b, int* n_entries, int* table) {
+  if (!b || !n_entries) return fail(RTE_EINVAL, "rte_batch_tuned: null argument");
+  const bool ok = b->tuned_nw.size() == b->tuned.size();
+  *n_entries = ok ? (int)b->tuned.size() : 0;
+  if (table && ok)
+    for (size_t k = 0; k < b->tuned.size(); ++k) {
+      table[3 * k] = b->tuned[k].first;
+      table[3 * k + 1] = b->tuned[k].second;
+      table[3 * k + 2] = b->tuned_nw[k];
+    }
+  return RTE_OK;
+}
+
 extern "C" int rte_batch_autotune(rte_batch_t b, void* stream, int* n_entries, int* table) {
   if (!b) return fail(RTE_EINVAL, "rte_batch_autotune: null argument");
   RTE_TRY(params_ready(b, "rte_batch_autotune"));

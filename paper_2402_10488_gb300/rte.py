@@ -62,6 +62,7 @@ SIGNATURES = {
     "rte_solve_many": (_I, [_I, _P, _P, _P, _P, _P, _P]),
     "rte_solve_lockstep": (_I, [_I, _P, _P, _P, _P, _P, _P]),
     "rte_solve_interleaved": (_I, [_I, _P, _P, _P, _P, _P, _P]),
+    "rte_batch_tuned": (_I, [_P, _P, _P]),
     "rte_server_create": (_I, [_I, _P]),
     "rte_server_add_bucket": (_I, [_P, _P, _P, _P, _P, _P]),
     "rte_server_start": (_I, [_P]),
@@ -349,6 +350,14 @@ class Batch:
         check(lib().rte_batch_autotune(self.h, _stream(stream), ctypes.byref(n),
                                        table.ctypes.data_as(_P)))
         return [(int(table[2 * k]), int(table[2 * k + 1])) for k in range(n.value)]
+
+    def tuned(self):
+        """rte_batch_tuned: [(count, dirs_per_warp, warps per direction group), ...] of the FP64
+        sweep after autotune(), ascending; [] when not autotuned."""
+        n = _I()
+        table = np.zeros(96, np.int32)
+        check(lib().rte_batch_tuned(self.h, ctypes.byref(n), table.ctypes.data_as(_P)))
+        return [tuple(int(x) for x in table[3 * k:3 * k + 3]) for k in range(n.value)]
 
     def timing(self, enable):
         """enable=1 reset+start, 0 reset+stop, -1 read.  Returns a dict of phase times (ms) and

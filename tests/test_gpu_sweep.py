@@ -151,14 +151,19 @@ def test_sweep_work_decomposition_does_not_change_results(dpw):
 
 
 def test_autotuned_decomposition_keeps_results():
-    """The empirical autotuner only changes which directions share a warp: results stay within
-    the sweep tolerance of the oracle, and every table entry is an allowed value."""
+    """The empirical autotuner only changes which directions share a warp and how many warps walk
+    a direction group's row blocks: results stay within the sweep tolerance of the oracle, and
+    every table entry is an allowed value."""
     rte = _rte()
     p = inputs.random_2d(48, 16, 4, 3, seed=78, B=6, inflow=(0.2, 0.0, 1.0, 0.5), ny=40)
     batch = rte.Batch.from_problem(p)
     table = batch.autotune()
     assert [n for n, _ in table] == sorted(n for n, _ in table) and table[-1][0] == 6
     assert all(d in (1, 2, 4, 8) for _, d in table)
+    # the FP64 choice with its warps per direction group (40 rows: two row blocks at most)
+    wide = batch.tuned()
+    assert [(n, d) for n, d, _ in wide] == table
+    assert all(w in (1, 2) for _, _, w in wide)
     rho_in = np.random.default_rng(9).normal(size=(6, p.n_dof))
     rin = torch.tensor(rho_in, device="cuda")
     rout = torch.empty_like(rin)
