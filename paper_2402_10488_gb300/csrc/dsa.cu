@@ -367,7 +367,8 @@ __device__ __forceinline__ void rbgs_cell(const LevelC& L, int b, int c, const f
 }
 
 // one cell of r = b - A x
-__device__ __forceinline__ void residual_cell(const LevelC& L, int b, int c) {
+// the 12 residual values of cell c of instance b
+__device__ __forceinline__ void residual_values(const LevelC& L, int b, int c, float bl[NB]) {
   const int i = c % L.nx, j = c / L.nx, col = (i + j) & 1, half = lhalf(L.nc);
   const size_t off = (size_t)b * lstride(L.nc);
   const float* xb = L.x + off;
@@ -376,11 +377,16 @@ __device__ __forceinline__ void residual_cell(const LevelC& L, int b, int c) {
   const int k = L.cls[c];
   apply_block(L, L.diag + ((size_t)b * L.n_class + k) * NB2, k, xl, acc);
   nbr_trace_sum(L.K, xb, half, i, j, L.nx, L.ny, acc);
-  float bl[NB];
   lload(L.b + off, half, c, col, bl);
 #pragma unroll
-  for (int k = 0; k < NB; ++k) bl[k] -= acc[k];
-  lstore(L.r + off, half, c, col, bl);
+  for (int q = 0; q < NB; ++q) bl[q] -= acc[q];
+}
+
+__device__ __forceinline__ void residual_cell(const LevelC& L, int b, int c) {
+  float bl[NB];
+  residual_values(L, b, c, bl);
+  const int i = c % L.nx, j = c / L.nx;
+  lstore(L.r + (size_t)b * lstride(L.nc), lhalf(L.nc), c, (i + j) & 1, bl);
 }
 
 // Prolongation coefficients: fine basis a_f in the coarse basis a_c restricted to child o (-1/+1):
@@ -652,6 +658,42 @@ __global__ void residual_kernel(LevelC L, const uint8_t* active) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.nc) return;
   residual_cell(L, b, c);
+}
+
+// r = b - A x on level F and its restriction b_coarse = sum_children P_c^T r[c] in one pass: one
+// thread per coarse cell computes its four children's residuals in registers (residual_cell's
+// arithmetic) and sums each coarse entry over the children in restrict_entry's order, so the
+// result is bit for bit that of residual_kernel followed by restrict_kernel without writing and
+// re-reading the residual.
+__global__ void residual_restrict_kernel(LevelC F, LevelC Cl, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int C = blockIdx.x * blockDim.x + threadIdx.x;
+  if (C >= Cl.nc) return;
+  const int I = C % Cl.nx, J = C / Cl.nx;
+  float r[4][NB];
+#pragma unroll
+  for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) residual_values(F, b, (2 * J + dy) * F.nx + 2 * I + dx, r[2 * dy + dx]);
+  float* bc = Cl.b + (size_t)b * lstride(Cl.nc);
+  const int ch = lhalf(Cl.nc), ccol = (I + J) & 1;
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    float out[4];
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+      float acc = 0.f;
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx)
+#pragma unroll
+          for (int kf = 0; kf < 4; ++kf) acc = fmaf(pk(dx, dy, kf, kc), r[2 * dy + dx][4 * f + kf], acc);
+      out[kc] = acc;
+    }
+    *reinterpret_cast<float4*>(bc + lword(ch, C, ccol, f)) = make_float4(out[0], out[1], out[2], out[3]);
+  }
 }
 
 __global__ void restrict_kernel(LevelC F, LevelC Cl, const uint8_t* active) {
@@ -1397,9 +1439,8 @@ static int vcycle(rte_batch_t bt, int l, const uint8_t* active, cudaStream_t st,
   } else {
     RTE_TRY(smooth_nu(0, nullptr));
   }
-  residual_kernel<<<dim3((L.nc + 127) / 128, B), 128, 0, st>>>(L, active); RTE_NOTE_LAUNCH();
   LevelC Cl = lvl_of(bt, l + 1);
-  restrict_kernel<<<dim3((Cl.nc * NB + 255) / 256, B), 256, 0, st>>>(L, Cl, active); RTE_NOTE_LAUNCH();
+  residual_restrict_kernel<<<dim3((Cl.nc + 127) / 128, B), 128, 0, st>>>(L, Cl, active); RTE_NOTE_LAUNCH();
   RTE_TRY(vcycle(bt, l + 1, active, st, nu));
   Cl = lvl_of(bt, l + 1);
   const bool fold = !blocked && !bt->dsa_tiled;  // the global form folds the prolongation in
