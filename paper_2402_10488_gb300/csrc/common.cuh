@@ -318,6 +318,11 @@ int axpy_launch(rte_batch_t b, const double* x, const double* y, double* out,
                 const uint8_t* active, cudaStream_t st);  // out = x + y (x when y is null)
 int dsa_apply(rte_batch_t b, const double* R, double* drho, double rtol, int max_it,
               const uint8_t* active, int* iters, cudaStream_t st);
+// A single FP32 V-cycle (2D, dsa_rtol 0, one cycle) whose result goes straight into the SI update:
+// rho_out = rho_star + delta rho for the instances in `active` (no delta-rho array)
+bool dsa_update_fusable(rte_batch_t b, double rtol, int max_it);
+int dsa_apply_update(rte_batch_t b, const double* R, const double* rho_star, double* rho_out,
+                     const uint8_t* active, cudaStream_t st);
 }  // namespace rte
 
 namespace rte { struct RomOnline; }

@@ -1518,6 +1518,25 @@ __global__ void extract_rho32_kernel(const float* x, double* drho, int nc, int n
   o[1] = make_double2((double)u.z, (double)u.w);
 }
 
+// out = base + the delta-rho field of a level-0 vector (FP64), for the instances in `active`: the
+// SI update after a DSA correction in the pass that reads the correction (extract_rho32_kernel
+// followed by the addition, bit for bit)
+__global__ void extract_add32_kernel(const float* x, const double* __restrict__ base, double* out,
+                                     int nc, int nx, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const float4 u = *reinterpret_cast<const float4*>(x + (size_t)b * lstride(nc) +
+                                                    lword(lhalf(nc), c, lcolour(c, nx), 0));
+  const size_t o = ((size_t)b * nc + c) * 4;
+  const double2 b01 = reinterpret_cast<const double2*>(base + o)[0];
+  const double2 b23 = reinterpret_cast<const double2*>(base + o)[1];
+  double2* w = reinterpret_cast<double2*>(out + o);
+  w[0] = make_double2(b01.x + (double)u.x, b01.y + (double)u.y);
+  w[1] = make_double2(b23.x + (double)u.z, b23.y + (double)u.w);
+}
+
 // residual on level 0 against an explicit right-hand side and iterate: r0 = borig - A0 xtot
 __global__ void residual_ext_kernel(LevelC L, const float* bvec, const float* xv, float* r,
                                     const uint8_t* active) {
@@ -1531,8 +1550,11 @@ __global__ void residual_ext_kernel(LevelC L, const float* bvec, const float* xv
 }
 
 // Stationary multigrid: k V-cycles on the FP32 system, x <- x + V(b - A x), no host round trip.
+// With base != nullptr (one cycle only) the result is not stored as drho but added to base:
+// drho[b] = base[b] + delta rho, extract_add32_kernel (the SI update rho^(l) = rho^(l,*) + delta rho
+// of Alg. 1 in the same pass).
 static int dsa2d_vcycles(rte_batch_t bt, const double* R, double* drho, int k,
-                         const uint8_t* active, cudaStream_t st) {
+                         const uint8_t* active, cudaStream_t st, const double* base = nullptr) {
   DsaState* s = bt->dsa;
   const int B = bt->B, nc = bt->disc->n_cells, nx = bt->disc->nx;
   const size_t per = lstride(nc);
@@ -1547,10 +1569,15 @@ static int dsa2d_vcycles(rte_batch_t bt, const double* R, double* drho, int k,
       pack_rhs32_kernel<<<gv, 256, 0, st>>>(R, s->bl[0]->p, nc, nx, active); RTE_NOTE_LAUNCH();
     }
     RTE_TRY(vcycle(bt, 0, active, st, bt->dsa_nu, fuse));
-    extract_rho32_kernel<<<gv, 256, 0, st>>>(s->xl[0]->p, drho, nc, nx, active); RTE_NOTE_LAUNCH();
+    if (base) {
+      extract_add32_kernel<<<gv, 256, 0, st>>>(s->xl[0]->p, base, drho, nc, nx, active); RTE_NOTE_LAUNCH();
+    } else {
+      extract_rho32_kernel<<<gv, 256, 0, st>>>(s->xl[0]->p, drho, nc, nx, active); RTE_NOTE_LAUNCH();
+    }
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
   }
+  if (base) return fail(RTE_EINVAL, "DSA: the fused update needs a single V-cycle");
   pack_rhs32_kernel<<<gv, 256, 0, st>>>(R, s->borig.p, nc, nx, active); RTE_NOTE_LAUNCH();
   const LevelC L0 = lvl_of(bt, 0);
   for (int it = 0; it < k; ++it) {
@@ -1756,6 +1783,16 @@ static int dsa2d_fgmres(rte_batch_t bt, const double* R, double* drho, double rt
   if (iters_out)
     for (int b = 0; b < B; ++b) iters_out[b] = its[b];
   return status;
+}
+
+bool dsa_update_fusable(rte_batch_t bt, double rtol, int max_it) {
+  return bt->dsa && bt->disc->dim == 2 && rtol == 0.0 && max_it == 1;
+}
+
+int dsa_apply_update(rte_batch_t bt, const double* R, const double* rho_star, double* rho_out,
+                     const uint8_t* active, cudaStream_t st) {
+  if (!dsa_update_fusable(bt, 0.0, 1)) return fail(RTE_EINVAL, "DSA: fused update not available");
+  return dsa2d_vcycles(bt, R, rho_out, 1, active, st, rho_star);
 }
 
 int dsa_apply(rte_batch_t bt, const double* R, double* drho, double rtol, int max_it,

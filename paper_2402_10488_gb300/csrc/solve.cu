@@ -266,20 +266,24 @@ int si_finish(SiState& s, cudaStream_t st, double* history) {
       RTE_TRY(axpy_launch(bt, rho_star, nullptr, rho_prev, d_corr, st));
     } else {
       RTE_TRY(correction_source_launch(bt, rho_star, rho_prev, R, d_corr, st));
+      // a single V-cycle writes rho^(l) = rho^(l,*) + delta rho^(l) itself (after R is formed from
+      // rho_prev), so only the ROMSA instances need the separate update below
+      const bool fused = anyd && dsa_update_fusable(bt, o.dsa_rtol, o.dsa_max_it);
       if (anyd) {
         std::vector<int> iters(B, 0);
         PhaseScope ps(bt, 1, st);
-        int e = dsa_apply(bt, R, drho, o.dsa_rtol, o.dsa_max_it, s.dm.p + 6 * B, iters.data(), st);
+        int e = fused ? dsa_apply_update(bt, R, rho_star, rho_prev, s.dm.p + 6 * B, st)
+                      : dsa_apply(bt, R, drho, o.dsa_rtol, o.dsa_max_it, s.dm.p + 6 * B, iters.data(), st);
         if (e != RTE_OK && e != RTE_ENOCONV) return e;
         for (int b = 0; b < B; ++b)
-          if (h_dsa[b]) s.rep[b].dsa_iters += iters[b];
+          if (h_dsa[b]) s.rep[b].dsa_iters += fused ? 1 : iters[b];
       }
       if (anyr) {
         PhaseScope ps(bt, 2, st);
         RTE_TRY(rom_correction(s.rom, bt, R, drho, s.dm.p + 5 * B, st, o.rom_bf16 != 0));
       }
       // rho^(l) = rho^(l,*) + delta rho^(l), written into the rho_prev slot
-      RTE_TRY(axpy_launch(bt, rho_star, drho, rho_prev, d_corr, st));
+      if (!fused || anyr) RTE_TRY(axpy_launch(bt, rho_star, drho, rho_prev, fused ? s.dm.p + 5 * B : d_corr, st));
     }
   }
   for (int b = 0; b < B; ++b)
