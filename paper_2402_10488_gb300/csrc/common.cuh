@@ -202,6 +202,9 @@ struct rte_batch_s {
   // when set, the next sweep launch records it on its stream right before its first sweep kernel
   // and clears it (rte_solve_interleaved: the host learns that the sweep has been dispatched)
   cudaEvent_t started_ev = nullptr;
+  // when set (the solve loop, 2D), the sweeps' partial-sum reductions also write the correction
+  // source R = sigma_s (rho_out - rho_in) of every swept instance there
+  double* fuse_R = nullptr;
   // optional phase timing with CUDA events on the launching stream (rte_batch_timing)
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> sweep_ev;
@@ -382,6 +385,7 @@ struct SiState {
   cudaEvent_t ev = nullptr;           // recorded after the norms copy
   cudaEvent_t started = nullptr;      // rte_solve_interleaved: recorded before the sweep kernel
   cudaEvent_t corr = nullptr;         // rte_solve_interleaved: recorded after the corrections
+  bool r_fused = false;               // the launch in flight also formed the correction source
   std::vector<uint8_t> act, lowp, done;
   std::vector<uint8_t> inner;         // the next sweep is an FP32 correction sweep
   std::vector<uint8_t> swept;         // swept in the launch in flight (not waiting, gang_wait)

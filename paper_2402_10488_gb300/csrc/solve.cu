@@ -130,6 +130,10 @@ int si_launch(SiState& s, cudaStream_t st, double* psi_cur, cudaEvent_t wait_ev)
   if (wait_ev) RTE_CUDA_TRY(cudaStreamWaitEvent(st, wait_ev, 0));
   RTE_CUDA_TRY(cudaMemcpyAsync(s.dm.p, s.hm, 4 * (size_t)B, cudaMemcpyHostToDevice, st));
   bt->started_ev = s.started;
+  // the reductions form the correction source of the next correction as they go (2D, not for the
+  // training solves' psi capture)
+  s.r_fused = s.o.sa != RTE_SA_NONE && bt->disc->dim == 2 && psi_cur == nullptr;
+  bt->fuse_R = s.r_fused ? bt->work.p + 2 * nb : nullptr;
   if (n_lo == 0) {
     RTE_TRY(sweep_launch(bt, rho_prev, rho_star, psi_cur, 1, s.dm.p, st, true, n_hi));
   } else {
@@ -142,6 +146,7 @@ int si_launch(SiState& s, cudaStream_t st, double* psi_cur, cudaEvent_t wait_ev)
       RTE_TRY(sweep_launch(bt, rho_prev, rho_star, psi_cur, 1, s.dm.p + 2 * B, st, true, n_hi, false));
   }
   bt->started_ev = nullptr;
+  bt->fuse_R = nullptr;
   RTE_CUDA_TRY(cudaMemcpyAsync(s.hn, bt->norms.p, sizeof(unsigned long long) * 2 * B,
                                cudaMemcpyDeviceToHost, st));
   RTE_CUDA_TRY(cudaEventRecord(s.ev, st));
@@ -265,7 +270,7 @@ int si_finish(SiState& s, cudaStream_t st, double* history) {
       // plain SI: rho^(l) = rho^(l,*)
       RTE_TRY(axpy_launch(bt, rho_star, nullptr, rho_prev, d_corr, st));
     } else {
-      RTE_TRY(correction_source_launch(bt, rho_star, rho_prev, R, d_corr, st));
+      if (!s.r_fused) RTE_TRY(correction_source_launch(bt, rho_star, rho_prev, R, d_corr, st));
       // a single V-cycle writes rho^(l) = rho^(l,*) + delta rho^(l) itself (after R is formed from
       // rho_prev), so only the ROMSA instances need the separate update below
       const bool fused = anyd && dsa_update_fusable(bt, o.dsa_rtol, o.dsa_max_it);

@@ -580,10 +580,14 @@ __device__ __forceinline__ void block_norms(unsigned long long dmax, unsigned lo
   }
 }
 
+// With R (2D, P = 4 moments per cell) the same pass also forms the correction source
+// R = sigma_s (rho_out - rho_in) of every swept instance, as correction_source_kernel does.
 __global__ void reduce_partials_kernel(const double* __restrict__ partial,
                                        const double* __restrict__ rho_in, double* rho_out,
                                        unsigned long long* norms, const uint8_t* active,
-                                       int n_groups, int n_dof) {
+                                       int n_groups, int n_dof, double* R = nullptr,
+                                       const double* __restrict__ sigma_s = nullptr,
+                                       const int32_t* __restrict__ mat = nullptr, int n_mat = 0) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   const int rank = active_rank(active, b);
@@ -598,10 +602,17 @@ __global__ void reduce_partials_kernel(const double* __restrict__ partial,
       acc.y += v.y;
     }
     reinterpret_cast<double2*>(rho_out + (size_t)b * n_dof + e)[0] = acc;
-    if (norms) {
+    if (norms || R) {
       const double2 ri = reinterpret_cast<const double2*>(rho_in + (size_t)b * n_dof + e)[0];
-      dmax = umax64(abs_bits(acc.x - ri.x), abs_bits(acc.y - ri.y));
-      rmax = umax64(abs_bits(acc.x), abs_bits(acc.y));
+      if (norms) {
+        dmax = umax64(abs_bits(acc.x - ri.x), abs_bits(acc.y - ri.y));
+        rmax = umax64(abs_bits(acc.x), abs_bits(acc.y));
+      }
+      if (R) {
+        const double ss = sigma_s[(size_t)b * n_mat + mat[e / 4]];
+        reinterpret_cast<double2*>(R + (size_t)b * n_dof + e)[0] =
+            make_double2(ss * (acc.x - ri.x), ss * (acc.y - ri.y));
+      }
     }
   }
   if (!norms) return;
@@ -845,9 +856,11 @@ int sweep_launch(rte_batch_t bt, const double* rho_in, double* rho_out, double* 
     RTE_CUDA_TRY(cudaMemsetAsync(bt->norms.p, 0, sizeof(unsigned long long) * 2 * bt->B, st));
   const int th = 256;
   dim3 grid((d->n_dof / 2 + th - 1) / th, bt->B);
+  double* fuse_R = d->dim == 2 ? bt->fuse_R : nullptr;
   reduce_partials_kernel<<<grid, th, 0, st>>>(bt->partial.p, rho_in, rho_out,
                                              fuse_norms ? bt->norms.p : nullptr, active, n_groups,
-                                             d->n_dof); RTE_NOTE_LAUNCH();
+                                             d->n_dof, fuse_R, bt->sigma_s.p, d->mat_id.p,
+                                             d->n_mat); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;
 }
@@ -1349,7 +1362,9 @@ __global__ void reduce_partials32_kernel(const float* __restrict__ partial,
                                          const double* __restrict__ rho_in, double* rho_out,
                                          unsigned long long* norms, const uint8_t* active,
                                          int n_groups, int n_dof, const uint8_t* inner,
-                                         const double* __restrict__ y0) {
+                                         const double* __restrict__ y0, double* R,
+                                         const double* __restrict__ sigma_s,
+                                         const int32_t* __restrict__ mat, int n_mat) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   const int rank = active_rank(active, b);
@@ -1369,11 +1384,18 @@ __global__ void reduce_partials32_kernel(const float* __restrict__ partial,
     }
     double* o = rho_out + (size_t)b * n_dof + e;
     o[0] = a0, o[1] = a1, o[2] = a2, o[3] = a3;
-    if (norms) {
+    if (norms || R) {
       const double* ri = rho_in + (size_t)b * n_dof + e;
-      dmax = umax64(umax64(abs_bits(a0 - ri[0]), abs_bits(a1 - ri[1])),
-                    umax64(abs_bits(a2 - ri[2]), abs_bits(a3 - ri[3])));
-      rmax = umax64(umax64(abs_bits(a0), abs_bits(a1)), umax64(abs_bits(a2), abs_bits(a3)));
+      if (norms) {
+        dmax = umax64(umax64(abs_bits(a0 - ri[0]), abs_bits(a1 - ri[1])),
+                      umax64(abs_bits(a2 - ri[2]), abs_bits(a3 - ri[3])));
+        rmax = umax64(umax64(abs_bits(a0), abs_bits(a1)), umax64(abs_bits(a2), abs_bits(a3)));
+      }
+      if (R) {   // the correction source, as correction_source_kernel forms it
+        const double ss = sigma_s[(size_t)b * n_mat + mat[e / 4]];
+        double* r = R + (size_t)b * n_dof + e;
+        r[0] = ss * (a0 - ri[0]), r[1] = ss * (a1 - ri[1]), r[2] = ss * (a2 - ri[2]), r[3] = ss * (a3 - ri[3]);
+      }
     }
   }
   if (!norms) return;
@@ -1449,7 +1471,8 @@ int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, cons
     RTE_CUDA_TRY(cudaMemsetAsync(bt->norms.p, 0, sizeof(unsigned long long) * 2 * bt->B, st));
   const int th = 256;
   reduce_partials32_kernel<<<dim3((d->n_dof / 4 + th - 1) / th, bt->B), th, 0, st>>>(
-      bt->partial32.p, rho_in, rho_out, bt->norms.p, active, n_groups, d->n_dof, inner, y0); RTE_NOTE_LAUNCH();
+      bt->partial32.p, rho_in, rho_out, bt->norms.p, active, n_groups, d->n_dof, inner, y0,
+      bt->fuse_R, bt->sigma_s.p, d->mat_id.p, d->n_mat); RTE_NOTE_LAUNCH();
   RTE_CUDA_TRY(cudaGetLastError());
   return RTE_OK;
 }
