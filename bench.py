@@ -39,9 +39,9 @@ FLOP_PER_CELL_DIR = 64
 BYTES_PER_CELL_SWEEP = 76   # rho_in 32 B + G0 8 B + material id 4 B + rho_out 32 B
 # DRAM bytes per sweep launch from the committed ncu capture, valid only for the 2D sweep
 # kernels' device code it was taken with (sha1 of that part of sweep.cu, sweep_source_sha1)
-NCU_TRAFFIC = {"sha1": "32a0ca5935ea53a2bf4d4e7a16f14e57c612f105", "bytes_per_launch": 716034467,
+NCU_TRAFFIC = {"sha1": "32a0ca5935ea53a2bf4d4e7a16f14e57c612f105", "bytes_per_launch": 723429811,
                "batch": 152, "n": 128, "angles": 64,
-               "workload": "lattice128x128_CL(16,4) batch 152, mean of the 11 sweep2d_kernel launches "
+               "workload": "lattice128x128_CL(16,4) batch 152, mean of the 10 sweep2d_kernel launches "
                            "of one ROMSAD step"}
 
 
