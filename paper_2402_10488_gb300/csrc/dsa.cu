@@ -481,23 +481,9 @@ __device__ __forceinline__ void nbr_prolonged(const float* __restrict__ xb, int 
     }
 }
 
-__global__ void rbgs_prolong_kernel(LevelC L, LevelC Cl, int color, const uint8_t* active) {
-  const int b = blockIdx.y;
-  if (active && !active[b]) return;
-  __shared__ float4 dsh4[kSmemClasses * NB2 / 4];
-  const float* dg = L.dinv + (size_t)b * L.n_class * NB2;
-  const bool dsm = L.n_class <= kSmemClasses;
-  if (dsm) {
-    for (int t = threadIdx.x; t < L.n_class * NB2 / 4; t += blockDim.x)
-      dsh4[t] = reinterpret_cast<const float4*>(dg)[t];
-    __syncthreads();
-  }
-  const int hx2 = (L.nx + 1) / 2;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= hx2 * L.ny) return;
-  const int j = idx / hx2;
-  const int i = 2 * (idx % hx2) + ((j + color) & 1);
-  if (i >= L.nx) return;
+// cell (i, j) of `color` in that half sweep; dinv_b the instance's D^-1 blocks
+__device__ __forceinline__ void rbgs_prolong_cell(const LevelC& L, const LevelC& Cl, int b, int i,
+                                                  int j, int color, const float* dinv_b) {
   const int c = j * L.nx + i, half = lhalf(L.nc);
   float* xb = L.x + (size_t)b * lstride(L.nc);
   float vw[NB], ve[NB], vs[NB], vn[NB];
@@ -516,8 +502,28 @@ __global__ void rbgs_prolong_kernel(LevelC L, LevelC Cl, int color, const uint8_
   for (int r = 0; r < NB; ++r) res[r] -= acc[r];
   float out[NB];
   const int k = L.cls[c];
-  apply_block(L, (dsm ? reinterpret_cast<const float*>(dsh4) : dg) + (size_t)k * NB2, k, res, out);
+  apply_block(L, dinv_b + (size_t)k * NB2, k, res, out);
   lstore(xb, half, c, color, out);
+}
+
+__global__ void rbgs_prolong_kernel(LevelC L, LevelC Cl, int color, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  __shared__ float4 dsh4[kSmemClasses * NB2 / 4];
+  const float* dg = L.dinv + (size_t)b * L.n_class * NB2;
+  const bool dsm = L.n_class <= kSmemClasses;
+  if (dsm) {
+    for (int t = threadIdx.x; t < L.n_class * NB2 / 4; t += blockDim.x)
+      dsh4[t] = reinterpret_cast<const float4*>(dg)[t];
+    __syncthreads();
+  }
+  const int hx2 = (L.nx + 1) / 2;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= hx2 * L.ny) return;
+  const int j = idx / hx2;
+  const int i = 2 * (idx % hx2) + ((j + color) & 1);
+  if (i >= L.nx) return;
+  rbgs_prolong_cell(L, Cl, b, i, j, color, dsm ? reinterpret_cast<const float*>(dsh4) : dg);
 }
 
 // Red-black Gauss-Seidel with temporal blocking: H = 2 nu half sweeps of one level, colours c0,
@@ -665,11 +671,7 @@ __global__ void residual_kernel(LevelC L, const uint8_t* active) {
 // arithmetic) and sums each coarse entry over the children in restrict_entry's order, so the
 // result is bit for bit that of residual_kernel followed by restrict_kernel without writing and
 // re-reading the residual.
-__global__ void residual_restrict_kernel(LevelC F, LevelC Cl, const uint8_t* active) {
-  const int b = blockIdx.y;
-  if (active && !active[b]) return;
-  const int C = blockIdx.x * blockDim.x + threadIdx.x;
-  if (C >= Cl.nc) return;
+__device__ __forceinline__ void residual_restrict_cell(const LevelC& F, const LevelC& Cl, int b, int C) {
   const int I = C % Cl.nx, J = C / Cl.nx;
   float r[4][NB];
 #pragma unroll
@@ -696,6 +698,14 @@ __global__ void residual_restrict_kernel(LevelC F, LevelC Cl, const uint8_t* act
   }
 }
 
+__global__ void residual_restrict_kernel(LevelC F, LevelC Cl, const uint8_t* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int C = blockIdx.x * blockDim.x + threadIdx.x;
+  if (C >= Cl.nc) return;
+  residual_restrict_cell(F, Cl, b, C);
+}
+
 __global__ void restrict_kernel(LevelC F, LevelC Cl, const uint8_t* active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
@@ -719,7 +729,12 @@ struct CoarseArgs {
 
 // The V-cycle from level lc down to the coarsest and back, one CTA per instance; phases are
 // separated by block barriers instead of launches.  lc is the first level with <= kFuseCells
-// cells.
+// cells.  The barriers bound this kernel, so it takes the fine levels' shortcuts, each the same
+// arithmetic as the phases it replaces: the first half sweep from x = 0 sets x_c = D_c^-1 b_c on
+// the cells of colour 0 without clearing x (the cells of colour 1 are overwritten by the next half
+// sweep before anything reads them); residual and restriction are one pass over the coarse cells
+// (residual_restrict_cell); the prolongation is folded into the first half sweep of
+// post-smoothing (rbgs_prolong_cell).
 __global__ void __launch_bounds__(512) coarse_vcycle_kernel(const CoarseArgs A, const uint8_t* active) {
   const int b = blockIdx.x;
   if (active && !active[b]) return;
@@ -732,31 +747,50 @@ __global__ void __launch_bounds__(512) coarse_vcycle_kernel(const CoarseArgs A, 
     }
     __syncthreads();
   };
+  // the first half sweep (colour 0) from x = 0: x_c = D_c^-1 b_c
+  auto first_half = [&](const LevelC& L) {
+    const float* dinv_b = L.dinv + (size_t)b * L.n_class * NB2;
+    const size_t off = (size_t)b * lstride(L.nc);
+    const int half = lhalf(L.nc), hx2 = (L.nx + 1) / 2;
+    for (int idx = tid; idx < hx2 * L.ny; idx += nt) {
+      const int j = idx / hx2, i = 2 * (idx % hx2) + (j & 1);
+      if (i >= L.nx) continue;
+      const int c = j * L.nx + i, k = L.cls[c];
+      float v[NB], out[NB];
+      lload(L.b + off, half, c, 0, v);
+      apply_block(L, dinv_b + (size_t)k * NB2, k, v, out);
+      lstore(L.x + off, half, c, 0, out);
+    }
+    __syncthreads();
+  };
   int l = A.lc;
   for (;; ++l) {  // down
     const LevelC& L = A.lv[l];
-    for (size_t e = tid; e < lstride(L.nc); e += nt) L.x[(size_t)b * lstride(L.nc) + e] = 0.f;
-    __syncthreads();
+    first_half(L);
     if (l == A.nL - 1) {  // coarsest: exact for one cell, else many sweeps
-      const int n = L.nc == 1 ? 1 : 30;
-      for (int k = 0; k < n; ++k) {
-        half_sweep(L, 0);
-        if (L.nc > 1) half_sweep(L, 1);
+      if (L.nc > 1) {
+        half_sweep(L, 1);
+        for (int k = 1; k < 30; ++k) half_sweep(L, 0), half_sweep(L, 1);
       }
       break;
     }
-    for (int k = 0; k < A.nu; ++k) half_sweep(L, 0), half_sweep(L, 1);
-    for (int c = tid; c < L.nc; c += nt) residual_cell(L, b, c);
-    __syncthreads();
+    half_sweep(L, 1);
+    for (int k = 1; k < A.nu; ++k) half_sweep(L, 0), half_sweep(L, 1);
     const LevelC& Cl = A.lv[l + 1];
-    for (int t = tid; t < Cl.nc * NB; t += nt) restrict_entry(L, Cl, b, t);
+    for (int C = tid; C < Cl.nc; C += nt) residual_restrict_cell(L, Cl, b, C);
     __syncthreads();
   }
   for (l = A.nL - 2; l >= A.lc; --l) {  // up
     const LevelC& L = A.lv[l];
-    for (int t = tid; t < L.nc * NB; t += nt) prolong_entry(L, A.lv[l + 1], b, t);
+    const float* dinv_b = L.dinv + (size_t)b * L.n_class * NB2;
+    const int hx2 = (L.nx + 1) / 2;
+    for (int idx = tid; idx < hx2 * L.ny; idx += nt) {   // colour 1, the prolongation folded in
+      const int j = idx / hx2, i = 2 * (idx % hx2) + ((j + 1) & 1);
+      if (i < L.nx) rbgs_prolong_cell(L, A.lv[l + 1], b, i, j, 1, dinv_b);
+    }
     __syncthreads();
-    for (int k = 0; k < A.nu; ++k) half_sweep(L, 1), half_sweep(L, 0);
+    half_sweep(L, 0);
+    for (int k = 1; k < A.nu; ++k) half_sweep(L, 1), half_sweep(L, 0);
   }
 }
 
