@@ -100,7 +100,8 @@ def parse():
                     help="romsad_refine: FP32 sweeps (with sources) until the relative change is "
                          "below this, then the FP64 outer residual correction")
     ap.add_argument("--methods", default="romsad,romsad_interleaved,si_dsa,romig,romig_romsad,"
-                                         "romsad_mixed,romsad_refine,pgmres,romig_pgmres")
+                                         "romsad_mixed,romsad_refine,romsad_refine_ff,pgmres,"
+                                         "romig_pgmres")
     ap.add_argument("--gmres-rtol", type=float, default=1e-7,
                     help="pgmres: relative residual of the preconditioned system")
     ap.add_argument("--profile-window", action="store_true",
@@ -134,13 +135,17 @@ def parse():
 def precision_kw(method, a):
     """Solver options of the precision variants: romsad_mixed sweeps in FP32 until the change is
     below --fp32-switch and in FP64 afterwards; romsad_refine follows its FP32 phase with the FP64
-    outer residual correction (FP64 sweeps of the iterate, FP32 sweeps of the error equation)."""
+    outer residual correction (FP64 sweeps of the iterate, FP32 sweeps of the error equation);
+    romsad_refine_ff is romsad_refine with those FP64 sweeps in float-float arithmetic."""
     if method == "romsad_mixed":
         return dict(fp32_switch=a.fp32_switch)
-    if method == "romsad_refine":
-        return dict(fp32_switch=a.refine_switch, refine_kappa=a.refine_kappa,
-                    refine_inner=a.refine_inner, gang_wait=a.gang_wait,
-                    rom_bf16=bool(a.refine_rom_bf16))
+    if method in ("romsad_refine", "romsad_refine_ff"):
+        kw = dict(fp32_switch=a.refine_switch, refine_kappa=a.refine_kappa,
+                  refine_inner=a.refine_inner, gang_wait=a.gang_wait,
+                  rom_bf16=bool(a.refine_rom_bf16))
+        if method == "romsad_refine_ff":
+            kw["outer_ff"] = True
+        return kw
     return {}
 
 
@@ -379,7 +384,7 @@ def run_ours(a, ws, rank, local):
             sa, kw = rte.SA_DSA, {}
         elif method == "romsad":
             sa, kw = rte.SA_ROMSAD, dict(rom_c=rom_c, theta=5, eps_romsad=eps_romsad)
-        elif method in ("romsad_mixed", "romsad_refine"):
+        elif method in ("romsad_mixed", "romsad_refine", "romsad_refine_ff"):
             sa, kw = rte.SA_ROMSAD, dict(rom_c=rom_c, theta=5, eps_romsad=eps_romsad,
                                          **precision_kw(method, a))
         elif method == "romig_romsad":
@@ -464,12 +469,17 @@ def run_ours(a, ws, rank, local):
                     n_sweep32_mean=float(np.mean([x["n_sweep32"] for x in r["reps"]])),
                     sweep_share=r["sweep_ms"] / float(np.sum(r["times"])),
                     phase_share={k: r["phases"][k + "_ms"] / float(np.sum(r["times"]))
-                                 for k in ("sweep", "sweep32", "dsa", "rom", "setup")},
+                                 for k in ("sweep", "sweep32", "sweepff", "dsa", "rom", "setup")},
                     sweep_tflops=(r["sweep_units"] * FLOP_PER_CELL_DIR / (r["sweep_ms"] / 1e3) / 1e12
                                   if r["sweep_ms"] > 0 else None),
                     sweep32_tflops=(r["phases"]["sweep32_units"] * FLOP_PER_CELL_DIR /
                                     (r["phases"]["sweep32_ms"] / 1e3) / 1e12
                                     if r["phases"]["sweep32_ms"] > 0 else None),
+                    # the float-float sweep's rate in the FP64 sweep's FLOPs (each of its FP64
+                    # operations costs ~15 FP32 operations)
+                    sweepff_tflops=(r["phases"]["sweepff_units"] * FLOP_PER_CELL_DIR /
+                                    (r["phases"]["sweepff_ms"] / 1e3) / 1e12
+                                    if r["phases"]["sweepff_ms"] > 0 else None),
                     p50_ms=float(np.percentile(r["times"], 50)),
                     p99_ms=float(np.percentile(r["times"], 99)), **r["resid"])
 
@@ -538,9 +548,10 @@ def run_ours(a, ws, rank, local):
         sid = summ["si_dsa"]["solves_per_s"]
         line["si_dsa_solves_per_s"] = sid
         line["romsad_vs_si_dsa"] = summ["romsad"]["solves_per_s"] / sid
-        if "romsad_refine" in summ:
-            line["romsad_refine_solves_per_s"] = summ["romsad_refine"]["solves_per_s"]
-            line["romsad_refine_vs_si_dsa"] = summ["romsad_refine"]["solves_per_s"] / sid
+        for m in ("romsad_refine", "romsad_refine_ff"):
+            if m in summ:
+                line[m + "_solves_per_s"] = summ[m]["solves_per_s"]
+                line[m + "_vs_si_dsa"] = summ[m]["solves_per_s"] / sid
     return line, dict(n_sweep=summ["romsad"]["n_sweep_mean"], n_dsa=summ["romsad"]["n_dsa_mean"],
                       n_romsa=summ["romsad"]["n_romsa_mean"], n=a.n, angles=a.angles)
 

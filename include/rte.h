@@ -210,6 +210,22 @@ int rte_sweep(rte_batch_t batch, const double* rho_in, double* rho_out, double* 
 int rte_sweep_f32(rte_batch_t batch, const double* rho_in, double* rho_out, const uint8_t* active,
                   void* stream);
 
+/* One float-float sweep (the precision variant's outer sweep, rte_solve_opts.outer_ff; no
+ * counterpart in the paper, which computes in FP64): the operator of rte_sweep with source, each
+ * cell solve in float-float arithmetic -- every value an unevaluated sum of two FP32 numbers,
+ * about 48 significant bits, from Knuth's TwoSum and Dekker's exact product in FMA form -- on the
+ * FP32 units, with cell sources formed in FP64 and the per-group partial sums reduced in FP64:
+ *     rho_out = sum_j omega_j (D_j + Sigma_t)^{-1} (Sigma_s rho_in + G + g^bc_j)
+ * to within 3e-11 of ||rho_out||_inf (the tested bound: the FP64 sweep's 1e-12 scaled by the ratio
+ * 32 of the two unit roundoffs; one float-float FMA rounds to ~1e-14 relative).
+ *   rho_in, rho_out  DEVICE double[B][n_dof], 16-byte aligned, not aliased
+ *   active           DEVICE uint8[B] or NULL (instances with active[b] == 0 are skipped)
+ * 2D only; 1, 2 or 4 directions per warp (the sweep's choice, 8 narrowed to 4; where the batch's
+ * partial-sum buffer holds only the groups of 8, the FP64 sweep runs instead).  Asynchronous on
+ * `stream`.  Errors: RTE_ESTATE, RTE_EINVAL, RTE_ENOMEM, RTE_ECUDA. */
+int rte_sweep_ff(rte_batch_t batch, const double* rho_in, double* rho_out, const uint8_t* active,
+                 void* stream);
+
 /* Work decomposition of the 2D sweep: dirs_per_warp in {1, 2, 4, 8} sets how many directions of
  * one quadrant a warp sweeps together (more directions: more instruction-level parallelism and
  * fewer partial sums; fewer: more warps in flight).  0 (the default) picks per launch the largest
@@ -288,10 +304,11 @@ int rte_residual(rte_batch_t batch, const double* rho, double* out, double* cell
 /* Sweep-kernel timing for throughput and roofline accounting.  Each 2D/1D sweep kernel launched
  * for this batch while timing is on is bracketed by CUDA events recorded on the stream it is
  * launched on, and so is each DSA correction, each ROM step (ROMSA correction, ROMIG, reduced
- * operator assembly), each per-instance set-up and each FP32 sweep (sources, sweep, no reduction).
- * out (HOST double[12], may be NULL) receives (FP64 sweep-kernel ms, timed FP64 sweep launches,
- * cell x distinct-direction local solves they performed, DSA ms, DSA calls, ROM ms, ROM calls,
- * set-up ms, set-up calls, FP32 sweep ms, FP32 sweep calls, their cell x direction solves); the
+ * operator assembly), each per-instance set-up and each FP32 or float-float sweep (sources, sweep,
+ * no reduction).  out (HOST double[15], may be NULL) receives (FP64 sweep-kernel ms, timed FP64
+ * sweep launches, cell x distinct-direction local solves they performed, DSA ms, DSA calls, ROM
+ * ms, ROM calls, set-up ms, set-up calls, FP32 sweep ms, FP32 sweep calls, their cell x direction
+ * solves, float-float sweep ms, float-float sweep calls, their cell x direction solves); the
  * call waits for the recorded events.  enable = 1 resets and starts, 0 resets and stops, -1 only
  * reads.  Errors: RTE_EINVAL, RTE_ECUDA. */
 int rte_batch_timing(rte_batch_t batch, int enable, double* out);
@@ -459,6 +476,10 @@ typedef struct {
                           the correction that followed it -- RTE_SA_NONE (none: plain SI, or the
                           stop test fired), RTE_SA_DSA or RTE_SA_ROMSA (Alg. 2's choice) --
                           plus 0x10 when sweep l ran in FP32.  Entries past n_sweep untouched. */
+  int outer_ff;        /* precision variant (fp32_switch or refine_kappa > 0): 1 -- its sweeps
+                          that would run in FP64 run as float-float sweeps (rte_sweep_ff) on the
+                          FP32 units, so the stop test needs eps well above their ~1e-13
+                          rounding (1e-11 relative is tested); 0 -- in FP64.                  */
 } rte_solve_opts;
 
 typedef struct {

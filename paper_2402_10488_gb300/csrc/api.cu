@@ -67,7 +67,7 @@ static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w
 
 using namespace rte;
 
-extern "C" int rte_version(void) { return 10800; }
+extern "C" int rte_version(void) { return 10900; }
 extern "C" const char* rte_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" int rte_disc_create(const rte_disc_desc* d, int device, rte_disc_t* out) {
@@ -380,7 +380,7 @@ extern "C" int rte_batch_tune(rte_batch_t b, int dpw) {
 size_t rte_batch_s::bytes() const {
   size_t t = 8 * (sigma_t.n + sigma_s.n + G0.n + inflow.n + tables.n + partial.n + S.n + norms.n + work.n +
                   outer.n + leak.n + vout.n);
-  t += 4 * (tables32.n + S32.n + partial32.n);
+  t += 4 * (tables32.n + S32.n + partial32.n + tablesff.n + Sff.n);
   t += sizeof(rte::SweepGroup) * (groups_dev.n + groups_all_dev.n) + slot_mask.n;
   return t + rte::dsa_bytes(this);
 }
@@ -411,7 +411,7 @@ extern "C" int rte_counters(int64_t* out) {
 extern "C" int rte_batch_timing(rte_batch_t b, int enable, double* out) {
   if (!b) return fail(RTE_EINVAL, "rte_batch_timing: null argument");
   DeviceGuard g(b->disc->device);
-  double ms = 0.0, pms[4] = {0, 0, 0, 0};
+  double ms = 0.0, pms[5] = {0, 0, 0, 0, 0};
   for (auto& e : b->sweep_ev) {
     RTE_CUDA_TRY(cudaEventSynchronize(e.second));
     float t = 0.f;
@@ -435,6 +435,9 @@ extern "C" int rte_batch_timing(rte_batch_t b, int enable, double* out) {
     out[9] = pms[0];
     out[10] = (double)b->phase_calls[0];
     out[11] = b->sweep32_units;
+    out[12] = pms[4];
+    out[13] = (double)b->phase_calls[4];
+    out[14] = b->sweepff_units;
   }
   if (enable >= 0) {
     for (auto& e : b->sweep_ev) {
@@ -450,6 +453,7 @@ extern "C" int rte_batch_timing(rte_batch_t b, int enable, double* out) {
     for (auto& c : b->phase_calls) c = 0;
     b->sweep_units = 0.0;
     b->sweep32_units = 0.0;
+    b->sweepff_units = 0.0;
     b->sweep_launches = 0;
     b->timing = enable != 0;
   }
@@ -609,6 +613,7 @@ extern "C" int rte_batch_set_params_device(rte_batch_t b, const double* sigma_t,
     PhaseScope ps(b, 3, st);
     RTE_TRY(setup_tables(b, st));
     b->tables32_stale = true;
+    b->tablesff_stale = true;
     RTE_TRY(dsa_setup(b, st));
   }
   RTE_CUDA_TRY(cudaMemcpyAsync(b->param_bad_h, b->param_bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -660,6 +665,7 @@ extern "C" int rte_batch_set_params(rte_batch_t b, const double* sigma_t, const 
     PhaseScope ps(b, 3, 0);
     RTE_TRY(setup_tables(b, 0));
     b->tables32_stale = true;
+    b->tablesff_stale = true;
     RTE_TRY(dsa_setup(b, 0));
   }
   RTE_CUDA_TRY(cudaDeviceSynchronize());
@@ -731,6 +737,7 @@ int set_slots(rte_batch_t b, int n, const int* slots, const double* sigma_t, con
     PhaseScope ps(b, 3, st);
     RTE_TRY(setup_tables(b, st, b->slot_mask.p));
     b->tables32_stale = true;
+    b->tablesff_stale = true;
     RTE_TRY(dsa_setup(b, st, b->slot_mask.p));
   }
   RTE_CUDA_TRY(cudaEventRecord(b->stage_ev, st));

@@ -182,6 +182,10 @@ struct rte_batch_s {
   rte::DevBuf<float> tables32, S32, partial32;
   bool tables32_stale = true;
   double sweep32_units = 0.0;
+  // float-float sweep state (the precision variant's outer sweeps), allocated on first use
+  rte::DevBuf<float> tablesff, Sff;
+  bool tablesff_stale = true;
+  double sweepff_units = 0.0;
   rte::DevBuf<unsigned long long> norms;  // [B][2] stop-test norms as ordered bit patterns
   rte::DevBuf<double> work;               // [B][n_dof] x 4 iteration scratch for rte_solve
   rte::DevBuf<double> outer;              // [2][B][n_dof] x0, y0 of the FP64 outer residual
@@ -211,8 +215,8 @@ struct rte_batch_s {
   double sweep_units = 0.0;   // cell x distinct-direction solves in the timed sweeps
   long long sweep_launches = 0;
   struct PhaseEv { int phase; cudaEvent_t a, b; };
-  std::vector<PhaseEv> phase_ev;   // phases: 0 FP32 sweep, 1 DSA, 2 ROM, 3 set-up
-  long long phase_calls[4] = {0, 0, 0, 0};
+  std::vector<PhaseEv> phase_ev;   // phases: 0 FP32 sweep, 1 DSA, 2 ROM, 3 set-up, 4 float-float sweep
+  long long phase_calls[5] = {0, 0, 0, 0, 0};
   size_t bytes() const;                   // device memory held by the batch
   ~rte_batch_s();
 };
@@ -300,6 +304,9 @@ int sweep_launch_f32(rte_batch_t bt, const double* rho_in, double* rho_out, cons
                      cudaStream_t st, int n_active, bool zero_norms = true,
                      const uint8_t* inner = nullptr, const double* x0 = nullptr,
                      const double* y0 = nullptr);
+// float-float sweep with source (the precision variant's outer sweeps), reduced in FP64
+int sweep_launch_ff(rte_batch_t bt, const double* rho_in, double* rho_out, const uint8_t* active,
+                    cudaStream_t st, int n_active, bool fuse_norms, bool zero_norms = true);
 int setup_tables(rte_batch_t b, cudaStream_t st, const uint8_t* mask = nullptr);
 // one FP64 sweep with source that also records each cell's net face outflow (bt->leak)
 int sweep_launch_leak(rte_batch_t bt, const double* rho_in, double* rho_out, const uint8_t* active,

@@ -276,7 +276,8 @@ extern "C" int rte_server_add_bucket(rte_server_t sv, rte_batch_t slots, rte_rom
   if (slots->disc->device != sv->device) return fail(RTE_EINVAL, "batch on another device");
   if (!(o->eps >= 0) || o->max_iter < 1 || o->sa < 0 || o->sa > 3 || !(o->fp32_switch >= 0) ||
       !(o->refine_kappa >= 0) || (o->refine_kappa > 0 && o->refine_inner < 1) ||
-      o->gang_wait < 0 || o->schedule || o->sa_history || o->verify)
+      o->gang_wait < 0 || o->schedule || o->sa_history || o->verify || o->outer_ff < 0 ||
+      o->outer_ff > 1)
     return fail(RTE_EINVAL, "rte_server_add_bucket: bad options");
   if (o->sa != RTE_SA_NONE && slots->disc->dim == 2 && (!(o->dsa_rtol >= 0) || o->dsa_max_it < 1))
     return fail(RTE_EINVAL, "rte_server_add_bucket: bad DSA tolerance");

@@ -134,8 +134,11 @@ int si_launch(SiState& s, cudaStream_t st, double* psi_cur, cudaEvent_t wait_ev)
   // training solves' psi capture)
   s.r_fused = s.o.sa != RTE_SA_NONE && bt->disc->dim == 2 && psi_cur == nullptr;
   bt->fuse_R = s.r_fused ? bt->work.p + 2 * nb : nullptr;
+  // the precision variant's FP64-grade sweeps in float-float arithmetic (rte_solve_opts.outer_ff)
+  const bool ff = s.o.outer_ff && (s.mixed || s.refine) && psi_cur == nullptr;
   if (n_lo == 0) {
-    RTE_TRY(sweep_launch(bt, rho_prev, rho_star, psi_cur, 1, s.dm.p, st, true, n_hi));
+    RTE_TRY(ff ? sweep_launch_ff(bt, rho_prev, rho_star, s.dm.p, st, n_hi, true)
+               : sweep_launch(bt, rho_prev, rho_star, psi_cur, 1, s.dm.p, st, true, n_hi));
   } else {
     RTE_CUDA_TRY(cudaMemsetAsync(bt->norms.p, 0, sizeof(unsigned long long) * 2 * B, st));
     const double* x0 = bt->outer.p;
@@ -143,7 +146,8 @@ int si_launch(SiState& s, cudaStream_t st, double* psi_cur, cudaEvent_t wait_ev)
     RTE_TRY(sweep_launch_f32(bt, rho_prev, rho_star, s.dm.p + B, st, n_lo, false,
                              n_in ? s.dm.p + 3 * B : nullptr, x0, y0));
     if (n_hi > 0)
-      RTE_TRY(sweep_launch(bt, rho_prev, rho_star, psi_cur, 1, s.dm.p + 2 * B, st, true, n_hi, false));
+      RTE_TRY(ff ? sweep_launch_ff(bt, rho_prev, rho_star, s.dm.p + 2 * B, st, n_hi, true, false)
+                 : sweep_launch(bt, rho_prev, rho_star, psi_cur, 1, s.dm.p + 2 * B, st, true, n_hi, false));
   }
   bt->started_ev = nullptr;
   bt->fuse_R = nullptr;
@@ -390,7 +394,7 @@ static int check_opts(rte_batch_t b, const rte_solve_opts* o, rte_rom_t rom_c) {
   RTE_TRY(params_ready(b, "rte_solve"));
   if (!(o->eps >= 0) || o->max_iter < 1 || o->sa < 0 || o->sa > 3 || !(o->fp32_switch >= 0) ||
       !(o->refine_kappa >= 0) || (o->refine_kappa > 0 && o->refine_inner < 1) || o->gang_wait < 0 ||
-      o->verify < 0 || o->verify > 1)
+      o->verify < 0 || o->verify > 1 || o->outer_ff < 0 || o->outer_ff > 1)
     return fail(RTE_EINVAL, "rte_solve: bad options");
   if (o->sa != RTE_SA_NONE && b->disc->dim == 2 && (!(o->dsa_rtol >= 0) || o->dsa_max_it < 1))
     return fail(RTE_EINVAL, "rte_solve: bad DSA tolerance");

@@ -1600,3 +1600,406 @@ extern "C" int rte_batch_autotune(rte_batch_t b, void* stream, int* n_entries, i
   DeviceGuard g(b->disc->device);
   return autotune(b, (cudaStream_t)stream, n_entries, table);
 }
+
+// ---- float-float sweep (the precision variant's outer sweeps) ------------------------------------
+//
+// The sweep and scalar-flux reduction of sweep2d_kernel in float-float arithmetic: every value is
+// an unevaluated sum hi + lo of two FP32 numbers (|lo| <= ulp(hi) / 2), about 48 significant
+// bits.  A sum uses Knuth's TwoSum (s + e = a + b exactly, six additions); a product uses the FMA
+// form of Dekker's exact product (fma(a, b, -p) is the rounding error of p = a * b); an FMA of two
+// such numbers is one exact product, the two cross terms, one TwoSum and a renormalisation, 15
+// FP32 operations.  On GB300 the FP32 pipe is about 60 times as wide as the FP64 pipe, so the 32
+// FMAs of a cell-direction solve take several times fewer pipe cycles this way than in FP64.  The
+// cell sources come from FP64 (rho and sigma_s in FP64, split once per cell), the per-group
+// partial sums go back to FP64 and are reduced by the FP64 sweep's kernel (with the stop-test
+// norms and the correction source), so only the sweep itself carries the float-float rounding
+// (~1e-14 relative per FMA): far below what the outer residual of the precision variant needs,
+// which is why its outer sweeps may run this way (rte_solve_opts.outer_ff).
+namespace rte {
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+// both signs flipped by one integer XOR (exact, and not on the FP32 pipe)
+__device__ __forceinline__ float2 neg2(float2 a) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra;\n\tmov.b64 ra, {%2, %3};\n\txor.b64 ra, ra, 0x8000000080000000;\n\t"
+      "mov.b64 {%0, %1}, ra;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y));
+  return d;
+}
+
+// Two float-float numbers side by side, (hi.x + lo.x, hi.y + lo.y), so that every step is one
+// packed instruction for both.  The asm statements are opaque to the compiler, so no addition is
+// contracted into an FMA or reassociated, which the error-free transformations rely on.
+struct FF2 {
+  float2 hi, lo;
+};
+
+// a * b + c
+__device__ __forceinline__ FF2 ff_fma2(const FF2& a, const FF2& b, const FF2& c) {
+  const float2 p = mul2(a.hi, b.hi);
+  float2 pe = fma2(a.hi, b.hi, neg2(p));   // exactly a.hi * b.hi - p
+  pe = fma2(a.hi, b.lo, pe);
+  pe = fma2(a.lo, b.hi, pe);
+  const float2 s = add2(p, c.hi);          // TwoSum: s + e = p + c.hi exactly
+  const float2 bv = sub2(s, p);
+  float2 e = add2(sub2(p, sub2(s, bv)), sub2(c.hi, bv));
+  e = add2(e, add2(pe, c.lo));
+  FF2 r;                                   // renormalised: |r.lo| <= ulp(r.hi) / 2
+  r.hi = add2(s, e);
+  r.lo = sub2(e, sub2(r.hi, s));
+  return r;
+}
+
+// a * b
+__device__ __forceinline__ FF2 ff_mul2(const FF2& a, const FF2& b) {
+  const float2 p = mul2(a.hi, b.hi);
+  float2 pe = fma2(a.hi, b.hi, neg2(p));
+  pe = fma2(a.hi, b.lo, pe);
+  pe = fma2(a.lo, b.hi, pe);
+  FF2 r;
+  r.hi = add2(p, pe);
+  r.lo = sub2(pe, sub2(r.hi, p));
+  return r;
+}
+
+__device__ __forceinline__ FF2 ff_pair(float h0, float h1, float l0, float l1) {
+  FF2 r;
+  r.hi = make_float2(h0, h1);
+  r.lo = make_float2(l0, l1);
+  return r;
+}
+
+// v = hi + lo with hi = v rounded to FP32 and lo the rest rounded to FP32
+__device__ __forceinline__ void ff_split(double v, float& hi, float& lo) {
+  hi = __double2float_rn(v);
+  lo = __double2float_rn(v - (double)hi);
+}
+
+// Float-float sweep tables: per (instance, material, direction) 32 floats, the 16 hi parts of
+// M^-1 in the pair-major order of tables_to_f32_kernel, then the 16 lo parts in the same order.
+__global__ void tables_to_ff_kernel(const double* t64, float* tff, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int k = (int)(i % kTab2D), row = k / 4, col = k % 4, pr = row / 2;
+  const int q = 8 * pr + 2 * col + (row - 2 * pr);
+  const size_t base = (i - k) * 2;
+  float h, l;
+  ff_split(t64[i], h, l);
+  tff[base + q] = h;
+  tff[base + kTab2D + q] = l;
+}
+
+// Cell sources S = Sigma_s rho + G in FP64 (as cell_source_kernel), stored split: per cell the 4
+// hi parts, then the 4 lo parts.
+__global__ void cell_source_ff_kernel(const double* __restrict__ rho, float* S,
+                                      const double* __restrict__ sigma_s,
+                                      const double* __restrict__ G0, const int32_t* __restrict__ mat,
+                                      const uint8_t* active, int n_cells, int n_mat) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  const double ss = sigma_s[(size_t)b * n_mat + mat[c]];
+  const double2* r = reinterpret_cast<const double2*>(rho + ((size_t)b * n_cells + c) * 4);
+  const double2 a = r[0], e = r[1];
+  const double v[4] = {fma(ss, a.x, G0[(size_t)b * n_cells + c]), ss * a.y, ss * e.x, ss * e.y};
+  float h[4], l[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) ff_split(v[k], h[k], l[k]);
+  float4* o = reinterpret_cast<float4*>(S) + ((size_t)b * n_cells + c) * 2;
+  o[0] = make_float4(h[0], h[1], h[2], h[3]);
+  o[1] = make_float4(l[0], l[1], l[2], l[3]);
+}
+
+struct Sweep2DFFArgs {
+  const float* S;           // [B][n_cells][8] split cell sources
+  double* partial;          // [running rank][n_groups][n_dof], as the FP64 sweep's
+  const uint8_t* active;
+  const float* tables;      // [B][n_mat][n_dirs][32] split sweep tables
+  const double* inflow;
+  const int32_t* mat;
+  const double* dirs;
+  const SweepGroup* groups;
+  int nx, ny, n_cells, n_dof, n_mat, n_dirs, n_groups;
+  double sq_area;
+  double ihx, ihy;          // 1 / h_x, 1 / h_y
+};
+
+// floats of the y-inflow line buffer ([nx][DPW][2 traces][hi, lo]) and of one material's tables
+// in shared memory (DPW directions of 32 floats, padded by 4 like tab32_stride)
+__host__ __device__ __forceinline__ int ybuf_ff_floats(int nx, int dpw) { return nx * dpw * 4; }
+__host__ __device__ __forceinline__ int tab_ff_stride(int dpw) { return dpw * 2 * kTab2D + 4; }
+
+// The wavefront of sweep2d_f32_kernel (lane = row of a block of 32 rows, one step per column,
+// the next step's material and sources loaded ahead), with the cell algebra of cell_solve in
+// float-float: right-hand side s + E_x t_x + E_y t_y, M^-1 applied column by column to the row
+// pairs (a0, a1), (a2, a3), the outflow traces and the weighted partial sums, each operation in
+// the order of the FP64 kernel.
+template <int DPW>
+__global__ void __launch_bounds__(32) sweep2d_ff_kernel(const Sweep2DFFArgs A) {
+  const int g = blockIdx.x, b = blockIdx.y, lane = threadIdx.x;
+  if (A.active && !A.active[b]) return;
+  const SweepGroup grp = A.groups[g];
+  const bool xneg = grp.quad & 1, yneg = (grp.quad & 2) != 0;
+  extern __shared__ float smf[];
+  float* ybuf = smf;
+  float* tab_s = smf + ybuf_ff_floats(A.nx, DPW);     // 16-byte aligned: nx * DPW * 4 floats
+  const int mstride = tab_ff_stride(DPW);
+  const int per_dir = 2 * kTab2D;
+  const float* __restrict__ tabg = A.tables + (size_t)b * A.n_mat * A.n_dirs * per_dir;
+  for (int e = lane; e < A.n_mat * DPW * per_dir; e += 32) {
+    const int m = e / (DPW * per_dir), r = e % (DPW * per_dir), dd = r / per_dir, k = r % per_dir;
+    tab_s[m * mstride + r] = dd < grp.nd ? tabg[((size_t)m * A.n_dirs + grp.d0 + dd) * per_dir + k] : 0.f;
+  }
+  __syncwarp();
+  // per direction: weight and inflow couplings (a = |v| / h, b = -s sqrt3 a), split
+  float wh[DPW], wl[DPW], axh[DPW], axl[DPW], bxh[DPW], bxl[DPW], ayh[DPW], ayl[DPW], byh[DPW],
+      byl[DPW];
+#pragma unroll
+  for (int dd = 0; dd < DPW; ++dd) {
+    const bool in = dd < grp.nd;
+    const double vx = in ? A.dirs[4 * (grp.d0 + dd)] : 0.0, vy = in ? A.dirs[4 * (grp.d0 + dd) + 1] : 0.0;
+    const double axd = fabs(vx) * A.ihx, ayd = fabs(vy) * A.ihy;
+    ff_split(in ? A.dirs[4 * (grp.d0 + dd) + 2] : 0.0, wh[dd], wl[dd]);
+    ff_split(axd, axh[dd], axl[dd]);
+    ff_split(ayd, ayh[dd], ayl[dd]);
+    ff_split((vx < 0 ? 1.7320508075688772 : -1.7320508075688772) * axd, bxh[dd], bxl[dd]);
+    ff_split((vy < 0 ? 1.7320508075688772 : -1.7320508075688772) * ayd, byh[dd], byl[dd]);
+  }
+  float s3h, s3l;
+  ff_split(1.7320508075688772, s3h, s3l);
+  const FF2 C3X = xneg ? ff_pair(-s3h, -s3h, -s3l, -s3l) : ff_pair(s3h, s3h, s3l, s3l);
+  const FF2 C3Y = yneg ? ff_pair(-s3h, -s3h, -s3l, -s3l) : ff_pair(s3h, s3h, s3l, s3l);
+  float gxh, gxl, gyh, gyl;
+  ff_split(A.inflow[4 * b + (xneg ? 1 : 0)] * A.sq_area, gxh, gxl);
+  ff_split(A.inflow[4 * b + (yneg ? 3 : 2)] * A.sq_area, gyh, gyl);
+  const int H = A.nx < 32 ? A.nx : 32;
+  const int nrb = (A.ny + H - 1) / H;
+  const int total = nrb * A.nx;
+  const float4* __restrict__ Sb = reinterpret_cast<const float4*>(A.S) + (size_t)b * A.n_cells * 2;
+  double* part = A.partial + ((size_t)active_rank(A.active, b) * A.n_groups + g) * A.n_dof;
+  // traces entering the next cell, per direction: x (from the left) and y (to the row below)
+  FF2 tx[DPW], typ[DPW];
+#pragma unroll
+  for (int dd = 0; dd < DPW; ++dd) tx[dd] = typ[dd] = ff_pair(0.f, 0.f, 0.f, 0.f);
+  auto cell_of = [&](int t_, int rb_) {
+    const int r_ = rb_ * H + lane;
+    return (yneg ? A.ny - 1 - r_ : r_) * A.nx + (xneg ? A.nx - 1 - t_ : t_);
+  };
+  int tn = 0, rbn = 0;
+  int m_next = 0;
+  float4 svh_next = make_float4(0.f, 0.f, 0.f, 0.f), svl_next = svh_next;
+  if (lane == 0 && H > 0 && A.ny > 0) {
+    const int c0 = cell_of(0, 0);
+    m_next = A.mat[c0], svh_next = Sb[2 * (size_t)c0], svl_next = Sb[2 * (size_t)c0 + 1];
+  }
+  for (int s = 0; s < total + H - 1; ++s) {
+    const int u = s - lane;
+    int t = 0, rb = 0;
+    if (u >= 0) {
+      t = tn, rb = rbn;
+      if (++tn == A.nx) tn = 0, ++rbn;
+    }
+    const bool inrange = lane < H && u >= 0 && u < total;
+    const int r = rb * H + lane;
+    const bool act = inrange && r < A.ny;
+    const int m = m_next;
+    const float4 svh = svh_next, svl = svl_next;
+    if (lane < H && u + 1 >= 0 && u + 1 < total && rbn * H + lane < A.ny) {
+      const int c1 = cell_of(tn, rbn);
+      m_next = A.mat[c1], svh_next = Sb[2 * (size_t)c1], svl_next = Sb[2 * (size_t)c1 + 1];
+    }
+    FF2 ty[DPW];
+#pragma unroll
+    for (int dd = 0; dd < DPW; ++dd) {
+      ty[dd].hi.x = __shfl_up_sync(0xffffffffu, typ[dd].hi.x, 1);
+      ty[dd].hi.y = __shfl_up_sync(0xffffffffu, typ[dd].hi.y, 1);
+      ty[dd].lo.x = __shfl_up_sync(0xffffffffu, typ[dd].lo.x, 1);
+      ty[dd].lo.y = __shfl_up_sync(0xffffffffu, typ[dd].lo.y, 1);
+    }
+    if (act) {
+      if (r == 0) {
+#pragma unroll
+        for (int dd = 0; dd < DPW; ++dd) ty[dd] = ff_pair(gyh, 0.f, gyl, 0.f);
+      } else if (lane == 0) {
+#pragma unroll
+        for (int dd = 0; dd < DPW; ++dd) {
+          const float4 v = *reinterpret_cast<const float4*>(ybuf + (t * DPW + dd) * 4);
+          ty[dd] = ff_pair(v.x, v.y, v.z, v.w);
+        }
+      }
+      if (t == 0) {
+#pragma unroll
+        for (int dd = 0; dd < DPW; ++dd) tx[dd] = ff_pair(gxh, 0.f, gxl, 0.f);
+      }
+      const int c = cell_of(t, rb);
+      const FF2 S01 = ff_pair(svh.x, svh.y, svl.x, svl.y);
+      const FF2 S23 = ff_pair(svh.z, svh.w, svl.z, svl.w);
+      FF2 acc01 = ff_pair(0.f, 0.f, 0.f, 0.f), acc23 = acc01;
+      const float4* Tm = reinterpret_cast<const float4*>(tab_s + m * mstride);
+#pragma unroll
+      for (int dd = 0; dd < DPW; ++dd) {
+        // every slot is computed; a slot beyond the group's directions has zero tables and
+        // weight and adds nothing
+        const float4* Th = Tm + dd * (per_dir / 4);
+        const float4* Tl = Th + kTab2D / 4;
+        // r0 = s0 + a_x t_x0 + a_y t_y0, r1 = s1 + b_x t_x0 + a_y t_y1 (and r2, r3 with t_x1, b_y)
+        const FF2 EX = ff_pair(axh[dd], bxh[dd], axl[dd], bxl[dd]);
+        const FF2 AY = ff_pair(ayh[dd], ayh[dd], ayl[dd], ayl[dd]);
+        const FF2 BY = ff_pair(byh[dd], byh[dd], byl[dd], byl[dd]);
+        const FF2 TX0 = ff_pair(tx[dd].hi.x, tx[dd].hi.x, tx[dd].lo.x, tx[dd].lo.x);
+        const FF2 TX1 = ff_pair(tx[dd].hi.y, tx[dd].hi.y, tx[dd].lo.y, tx[dd].lo.y);
+        const FF2 r01 = ff_fma2(AY, ty[dd], ff_fma2(EX, TX0, S01));
+        const FF2 r23 = ff_fma2(BY, ty[dd], ff_fma2(EX, TX1, S23));
+        const FF2 R0 = ff_pair(r01.hi.x, r01.hi.x, r01.lo.x, r01.lo.x);
+        const FF2 R1 = ff_pair(r01.hi.y, r01.hi.y, r01.lo.y, r01.lo.y);
+        const FF2 R2 = ff_pair(r23.hi.x, r23.hi.x, r23.lo.x, r23.lo.x);
+        const FF2 R3 = ff_pair(r23.hi.y, r23.hi.y, r23.lo.y, r23.lo.y);
+        const float4 h0 = Th[0], h1 = Th[1], h2 = Th[2], h3 = Th[3];
+        const float4 l0 = Tl[0], l1 = Tl[1], l2 = Tl[2], l3 = Tl[3];
+        FF2 a01 = ff_mul2(ff_pair(h0.x, h0.y, l0.x, l0.y), R0);
+        a01 = ff_fma2(ff_pair(h0.z, h0.w, l0.z, l0.w), R1, a01);
+        a01 = ff_fma2(ff_pair(h1.x, h1.y, l1.x, l1.y), R2, a01);
+        a01 = ff_fma2(ff_pair(h1.z, h1.w, l1.z, l1.w), R3, a01);
+        FF2 a23 = ff_mul2(ff_pair(h2.x, h2.y, l2.x, l2.y), R0);
+        a23 = ff_fma2(ff_pair(h2.z, h2.w, l2.z, l2.w), R1, a23);
+        a23 = ff_fma2(ff_pair(h3.x, h3.y, l3.x, l3.y), R2, a23);
+        a23 = ff_fma2(ff_pair(h3.z, h3.w, l3.z, l3.w), R3, a23);
+        // outflow traces: t_x = (a0 + c3x a1, a2 + c3x a3), t_y = (a0 + c3y a2, a1 + c3y a3)
+        tx[dd] = ff_fma2(C3X, ff_pair(a01.hi.y, a23.hi.y, a01.lo.y, a23.lo.y),
+                         ff_pair(a01.hi.x, a23.hi.x, a01.lo.x, a23.lo.x));
+        typ[dd] = ff_fma2(C3Y, a23, a01);
+        const FF2 W = ff_pair(wh[dd], wh[dd], wl[dd], wl[dd]);
+        acc01 = ff_fma2(W, a01, acc01);
+        acc23 = ff_fma2(W, a23, acc23);
+      }
+      double2* po = reinterpret_cast<double2*>(part + 4 * (size_t)c);
+      po[0] = make_double2((double)acc01.hi.x + (double)acc01.lo.x,
+                           (double)acc01.hi.y + (double)acc01.lo.y);
+      po[1] = make_double2((double)acc23.hi.x + (double)acc23.lo.x,
+                           (double)acc23.hi.y + (double)acc23.lo.y);
+      if (lane == H - 1 && rb + 1 < nrb) {
+#pragma unroll
+        for (int dd = 0; dd < DPW; ++dd)
+          *reinterpret_cast<float4*>(ybuf + (t * DPW + dd) * 4) =
+              make_float4(typ[dd].hi.x, typ[dd].hi.y, typ[dd].lo.x, typ[dd].lo.y);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <int DPW>
+static int launch2d_ff(const Sweep2DFFArgs& A, int B, int n_groups, cudaStream_t st) {
+  const size_t bytes =
+      ((size_t)ybuf_ff_floats(A.nx, DPW) + (size_t)A.n_mat * tab_ff_stride(DPW)) * sizeof(float);
+  if (bytes > 200 * 1024) return fail(RTE_EINVAL, "float-float sweep: shared memory exceeded");
+  if (bytes > 48 * 1024) {
+    RTE_CUDA_TRY(cudaFuncSetAttribute(sweep2d_ff_kernel<DPW>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  }
+  sweep2d_ff_kernel<DPW><<<dim3(n_groups, B), 32, bytes, st>>>(A); RTE_NOTE_LAUNCH();
+  RTE_CUDA_TRY(cudaGetLastError());
+  return RTE_OK;
+}
+
+// One float-float sweep with source of the active instances of a 2D batch, its partial sums
+// reduced in FP64 into rho_out by reduce_partials_kernel (with the stop-test norms when
+// fuse_norms, and the correction source when bt->fuse_R is set), as sweep_launch.  Directions
+// per warp: the FP64 sweep's choice for this running count, at most 4 (the float-float state of
+// 8 directions does not fit the registers of one thread); when the batch's partial-sum buffer
+// holds only the groups of 8 directions per warp, the FP64 sweep runs instead.
+int sweep_launch_ff(rte_batch_t bt, const double* rho_in, double* rho_out, const uint8_t* active,
+                    cudaStream_t st, int n_active, bool fuse_norms, bool zero_norms) {
+  const rte_disc_s* d = bt->disc;
+  if (d->dim != 2) return fail(RTE_EINVAL, "float-float sweep: 2D only");
+  if (n_active < 0) n_active = bt->B;
+  int dpw = bt->dpw, n_groups = 0;
+  const SweepGroup* gdev = nullptr;
+  pick_groups(bt, n_active, &dpw, &n_groups, &gdev);
+  if (dpw > 4) {
+    if (!bt->groups_all_dev.p ||
+        (size_t)std::max(n_active, 1) * bt->gcount[2] * d->n_dof > bt->partial.n)
+      return sweep_launch(bt, rho_in, rho_out, nullptr, 1, active, st, fuse_norms, n_active,
+                          zero_norms);
+    dpw = 4;
+    n_groups = bt->gcount[2];
+    gdev = bt->groups_all_dev.p + bt->goff[2];
+  }
+  if (!bt->tablesff.p) {
+    RTE_TRY(bt->tablesff.alloc(2 * bt->tables.n));
+    RTE_TRY(bt->Sff.alloc(2 * (size_t)bt->B * d->n_dof));
+    bt->tablesff_stale = true;
+  }
+  if (bt->tablesff_stale) {
+    const size_t n = bt->tables.n;
+    tables_to_ff_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(bt->tables.p, bt->tablesff.p, n); RTE_NOTE_LAUNCH();
+    bt->tablesff_stale = false;
+  }
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (bt->timing) {
+    RTE_CUDA_TRY(cudaEventCreate(&ev0));
+    RTE_CUDA_TRY(cudaEventCreate(&ev1));
+    RTE_CUDA_TRY(cudaEventRecord(ev0, st));
+  }
+  cell_source_ff_kernel<<<dim3((d->n_cells + 127) / 128, bt->B), 128, 0, st>>>(
+      rho_in, bt->Sff.p, bt->sigma_s.p, bt->G0.p, d->mat_id.p, active, d->n_cells, d->n_mat); RTE_NOTE_LAUNCH();
+  RTE_TRY(note_started(bt, st));
+  Sweep2DFFArgs A{bt->Sff.p,   bt->partial.p, active,    bt->tablesff.p, bt->inflow.p,
+                  d->mat_id.p, d->dir_dev.p,  gdev,      d->nx,          d->ny,
+                  d->n_cells,  d->n_dof,      d->n_mat,  d->n_dirs,      n_groups,
+                  std::sqrt(d->hx * d->hy),   1.0 / d->hx, 1.0 / d->hy};
+  switch (dpw) {
+    case 1: RTE_TRY(launch2d_ff<1>(A, bt->B, n_groups, st)); break;
+    case 2: RTE_TRY(launch2d_ff<2>(A, bt->B, n_groups, st)); break;
+    case 4: RTE_TRY(launch2d_ff<4>(A, bt->B, n_groups, st)); break;
+    default: return fail(RTE_EINVAL, "unsupported directions-per-warp");
+  }
+  if (bt->timing) {
+    RTE_CUDA_TRY(cudaEventRecord(ev1, st));
+    bt->phase_ev.push_back({4, ev0, ev1});
+    bt->phase_calls[4] += 1;
+    bt->sweepff_units += (double)n_active * d->n_cells * d->n_dirs;
+  }
+  if (fuse_norms && zero_norms)
+    RTE_CUDA_TRY(cudaMemsetAsync(bt->norms.p, 0, sizeof(unsigned long long) * 2 * bt->B, st));
+  const int th = 256;
+  dim3 grid((d->n_dof / 2 + th - 1) / th, bt->B);
+  reduce_partials_kernel<<<grid, th, 0, st>>>(bt->partial.p, rho_in, rho_out,
+                                             fuse_norms ? bt->norms.p : nullptr, active, n_groups,
+                                             d->n_dof, bt->fuse_R, bt->sigma_s.p, d->mat_id.p,
+                                             d->n_mat); RTE_NOTE_LAUNCH();
+  RTE_CUDA_TRY(cudaGetLastError());
+  return RTE_OK;
+}
+
+}  // namespace rte
+
+extern "C" int rte_sweep_ff(rte_batch_t b, const double* rho_in, double* rho_out,
+                            const uint8_t* active, void* stream) {
+  if (!b || !rho_in || !rho_out) return fail(RTE_EINVAL, "rte_sweep_ff: null argument");
+  RTE_TRY(params_ready(b, "rte_sweep_ff"));
+  if (b->disc->dim != 2) return fail(RTE_EINVAL, "rte_sweep_ff: 2D batches only");
+  if (rho_in == rho_out) return fail(RTE_EINVAL, "rte_sweep_ff: rho_out aliases rho_in");
+  if (((uintptr_t)rho_in | (uintptr_t)rho_out) & 15)
+    return fail(RTE_EINVAL, "rte_sweep_ff: arrays must be 16-byte aligned");
+  DeviceGuard g(b->disc->device);
+  // the group choice is sized for every instance running (the mask is device memory)
+  return sweep_launch_ff(b, rho_in, rho_out, active, (cudaStream_t)stream, b->B, false, false);
+}

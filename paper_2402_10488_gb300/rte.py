@@ -46,6 +46,7 @@ SIGNATURES = {
     "rte_residual": (_I, [_P, _P, _P, _P, _P, _P]),
     "rte_fma_peak": (_I, [_I, _I, _P, _P]),
     "rte_sweep_f32": (_I, [_P, _P, _P, _P, _P]),
+    "rte_sweep_ff": (_I, [_P, _P, _P, _P, _P]),
     "rte_change_norm": (_I, [_P, _P, _P, _P, _P]),
     "rte_dsa_correction": (_I, [_P, _P, _P, _D, _I, _P, _P, _P]),
     "rte_correction_source": (_I, [_P, _P, _P, _P, _P]),
@@ -169,7 +170,8 @@ class _SolveOpts(ctypes.Structure):
     _fields_ = [("eps", _D), ("rel", _I), ("max_iter", _I), ("sa", _I), ("theta", _I),
                 ("eps_romsad", _D), ("dsa_rtol", _D), ("dsa_max_it", _I), ("schedule", _P),
                 ("fp32_switch", _D), ("refine_kappa", _D), ("refine_inner", _I),
-                ("rom_bf16", _I), ("gang_wait", _I), ("verify", _I), ("sa_history", _P)]
+                ("rom_bf16", _I), ("gang_wait", _I), ("verify", _I), ("sa_history", _P),
+                ("outer_ff", _I)]
 
 
 class SolveReport(ctypes.Structure):
@@ -197,7 +199,7 @@ def _report(r):
 
 def solve_opts(eps, sa=SA_DSA, rel=False, max_iter=1000, theta=0, eps_romsad=0.0, dsa_rtol=1e-10,
                dsa_max_it=500, schedule=None, fp32_switch=0.0, refine_kappa=0.0, refine_inner=0,
-               gang_wait=0, rom_bf16=False, verify=False, sa_history=None):
+               gang_wait=0, rom_bf16=False, verify=False, sa_history=None, outer_ff=False):
     """rte_solve_opts; `schedule` (uint8 per iteration) and `sa_history` (a writable uint8 numpy
     array [B][max_iter]) are kept alive on the returned struct."""
     sched = None if schedule is None else _host(schedule, np.uint8)
@@ -208,7 +210,8 @@ def solve_opts(eps, sa=SA_DSA, rel=False, max_iter=1000, theta=0, eps_romsad=0.0
                    None if sched is None else sched.ctypes.data_as(_P), float(fp32_switch),
                    float(refine_kappa), int(refine_inner), 1 if rom_bf16 else 0, int(gang_wait),
                    1 if verify else 0,
-                   None if sa_history is None else sa_history.ctypes.data_as(_P))
+                   None if sa_history is None else sa_history.ctypes.data_as(_P),
+                   1 if outer_ff else 0)
     o._sched = sched
     o._hist = sa_history
     return o
@@ -362,13 +365,14 @@ class Batch:
     def timing(self, enable):
         """enable=1 reset+start, 0 reset+stop, -1 read.  Returns a dict of phase times (ms) and
         counts: sweep (kernel only), dsa, rom, setup."""
-        out = np.zeros(12)
+        out = np.zeros(15)
         check(lib().rte_batch_timing(self.h, int(enable), out.ctypes.data_as(_P)))
         return dict(sweep_ms=float(out[0]), sweep_launches=int(out[1]), sweep_units=float(out[2]),
                     dsa_ms=float(out[3]), dsa_calls=int(out[4]), rom_ms=float(out[5]),
                     rom_calls=int(out[6]), setup_ms=float(out[7]), setup_calls=int(out[8]),
                     sweep32_ms=float(out[9]), sweep32_launches=int(out[10]),
-                    sweep32_units=float(out[11]))
+                    sweep32_units=float(out[11]), sweepff_ms=float(out[12]),
+                    sweepff_launches=int(out[13]), sweepff_units=float(out[14]))
 
     def directions(self):
         d = np.zeros((self.disc.n_dirs, 4))
@@ -383,6 +387,11 @@ class Batch:
         """rte_sweep_f32: one FP32 sweep with source (2D), result in FP64."""
         check(lib().rte_sweep_f32(self.h, _ptr(rho_in), _ptr(rho_out), _ptr(active),
                                   _stream(stream)))
+
+    def sweep_ff(self, rho_in, rho_out, active=None, stream=None):
+        """rte_sweep_ff: one float-float sweep with source (2D), result in FP64."""
+        check(lib().rte_sweep_ff(self.h, _ptr(rho_in), _ptr(rho_out), _ptr(active),
+                                 _stream(stream)))
 
     def sweep_static(self, rho_in, rho_out, with_source=True, stream=None):
         """rte_sweep_static: the same sweep with the library's fixed scratch (no allocation)."""
@@ -407,13 +416,14 @@ class Batch:
     def solve(self, rho, eps, sa=SA_DSA, rel=False, max_iter=1000, theta=0, eps_romsad=0.0,
               dsa_rtol=1e-10, dsa_max_it=500, rom_c=None, schedule=None, history=False,
               fp32_switch=0.0, refine_kappa=0.0, refine_inner=0, gang_wait=0, rom_bf16=False,
-              verify=False, stream=None):
+              verify=False, outer_ff=False, stream=None):
         """rte_solve.  Returns (reports, hist, status); with history=True, hist is the change per
         sweep [B][max_iter] and each report also carries "sa_history", the codes of
         rte_solve_opts.sa_history for its n_sweep sweeps."""
         sah = np.zeros((self.B, max_iter), np.uint8) if history else None
         opts = solve_opts(eps, sa, rel, max_iter, theta, eps_romsad, dsa_rtol, dsa_max_it, schedule,
-                          fp32_switch, refine_kappa, refine_inner, gang_wait, rom_bf16, verify, sah)
+                          fp32_switch, refine_kappa, refine_inner, gang_wait, rom_bf16, verify, sah,
+                          outer_ff)
         reps = (SolveReport * self.B)()
         hist = np.zeros((self.B, max_iter)) if history else None
         st = check(lib().rte_solve(self.h, ctypes.byref(opts), None if rom_c is None else rom_c.h,

@@ -24,7 +24,7 @@ def test_library_builds_and_exports_every_declared_symbol():
     missing = [s for s in syms if not hasattr(L, s)]
     assert not missing, missing
     assert set(syms) == set(rte.SIGNATURES), set(syms) ^ set(rte.SIGNATURES)
-    assert L.rte_version() == 10800
+    assert L.rte_version() == 10900
 
 
 def test_calls_without_gpu_fail_cleanly():

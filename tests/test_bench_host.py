@@ -23,7 +23,10 @@ def test_precision_methods_map_to_solver_options(monkeypatch):
     o = rte.solve_opts(2e-7, rte.SA_ROMSAD, rel=True, theta=5, eps_romsad=1e-4, **kw)
     assert (o.fp32_switch, o.refine_kappa, o.refine_inner, o.gang_wait, o.rom_bf16) == \
         (1e-5, 0.1, 8, 4, 0)
-    assert o.sa == rte.SA_ROMSAD and o.rel == 1 and o.theta == 5
+    assert o.sa == rte.SA_ROMSAD and o.rel == 1 and o.theta == 5 and o.outer_ff == 0
+    kff = bench.precision_kw("romsad_refine_ff", a)
+    assert kff == dict(kw, outer_ff=True)
+    assert rte.solve_opts(2e-7, rte.SA_ROMSAD, rel=True, **kff).outer_ff == 1
 
 
 def test_default_bench_runs_every_method_on_one_sm_per_instance(monkeypatch):
@@ -31,7 +34,8 @@ def test_default_bench_runs_every_method_on_one_sm_per_instance(monkeypatch):
     assert a.batch == 152 and a.n == 128 and a.angles == 64 and a.rank == 20
     methods = a.methods.split(",")
     assert methods[0] == "romsad"
-    assert {"si_dsa", "romig", "romsad_mixed", "romsad_refine", "pgmres"} <= set(methods)
+    assert {"si_dsa", "romig", "romsad_mixed", "romsad_refine", "romsad_refine_ff",
+            "pgmres"} <= set(methods)
     assert a.warmup >= 3 and a.dsa_smoother == -1
 
 
