@@ -456,8 +456,9 @@ typedef struct {
                           (rho^(l,*) = y0 + L (rho^(l-1) - x0), so FP32 rounding only touches the
                           small e; the corrections are Alg. 1's), until the change falls below
                           refine_kappa x the FP64 change or refine_inner FP32 sweeps are done;
-                          then the next sweep is FP64 again.  Only FP64 sweeps take the stop
-                          test.  Combines with fp32_switch (its FP32 phase comes first).      */
+                          then the next sweep is FP64 again.  Only FP64 sweeps (float-float
+                          ones with outer_ff) take the stop test.  Combines with fp32_switch
+                          (its FP32 phase comes first).                                       */
   int refine_inner;    /* cap on the FP32 sweeps per outer step (>= 1 when refine_kappa > 0) */
   int rom_bf16;        /* 1: ROMSA's project and lift products (Eq. (rom_correction)) in BF16
                           on the tensor cores with FP32 accumulation (rte_pod_project_bf16,

@@ -14,7 +14,7 @@
 // e in FP32, rho^(l,*) = y0 + L (rho^(l-1) - x0), until the change is refine_kappa times smaller
 // than the FP64 one; then the next FP64 sweep evaluates the new residual.  FP32 rounding thus only
 // enters through e, which shrinks from one outer step to the next, and the stop test sees FP64
-// sweeps only.
+// sweeps only (with outer_ff those FP64-grade sweeps run in float-float arithmetic, sweep.cu).
 //
 // The iteration is a small state machine per batch (SiState): instances are slots that may
 // start at different iterations (serving), and si_launch / si_finish only enqueue work, so one
