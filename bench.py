@@ -129,7 +129,10 @@ def parse():
                          "with the paper's AMG) or by --dsa-vcycles FP32 V-cycles (speed)")
     ap.add_argument("--kappa", type=float, default=0.1,
                     help="mixed/serving: stop at relative change kappa * error target")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.impl == "ours" and a.workload == "lattice" and "romsad" not in a.methods.split(","):
+        ap.error("--methods must include romsad: the lattice workload's headline line is ROMSAD's")
+    return a
 
 
 def precision_kw(method, a):

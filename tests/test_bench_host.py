@@ -73,3 +73,15 @@ def test_cpu_baseline_leg_runs_one_instance_per_core(monkeypatch):
     cb = bench.cpu_baseline_leg(a, dict(n_sweep=4.4))
     assert cb["cores"] == bench.oracle_workers() and cb["value"] > 0
     assert "4 iterations" in cb["sample"]
+
+
+def test_lattice_methods_without_the_headline_are_refused(monkeypatch):
+    """The lattice workload's JSON line is ROMSAD's: a --methods list without it is refused with a
+    message at parse time instead of failing after the GPU work."""
+    import pytest
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--methods", "si_dsa,romsad_refine"])
+    with pytest.raises(SystemExit):
+        bench.parse()
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "mixed", "--methods", "si_dsa"])
+    assert bench.parse().methods == "si_dsa"
