@@ -479,8 +479,8 @@ typedef struct {
                           plus 0x10 when sweep l ran in FP32.  Entries past n_sweep untouched. */
   int outer_ff;        /* precision variant (fp32_switch or refine_kappa > 0): 1 -- its sweeps
                           that would run in FP64 run as float-float sweeps (rte_sweep_ff) on the
-                          FP32 units, so the stop test needs eps well above their ~1e-13
-                          rounding (1e-11 relative is tested); 0 -- in FP64.                  */
+                          FP32 units, so eps must stay above their rounding (a relative change
+                          of 1e-11 is tested to converge to the FP64 solution); 0 -- FP64.    */
 } rte_solve_opts;
 
 typedef struct {
